@@ -1,0 +1,826 @@
+/*
+ * bgk_oracle.c -- FP64 CPU oracle for one explicit SSP-RK3 step of the Boltzmann-BGK equation
+ * (Dzanic & Martinelli, Sec. 2). TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark use it to check and time the CUDA library; the library never
+ * calls it. Everything is plain FP64 loops in the order the paper states the method, with no
+ * blocking, fusion or reordering. OpenMP only splits the outer loop over elements or points.
+ *
+ * Readings of the paper taken here (the paper is silent or ambiguous on each):
+ *   - The Maxwellian exponent uses the velocity dimension m = 3 (Eq. 4 writes d/2).
+ *   - Monatomic gas, gamma = 5/3, so P = rho*theta and E = rho|U|^2/2 + 3/2 rho theta (Eq. 4).
+ *   - Velocity grid nodes include both endpoints; trapezoid weights; tensor product (Eq. 12).
+ *   - Correction functions: left/right Radau polynomials (Huynh's g_DG), which recover nodal DG.
+ *   - Interface flux points are the tensor Gauss-Legendre points of each face.
+ *   - Upwind tie u_n = 0 gives zero flux either way (Eq. 9).
+ *   - Conservative Maxwellian: Newton on (rho', U', theta') from the continuous state of Q,
+ *     scaled max-norm residual (mass / rho, momentum / (rho sqrt(theta)), energy / E).
+ *   - Boundaries (the paper gives none for this path): Dirichlet ghost = sampled continuous
+ *     Maxwellian of the prescribed state; diffuse wall ghost = rho_w * M(T_w, U_w) with rho_w
+ *     chosen per face point for zero net discrete mass flux.
+ *   - Body force: source g * (beta . psi) with (sum_k w g psi psi^T) beta = (0, rho F, rho U.F),
+ *     whose discrete moments are exactly those of -F . grad_xi f.
+ */
+#include "bgk_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define MAXN 16
+
+struct orc_ctx {
+    int dim, p, n1, np;     /* n1 = p + 1 nodes per direction, np = n1^dim nodes per element */
+    int ne[3];
+    double lo[3], hi[3], h[3];
+    int64_t nelem, npts;
+    int bc[6];
+    double bcs[30];
+    int nv[3];
+    int64_t nvel;
+    double *xi;             /* [nvel][3] */
+    double *w;              /* [nvel] */
+    double tau;
+    int collide;
+    double force[3];
+    int has_force;
+    double xg[MAXN], wg[MAXN], D[MAXN * MAXN], lm[MAXN], lp[MAXN], dgl[MAXN], dgr[MAXN];
+    double *f;              /* [npts][nvel] */
+    double *ghost;          /* [6][nvel]: Dirichlet ghost Maxwellian, or unit-density wall Maxwellian */
+    double newton_tol;
+    int newton_max;
+};
+
+/* ------------------------------------------------------------------------------------------ */
+/* Reference-element operators (Sec. 2.1, Eqs. 7-8)                                            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Legendre polynomial P_n(x) and its derivative by the three-term recurrence
+ * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} and P'_{k+1} = P'_{k-1} + (2k+1) P_k. */
+static void legendre(int n, double x, double *P, double *dP)
+{
+    double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+    if (n == 0) {
+        *P = 1.0;
+        *dP = 0.0;
+        return;
+    }
+    for (int k = 1; k < n; k++) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        double d2 = d0 + (2.0 * k + 1.0) * p1;
+        p0 = p1;
+        p1 = p2;
+        d0 = d1;
+        d1 = d2;
+    }
+    *P = p1;
+    *dP = d1;
+}
+
+int oracle_gauss_legendre(int n, double *x, double *w)
+{
+    if (n < 1 || n > MAXN || !x || !w)
+        return -1;
+    for (int i = 0; i < n; i++) {
+        /* roots of P_n by Newton from the usual cosine guess, then w = 2 / ((1 - x^2) P_n'(x)^2) */
+        double r = cos(ORC_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; it++) {
+            double P, dP;
+            legendre(n, r, &P, &dP);
+            double dr = P / dP;
+            r -= dr;
+            if (fabs(dr) < 1e-16)
+                break;
+        }
+        double P, dP;
+        legendre(n, r, &P, &dP);
+        x[n - 1 - i] = r;
+        w[n - 1 - i] = 2.0 / ((1.0 - r * r) * dP * dP);
+    }
+    return 0;
+}
+
+/* Lagrange basis polynomial l_j of the nodes x[0..n-1], evaluated at y. */
+static double lagrange(int n, const double *x, int j, double y)
+{
+    double v = 1.0;
+    for (int k = 0; k < n; k++)
+        if (k != j)
+            v *= (y - x[k]) / (x[j] - x[k]);
+    return v;
+}
+
+/* Derivative l_j'(y) by the product rule. */
+static double lagrange_deriv(int n, const double *x, int j, double y)
+{
+    double s = 0.0;
+    for (int m = 0; m < n; m++) {
+        if (m == j)
+            continue;
+        double t = 1.0 / (x[j] - x[m]);
+        for (int k = 0; k < n; k++)
+            if (k != j && k != m)
+                t *= (y - x[k]) / (x[j] - x[k]);
+        s += t;
+    }
+    return s;
+}
+
+int oracle_fr_operators(int p, double *D, double *lm, double *lp, double *dgl, double *dgr)
+{
+    int n = p + 1;
+    double x[MAXN], w[MAXN];
+    if (p < 0 || n > MAXN)
+        return -1;
+    oracle_gauss_legendre(n, x, w);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            D[i * n + j] = lagrange_deriv(n, x, j, x[i]);
+    for (int j = 0; j < n; j++) {
+        lm[j] = lagrange(n, x, j, -1.0);
+        lp[j] = lagrange(n, x, j, 1.0);
+    }
+    /* g_L = (-1)^p / 2 (P_p - P_{p+1}) and g_R = (P_p + P_{p+1}) / 2: g_L(-1) = 1, g_L(1) = 0 and
+     * mirror for g_R (Huynh's DG-recovering correction functions). */
+    double sgn = (p % 2 == 0) ? 1.0 : -1.0;
+    for (int i = 0; i < n; i++) {
+        double Pp, dPp, Pq, dPq;
+        legendre(p, x[i], &Pp, &dPp);
+        legendre(p + 1, x[i], &Pq, &dPq);
+        dgl[i] = 0.5 * sgn * (dPp - dPq);
+        dgr[i] = 0.5 * (dPp + dPq);
+    }
+    return 0;
+}
+
+int oracle_velocity_grid(const int *nv, const double *vlo, const double *vhi, double *xi, double *w)
+{
+    double x1[3][256], w1[3][256];
+    for (int d = 0; d < 3; d++) {
+        if (nv[d] < 2 || nv[d] > 256 || !(vhi[d] > vlo[d]))
+            return -1;
+        double dx = (vhi[d] - vlo[d]) / (nv[d] - 1);
+        for (int k = 0; k < nv[d]; k++) {
+            x1[d][k] = vlo[d] + k * dx;
+            w1[d][k] = (k == 0 || k == nv[d] - 1) ? 0.5 * dx : dx;
+        }
+    }
+    int64_t k = 0;
+    for (int kz = 0; kz < nv[2]; kz++)
+        for (int ky = 0; ky < nv[1]; ky++)
+            for (int kx = 0; kx < nv[0]; kx++, k++) {
+                xi[3 * k + 0] = x1[0][kx];
+                xi[3 * k + 1] = x1[1][ky];
+                xi[3 * k + 2] = x1[2][kz];
+                w[k] = w1[0][kx] * w1[1][ky] * w1[2][kz];
+            }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Maxwellian and moments (Sec. 2, Eqs. 2 and 4; Sec. 2.1, Eq. 12)                            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Continuous Maxwellian at velocity v for (rho, U, theta), velocity dimension 3. */
+static double maxwellian(double rho, const double *U, double theta, const double *v)
+{
+    double r2 = 0.0;
+    for (int d = 0; d < 3; d++)
+        r2 += (v[d] - U[d]) * (v[d] - U[d]);
+    return rho / pow(2.0 * ORC_PI * theta, 1.5) * exp(-r2 / (2.0 * theta));
+}
+
+static void psi_of(const double *v, double *psi)
+{
+    psi[0] = 1.0;
+    psi[1] = v[0];
+    psi[2] = v[1];
+    psi[3] = v[2];
+    psi[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+/* Q = sum_k w_k psi(xi_k) f_k for one point. */
+static void moments_point(const orc_ctx *c, const double *fp, double *Q)
+{
+    for (int m = 0; m < 5; m++)
+        Q[m] = 0.0;
+    for (int64_t k = 0; k < c->nvel; k++) {
+        double psi[5];
+        psi_of(c->xi + 3 * k, psi);
+        for (int m = 0; m < 5; m++)
+            Q[m] += c->w[k] * psi[m] * fp[k];
+    }
+}
+
+int oracle_moments_of(const orc_ctx *c, const double *f, double *Q)
+{
+    if (!c || !f || !Q)
+        return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < c->npts; i++)
+        moments_point(c, f + i * c->nvel, Q + 5 * i);
+    return 0;
+}
+
+int oracle_moments(const orc_ctx *c, double *Q) { return oracle_moments_of(c, c->f, Q); }
+
+int oracle_sample_maxwellian(const orc_ctx *c, const double *prim, double *g)
+{
+    if (!c || !prim || !g || !(prim[0] > 0) || !(prim[4] > 0))
+        return -1;
+    for (int64_t k = 0; k < c->nvel; k++)
+        g[k] = maxwellian(prim[0], prim + 1, prim[4], c->xi + 3 * k);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Discretely-conservative Maxwellian (Sec. 2.1, text after Eq. 13)                            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Solve A x = b (n x n, row-major, copied) by Gaussian elimination with partial pivoting. */
+static int solve_dense(int n, const double *A_in, const double *b_in, double *x)
+{
+    double A[25], b[5];
+    memcpy(A, A_in, sizeof(double) * n * n);
+    memcpy(b, b_in, sizeof(double) * n);
+    for (int col = 0; col < n; col++) {
+        int piv = col;
+        for (int r = col + 1; r < n; r++)
+            if (fabs(A[r * n + col]) > fabs(A[piv * n + col]))
+                piv = r;
+        if (A[piv * n + col] == 0.0 || !isfinite(A[piv * n + col]))
+            return -1;
+        if (piv != col) {
+            for (int k = 0; k < n; k++) {
+                double t = A[col * n + k];
+                A[col * n + k] = A[piv * n + k];
+                A[piv * n + k] = t;
+            }
+            double t = b[col];
+            b[col] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = col + 1; r < n; r++) {
+            double m = A[r * n + col] / A[col * n + col];
+            for (int k = col; k < n; k++)
+                A[r * n + k] -= m * A[col * n + k];
+            b[r] -= m * b[col];
+        }
+    }
+    for (int r = n - 1; r >= 0; r--) {
+        double s = b[r];
+        for (int k = r + 1; k < n; k++)
+            s -= A[r * n + k] * x[k];
+        x[r] = s / A[r * n + r];
+    }
+    return 0;
+}
+
+/* Residual G(P) = sum_k w_k psi_k g_k(P) - Q and, when J is non-NULL, its Jacobian with respect to
+ * P = (rho', U'x, U'y, U'z, theta'), written out from the closed-form derivatives of the Maxwellian:
+ * dg/drho' = g / rho', dg/dU'_d = g (xi_d - U'_d) / theta', dg/dtheta' = g (|xi - U'|^2 / (2 theta'^2)
+ * - 3 / (2 theta')). */
+static void newton_eval(const orc_ctx *c, const double *P, const double *Q, double *G, double *J)
+{
+    for (int m = 0; m < 5; m++)
+        G[m] = -Q[m];
+    if (J)
+        for (int m = 0; m < 25; m++)
+            J[m] = 0.0;
+    for (int64_t k = 0; k < c->nvel; k++) {
+        const double *v = c->xi + 3 * k;
+        double g = maxwellian(P[0], P + 1, P[4], v);
+        double psi[5];
+        psi_of(v, psi);
+        for (int m = 0; m < 5; m++)
+            G[m] += c->w[k] * psi[m] * g;
+        if (J) {
+            double r2 = 0.0, dg[5];
+            for (int d = 0; d < 3; d++)
+                r2 += (v[d] - P[1 + d]) * (v[d] - P[1 + d]);
+            dg[0] = g / P[0];
+            for (int d = 0; d < 3; d++)
+                dg[1 + d] = g * (v[d] - P[1 + d]) / P[4];
+            dg[4] = g * (r2 / (2.0 * P[4] * P[4]) - 1.5 / P[4]);
+            for (int m = 0; m < 5; m++)
+                for (int n = 0; n < 5; n++)
+                    J[m * 5 + n] += c->w[k] * psi[m] * dg[n];
+        }
+    }
+}
+
+static double scaled_norm(const double *G, const double *s)
+{
+    double r = 0.0;
+    for (int m = 0; m < 5; m++) {
+        double a = fabs(G[m]) / s[m];
+        if (!(a <= r))
+            r = a; /* also propagates NaN */
+    }
+    return r;
+}
+
+/* Newton for one point. Returns 0 when converged, -1 otherwise. */
+static int newton_point(const orc_ctx *c, const double *Q, double *P, int *iters, double *resid)
+{
+    double rho = Q[0];
+    double U[3] = {0, 0, 0}, theta = -1.0;
+    if (rho > 0) {
+        for (int d = 0; d < 3; d++)
+            U[d] = Q[1 + d] / rho;
+        theta = (2.0 / 3.0) * (Q[4] / rho - 0.5 * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]));
+    }
+    P[0] = rho;
+    P[1] = U[0];
+    P[2] = U[1];
+    P[3] = U[2];
+    P[4] = theta;
+    if (iters)
+        *iters = 0;
+    if (resid)
+        *resid = INFINITY;
+    if (!(rho > 0) || !(theta > 0) || !isfinite(rho) || !isfinite(theta))
+        return -1;
+    double s[5] = {rho, rho * sqrt(theta), rho * sqrt(theta), rho * sqrt(theta), fabs(Q[4])};
+    double G[5], J[25];
+    newton_eval(c, P, Q, G, J);
+    double res = scaled_norm(G, s);
+    int it = 0;
+    while (!(res <= c->newton_tol) && it < c->newton_max) {
+        double rhs[5], dP[5];
+        for (int m = 0; m < 5; m++)
+            rhs[m] = -G[m];
+        if (solve_dense(5, J, rhs, dP) != 0)
+            break;
+        it++;
+        /* full Newton step, halved only while it leaves the admissible set or raises the residual */
+        double lam = 1.0, Pt[5], Gt[5], Jt[25], rest = INFINITY;
+        int accepted = 0;
+        for (int h = 0; h < 40; h++, lam *= 0.5) {
+            for (int m = 0; m < 5; m++)
+                Pt[m] = P[m] + lam * dP[m];
+            if (!(Pt[0] > 0) || !(Pt[4] > 0))
+                continue;
+            newton_eval(c, Pt, Q, Gt, Jt);
+            rest = scaled_norm(Gt, s);
+            if (rest < res) {
+                accepted = 1;
+                break;
+            }
+        }
+        if (!accepted)
+            break;
+        memcpy(P, Pt, sizeof Pt);
+        memcpy(G, Gt, sizeof Gt);
+        memcpy(J, Jt, sizeof Jt);
+        res = rest;
+    }
+    if (iters)
+        *iters = it;
+    if (resid)
+        *resid = res;
+    /* a stalled line search at the round-off floor still counts as converged */
+    return (res <= c->newton_tol || res <= 1e-11) ? 0 : -1;
+}
+
+int oracle_conservative_maxwellian(const orc_ctx *c, int64_t n, const double *Q, double *prim_out,
+                                   int *iters, double *resid)
+{
+    if (!c || !Q || !prim_out || n < 0)
+        return -1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
+    for (int64_t i = 0; i < n; i++) {
+        int it;
+        double r;
+        if (newton_point(c, Q + 5 * i, prim_out + 5 * i, &it, &r) != 0)
+            bad++;
+        if (iters)
+            iters[i] = it;
+        if (resid)
+            resid[i] = r;
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Mesh and problem                                                                            */
+/* ------------------------------------------------------------------------------------------ */
+
+static int64_t ipow(int b, int e)
+{
+    int64_t r = 1;
+    for (int i = 0; i < e; i++)
+        r *= b;
+    return r;
+}
+
+orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double *hi, const int *bc,
+                       const double *bc_state, int p, const int *nv, const double *vlo,
+                       const double *vhi, double tau, const double *force)
+{
+    if (dim < 1 || dim > 3 || p < 0 || p + 1 > MAXN || !nelem || !lo || !hi || !nv || !vlo || !vhi)
+        return NULL;
+    orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+    if (!c)
+        return NULL;
+    c->dim = dim;
+    c->p = p;
+    c->n1 = p + 1;
+    c->np = (int)ipow(c->n1, dim);
+    c->nelem = 1;
+    for (int d = 0; d < 3; d++) {
+        c->ne[d] = (d < dim) ? nelem[d] : 1;
+        c->lo[d] = (d < dim) ? lo[d] : 0.0;
+        c->hi[d] = (d < dim) ? hi[d] : 1.0;
+        if (c->ne[d] < 1 || !(c->hi[d] > c->lo[d])) {
+            free(c);
+            return NULL;
+        }
+        c->h[d] = (c->hi[d] - c->lo[d]) / c->ne[d];
+        c->nelem *= c->ne[d];
+    }
+    c->npts = c->nelem * c->np;
+    for (int i = 0; i < 6; i++)
+        c->bc[i] = bc ? bc[i] : ORC_PERIODIC;
+    for (int i = 0; i < 30; i++)
+        c->bcs[i] = bc_state ? bc_state[i] : 0.0;
+    for (int d = 0; d < 3; d++)
+        c->nv[d] = nv[d];
+    c->nvel = (int64_t)nv[0] * nv[1] * nv[2];
+    c->xi = (double *)malloc(sizeof(double) * 3 * c->nvel);
+    c->w = (double *)malloc(sizeof(double) * c->nvel);
+    c->f = (double *)calloc((size_t)(c->npts * c->nvel), sizeof(double));
+    c->ghost = (double *)calloc((size_t)(6 * c->nvel), sizeof(double));
+    if (!c->xi || !c->w || !c->f || !c->ghost || oracle_velocity_grid(nv, vlo, vhi, c->xi, c->w) != 0) {
+        oracle_destroy(c);
+        return NULL;
+    }
+    c->tau = tau;
+    c->collide = (tau > 0.0 && isfinite(tau));
+    for (int d = 0; d < 3; d++)
+        c->force[d] = force ? force[d] : 0.0;
+    c->has_force = force && (force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0);
+    oracle_fr_operators(p, c->D, c->lm, c->lp, c->dgl, c->dgr);
+    oracle_gauss_legendre(c->n1, c->xg, c->wg);
+    c->newton_tol = 1e-13;
+    c->newton_max = 50;
+    /* ghost Maxwellians of non-periodic faces */
+    for (int fc = 0; fc < 6; fc++) {
+        if (fc / 2 >= dim)
+            continue;
+        const double *s = c->bcs + 5 * fc;
+        if (c->bc[fc] == ORC_DIRICHLET || c->bc[fc] == ORC_WALL) {
+            double rho = (c->bc[fc] == ORC_DIRICHLET) ? s[0] : 1.0;
+            if (!(rho > 0) || !(s[4] > 0)) {
+                oracle_destroy(c);
+                return NULL;
+            }
+            for (int64_t k = 0; k < c->nvel; k++)
+                c->ghost[fc * c->nvel + k] = maxwellian(rho, s + 1, s[4], c->xi + 3 * k);
+        } else if (c->bc[fc] != ORC_PERIODIC) {
+            oracle_destroy(c);
+            return NULL;
+        }
+    }
+    return c;
+}
+
+void oracle_destroy(orc_ctx *c)
+{
+    if (!c)
+        return;
+    free(c->xi);
+    free(c->w);
+    free(c->f);
+    free(c->ghost);
+    free(c);
+}
+
+int64_t oracle_npoints(const orc_ctx *c) { return c ? c->npts : -1; }
+int64_t oracle_nvel(const orc_ctx *c) { return c ? c->nvel : -1; }
+
+void oracle_set_newton(orc_ctx *c, double tol, int max_it)
+{
+    c->newton_tol = tol;
+    c->newton_max = max_it;
+}
+
+/* element coordinates (ex, ey, ez) <-> index, x fastest */
+static void elem_coords(const orc_ctx *c, int64_t e, int *ec)
+{
+    ec[0] = (int)(e % c->ne[0]);
+    ec[1] = (int)((e / c->ne[0]) % c->ne[1]);
+    ec[2] = (int)(e / ((int64_t)c->ne[0] * c->ne[1]));
+}
+
+static int64_t elem_index(const orc_ctx *c, const int *ec)
+{
+    return ec[0] + (int64_t)c->ne[0] * (ec[1] + (int64_t)c->ne[1] * ec[2]);
+}
+
+/* node (ix, iy, iz) -> index within an element, x fastest (unused directions 0) */
+static int node_index(const orc_ctx *c, const int *ic)
+{
+    int i = 0;
+    for (int d = c->dim - 1; d >= 0; d--)
+        i = i * c->n1 + ic[d];
+    return i;
+}
+
+int oracle_points(const orc_ctx *c, double *x)
+{
+    if (!c || !x)
+        return -1;
+    for (int64_t e = 0; e < c->nelem; e++) {
+        int ec[3];
+        elem_coords(c, e, ec);
+        for (int i = 0; i < c->np; i++) {
+            int ic[3] = {0, 0, 0}, t = i;
+            for (int d = 0; d < c->dim; d++) {
+                ic[d] = t % c->n1;
+                t /= c->n1;
+            }
+            double *xp = x + 3 * (e * c->np + i);
+            for (int d = 0; d < 3; d++)
+                xp[d] = (d < c->dim) ? c->lo[d] + (ec[d] + 0.5 * (c->xg[ic[d]] + 1.0)) * c->h[d] : 0.0;
+        }
+    }
+    return 0;
+}
+
+int oracle_set_state(orc_ctx *c, const double *prim)
+{
+    if (!c || !prim)
+        return -1;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t i = 0; i < c->npts; i++) {
+        const double *s = prim + 5 * i;
+        if (!(s[0] > 0) || !(s[4] > 0)) {
+            bad++;
+            continue;
+        }
+        for (int64_t k = 0; k < c->nvel; k++)
+            c->f[i * c->nvel + k] = maxwellian(s[0], s + 1, s[4], c->xi + 3 * k);
+    }
+    return bad ? -2 : 0;
+}
+
+int oracle_set_f(orc_ctx *c, const double *f)
+{
+    if (!c || !f)
+        return -1;
+    memcpy(c->f, f, sizeof(double) * (size_t)(c->npts * c->nvel));
+    return 0;
+}
+
+int oracle_get_f(const orc_ctx *c, double *f)
+{
+    if (!c || !f)
+        return -1;
+    memcpy(f, c->f, sizeof(double) * (size_t)(c->npts * c->nvel));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* FR advection residual with the upwind flux (Sec. 2.1, Eqs. 7-9)                             */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Exterior value seen from the face (direction d, side) of the element at ec, for the face point
+ * whose node coordinates along the other directions are ic (ic[d] ignored), velocity k.
+ * Periodic / interior faces: the neighbour's trace interpolated to the shared face.
+ * Dirichlet: the ghost Maxwellian. Wall: rho_w * unit-density wall Maxwellian, rho_w from zero net
+ * discrete mass flux through this face point (computed by the caller and passed as rho_w). */
+static double exterior_value(const orc_ctx *c, const double *f, const int *ec, int d, int side,
+                             const int *ic, int64_t k, double rho_w)
+{
+    int nc[3] = {ec[0], ec[1], ec[2]};
+    nc[d] += side ? 1 : -1;
+    int fc = 2 * d + side;
+    if (nc[d] < 0 || nc[d] >= c->ne[d]) {
+        if (c->bc[fc] == ORC_DIRICHLET)
+            return c->ghost[fc * c->nvel + k];
+        if (c->bc[fc] == ORC_WALL)
+            return rho_w * c->ghost[fc * c->nvel + k];
+        nc[d] = (nc[d] + c->ne[d]) % c->ne[d];
+    }
+    int64_t en = elem_index(c, nc);
+    /* the neighbour's trace at its face opposite to ours: its +1 end if we look left, -1 if right */
+    const double *l = side ? c->lm : c->lp;
+    double t = 0.0;
+    int jc[3] = {ic[0], ic[1], ic[2]};
+    for (int j = 0; j < c->n1; j++) {
+        jc[d] = j;
+        t += l[j] * f[(en * c->np + node_index(c, jc)) * c->nvel + k];
+    }
+    return t;
+}
+
+/* Interior trace of the element at the face (d, side), face point ic, velocity k. */
+static double interior_trace(const orc_ctx *c, const double *f, int64_t e, int d, int side,
+                             const int *ic, int64_t k)
+{
+    const double *l = side ? c->lp : c->lm;
+    double t = 0.0;
+    int jc[3] = {ic[0], ic[1], ic[2]};
+    for (int j = 0; j < c->n1; j++) {
+        jc[d] = j;
+        t += l[j] * f[(e * c->np + node_index(c, jc)) * c->nvel + k];
+    }
+    return t;
+}
+
+/* Wall density at a face point: sum over outgoing velocities of w |xi_n| f_trace divided by the
+ * sum over incoming velocities of w |xi_n| M_w (unit density). Outgoing = leaving the domain. */
+static double wall_density(const orc_ctx *c, const double *f, int64_t e, int d, int side, const int *ic)
+{
+    int fc = 2 * d + side;
+    double out = 0.0, in = 0.0;
+    for (int64_t k = 0; k < c->nvel; k++) {
+        double un = side ? c->xi[3 * k + d] : -c->xi[3 * k + d]; /* xi . n_out */
+        if (un > 0)
+            out += c->w[k] * un * interior_trace(c, f, e, d, side, ic, k);
+        else if (un < 0)
+            in += c->w[k] * (-un) * c->ghost[fc * c->nvel + k];
+    }
+    return out / in;
+}
+
+int oracle_residual(const orc_ctx *c, const double *f, double *R)
+{
+    if (!c || !f || !R)
+        return -1;
+    const int n1 = c->n1;
+    memset(R, 0, sizeof(double) * (size_t)(c->npts * c->nvel));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < c->nelem; e++) {
+        int ec[3];
+        elem_coords(c, e, ec);
+        for (int d = 0; d < c->dim; d++) {
+            int nlines = (int)ipow(n1, c->dim - 1);
+            for (int ln = 0; ln < nlines; ln++) {
+                /* node coordinates of this line along the directions other than d */
+                int ic[3] = {0, 0, 0}, t = ln;
+                for (int q = 0; q < c->dim; q++) {
+                    if (q == d)
+                        continue;
+                    ic[q] = t % n1;
+                    t /= n1;
+                }
+                int64_t pts[MAXN];
+                for (int j = 0; j < n1; j++) {
+                    int jc[3] = {ic[0], ic[1], ic[2]};
+                    jc[d] = j;
+                    pts[j] = e * c->np + node_index(c, jc);
+                }
+                /* wall densities of the two faces of this line, if they are walls */
+                double rw[2] = {0.0, 0.0};
+                for (int side = 0; side < 2; side++) {
+                    int edge = side ? (ec[d] == c->ne[d] - 1) : (ec[d] == 0);
+                    if (edge && c->bc[2 * d + side] == ORC_WALL)
+                        rw[side] = wall_density(c, f, e, d, side, ic);
+                }
+                for (int64_t k = 0; k < c->nvel; k++) {
+                    double a = c->xi[3 * k + d];
+                    double fl[MAXN];
+                    for (int j = 0; j < n1; j++)
+                        fl[j] = f[pts[j] * c->nvel + k];
+                    double fL = 0.0, fR = 0.0;
+                    for (int j = 0; j < n1; j++) {
+                        fL += c->lm[j] * fl[j];
+                        fR += c->lp[j] * fl[j];
+                    }
+                    /* upwind common fluxes (Eq. 9) expressed as fluxes in +x_d */
+                    double FL, FR;
+                    if (a > 0) {
+                        FL = a * exterior_value(c, f, ec, d, 0, ic, k, rw[0]);
+                        FR = a * fR;
+                    } else {
+                        FL = a * fL;
+                        FR = a * exterior_value(c, f, ec, d, 1, ic, k, rw[1]);
+                    }
+                    for (int i = 0; i < n1; i++) {
+                        double dF = 0.0;
+                        for (int j = 0; j < n1; j++)
+                            dF += c->D[i * n1 + j] * a * fl[j];
+                        dF += (FL - a * fL) * c->dgl[i] + (FR - a * fR) * c->dgr[i];
+                        R[pts[i] * c->nvel + k] -= (2.0 / c->h[d]) * dF;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* BGK relaxation and SSP-RK3 (Sec. 2, Eq. 3; Sec. 2.2)                                        */
+/* ------------------------------------------------------------------------------------------ */
+
+int oracle_rhs(const orc_ctx *c, const double *f, double *L)
+{
+    if (oracle_residual(c, f, L) != 0)
+        return -1;
+    if (!c->collide && !c->has_force)
+        return 0;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : bad)
+    for (int64_t i = 0; i < c->npts; i++) {
+        const double *fp = f + i * c->nvel;
+        double *Lp = L + i * c->nvel;
+        double Q[5], P[5];
+        moments_point(c, fp, Q);
+        if (newton_point(c, Q, P, NULL, NULL) != 0) {
+            bad++;
+            continue;
+        }
+        double beta[5] = {0, 0, 0, 0, 0};
+        if (c->has_force) {
+            /* (sum_k w g psi psi^T) beta = (0, rho F, rho U . F) */
+            double A[25] = {0}, b[5];
+            for (int64_t k = 0; k < c->nvel; k++) {
+                double g = maxwellian(P[0], P + 1, P[4], c->xi + 3 * k), psi[5];
+                psi_of(c->xi + 3 * k, psi);
+                for (int m = 0; m < 5; m++)
+                    for (int n = 0; n < 5; n++)
+                        A[m * 5 + n] += c->w[k] * g * psi[m] * psi[n];
+            }
+            double rho = Q[0];
+            b[0] = 0.0;
+            for (int d = 0; d < 3; d++)
+                b[1 + d] = rho * c->force[d];
+            b[4] = Q[1] * c->force[0] + Q[2] * c->force[1] + Q[3] * c->force[2];
+            if (solve_dense(5, A, b, beta) != 0) {
+                bad++;
+                continue;
+            }
+        }
+        for (int64_t k = 0; k < c->nvel; k++) {
+            double g = maxwellian(P[0], P + 1, P[4], c->xi + 3 * k);
+            if (c->collide)
+                Lp[k] += (g - fp[k]) / c->tau;
+            if (c->has_force) {
+                double psi[5], s = 0.0;
+                psi_of(c->xi + 3 * k, psi);
+                for (int m = 0; m < 5; m++)
+                    s += beta[m] * psi[m];
+                Lp[k] += g * s;
+            }
+        }
+    }
+    return bad ? -bad : 0;
+}
+
+int oracle_step(orc_ctx *c, double dt, int nsteps)
+{
+    if (!c || nsteps < 0 || !(dt > 0))
+        return -1;
+    size_t n = (size_t)(c->npts * c->nvel);
+    double *f1 = (double *)malloc(sizeof(double) * n);
+    double *f2 = (double *)malloc(sizeof(double) * n);
+    double *L = (double *)malloc(sizeof(double) * n);
+    if (!f1 || !f2 || !L) {
+        free(f1);
+        free(f2);
+        free(L);
+        return -1;
+    }
+    int fails = 0;
+    double *f = c->f;
+    for (int s = 0; s < nsteps; s++) {
+        /* Shu-Osher SSP-RK3 */
+        fails += -oracle_rhs(c, f, L);
+#pragma omp parallel for schedule(static)
+        for (size_t q = 0; q < n; q++)
+            f1[q] = f[q] + dt * L[q];
+        fails += -oracle_rhs(c, f1, L);
+#pragma omp parallel for schedule(static)
+        for (size_t q = 0; q < n; q++)
+            f2[q] = 0.75 * f[q] + 0.25 * (f1[q] + dt * L[q]);
+        fails += -oracle_rhs(c, f2, L);
+#pragma omp parallel for schedule(static)
+        for (size_t q = 0; q < n; q++)
+            f[q] = (1.0 / 3.0) * f[q] + (2.0 / 3.0) * (f2[q] + dt * L[q]);
+    }
+    free(f1);
+    free(f2);
+    free(L);
+    return fails ? -fails : 0;
+}
+
+double oracle_dt(const orc_ctx *c, double cfl)
+{
+    double smax = 0.0;
+    for (int64_t k = 0; k < c->nvel; k++) {
+        double s = 0.0;
+        for (int d = 0; d < c->dim; d++)
+            s += fabs(c->xi[3 * k + d]) / c->h[d];
+        if (s > smax)
+            smax = s;
+    }
+    double dt = cfl / smax;
+    if (c->collide && c->tau < dt)
+        dt = c->tau;
+    return dt;
+}

@@ -1,0 +1,107 @@
+/*
+ * bgk_oracle.h -- FP64 CPU oracle for the Boltzmann-BGK hot path of Dzanic & Martinelli,
+ * "Towards full molecular gas dynamics simulations of complex flows via the Boltzmann equation".
+ *
+ * TEST INFRASTRUCTURE ONLY. This is the slow, plain reference that the CUDA library is checked
+ * against. Only the test suite, the smoke check and the CPU-baseline leg of the benchmark load it.
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * What it computes (paper section / equation):
+ *   - Gauss-Legendre solution points, Lagrange derivative matrix, end interpolants and the
+ *     DG-recovering (Radau) correction-function derivatives of flux reconstruction (Sec. 2.1, Eqs. 7-8).
+ *   - The upwind common interface flux (Sec. 2.1, Eq. 9) and the FR advection residual of every
+ *     velocity node on a structured affine line/hex mesh (Sec. 2.1, Eqs. 6-9).
+ *   - The uniform velocity grid with trapezoid weights (Sec. 2.1 "Velocity discretization", Eq. 12),
+ *     the moments Q = M[f psi] (Sec. 2, Eq. 2; Eq. 12).
+ *   - The discretely-conservative Maxwellian: a Maxwellian at a perturbed state (rho', U', theta')
+ *     found by Newton's method with a closed-form Jacobian so that its discrete moments equal Q
+ *     (Sec. 2.1, the text after Eq. 13).
+ *   - The BGK relaxation (g - f)/tau (Sec. 2, Eq. 3) and explicit SSP-RK3 time stepping (Sec. 2.2).
+ *
+ * Conventions: all arrays are FP64 and caller-owned. Point order = element-major (element index
+ * x-fastest), then node index x-fastest. Velocity order k = kx + nx*(ky + ny*kz). f is [n_x][N_v].
+ * Functions return 0 on success and a negative value on bad arguments or failure.
+ */
+#ifndef BGK_ORACLE_H
+#define BGK_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* boundary kinds, one per (direction, side) */
+#define ORC_PERIODIC 0
+#define ORC_DIRICHLET 1
+#define ORC_WALL 2
+
+typedef struct orc_ctx orc_ctx;
+
+/* Gauss-Legendre nodes x[n] and weights w[n] on [-1, 1]. */
+int oracle_gauss_legendre(int n, double *x, double *w);
+
+/* FR reference operators for degree p (n = p + 1 nodes):
+ *   D[i*n + j] = l_j'(x_i), lm[j] = l_j(-1), lp[j] = l_j(+1),
+ *   dgl[i] = g_L'(x_i), dgr[i] = g_R'(x_i) for the left/right Radau correction functions
+ *   (Huynh's g_DG, which makes FR identical to nodal DG). */
+int oracle_fr_operators(int p, double *D, double *lm, double *lp, double *dgl, double *dgr);
+
+/* Uniform velocity grid, endpoints included, tensor trapezoid weights.
+ * nv[3] nodes per axis on [vlo, vhi]; xi is [N_v][3], w is [N_v]. */
+int oracle_velocity_grid(const int *nv, const double *vlo, const double *vhi, double *xi, double *w);
+
+/* Create a problem. dim in {1,2,3}; nelem[dim], lo[dim], hi[dim] describe an affine structured mesh.
+ * bc[2*d + side] is ORC_PERIODIC / ORC_DIRICHLET / ORC_WALL; bc_state[(2*d+side)*5 + c] holds
+ * (rho, u, v, w, T) of a Dirichlet state or (unused, u_w, v_w, w_w, T_w) of a wall.
+ * tau <= 0 or tau = +inf switches the collision term off (pure advection).
+ * force[3] is a constant body force per unit mass (may be NULL). Returns NULL on error. */
+orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double *hi,
+                       const int *bc, const double *bc_state, int p,
+                       const int *nv, const double *vlo, const double *vhi,
+                       double tau, const double *force);
+void oracle_destroy(orc_ctx *c);
+int64_t oracle_npoints(const orc_ctx *c);
+int64_t oracle_nvel(const orc_ctx *c);
+
+/* Node coordinates, [n_x][3] (unused components 0). */
+int oracle_points(const orc_ctx *c, double *x);
+
+/* Set f to the sampled continuous Maxwellian of prim [n_x][5] = (rho, u, v, w, T). */
+int oracle_set_state(orc_ctx *c, const double *prim);
+int oracle_set_f(orc_ctx *c, const double *f);
+int oracle_get_f(const orc_ctx *c, double *f);
+
+/* Moments Q [n_x][5] = (rho, rho u, rho v, rho w, E) of the current f (Eq. 2 with Eq. 12). */
+int oracle_moments(const orc_ctx *c, double *Q);
+
+/* Moments of an arbitrary f [n_x][N_v]. */
+int oracle_moments_of(const orc_ctx *c, const double *f, double *Q);
+
+/* Advection residual R = -xi . grad f of an arbitrary f (FR, upwind flux, boundary ghosts). */
+int oracle_residual(const orc_ctx *c, const double *f, double *R);
+
+/* Discretely-conservative Maxwellian for n moment vectors Q[n][5] on this problem's velocity grid.
+ * prim_out[n][5] = (rho', U'x, U'y, U'z, theta'); iters[n] and resid[n] (scaled max-norm) may be NULL.
+ * Returns the number of points that did not converge (0 on success), negative on bad input. */
+int oracle_conservative_maxwellian(const orc_ctx *c, int64_t n, const double *Q, double *prim_out,
+                                   int *iters, double *resid);
+
+/* Sample the Maxwellian of prim (rho, U, theta) on the velocity grid: g[N_v]. */
+int oracle_sample_maxwellian(const orc_ctx *c, const double *prim, double *g);
+
+/* The right-hand side L(f) = R_adv(f) + (g[f] - f)/tau (+ body-force source) of an arbitrary f. */
+int oracle_rhs(const orc_ctx *c, const double *f, double *L);
+
+/* Advance the stored f by nsteps SSP-RK3 steps of size dt. Returns 0, or the negative count of
+ * Newton failures met. */
+int oracle_step(orc_ctx *c, double dt, int nsteps);
+
+/* Largest stable explicit step: min(cfl / max_k sum_d |xi_kd| / h_d, tau). */
+double oracle_dt(const orc_ctx *c, double cfl);
+
+/* Newton tolerance and iteration cap used by the conservative Maxwellian (defaults 1e-13, 50). */
+void oracle_set_newton(orc_ctx *c, double tol, int max_it);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

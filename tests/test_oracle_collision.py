@@ -1,0 +1,254 @@
+"""Pins of the oracle's moments, discretely-conservative Maxwellian, BGK relaxation, SSP-RK3 and
+boundary/force terms (paper Sec. 2, Eqs. 2-4; Sec. 2.1 Eq. 12 and the text after Eq. 13; Sec. 2.2)
+against closed forms, an independent convex solver and conservation laws. CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import optimize
+
+from oracle import oracle as orc
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_facts.json")))
+INF = float("inf")
+
+
+def vproblem(n=16, L=6.0, tau=1.0, dim=1, ne=(1,), p=0, **kw):
+    return orc.Problem(dim, list(ne), [0.0] * dim, [1.0] * dim, p, (n, n, n), (-L,) * 3, (L,) * 3, tau, **kw)
+
+
+def maxwell(xi, rho, U, th):
+    # Eq. 4 with the velocity dimension 3
+    return rho / (2 * np.pi * th) ** 1.5 * np.exp(-((xi - np.asarray(U)) ** 2).sum(1) / (2 * th))
+
+
+def psi(xi):
+    return np.stack([np.ones(len(xi)), xi[:, 0], xi[:, 1], xi[:, 2], 0.5 * (xi**2).sum(1)], 1)
+
+
+def test_sampled_maxwellian_moments_closed_form():
+    pr = vproblem(n=24, L=8.0)
+    rho, U, th = 1.3, np.array([0.2, -0.1, 0.3]), 0.9
+    f = pr.sample_maxwellian([rho, *U, th])
+    assert np.allclose(f, maxwell(pr.xi, rho, U, th), rtol=1e-14, atol=0)
+    Q = pr.moments(np.tile(f, (pr.npts, 1)))[0]
+    E = 0.5 * rho * U @ U + 1.5 * rho * th  # gamma = 5/3: P = rho theta
+    assert np.allclose(Q, [rho, *(rho * U), E], rtol=1e-12, atol=1e-13)
+
+
+def test_paper_velocity_extent_holds_99_percent():
+    # an extent of 4x the thermal velocity keeps >= 99% of a Maxwellian's mass inside the grid
+    k = GOLD["velocity_extent_over_max_thermal_velocity"]
+    th = 1.7
+    L = k * math.sqrt(th)
+    pr = vproblem(n=48, L=L)
+    f = pr.sample_maxwellian([1.0, 0, 0, 0, th])
+    mass = (pr.w * f).sum()
+    assert mass >= GOLD["mass_fraction_inside_extent_min"]
+    # the box integral is erf(k/sqrt 2)^3; the trapezoid rule on the truncated box differs from it
+    # by the Euler-Maclaurin end term dv^2/12 (f'(L) - f'(-L)) per axis (in units of sqrt(theta))
+    dv = 2 * k / 47
+    em = dv**2 / 12 * 2 * k * math.exp(-k * k / 2) / math.sqrt(2 * math.pi)
+    assert abs(mass - math.erf(k / math.sqrt(2)) ** 3) < 3 * em * 1.05
+
+
+def _states(pr, n, rng):
+    """Seeded non-equilibrium distributions: sums of two Maxwellians."""
+    fs = []
+    for _ in range(n):
+        a = maxwell(pr.xi, rng.uniform(0.5, 1.5), rng.uniform(-0.8, 0.8, 3), rng.uniform(0.5, 1.5))
+        b = maxwell(pr.xi, rng.uniform(0.1, 0.8), rng.uniform(-1.0, 1.0, 3), rng.uniform(0.3, 1.2))
+        fs.append(a + b)
+    return np.array(fs)
+
+
+def test_conservative_maxwellian_matches_moments():
+    pr = vproblem(n=16, L=6.0)
+    rng = np.random.default_rng(5)
+    f = _states(pr, 40, rng)
+    Q = f @ (pr.w[:, None] * psi(pr.xi))
+    P, it, res, bad = pr.conservative_maxwellian(Q)
+    assert bad == 0
+    for q, pp in zip(Q, P):
+        g = maxwell(pr.xi, pp[0], pp[1:4], pp[4])
+        Qg = (pr.w * g) @ psi(pr.xi)
+        assert np.all(np.abs(Qg - q) <= 1e-12 * np.abs(q).max())
+
+
+def test_fixed_point_sampled_maxwellian():
+    # a sampled Maxwellian is its own discrete equilibrium: Newton returns its parameters
+    pr = vproblem(n=8, L=4.0)
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        rho, U, th = rng.uniform(0.5, 2.0), rng.uniform(-0.5, 0.5, 3), rng.uniform(0.6, 1.4)
+        f = maxwell(pr.xi, rho, U, th)
+        Q = (pr.w * f) @ psi(pr.xi)
+        P, it, res, bad = pr.conservative_maxwellian(Q[None])
+        assert bad == 0
+        assert np.allclose(P[0], [rho, *U, th], rtol=1e-10, atol=1e-11)
+
+
+def test_agrees_with_independent_convex_solver():
+    # uniqueness: the conservative Maxwellian minimises the convex dual
+    #   Phi(alpha) = sum_k w_k exp(alpha . psi_k) - alpha . Q,
+    # so a quasi-Newton minimiser of Phi (no shared code with the oracle) finds the same g.
+    pr = vproblem(n=12, L=5.0)
+    rng = np.random.default_rng(7)
+    f = _states(pr, 6, rng)
+    Ps = psi(pr.xi)
+    for fk in f:
+        Q = (pr.w * fk) @ Ps
+        P = pr.conservative_maxwellian(Q[None])[0][0]
+        g_or = maxwell(pr.xi, P[0], P[1:4], P[4])
+
+        def phi(a):
+            return (pr.w * np.exp(Ps @ a)).sum() - a @ Q
+
+        def grad(a):
+            return (pr.w * np.exp(Ps @ a)) @ Ps - Q
+
+        def hess(a):
+            return (Ps * (pr.w * np.exp(Ps @ a))[:, None]).T @ Ps
+
+        rho = Q[0]
+        U = Q[1:4] / rho
+        th = (2 / 3) * (Q[4] / rho - 0.5 * U @ U)
+        a0 = np.array([math.log(rho / (2 * math.pi * th) ** 1.5) - U @ U / (2 * th), *(U / th), -1 / th])
+        r = optimize.minimize(phi, a0, jac=grad, hess=hess, method="trust-exact",
+                              options={"gtol": 1e-14, "maxiter": 500})
+        a = r.x
+        for _ in range(3):  # polish the minimiser with plain Newton steps on grad Phi = 0
+            a = a - np.linalg.solve(hess(a), grad(a))
+        g_sc = np.exp(Ps @ a)
+        assert np.abs(g_or - g_sc).max() <= 1e-9 * g_or.max()
+
+
+def test_paper_two_newton_iterations_near_equilibrium():
+    # near-equilibrium states on the paper's smallest grid (8 nodes per dimension): two Newton
+    # iterations from the continuous Maxwellian already give a tiny residual; the third reaches
+    # round-off (quadratic convergence).
+    n = GOLD["velocity_nodes_per_dimension_as_few_as"]
+    pr = vproblem(n=n, L=4.0)
+    rng = np.random.default_rng(8)
+    Ps = psi(pr.xi)
+    res2 = []
+    for _ in range(20):
+        f = maxwell(pr.xi, rng.uniform(0.8, 1.2), rng.uniform(-0.2, 0.2, 3), rng.uniform(0.8, 1.2))
+        f *= 1 + 0.01 * rng.standard_normal(pr.nvel)
+        Q = (pr.w * f) @ Ps
+        pr.set_newton(0.0, GOLD["newton_iterations_as_few_as"])
+        _, it, res, _ = pr.conservative_maxwellian(Q[None])
+        res2.append(res[0])
+        pr.set_newton(1e-13, 50)
+        _, it, res, bad = pr.conservative_maxwellian(Q[None])
+        assert bad == 0 and it[0] <= 4
+    assert max(res2) < 1e-8
+
+
+def _bimodal_uniform(pr, rng):
+    f0 = _states(pr, 1, rng)[0]
+    return np.tile(f0, (pr.npts, 1))
+
+
+def test_space_homogeneous_relaxation_exact():
+    # uniform state: advection vanishes and M is constant, so SSP-RK3 gives exactly
+    #   f_n = M + (f0 - M) R(-dt/tau)^n,  R(z) = 1 + z + z^2/2 + z^3/6,
+    # and the closed form M + (f0 - M) exp(-t/tau) up to the O((dt/tau)^4) per-step error.
+    tau = 0.01
+    pr = vproblem(n=10, L=5.0, tau=tau, dim=1, ne=(3,), p=1)
+    rng = np.random.default_rng(9)
+    f0 = _bimodal_uniform(pr, rng)
+    pr.set_f(f0)
+    Q = pr.moments()[0]
+    P = pr.conservative_maxwellian(Q[None])[0][0]
+    M = maxwell(pr.xi, P[0], P[1:4], P[4])
+    dt, n = 0.2 * tau, 25
+    pr.step(dt, n)
+    z = -dt / tau
+    R = 1 + z + z * z / 2 + z**3 / 6
+    exact_rk = M + (f0[0] - M) * R**n
+    f = pr.get_f()
+    assert np.abs(f - exact_rk).max() <= 1e-13 * np.abs(f0).max()
+    exact = M + (f0[0] - M) * math.exp(-n * dt / tau)
+    assert np.abs(f - exact).max() <= n * (dt / tau) ** 4 / 24 * np.abs(f0 - M).max()
+
+
+def _global(pr, Q):
+    # spatial integral sum_e prod_d (h_d/2) sum_i W_i Q_i on the unit box
+    x, W = orc.gauss_legendre(pr.p + 1)
+    Wn = W if pr.dim == 1 else np.einsum("i,j,k->kji", W, W, W).ravel()
+    ne = pr.npts // len(Wn)
+    h = 1.0 / round(ne ** (1 / pr.dim))
+    return (Q.reshape(ne, len(Wn), 5) * Wn[None, :, None]).sum((0, 1)) * (h / 2) ** pr.dim
+
+
+def test_conservation_1000_periodic_steps():
+    pr = vproblem(n=6, L=5.0, tau=0.05, dim=1, ne=(4,), p=2)
+    x = pr.points()[:, 0]
+    prim = np.stack([1 + 0.3 * np.sin(2 * np.pi * x), 0.2 * np.cos(2 * np.pi * x), 0.1 + 0 * x,
+                     -0.1 * np.sin(4 * np.pi * x), 1 + 0.2 * np.cos(2 * np.pi * x)], 1)
+    pr.set_state(prim)
+    G0 = _global(pr, pr.moments())
+    pr.step(pr.dt(0.1), 1000)
+    G1 = _global(pr, pr.moments())
+    assert np.all(np.abs(G1 - G0) <= 1e-12 * np.abs(G0).max())
+
+
+def test_conservation_3d_periodic():
+    pr = orc.Problem(3, [2, 2, 2], [0.0] * 3, [1.0] * 3, 1, (6, 6, 6), (-4.0,) * 3, (4.0,) * 3, 0.05)
+    X = pr.points()
+    prim = np.stack([1 + 0.2 * np.sin(2 * np.pi * X[:, 0]) * np.cos(2 * np.pi * X[:, 1]),
+                     0.1 * np.sin(2 * np.pi * X[:, 2]), 0.05 + 0 * X[:, 0], 0 * X[:, 0],
+                     1 + 0.1 * np.cos(2 * np.pi * X[:, 1])], 1)
+    pr.set_state(prim)
+    G0 = _global(pr, pr.moments())
+    pr.step(pr.dt(0.1), 100)
+    G1 = _global(pr, pr.moments())
+    assert np.all(np.abs(G1 - G0) <= 1e-12 * np.abs(G0).max())
+
+
+def test_dirichlet_uniform_state_stays_uniform():
+    st = [1.2, 0.3, -0.1, 0.05, 0.9]
+    bc = [orc.DIRICHLET, orc.DIRICHLET, 0, 0, 0, 0]
+    bcs = np.zeros((6, 5))
+    bcs[0] = bcs[1] = st
+    pr = orc.Problem(1, [5], [0.0], [1.0], 2, (8, 8, 8), (-4.0,) * 3, (4.0,) * 3, 0.02, bc=bc, bc_state=bcs)
+    pr.set_state(np.tile(st, (pr.npts, 1)))
+    f0 = pr.get_f()
+    pr.step(0.002, 20)
+    assert np.abs(pr.get_f() - f0).max() <= 1e-12 * f0.max()
+
+
+def test_diffuse_wall_zero_net_mass_flux():
+    # walls at y = 0 and y = 1 (periodic x, z): the advection residual's mass integral is the net
+    # mass flux through the walls, which the discretely-conservative wall density makes zero.
+    bc = [0, 0, orc.WALL, orc.WALL, 0, 0]
+    bcs = np.zeros((6, 5))
+    bcs[2] = [0, 0, 0, 0, 1.0]
+    bcs[3] = [0, 0.1, 0, 0, 1.3]
+    pr = orc.Problem(3, [2, 3, 2], [0.0] * 3, [1.0] * 3, 2, (6, 6, 6), (-4.0,) * 3, (4.0,) * 3, INF,
+                     bc=bc, bc_state=bcs)
+    rng = np.random.default_rng(10)
+    f = rng.uniform(0.01, 0.1, (pr.npts, pr.nvel))
+    R = pr.residual(f)
+    x, W = orc.gauss_legendre(3)
+    Wn = np.einsum("i,j,k->kji", W, W, W).ravel()
+    mass = ((R @ pr.w).reshape(-1, 27) * Wn).sum()
+    assert abs(mass) <= 1e-13 * np.abs(R @ pr.w).max()
+
+
+def test_body_force_source_moments():
+    # the force source g (beta . psi) has discrete moments exactly (0, rho F, rho U . F)
+    F = np.array([0.01, -0.02, 0.03])
+    kw = dict(n=8, L=5.0, tau=0.1, dim=1, ne=(2,), p=1)
+    a = vproblem(**kw)
+    b = vproblem(force=F, **kw)
+    rng = np.random.default_rng(11)
+    f = np.concatenate([_states(a, 1, rng) for _ in range(a.npts)])
+    S = b.rhs(f) - a.rhs(f)
+    Q = f @ (a.w[:, None] * psi(a.xi))
+    MS = S @ (a.w[:, None] * psi(a.xi))
+    ref = np.stack([0 * Q[:, 0], Q[:, 0] * F[0], Q[:, 0] * F[1], Q[:, 0] * F[2], Q[:, 1:4] @ F], 1)
+    assert np.allclose(MS, ref, atol=1e-13, rtol=1e-10)
