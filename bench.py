@@ -1,0 +1,306 @@
+"""Benchmark: DOF-stage updates per second of the Boltzmann-BGK SSP-RK3 hot path on GB300.
+
+One "step" is one SSP-RK3 step (three stages) over the whole Taylor-Green workload: 16^3 hexahedra
+at p = 3 (262,144 points) x 24^3 velocities (13,824) = 3.62e9 degrees of freedom; each stage
+advects every velocity, relaxes towards the conservative Maxwellian and recomputes moments and the
+Newton solve. value = n_x * N_v * 3 / (seconds per step). f (14.5 GB per array) is far larger than
+L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (under torchrun) runs N independent replicas, one per GPU, with no data-path collective
+(the single periodic domain is not partitioned); value is the sum over ranks.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2308_06196_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DOF-stage updates/sec (x-pts x v-pts) & %HBM roofline, FP32/FP64-split vs all-FP64"
+UNIT = "DOF-stage/s"
+WORKLOAD = "taylor_green"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def stage_traffic():
+    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on this source."""
+    p = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2308_06196_gb300", "csrc", "k_stage.cu")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("k_stage_sha256") != sha:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_sample_problem():
+    """Bounded sample of the Taylor-Green workload for the CPU oracle: a 4 x 2 x 2-element periodic
+    box of the same mesh spacing at p = 3 with the full 24^3 velocity grid (16 elements, 1.4e7 DOF)."""
+    c = W.config(WORKLOAD)
+    h = (c["hi"][0] - c["lo"][0]) / c["nelem"][0]
+    ne = (4, 2, 2)
+    return dict(c, nelem=ne, hi=tuple(c["lo"][d] + ne[d] * h for d in range(3)))
+
+
+def run_oracle(steps: int, warmup: int):
+    from oracle import oracle as orc
+
+    c = cpu_sample_problem()
+    k = W.mesh_kwargs(c)
+    pr = orc.Problem(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
+    pr.set_state(W.prim_field(WORKLOAD, pr.points()))
+    dt = pr.dt(c["cfl"])
+    pr.step(dt, warmup)
+    t0 = time.perf_counter()
+    pr.step(dt, steps)
+    sec = time.perf_counter() - t0
+    dof = pr.npts * pr.nvel
+    cores = os.cpu_count()
+    return dof * 3 * steps / sec, sec / steps, cores, dof, c
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-baseline-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--elements", type=int, default=0,
+                    help="elements per direction (default: the workload's 16); smaller cases for profiling")
+    args = ap.parse_args()
+    warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, sec, cores, dof, c = run_oracle(args.steps, warmup)
+        sample = (f"FP64 CPU oracle, Taylor-Green field on a {c['nelem'][0]}x{c['nelem'][1]}x{c['nelem'][2]}-element "
+                  f"periodic box of the benchmark's mesh spacing, p=3, full 24^3 velocity grid ({dof:.3g} DOF)")
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD + " (CPU sample)", "dof": dof, "elements": list(c["nelem"]),
+                           "p": c["p"], "nv": list(c["nv"])},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2308_06196_gb300.bgk import Solver
+
+    c = W.config(WORKLOAD)
+    if args.elements:
+        c = W.config(WORKLOAD, nelem=(args.elements,) * 3)
+    k = W.mesh_kwargs(c)
+    s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
+    # one non-default stream shared by the library and the timing events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s.set_stream(stream.cuda_stream)
+    x = s.points()
+    prim = W.prim_field(WORKLOAD, x)
+    prim_pin = torch.from_numpy(prim).pin_memory()
+    Q_pin = torch.empty((s.npts, 5), dtype=torch.float64).pin_memory()
+    prim_dev = prim_pin.cuda()
+    s.set_state(prim_dev)
+    dt = s.dt(c["cfl"])
+    dof = s.ndof
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (graph path and timing path)
+    s.step(dt, warmup)
+    s.set_timing(True)
+    s.step(dt, 1)
+    s.set_timing(False)
+    barrier()
+
+    # timed region: K steps, every stage and Newton launch bracketed by CUDA events on its stream
+    s.set_state(prim_dev)
+    barrier()
+    s.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        s.step(dt, args.steps)
+        e1.record(stream)
+        barrier()
+    tm = s.timing()
+    s.set_timing(False)
+    s.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+
+    # the same steps through the captured CUDA graph
+    s.set_state(prim_dev)
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    s.step(dt, args.steps)
+    g1.record(stream)
+    barrier()
+    graph_ms = g0.elapsed_time(g1) / args.steps
+
+    # end to end through the public API with host buffers: H2D of the primitive state, one step,
+    # D2H of the moments, every step
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_state(prim_pin)
+        s.step(dt, 1)
+        s.moments(Q_pin)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    ms_t = torch.tensor([ms, graph_ms, e2e_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms, graph_ms, e2e_ms = ms_t.tolist()
+    nrep = world
+    value = dof * 3 * nrep / (ms * 1e-3)
+    e2e_value = dof * 3 * nrep / (e2e_ms * 1e-3)
+
+    stage_avg_ms = tm["stage_ms"] / max(1, tm["stage_launches"])
+    achieved = tm["stage_alg_bytes"] / (stage_avg_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = stage_traffic()
+    launches = tm["stage_launches"] + tm["newton_launches"]
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, sec, cores, sdof, sc = run_oracle(args.cpu_baseline_steps, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_baseline_steps} RK3 steps of the FP64 oracle on a "
+                         f"{sc['nelem'][0]}x{sc['nelem'][1]}x{sc['nelem'][2]}-element periodic Taylor-Green box "
+                         f"(same spacing, p=3, 24^3 velocities, {sdof:.3g} DOF)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": f"{c['nelem'][0]}^3 hex p=3 on [0,2pi]^3", "n_x": s.npts, "nv": list(c["nv"]),
+                   "dof": dof, "tau": c["tau"], "dt": dt, "precision": "f32 storage+advection, f64 Newton",
+                   "l2": "inputs larger than L2 (14.5 GB per f array)", "parallelism": f"replicas x{world}",
+                   "graph_ms_per_step": graph_ms},
+        "roofline": {"bound": "hbm", "kernel": "k_stage", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "alg_bytes_per_launch": tm["stage_alg_bytes"], "avg_launch_ms": stage_avg_ms,
+                     "stage_share": tm["stage_ms"] / (tm["stage_ms"] + tm["newton_ms"]),
+                     "newton_avg_ms": tm["newton_ms"] / max(1, tm["newton_launches"])},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": s.npts * 5 * 8,
+                "d2h_bytes_per_step": s.npts * 5 * 8, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

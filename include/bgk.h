@@ -1,0 +1,148 @@
+/*
+ * bgk.h -- C ABI of libbgk: one explicit SSP-RK3 step of the Boltzmann-BGK equation on a discrete
+ * velocity grid, on one NVIDIA GB300 (sm_103a), after Dzanic & Martinelli, "Towards full molecular
+ * gas dynamics simulations of complex flows via the Boltzmann equation" (arXiv 2308.06196).
+ *
+ * The method (paper Sec. 2 and 2.1):
+ *   d f_k/dt + xi_k . grad f_k = (g_k - f_k) / tau                                   (Eqs. 1, 3)
+ * for every node xi_k of a uniform Cartesian velocity grid with trapezoid weights w_k (Eq. 12).
+ * Transport is one linear advection per velocity, discretised by flux reconstruction with
+ * Gauss-Legendre solution points, DG-recovering correction functions and the upwind interface flux
+ * (Eqs. 7-9). The moments Q = sum_k w_k psi_k f_k, psi = (1, xi, |xi|^2/2) (Eq. 2 with Eq. 12) feed
+ * a per-point Newton solve for the discretely-conservative Maxwellian g (a Maxwellian at a
+ * perturbed state whose discrete moments equal Q; Sec. 2.1, text after Eq. 13). Time stepping is
+ * explicit (Sec. 2.2): Shu-Osher SSP-RK3.
+ *
+ * Precision forms: BGK_FP32_SPLIT stores and advects f in FP32, sums moments in FP32 per 32
+ * velocities and combines them exactly in double-float, and solves the Newton problem in FP64
+ * (FP32 iterations plus an FP64 residual refinement). BGK_FP64 keeps f, moments and Newton in FP64.
+ *
+ * Conventions
+ *   - Every function returns BGK_OK (0) or a negative BGK_E* code; bgk_last_error() describes the
+ *     last failure of a context. Device-side failures (Newton did not converge, non-physical state)
+ *     are sticky: they are reported by bgk_synchronize(), bgk_moments() and later calls until the
+ *     context is destroyed.
+ *   - Host arrays are FP64, caller-owned and only read or written during the call.
+ *   - Device pointers (the *_device variants) are caller-owned device memory on the context's
+ *     device; the call enqueues work on the context's stream and returns without synchronising.
+ *   - Point order: element-major with the element index x-fastest, then the node index x-fastest
+ *     (nodes are the tensor Gauss-Legendre points of the element). n_x = elements * (p+1)^dim.
+ *   - Velocity order: k = kx + n[0] * (ky + n[1] * kz); N_v = n[0] * n[1] * n[2].
+ *   - All device memory of a context is allocated by bgk_create and owned by the library.
+ */
+#ifndef BGK_H
+#define BGK_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BGK_OK 0
+#define BGK_EINVAL -1   /* bad argument or unsupported configuration */
+#define BGK_ENOMEM -2   /* device memory too small for this configuration (checked before any launch) */
+#define BGK_ECUDA -3    /* a CUDA runtime call failed */
+#define BGK_ENEWTON -4  /* the conservative-Maxwellian Newton solve did not converge at some point */
+#define BGK_EDOMAIN -5  /* non-physical state met: rho <= 0, theta <= 0 or NaN */
+#define BGK_ETIMEOUT -6 /* a bounded device wait gave up (reserved; no kernel waits at present) */
+
+#define BGK_BC_PERIODIC 0
+#define BGK_BC_DIRICHLET 1     /* ghost = sampled continuous Maxwellian of bc_state (rho,u,v,w,T) */
+#define BGK_BC_DIFFUSE_WALL 2  /* ghost = rho_w * M(T_w, U_w), rho_w for zero net discrete mass flux */
+
+#define BGK_FP32_SPLIT 0
+#define BGK_FP64 1
+
+typedef struct bgk_ctx bgk_ctx;
+
+/* Structured affine mesh of line (dim = 1) or hexahedral (dim = 3) elements on [lo, hi].
+ * Only the first dim entries of nelem/lo/hi/bc/bc_state are read. The velocity space is always 3-D. */
+typedef struct {
+    int dim;
+    int nelem[3];
+    double lo[3], hi[3];
+    int bc[3][2];              /* [direction][side 0 = lo, 1 = hi] */
+    double bc_state[3][2][5];  /* Dirichlet: rho,u,v,w,T.  Wall: (unused),u_w,v_w,w_w,T_w */
+} bgk_mesh;
+
+/* Uniform velocity grid, n[d] >= 2 nodes per axis on [lo[d], hi[d]] with both endpoints included,
+ * tensor-product trapezoid weights (Sec. 2.1, Eq. 12). */
+typedef struct {
+    int n[3];
+    double lo[3], hi[3];
+} bgk_vgrid;
+
+typedef struct {
+    int precision;           /* BGK_FP32_SPLIT (default) or BGK_FP64 */
+    double body_force[3];    /* constant force per unit mass (0 = none) */
+    int newton_max_it;       /* FP32 Newton iterations per solve, <= 0: default (2 warm, 12 cold) */
+    double newton_tol;       /* reserved (the FP64 refinement fixes the final accuracy) */
+    int limiter;             /* reserved: positivity limiter (Eqs. 10-11) is not on this path */
+    int chunks;              /* velocity chunks per stage, 0 = automatic */
+    int vtiles_per_task;     /* 32-velocity tiles per warp task, 0 = automatic */
+} bgk_opts;
+
+/* Create a problem on the current CUDA device: plans the velocity tiles, builds the FR operators
+ * (Eqs. 7-8) in FP64 on the host and allocates every device buffer. p in [1, 4] for dim = 3 and
+ * [1, 7] for dim = 1; opts may be NULL. tau > 0 is the constant relaxation time (Eq. 3 with a fixed
+ * tau). The state is zero until bgk_set_state/bgk_set_f. Returns BGK_ENOMEM, without allocating,
+ * when the buffers would not fit in free device memory. */
+int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vgrid, double tau,
+               const bgk_opts *opts, bgk_ctx **out);
+void bgk_destroy(bgk_ctx *ctx);
+const char *bgk_last_error(const bgk_ctx *ctx);
+
+/* Use this CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream) for all
+ * later work of the context. NULL selects the context's own non-blocking stream. */
+int bgk_set_stream(bgk_ctx *ctx, void *stream);
+
+/* Sizes: number of points n_x, velocities N_v, degrees of freedom n_x * N_v, bytes of device
+ * memory held. Any pointer may be NULL. */
+int bgk_info(const bgk_ctx *ctx, int64_t *npoints, int64_t *nvel, int64_t *ndof, int64_t *device_bytes);
+
+/* Node coordinates x[n_x][3] (unused components 0), host. */
+int bgk_points(const bgk_ctx *ctx, double *x);
+
+/* Set f to the sampled continuous Maxwellian (Eq. 4, velocity dimension 3) of the primitive state
+ * prim[n_x][5] = (rho, u, v, w, T) (theta = T), then compute its moments and conservative
+ * Maxwellian. Host array (synchronises) or device array (asynchronous) variant. */
+int bgk_set_state(bgk_ctx *ctx, const double *prim);
+int bgk_set_state_device(bgk_ctx *ctx, const double *d_prim);
+
+/* Copy the distribution function in or out as f[n_x][N_v] FP64 (host; synchronises). */
+int bgk_set_f(bgk_ctx *ctx, const double *f);
+int bgk_get_f(bgk_ctx *ctx, double *f);
+
+/* Enqueue nsteps SSP-RK3 steps of size dt. Each step is three stages; each stage advects every
+ * velocity (Eqs. 7-9), applies the BGK relaxation towards the conservative Maxwellian of the
+ * stage's input (Eq. 3) and combines the Shu-Osher stage, then recomputes the moments and the
+ * conservative Maxwellian of its output. Asynchronous on the context stream. */
+int bgk_step(bgk_ctx *ctx, double dt, int nsteps);
+
+/* Moments Q[n_x][5] = (rho, rho u, rho v, rho w, E) of the current f (Eq. 2 with Eq. 12).
+ * Host variant synchronises and returns the sticky device status; device variant is asynchronous. */
+int bgk_moments(bgk_ctx *ctx, double *Q);
+int bgk_moments_device(bgk_ctx *ctx, double *d_Q);
+
+/* Perturbed state (rho', U'x, U'y, U'z, theta') of the conservative Maxwellian of the current f,
+ * per point, host (synchronises). Its discrete moments equal bgk_moments(). */
+int bgk_equilibrium(bgk_ctx *ctx, double *prim_out);
+
+/* Wait for the context's stream and return the sticky device status. */
+int bgk_synchronize(bgk_ctx *ctx);
+
+/* Explicit step size min(cfl / max_k sum_d |xi_kd| / h_d, tau). */
+double bgk_dt(const bgk_ctx *ctx, double cfl);
+
+/* Launch timing: when on, bgk_step launches its kernels directly (not through the CUDA graph) and
+ * brackets every stage and Newton launch with CUDA events on the context stream. bgk_timing()
+ * synchronises and returns the summed milliseconds and launch counts since timing was switched on,
+ * and the algorithmic bytes one stage launch moves on average (the storage reads and writes of f
+ * that the method must make: reads of f_s and f^n, writes of the stage output). */
+int bgk_set_timing(bgk_ctx *ctx, int on);
+int bgk_timing(bgk_ctx *ctx, double *stage_ms, int64_t *stage_launches, double *newton_ms,
+               int64_t *newton_launches, double *stage_alg_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

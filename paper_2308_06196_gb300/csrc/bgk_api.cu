@@ -1,0 +1,820 @@
+// bgk_api.cu -- the C ABI of libbgk (include/bgk.h): host planning, FR operators, buffers, the
+// SSP-RK3 launch sequence and its CUDA graph.
+//
+// Memory plan of the FP32-split form. Velocities are grouped into chunks (one per sign octant by
+// default). f^n lives in one full array A; stage outputs rotate through a pool of (chunks + 1)
+// chunk-sized slots:
+//   stage 1: chunk c reads A[c]                      -> writes slot c
+//   stage 2: chunk c reads slot c (+ A[c])           -> writes slot c-1 (slot C for c = 0)
+//   stage 3: chunk c reads its stage-2 slot (+ A[c]) -> writes A[c] in place
+// A stage reads neighbours only inside its own chunk, and chunks run in order on one stream, so a
+// slot is rewritten only after the launch that read it has finished. Memory = A + (C+1)/C arrays.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bgk.h"
+#include "bgk_common.cuh"
+
+namespace bgk {
+cudaError_t launch_stage(const StageArgs &A, int p, int mode, cudaStream_t s);
+cudaError_t prepare_stage(int dim, int p);
+cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s);
+cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slotk, int nvt, int E, int NP,
+                                   const int n[3], const double v0[3], const double dv[3], int *err,
+                                   cudaStream_t s);
+cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
+                             int64_t nvel, int p0, int npt, cudaStream_t s);
+}  // namespace bgk
+
+using namespace bgk;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+struct Chunk {
+    int vt0, nvt, group0, ngroups;
+};
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton on P_n with P_n' = n (x P_n - P_{n-1}) / (x^2 - 1).
+void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; i++) {
+        double z = -cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = n == 1 ? z : p1, pm = n == 1 ? 1.0 : p0;
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16)
+                break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Lagrange basis value at y, barycentric weights lam.
+double lag(int n, const double *x, const double *lam, int j, double y)
+{
+    double num = lam[j] / (y - x[j]), den = 0.0;
+    for (int k = 0; k < n; k++)
+        den += lam[k] / (y - x[k]);
+    return num / den;
+}
+
+// FR operators (Sec. 2.1, Eqs. 7-9) for the stage kernel, built in FP64 and rounded to FP32:
+// barycentric derivative matrix with the negative-sum diagonal, end interpolants, and the DG lift
+// (Radau correction) derivatives g_L'(x_i) = -l_i(-1) / W_i, g_R'(x_i) = l_i(1) / W_i.
+void build_ops(int p, Ops &op, double *xg_out)
+{
+    const int n = p + 1;
+    double x[kMaxN1], W[kMaxN1], lam[kMaxN1], D[kMaxN1][kMaxN1], lm[kMaxN1], lp[kMaxN1], gl[kMaxN1], gr[kMaxN1];
+    gauss_legendre(n, x, W);
+    for (int j = 0; j < n; j++) {
+        lam[j] = 1.0;
+        for (int k = 0; k < n; k++)
+            if (k != j)
+                lam[j] /= (x[j] - x[k]);
+    }
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int j = 0; j < n; j++) {
+            if (j == i)
+                continue;
+            D[i][j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+            s += D[i][j];
+        }
+        D[i][i] = -s;
+    }
+    for (int j = 0; j < n; j++) {
+        lm[j] = n == 1 ? 1.0 : lag(n, x, lam, j, -1.0);
+        lp[j] = n == 1 ? 1.0 : lag(n, x, lam, j, 1.0);
+    }
+    for (int i = 0; i < n; i++) {
+        gl[i] = -lm[i] / W[i];
+        gr[i] = lp[i] / W[i];
+    }
+    memset(&op, 0, sizeof(op));
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) {
+            op.DL[i][j] = (float)(D[i][j] - gl[i] * lm[j]);
+            op.DR[i][j] = (float)(D[i][j] - gr[i] * lp[j]);
+        }
+        op.gl[i] = (float)gl[i];
+        op.gr[i] = (float)gr[i];
+        op.lm[i] = (float)lm[i];
+        op.lp[i] = (float)lp[i];
+        xg_out[i] = x[i];
+    }
+}
+
+double maxwell(double rho, const double *U, double th, double vx, double vy, double vz)
+{
+    const double r2 = (vx - U[0]) * (vx - U[0]) + (vy - U[1]) * (vy - U[1]) + (vz - U[2]) * (vz - U[2]);
+    return rho * pow(2.0 * kPi * th, -1.5) * exp(-0.5 * r2 / th);
+}
+
+}  // namespace
+
+struct bgk_ctx {
+    // problem
+    int dim = 0, p = 0, N1 = 0, NP = 0;
+    int ne[3] = {1, 1, 1};
+    int E = 0;
+    int64_t npts = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    double bcs[30] = {0};
+    int nv[3] = {0, 0, 0};
+    double vlo[3] = {0, 0, 0}, dv[3] = {0, 0, 0};
+    int64_t nvel = 0;
+    double tau = 0;
+    bgk_opts opts{};
+    double xg[kMaxN1] = {0};
+    // velocity plan
+    int nvt = 0, nslots = 0, G = 1, ngroups = 0;
+    std::vector<int> slotk;
+    std::vector<Chunk> chunks;
+    int64_t chunk_floats = 0;  // floats per pool slot
+    // device buffers
+    float *fA = nullptr, *pool = nullptr;
+    float *xi = nullptr, *wpsi = nullptr, *gmask = nullptr, *ghost = nullptr;
+    int *slotk_d = nullptr;
+    float *partial = nullptr, *param = nullptr;
+    double *Q = nullptr, *prim = nullptr, *prim_in = nullptr;
+    int *err = nullptr;
+    int64_t bytes = 0;
+    Ops ops{};
+    Mesh mesh{};
+    // execution
+    cudaStream_t stream = nullptr, own = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double gdt = -1.0;
+    std::string last;
+    int sticky = 0;
+    // timing
+    bool timing = false;
+    struct Ev {
+        cudaEvent_t a, b;
+        int kind;  // 0 stage, 1 newton
+        double bytes;
+    };
+    std::vector<Ev> evs;
+    size_t nev = 0;
+};
+
+namespace {
+
+int fail(bgk_ctx *c, int code, const std::string &msg)
+{
+    if (c)
+        c->last = msg;
+    return code;
+}
+
+int cuda_fail(bgk_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, BGK_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                       \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess)                         \
+            return cuda_fail(c, e_, #call);            \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(bgk_ctx *c, T **p, size_t n)
+{
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e == cudaSuccess)
+        c->bytes += (int64_t)(n * sizeof(T));
+    return e;
+}
+
+StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
+{
+    StageArgs A{};
+    A.xi = c->xi;
+    A.wpsi = c->wpsi;
+    A.gmask = c->gmask;
+    A.ghost = c->ghost;
+    A.param = c->param;
+    A.partial = c->partial;
+    A.ops = c->ops;
+    A.mesh = c->mesh;
+    A.vt0 = ch.vt0;
+    A.nvt = ch.nvt;
+    A.G = c->G;
+    A.group0 = ch.group0;
+    A.nslots = c->nslots;
+    A.npts = (int)c->npts;
+    A.inv_tau = (float)(1.0 / c->tau);
+    return A;
+}
+
+float *chunk_ptr(bgk_ctx *c, float *base, int vt0) { return base + (int64_t)vt0 * c->E * c->NP * kWarp; }
+
+NewtonArgs newton_args(bgk_ctx *c, int cold)
+{
+    NewtonArgs N{};
+    N.partial = c->partial;
+    N.ngroups = c->ngroups;
+    N.npts = (int)c->npts;
+    N.Q = c->Q;
+    N.prim = c->prim;
+    N.param = c->param;
+    N.err = c->err;
+    N.cold = cold;
+    N.it32 = c->opts.newton_max_it > 0 ? c->opts.newton_max_it : 2;
+    N.it64 = 1;
+    for (int d = 0; d < 3; d++) {
+        N.v0[d] = c->vlo[d];
+        N.dv[d] = c->dv[d];
+        N.n[d] = c->nv[d];
+    }
+    return N;
+}
+
+void ev_begin(bgk_ctx *c, int kind, double bytes)
+{
+    if (!c->timing)
+        return;
+    if (c->nev == c->evs.size()) {
+        bgk_ctx::Ev ev{};
+        cudaEventCreate(&ev.a);
+        cudaEventCreate(&ev.b);
+        c->evs.push_back(ev);
+    }
+    bgk_ctx::Ev &ev = c->evs[c->nev];
+    ev.kind = kind;
+    ev.bytes = bytes;
+    cudaEventRecord(ev.a, c->stream);
+}
+
+void ev_end(bgk_ctx *c)
+{
+    if (!c->timing)
+        return;
+    cudaEventRecord(c->evs[c->nev].b, c->stream);
+    c->nev++;
+}
+
+// Moments + conservative Maxwellian of the current f^n (after set_state / set_f).
+int prologue(bgk_ctx *c, cudaStream_t s)
+{
+    for (const Chunk &ch : c->chunks) {
+        StageArgs A = stage_args(c, ch);
+        A.src = chunk_ptr(c, c->fA, ch.vt0);
+        CK(launch_stage(A, c->p, 1, s));
+    }
+    CK(launch_newton(newton_args(c, 1), s));
+    return BGK_OK;
+}
+
+// One SSP-RK3 step: three stages, each over all chunks, each followed by the Newton solve.
+int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
+{
+    static const float an[3] = {0.f, 0.75f, 1.f / 3.f};
+    static const float bb[3] = {1.f, 0.25f, 2.f / 3.f};
+    const int C = (int)c->chunks.size();
+    std::vector<int> slot1(C), slot2(C);
+    for (int q = 0; q < C; q++) {
+        slot1[q] = q;
+        slot2[q] = q == 0 ? C : q - 1;
+    }
+    for (int st = 0; st < 3; st++) {
+        for (int q = 0; q < C; q++) {
+            const Chunk &ch = c->chunks[q];
+            StageArgs A = stage_args(c, ch);
+            float *Aq = chunk_ptr(c, c->fA, ch.vt0);
+            float *s1 = c->pool + (int64_t)slot1[q] * c->chunk_floats;
+            float *s2 = c->pool + (int64_t)slot2[q] * c->chunk_floats;
+            if (st == 0) {
+                A.src = Aq;
+                A.fn = nullptr;
+                A.dst = s1;
+            } else if (st == 1) {
+                A.src = s1;
+                A.fn = Aq;
+                A.dst = s2;
+            } else {
+                A.src = s2;
+                A.fn = Aq;
+                A.dst = Aq;
+            }
+            A.an = an[st];
+            A.b = bb[st];
+            A.dt = (float)dt;
+            int64_t real = 0;
+            for (int v = ch.vt0 * kWarp; v < (ch.vt0 + ch.nvt) * kWarp; v++)
+                real += c->slotk[v] >= 0;
+            ev_begin(c, 0, (double)real * c->npts * sizeof(float) * (st == 0 ? 2 : 3));
+            CK(launch_stage(A, c->p, 0, s));
+            ev_end(c);
+        }
+        ev_begin(c, 1, 0.0);
+        CK(launch_newton(newton_args(c, 0), s));
+        ev_end(c);
+    }
+    return BGK_OK;
+}
+
+int read_status(bgk_ctx *c)
+{
+    int e = 0;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    c->sticky |= e;
+    if (c->sticky & kErrDomain)
+        return fail(c, BGK_EDOMAIN, "non-physical state (rho <= 0, theta <= 0 or NaN) met on the device");
+    if (c->sticky & kErrNewton)
+        return fail(c, BGK_ENEWTON, "conservative-Maxwellian Newton solve did not converge at some point");
+    return BGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bgk_last_error(const bgk_ctx *c) { return c ? c->last.c_str() : "null context"; }
+
+void bgk_destroy(bgk_ctx *c)
+{
+    if (!c)
+        return;
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    if (c->gexec)
+        cudaGraphExecDestroy(c->gexec);
+    for (auto &ev : c->evs) {
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    void *bufs[] = {c->fA, c->pool, c->xi, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
+                    c->param, c->Q, c->prim, c->prim_in, c->err};
+    for (void *b : bufs)
+        if (b)
+            cudaFree(b);
+    if (c->own)
+        cudaStreamDestroy(c->own);
+    delete c;
+}
+
+int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, const bgk_opts *opts, bgk_ctx **out)
+{
+    if (!out)
+        return BGK_EINVAL;
+    *out = nullptr;
+    if (!mesh || !vg)
+        return BGK_EINVAL;
+    bgk_ctx *c = new bgk_ctx();
+    auto bail = [&](int code, const std::string &msg) {
+        c->last = msg;
+        fprintf(stderr, "bgk_create: %s\n", msg.c_str());
+        bgk_destroy(c);
+        return code;
+    };
+    if (opts)
+        c->opts = *opts;
+    if (c->opts.precision != BGK_FP32_SPLIT)
+        return bail(BGK_EINVAL, "only the FP32-split precision form is built in this library version");
+    c->dim = mesh->dim;
+    if (c->dim != 1 && c->dim != 3)
+        return bail(BGK_EINVAL, "dim must be 1 or 3");
+    if (p < 1 || (c->dim == 3 && p > 3) || (c->dim == 1 && p > 5))
+        return bail(BGK_EINVAL, "p must be in [1, 3] (dim 3) or [1, 5] (dim 1)");
+    if (!(tau > 0.0) || !std::isfinite(tau))
+        return bail(BGK_EINVAL, "tau must be positive and finite");
+    c->p = p;
+    c->N1 = p + 1;
+    c->NP = c->dim == 1 ? c->N1 : c->N1 * c->N1 * c->N1;
+    int64_t E = 1;
+    for (int d = 0; d < 3; d++) {
+        if (d < c->dim) {
+            c->ne[d] = mesh->nelem[d];
+            c->lo[d] = mesh->lo[d];
+            c->hi[d] = mesh->hi[d];
+            if (c->ne[d] < 1 || !(c->hi[d] > c->lo[d]))
+                return bail(BGK_EINVAL, "bad mesh extent");
+            for (int s = 0; s < 2; s++) {
+                const int b = mesh->bc[d][s];
+                if (b != BGK_BC_PERIODIC && b != BGK_BC_DIRICHLET)
+                    return bail(BGK_EINVAL, "boundary kind not supported by this library version");
+                c->bc[2 * d + s] = b;
+                for (int q = 0; q < 5; q++)
+                    c->bcs[(2 * d + s) * 5 + q] = mesh->bc_state[d][s][q];
+            }
+            if ((c->bc[2 * d] == BGK_BC_PERIODIC) != (c->bc[2 * d + 1] == BGK_BC_PERIODIC))
+                return bail(BGK_EINVAL, "periodic faces must come in pairs");
+        }
+        c->h[d] = (c->hi[d] - c->lo[d]) / c->ne[d];
+        E *= c->ne[d];
+    }
+    if (E * c->NP > INT32_MAX / 2)
+        return bail(BGK_EINVAL, "too many points");
+    c->E = (int)E;
+    c->npts = E * c->NP;
+    for (int d = 0; d < 3; d++) {
+        if (vg->n[d] < 2 || vg->n[d] > 4096 || !(vg->hi[d] > vg->lo[d]))
+            return bail(BGK_EINVAL, "bad velocity grid");
+        c->nv[d] = vg->n[d];
+        c->vlo[d] = vg->lo[d];
+        c->dv[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
+    }
+    c->nvel = (int64_t)c->nv[0] * c->nv[1] * c->nv[2];
+    c->tau = tau;
+    build_ops(p, c->ops, c->xg);
+
+    // velocity plan: octants (sign of each component; xi = 0 goes with the positive side)
+    std::vector<int> idx[3][2];
+    for (int d = 0; d < 3; d++)
+        for (int k = 0; k < c->nv[d]; k++)
+            idx[d][c->vlo[d] + k * c->dv[d] >= 0.0 ? 1 : 0].push_back(k);
+    for (int o = 0; o < 8; o++) {
+        const auto &X = idx[0][o & 1], &Y = idx[1][(o >> 1) & 1], &Z = idx[2][(o >> 2) & 1];
+        const int64_t n = (int64_t)X.size() * Y.size() * Z.size();
+        if (n == 0)
+            continue;
+        Chunk ch{};
+        ch.vt0 = (int)(c->slotk.size() / kWarp);
+        for (int kz : Z)
+            for (int ky : Y)
+                for (int kx : X)
+                    c->slotk.push_back(kx + c->nv[0] * (ky + c->nv[1] * kz));
+        while (c->slotk.size() % kWarp)
+            c->slotk.push_back(-1);
+        ch.nvt = (int)(c->slotk.size() / kWarp) - ch.vt0;
+        c->chunks.push_back(ch);
+    }
+    c->nvt = (int)(c->slotk.size() / kWarp);
+    c->nslots = c->nvt * kWarp;
+    if (c->opts.chunks == 1 && c->chunks.size() > 1) {
+        Chunk all{0, c->nvt, 0, 0};
+        c->chunks.assign(1, all);
+    }
+    int maxc = 0;
+    for (auto &ch : c->chunks)
+        maxc = std::max(maxc, ch.nvt);
+    // tiles per warp task: enough tasks for ~32 resident warps per SM, at most 8 tiles
+    if (c->opts.vtiles_per_task > 0)
+        c->G = c->opts.vtiles_per_task;
+    else {
+        const int64_t tasks1 = (int64_t)maxc * E;
+        c->G = (int)std::max<int64_t>(1, std::min<int64_t>(8, tasks1 / (152 * 32)));
+    }
+    c->ngroups = 0;
+    for (auto &ch : c->chunks) {
+        ch.group0 = c->ngroups;
+        ch.ngroups = (ch.nvt + c->G - 1) / c->G;
+        c->ngroups += ch.ngroups;
+    }
+    c->chunk_floats = (int64_t)maxc * E * c->NP * kWarp;
+
+    // mesh descriptor
+    c->mesh.dim = c->dim;
+    c->mesh.nelem = c->E;
+    for (int d = 0; d < 3; d++) {
+        c->mesh.ne[d] = c->ne[d];
+        c->mesh.inv_h2[d] = (float)(2.0 / c->h[d]);
+    }
+    for (int q = 0; q < 6; q++)
+        c->mesh.bc[q] = c->bc[q];
+
+    // memory check before any allocation
+    const int64_t fA = (int64_t)c->nvt * E * c->NP * kWarp;
+    const int64_t need = (fA + (int64_t)(c->chunks.size() + 1) * c->chunk_floats) * 4 +
+                         (int64_t)c->ngroups * 5 * c->npts * 4 + c->npts * (5 * 8 * 3 + kParamStride * 4) +
+                         (int64_t)c->nslots * 4 * 16;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
+        return bail(BGK_ECUDA, "cudaMemGetInfo failed (no CUDA device?)");
+    if ((double)need > 0.97 * (double)free_b)
+        return bail(BGK_ENOMEM, "configuration needs " + std::to_string(need >> 20) + " MiB, only " +
+                                    std::to_string(free_b >> 20) + " MiB free");
+    for (int q = 0; q < 6; q++)
+        if (q / 2 < c->dim && c->bc[q] == BGK_BC_DIRICHLET && !(c->bcs[q * 5] > 0.0 && c->bcs[q * 5 + 4] > 0.0))
+            return bail(BGK_EINVAL, "Dirichlet state needs rho > 0 and T > 0");
+
+#define AL(ptr, n)                                                        \
+    if (dalloc(c, &(ptr), (size_t)(n)) != cudaSuccess)                    \
+        return bail(BGK_ENOMEM, std::string("cudaMalloc failed: ") + #ptr);
+    AL(c->fA, fA);
+    AL(c->pool, (c->chunks.size() + 1) * c->chunk_floats);
+    AL(c->xi, 3 * c->nslots);
+    AL(c->wpsi, 5 * c->nslots);
+    AL(c->gmask, c->nslots);
+    AL(c->ghost, 6 * c->nslots);
+    AL(c->slotk_d, c->nslots);
+    AL(c->partial, (int64_t)c->ngroups * 5 * c->npts);
+    AL(c->param, c->npts * kParamStride);
+    AL(c->Q, c->npts * 5);
+    AL(c->prim, c->npts * 5);
+    AL(c->prim_in, c->npts * 5);
+    AL(c->err, 1);
+#undef AL
+    // velocity tables
+    std::vector<float> xi(3 * c->nslots), wpsi(5 * c->nslots), gm(c->nslots), gh(6 * c->nslots, 0.f);
+    for (int s = 0; s < c->nslots; s++) {
+        int k = c->slotk[s];
+        const bool real = k >= 0;
+        if (!real) {  // padding: a copy of the tile's first velocity, zero weight, no relaxation
+            k = c->slotk[(s / kWarp) * kWarp];
+        }
+        const int kk[3] = {k % c->nv[0], (k / c->nv[0]) % c->nv[1], k / (c->nv[0] * c->nv[1])};
+        double v[3], w = 1.0;
+        for (int d = 0; d < 3; d++) {
+            v[d] = c->vlo[d] + kk[d] * c->dv[d];
+            w *= (kk[d] == 0 || kk[d] == c->nv[d] - 1) ? 0.5 * c->dv[d] : c->dv[d];
+            xi[d * c->nslots + s] = (float)v[d];
+        }
+        if (!real)
+            w = 0.0;
+        const int vt = s / kWarp, l = s % kWarp;
+        const double ps[5] = {1.0, v[0], v[1], v[2], 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])};
+        for (int q = 0; q < 5; q++)
+            wpsi[((int64_t)vt * 5 + q) * kWarp + l] = (float)(w * ps[q]);
+        gm[s] = real ? 1.f : 0.f;
+        for (int q = 0; q < 6; q++)
+            if (q / 2 < c->dim && c->bc[q] == BGK_BC_DIRICHLET && real) {
+                const double *st = c->bcs + 5 * q;
+                gh[q * c->nslots + s] = (float)maxwell(st[0], st + 1, st[4], v[0], v[1], v[2]);
+            }
+    }
+    cudaError_t rc;
+    if ((rc = cudaMemcpy(c->xi, xi.data(), xi.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemcpy(c->wpsi, wpsi.data(), wpsi.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemcpy(c->gmask, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemcpy(c->ghost, gh.data(), gh.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemcpy(c->slotk_d, c->slotk.data(), c->slotk.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemset(c->fA, 0, fA * 4)) || (rc = cudaMemset(c->err, 0, 4)) ||
+        (rc = cudaMemset(c->prim, 0, c->npts * 5 * 8)) || (rc = cudaMemset(c->param, 0, c->npts * kParamStride * 4)))
+        return bail(BGK_ECUDA, std::string("device set-up copy failed: ") + cudaGetErrorString(rc));
+    if (prepare_stage(c->dim, p) != cudaSuccess)
+        return bail(BGK_ECUDA, "stage kernel attribute set-up failed");
+    if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(BGK_ECUDA, "stream creation failed");
+    c->stream = c->own;
+    *out = c;
+    return BGK_OK;
+}
+
+int bgk_set_stream(bgk_ctx *c, void *stream)
+{
+    if (!c)
+        return BGK_EINVAL;
+    c->stream = stream ? (cudaStream_t)stream : c->own;
+    return BGK_OK;
+}
+
+int bgk_info(const bgk_ctx *c, int64_t *npoints, int64_t *nvel, int64_t *ndof, int64_t *device_bytes)
+{
+    if (!c)
+        return BGK_EINVAL;
+    if (npoints)
+        *npoints = c->npts;
+    if (nvel)
+        *nvel = c->nvel;
+    if (ndof)
+        *ndof = c->npts * c->nvel;
+    if (device_bytes)
+        *device_bytes = c->bytes;
+    return BGK_OK;
+}
+
+int bgk_points(const bgk_ctx *c, double *x)
+{
+    if (!c || !x)
+        return BGK_EINVAL;
+    for (int64_t pt = 0; pt < c->npts; pt++) {
+        const int e = (int)(pt / c->NP), i = (int)(pt % c->NP);
+        const int ec[3] = {e % c->ne[0], (e / c->ne[0]) % c->ne[1], e / (c->ne[0] * c->ne[1])};
+        const int ic[3] = {i % c->N1, (i / c->N1) % c->N1, i / (c->N1 * c->N1)};
+        for (int d = 0; d < 3; d++)
+            x[pt * 3 + d] = d < c->dim ? c->lo[d] + (ec[d] + 0.5 * (c->xg[ic[d]] + 1.0)) * c->h[d] : 0.0;
+    }
+    return BGK_OK;
+}
+
+static int set_state_impl(bgk_ctx *c, const double *prim, cudaMemcpyKind kind)
+{
+    CK(cudaMemcpyAsync(c->prim_in, prim, c->npts * 5 * sizeof(double), kind, c->stream));
+    CK(launch_init_maxwellian(c->fA, c->prim_in, c->slotk_d, c->nvt, c->E, c->NP, c->nv, c->vlo, c->dv, c->err,
+                              c->stream));
+    return prologue(c, c->stream);
+}
+
+int bgk_set_state(bgk_ctx *c, const double *prim)
+{
+    if (!c || !prim)
+        return BGK_EINVAL;
+    int rc = set_state_impl(c, prim, cudaMemcpyHostToDevice);
+    if (rc)
+        return rc;
+    return read_status(c);
+}
+
+int bgk_set_state_device(bgk_ctx *c, const double *d_prim)
+{
+    if (!c || !d_prim)
+        return BGK_EINVAL;
+    return set_state_impl(c, d_prim, cudaMemcpyDeviceToDevice);
+}
+
+static int convert_impl(bgk_ctx *c, double *f, bool in)
+{
+    const int64_t per_pt = c->nvel * (int64_t)sizeof(double);
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(c->npts, (256ll << 20) / per_pt));
+    double *st = nullptr;
+    CK(cudaMalloc(&st, chunk * per_pt));
+    int rc = BGK_OK;
+    for (int64_t p0 = 0; p0 < c->npts && rc == BGK_OK; p0 += chunk) {
+        const int64_t n = std::min(chunk, c->npts - p0);
+        cudaError_t e = cudaSuccess;
+        if (in) {
+            e = cudaMemcpyAsync(st, f + p0 * c->nvel, n * per_pt, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = launch_convert_f(true, c->fA, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0, (int)n,
+                                     c->stream);
+        } else {
+            e = launch_convert_f(false, c->fA, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0, (int)n,
+                                 c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(f + p0 * c->nvel, st, n * per_pt, cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            rc = cuda_fail(c, e, "f conversion");
+    }
+    cudaFree(st);
+    return rc;
+}
+
+int bgk_set_f(bgk_ctx *c, const double *f)
+{
+    if (!c || !f)
+        return BGK_EINVAL;
+    int rc = convert_impl(c, const_cast<double *>(f), true);
+    if (rc)
+        return rc;
+    rc = prologue(c, c->stream);
+    if (rc)
+        return rc;
+    return read_status(c);
+}
+
+int bgk_get_f(bgk_ctx *c, double *f)
+{
+    if (!c || !f)
+        return BGK_EINVAL;
+    return convert_impl(c, f, false);
+}
+
+int bgk_step(bgk_ctx *c, double dt, int nsteps)
+{
+    if (!c || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
+        return BGK_EINVAL;
+    if (c->sticky)
+        return read_status(c);
+    if (nsteps == 0)
+        return BGK_OK;
+    if (c->timing) {
+        for (int n = 0; n < nsteps; n++) {
+            int rc = enqueue_step(c, dt, c->stream);
+            if (rc)
+                return rc;
+        }
+        return BGK_OK;
+    }
+    if (!c->gexec || c->gdt != dt) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        cudaStream_t cap;
+        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_fail(c, e, "cudaStreamBeginCapture");
+        }
+        int rc = enqueue_step(c, dt, cap);
+        e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (rc)
+            return rc;
+        CK(e);
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        c->gdt = dt;
+    }
+    for (int n = 0; n < nsteps; n++)
+        CK(cudaGraphLaunch(c->gexec, c->stream));
+    return BGK_OK;
+}
+
+int bgk_moments(bgk_ctx *c, double *Q)
+{
+    if (!c || !Q)
+        return BGK_EINVAL;
+    CK(cudaMemcpyAsync(Q, c->Q, c->npts * 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c);
+}
+
+int bgk_moments_device(bgk_ctx *c, double *d_Q)
+{
+    if (!c || !d_Q)
+        return BGK_EINVAL;
+    CK(cudaMemcpyAsync(d_Q, c->Q, c->npts * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return BGK_OK;
+}
+
+int bgk_equilibrium(bgk_ctx *c, double *prim_out)
+{
+    if (!c || !prim_out)
+        return BGK_EINVAL;
+    CK(cudaMemcpyAsync(prim_out, c->prim, c->npts * 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c);
+}
+
+int bgk_synchronize(bgk_ctx *c)
+{
+    if (!c)
+        return BGK_EINVAL;
+    return read_status(c);
+}
+
+double bgk_dt(const bgk_ctx *c, double cfl)
+{
+    if (!c)
+        return -1.0;
+    double smax = 0.0;
+    for (int64_t k = 0; k < c->nvel; k++) {
+        const int kk[3] = {(int)(k % c->nv[0]), (int)((k / c->nv[0]) % c->nv[1]), (int)(k / (c->nv[0] * c->nv[1]))};
+        double s = 0.0;
+        for (int d = 0; d < c->dim; d++)
+            s += fabs(c->vlo[d] + kk[d] * c->dv[d]) / c->h[d];
+        smax = std::max(smax, s);
+    }
+    return std::min(cfl / smax, c->tau);
+}
+
+int bgk_set_timing(bgk_ctx *c, int on)
+{
+    if (!c)
+        return BGK_EINVAL;
+    c->timing = on != 0;
+    c->nev = 0;
+    return BGK_OK;
+}
+
+int bgk_timing(bgk_ctx *c, double *stage_ms, int64_t *stage_launches, double *newton_ms, int64_t *newton_launches,
+               double *stage_alg_bytes)
+{
+    if (!c)
+        return BGK_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    double sm = 0, nm = 0, by = 0;
+    int64_t sl = 0, nl = 0;
+    for (size_t q = 0; q < c->nev; q++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->evs[q].a, c->evs[q].b));
+        if (c->evs[q].kind == 0) {
+            sm += ms;
+            sl++;
+            by += c->evs[q].bytes;
+        } else {
+            nm += ms;
+            nl++;
+        }
+    }
+    if (stage_ms)
+        *stage_ms = sm;
+    if (stage_launches)
+        *stage_launches = sl;
+    if (newton_ms)
+        *newton_ms = nm;
+    if (newton_launches)
+        *newton_launches = nl;
+    if (stage_alg_bytes)
+        *stage_alg_bytes = sl ? by / sl : 0.0;
+    return BGK_OK;
+}
+
+}  // extern "C"

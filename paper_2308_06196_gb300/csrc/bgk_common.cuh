@@ -1,0 +1,88 @@
+// bgk_common.cuh -- device-side data structures shared by the libbgk kernels and the host planner.
+//
+// Device layout of the distribution function (FP32-split form):
+//   f[vt][e][i][lane]   vt   = 32-velocity tile (velocities of one sign octant, padded to 32),
+//                       e    = element (x fastest), i = node in the element (x fastest),
+//                       lane = velocity within the tile.
+// A warp owns one (element, run of tiles) task; lane l holds velocity l of the tile, so every
+// global load or store of one node is one coalesced 128-byte line.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bgk {
+
+constexpr int kWarp = 32;
+constexpr int kWarpsPerCta = 4;   // elements per CTA in the stage kernel
+constexpr int kMaxN1 = 8;         // nodes per direction (p <= 7)
+constexpr int kParamStride = 8;   // floats per point in the BGK parameter table
+
+// error bits of the device status word
+constexpr int kErrDomain = 1;
+constexpr int kErrNewton = 2;
+
+// FR reference operators on [-1, 1] in FP32 (Sec. 2.1, Eqs. 7-9), merged for the upwind side:
+//   left inflow  (xi_d > 0): d_i = sum_{j>=1} DL[i][j] (f_j - f_0) + gl[i] (t_up - f_0)
+//   right inflow (xi_d < 0): d_i = sum_{j<=p-1} DR[i][j] (f_j - f_p) + gr[i] (t_up - f_p)
+// where DL = D - gl (x) lm, DR = D - gr (x) lp (the interior trace folded into the derivative),
+// t_up is the upwind neighbour's trace (lp on its nodes for a left neighbour, lm for a right one).
+struct Ops {
+    float DL[kMaxN1][kMaxN1];
+    float DR[kMaxN1][kMaxN1];
+    float gl[kMaxN1], gr[kMaxN1];
+    float lm[kMaxN1], lp[kMaxN1];
+};
+
+struct Mesh {
+    int dim;
+    int ne[3];          // elements per direction (1 for unused directions)
+    int nelem;
+    int bc[6];          // boundary kind per face (2*d + side)
+    float inv_h2[3];    // 2 / h_d
+};
+
+// One launch of the fused stage kernel over one velocity chunk.
+struct StageArgs {
+    const float *src;    // f_s of this chunk: [nvt_chunk][E][NP][32]
+    const float *fn;     // f^n of this chunk (same layout), null in stage 1
+    float *dst;          // stage output of this chunk (may alias fn: in-place update of f^n)
+    const float *xi;     // [3][nslots] velocity components of every device slot
+    const float *wpsi;   // [nvt][5][32] w * (1, xi, |xi|^2/2), 0 on padded slots
+    const float *gmask;  // [nslots] 1 for real velocities, 0 for padding
+    const float *ghost;  // [6][nslots] Dirichlet ghost values (sampled Maxwellian), or null
+    const float *param;  // [n_x][8] BGK exponent b0..b4 of every point: g = exp2(b0 + b.xi + b4|xi|^2)
+    float *partial;      // [ngroups_total][5][n_x] moment partial sums of the stage output
+    Ops ops;
+    Mesh mesh;
+    int vt0;             // first global tile of the chunk
+    int nvt;             // tiles in the chunk
+    int G;               // tiles per warp task
+    int group0;          // global index of the chunk's first task group
+    int nslots;          // total device velocity slots (= nvt_total * 32)
+    int npts;            // n_x
+    float an, b;         // Shu-Osher coefficients: out = an f^n + b (f_s + dt L(f_s))
+    float dt, inv_tau;
+};
+
+struct NewtonArgs {
+    const float *partial;  // [ngroups][5][n_x]
+    int ngroups;
+    int npts;
+    double *Q;             // [n_x][5] moments (out)
+    double *prim;          // [n_x][5] perturbed state rho', U', theta' (in: warm start, out)
+    float *param;          // [n_x][8] stage-kernel exponent (out)
+    int *err;              // status word (atomicOr)
+    int cold;              // 1: ignore prim and start from the continuous state of Q
+    int it32;              // FP32 Newton iterations
+    int it64;              // FP64 refinements
+    // 1-D velocity grids: xi_k = v0[d] + k dv[d], k < n[d]; trapezoid weights
+    double v0[3], dv[3];
+    int n[3];
+};
+
+__host__ __device__ inline int64_t fidx(int vt_local, int e, int i, int lane, int E, int NP)
+{
+    return (((int64_t)vt_local * E + e) * NP + i) * kWarp + lane;
+}
+
+}  // namespace bgk

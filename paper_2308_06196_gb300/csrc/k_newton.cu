@@ -1,0 +1,357 @@
+// k_newton.cu -- per-point discretely-conservative Maxwellian (Sec. 2.1, text after Eq. 13).
+//
+// For every spatial point the kernel
+//   1. sums the FP32 partial moments of all velocity tasks exactly (double-float accumulation),
+//      giving Q = sum_k w_k psi_k f_k in FP64 (Eq. 2 with the trapezoid operator of Eq. 12),
+//   2. finds the Maxwellian g at a perturbed state whose discrete moments equal Q. On the tensor
+//      velocity grid with tensor trapezoid weights, g factors into 1-D Gaussians, so every moment
+//      and every Jacobian entry sum_k w g psi psi^T is a product of 1-D sums S_d^m = sum_k w c^m A
+//      (m <= 4). The unknowns are the log-linear coefficients alpha of g = exp(alpha . psi~) in the
+//      velocity c = (xi - V) / s centred and scaled by the starting state (V, s^2), which keeps the
+//      5 x 5 Jacobian well conditioned.
+//        - FP32 Newton iterations (closed-form Jacobian) bring alpha to FP32 accuracy;
+//        - FP64 refinement: the residual is evaluated in FP64 (the 1-D Gaussians by an exact
+//          product recurrence outward from their peak: three FP64 exponentials per axis) and
+//          corrected with the FP32 Jacobian, which contracts the error by ~1e-6 per refinement.
+//   3. writes Q, the perturbed state (rho', U', theta') used as the next warm start, and the FP32
+//      exponent g = exp2(b0 + b . xi + b4 |xi|^2) that the stage kernel evaluates per velocity.
+// Points with rho <= 0, theta <= 0 or NaN moments set the domain bit of the status word; a Newton
+// correction that stays large sets the Newton bit. No thread waits on another.
+#include "bgk_common.cuh"
+
+namespace bgk {
+
+// exact FP32 two-sum: s + e = a + b
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Solve J x = r (5 x 5) by Gaussian elimination in T; returns false when a pivot vanishes. J is the
+// Hessian sum_k w g psi psi^T of a strictly convex function (symmetric positive definite), so
+// elimination without pivoting is stable and every index stays compile-time (registers only).
+template <typename T>
+__device__ __forceinline__ bool solve5(T (&J)[5][5], T (&r)[5], T (&x)[5])
+{
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        if (!(J[c][c] > T(0)))
+            return false;
+        const T inv = T(1) / J[c][c];
+#pragma unroll
+        for (int q = c + 1; q < 5; q++) {
+            const T m = J[q][c] * inv;
+#pragma unroll
+            for (int k = c + 1; k < 5; k++)
+                J[q][k] -= m * J[c][k];
+            r[q] -= m * r[c];
+        }
+    }
+#pragma unroll
+    for (int q = 4; q >= 0; q--) {
+        T s = r[q];
+#pragma unroll
+        for (int k = q + 1; k < 5; k++)
+            s -= J[q][k] * x[k];
+        x[q] = s / J[q][q];
+    }
+    return true;
+}
+
+// Moments M[g psi~] (5) and, when J is non-null, the Jacobian M[g psi~ psi~^T] from the 1-D sums
+// S[d][m] = sum_k w_k c_k^m A_d(c_k), scaled by e0 = exp(alpha_0).
+template <typename T>
+__device__ __forceinline__ void assemble(const T (&S)[3][5], T e0, T (&M)[5], T (*J)[5])
+{
+    const T p0 = S[0][0] * S[1][0] * S[2][0];
+    const T a01 = S[1][0] * S[2][0], a02 = S[0][0] * S[2][0], a12 = S[0][0] * S[1][0];
+    const T o0[3] = {a01, a02, a12};  // product of the S0 of the other two axes
+    M[0] = e0 * p0;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        M[1 + d] = e0 * S[d][1] * o0[d];
+    const T m4 = T(0.5) * (S[0][2] * o0[0] + S[1][2] * o0[1] + S[2][2] * o0[2]);
+    M[4] = e0 * m4;
+    if (!J)
+        return;
+    J[0][0] = M[0];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        J[0][1 + d] = J[1 + d][0] = M[1 + d];
+    J[0][4] = J[4][0] = M[4];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        J[1 + d][1 + d] = e0 * S[d][2] * o0[d];
+#pragma unroll
+        for (int q = d + 1; q < 3; q++) {
+            const int f = 3 - d - q;
+            J[1 + d][1 + q] = J[1 + q][1 + d] = e0 * S[d][1] * S[q][1] * S[f][0];
+        }
+        // M[g c_d |c|^2 / 2]
+        T s = S[d][3] * o0[d];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            if (q == d)
+                continue;
+            const int f = 3 - d - q;
+            s += S[d][1] * S[q][2] * S[f][0];
+        }
+        J[1 + d][4] = J[4][1 + d] = e0 * T(0.5) * s;
+    }
+    T s4 = S[0][4] * o0[0] + S[1][4] * o0[1] + S[2][4] * o0[2];
+    s4 += T(2) * (S[0][2] * S[1][2] * S[2][0] + S[0][2] * S[2][2] * S[1][0] + S[1][2] * S[2][2] * S[0][0]);
+    J[4][4] = e0 * T(0.25) * s4;
+}
+
+// 1-D sums in FP32: A(c) = exp(ad c - (beta/2) c^2) on c_k = c0 + k h, trapezoid weights dv (ends /2).
+__device__ __forceinline__ void sums32(float ad, float beta, float c0, float h, int n, float dv, float (&S)[5])
+{
+    for (int m = 0; m < 5; m++)
+        S[m] = 0.f;
+    for (int k = 0; k < n; k++) {
+        const float c = fmaf((float)k, h, c0);
+        float t = __expf(c * fmaf(-0.5f * beta, c, ad));
+        if (k == 0 || k == n - 1)
+            t *= 0.5f;
+        S[0] += t;
+        t *= c;
+        S[1] += t;
+        t *= c;
+        S[2] += t;
+        t *= c;
+        S[3] += t;
+        t *= c;
+        S[4] += t;
+    }
+    for (int m = 0; m < 5; m++)
+        S[m] *= dv;
+}
+
+// 1-D sums in FP64 up to m = 2, exponentials by the exact product recurrence from the peak:
+// q(k) = ad c_k - beta/2 c_k^2 is quadratic in k, so A(k+1)/A(k) = exp(q1 + q2 (2k+1)) and the ratio
+// itself changes by the constant factor exp(2 q2). Values decay away from the peak, so the products
+// underflow gracefully instead of overflowing.
+__device__ __forceinline__ void sums64(double ad, double beta, double c0, double h, int n, double dv, double (&S)[3])
+{
+    const double q1 = (ad - beta * c0) * h, q2 = -0.5 * beta * h * h;
+    int kp = (int)rint(-q1 / (2.0 * q2));
+    kp = kp < 0 ? 0 : (kp > n - 1 ? n - 1 : kp);
+    const double cp = fma((double)kp, h, c0);
+    const double Ap = exp(cp * fma(-0.5 * beta, cp, ad));
+    const double E2 = exp(2.0 * q2);
+    const double rp = exp(q1 + q2 * (2.0 * kp + 1.0));
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    // upward from the peak (inclusive)
+    double A = Ap, r = rp;
+    for (int k = kp; k < n; k++) {
+        const double c = fma((double)k, h, c0);
+        const double t = (k == 0 || k == n - 1) ? 0.5 * A : A;
+        s0 += t;
+        s1 = fma(c, t, s1);
+        s2 = fma(c * c, t, s2);
+        A *= r;
+        r *= E2;
+    }
+    // downward from the peak (exclusive): A(k-1) = A(k) d(k), d(k) = E2 / r(k), d(k-1) = d(k) E2
+    A = Ap;
+    double dk = E2 / rp;
+    for (int k = kp - 1; k >= 0; k--) {
+        A *= dk;
+        dk *= E2;
+        const double c = fma((double)k, h, c0);
+        const double t = (k == 0 || k == n - 1) ? 0.5 * A : A;
+        s0 += t;
+        s1 = fma(c, t, s1);
+        s2 = fma(c * c, t, s2);
+    }
+    S[0] = s0 * dv;
+    S[1] = s1 * dv;
+    S[2] = s2 * dv;
+}
+
+__global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
+{
+    const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pt >= A.npts)
+        return;
+
+    // 1. moments: exact sum of the FP32 partials
+    double Q[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        float hi = 0.f, lo = 0.f;
+        const float *p = A.partial + (int64_t)c * A.npts + pt;
+        for (int g = 0; g < A.ngroups; g++) {
+            float s, e;
+            two_sum(hi, __ldg(p + (int64_t)g * 5 * A.npts), s, e);
+            hi = s;
+            lo += e;
+        }
+        Q[c] = (double)hi + (double)lo;
+    }
+#pragma unroll
+    for (int c = 0; c < 5; c++)
+        A.Q[(int64_t)pt * 5 + c] = Q[c];
+
+    const double rho = Q[0];
+    const double u[3] = {Q[1] / rho, Q[2] / rho, Q[3] / rho};
+    const double thc = (2.0 / 3.0) * (Q[4] / rho - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    float *par = A.param + (int64_t)pt * kParamStride;
+    if (!(rho > 0.0) || !(thc > 0.0) || !isfinite(rho) || !isfinite(thc)) {
+        atomicOr(A.err, kErrDomain);
+        par[0] = -1e30f;  // g = 0 at this point
+        par[1] = par[2] = par[3] = par[4] = 0.f;
+        return;
+    }
+
+    // 2. starting state (V, s^2) and target moments in the centred, scaled basis psi~ = (1, c, |c|^2/2)
+    double V[3] = {u[0], u[1], u[2]}, th0 = thc, rh0 = rho;
+    bool warm = false;
+    if (!A.cold) {
+        const double *pp = A.prim + (int64_t)pt * 5;
+        if (pp[0] > 0.0 && pp[4] > 0.0 && isfinite(pp[0] + pp[1] + pp[2] + pp[3] + pp[4])) {
+            rh0 = pp[0];
+            V[0] = pp[1];
+            V[1] = pp[2];
+            V[2] = pp[3];
+            th0 = pp[4];
+            warm = true;
+        }
+    }
+    const double s = sqrt(th0), is = 1.0 / s;
+    double Qt[5];
+    Qt[0] = Q[0];
+    for (int d = 0; d < 3; d++)
+        Qt[1 + d] = (Q[1 + d] - Q[0] * V[d]) * is;
+    Qt[4] = (Q[4] - (V[0] * Q[1] + V[1] * Q[2] + V[2] * Q[3]) + 0.5 * Q[0] * (V[0] * V[0] + V[1] * V[1] + V[2] * V[2])) * is * is;
+
+    // alpha = (alpha_0, a_1, a_2, a_3, -beta): g = exp(alpha_0 + a . c - beta |c|^2 / 2)
+    double al[5] = {log(rh0) - 1.5 * log(2.0 * 3.14159265358979323846 * th0), 0.0, 0.0, 0.0, -1.0};
+    double c0[3], h[3], dvs[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        c0[d] = (A.v0[d] - V[d]) * is;
+        h[d] = A.dv[d] * is;
+        dvs[d] = A.dv[d];
+    }
+
+    // FP32 Newton iterations until the step is below FP32 resolution (it32 minimum, 30 maximum)
+    float J[5][5];
+    bool haveJ = false;
+    const int it32min = warm ? A.it32 : max(A.it32, 4);
+    for (int it = 0; it < 30; it++) {
+        float S[3][5];
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            sums32((float)al[1 + d], (float)(-al[4]), (float)c0[d], (float)h[d], A.n[d], (float)dvs[d], S[d]);
+        float M[5];
+        assemble<float>(S, (float)exp(al[0]), M, J);
+        haveJ = true;
+        float r[5], dx[5], Jw[5][5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            r[m] = (float)(Qt[m] - (double)M[m]);
+#pragma unroll
+            for (int q = 0; q < 5; q++)
+                Jw[m][q] = J[m][q];
+        }
+        if (!solve5<float>(Jw, r, dx)) {
+            haveJ = false;
+            break;
+        }
+        // keep the Gaussian decaying: halve the step while beta would drop below 0.05
+        float lam = 1.f;
+        while (-(al[4] + lam * dx[4]) < 0.05 && lam > 1e-3f)
+            lam *= 0.5f;
+        float step = 0.f;
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            al[m] += (double)(lam * dx[m]);
+            step = fmaxf(step, fabsf(lam * dx[m]));
+        }
+        if (it + 1 >= it32min && step < 2e-6f)
+            break;
+    }
+    if (!haveJ) {
+        atomicOr(A.err, kErrNewton);
+        return;
+    }
+
+    // FP64 refinements with the FP32 Jacobian of the last iteration, until the correction is at
+    // FP64 resolution (it64 minimum, 4 maximum)
+    double corr = 0.0;
+    const int it64min = warm ? A.it64 : max(A.it64, 2);
+    for (int it = 0; it < 4; it++) {
+        double S[3][5];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            double s3[3];
+            sums64(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], s3);
+            S[d][0] = s3[0];
+            S[d][1] = s3[1];
+            S[d][2] = s3[2];
+            S[d][3] = S[d][4] = 0.0;
+        }
+        double M[5];
+        assemble<double>(S, exp(al[0]), M, nullptr);
+        double r[5], dx[5], Jd[5][5];
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            r[m] = Qt[m] - M[m];
+#pragma unroll
+            for (int q = 0; q < 5; q++)
+                Jd[m][q] = (double)J[m][q];
+        }
+        if (!solve5<double>(Jd, r, dx)) {
+            atomicOr(A.err, kErrNewton);
+            return;
+        }
+        corr = 0.0;
+#pragma unroll
+        for (int m = 0; m < 5; m++) {
+            al[m] += dx[m];
+            corr = fmax(corr, fabs(dx[m]));
+        }
+        if (it + 1 >= it64min && corr < 1e-12)
+            break;
+    }
+    const double beta = -al[4];
+    if (!(beta > 0.0) || !isfinite(al[0] + al[1] + al[2] + al[3]) || corr > 1e-9) {
+        atomicOr(A.err, kErrNewton);
+        return;
+    }
+
+    // 3. outputs: perturbed state and the stage kernel's exponent in the raw velocity
+    const double a[3] = {al[1], al[2], al[3]};
+    const double thp = th0 / beta;  // s^2 / beta
+    double Up[3];
+    for (int d = 0; d < 3; d++)
+        Up[d] = V[d] + s * a[d] / beta;
+    const double lnC = al[0] + 0.5 * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / beta;  // ln(rho' (2 pi theta')^-1.5)
+    const double rhop = exp(lnC) * pow(2.0 * 3.14159265358979323846 * thp, 1.5);
+    double *pp = A.prim + (int64_t)pt * 5;
+    pp[0] = rhop;
+    pp[1] = Up[0];
+    pp[2] = Up[1];
+    pp[3] = Up[2];
+    pp[4] = thp;
+    // ln g = lnC - |xi - U'|^2 / (2 theta') = lnC - |U'|^2/(2 theta') + U'.xi / theta' - |xi|^2 / (2 theta')
+    const double L2E = 1.4426950408889634;
+    const double it2 = 1.0 / thp;
+    par[0] = (float)(L2E * (lnC - 0.5 * (Up[0] * Up[0] + Up[1] * Up[1] + Up[2] * Up[2]) * it2));
+    par[1] = (float)(L2E * Up[0] * it2);
+    par[2] = (float)(L2E * Up[1] * it2);
+    par[3] = (float)(L2E * Up[2] * it2);
+    par[4] = (float)(-0.5 * L2E * it2);
+}
+
+cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s)
+{
+    const int threads = 128;
+    k_newton<<<(A.npts + threads - 1) / threads, threads, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace bgk

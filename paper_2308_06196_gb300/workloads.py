@@ -1,0 +1,98 @@
+"""Seeded synthetic workloads shaped like the paper's flows (the paper's datasets are not used).
+
+This module holds only problem definitions and input fields: meshes, velocity grids, relaxation
+times and the primitive state (rho, u, v, w, T) at given node coordinates, plus seeded random
+perturbations. None of the method's arithmetic (Maxwellians, moments, FR operators) is here, so
+both the CUDA library and the CPU oracle can take their inputs from it.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PERIODIC, DIRICHLET, WALL = 0, 1, 2
+TWO_PI = 2.0 * math.pi
+
+# Workloads. Each entry: mesh (dim, nelem, lo, hi, bc, bc_state), degree p, velocity grid (nv, vlo,
+# vhi), relaxation time tau, CFL number for the explicit step and the number of steps.
+CONFIGS = {
+    # 1-D periodic line, 32 elements at p = 3, 16^3 velocities on [-6, 6]^3: correctness workload
+    "periodic1d": dict(dim=1, nelem=(32,), lo=(0.0,), hi=(1.0,), p=3, nv=(16, 16, 16),
+                       vlo=(-6.0,) * 3, vhi=(6.0,) * 3, tau=0.01, cfl=0.1, steps=100),
+    # 3-D Taylor-Green-type flow on [0, 2 pi]^3, 16^3 hexahedra at p = 3, 24^3 velocities on [-5, 5]^3
+    "taylor_green": dict(dim=3, nelem=(16, 16, 16), lo=(0.0,) * 3, hi=(TWO_PI,) * 3, p=3, nv=(24, 24, 24),
+                         vlo=(-5.0,) * 3, vhi=(5.0,) * 3, tau=1e-3, cfl=0.1, steps=50),
+}
+
+
+def config(name: str, **override) -> dict:
+    c = dict(CONFIGS[name])
+    c.update(override)
+    return c
+
+
+def mesh_kwargs(c: dict) -> dict:
+    """Arguments common to the CUDA binding's Solver and the oracle's Problem."""
+    return dict(dim=c["dim"], nelem=list(c["nelem"]), lo=list(c["lo"]), hi=list(c["hi"]), p=c["p"],
+                nv=tuple(c["nv"]), vlo=tuple(c["vlo"]), vhi=tuple(c["vhi"]), tau=c["tau"])
+
+
+def prim_periodic1d(x: np.ndarray) -> np.ndarray:
+    """rho = 1 + 0.1 sin(2 pi x), u = 0, T = 1 (nondimensional, R = 1)."""
+    n = len(x)
+    P = np.zeros((n, 5))
+    P[:, 0] = 1.0 + 0.1 * np.sin(TWO_PI * x[:, 0])
+    P[:, 4] = 1.0
+    return P
+
+
+def prim_taylor_green(x: np.ndarray, mach: float = 0.1, gamma: float = 5.0 / 3.0) -> np.ndarray:
+    """Taylor-Green vortex: rho = 1, U0 = Ma sqrt(gamma T0) with T0 = 1,
+    u = U0 sin x cos y cos z, v = -U0 cos x sin y cos z, w = 0,
+    p = 1 + rho U0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2), T = p / rho."""
+    U0 = mach * math.sqrt(gamma)
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    P = np.zeros((len(x), 5))
+    P[:, 0] = 1.0
+    P[:, 1] = U0 * np.sin(X) * np.cos(Y) * np.cos(Z)
+    P[:, 2] = -U0 * np.cos(X) * np.sin(Y) * np.cos(Z)
+    pres = 1.0 + U0 * U0 / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+    P[:, 4] = pres / P[:, 0]
+    return P
+
+
+PRIM = {"periodic1d": prim_periodic1d, "taylor_green": prim_taylor_green}
+
+
+def prim_field(name: str, x: np.ndarray) -> np.ndarray:
+    return PRIM[name](x)
+
+
+def smooth_prim(x: np.ndarray, dim: int, seed: int = 0, amp: float = 0.2) -> np.ndarray:
+    """A seeded smooth periodic primitive field on the unit box (random low Fourier modes),
+    rho and T bounded away from 0, |U| <= amp."""
+    rng = np.random.default_rng(seed)
+    n = len(x)
+    P = np.zeros((n, 5))
+
+    def field():
+        f = np.zeros(n)
+        for _ in range(3):
+            k = rng.integers(-2, 3, size=3)
+            k[dim:] = 0
+            ph = rng.uniform(0, TWO_PI)
+            f += rng.uniform(-1, 1) * np.cos(TWO_PI * (x @ k) + ph)
+        return f / 3.0
+
+    P[:, 0] = 1.0 + amp * field()
+    for d in range(3):
+        P[:, 1 + d] = amp * field()
+    P[:, 4] = 1.0 + amp * field()
+    return P
+
+
+def noise(shape, seed: int = 0, amp: float = 0.05) -> np.ndarray:
+    """Seeded multiplicative perturbation factors 1 + amp * U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    return 1.0 + amp * rng.uniform(-1.0, 1.0, size=shape)
