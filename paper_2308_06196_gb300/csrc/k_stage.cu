@@ -71,31 +71,50 @@ __device__ __forceinline__ int upwind_neighbour(const Mesh &m, const int ec[3], 
     return c[0] + m.ne[0] * (c[1] + m.ne[1] * c[2]);
 }
 
-// Advection of all lines of one direction, inflow from the left (LEFT = true, xi_d > 0) or right.
-// acc += cd * (derivative along d) with cd = -(2/h_d) xi_d b dt folded in.
+// Raw values of the upwind neighbour along every line of direction D (one coalesced 128-byte load
+// per node; all NL * N1 loads of a direction are issued together so their latency overlaps).
+template <int N1, int DIM, int D>
+__device__ __forceinline__ void load_lines(float (&v)[Geo<N1, DIM>::NL][N1], const float *__restrict__ nb)
+{
+    using Gm = Geo<N1, DIM>;
+#pragma unroll
+    for (int ln = 0; ln < Gm::NL; ln++)
+#pragma unroll
+        for (int j = 0; j < N1; j++)
+            v[ln][j] = __ldg(nb + Gm::node(D, ln, j) * kWarp);
+}
+
+// Upwind trace of every line: the neighbour's interpolant at the shared face, in the difference form
+// t = v_0 + sum_j l_j (v_j - v_0), exact for a constant state. A left neighbour is evaluated at its
+// +1 end (lp), a right neighbour at its -1 end (lm).
+template <int N1, int NL>
+__device__ __forceinline__ void reduce_trace(float (&T)[NL], const float (&v)[NL][N1], const Ops &op, bool left)
+{
+#pragma unroll
+    for (int ln = 0; ln < NL; ln++) {
+        float t = 0.f;
+#pragma unroll
+        for (int j = 1; j < N1; j++)
+            t = fmaf(left ? op.lp[j] : op.lm[j], v[ln][j] - v[ln][0], t);
+        T[ln] = v[ln][0] + t;
+    }
+}
+
+// Advection of all lines of one direction given the upwind traces T, inflow from the left
+// (LEFT, xi_d > 0) or the right. acc += cd * (derivative along d), cd = -(2/h_d) xi_d b dt:
+//   d_i = sum_{j != R} Dm[i][j] (f_j - f_R) + g[i] (T - f_R),  R = the inflow end of the line,
+// Dm = D - g (x) l the derivative matrix with the interior trace folded in (exact zero for constants).
 template <int N1, int DIM, int D, bool LEFT>
-__device__ __forceinline__ void advect_dir(float (&acc)[Geo<N1, DIM>::NP], const float (&f)[Geo<N1, DIM>::NP],
-                                           const Ops &op, const float *__restrict__ nb, float ghost,
-                                           float cd)
+__device__ __forceinline__ void apply_dir(float (&acc)[Geo<N1, DIM>::NP], const float (&f)[Geo<N1, DIM>::NP],
+                                          const float (&T)[Geo<N1, DIM>::NL], const Ops &op, float cd)
 {
     using Gm = Geo<N1, DIM>;
     constexpr int P = N1 - 1;
-    constexpr int R = LEFT ? 0 : P;  // reference node: the inflow end of the line
+    constexpr int R = LEFT ? 0 : P;
 #pragma unroll
     for (int ln = 0; ln < Gm::NL; ln++) {
         const float fr = f[Gm::node(D, ln, R)];
-        float T;
-        if (nb) {
-            float t = 0.f;
-#pragma unroll
-            for (int j = 0; j < N1; j++) {
-                const float v = __ldg(nb + Gm::node(D, ln, j) * kWarp);
-                t = fmaf(LEFT ? op.lp[j] : op.lm[j], v - fr, t);
-            }
-            T = cd * t;
-        } else {
-            T = cd * (ghost - fr);
-        }
+        const float Tc = cd * (T[ln] - fr);
         float Gv[N1];
 #pragma unroll
         for (int j = 0; j < N1; j++)
@@ -109,30 +128,47 @@ __device__ __forceinline__ void advect_dir(float (&acc)[Geo<N1, DIM>::NP], const
                     continue;
                 s = fmaf(LEFT ? op.DL[i][j] : op.DR[i][j], Gv[j], s);
             }
-            acc[Gm::node(D, ln, i)] = fmaf(LEFT ? op.gl[i] : op.gr[i], T, s);
+            acc[Gm::node(D, ln, i)] = fmaf(LEFT ? op.gl[i] : op.gr[i], Tc, s);
         }
     }
 }
 
 template <int N1, int DIM, int D>
-__device__ __forceinline__ void advect(float (&acc)[Geo<N1, DIM>::NP], const float (&f)[Geo<N1, DIM>::NP],
-                                       const StageArgs &A, const int ec[3], int vl, int slot, float xid,
-                                       bool left)
+__device__ __forceinline__ void apply(float (&acc)[Geo<N1, DIM>::NP], const float (&f)[Geo<N1, DIM>::NP],
+                                      const float (&T)[Geo<N1, DIM>::NL], const StageArgs &A, float xid, bool left)
 {
-    using Gm = Geo<N1, DIM>;
-    const int E = A.mesh.nelem;
-    const int en = upwind_neighbour(A.mesh, ec, D, left);
-    const float *nb = nullptr;
-    float ghost = 0.f;
-    if (en >= 0)
-        nb = A.src + fidx(vl, en, 0, threadIdx.x & 31, E, Gm::NP);
-    else
-        ghost = A.ghost[(2 * D + (left ? 0 : 1)) * A.nslots + slot];
     const float cd = -A.mesh.inv_h2[D] * xid * (A.b * A.dt);
     if (left)
-        advect_dir<N1, DIM, D, true>(acc, f, A.ops, nb, ghost, cd);
+        apply_dir<N1, DIM, D, true>(acc, f, T, A.ops, cd);
     else
-        advect_dir<N1, DIM, D, false>(acc, f, A.ops, nb, ghost, cd);
+        apply_dir<N1, DIM, D, false>(acc, f, T, A.ops, cd);
+}
+
+// Issue the neighbour loads of direction D (or fill the ghost value on a non-periodic boundary).
+template <int N1, int DIM, int D>
+__device__ __forceinline__ bool fetch_dir(float (&v)[Geo<N1, DIM>::NL][N1], float &ghost, const StageArgs &A,
+                                          const int ec[3], int vl, int slot, bool left)
+{
+    const int en = upwind_neighbour(A.mesh, ec, D, left);
+    if (en >= 0) {
+        load_lines<N1, DIM, D>(v, A.src + fidx(vl, en, 0, threadIdx.x & 31, A.mesh.nelem, Geo<N1, DIM>::NP));
+        return true;
+    }
+    ghost = __ldg(A.ghost + (2 * D + (left ? 0 : 1)) * A.nslots + slot);
+    return false;
+}
+
+template <int N1, int NL>
+__device__ __forceinline__ void traces(float (&T)[NL], const float (&v)[NL][N1], bool have, float ghost,
+                                       const Ops &op, bool left)
+{
+    if (have) {
+        reduce_trace<N1, NL>(T, v, op, left);
+    } else {
+#pragma unroll
+        for (int ln = 0; ln < NL; ln++)
+            T[ln] = ghost;
+    }
 }
 
 template <int NP>
@@ -188,6 +224,19 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, MinCtas<Geo<N1, DIM>::NP>
             sm.macc[wid][c][q * 32 + lane] = 0.f;
 
     const float kb = A.b * (1.f - A.dt * A.inv_tau);
+    // f: f_s of the current tile; acc: f^n of the current tile (or 0), prefetched one tile ahead
+    float f[NP], acc[NP];
+    {
+        const int64_t b0 = fidx(vl0, e, 0, lane, E, NP);
+#pragma unroll
+        for (int i = 0; i < NP; i++)
+            f[i] = __ldg(A.src + b0 + i * kWarp);
+        if (MODE == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; i++)
+                acc[i] = A.fn ? __ldcs(A.fn + b0 + i * kWarp) : 0.f;
+        }
+    }
     for (int vl = vl0; vl < vl1; vl++) {
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
@@ -195,36 +244,38 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, MinCtas<Geo<N1, DIM>::NP>
 #pragma unroll
         for (int c = 0; c < 5; c++)
             sm.wpsi[wid][c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
-
         const int64_t base = fidx(vl, e, 0, lane, E, NP);
-        float f[NP];
-#pragma unroll
-        for (int i = 0; i < NP; i++)
-            f[i] = __ldg(A.src + base + i * kWarp);
 
         if (MODE == 0) {
-            float acc[NP];
+            // acc = an f^n + b (1 - dt/tau) f_s, then the advection of every direction
 #pragma unroll
             for (int i = 0; i < NP; i++)
-                acc[i] = kb * f[i];
-            advect<N1, DIM, 0>(acc, f, A, ec, vl, slot, x0, x0 >= 0.f);
+                acc[i] = fmaf(A.an, acc[i], kb * f[i]);
+            const bool l0 = x0 >= 0.f, l1 = x1 >= 0.f, l2 = x2 >= 0.f;
+            float v[Gm::NL][N1], T[Gm::NL], gh = 0.f;
+            bool have = fetch_dir<N1, DIM, 0>(v, gh, A, ec, vl, slot, l0);
+            traces<N1, Gm::NL>(T, v, have, gh, A.ops, l0);
             if constexpr (DIM > 1) {
-                advect<N1, DIM, 1>(acc, f, A, ec, vl, slot, x1, x1 >= 0.f);
-                advect<N1, DIM, 2>(acc, f, A, ec, vl, slot, x2, x2 >= 0.f);
+                apply<N1, DIM, 0>(acc, f, T, A, x0, l0);
+                have = fetch_dir<N1, DIM, 1>(v, gh, A, ec, vl, slot, l1);
+                traces<N1, Gm::NL>(T, v, have, gh, A.ops, l1);
+                apply<N1, DIM, 1>(acc, f, T, A, x1, l1);
+                have = fetch_dir<N1, DIM, 2>(v, gh, A, ec, vl, slot, l2);
+                traces<N1, Gm::NL>(T, v, have, gh, A.ops, l2);
+                apply<N1, DIM, 2>(acc, f, T, A, x2, l2);
+            } else {
+                apply<N1, DIM, 0>(acc, f, T, A, x0, l0);
             }
-            // BGK source towards the conservative Maxwellian + Shu-Osher combination
+            // BGK source towards the conservative Maxwellian (cg g) and the store of f_{s+1}
             const float cg = A.b * A.dt * A.inv_tau * __ldg(A.gmask + slot);
             const float xs = x0 * x0 + x1 * x1 + x2 * x2;
-            const float *fn = A.fn ? A.fn + base : nullptr;
             float *dst = A.dst + base;
 #pragma unroll
             for (int i = 0; i < NP; i++) {
                 const float4 pb = *reinterpret_cast<const float4 *>(&sm.par[wid][i][0]);
                 const float b4 = sm.par[wid][i][4];
                 const float ex = fmaf(b4, xs, fmaf(pb.w, x2, fmaf(pb.z, x1, fmaf(pb.y, x0, pb.x))));
-                float o = fmaf(cg, exp2f(ex), acc[i]);
-                if (fn)
-                    o = fmaf(A.an, __ldcs(fn + i * kWarp), o);
+                const float o = fmaf(cg, exp2f(ex), acc[i]);
                 __stcs(dst + i * kWarp, o);
                 sm.wf[wid][i][lane] = o;
             }
@@ -234,6 +285,18 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, MinCtas<Geo<N1, DIM>::NP>
                 sm.wf[wid][i][lane] = f[i];
         }
         __syncwarp();
+        // prefetch the next tile (its latency overlaps the moment sums below)
+        if (vl + 1 < vl1) {
+            const int64_t b1 = fidx(vl + 1, e, 0, lane, E, NP);
+#pragma unroll
+            for (int i = 0; i < NP; i++)
+                f[i] = __ldg(A.src + b1 + i * kWarp);
+            if (MODE == 0) {
+#pragma unroll
+                for (int i = 0; i < NP; i++)
+                    acc[i] = A.fn ? __ldcs(A.fn + b1 + i * kWarp) : 0.f;
+            }
+        }
 
         // moments of the 32 velocities of this tile, node = lane + 32 q, pairs over k
 #pragma unroll
@@ -275,28 +338,334 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, MinCtas<Geo<N1, DIM>::NP>
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Hexahedra: one CTA per (element, run of G tiles), one warp per z-layer of the element's nodes.
+// Lane l owns velocity l of the tile. A warp keeps its layer's N1^2 values (f_s, the accumulator and
+// the x/y neighbour lines) in registers, so x and y derivatives are register-local; the z-lines cross
+// the layers and are read from a shared copy of the element tile. The z-upwind traces are split
+// over the warps (warp w interpolates the z-lines with iy = w) and shared the same way.
+// ------------------------------------------------------------------------------------------------
+template <int N1>
+struct Stage3Smem {
+    static constexpr int NP = N1 * N1 * N1;
+    float tile[NP][kWarp];        // f_s of the element, [node][lane]
+    float tz[N1 * N1][kWarp];     // z-upwind traces per z-line (ix + N1 iy)
+    float wf[NP][36];             // stage output transposed for the moment sums
+    float par[NP][kParamStride];  // BGK exponents of the element's points
+    float wpsi[5][kWarp];         // w psi of the tile's velocities
+};
+
+template <int N1, bool LEFT>
+__device__ __forceinline__ float trace_line(const float (&v)[N1], const Ops &op)
+{
+    float t = 0.f;
+#pragma unroll
+    for (int j = 1; j < N1; j++)
+        t = fmaf(LEFT ? op.lp[j] : op.lm[j], v[j] - v[0], t);
+    return v[0] + t;
+}
+
+// Derivative contribution along one register line (nodes off + STRIDE j of the layer):
+// acc_i += cd * d_i with d_i as in apply_dir.
+template <int N1, bool LEFT, int STRIDE, int NQ>
+__device__ __forceinline__ void line_update(float (&acc)[NQ], const float (&f)[NQ], int off, float T, const Ops &op,
+                                            float cd)
+{
+    constexpr int R = LEFT ? 0 : N1 - 1;
+    const float fr = f[off + STRIDE * R];
+    const float Tc = cd * (T - fr);
+    float Gv[N1];
+#pragma unroll
+    for (int j = 0; j < N1; j++)
+        Gv[j] = cd * (f[off + STRIDE * j] - fr);
+#pragma unroll
+    for (int i = 0; i < N1; i++) {
+        float s = acc[off + STRIDE * i];
+#pragma unroll
+        for (int j = 0; j < N1; j++) {
+            if (j == R)
+                continue;
+            s = fmaf(LEFT ? op.DL[i][j] : op.DR[i][j], Gv[j], s);
+        }
+        acc[off + STRIDE * i] = fmaf(LEFT ? op.gl[i] : op.gr[i], Tc, s);
+    }
+}
+
+template <int N1, int MODE>
+__global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) k_stage3(const StageArgs A)
+{
+    constexpr int NQ = N1 * N1;      // nodes per layer
+    constexpr int NP = NQ * N1;
+    constexpr int NT = kWarp * N1;   // threads
+    constexpr int NITEM = NP * 4;    // moment items: (node, quarter of the 32 velocities)
+    constexpr int NR = (NITEM + NT - 1) / NT;
+    using Sm = Stage3Smem<N1>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smraw);
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;  // w = z-layer
+    const int E = A.mesh.nelem;
+    const int gl = blockIdx.x / E;
+    const int e = blockIdx.x % E;
+    const int vl0 = gl * A.G;
+    const int vl1 = min(vl0 + A.G, A.nvt);
+    int ec[3];
+    ec[0] = e % A.mesh.ne[0];
+    ec[1] = (e / A.mesh.ne[0]) % A.mesh.ne[1];
+    ec[2] = e / (A.mesh.ne[0] * A.mesh.ne[1]);
+
+    if (MODE == 0) {
+        const float4 *src4 = reinterpret_cast<const float4 *>(A.param + (int64_t)e * NP * kParamStride);
+        float4 *dst4 = reinterpret_cast<float4 *>(&sm.par[0][0]);
+        for (int q = tid; q < NP * kParamStride / 4; q += NT)
+            dst4[q] = __ldg(src4 + q);
+    }
+    float macc[NR][5];
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int c = 0; c < 5; c++)
+            macc[r][c] = 0.f;
+    const float kb = A.b * (1.f - A.dt * A.inv_tau);
+    const float bdt = A.b * A.dt;
+
+    for (int vl = vl0; vl < vl1; vl++) {
+        const int vt = A.vt0 + vl;
+        const int slot = vt * kWarp + lane;
+        const float x0 = __ldg(A.xi + slot), x1 = __ldg(A.xi + A.nslots + slot), x2 = __ldg(A.xi + 2 * A.nslots + slot);
+        const float *tileg = A.src + fidx(vl, e, 0, lane, E, NP);
+        float f[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++)
+            f[q] = __ldg(tileg + (q + NQ * w) * kWarp);
+
+        if (MODE == 0) {
+            const bool l0 = x0 >= 0.f, l1 = x1 >= 0.f, l2 = x2 >= 0.f;
+            float acc[NQ];
+            if (A.fn) {
+                const float *fng = A.fn + fidx(vl, e, 0, lane, E, NP);
+#pragma unroll
+                for (int q = 0; q < NQ; q++)
+                    acc[q] = __ldcs(fng + (q + NQ * w) * kWarp);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NQ; q++)
+                    acc[q] = 0.f;
+            }
+            // upwind neighbour values: x-lines and y-lines of this layer, z-lines with iy = w
+            float vx[N1][N1], vy[N1][N1], vz[N1][N1];
+            const int enx = upwind_neighbour(A.mesh, ec, 0, l0);
+            const int eny = upwind_neighbour(A.mesh, ec, 1, l1);
+            const int enz = upwind_neighbour(A.mesh, ec, 2, l2);
+            if (enx >= 0) {
+                const float *nb = A.src + fidx(vl, enx, 0, lane, E, NP);
+#pragma unroll
+                for (int iy = 0; iy < N1; iy++)
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        vx[iy][j] = __ldg(nb + (j + N1 * iy + NQ * w) * kWarp);
+            }
+            if (eny >= 0) {
+                const float *nb = A.src + fidx(vl, eny, 0, lane, E, NP);
+#pragma unroll
+                for (int ix = 0; ix < N1; ix++)
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        vy[ix][j] = __ldg(nb + (ix + N1 * j + NQ * w) * kWarp);
+            }
+            if (enz >= 0) {
+                const float *nb = A.src + fidx(vl, enz, 0, lane, E, NP);
+#pragma unroll
+                for (int ix = 0; ix < N1; ix++)
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        vz[ix][j] = __ldg(nb + (ix + N1 * w + NQ * j) * kWarp);
+            }
+            // share this layer and this warp's z-traces
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                sm.tile[q + NQ * w][lane] = f[q];
+#pragma unroll
+            for (int ix = 0; ix < N1; ix++) {
+                float t;
+                if (enz >= 0)
+                    t = l2 ? trace_line<N1, true>(vz[ix], A.ops) : trace_line<N1, false>(vz[ix], A.ops);
+                else
+                    t = __ldg(A.ghost + (4 + (l2 ? 0 : 1)) * A.nslots + slot);
+                sm.tz[ix + N1 * w][lane] = t;
+            }
+            // acc = an f^n + b (1 - dt/tau) f_s, then x and y from registers
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                acc[q] = fmaf(A.an, acc[q], kb * f[q]);
+            const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt,
+                        cz = -A.mesh.inv_h2[2] * x2 * bdt;
+            const float gx = enx >= 0 ? 0.f : __ldg(A.ghost + (l0 ? 0 : 1) * A.nslots + slot);
+            const float gy = eny >= 0 ? 0.f : __ldg(A.ghost + (2 + (l1 ? 0 : 1)) * A.nslots + slot);
+#pragma unroll
+            for (int iy = 0; iy < N1; iy++) {
+                const float T = enx >= 0 ? (l0 ? trace_line<N1, true>(vx[iy], A.ops) : trace_line<N1, false>(vx[iy], A.ops)) : gx;
+                if (l0)
+                    line_update<N1, true, 1>(acc, f, N1 * iy, T, A.ops, cx);
+                else
+                    line_update<N1, false, 1>(acc, f, N1 * iy, T, A.ops, cx);
+            }
+#pragma unroll
+            for (int ix = 0; ix < N1; ix++) {
+                const float T = eny >= 0 ? (l1 ? trace_line<N1, true>(vy[ix], A.ops) : trace_line<N1, false>(vy[ix], A.ops)) : gy;
+                if (l1)
+                    line_update<N1, true, N1>(acc, f, ix, T, A.ops, cy);
+                else
+                    line_update<N1, false, N1>(acc, f, ix, T, A.ops, cy);
+            }
+            __syncthreads();  // B1: tile and z-traces complete
+            // z: node (ix, iy, w) on the z-line (ix, iy), read from the shared tile; row w of the merged
+            // operator (the layer index is warp-uniform)
+            {
+                float row[N1], gw = 0.f;
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    row[j] = 0.f;
+#pragma unroll
+                for (int ww = 0; ww < N1; ww++)
+                    if (ww == w) {
+#pragma unroll
+                        for (int j = 0; j < N1; j++)
+                            row[j] = l2 ? A.ops.DL[ww][j] : A.ops.DR[ww][j];
+                        gw = l2 ? A.ops.gl[ww] : A.ops.gr[ww];
+                    }
+#pragma unroll
+                for (int q = 0; q < NQ; q++) {
+                    float fl[N1];
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        fl[j] = sm.tile[q + NQ * j][lane];
+                    const float fr = l2 ? fl[0] : fl[N1 - 1];
+                    float s = gw * (sm.tz[q][lane] - fr);
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        s = fmaf(row[j], fl[j] - fr, s);  // the reference node contributes 0
+                    acc[q] = fmaf(cz, s, acc[q]);
+                }
+            }
+            // BGK source and store
+            if (w == 0) {
+#pragma unroll
+                for (int c = 0; c < 5; c++)
+                    sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+            }
+            const float cg = bdt * A.inv_tau * __ldg(A.gmask + slot);
+            const float xs = x0 * x0 + x1 * x1 + x2 * x2;
+            float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                const int i = q + NQ * w;
+                const float4 pb = *reinterpret_cast<const float4 *>(&sm.par[i][0]);
+                const float b4 = sm.par[i][4];
+                const float ex = fmaf(b4, xs, fmaf(pb.w, x2, fmaf(pb.z, x1, fmaf(pb.y, x0, pb.x))));
+                const float o = fmaf(cg, exp2f(ex), acc[q]);
+                __stcs(dst + i * kWarp, o);
+                sm.wf[i][lane] = o;
+            }
+        } else {
+            __syncthreads();  // B1 (keeps the barrier count equal in both modes)
+            if (w == 0) {
+#pragma unroll
+                for (int c = 0; c < 5; c++)
+                    sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                sm.wf[q + NQ * w][lane] = f[q];
+        }
+        __syncthreads();  // B2: wf and wpsi complete
+        // moment sums: item = (node, quarter kq of the velocities); the 4 quarters of a node sit in
+        // 4 consecutive lanes and are combined by shuffles
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            const int it = tid + r * NT;
+            const int nd = it >> 2, kq = it & 3;
+            unsigned long long m[5];
+#pragma unroll
+            for (int c = 0; c < 5; c++)
+                m[c] = 0ull;
+            if (nd < NP) {
+#pragma unroll
+                for (int k = 0; k < 8; k += 4) {
+                    const int kk = kq * 8 + k;
+                    const float4 v = *reinterpret_cast<const float4 *>(&sm.wf[nd][kk]);
+                    const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
+#pragma unroll
+                    for (int c = 0; c < 5; c++) {
+                        const float4 wv = *reinterpret_cast<const float4 *>(&sm.wpsi[c][kk]);
+                        m[c] = ffma2(pack2(wv.x, wv.y), v01, m[c]);
+                        m[c] = ffma2(pack2(wv.z, wv.w), v23, m[c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 5; c++) {
+                float x = sum2(m[c]);
+                x += __shfl_xor_sync(0xffffffffu, x, 1);
+                x += __shfl_xor_sync(0xffffffffu, x, 2);
+                macc[r][c] += x;
+            }
+        }
+    }
+    // partial moments of this task (the kq = 0 lane of every node writes)
+    const int grp = A.group0 + gl;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        const int it = tid + r * NT;
+        const int nd = it >> 2, kq = it & 3;
+        if (nd < NP && kq == 0)
+#pragma unroll
+            for (int c = 0; c < 5; c++)
+                A.partial[((int64_t)grp * 5 + c) * A.npts + (int64_t)e * NP + nd] = macc[r][c];
+    }
+}
+
 template <int N1, int DIM>
 static cudaError_t prepare_nd()
 {
-    const int smem = (int)sizeof(StageSmem<Geo<N1, DIM>::NP>);
-    cudaError_t err = cudaFuncSetAttribute(k_stage<N1, DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_stage<N1, DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return err;
+    if constexpr (DIM == 3) {
+        const int smem3 = (int)sizeof(Stage3Smem<N1>);
+        cudaError_t err = cudaFuncSetAttribute(k_stage3<N1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_stage3<N1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
+        return err;
+    } else {
+        const int smem = (int)sizeof(StageSmem<Geo<N1, DIM>::NP>);
+        cudaError_t err = cudaFuncSetAttribute(k_stage<N1, DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_stage<N1, DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        return err;
+    }
 }
 
 template <int N1, int DIM>
 static cudaError_t launch_nd(const StageArgs &A, int mode, cudaStream_t s)
 {
-    const int nEB = (A.mesh.nelem + kWarpsPerCta - 1) / kWarpsPerCta;
-    const int ngroups = (A.nvt + A.G - 1) / A.G;
-    dim3 grid(nEB * ngroups), block(kWarp * kWarpsPerCta);
-    const int smem = (int)sizeof(StageSmem<Geo<N1, DIM>::NP>);
-    if (mode == 0)
-        k_stage<N1, DIM, 0><<<grid, block, smem, s>>>(A);
-    else
-        k_stage<N1, DIM, 1><<<grid, block, smem, s>>>(A);
-    return cudaGetLastError();
+    if constexpr (DIM == 3) {
+        const int ngroups3 = (A.nvt + A.G - 1) / A.G;
+        const int smem3 = (int)sizeof(Stage3Smem<N1>);
+        dim3 grid3(A.mesh.nelem * ngroups3), block3(kWarp * N1);
+        if (mode == 0)
+            k_stage3<N1, 0><<<grid3, block3, smem3, s>>>(A);
+        else
+            k_stage3<N1, 1><<<grid3, block3, smem3, s>>>(A);
+        return cudaGetLastError();
+    } else {
+        const int nEB = (A.mesh.nelem + kWarpsPerCta - 1) / kWarpsPerCta;
+        const int ngroups = (A.nvt + A.G - 1) / A.G;
+        dim3 grid(nEB * ngroups), block(kWarp * kWarpsPerCta);
+        const int smem = (int)sizeof(StageSmem<Geo<N1, DIM>::NP>);
+        if (mode == 0)
+            k_stage<N1, DIM, 0><<<grid, block, smem, s>>>(A);
+        else
+            k_stage<N1, DIM, 1><<<grid, block, smem, s>>>(A);
+        return cudaGetLastError();
+    }
 }
 
 #define BGK_DISPATCH(FN, ...)                                                        \
