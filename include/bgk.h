@@ -142,6 +142,34 @@ int bgk_set_timing(bgk_ctx *ctx, int on);
 int bgk_timing(bgk_ctx *ctx, double *stage_ms, int64_t *stage_launches, double *newton_ms,
                int64_t *newton_launches, double *stage_alg_bytes);
 
+/* ---------------------------------------------------------------------------------------------
+ * Allocation-free entry point. The paper has no counterpart: this exists for callers that cannot
+ * call cudaMalloc (code running under another framework's device-memory pool or allocator hooks,
+ * processes with a no-allocation policy after start-up, or ones whose device footprint is fixed
+ * once sized), for whom bgk_create, which allocates its own buffers, is not an option.
+ *
+ * bgk_equilibrium_noalloc computes the moments Q and the discretely-conservative Maxwellian
+ * (rho', U', theta') of every point of a distribution function that the caller already holds on
+ * the device -- the same quantities that bgk_moments / bgk_equilibrium return for a context after
+ * bgk_set_f -- and allocates nothing:
+ *   d_f     device, FP32, [npts][N_v], velocity order k = kx + n[0] * (ky + n[1] * kz) (read only);
+ *   vg      the uniform velocity grid (host struct, read during the call);
+ *   d_Q     device, FP64, [npts][5] (rho, rho u, rho v, rho w, E), written;
+ *   d_prim  device, FP64, [npts][5] (rho', U'x, U'y, U'z, theta'), written;
+ *   stream  cudaStream_t to run on (NULL: the legacy default stream). The call waits for its own
+ *           work on that stream and returns its status (BGK_OK, BGK_EDOMAIN, BGK_ENEWTON).
+ * Scratch: one static device array of BGK_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the
+ * library until the process exits. It must hold 4 * (64 + npts * (5 * ceil(N_v / 2048) + 8)) bytes;
+ * larger requests return BGK_EINVAL with a message on stderr, before any work is enqueued.
+ * The first call on a device looks up that device's address of the array (with the device
+ * current); make that first call before any stream capture. Every call uses the same array, which
+ * keeps the last call's contents: calls that overlap on the GPU (other streams, other host threads)
+ * race on it, so serialise them. No cudaMalloc, cudaFree or allocating library routine is called.
+ * ------------------------------------------------------------------------------------------- */
+#define BGK_NOALLOC_SCRATCH_BYTES (16ll << 20)
+int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk_vgrid *vg, double *d_Q, double *d_prim,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ SYMBOLS = (
     "bgk_create", "bgk_destroy", "bgk_last_error", "bgk_set_stream", "bgk_info", "bgk_points",
     "bgk_set_state", "bgk_set_state_device", "bgk_set_f", "bgk_get_f", "bgk_step", "bgk_moments",
     "bgk_moments_device", "bgk_equilibrium", "bgk_synchronize", "bgk_dt", "bgk_set_timing", "bgk_timing",
+    "bgk_equilibrium_noalloc",
 )
 
 
@@ -82,6 +83,7 @@ def lib():
             L.bgk_dt.restype = C.c_double
             L.bgk_set_timing.argtypes = [vp, C.c_int]
             L.bgk_timing.argtypes = [vp, dp, i64p, dp, i64p, dp]
+            L.bgk_equilibrium_noalloc.argtypes = [vp, C.c_int64, C.POINTER(bgk_vgrid), vp, vp, vp]
             _lib = L
     return _lib
 
@@ -134,6 +136,18 @@ def make_opts(precision=FP32_SPLIT, body_force=(0.0, 0.0, 0.0), newton_max_it=0,
     o.chunks = chunks
     o.vtiles_per_task = vtiles_per_task
     return o
+
+
+def equilibrium_noalloc(f_dev, nv, vlo, vhi, Q_dev, prim_dev, stream_ptr=0):
+    """bgk_equilibrium_noalloc on caller-owned CUDA tensors: f_dev float32 [npts, N_v], Q_dev and
+    prim_dev float64 [npts, 5]. For callers that cannot allocate device memory: the library uses
+    only its fixed static scratch. Returns the status code (0 on success)."""
+    assert f_dev.is_cuda and f_dev.dtype.itemsize == 4 and f_dev.is_contiguous()
+    assert Q_dev.is_cuda and prim_dev.is_cuda and Q_dev.is_contiguous() and prim_dev.is_contiguous()
+    vg = make_vgrid(nv, vlo, vhi)
+    return lib().bgk_equilibrium_noalloc(C.c_void_p(f_dev.data_ptr()), int(f_dev.shape[0]), C.byref(vg),
+                                         C.c_void_p(Q_dev.data_ptr()), C.c_void_p(prim_dev.data_ptr()),
+                                         C.c_void_p(stream_ptr or 0))
 
 
 class Solver:
