@@ -349,12 +349,38 @@ template <int N1>
 struct Stage3Smem {
     static constexpr int NP = N1 * N1 * N1;
     float tile[NP][kWarp];        // f_s of the element, [node][lane]
-    float tz[N1 * N1][kWarp];     // z-upwind traces per z-line (ix + N1 iy)
-    float wf[NP][36];             // stage output transposed for the moment sums
+    float zc[NP][kWarp];          // z-derivative sums, [node][lane]
+    float wf[N1][16][36];         // per warp: its layer's stage output, [node][velocity] (16 rows)
     float par[NP][kParamStride];  // BGK exponents of the element's points
     float wpsi[5][kWarp];         // w psi of the tile's velocities
 };
 
+// The 1-D line computation shared by the three directions: for the line values fl (inflow end R,
+// upwind trace T) returns s_i = sum_{j != R} Dm[i][j] (f_j - f_R) + g_i (T - f_R) for all nodes i
+// (Dm = D - g (x) l, the derivative with the interior trace folded in; d f_i/dt gains cd * s_i).
+template <int N1, bool LEFT>
+__device__ __forceinline__ void line_sums(float (&s)[N1], const float (&fl)[N1], float T, const Ops &op)
+{
+    constexpr int R = LEFT ? 0 : N1 - 1;
+    const float fr = fl[R];
+    const float tr = T - fr;
+    float G[N1];
+#pragma unroll
+    for (int j = 0; j < N1; j++)
+        G[j] = fl[j] - fr;
+#pragma unroll
+    for (int i = 0; i < N1; i++) {
+        float v = (LEFT ? op.gl[i] : op.gr[i]) * tr;
+#pragma unroll
+        for (int j = 0; j < N1; j++)
+            if (j != R)
+                v = fmaf(LEFT ? op.DL[i][j] : op.DR[i][j], G[j], v);
+        s[i] = v;
+    }
+}
+
+// Upwind trace of one neighbour line v (difference form, exact for a constant state): a left
+// neighbour is evaluated at its +1 end (lp), a right neighbour at its -1 end (lm).
 template <int N1, bool LEFT>
 __device__ __forceinline__ float trace_line(const float (&v)[N1], const Ops &op)
 {
@@ -365,45 +391,17 @@ __device__ __forceinline__ float trace_line(const float (&v)[N1], const Ops &op)
     return v[0] + t;
 }
 
-// Derivative contribution along one register line (nodes off + STRIDE j of the layer):
-// acc_i += cd * d_i with d_i as in apply_dir.
-template <int N1, bool LEFT, int STRIDE, int NQ>
-__device__ __forceinline__ void line_update(float (&acc)[NQ], const float (&f)[NQ], int off, float T, const Ops &op,
-                                            float cd)
-{
-    constexpr int R = LEFT ? 0 : N1 - 1;
-    const float fr = f[off + STRIDE * R];
-    const float Tc = cd * (T - fr);
-    float Gv[N1];
-#pragma unroll
-    for (int j = 0; j < N1; j++)
-        Gv[j] = cd * (f[off + STRIDE * j] - fr);
-#pragma unroll
-    for (int i = 0; i < N1; i++) {
-        float s = acc[off + STRIDE * i];
-#pragma unroll
-        for (int j = 0; j < N1; j++) {
-            if (j == R)
-                continue;
-            s = fmaf(LEFT ? op.DL[i][j] : op.DR[i][j], Gv[j], s);
-        }
-        acc[off + STRIDE * i] = fmaf(LEFT ? op.gl[i] : op.gr[i], Tc, s);
-    }
-}
-
 template <int N1, int MODE>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) k_stage3(const StageArgs A)
 {
     constexpr int NQ = N1 * N1;      // nodes per layer
     constexpr int NP = NQ * N1;
     constexpr int NT = kWarp * N1;   // threads
-    constexpr int NITEM = NP * 4;    // moment items: (node, quarter of the 32 velocities)
-    constexpr int NR = (NITEM + NT - 1) / NT;
     using Sm = Stage3Smem<N1>;
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm &sm = *reinterpret_cast<Sm *>(smraw);
 
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;  // w = z-layer
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;  // w: this warp's z-layer and y-slice
     const int E = A.mesh.nelem;
     const int gl = blockIdx.x / E;
     const int e = blockIdx.x % E;
@@ -420,12 +418,16 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) 
         for (int q = tid; q < NP * kParamStride / 4; q += NT)
             dst4[q] = __ldg(src4 + q);
     }
-    float macc[NR][5];
+    // moment sums: lane = (node pair np = lane / 4: layer nodes np and np + 8) x (velocity eighth
+    // kg = lane % 4: velocities 8 kg .. 8 kg + 7 of every tile); FP32 pairs over even/odd velocities,
+    // accumulated over the whole task and combined across the 4 lanes of a pair at the end
+    const int np = lane >> 2, kg = lane & 3;
+    unsigned long long ms[2][5];
 #pragma unroll
-    for (int r = 0; r < NR; r++)
+    for (int h = 0; h < 2; h++)
 #pragma unroll
         for (int c = 0; c < 5; c++)
-            macc[r][c] = 0.f;
+            ms[h][c] = 0ull;
     const float kb = A.b * (1.f - A.dt * A.inv_tau);
     const float bdt = A.b * A.dt;
 
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) 
 #pragma unroll
         for (int q = 0; q < NQ; q++)
             f[q] = __ldg(tileg + (q + NQ * w) * kWarp);
-
+        float o[NQ];
         if (MODE == 0) {
             const bool l0 = x0 >= 0.f, l1 = x1 >= 0.f, l2 = x2 >= 0.f;
             float acc[NQ];
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) 
                 for (int q = 0; q < NQ; q++)
                     acc[q] = 0.f;
             }
-            // upwind neighbour values: x-lines and y-lines of this layer, z-lines with iy = w
+            // upwind neighbour values: x-lines and y-lines of layer w, z-lines of slice iy = w
             float vx[N1][N1], vy[N1][N1], vz[N1][N1];
             const int enx = upwind_neighbour(A.mesh, ec, 0, l0);
             const int eny = upwind_neighbour(A.mesh, ec, 1, l1);
@@ -481,20 +483,10 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) 
                     for (int j = 0; j < N1; j++)
                         vz[ix][j] = __ldg(nb + (ix + N1 * w + NQ * j) * kWarp);
             }
-            // share this layer and this warp's z-traces
 #pragma unroll
             for (int q = 0; q < NQ; q++)
                 sm.tile[q + NQ * w][lane] = f[q];
-#pragma unroll
-            for (int ix = 0; ix < N1; ix++) {
-                float t;
-                if (enz >= 0)
-                    t = l2 ? trace_line<N1, true>(vz[ix], A.ops) : trace_line<N1, false>(vz[ix], A.ops);
-                else
-                    t = __ldg(A.ghost + (4 + (l2 ? 0 : 1)) * A.nslots + slot);
-                sm.tz[ix + N1 * w][lane] = t;
-            }
-            // acc = an f^n + b (1 - dt/tau) f_s, then x and y from registers
+            // acc = an f^n + b (1 - dt/tau) f_s, then x and y lines from registers
 #pragma unroll
             for (int q = 0; q < NQ; q++)
                 acc[q] = fmaf(A.an, acc[q], kb * f[q]);
@@ -502,58 +494,59 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) 
                         cz = -A.mesh.inv_h2[2] * x2 * bdt;
             const float gx = enx >= 0 ? 0.f : __ldg(A.ghost + (l0 ? 0 : 1) * A.nslots + slot);
             const float gy = eny >= 0 ? 0.f : __ldg(A.ghost + (2 + (l1 ? 0 : 1)) * A.nslots + slot);
+            const float gz = enz >= 0 ? 0.f : __ldg(A.ghost + (4 + (l2 ? 0 : 1)) * A.nslots + slot);
 #pragma unroll
             for (int iy = 0; iy < N1; iy++) {
-                const float T = enx >= 0 ? (l0 ? trace_line<N1, true>(vx[iy], A.ops) : trace_line<N1, false>(vx[iy], A.ops)) : gx;
+                float fl[N1], sv[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    fl[j] = f[j + N1 * iy];
                 if (l0)
-                    line_update<N1, true, 1>(acc, f, N1 * iy, T, A.ops, cx);
+                    line_sums<N1, true>(sv, fl, enx >= 0 ? trace_line<N1, true>(vx[iy], A.ops) : gx, A.ops);
                 else
-                    line_update<N1, false, 1>(acc, f, N1 * iy, T, A.ops, cx);
+                    line_sums<N1, false>(sv, fl, enx >= 0 ? trace_line<N1, false>(vx[iy], A.ops) : gx, A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
             }
 #pragma unroll
             for (int ix = 0; ix < N1; ix++) {
-                const float T = eny >= 0 ? (l1 ? trace_line<N1, true>(vy[ix], A.ops) : trace_line<N1, false>(vy[ix], A.ops)) : gy;
-                if (l1)
-                    line_update<N1, true, N1>(acc, f, ix, T, A.ops, cy);
-                else
-                    line_update<N1, false, N1>(acc, f, ix, T, A.ops, cy);
-            }
-            __syncthreads();  // B1: tile and z-traces complete
-            // z: node (ix, iy, w) on the z-line (ix, iy), read from the shared tile; row w of the merged
-            // operator (the layer index is warp-uniform)
-            {
-                float row[N1], gw = 0.f;
+                float fl[N1], sv[N1];
 #pragma unroll
                 for (int j = 0; j < N1; j++)
-                    row[j] = 0.f;
+                    fl[j] = f[ix + N1 * j];
+                if (l1)
+                    line_sums<N1, true>(sv, fl, eny >= 0 ? trace_line<N1, true>(vy[ix], A.ops) : gy, A.ops);
+                else
+                    line_sums<N1, false>(sv, fl, eny >= 0 ? trace_line<N1, false>(vy[ix], A.ops) : gy, A.ops);
 #pragma unroll
-                for (int ww = 0; ww < N1; ww++)
-                    if (ww == w) {
-#pragma unroll
-                        for (int j = 0; j < N1; j++)
-                            row[j] = l2 ? A.ops.DL[ww][j] : A.ops.DR[ww][j];
-                        gw = l2 ? A.ops.gl[ww] : A.ops.gr[ww];
-                    }
-#pragma unroll
-                for (int q = 0; q < NQ; q++) {
-                    float fl[N1];
-#pragma unroll
-                    for (int j = 0; j < N1; j++)
-                        fl[j] = sm.tile[q + NQ * j][lane];
-                    const float fr = l2 ? fl[0] : fl[N1 - 1];
-                    float s = gw * (sm.tz[q][lane] - fr);
-#pragma unroll
-                    for (int j = 0; j < N1; j++)
-                        s = fmaf(row[j], fl[j] - fr, s);  // the reference node contributes 0
-                    acc[q] = fmaf(cz, s, acc[q]);
-                }
+                for (int j = 0; j < N1; j++)
+                    acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
             }
-            // BGK source and store
+            __syncthreads();  // B1: the element tile is complete
             if (w == 0) {
 #pragma unroll
                 for (int c = 0; c < 5; c++)
                     sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
             }
+            // z-lines of slice iy = w (all layers), from the shared tile; results to zc
+#pragma unroll
+            for (int ix = 0; ix < N1; ix++) {
+                const int q = ix + N1 * w;
+                float fl[N1], sv[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    fl[j] = sm.tile[q + NQ * j][lane];
+                if (l2)
+                    line_sums<N1, true>(sv, fl, enz >= 0 ? trace_line<N1, true>(vz[ix], A.ops) : gz, A.ops);
+                else
+                    line_sums<N1, false>(sv, fl, enz >= 0 ? trace_line<N1, false>(vz[ix], A.ops) : gz, A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    sm.zc[q + NQ * j][lane] = sv[j];
+            }
+            __syncthreads();  // B2: z-sums complete
+            // BGK source towards the conservative Maxwellian, Shu-Osher combination, store
             const float cg = bdt * A.inv_tau * __ldg(A.gmask + slot);
             const float xs = x0 * x0 + x1 * x1 + x2 * x2;
             float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
@@ -563,65 +556,63 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? 4 : (N1 == 3 ? 6 : 8))) 
                 const float4 pb = *reinterpret_cast<const float4 *>(&sm.par[i][0]);
                 const float b4 = sm.par[i][4];
                 const float ex = fmaf(b4, xs, fmaf(pb.w, x2, fmaf(pb.z, x1, fmaf(pb.y, x0, pb.x))));
-                const float o = fmaf(cg, exp2f(ex), acc[q]);
-                __stcs(dst + i * kWarp, o);
-                sm.wf[i][lane] = o;
+                const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
+                o[q] = fmaf(cg, exp2f(ex), a);
+                __stcs(dst + i * kWarp, o[q]);
             }
         } else {
-            __syncthreads();  // B1 (keeps the barrier count equal in both modes)
+            __syncthreads();  // B1 (same barrier sequence in both modes)
             if (w == 0) {
 #pragma unroll
                 for (int c = 0; c < 5; c++)
                     sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
             }
+            __syncthreads();  // B2
 #pragma unroll
             for (int q = 0; q < NQ; q++)
-                sm.wf[q + NQ * w][lane] = f[q];
+                o[q] = f[q];
         }
-        __syncthreads();  // B2: wf and wpsi complete
-        // moment sums: item = (node, quarter kq of the velocities); the 4 quarters of a node sit in
-        // 4 consecutive lanes and are combined by shuffles
+        // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values
 #pragma unroll
-        for (int r = 0; r < NR; r++) {
-            const int it = tid + r * NT;
-            const int nd = it >> 2, kq = it & 3;
-            unsigned long long m[5];
+        for (int q = 0; q < NQ; q++)
+            sm.wf[w][q][lane] = o[q];
+        __syncwarp();
 #pragma unroll
-            for (int c = 0; c < 5; c++)
-                m[c] = 0ull;
-            if (nd < NP) {
-#pragma unroll
-                for (int k = 0; k < 8; k += 4) {
-                    const int kk = kq * 8 + k;
-                    const float4 v = *reinterpret_cast<const float4 *>(&sm.wf[nd][kk]);
-                    const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
-#pragma unroll
-                    for (int c = 0; c < 5; c++) {
-                        const float4 wv = *reinterpret_cast<const float4 *>(&sm.wpsi[c][kk]);
-                        m[c] = ffma2(pack2(wv.x, wv.y), v01, m[c]);
-                        m[c] = ffma2(pack2(wv.z, wv.w), v23, m[c]);
-                    }
-                }
-            }
+        for (int k = 0; k < 8; k += 4) {
+            const int kk = 8 * kg + k;
+            unsigned long long wv[5][2];
 #pragma unroll
             for (int c = 0; c < 5; c++) {
-                float x = sum2(m[c]);
-                x += __shfl_xor_sync(0xffffffffu, x, 1);
-                x += __shfl_xor_sync(0xffffffffu, x, 2);
-                macc[r][c] += x;
+                const float4 w4 = *reinterpret_cast<const float4 *>(&sm.wpsi[c][kk]);
+                wv[c][0] = pack2(w4.x, w4.y);
+                wv[c][1] = pack2(w4.z, w4.w);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const float4 v = *reinterpret_cast<const float4 *>(&sm.wf[w][np + 8 * h][kk]);
+                const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
+#pragma unroll
+                for (int c = 0; c < 5; c++) {
+                    ms[h][c] = ffma2(wv[c][0], v01, ms[h][c]);
+                    ms[h][c] = ffma2(wv[c][1], v23, ms[h][c]);
+                }
             }
         }
+        __syncwarp();
     }
-    // partial moments of this task (the kq = 0 lane of every node writes)
+    // partial moments of this task: combine the 4 velocity eighths of every node pair
     const int grp = A.group0 + gl;
 #pragma unroll
-    for (int r = 0; r < NR; r++) {
-        const int it = tid + r * NT;
-        const int nd = it >> 2, kq = it & 3;
-        if (nd < NP && kq == 0)
+    for (int h = 0; h < 2; h++) {
+        const int q = np + 8 * h;
 #pragma unroll
-            for (int c = 0; c < 5; c++)
-                A.partial[((int64_t)grp * 5 + c) * A.npts + (int64_t)e * NP + nd] = macc[r][c];
+        for (int c = 0; c < 5; c++) {
+            float x = sum2(ms[h][c]);
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            if (kg == 0 && q < NQ)
+                A.partial[((int64_t)grp * 5 + c) * A.npts + (int64_t)e * NP + q + NQ * w] = x;
+        }
     }
 }
 
