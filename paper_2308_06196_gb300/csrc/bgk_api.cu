@@ -20,7 +20,7 @@
 #include "bgk_common.cuh"
 
 namespace bgk {
-cudaError_t launch_stage(const StageArgs &A, int p, int mode, cudaStream_t s);
+cudaError_t launch_stage(const StageArgs &A, int p, int mode, int oct, cudaStream_t s);
 cudaError_t prepare_stage(int dim, int p);
 cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s);
 cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slotk, int nvt, int E, int NP,
@@ -38,6 +38,7 @@ const double kPi = 3.14159265358979323846;
 
 struct Chunk {
     int vt0, nvt, group0, ngroups;
+    int oct;  // sign octant of every tile (bit d: xi_d >= 0), 8 when the chunk mixes octants
 };
 
 // Gauss-Legendre nodes and weights on [-1, 1]: Newton on P_n with P_n' = n (x P_n - P_{n-1}) / (x^2 - 1).
@@ -279,7 +280,7 @@ int prologue(bgk_ctx *c, cudaStream_t s)
     for (const Chunk &ch : c->chunks) {
         StageArgs A = stage_args(c, ch);
         A.src = chunk_ptr(c, c->fA, ch.vt0);
-        CK(launch_stage(A, c->p, 1, s));
+        CK(launch_stage(A, c->p, 1, ch.oct, s));
     }
     CK(launch_newton(newton_args(c, 1), s));
     return BGK_OK;
@@ -323,7 +324,7 @@ int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
             for (int v = ch.vt0 * kWarp; v < (ch.vt0 + ch.nvt) * kWarp; v++)
                 real += c->slotk[v] >= 0;
             ev_begin(c, 0, (double)real * c->npts * sizeof(float) * (st == 0 ? 2 : 3));
-            CK(launch_stage(A, c->p, 0, s));
+            CK(launch_stage(A, c->p, 0, ch.oct, s));
             ev_end(c);
         }
         ev_begin(c, 1, 0.0);
@@ -450,6 +451,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         if (n == 0)
             continue;
         Chunk ch{};
+        ch.oct = o;
         ch.vt0 = (int)(c->slotk.size() / kWarp);
         for (int kz : Z)
             for (int ky : Y)
@@ -463,7 +465,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     c->nvt = (int)(c->slotk.size() / kWarp);
     c->nslots = c->nvt * kWarp;
     if (c->opts.chunks == 1 && c->chunks.size() > 1) {
-        Chunk all{0, c->nvt, 0, 0};
+        Chunk all{0, c->nvt, 0, 0, 8};
         c->chunks.assign(1, all);
     }
     int maxc = 0;

@@ -1,0 +1,303 @@
+// k_stage3.cuh -- the fused SSP-RK3 stage kernel for hexahedra (FP32-split form); instantiated per
+// degree in k_stage3_p*.cu so the octant variants compile in parallel.
+#pragma once
+#include "stage_common.cuh"
+
+// Resident CTAs per SM the register allocation is sized for (p = 3 / p = 2 / p = 1).
+#ifndef BGK_STAGE3_MINCTAS_P3
+#define BGK_STAGE3_MINCTAS_P3 4
+#endif
+#ifndef BGK_STAGE3_MINCTAS_P2
+#define BGK_STAGE3_MINCTAS_P2 6
+#endif
+
+namespace bgk {
+
+// ------------------------------------------------------------------------------------------------
+// Hexahedra: one CTA per (element, run of G tiles), one warp per z-layer of the element's nodes.
+// Lane l owns velocity l of the tile. A warp keeps its layer's N1^2 values (f_s, the accumulator and
+// the x/y neighbour lines) in registers, so x and y derivatives are register-local; the z-lines cross
+// the layers and are read from a shared copy of the element tile. The z-upwind traces are split
+// over the warps (warp w interpolates the z-lines with iy = w) and shared the same way.
+// ------------------------------------------------------------------------------------------------
+template <int N1>
+struct Stage3Smem {
+    static constexpr int NP = N1 * N1 * N1;
+    float tile[NP][kWarp];        // f_s of the element, [node][lane]
+    float zc[NP][kWarp];          // z-derivative sums, [node][lane]
+    float wf[N1][16][36];         // per warp: its layer's stage output, [node][velocity] (16 rows)
+    float par[NP][kParamStride];  // BGK exponents of the element's points
+    float wpsi[5][kWarp];         // w psi of the tile's velocities
+};
+
+// OCT in 0..7: every tile of the launch lies in that sign octant (bit d set: xi_d >= 0, the upwind
+// neighbour in direction d is on the low side); OCT = 8: the octant is read per tile.
+template <int N1, int MODE, int OCT>
+__global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
+{
+    constexpr int NQ = N1 * N1;      // nodes per layer
+    constexpr int NP = NQ * N1;
+    constexpr int NT = kWarp * N1;   // threads
+    using Sm = Stage3Smem<N1>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smraw);
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;  // w: this warp's z-layer and y-slice
+    const int E = A.mesh.nelem;
+    const int gl = blockIdx.x / E;
+    const int e = blockIdx.x % E;
+    const int vl0 = gl * A.G;
+    const int vl1 = min(vl0 + A.G, A.nvt);
+    int ec[3];
+    ec[0] = e % A.mesh.ne[0];
+    ec[1] = (e / A.mesh.ne[0]) % A.mesh.ne[1];
+    ec[2] = e / (A.mesh.ne[0] * A.mesh.ne[1]);
+
+    if (MODE == 0) {
+        const float4 *src4 = reinterpret_cast<const float4 *>(A.param + (int64_t)e * NP * kParamStride);
+        float4 *dst4 = reinterpret_cast<float4 *>(&sm.par[0][0]);
+        for (int q = tid; q < NP * kParamStride / 4; q += NT)
+            dst4[q] = __ldg(src4 + q);
+    }
+    // moment sums: lane = (node pair np = lane / 4: layer nodes np and np + 8) x (velocity eighth
+    // kg = lane % 4: velocities 8 kg .. 8 kg + 7 of every tile); FP32 pairs over even/odd velocities,
+    // accumulated over the whole task and combined across the 4 lanes of a pair at the end
+    const int np = lane >> 2, kg = lane & 3;
+    unsigned long long ms[2][5];
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int c = 0; c < 5; c++)
+            ms[h][c] = 0ull;
+    const float kb = A.b * (1.f - A.dt * A.inv_tau);
+    const float bdt = A.b * A.dt;
+
+    for (int vl = vl0; vl < vl1; vl++) {
+        const int vt = A.vt0 + vl;
+        const int slot = vt * kWarp + lane;
+        const float x0 = __ldg(A.xi + slot), x1 = __ldg(A.xi + A.nslots + slot), x2 = __ldg(A.xi + 2 * A.nslots + slot);
+        const float *tileg = A.src + fidx(vl, e, 0, lane, E, NP);
+        float f[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++)
+            f[q] = __ldg(tileg + (q + NQ * w) * kWarp);
+        float o[NQ];
+        if (MODE == 0) {
+            const bool l0 = OCT < 8 ? (OCT & 1) != 0 : x0 >= 0.f;
+            const bool l1 = OCT < 8 ? (OCT & 2) != 0 : x1 >= 0.f;
+            const bool l2 = OCT < 8 ? (OCT & 4) != 0 : x2 >= 0.f;
+            float acc[NQ];
+            if (A.fn) {
+                const float *fng = A.fn + fidx(vl, e, 0, lane, E, NP);
+#pragma unroll
+                for (int q = 0; q < NQ; q++)
+                    acc[q] = __ldcs(fng + (q + NQ * w) * kWarp);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NQ; q++)
+                    acc[q] = 0.f;
+            }
+            // upwind neighbour values: x-lines and y-lines of layer w, z-lines of slice iy = w
+            float vx[N1][N1], vy[N1][N1], vz[N1][N1];
+            const int enx = upwind_neighbour(A.mesh, ec, 0, l0);
+            const int eny = upwind_neighbour(A.mesh, ec, 1, l1);
+            const int enz = upwind_neighbour(A.mesh, ec, 2, l2);
+            if (enx >= 0) {
+                const float *nb = A.src + fidx(vl, enx, 0, lane, E, NP);
+#pragma unroll
+                for (int iy = 0; iy < N1; iy++)
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        vx[iy][j] = __ldg(nb + (j + N1 * iy + NQ * w) * kWarp);
+            }
+            if (eny >= 0) {
+                const float *nb = A.src + fidx(vl, eny, 0, lane, E, NP);
+#pragma unroll
+                for (int ix = 0; ix < N1; ix++)
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        vy[ix][j] = __ldg(nb + (ix + N1 * j + NQ * w) * kWarp);
+            }
+            if (enz >= 0) {
+                const float *nb = A.src + fidx(vl, enz, 0, lane, E, NP);
+#pragma unroll
+                for (int ix = 0; ix < N1; ix++)
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        vz[ix][j] = __ldg(nb + (ix + N1 * w + NQ * j) * kWarp);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                sm.tile[q + NQ * w][lane] = f[q];
+            // acc = an f^n + b (1 - dt/tau) f_s, then x and y lines from registers
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                acc[q] = fmaf(A.an, acc[q], kb * f[q]);
+            const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt,
+                        cz = -A.mesh.inv_h2[2] * x2 * bdt;
+            const float gx = enx >= 0 ? 0.f : __ldg(A.ghost + (l0 ? 0 : 1) * A.nslots + slot);
+            const float gy = eny >= 0 ? 0.f : __ldg(A.ghost + (2 + (l1 ? 0 : 1)) * A.nslots + slot);
+            const float gz = enz >= 0 ? 0.f : __ldg(A.ghost + (4 + (l2 ? 0 : 1)) * A.nslots + slot);
+#pragma unroll
+            for (int iy = 0; iy < N1; iy++) {
+                float fl[N1], sv[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    fl[j] = f[j + N1 * iy];
+                if (l0)
+                    line_sums<N1, true>(sv, fl, enx >= 0 ? trace_line<N1, true>(vx[iy], A.ops) : gx, A.ops);
+                else
+                    line_sums<N1, false>(sv, fl, enx >= 0 ? trace_line<N1, false>(vx[iy], A.ops) : gx, A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
+            }
+#pragma unroll
+            for (int ix = 0; ix < N1; ix++) {
+                float fl[N1], sv[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    fl[j] = f[ix + N1 * j];
+                if (l1)
+                    line_sums<N1, true>(sv, fl, eny >= 0 ? trace_line<N1, true>(vy[ix], A.ops) : gy, A.ops);
+                else
+                    line_sums<N1, false>(sv, fl, eny >= 0 ? trace_line<N1, false>(vy[ix], A.ops) : gy, A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
+            }
+            __syncthreads();  // B1: the element tile is complete
+            if (w == 0) {
+#pragma unroll
+                for (int c = 0; c < 5; c++)
+                    sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+            }
+            // z-lines of slice iy = w (all layers), from the shared tile; results to zc
+#pragma unroll
+            for (int ix = 0; ix < N1; ix++) {
+                const int q = ix + N1 * w;
+                float fl[N1], sv[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    fl[j] = sm.tile[q + NQ * j][lane];
+                if (l2)
+                    line_sums<N1, true>(sv, fl, enz >= 0 ? trace_line<N1, true>(vz[ix], A.ops) : gz, A.ops);
+                else
+                    line_sums<N1, false>(sv, fl, enz >= 0 ? trace_line<N1, false>(vz[ix], A.ops) : gz, A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    sm.zc[q + NQ * j][lane] = sv[j];
+            }
+            __syncthreads();  // B2: z-sums complete
+            // BGK source towards the conservative Maxwellian, Shu-Osher combination, store
+            const float cg = bdt * A.inv_tau * __ldg(A.gmask + slot);
+            const float xs = x0 * x0 + x1 * x1 + x2 * x2;
+            float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                const int i = q + NQ * w;
+                const float4 pb = *reinterpret_cast<const float4 *>(&sm.par[i][0]);
+                const float b4 = sm.par[i][4];
+                const float ex = fmaf(b4, xs, fmaf(pb.w, x2, fmaf(pb.z, x1, fmaf(pb.y, x0, pb.x))));
+                const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
+                o[q] = fmaf(cg, exp2f(ex), a);
+                __stcs(dst + i * kWarp, o[q]);
+            }
+        } else {
+            __syncthreads();  // B1 (same barrier sequence in both modes)
+            if (w == 0) {
+#pragma unroll
+                for (int c = 0; c < 5; c++)
+                    sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+            }
+            __syncthreads();  // B2
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                o[q] = f[q];
+        }
+        // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values
+#pragma unroll
+        for (int q = 0; q < NQ; q++)
+            sm.wf[w][q][lane] = o[q];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k += 4) {
+            const int kk = 8 * kg + k;
+            unsigned long long wv[5][2];
+#pragma unroll
+            for (int c = 0; c < 5; c++) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(&sm.wpsi[c][kk]);
+                wv[c][0] = pack2(w4.x, w4.y);
+                wv[c][1] = pack2(w4.z, w4.w);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const float4 v = *reinterpret_cast<const float4 *>(&sm.wf[w][np + 8 * h][kk]);
+                const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
+#pragma unroll
+                for (int c = 0; c < 5; c++) {
+                    ms[h][c] = ffma2(wv[c][0], v01, ms[h][c]);
+                    ms[h][c] = ffma2(wv[c][1], v23, ms[h][c]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // partial moments of this task: combine the 4 velocity eighths of every node pair
+    const int grp = A.group0 + gl;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int q = np + 8 * h;
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+            float x = sum2(ms[h][c]);
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            if (kg == 0 && q < NQ)
+                A.partial[((int64_t)grp * 5 + c) * A.npts + (int64_t)e * NP + q + NQ * w] = x;
+        }
+    }
+}
+
+
+template <int N1, int MODE, int OCT>
+cudaError_t launch3(const StageArgs &A, cudaStream_t s)
+{
+    const int ngroups = (A.nvt + A.G - 1) / A.G;
+    k_stage3<N1, MODE, OCT><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3Smem<N1>), s>>>(A);
+    return cudaGetLastError();
+}
+
+template <int N1>
+cudaError_t prepare3()
+{
+    const int smem = (int)sizeof(Stage3Smem<N1>);
+    cudaError_t e = cudaFuncSetAttribute(k_stage3<N1, 1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+#define BGK_P3(O)                                                                                     \
+    if (e == cudaSuccess)                                                                             \
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    BGK_P3(0) BGK_P3(1) BGK_P3(2) BGK_P3(3) BGK_P3(4) BGK_P3(5) BGK_P3(6) BGK_P3(7) BGK_P3(8)
+#undef BGK_P3
+    return e;
+}
+
+// mode 0: stage of octant oct (8 = mixed octants); mode 1: moments only
+template <int N1>
+cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
+{
+    if (mode == 1)
+        return launch3<N1, 1, 8>(A, s);
+    switch (oct) {
+    case 0: return launch3<N1, 0, 0>(A, s);
+    case 1: return launch3<N1, 0, 1>(A, s);
+    case 2: return launch3<N1, 0, 2>(A, s);
+    case 3: return launch3<N1, 0, 3>(A, s);
+    case 4: return launch3<N1, 0, 4>(A, s);
+    case 5: return launch3<N1, 0, 5>(A, s);
+    case 6: return launch3<N1, 0, 6>(A, s);
+    case 7: return launch3<N1, 0, 7>(A, s);
+    default: return launch3<N1, 0, 8>(A, s);
+    }
+}
+
+}  // namespace bgk
