@@ -152,6 +152,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-baseline-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the plain all-FP64 form timed for the comparison (0: skip)")
     ap.add_argument("--elements", type=int, default=0,
                     help="elements per direction (default: the workload's 16); smaller cases for profiling")
     args = ap.parse_args()
@@ -258,6 +260,37 @@ def main():
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
+    # the plain all-FP64 form on the same workload: time, and the FP32-split moments' distance from it
+    fp64 = None
+    if args.fp64_steps > 0:
+        from paper_2308_06196_gb300.bgk import FP64
+
+        s64 = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"],
+                     precision=FP64)
+        s64.set_stream(stream.cuda_stream)
+        s64.set_state(prim_dev)
+        s64.step(dt, 1)  # warm-up (graph capture)
+        s64.set_state(prim_dev)
+        s.set_state(prim_dev)
+        barrier()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        s64.step(dt, args.fp64_steps)
+        h1.record(stream)
+        barrier()
+        ms64 = h0.elapsed_time(h1) / args.fp64_steps
+        s.step(dt, args.fp64_steps)
+        Q32, Q64 = s.moments(), s64.moments()
+        # component scales: rho for mass, rho sqrt(theta) for momentum (a component of the mean
+        # velocity can vanish identically), E for energy
+        rho = Q64[:, 0]
+        th = (2.0 / 3.0) * (Q64[:, 4] / rho - 0.5 * (Q64[:, 1:4] ** 2).sum(1) / rho**2)
+        scale = np.array([rho.max()] + [(rho * np.sqrt(th)).max()] * 3 + [np.abs(Q64[:, 4]).max()])
+        err = float((np.abs(Q32 - Q64).max(axis=0) / scale).max())
+        fp64 = {"value": dof * 3 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+                "moments_max_rel_diff_fp32_split": err}
+        s64.close()
+
     ms_t = torch.tensor([ms, graph_ms, e2e_ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -302,6 +335,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": s.npts * 5 * 8,
                 "d2h_bytes_per_step": s.npts * 5 * 8, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
+        "fp64_form": None if fp64 is None else dict(fp64, speedup_of_fp32_split=value / world / fp64["value"]),
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

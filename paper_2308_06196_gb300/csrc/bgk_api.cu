@@ -28,6 +28,12 @@ cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slot
                                    cudaStream_t s);
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
+cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s);
+cudaError_t launch_moments64(const Moments64Args &A, cudaStream_t s);
+cudaError_t launch_init64(double *f, const double *prim, const double *xi, const float *gmask, int nvt, int E, int NP,
+                          int nslots, int *err, cudaStream_t s);
+cudaError_t launch_convert64(bool to_device, double *f, double *st, const int *slotk, int nvt, int E, int NP,
+                             int64_t nvel, int p0, int npt, cudaStream_t s);
 }  // namespace bgk
 
 using namespace bgk;
@@ -78,7 +84,7 @@ double lag(int n, const double *x, const double *lam, int j, double y)
 // FR operators (Sec. 2.1, Eqs. 7-9) for the stage kernel, built in FP64 and rounded to FP32:
 // barycentric derivative matrix with the negative-sum diagonal, end interpolants, and the DG lift
 // (Radau correction) derivatives g_L'(x_i) = -l_i(-1) / W_i, g_R'(x_i) = l_i(1) / W_i.
-void build_ops(int p, Ops &op, double *xg_out)
+void build_ops(int p, Ops &op, Ops64 &o64, double *xg_out)
 {
     const int n = p + 1;
     double x[kMaxN1], W[kMaxN1], lam[kMaxN1], D[kMaxN1][kMaxN1], lm[kMaxN1], lp[kMaxN1], gl[kMaxN1], gr[kMaxN1];
@@ -108,6 +114,15 @@ void build_ops(int p, Ops &op, double *xg_out)
         gr[i] = lp[i] / W[i];
     }
     memset(&op, 0, sizeof(op));
+    memset(&o64, 0, sizeof(o64));
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++)
+            o64.D[i][j] = D[i][j];
+        o64.lm[i] = lm[i];
+        o64.lp[i] = lp[i];
+        o64.gl[i] = gl[i];
+        o64.gr[i] = gr[i];
+    }
     for (int i = 0; i < n; i++) {
         for (int j = 0; j < n; j++) {
             op.DL[i][j] = (float)(D[i][j] - gl[i] * lm[j]);
@@ -154,11 +169,16 @@ struct bgk_ctx {
     float *xi = nullptr, *wpsi = nullptr, *gmask = nullptr, *ghost = nullptr;
     int *slotk_d = nullptr;
     float *partial = nullptr, *param = nullptr;
+    // all-FP64 form
+    int prec = BGK_FP32_SPLIT;
+    double *fA64 = nullptr, *pool64 = nullptr, *xi64 = nullptr, *wpsi64 = nullptr, *ghost64 = nullptr, *par64 = nullptr;
+    Ops64 ops64{};
     double *Q = nullptr, *prim = nullptr, *prim_in = nullptr;
     int *err = nullptr;
     int64_t bytes = 0;
     Ops ops{};
     Mesh mesh{};
+    int64_t esize = 4;  // bytes per stored value of f
     // execution
     cudaStream_t stream = nullptr, own = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -242,6 +262,10 @@ NewtonArgs newton_args(bgk_ctx *c, int cold)
     N.cold = cold;
     N.it32 = c->opts.newton_max_it > 0 ? c->opts.newton_max_it : 2;
     N.it64 = 1;
+    if (c->prec == BGK_FP64) {  // FP64 moments from k64_moments; FP64 Maxwellian parameters out
+        N.Qin = c->Q;
+        N.param64 = c->par64;
+    }
     for (int d = 0; d < 3; d++) {
         N.v0[d] = c->vlo[d];
         N.dv[d] = c->dv[d];
@@ -274,15 +298,94 @@ void ev_end(bgk_ctx *c)
     c->nev++;
 }
 
+double *chunk_ptr64(bgk_ctx *c, double *base, int vt0) { return base + (int64_t)vt0 * c->E * c->NP * kWarp; }
+
+Moments64Args moments64_args(bgk_ctx *c)
+{
+    Moments64Args M{};
+    M.nchunks = (int)c->chunks.size();
+    M.wpsi = c->wpsi64;
+    M.E = c->E;
+    M.NP = c->NP;
+    M.npts = (int)c->npts;
+    M.Q = c->Q;
+    return M;
+}
+
 // Moments + conservative Maxwellian of the current f^n (after set_state / set_f).
 int prologue(bgk_ctx *c, cudaStream_t s)
 {
+    if (c->prec == BGK_FP64) {
+        Moments64Args M = moments64_args(c);
+        for (int q = 0; q < M.nchunks; q++) {
+            M.base[q] = chunk_ptr64(c, c->fA64, c->chunks[q].vt0);
+            M.vt0[q] = c->chunks[q].vt0;
+            M.nvt[q] = c->chunks[q].nvt;
+        }
+        CK(launch_moments64(M, s));
+        CK(launch_newton(newton_args(c, 1), s));
+        return BGK_OK;
+    }
     for (const Chunk &ch : c->chunks) {
         StageArgs A = stage_args(c, ch);
         A.src = chunk_ptr(c, c->fA, ch.vt0);
         CK(launch_stage(A, c->p, 1, ch.oct, s));
     }
     CK(launch_newton(newton_args(c, 1), s));
+    return BGK_OK;
+}
+
+// One SSP-RK3 step of the plain all-FP64 form: per stage, the unfused stage kernel over every chunk,
+// the FP64 moments of all chunk outputs, then the Newton solve.
+int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int> &slot1,
+                   const std::vector<int> &slot2)
+{
+    static const double an[3] = {0.0, 0.75, 1.0 / 3.0};
+    static const double bb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const int C = (int)c->chunks.size();
+    for (int st = 0; st < 3; st++) {
+        Moments64Args M = moments64_args(c);
+        for (int q = 0; q < C; q++) {
+            const Chunk &ch = c->chunks[q];
+            double *Aq = chunk_ptr64(c, c->fA64, ch.vt0);
+            double *s1 = c->pool64 + (int64_t)slot1[q] * c->chunk_floats;
+            double *s2 = c->pool64 + (int64_t)slot2[q] * c->chunk_floats;
+            Stage64Args A{};
+            A.src = st == 0 ? Aq : (st == 1 ? s1 : s2);
+            A.fn = st == 0 ? nullptr : Aq;
+            A.dst = st == 0 ? s1 : (st == 1 ? s2 : Aq);
+            A.xi = c->xi64;
+            A.ghost = c->ghost64;
+            A.par = c->par64;
+            A.gmask = c->gmask;
+            A.ops = c->ops64;
+            A.mesh = c->mesh;
+            for (int d = 0; d < 3; d++)
+                A.h[d] = c->h[d];
+            A.N1 = c->N1;
+            A.NP = c->NP;
+            A.vt0 = ch.vt0;
+            A.nvt = ch.nvt;
+            A.nslots = c->nslots;
+            A.an = an[st];
+            A.b = bb[st];
+            A.dt = dt;
+            A.inv_tau = 1.0 / c->tau;
+            int64_t real = 0;
+            for (int v = ch.vt0 * kWarp; v < (ch.vt0 + ch.nvt) * kWarp; v++)
+                real += c->slotk[v] >= 0;
+            ev_begin(c, 0, (double)real * c->npts * sizeof(double) * (st == 0 ? 2 : 3));
+            CK(launch_stage64(A, s));
+            ev_end(c);
+            M.base[q] = A.dst;
+            M.vt0[q] = ch.vt0;
+            M.nvt[q] = ch.nvt;
+        }
+        ev_begin(c, 1, 0.0);
+        CK(launch_moments64(M, s));
+        CK(launch_newton(newton_args(c, 0), s));
+        ev_end(c);
+    }
     return BGK_OK;
 }
 
@@ -297,6 +400,8 @@ int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
         slot1[q] = q;
         slot2[q] = q == 0 ? C : q - 1;
     }
+    if (c->prec == BGK_FP64)
+        return enqueue_step64(c, dt, s, slot1, slot2);
     for (int st = 0; st < 3; st++) {
         for (int q = 0; q < C; q++) {
             const Chunk &ch = c->chunks[q];
@@ -366,7 +471,8 @@ void bgk_destroy(bgk_ctx *c)
         cudaEventDestroy(ev.b);
     }
     void *bufs[] = {c->fA, c->pool, c->xi, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
-                    c->param, c->Q, c->prim, c->prim_in, c->err};
+                    c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
+                    c->wpsi64, c->ghost64, c->par64};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -391,8 +497,10 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     };
     if (opts)
         c->opts = *opts;
-    if (c->opts.precision != BGK_FP32_SPLIT)
-        return bail(BGK_EINVAL, "only the FP32-split precision form is built in this library version");
+    if (c->opts.precision != BGK_FP32_SPLIT && c->opts.precision != BGK_FP64)
+        return bail(BGK_EINVAL, "precision must be BGK_FP32_SPLIT or BGK_FP64");
+    c->prec = c->opts.precision;
+    c->esize = c->prec == BGK_FP64 ? 8 : 4;
     c->dim = mesh->dim;
     if (c->dim != 1 && c->dim != 3)
         return bail(BGK_EINVAL, "dim must be 1 or 3");
@@ -438,7 +546,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     }
     c->nvel = (int64_t)c->nv[0] * c->nv[1] * c->nv[2];
     c->tau = tau;
-    build_ops(p, c->ops, c->xg);
+    build_ops(p, c->ops, c->ops64, c->xg);
 
     // velocity plan: octants (sign of each component; xi = 0 goes with the positive side)
     std::vector<int> idx[3][2];
@@ -498,7 +606,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
 
     // memory check before any allocation
     const int64_t fA = (int64_t)c->nvt * E * c->NP * kWarp;
-    const int64_t need = (fA + (int64_t)(c->chunks.size() + 1) * c->chunk_floats) * 4 +
+    const int64_t need = (fA + (int64_t)(c->chunks.size() + 1) * c->chunk_floats) * c->esize +
                          (int64_t)c->ngroups * 5 * c->npts * 4 + c->npts * (5 * 8 * 3 + kParamStride * 4) +
                          (int64_t)c->nslots * 4 * 16;
     size_t free_b = 0, total_b = 0;
@@ -514,8 +622,17 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
 #define AL(ptr, n)                                                        \
     if (dalloc(c, &(ptr), (size_t)(n)) != cudaSuccess)                    \
         return bail(BGK_ENOMEM, std::string("cudaMalloc failed: ") + #ptr);
-    AL(c->fA, fA);
-    AL(c->pool, (c->chunks.size() + 1) * c->chunk_floats);
+    if (c->prec == BGK_FP64) {
+        AL(c->fA64, fA);
+        AL(c->pool64, (c->chunks.size() + 1) * c->chunk_floats);
+        AL(c->xi64, 3 * c->nslots);
+        AL(c->wpsi64, 5 * c->nslots);
+        AL(c->ghost64, 6 * c->nslots);
+        AL(c->par64, c->npts * 5);
+    } else {
+        AL(c->fA, fA);
+        AL(c->pool, (c->chunks.size() + 1) * c->chunk_floats);
+    }
     AL(c->xi, 3 * c->nslots);
     AL(c->wpsi, 5 * c->nslots);
     AL(c->gmask, c->nslots);
@@ -530,6 +647,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
 #undef AL
     // velocity tables
     std::vector<float> xi(3 * c->nslots), wpsi(5 * c->nslots), gm(c->nslots), gh(6 * c->nslots, 0.f);
+    std::vector<double> xi64(3 * c->nslots), wpsi64(5 * c->nslots), gh64(6 * c->nslots, 0.0);
     for (int s = 0; s < c->nslots; s++) {
         int k = c->slotk[s];
         const bool real = k >= 0;
@@ -542,18 +660,22 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
             v[d] = c->vlo[d] + kk[d] * c->dv[d];
             w *= (kk[d] == 0 || kk[d] == c->nv[d] - 1) ? 0.5 * c->dv[d] : c->dv[d];
             xi[d * c->nslots + s] = (float)v[d];
+            xi64[d * c->nslots + s] = v[d];
         }
         if (!real)
             w = 0.0;
         const int vt = s / kWarp, l = s % kWarp;
         const double ps[5] = {1.0, v[0], v[1], v[2], 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])};
-        for (int q = 0; q < 5; q++)
+        for (int q = 0; q < 5; q++) {
             wpsi[((int64_t)vt * 5 + q) * kWarp + l] = (float)(w * ps[q]);
+            wpsi64[(int64_t)s * 5 + q] = w * ps[q];
+        }
         gm[s] = real ? 1.f : 0.f;
         for (int q = 0; q < 6; q++)
             if (q / 2 < c->dim && c->bc[q] == BGK_BC_DIRICHLET && real) {
                 const double *st = c->bcs + 5 * q;
-                gh[q * c->nslots + s] = (float)maxwell(st[0], st + 1, st[4], v[0], v[1], v[2]);
+                gh64[q * c->nslots + s] = maxwell(st[0], st + 1, st[4], v[0], v[1], v[2]);
+                gh[q * c->nslots + s] = (float)gh64[q * c->nslots + s];
             }
     }
     cudaError_t rc;
@@ -562,7 +684,12 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         (rc = cudaMemcpy(c->gmask, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->ghost, gh.data(), gh.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->slotk_d, c->slotk.data(), c->slotk.size() * 4, cudaMemcpyHostToDevice)) ||
-        (rc = cudaMemset(c->fA, 0, fA * 4)) || (rc = cudaMemset(c->err, 0, 4)) ||
+        (c->prec == BGK_FP64 &&
+         ((rc = cudaMemcpy(c->xi64, xi64.data(), xi64.size() * 8, cudaMemcpyHostToDevice)) ||
+          (rc = cudaMemcpy(c->wpsi64, wpsi64.data(), wpsi64.size() * 8, cudaMemcpyHostToDevice)) ||
+          (rc = cudaMemcpy(c->ghost64, gh64.data(), gh64.size() * 8, cudaMemcpyHostToDevice)) ||
+          (rc = cudaMemset(c->fA64, 0, fA * 8)) || (rc = cudaMemset(c->par64, 0, c->npts * 5 * 8)))) ||
+        (c->prec != BGK_FP64 && (rc = cudaMemset(c->fA, 0, fA * 4))) || (rc = cudaMemset(c->err, 0, 4)) ||
         (rc = cudaMemset(c->prim, 0, c->npts * 5 * 8)) || (rc = cudaMemset(c->param, 0, c->npts * kParamStride * 4)))
         return bail(BGK_ECUDA, std::string("device set-up copy failed: ") + cudaGetErrorString(rc));
     if (prepare_stage(c->dim, p) != cudaSuccess)
@@ -614,8 +741,11 @@ int bgk_points(const bgk_ctx *c, double *x)
 static int set_state_impl(bgk_ctx *c, const double *prim, cudaMemcpyKind kind)
 {
     CK(cudaMemcpyAsync(c->prim_in, prim, c->npts * 5 * sizeof(double), kind, c->stream));
-    CK(launch_init_maxwellian(c->fA, c->prim_in, c->slotk_d, c->nvt, c->E, c->NP, c->nv, c->vlo, c->dv, c->err,
-                              c->stream));
+    if (c->prec == BGK_FP64)
+        CK(launch_init64(c->fA64, c->prim_in, c->xi64, c->gmask, c->nvt, c->E, c->NP, c->nslots, c->err, c->stream));
+    else
+        CK(launch_init_maxwellian(c->fA, c->prim_in, c->slotk_d, c->nvt, c->E, c->NP, c->nv, c->vlo, c->dv,
+                                  c->err, c->stream));
     return prologue(c, c->stream);
 }
 
@@ -649,11 +779,17 @@ static int convert_impl(bgk_ctx *c, double *f, bool in)
         if (in) {
             e = cudaMemcpyAsync(st, f + p0 * c->nvel, n * per_pt, cudaMemcpyHostToDevice, c->stream);
             if (e == cudaSuccess)
-                e = launch_convert_f(true, c->fA, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0, (int)n,
-                                     c->stream);
+                e = c->prec == BGK_FP64
+                        ? launch_convert64(true, c->fA64, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0,
+                                           (int)n, c->stream)
+                        : launch_convert_f(true, c->fA, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0,
+                                           (int)n, c->stream);
         } else {
-            e = launch_convert_f(false, c->fA, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0, (int)n,
-                                 c->stream);
+            e = c->prec == BGK_FP64
+                    ? launch_convert64(false, c->fA64, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0, (int)n,
+                                       c->stream)
+                    : launch_convert_f(false, c->fA, st, c->slotk_d, c->nvt, c->E, c->NP, c->nvel, (int)p0, (int)n,
+                                       c->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(f + p0 * c->nvel, st, n * per_pt, cudaMemcpyDeviceToHost, c->stream);
         }

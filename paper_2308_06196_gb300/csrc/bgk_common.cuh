@@ -66,6 +66,8 @@ struct StageArgs {
 
 struct NewtonArgs {
     const float *partial;  // [ngroups][5][n_x]
+    const double *Qin;     // [n_x][5] FP64 moments; when set, used instead of the partial sums
+    double *param64;       // [n_x][5] (C, U'x, U'y, U'z, 1/(2 theta')) of g in FP64, or null
     int ngroups;
     int npts;
     double *Q;             // [n_x][5] moments (out)
@@ -78,6 +80,39 @@ struct NewtonArgs {
     // 1-D velocity grids: xi_k = v0[d] + k dv[d], k < n[d]; trapezoid weights
     double v0[3], dv[3];
     int n[3];
+};
+
+// FR reference operators in FP64 for the plain all-FP64 form (Sec. 2.1, Eqs. 7-9).
+struct Ops64 {
+    double D[kMaxN1][kMaxN1];
+    double lm[kMaxN1], lp[kMaxN1];
+    double gl[kMaxN1], gr[kMaxN1];
+};
+
+// One launch of the plain FP64 stage kernel over one velocity chunk (thread per degree of freedom).
+struct Stage64Args {
+    const double *src, *fn;
+    double *dst;
+    const double *xi;      // [3][nslots]
+    const double *ghost;   // [6][nslots]
+    const double *par;     // [n_x][5] (C, U', 1/(2 theta')) of the conservative Maxwellian
+    const float *gmask;    // [nslots]
+    Ops64 ops;
+    Mesh mesh;
+    double h[3];
+    int N1, NP;
+    int vt0, nvt, nslots;
+    double an, b, dt, inv_tau;
+};
+
+// FP64 moments of the stage output over all chunks (warp per point).
+struct Moments64Args {
+    const double *base[9];  // chunk output bases
+    int vt0[9], nvt[9];
+    int nchunks;
+    const double *wpsi;     // [nslots][5] w psi in FP64
+    int E, NP, npts;
+    double *Q;              // [n_x][5]
 };
 
 __host__ __device__ inline int64_t fidx(int vt_local, int e, int i, int lane, int E, int NP)

@@ -184,10 +184,14 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
     if (pt >= A.npts)
         return;
 
-    // 1. moments: exact sum of the FP32 partials
+    // 1. moments: exact sum of the FP32 partials (or the FP64 moments of the all-FP64 form)
     double Q[5];
 #pragma unroll
     for (int c = 0; c < 5; c++) {
+        if (A.Qin) {
+            Q[c] = A.Qin[(int64_t)pt * 5 + c];
+            continue;
+        }
         float hi = 0.f, lo = 0.f;
         const float *p = A.partial + (int64_t)c * A.npts + pt;
         for (int g = 0; g < A.ngroups; g++) {
@@ -210,6 +214,9 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
         atomicOr(A.err, kErrDomain);
         par[0] = -1e30f;  // g = 0 at this point
         par[1] = par[2] = par[3] = par[4] = 0.f;
+        if (A.param64)
+            for (int c = 0; c < 5; c++)
+                A.param64[(int64_t)pt * 5 + c] = 0.0;
         return;
     }
 
@@ -354,6 +361,14 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
     par[2] = (float)(L2E * Up[1] * it2);
     par[3] = (float)(L2E * Up[2] * it2);
     par[4] = (float)(-0.5 * L2E * it2);
+    if (A.param64) {
+        double *p64 = A.param64 + (int64_t)pt * 5;
+        p64[0] = exp(lnC);
+        p64[1] = Up[0];
+        p64[2] = Up[1];
+        p64[3] = Up[2];
+        p64[4] = 0.5 * it2;
+    }
 }
 
 cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s)

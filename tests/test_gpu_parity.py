@@ -263,3 +263,60 @@ def test_taylor_green_full_size_properties():
     s.set_state(prim)
     s.step(dt, 2)
     assert np.array_equal(s.moments(), Q1)
+
+
+# ---------------------------------------------------------------------------------------------
+# the plain all-FP64 form (precision = BGK_FP64): the same method in FP64, unfused
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_fp64_one_step_3d(p):
+    from paper_2308_06196_gb300.bgk import FP64
+
+    c = small(3, [3, 2, 3], p, 6, L=4.0, tau=0.05)
+    pr = oracle_problem(c)
+    f = random_f(pr, seed=40 + p)
+    s = solver(c, precision=FP64)
+    s.set_f(f)
+    pr.set_f(f)
+    dt = pr.dt(0.1)
+    s.step(dt, 2)
+    pr.step(dt, 2)
+    # FP64 on both sides: differences come from summation order and the two Newton solvers
+    # (each converged to ~1e-13 of the moments)
+    assert rel(s.get_f(), pr.get_f()) < 1e-10
+    assert rel(s.moments(), pr.moments()) < 1e-10
+
+
+def test_fp64_periodic1d_100_steps_and_conservation():
+    from paper_2308_06196_gb300.bgk import FP64
+
+    c = W.config("periodic1d")
+    pr = oracle_problem(c)
+    s = solver(c, precision=FP64)
+    prim = W.prim_field("periodic1d", pr.points())
+    pr.set_state(prim)
+    s.set_state(prim)
+    Q0 = s.moments()
+    dt = pr.dt(c["cfl"])
+    s.step(dt, c["steps"])
+    pr.step(dt, c["steps"])
+    Qg, Qo = s.moments(), pr.moments()
+    assert np.abs(Qg - Qo).max() <= 1e-10 * np.abs(Qo).max()
+    _, Wg = orc.gauss_legendre(4)
+    G0 = (Q0.reshape(-1, 4, 5) * Wg[None, :, None]).sum((0, 1))
+    G1 = (Qg.reshape(-1, 4, 5) * Wg[None, :, None]).sum((0, 1))
+    assert np.abs(G1 - G0).max() <= 1e-12 * max(abs(G0[0]), abs(G0[4]))
+
+
+def test_fp64_free_stream():
+    from paper_2308_06196_gb300.bgk import FP64
+
+    c = small(3, [2, 3, 2], 3, 6, tau=1e30)
+    s = solver(c, precision=FP64)
+    pr = oracle_problem(c)
+    rng = np.random.default_rng(4)
+    f = np.tile(pr.sample_maxwellian([1.0, 0.2, -0.1, 0.3, 1.1]) * rng.uniform(0.9, 1.1, 216), (s.npts, 1))
+    s.set_f(f)
+    s.step(0.001, 10)
+    assert rel(s.get_f(), f) < 1e-13
