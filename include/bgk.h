@@ -47,7 +47,8 @@ extern "C" {
 
 #define BGK_BC_PERIODIC 0
 #define BGK_BC_DIRICHLET 1     /* ghost = sampled continuous Maxwellian of bc_state (rho,u,v,w,T) */
-#define BGK_BC_DIFFUSE_WALL 2  /* ghost = rho_w * M(T_w, U_w), rho_w for zero net discrete mass flux */
+#define BGK_BC_DIFFUSE_WALL 2  /* ghost = rho_w * M(T_w, U_w), rho_w per face point for zero net discrete
+                                  mass flux, recomputed every stage (hexahedral meshes, dim = 3) */
 
 #define BGK_FP32_SPLIT 0
 #define BGK_FP64 1
@@ -73,7 +74,9 @@ typedef struct {
 
 typedef struct {
     int precision;           /* BGK_FP32_SPLIT (default) or BGK_FP64 */
-    double body_force[3];    /* constant force per unit mass (0 = none) */
+    double body_force[3];    /* constant force per unit mass (0 = none; dim = 3). Source g (beta . psi) with
+                                (sum_k w g psi psi^T) beta = (0, rho F, rho U . F): its discrete moments are
+                                exactly those of -F . grad_xi f */
     int newton_max_it;       /* FP32 Newton iterations per solve, <= 0: default (2 warm, 12 cold) */
     double newton_tol;       /* reserved (the FP64 refinement fixes the final accuracy) */
     int limiter;             /* reserved: positivity limiter (Eqs. 10-11) is not on this path */
@@ -82,8 +85,8 @@ typedef struct {
 } bgk_opts;
 
 /* Create a problem on the current CUDA device: plans the velocity tiles, builds the FR operators
- * (Eqs. 7-8) in FP64 on the host and allocates every device buffer. p in [1, 4] for dim = 3 and
- * [1, 7] for dim = 1; opts may be NULL. tau > 0 is the constant relaxation time (Eq. 3 with a fixed
+ * (Eqs. 7-8) in FP64 on the host and allocates every device buffer. p in [1, 3] for dim = 3 and
+ * [1, 5] for dim = 1; opts may be NULL. tau > 0 is the constant relaxation time (Eq. 3 with a fixed
  * tau). The state is zero until bgk_set_state/bgk_set_f. Returns BGK_ENOMEM, without allocating,
  * when the buffers would not fit in free device memory. */
 int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vgrid, double tau,

@@ -29,6 +29,7 @@ cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slot
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
 cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s);
+cudaError_t launch_wall(const WallArgs &A, bool fp64, const void *w, const void *xi, cudaStream_t s);
 cudaError_t launch_moments64(const Moments64Args &A, cudaStream_t s);
 cudaError_t launch_init64(double *f, const double *prim, const double *xi, const float *gmask, int nvt, int E, int NP,
                           int nslots, int *err, cudaStream_t s);
@@ -172,6 +173,13 @@ struct bgk_ctx {
     // all-FP64 form
     int prec = BGK_FP32_SPLIT;
     double *fA64 = nullptr, *pool64 = nullptr, *xi64 = nullptr, *wpsi64 = nullptr, *ghost64 = nullptr, *par64 = nullptr;
+    // diffuse walls and body force
+    bool has_wall = false, has_force = false;
+    double force[3] = {0, 0, 0};
+    double inv_in[6] = {0, 0, 0, 0, 0, 0};
+    int nfmax = 0;
+    float *rhow32 = nullptr, *fpar32 = nullptr, *w32 = nullptr;
+    double *rhow64 = nullptr, *fpar64 = nullptr, *w64 = nullptr;
     Ops64 ops64{};
     double *Q = nullptr, *prim = nullptr, *prim_in = nullptr;
     int *err = nullptr;
@@ -234,6 +242,9 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.gmask = c->gmask;
     A.ghost = c->ghost;
     A.param = c->param;
+    A.rhow = c->rhow32;
+    A.fpar = c->fpar32;
+    A.nfmax = c->nfmax;
     A.partial = c->partial;
     A.ops = c->ops;
     A.mesh = c->mesh;
@@ -266,6 +277,10 @@ NewtonArgs newton_args(bgk_ctx *c, int cold)
         N.Qin = c->Q;
         N.param64 = c->par64;
     }
+    for (int d = 0; d < 3; d++)
+        N.force[d] = c->force[d];
+    N.fpar = c->fpar32;
+    N.fpar64 = c->fpar64;
     for (int d = 0; d < 3; d++) {
         N.v0[d] = c->vlo[d];
         N.dv[d] = c->dv[d];
@@ -335,6 +350,37 @@ int prologue(bgk_ctx *c, cudaStream_t s)
     return BGK_OK;
 }
 
+// Diffuse-wall densities of the stage whose chunk sources are src[q].
+int enqueue_wall(bgk_ctx *c, const std::vector<const void *> &src, cudaStream_t s)
+{
+    if (!c->has_wall)
+        return BGK_OK;
+    WallArgs W{};
+    W.nchunks = (int)c->chunks.size();
+    for (int q = 0; q < W.nchunks; q++) {
+        W.src[q] = src[q];
+        W.vt0[q] = c->chunks[q].vt0;
+        W.nvt[q] = c->chunks[q].nvt;
+        W.oct[q] = c->chunks[q].oct;
+    }
+    W.nslots = c->nslots;
+    for (int q = 0; q < 6; q++)
+        W.inv_in[q] = c->inv_in[q];
+    W.mesh = c->mesh;
+    W.N1 = c->N1;
+    W.NP = c->NP;
+    W.nfmax = c->nfmax;
+    for (int j = 0; j < c->N1; j++) {
+        W.lm[j] = c->ops64.lm[j];
+        W.lp[j] = c->ops64.lp[j];
+    }
+    const bool f64 = c->prec == BGK_FP64;
+    W.rhow = f64 ? (void *)c->rhow64 : (void *)c->rhow32;
+    CK(launch_wall(W, f64, f64 ? (const void *)c->w64 : (const void *)c->w32,
+                   f64 ? (const void *)c->xi64 : (const void *)c->xi, s));
+    return BGK_OK;
+}
+
 // One SSP-RK3 step of the plain all-FP64 form: per stage, the unfused stage kernel over every chunk,
 // the FP64 moments of all chunk outputs, then the Newton solve.
 int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int> &slot1,
@@ -345,6 +391,17 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
     const int C = (int)c->chunks.size();
     for (int st = 0; st < 3; st++) {
         Moments64Args M = moments64_args(c);
+        if (c->has_wall) {
+            std::vector<const void *> srcs(C);
+            for (int q = 0; q < C; q++) {
+                double *Aq = chunk_ptr64(c, c->fA64, c->chunks[q].vt0);
+                srcs[q] = st == 0 ? (const void *)Aq
+                                  : (const void *)(c->pool64 + (int64_t)(st == 1 ? slot1[q] : slot2[q]) * c->chunk_floats);
+            }
+            int rc = enqueue_wall(c, srcs, s);
+            if (rc)
+                return rc;
+        }
         for (int q = 0; q < C; q++) {
             const Chunk &ch = c->chunks[q];
             double *Aq = chunk_ptr64(c, c->fA64, ch.vt0);
@@ -357,6 +414,9 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
             A.xi = c->xi64;
             A.ghost = c->ghost64;
             A.par = c->par64;
+            A.rhow = c->rhow64;
+            A.fpar = c->fpar64;
+            A.nfmax = c->nfmax;
             A.gmask = c->gmask;
             A.ops = c->ops64;
             A.mesh = c->mesh;
@@ -403,6 +463,17 @@ int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
     if (c->prec == BGK_FP64)
         return enqueue_step64(c, dt, s, slot1, slot2);
     for (int st = 0; st < 3; st++) {
+        if (c->has_wall) {
+            std::vector<const void *> srcs(C);
+            for (int q = 0; q < C; q++) {
+                float *Aq = chunk_ptr(c, c->fA, c->chunks[q].vt0);
+                srcs[q] = st == 0 ? (const void *)Aq
+                                  : (const void *)(c->pool + (int64_t)(st == 1 ? slot1[q] : slot2[q]) * c->chunk_floats);
+            }
+            int rc = enqueue_wall(c, srcs, s);
+            if (rc)
+                return rc;
+        }
         for (int q = 0; q < C; q++) {
             const Chunk &ch = c->chunks[q];
             StageArgs A = stage_args(c, ch);
@@ -472,7 +543,8 @@ void bgk_destroy(bgk_ctx *c)
     }
     void *bufs[] = {c->fA, c->pool, c->xi, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
-                    c->wpsi64, c->ghost64, c->par64};
+                    c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
+                    c->fpar64, c->w64};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -508,6 +580,14 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         return bail(BGK_EINVAL, "p must be in [1, 3] (dim 3) or [1, 5] (dim 1)");
     if (!(tau > 0.0) || !std::isfinite(tau))
         return bail(BGK_EINVAL, "tau must be positive and finite");
+    for (int d = 0; d < 3; d++) {
+        c->force[d] = c->opts.body_force[d];
+        if (!std::isfinite(c->force[d]))
+            return bail(BGK_EINVAL, "body force must be finite");
+        c->has_force = c->has_force || c->force[d] != 0.0;
+    }
+    if (c->has_force && c->dim != 3)
+        return bail(BGK_EINVAL, "the body-force source is built for hexahedral meshes (dim = 3)");
     c->p = p;
     c->N1 = p + 1;
     c->NP = c->dim == 1 ? c->N1 : c->N1 * c->N1 * c->N1;
@@ -521,8 +601,12 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
                 return bail(BGK_EINVAL, "bad mesh extent");
             for (int s = 0; s < 2; s++) {
                 const int b = mesh->bc[d][s];
-                if (b != BGK_BC_PERIODIC && b != BGK_BC_DIRICHLET)
-                    return bail(BGK_EINVAL, "boundary kind not supported by this library version");
+                if (b != BGK_BC_PERIODIC && b != BGK_BC_DIRICHLET && b != BGK_BC_DIFFUSE_WALL)
+                    return bail(BGK_EINVAL, "unknown boundary kind");
+                if (b == BGK_BC_DIFFUSE_WALL && c->dim != 3)
+                    return bail(BGK_EINVAL, "diffuse walls are built for hexahedral meshes (dim = 3)");
+                if (b == BGK_BC_DIFFUSE_WALL)
+                    c->has_wall = true;
                 c->bc[2 * d + s] = b;
                 for (int q = 0; q < 5; q++)
                     c->bcs[(2 * d + s) * 5 + q] = mesh->bc_state[d][s][q];
@@ -638,6 +722,21 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     AL(c->gmask, c->nslots);
     AL(c->ghost, 6 * c->nslots);
     AL(c->slotk_d, c->nslots);
+    c->nfmax = std::max(c->ne[1] * c->ne[2], std::max(c->ne[0] * c->ne[2], c->ne[0] * c->ne[1]));
+    if (c->has_wall) {
+        if (c->prec == BGK_FP64) {
+            AL(c->rhow64, 6ll * c->nfmax * c->N1 * c->N1);
+            AL(c->w64, c->nslots);
+        } else {
+            AL(c->rhow32, 6ll * c->nfmax * c->N1 * c->N1);
+            AL(c->w32, c->nslots);
+        }
+    }
+    if (c->has_force) {
+        AL(c->fpar32, c->npts * kParamStride);
+        if (c->prec == BGK_FP64)
+            AL(c->fpar64, c->npts * 5);
+    }
     AL(c->partial, (int64_t)c->ngroups * 5 * c->npts);
     AL(c->param, c->npts * kParamStride);
     AL(c->Q, c->npts * 5);
@@ -647,7 +746,9 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
 #undef AL
     // velocity tables
     std::vector<float> xi(3 * c->nslots), wpsi(5 * c->nslots), gm(c->nslots), gh(6 * c->nslots, 0.f);
-    std::vector<double> xi64(3 * c->nslots), wpsi64(5 * c->nslots), gh64(6 * c->nslots, 0.0);
+    std::vector<double> xi64(3 * c->nslots), wpsi64(5 * c->nslots), gh64(6 * c->nslots, 0.0), w64h(c->nslots);
+    std::vector<float> w32h(c->nslots);
+    double win[6] = {0, 0, 0, 0, 0, 0};
     for (int s = 0; s < c->nslots; s++) {
         int k = c->slotk[s];
         const bool real = k >= 0;
@@ -671,15 +772,28 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
             wpsi64[(int64_t)s * 5 + q] = w * ps[q];
         }
         gm[s] = real ? 1.f : 0.f;
+        w32h[s] = (float)w;
+        w64h[s] = w;
         for (int q = 0; q < 6; q++)
-            if (q / 2 < c->dim && c->bc[q] == BGK_BC_DIRICHLET && real) {
+            if (q / 2 < c->dim && c->bc[q] != BGK_BC_PERIODIC && real) {
+                // Dirichlet: the prescribed Maxwellian; diffuse wall: the unit-density wall Maxwellian
                 const double *st = c->bcs + 5 * q;
-                gh64[q * c->nslots + s] = maxwell(st[0], st + 1, st[4], v[0], v[1], v[2]);
+                const double rho = c->bc[q] == BGK_BC_DIRICHLET ? st[0] : 1.0;
+                gh64[q * c->nslots + s] = maxwell(rho, st + 1, st[4], v[0], v[1], v[2]);
                 gh[q * c->nslots + s] = (float)gh64[q * c->nslots + s];
+                if (c->bc[q] == BGK_BC_DIFFUSE_WALL) {
+                    const double un = (q & 1) ? v[q / 2] : -v[q / 2];  // xi . n_out
+                    if (un < 0.0)
+                        win[q] += w * (-un) * gh64[q * c->nslots + s];
+                }
             }
     }
+    for (int q = 0; q < 6; q++)
+        c->inv_in[q] = (c->bc[q] == BGK_BC_DIFFUSE_WALL && win[q] > 0.0) ? 1.0 / win[q] : 0.0;
     cudaError_t rc;
-    if ((rc = cudaMemcpy(c->xi, xi.data(), xi.size() * 4, cudaMemcpyHostToDevice)) ||
+    if ((c->w32 && (rc = cudaMemcpy(c->w32, w32h.data(), w32h.size() * 4, cudaMemcpyHostToDevice))) ||
+        (c->w64 && (rc = cudaMemcpy(c->w64, w64h.data(), w64h.size() * 8, cudaMemcpyHostToDevice))) ||
+        (rc = cudaMemcpy(c->xi, xi.data(), xi.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->wpsi, wpsi.data(), wpsi.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->gmask, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->ghost, gh.data(), gh.size() * 4, cudaMemcpyHostToDevice)) ||

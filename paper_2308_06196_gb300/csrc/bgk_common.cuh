@@ -51,6 +51,9 @@ struct StageArgs {
     const float *gmask;  // [nslots] 1 for real velocities, 0 for padding
     const float *ghost;  // [6][nslots] Dirichlet ghost values (sampled Maxwellian), or null
     const float *param;  // [n_x][8] BGK exponent b0..b4 of every point: g = exp2(b0 + b.xi + b4|xi|^2)
+    const float *rhow;   // [6][nfmax][N1^2] diffuse-wall density per wall face point, or null
+    const float *fpar;   // [n_x][8] body-force source polynomial q0..q4: S = g (q0 + q.xi + q4|xi|^2), or null
+    int nfmax;           // face elements per face slot of rhow
     float *partial;      // [ngroups_total][5][n_x] moment partial sums of the stage output
     Ops ops;
     Mesh mesh;
@@ -66,6 +69,9 @@ struct StageArgs {
 
 struct NewtonArgs {
     const float *partial;  // [ngroups][5][n_x]
+    double force[3];       // body force per unit mass (zero: no force source)
+    float *fpar;           // [n_x][8] force polynomial of the stage kernel (out, when force != 0)
+    double *fpar64;        // [n_x][5] force polynomial in FP64 (out, all-FP64 form), or null
     const double *Qin;     // [n_x][5] FP64 moments; when set, used instead of the partial sums
     double *param64;       // [n_x][5] (C, U'x, U'y, U'z, 1/(2 theta')) of g in FP64, or null
     int ngroups;
@@ -96,6 +102,9 @@ struct Stage64Args {
     const double *xi;      // [3][nslots]
     const double *ghost;   // [6][nslots]
     const double *par;     // [n_x][5] (C, U', 1/(2 theta')) of the conservative Maxwellian
+    const double *rhow;    // [6][nfmax][N1^2] diffuse-wall densities, or null
+    const double *fpar;    // [n_x][5] body-force polynomial, or null
+    int nfmax;
     const float *gmask;    // [nslots]
     Ops64 ops;
     Mesh mesh;
@@ -114,6 +123,26 @@ struct Moments64Args {
     int E, NP, npts;
     double *Q;              // [n_x][5]
 };
+
+// Diffuse-wall densities of one stage (Sec. 2.1 boundary reading: zero net discrete mass flux through
+// every wall face point): rho_w = sum_{out} w |xi_n| f_trace / sum_{in} w |xi_n| M_w.
+struct WallArgs {
+    const void *src[9];    // stage source of every chunk (float or double)
+    int vt0[9], nvt[9], oct[9];
+    int nchunks;
+    int nslots;
+    double inv_in[6];      // 1 / sum_{in} w |xi_n| M_w per face (0: not a wall)
+    Mesh mesh;
+    int N1, NP, nfmax;
+    double lm[kMaxN1], lp[kMaxN1];
+    void *rhow;            // out: float or double [6][nfmax][N1^2]
+};
+
+// Index of the face element of element (ec) on face direction d: the two other coordinates.
+__host__ __device__ inline int face_elem(const Mesh &m, const int ec[3], int d)
+{
+    return d == 0 ? ec[1] + m.ne[1] * ec[2] : (d == 1 ? ec[0] + m.ne[0] * ec[2] : ec[0] + m.ne[0] * ec[1]);
+}
 
 __host__ __device__ inline int64_t fidx(int vt_local, int e, int i, int lane, int E, int NP)
 {

@@ -133,7 +133,8 @@ __device__ __forceinline__ void sums32(float ad, float beta, float c0, float h, 
 // q(k) = ad c_k - beta/2 c_k^2 is quadratic in k, so A(k+1)/A(k) = exp(q1 + q2 (2k+1)) and the ratio
 // itself changes by the constant factor exp(2 q2). Values decay away from the peak, so the products
 // underflow gracefully instead of overflowing.
-__device__ __forceinline__ void sums64(double ad, double beta, double c0, double h, int n, double dv, double (&S)[3])
+template <int M>
+__device__ __forceinline__ void sums64(double ad, double beta, double c0, double h, int n, double dv, double (&S)[M])
 {
     const double q1 = (ad - beta * c0) * h, q2 = -0.5 * beta * h * h;
     int kp = (int)rintf((float)(-q1) / (float)(2.0 * q2));
@@ -142,13 +143,17 @@ __device__ __forceinline__ void sums64(double ad, double beta, double c0, double
     const double Ap = exp(cp * fma(-0.5 * beta, cp, ad));
     const double E2 = exp(2.0 * q2);
     const double rp = exp(q1 + q2 * (2.0 * kp + 1.0));
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
     // upward from the peak (inclusive); unit weights, the trapezoid ends are corrected below
     double A = Ap, r = rp, c = cp, Aend = Ap, cend = cp;
     for (int k = kp; k < n; k++) {
         s0 += A;
         s1 = fma(c, A, s1);
         s2 = fma(c * c, A, s2);
+        if (M > 3) {
+            s3 = fma(c * c * c, A, s3);
+            s4 = fma(c * c * c * c, A, s4);
+        }
         Aend = A;
         cend = c;
         A *= r;
@@ -166,6 +171,10 @@ __device__ __forceinline__ void sums64(double ad, double beta, double c0, double
         s0 += A;
         s1 = fma(c, A, s1);
         s2 = fma(c * c, A, s2);
+        if (M > 3) {
+            s3 = fma(c * c * c, A, s3);
+            s4 = fma(c * c * c * c, A, s4);
+        }
         A0 = A;
         c0e = c;
     }
@@ -176,6 +185,12 @@ __device__ __forceinline__ void sums64(double ad, double beta, double c0, double
     S[0] = s0 * dv;
     S[1] = s1 * dv;
     S[2] = s2 * dv;
+    if constexpr (M > 3) {
+        s3 -= 0.5 * (c0e * c0e * c0e * A0 + cend * cend * cend * Aend);
+        s4 -= 0.5 * (c0e * c0e * c0e * c0e * A0 + cend * cend * cend * cend * Aend);
+        S[3] = s3 * dv;
+        S[4] = s4 * dv;
+    }
 }
 
 __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             double s3[3];
-            sums64(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], s3);
+            sums64<3>(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], s3);
             S[d][0] = s3[0];
             S[d][1] = s3[1];
             S[d][2] = s3[2];
@@ -361,6 +376,40 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
     par[2] = (float)(L2E * Up[1] * it2);
     par[3] = (float)(L2E * Up[2] * it2);
     par[4] = (float)(-0.5 * L2E * it2);
+    // body force: source S = g (beta . psi~) with M[g psi~ psi~^T] beta = M[S psi~] =
+    // (0, rho F / s, rho (U - V) . F / s^2), whose raw moments are (0, rho F, rho U . F); written as
+    // the polynomial q0 + q . xi + q4 |xi|^2 in the raw velocity
+    if (A.force[0] != 0.0 || A.force[1] != 0.0 || A.force[2] != 0.0) {
+        double S[3][5];
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            sums64<5>(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], S[d]);
+        double M[5], J[5][5], r[5], b[5];
+        assemble<double>(S, exp(al[0]), M, J);
+        r[0] = 0.0;
+        double uf = 0.0;
+        for (int d = 0; d < 3; d++) {
+            r[1 + d] = rho * A.force[d] * is;
+            uf += (u[d] - V[d]) * A.force[d];
+        }
+        r[4] = rho * uf * is * is;
+        float *fp = A.fpar + (int64_t)pt * kParamStride;
+        if (!solve5<double>(J, r, b)) {
+            atomicOr(A.err, kErrNewton);
+            return;
+        }
+        double q[5];
+        q[0] = b[0] - (b[1] * V[0] + b[2] * V[1] + b[3] * V[2]) * is +
+               0.5 * b[4] * (V[0] * V[0] + V[1] * V[1] + V[2] * V[2]) * is * is;
+        for (int d = 0; d < 3; d++)
+            q[1 + d] = b[1 + d] * is - b[4] * V[d] * is * is;
+        q[4] = 0.5 * b[4] * is * is;
+        for (int m = 0; m < 5; m++)
+            fp[m] = (float)q[m];
+        if (A.fpar64)
+            for (int m = 0; m < 5; m++)
+                A.fpar64[(int64_t)pt * 5 + m] = q[m];
+    }
     if (A.param64) {
         double *p64 = A.param64 + (int64_t)pt * 5;
         p64[0] = exp(lnC);

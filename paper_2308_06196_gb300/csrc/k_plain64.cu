@@ -47,8 +47,14 @@ __global__ void __launch_bounds__(256) k64_stage(const Stage64Args A)
             nc[d] += left ? -1 : 1;
             double up;
             if (nc[d] < 0 || nc[d] >= A.mesh.ne[d]) {
-                if (A.mesh.bc[2 * d + (left ? 0 : 1)] != 0) {
-                    up = A.ghost[(2 * d + (left ? 0 : 1)) * A.nslots + slot];
+                const int fc = 2 * d + (left ? 0 : 1);
+                if (A.mesh.bc[fc] != 0) {
+                    up = A.ghost[fc * A.nslots + slot];
+                    if (A.mesh.bc[fc] == 2) {  // diffuse wall: density of this face point
+                        const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
+                        const int fnode = ic[o1] + N1 * ic[o2];
+                        up *= A.rhow[((int64_t)fc * A.nfmax + face_elem(A.mesh, ec, d)) * N1 * N1 + fnode];
+                    }
                     goto have_up;
                 }
                 nc[d] = (nc[d] + A.mesh.ne[d]) % A.mesh.ne[d];
@@ -67,7 +73,12 @@ __global__ void __launch_bounds__(256) k64_stage(const Stage64Args A)
         const double *p = A.par + ((int64_t)e * NP + i) * 5;
         const double r2 = (xi[0] - p[1]) * (xi[0] - p[1]) + (xi[1] - p[2]) * (xi[1] - p[2]) + (xi[2] - p[3]) * (xi[2] - p[3]);
         const double g = A.gmask[slot] * p[0] * exp(-r2 * p[4]);
-        double out = A.b * (fs + A.dt * (R + (g - fs) * A.inv_tau));
+        double src = (g - fs) * A.inv_tau;
+        if (A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
+            const double *q = A.fpar + ((int64_t)e * NP + i) * 5;
+            src += g * (q[0] + q[1] * xi[0] + q[2] * xi[1] + q[3] * xi[2] + q[4] * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]));
+        }
+        double out = A.b * (fs + A.dt * (R + src));
         if (A.fn)
             out += A.an * A.fn[q];
         A.dst[q] = out;

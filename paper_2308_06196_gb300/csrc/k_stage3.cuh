@@ -27,12 +27,15 @@ struct Stage3Smem {
     float zc[NP][kWarp];          // z-derivative sums, [node][lane]
     float wf[N1][16][36];         // per warp: its layer's stage output, [node][velocity] (16 rows)
     float par[NP][kParamStride];  // BGK exponents of the element's points
+    float fpar[NP][kParamStride]; // body-force polynomials of the element's points (when a force acts)
     float wpsi[5][kWarp];         // w psi of the tile's velocities
 };
 
 // OCT in 0..7: every tile of the launch lies in that sign octant (bit d set: xi_d >= 0, the upwind
 // neighbour in direction d is on the low side); OCT = 8: the octant is read per tile.
-template <int N1, int MODE, int OCT>
+// GEN = 0: every face periodic and no body force (the lean form); GEN = 1: Dirichlet and diffuse-wall
+// faces and the body-force source.
+template <int N1, int MODE, int OCT, int GEN>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
 {
     constexpr int NQ = N1 * N1;      // nodes per layer
@@ -58,6 +61,12 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
         float4 *dst4 = reinterpret_cast<float4 *>(&sm.par[0][0]);
         for (int q = tid; q < NP * kParamStride / 4; q += NT)
             dst4[q] = __ldg(src4 + q);
+        if (GEN && A.fpar) {
+            const float4 *f4 = reinterpret_cast<const float4 *>(A.fpar + (int64_t)e * NP * kParamStride);
+            float4 *d4 = reinterpret_cast<float4 *>(&sm.fpar[0][0]);
+            for (int q = tid; q < NP * kParamStride / 4; q += NT)
+                d4[q] = __ldg(f4 + q);
+        }
     }
     // moment sums: lane = (node pair np = lane / 4: layer nodes np and np + 8) x (velocity eighth
     // kg = lane % 4: velocities 8 kg .. 8 kg + 7 of every tile); FP32 pairs over even/odd velocities,
@@ -135,19 +144,34 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                 acc[q] = fmaf(A.an, acc[q], kb * f[q]);
             const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt,
                         cz = -A.mesh.inv_h2[2] * x2 * bdt;
-            const float gx = enx >= 0 ? 0.f : __ldg(A.ghost + (l0 ? 0 : 1) * A.nslots + slot);
-            const float gy = eny >= 0 ? 0.f : __ldg(A.ghost + (2 + (l1 ? 0 : 1)) * A.nslots + slot);
-            const float gz = enz >= 0 ? 0.f : __ldg(A.ghost + (4 + (l2 ? 0 : 1)) * A.nslots + slot);
+            // upwind value on a non-periodic face: the Dirichlet ghost Maxwellian, or the diffuse-wall
+            // Maxwellian scaled by the wall density of the face point (face point of every line of
+            // this warp: its index + N1 * w)
+            const int fx = 0 + (l0 ? 0 : 1), fy = 2 + (l1 ? 0 : 1), fz = 4 + (l2 ? 0 : 1);
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+            const float *rwx = nullptr, *rwy = nullptr, *rwz = nullptr;
+            if (GEN) {
+                gx = enx >= 0 ? 0.f : __ldg(A.ghost + fx * A.nslots + slot);
+                gy = eny >= 0 ? 0.f : __ldg(A.ghost + fy * A.nslots + slot);
+                gz = enz >= 0 ? 0.f : __ldg(A.ghost + fz * A.nslots + slot);
+                if (enx < 0 && A.mesh.bc[fx] == 2)
+                    rwx = A.rhow + ((int64_t)fx * A.nfmax + face_elem(A.mesh, ec, 0)) * NQ + N1 * w;
+                if (eny < 0 && A.mesh.bc[fy] == 2)
+                    rwy = A.rhow + ((int64_t)fy * A.nfmax + face_elem(A.mesh, ec, 1)) * NQ + N1 * w;
+                if (enz < 0 && A.mesh.bc[fz] == 2)
+                    rwz = A.rhow + ((int64_t)fz * A.nfmax + face_elem(A.mesh, ec, 2)) * NQ + N1 * w;
+            }
 #pragma unroll
             for (int iy = 0; iy < N1; iy++) {
                 float fl[N1], sv[N1];
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     fl[j] = f[j + N1 * iy];
+                const float bx = rwx ? gx * __ldg(rwx + iy) : gx;
                 if (l0)
-                    line_sums<N1, true>(sv, fl, enx >= 0 ? trace_line<N1, true>(vx[iy], A.ops) : gx, A.ops);
+                    line_sums<N1, true>(sv, fl, enx >= 0 ? trace_line<N1, true>(vx[iy], A.ops) : bx, A.ops);
                 else
-                    line_sums<N1, false>(sv, fl, enx >= 0 ? trace_line<N1, false>(vx[iy], A.ops) : gx, A.ops);
+                    line_sums<N1, false>(sv, fl, enx >= 0 ? trace_line<N1, false>(vx[iy], A.ops) : bx, A.ops);
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
@@ -158,10 +182,11 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     fl[j] = f[ix + N1 * j];
+                const float by = rwy ? gy * __ldg(rwy + ix) : gy;
                 if (l1)
-                    line_sums<N1, true>(sv, fl, eny >= 0 ? trace_line<N1, true>(vy[ix], A.ops) : gy, A.ops);
+                    line_sums<N1, true>(sv, fl, eny >= 0 ? trace_line<N1, true>(vy[ix], A.ops) : by, A.ops);
                 else
-                    line_sums<N1, false>(sv, fl, eny >= 0 ? trace_line<N1, false>(vy[ix], A.ops) : gy, A.ops);
+                    line_sums<N1, false>(sv, fl, eny >= 0 ? trace_line<N1, false>(vy[ix], A.ops) : by, A.ops);
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
@@ -180,17 +205,19 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     fl[j] = sm.tile[q + NQ * j][lane];
+                const float bz = rwz ? gz * __ldg(rwz + ix) : gz;
                 if (l2)
-                    line_sums<N1, true>(sv, fl, enz >= 0 ? trace_line<N1, true>(vz[ix], A.ops) : gz, A.ops);
+                    line_sums<N1, true>(sv, fl, enz >= 0 ? trace_line<N1, true>(vz[ix], A.ops) : bz, A.ops);
                 else
-                    line_sums<N1, false>(sv, fl, enz >= 0 ? trace_line<N1, false>(vz[ix], A.ops) : gz, A.ops);
+                    line_sums<N1, false>(sv, fl, enz >= 0 ? trace_line<N1, false>(vz[ix], A.ops) : bz, A.ops);
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     sm.zc[q + NQ * j][lane] = sv[j];
             }
             __syncthreads();  // B2: z-sums complete
             // BGK source towards the conservative Maxwellian, Shu-Osher combination, store
-            const float cg = bdt * A.inv_tau * __ldg(A.gmask + slot);
+            const float gm = __ldg(A.gmask + slot);
+            const float cg = bdt * A.inv_tau * gm, cf = bdt * gm;
             const float xs = x0 * x0 + x1 * x1 + x2 * x2;
             float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
 #pragma unroll
@@ -200,7 +227,13 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                 const float b4 = sm.par[i][4];
                 const float ex = fmaf(b4, xs, fmaf(pb.w, x2, fmaf(pb.z, x1, fmaf(pb.y, x0, pb.x))));
                 const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
-                o[q] = fmaf(cg, exp2f(ex), a);
+                float gc = cg;
+                if (GEN && A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
+                    const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
+                    const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
+                    gc = fmaf(cf, qv, cg);
+                }
+                o[q] = fmaf(gc, exp2f(ex), a);
                 __stcs(dst + i * kWarp, o[q]);
             }
         } else {
@@ -260,11 +293,11 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
 }
 
 
-template <int N1, int MODE, int OCT>
+template <int N1, int MODE, int OCT, int GEN>
 cudaError_t launch3(const StageArgs &A, cudaStream_t s)
 {
     const int ngroups = (A.nvt + A.G - 1) / A.G;
-    k_stage3<N1, MODE, OCT><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3Smem<N1>), s>>>(A);
+    k_stage3<N1, MODE, OCT, GEN><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3Smem<N1>), s>>>(A);
     return cudaGetLastError();
 }
 
@@ -272,32 +305,44 @@ template <int N1>
 cudaError_t prepare3()
 {
     const int smem = (int)sizeof(Stage3Smem<N1>);
-    cudaError_t e = cudaFuncSetAttribute(k_stage3<N1, 1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-#define BGK_P3(O)                                                                                     \
-    if (e == cudaSuccess)                                                                             \
-        e = cudaFuncSetAttribute(k_stage3<N1, 0, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_stage3<N1, 1, 8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+#define BGK_P3(O)                                                                                         \
+    if (e == cudaSuccess)                                                                                 \
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    if (e == cudaSuccess)                                                                                 \
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     BGK_P3(0) BGK_P3(1) BGK_P3(2) BGK_P3(3) BGK_P3(4) BGK_P3(5) BGK_P3(6) BGK_P3(7) BGK_P3(8)
 #undef BGK_P3
     return e;
 }
 
-// mode 0: stage of octant oct (8 = mixed octants); mode 1: moments only
+template <int N1, int GEN>
+cudaError_t launch3_oct(const StageArgs &A, int oct, cudaStream_t s)
+{
+    switch (oct) {
+    case 0: return launch3<N1, 0, 0, GEN>(A, s);
+    case 1: return launch3<N1, 0, 1, GEN>(A, s);
+    case 2: return launch3<N1, 0, 2, GEN>(A, s);
+    case 3: return launch3<N1, 0, 3, GEN>(A, s);
+    case 4: return launch3<N1, 0, 4, GEN>(A, s);
+    case 5: return launch3<N1, 0, 5, GEN>(A, s);
+    case 6: return launch3<N1, 0, 6, GEN>(A, s);
+    case 7: return launch3<N1, 0, 7, GEN>(A, s);
+    default: return launch3<N1, 0, 8, GEN>(A, s);
+    }
+}
+
+// mode 0: stage of octant oct (8 = mixed octants), lean (all periodic, no force) or general form;
+// mode 1: moments only
 template <int N1>
 cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
 {
     if (mode == 1)
-        return launch3<N1, 1, 8>(A, s);
-    switch (oct) {
-    case 0: return launch3<N1, 0, 0>(A, s);
-    case 1: return launch3<N1, 0, 1>(A, s);
-    case 2: return launch3<N1, 0, 2>(A, s);
-    case 3: return launch3<N1, 0, 3>(A, s);
-    case 4: return launch3<N1, 0, 4>(A, s);
-    case 5: return launch3<N1, 0, 5>(A, s);
-    case 6: return launch3<N1, 0, 6>(A, s);
-    case 7: return launch3<N1, 0, 7>(A, s);
-    default: return launch3<N1, 0, 8>(A, s);
-    }
+        return launch3<N1, 1, 8, 0>(A, s);
+    bool general = A.fpar != nullptr;
+    for (int f = 0; f < 6; f++)
+        general = general || A.mesh.bc[f] != 0;
+    return general ? launch3_oct<N1, 1>(A, oct, s) : launch3_oct<N1, 0>(A, oct, s);
 }
 
 }  // namespace bgk

@@ -23,6 +23,14 @@ CONFIGS = {
     # 3-D Taylor-Green-type flow on [0, 2 pi]^3, 16^3 hexahedra at p = 3, 24^3 velocities on [-5, 5]^3
     "taylor_green": dict(dim=3, nelem=(16, 16, 16), lo=(0.0,) * 3, hi=(TWO_PI,) * 3, p=3, nv=(24, 24, 24),
                          vlo=(-5.0,) * 3, vhi=(5.0,) * 3, tau=1e-3, cfl=0.1, steps=50),
+    # rarefied channel between two diffuse isothermal walls (y = 0, 1; T_w = 1), periodic in x and z,
+    # 32 x 16 x 4 hexahedra at p = 2, 32^3 velocities on [-6, 6]^3, body force 0.01 in x, Kn = 0.1
+    # (tau = Kn H / sqrt(pi theta_w / 2), the BGK mean free path with H = 1, theta_w = 1)
+    "channel": dict(dim=3, nelem=(32, 16, 4), lo=(0.0,) * 3, hi=(2.0, 1.0, 0.25), p=2, nv=(32, 32, 32),
+                    vlo=(-6.0,) * 3, vhi=(6.0,) * 3, tau=0.1 / math.sqrt(math.pi / 2.0), cfl=0.1, steps=50,
+                    bc=((PERIODIC, PERIODIC), (WALL, WALL), (PERIODIC, PERIODIC)),
+                    bc_state=(((0,) * 5, (0,) * 5), ((0, 0, 0, 0, 1.0), (0, 0, 0, 0, 1.0)), ((0,) * 5, (0,) * 5)),
+                    force=(0.01, 0.0, 0.0)),
 }
 
 
@@ -62,7 +70,15 @@ def prim_taylor_green(x: np.ndarray, mach: float = 0.1, gamma: float = 5.0 / 3.0
     return P
 
 
-PRIM = {"periodic1d": prim_periodic1d, "taylor_green": prim_taylor_green}
+def prim_channel(x: np.ndarray) -> np.ndarray:
+    """Gas at rest, rho = 1, T = 1."""
+    P = np.zeros((len(x), 5))
+    P[:, 0] = 1.0
+    P[:, 4] = 1.0
+    return P
+
+
+PRIM = {"periodic1d": prim_periodic1d, "taylor_green": prim_taylor_green, "channel": prim_channel}
 
 
 def prim_field(name: str, x: np.ndarray) -> np.ndarray:

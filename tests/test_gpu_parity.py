@@ -28,6 +28,8 @@ def solver(c, **opts):
     from paper_2308_06196_gb300.bgk import Solver
 
     k = W.mesh_kwargs(c)
+    if c.get("force") is not None:
+        opts.setdefault("body_force", c["force"])
     return Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"],
                   bc=c.get("bc"), bc_state=c.get("bc_state"), **opts)
 
@@ -38,7 +40,8 @@ def oracle_problem(c):
     bcs = c.get("bc_state")
     return orc.Problem(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"],
                        bc=None if bc is None else np.asarray(bc).reshape(6),
-                       bc_state=None if bcs is None else np.asarray(bcs).reshape(30))
+                       bc_state=None if bcs is None else np.asarray(bcs, dtype=float).reshape(30),
+                       force=c.get("force"))
 
 
 def psi(xi):
@@ -320,3 +323,58 @@ def test_fp64_free_stream():
     s.set_f(f)
     s.step(0.001, 10)
     assert rel(s.get_f(), f) < 1e-13
+
+
+# ---------------------------------------------------------------------------------------------
+# diffuse walls and the body force (the channel workload's boundary and source)
+
+
+def small_channel(**kw):
+    return W.config("channel", nelem=(4, 3, 2), hi=(1.0, 1.0, 0.5), nv=(8, 8, 8), vlo=(-5.0,) * 3,
+                    vhi=(5.0,) * 3, **kw)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_channel_walls_and_force_vs_oracle(fp64):
+    from paper_2308_06196_gb300.bgk import FP64, FP32_SPLIT
+
+    c = small_channel(force=(0.05, 0.02, 0.0))
+    pr = oracle_problem(c)
+    s = solver(c, precision=FP64 if fp64 else FP32_SPLIT)
+    # a non-uniform state so the walls see different densities at every face point
+    f = random_f(pr, seed=50)
+    s.set_f(f)
+    pr.set_f(f if fp64 else f.astype(np.float32).astype(np.float64))
+    dt = pr.dt(0.1)
+    s.step(dt, 3)
+    pr.step(dt, 3)
+    tol = 1e-10 if fp64 else 1e-5
+    assert rel(s.get_f(), pr.get_f()) < tol
+    assert rel(s.moments(), pr.moments()) < tol
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_channel_mass_conserved_momentum_driven(fp64):
+    # walls have zero net discrete mass flux and x, z are periodic: total mass is conserved; at rest
+    # the first step gains x-momentum rho F dt per unit volume (no wall shear yet)
+    from paper_2308_06196_gb300.bgk import FP64, FP32_SPLIT
+
+    c = small_channel()
+    s = solver(c, precision=FP64 if fp64 else FP32_SPLIT)
+    s.set_state(W.prim_field("channel", s.points()))
+    _, Wg = orc.gauss_legendre(3)
+    Wn = np.einsum("i,j,k->kji", Wg, Wg, Wg).ravel()
+    vol = 1.0 * 1.0 * 0.5
+    jac = vol / (4 * 3 * 2) / 8.0  # element volume / reference volume
+
+    def glob(Q):
+        return (Q.reshape(-1, 27, 5) * Wn[None, :, None]).sum((0, 1)) * jac
+
+    G0 = glob(s.moments())
+    dt = s.dt(0.1)
+    s.step(dt, 1)
+    G1 = glob(s.moments())
+    assert abs(G1[1] - G0[1] - G0[0] * 0.01 * dt) <= 0.05 * G0[0] * 0.01 * dt
+    s.step(dt, 19)
+    G2 = glob(s.moments())
+    assert abs(G2[0] - G0[0]) <= (1e-12 if fp64 else 2e-6) * G0[0]
