@@ -23,7 +23,8 @@ namespace bgk {
 template <int N1>
 struct Stage3Smem {
     static constexpr int NP = N1 * N1 * N1;
-    float tile[NP][kWarp];        // f_s of the element, [node][lane]
+    float tile[2][NP][kWarp];     // f_s of the element, [node][lane], double-buffered (cp.async)
+    float fnb[2][NP][kWarp];      // f^n of the element (each warp its own layer), double-buffered
     float zc[NP][kWarp];          // z-derivative sums, [node][lane]
     float wf[N1][16][36];         // per warp: its layer's stage output, [node][velocity] (16 rows)
     float par[NP][kParamStride];  // BGK exponents of the element's points
@@ -81,26 +82,54 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
     const float kb = A.b * (1.f - A.dt * A.inv_tau);
     const float bdt = A.b * A.dt;
 
+    // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
+    // 128 bytes, contiguous in global and shared memory
+    const bool has_fn = MODE == 0 && A.fn != nullptr;
+    auto prefetch = [&](int vl, int b) {
+        constexpr int NCH = NQ * kWarp / 4;  // 16-byte chunks of one layer
+        const float4 *gs = reinterpret_cast<const float4 *>(A.src + fidx(vl, e, NQ * w, 0, E, NP));
+        float4 *ss = reinterpret_cast<float4 *>(&sm.tile[b][NQ * w][0]);
+#pragma unroll
+        for (int m = lane; m < NCH; m += kWarp)
+            cp_async16(ss + m, gs + m);
+        if (has_fn) {
+            const float4 *gf = reinterpret_cast<const float4 *>(A.fn + fidx(vl, e, NQ * w, 0, E, NP));
+            float4 *sf = reinterpret_cast<float4 *>(&sm.fnb[b][NQ * w][0]);
+#pragma unroll
+            for (int m = lane; m < NCH; m += kWarp)
+                cp_async16(sf + m, gf + m);
+        }
+        cp_commit();
+    };
+    prefetch(vl0, 0);
+
     for (int vl = vl0; vl < vl1; vl++) {
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
+        const int b = (vl - vl0) & 1;
+        // the other buffer was last read before the previous tile's B2, which every warp has passed
+        if (vl + 1 < vl1) {
+            prefetch(vl + 1, b ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncwarp();
         const float x0 = __ldg(A.xi + slot), x1 = __ldg(A.xi + A.nslots + slot), x2 = __ldg(A.xi + 2 * A.nslots + slot);
-        const float *tileg = A.src + fidx(vl, e, 0, lane, E, NP);
         float f[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++)
-            f[q] = __ldg(tileg + (q + NQ * w) * kWarp);
+            f[q] = sm.tile[b][q + NQ * w][lane];
         float o[NQ];
         if (MODE == 0) {
             const bool l0 = OCT < 8 ? (OCT & 1) != 0 : x0 >= 0.f;
             const bool l1 = OCT < 8 ? (OCT & 2) != 0 : x1 >= 0.f;
             const bool l2 = OCT < 8 ? (OCT & 4) != 0 : x2 >= 0.f;
             float acc[NQ];
-            if (A.fn) {
-                const float *fng = A.fn + fidx(vl, e, 0, lane, E, NP);
+            if (has_fn) {
 #pragma unroll
                 for (int q = 0; q < NQ; q++)
-                    acc[q] = __ldcs(fng + (q + NQ * w) * kWarp);
+                    acc[q] = sm.fnb[b][q + NQ * w][lane];
             } else {
 #pragma unroll
                 for (int q = 0; q < NQ; q++)
@@ -135,9 +164,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                     for (int j = 0; j < N1; j++)
                         vz[ix][j] = __ldg(nb + (ix + N1 * w + NQ * j) * kWarp);
             }
-#pragma unroll
-            for (int q = 0; q < NQ; q++)
-                sm.tile[q + NQ * w][lane] = f[q];
             // acc = an f^n + b (1 - dt/tau) f_s, then x and y lines from registers
 #pragma unroll
             for (int q = 0; q < NQ; q++)
@@ -204,7 +230,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                 float fl[N1], sv[N1];
 #pragma unroll
                 for (int j = 0; j < N1; j++)
-                    fl[j] = sm.tile[q + NQ * j][lane];
+                    fl[j] = sm.tile[b][q + NQ * j][lane];
                 const float bz = rwz ? gz * __ldg(rwz + ix) : gz;
                 if (l2)
                     line_sums<N1, true>(sv, fl, enz >= 0 ? trace_line<N1, true>(vz[ix], A.ops) : bz, A.ops);
@@ -233,7 +259,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                     const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
                     gc = fmaf(cf, qv, cg);
                 }
-                o[q] = fmaf(gc, exp2f(ex), a);
+                o[q] = fmaf(gc, ex2(ex), a);
                 __stcs(dst + i * kWarp, o[q]);
             }
         } else {

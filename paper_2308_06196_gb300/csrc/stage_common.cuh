@@ -65,6 +65,26 @@ __device__ __forceinline__ void line_sums(float (&s)[N1], const float (&fl)[N1],
 
 // Upwind trace of one neighbour line v (difference form, exact for a constant state): a left
 // neighbour is evaluated at its +1 end (lp), a right neighbour at its -1 end (lm).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
+// 2^x on the special-function unit (inputs below -126 flush the result to 0)
+__device__ __forceinline__ float ex2(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int N1, bool LEFT>
 __device__ __forceinline__ float trace_line(const float (&v)[N1], const Ops &op)
 {
