@@ -208,6 +208,7 @@ def main():
     Q_pin = torch.empty((s.npts, 5), dtype=torch.float64).pin_memory()
     prim_dev = prim_pin.cuda()
     s.set_state(prim_dev)
+    tiles_per_task = s.autotune()
     dt = s.dt(c["cfl"])
     dof = s.ndof
 
@@ -325,7 +326,7 @@ def main():
         "config": {"workload": WORKLOAD, "mesh": f"{c['nelem'][0]}^3 hex p=3 on [0,2pi]^3", "n_x": s.npts, "nv": list(c["nv"]),
                    "dof": dof, "tau": c["tau"], "dt": dt, "precision": "f32 storage+advection, f64 Newton",
                    "l2": "inputs larger than L2 (14.5 GB per f array)", "parallelism": f"replicas x{world}",
-                   "graph_ms_per_step": graph_ms},
+                   "graph_ms_per_step": graph_ms, "tiles_per_task": tiles_per_task},
         "roofline": {"bound": "hbm", "kernel": "k_stage", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "alg_bytes_per_launch": tm["stage_alg_bytes"], "avg_launch_ms": stage_avg_ms,

@@ -136,6 +136,13 @@ int bgk_synchronize(bgk_ctx *ctx);
 /* Explicit step size min(cfl / max_k sum_d |xi_kd| / h_d, tau). */
 double bgk_dt(const bgk_ctx *ctx, double cfl);
 
+/* Tile-shape autotuner: times the stage kernel for several task lengths (32-velocity tiles per warp
+ * task: 2, 4, 8, 16) on this context's own buffers, keeps the fastest for this context and caches it
+ * per (dim, degree, velocity grid, mesh, chunking) for the rest of the process. Does not change f,
+ * the moments or the equilibrium; invalidates the captured graph. *g_out (may be NULL) receives the
+ * chosen length (0 for the all-FP64 form, which has no task shape). */
+int bgk_autotune(bgk_ctx *ctx, int *g_out);
+
 /* Launch timing: when on, bgk_step launches its kernels directly (not through the CUDA graph) and
  * brackets every stage and Newton launch with CUDA events on the context stream. bgk_timing()
  * synchronises and returns the summed milliseconds and launch counts since timing was switched on,

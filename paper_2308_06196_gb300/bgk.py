@@ -23,7 +23,7 @@ SYMBOLS = (
     "bgk_create", "bgk_destroy", "bgk_last_error", "bgk_set_stream", "bgk_info", "bgk_points",
     "bgk_set_state", "bgk_set_state_device", "bgk_set_f", "bgk_get_f", "bgk_step", "bgk_moments",
     "bgk_moments_device", "bgk_equilibrium", "bgk_synchronize", "bgk_dt", "bgk_set_timing", "bgk_timing",
-    "bgk_equilibrium_noalloc",
+    "bgk_equilibrium_noalloc", "bgk_autotune",
 )
 
 
@@ -84,6 +84,7 @@ def lib():
             L.bgk_set_timing.argtypes = [vp, C.c_int]
             L.bgk_timing.argtypes = [vp, dp, i64p, dp, i64p, dp]
             L.bgk_equilibrium_noalloc.argtypes = [vp, C.c_int64, C.POINTER(bgk_vgrid), vp, vp, vp]
+            L.bgk_autotune.argtypes = [vp, C.POINTER(C.c_int)]
             _lib = L
     return _lib
 
@@ -237,6 +238,12 @@ class Solver:
 
     def dt(self, cfl):
         return lib().bgk_dt(self.h, float(cfl))
+
+    def autotune(self):
+        """Pick the fastest task length for this problem (cached per shape); returns it."""
+        g = C.c_int()
+        self._check(lib().bgk_autotune(self.h, C.byref(g)))
+        return g.value
 
     def set_timing(self, on):
         self._check(lib().bgk_set_timing(self.h, int(bool(on))))

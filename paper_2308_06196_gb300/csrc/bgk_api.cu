@@ -42,6 +42,7 @@ using namespace bgk;
 namespace {
 
 const double kPi = 3.14159265358979323846;
+const int kMinTuneG = 2;  // shortest task (tiles per warp task) the autotuner tries
 
 struct Chunk {
     int vt0, nvt, group0, ngroups;
@@ -161,7 +162,7 @@ struct bgk_ctx {
     bgk_opts opts{};
     double xg[kMaxN1] = {0};
     // velocity plan
-    int nvt = 0, nslots = 0, G = 1, ngroups = 0;
+    int nvt = 0, nslots = 0, G = 1, ngroups = 0, max_groups = 0;
     std::vector<int> slotk;
     std::vector<Chunk> chunks;
     int64_t chunk_floats = 0;  // floats per pool slot
@@ -676,6 +677,10 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         ch.ngroups = (ch.nvt + c->G - 1) / c->G;
         c->ngroups += ch.ngroups;
     }
+    // the partial-moment table is sized for the shortest task the autotuner tries
+    c->max_groups = 0;
+    for (auto &ch : c->chunks)
+        c->max_groups += (ch.nvt + std::min(c->G, kMinTuneG) - 1) / std::min(c->G, kMinTuneG);
     c->chunk_floats = (int64_t)maxc * E * c->NP * kWarp;
 
     // mesh descriptor
@@ -691,7 +696,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     // memory check before any allocation
     const int64_t fA = (int64_t)c->nvt * E * c->NP * kWarp;
     const int64_t need = (fA + (int64_t)(c->chunks.size() + 1) * c->chunk_floats) * c->esize +
-                         (int64_t)c->ngroups * 5 * c->npts * 4 + c->npts * (5 * 8 * 3 + kParamStride * 4) +
+                         (int64_t)c->max_groups * 5 * c->npts * 4 + c->npts * (5 * 8 * 3 + kParamStride * 4) +
                          (int64_t)c->nslots * 4 * 16;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
@@ -737,7 +742,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         if (c->prec == BGK_FP64)
             AL(c->fpar64, c->npts * 5);
     }
-    AL(c->partial, (int64_t)c->ngroups * 5 * c->npts);
+    AL(c->partial, (int64_t)c->max_groups * 5 * c->npts);
     AL(c->param, c->npts * kParamStride);
     AL(c->Q, c->npts * 5);
     AL(c->prim, c->npts * 5);
@@ -1025,6 +1030,92 @@ double bgk_dt(const bgk_ctx *c, double cfl)
         smax = std::max(smax, s);
     }
     return std::min(cfl / smax, c->tau);
+}
+
+// Tile-shape autotuner: tiles per task G, per (mesh, degree, velocity grid), cached for the process.
+static std::vector<std::pair<std::string, int>> g_tuned;
+
+static void set_task_length(bgk_ctx *c, int G)
+{
+    c->G = G;
+    c->ngroups = 0;
+    for (auto &ch : c->chunks) {
+        ch.group0 = c->ngroups;
+        ch.ngroups = (ch.nvt + G - 1) / G;
+        c->ngroups += ch.ngroups;
+    }
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+}
+
+int bgk_autotune(bgk_ctx *c, int *g_out)
+{
+    if (!c)
+        return BGK_EINVAL;
+    if (c->prec == BGK_FP64) {  // the plain form has no task shape
+        if (g_out)
+            *g_out = 0;
+        return BGK_OK;
+    }
+    char key[256];
+    snprintf(key, sizeof key, "%d/%d/%d,%d,%d/%d,%d,%d/%zu/%d", c->dim, c->p, c->nv[0], c->nv[1], c->nv[2], c->ne[0],
+             c->ne[1], c->ne[2], c->chunks.size(), (int)(c->has_wall || c->has_force || c->bc[0] || c->bc[2] || c->bc[4]));
+    for (auto &kv : g_tuned)
+        if (kv.first == key) {
+            set_task_length(c, kv.second);
+            if (g_out)
+                *g_out = c->G;
+            return BGK_OK;
+        }
+    int maxc = 0;
+    for (auto &ch : c->chunks)
+        maxc = std::max(maxc, ch.nvt);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestG = c->G;
+    const int C = (int)c->chunks.size();
+    for (int G = kMinTuneG; G <= 16 && G <= std::max(kMinTuneG, maxc); G *= 2) {
+        set_task_length(c, G);
+        float tot = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+            CK(cudaEventRecord(e0, c->stream));
+            // stage 2 of every chunk: reads the first pool slots and f^n, writes the second slots
+            for (int q = 0; q < C; q++) {
+                const Chunk &ch = c->chunks[q];
+                StageArgs A = stage_args(c, ch);
+                A.src = c->pool + (int64_t)q * c->chunk_floats;
+                A.fn = chunk_ptr(c, c->fA, ch.vt0);
+                A.dst = c->pool + (int64_t)(q == 0 ? C : q - 1) * c->chunk_floats;
+                A.an = 0.75f;
+                A.b = 0.25f;
+                A.dt = (float)(0.1 * c->tau);
+                if (q == 0 && C > 1)
+                    A.dst = c->pool + (int64_t)C * c->chunk_floats;
+                CK(launch_stage(A, c->p, 0, ch.oct, c->stream));
+            }
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0)
+                tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            bestG = G;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_task_length(c, bestG);
+    g_tuned.emplace_back(key, bestG);
+    if (g_out)
+        *g_out = bestG;
+    return BGK_OK;
 }
 
 int bgk_set_timing(bgk_ctx *c, int on)
