@@ -153,6 +153,44 @@ int bgk_timing(bgk_ctx *ctx, double *stage_ms, int64_t *stage_launches, double *
                int64_t *newton_launches, double *stage_alg_bytes);
 
 /* ---------------------------------------------------------------------------------------------
+ * Batches of independent problems. The paper runs one problem at a time; the method's steps are
+ * the same per member (Sec. 2.1-2.2), only scheduled together: each RK stage of every member runs
+ * in one persistent stage launch (CTAs take (member, element block, tile run) tasks from an atomic
+ * work counter, reset by a memset in the same stream) followed by one Newton launch over all
+ * members' points, and one step of all members is captured in one CUDA graph.
+ *
+ * bgk_batch_create: members are n distinct contexts created on the current device with
+ *   precision BGK_FP32_SPLIT, dim = 1, p <= 3 and opts.chunks = 1 (the three stage buffers of a
+ *   member are then disjoint, so members and their tiles run concurrently). Their meshes, degrees,
+ *   velocity grids, relaxation times and boundary kinds may all differ. The batch keeps pointers to
+ *   the members (not owned): destroy the batch before any member. BGK_EINVAL for an unsuitable
+ *   member or a repeated one. The batch has its own stream (bgk_batch_set_stream replaces it).
+ * bgk_batch_step: enqueues nsteps steps of every member, member q with time step dt[q] (host array
+ *   of n). Waits on the GPU for work already enqueued on the members' streams (e.g. bgk_set_state)
+ *   and makes the members' streams wait for the batch, so bgk_moments / bgk_get_f of a member
+ *   afterwards see the new state. Asynchronous; returns the sticky batch status.
+ * bgk_batch_synchronize: waits for the batch stream and returns the status of all members' Newton
+ *   solves (BGK_EDOMAIN / BGK_ENEWTON also become sticky in every member).
+ * bgk_batch_autotune: the tile-shape autotuner of the batch: for every (degree, velocity grid) class
+ *   of members in turn, times the persistent stage launch with the class's task length at 2, 4, 8
+ *   and 16 tiles (the other classes fixed) and keeps the fastest. Changes no state.
+ * bgk_batch_info: total points, degrees of freedom and stage tasks of the batch.
+ * bgk_batch_set_timing / bgk_batch_timing: as bgk_set_timing / bgk_timing, for the batch launches.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct bgk_batch bgk_batch;
+int bgk_batch_create(int n, bgk_ctx *const *members, bgk_batch **out);
+void bgk_batch_destroy(bgk_batch *batch);
+const char *bgk_batch_last_error(const bgk_batch *batch);
+int bgk_batch_set_stream(bgk_batch *batch, void *stream);
+int bgk_batch_step(bgk_batch *batch, const double *dt, int nsteps);
+int bgk_batch_synchronize(bgk_batch *batch);
+int bgk_batch_autotune(bgk_batch *batch);
+int bgk_batch_info(const bgk_batch *batch, int64_t *npoints, int64_t *ndof, int64_t *tasks);
+int bgk_batch_set_timing(bgk_batch *batch, int on);
+int bgk_batch_timing(bgk_batch *batch, double *stage_ms, int64_t *stage_launches, double *newton_ms,
+                     int64_t *newton_launches, double *stage_alg_bytes);
+
+/* ---------------------------------------------------------------------------------------------
  * Allocation-free entry point. The paper has no counterpart: this exists for callers that cannot
  * call cudaMalloc (code running under another framework's device-memory pool or allocator hooks,
  * processes with a no-allocation policy after start-up, or ones whose device footprint is fixed

@@ -24,6 +24,8 @@ SYMBOLS = (
     "bgk_set_state", "bgk_set_state_device", "bgk_set_f", "bgk_get_f", "bgk_step", "bgk_moments",
     "bgk_moments_device", "bgk_equilibrium", "bgk_synchronize", "bgk_dt", "bgk_set_timing", "bgk_timing",
     "bgk_equilibrium_noalloc", "bgk_autotune",
+    "bgk_batch_create", "bgk_batch_destroy", "bgk_batch_last_error", "bgk_batch_set_stream", "bgk_batch_step",
+    "bgk_batch_synchronize", "bgk_batch_autotune", "bgk_batch_info", "bgk_batch_set_timing", "bgk_batch_timing",
 )
 
 
@@ -85,6 +87,18 @@ def lib():
             L.bgk_timing.argtypes = [vp, dp, i64p, dp, i64p, dp]
             L.bgk_equilibrium_noalloc.argtypes = [vp, C.c_int64, C.POINTER(bgk_vgrid), vp, vp, vp]
             L.bgk_autotune.argtypes = [vp, C.POINTER(C.c_int)]
+            L.bgk_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
+            L.bgk_batch_destroy.argtypes = [vp]
+            L.bgk_batch_destroy.restype = None
+            L.bgk_batch_last_error.argtypes = [vp]
+            L.bgk_batch_last_error.restype = C.c_char_p
+            L.bgk_batch_set_stream.argtypes = [vp, vp]
+            L.bgk_batch_step.argtypes = [vp, dp, C.c_int]
+            L.bgk_batch_synchronize.argtypes = [vp]
+            L.bgk_batch_autotune.argtypes = [vp]
+            L.bgk_batch_info.argtypes = [vp, i64p, i64p, i64p]
+            L.bgk_batch_set_timing.argtypes = [vp, C.c_int]
+            L.bgk_batch_timing.argtypes = [vp, dp, i64p, dp, i64p, dp]
             _lib = L
     return _lib
 
@@ -252,5 +266,67 @@ class Solver:
         sm, nm, by = C.c_double(), C.c_double(), C.c_double()
         sl, nl = C.c_int64(), C.c_int64()
         self._check(lib().bgk_timing(self.h, C.byref(sm), C.byref(sl), C.byref(nm), C.byref(nl), C.byref(by)))
+        return dict(stage_ms=sm.value, stage_launches=sl.value, newton_ms=nm.value, newton_launches=nl.value,
+                    stage_alg_bytes=by.value)
+
+
+class Batch:
+    """A batch of Solver members stepped together (bgk_batch_create ... bgk_batch_destroy).
+    Members must be FP32-split line problems created with chunks=1; the batch does not own them."""
+
+    def __init__(self, members):
+        L = lib()
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m.h for m in self.members])
+        h = C.c_void_p()
+        rc = L.bgk_batch_create(len(self.members), arr, C.byref(h))
+        if rc != BGK_OK:
+            raise BgkError(rc, "bgk_batch_create failed (see stderr)")
+        self.h = h
+        n, d, t = C.c_int64(), C.c_int64(), C.c_int64()
+        L.bgk_batch_info(self.h, C.byref(n), C.byref(d), C.byref(t))
+        self.npts, self.ndof, self.tasks = n.value, d.value, t.value
+
+    def _check(self, rc):
+        if rc != BGK_OK:
+            raise BgkError(rc, lib().bgk_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bgk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        self._check(lib().bgk_batch_set_stream(self.h, C.c_void_p(stream_ptr or 0)))
+
+    def step(self, dt, nsteps=1):
+        """dt: one time step per member (sequence of floats)."""
+        a = np.ascontiguousarray(dt, dtype=np.float64)
+        assert a.shape == (len(self.members),)
+        self._dt = a  # the library reads it during the call only
+        self._check(lib().bgk_batch_step(self.h, _dptr(a), int(nsteps)))
+
+    def synchronize(self):
+        self._check(lib().bgk_batch_synchronize(self.h))
+
+    def autotune(self):
+        self._check(lib().bgk_batch_autotune(self.h))
+        n, d, t = C.c_int64(), C.c_int64(), C.c_int64()
+        lib().bgk_batch_info(self.h, C.byref(n), C.byref(d), C.byref(t))
+        self.tasks = t.value
+
+    def set_timing(self, on):
+        self._check(lib().bgk_batch_set_timing(self.h, int(bool(on))))
+
+    def timing(self):
+        sm, nm, by = C.c_double(), C.c_double(), C.c_double()
+        sl, nl = C.c_int64(), C.c_int64()
+        self._check(lib().bgk_batch_timing(self.h, C.byref(sm), C.byref(sl), C.byref(nm), C.byref(nl), C.byref(by)))
         return dict(stage_ms=sm.value, stage_launches=sl.value, newton_ms=nm.value, newton_launches=nl.value,
                     stage_alg_bytes=by.value)

@@ -23,6 +23,13 @@ namespace bgk {
 cudaError_t launch_stage(const StageArgs &A, int p, int mode, int oct, cudaStream_t s);
 cudaError_t prepare_stage(int dim, int p);
 cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s);
+cudaError_t launch_newton_batch(const NewtonArgs *d_args, const int *d_pt_start, int n, int total_pts,
+                                cudaStream_t s);
+cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int *d_task_start, int n, int *d_counter,
+                                 int ctas, cudaStream_t s);
+cudaError_t set_batch_ops(int n1, const Ops &op);
+int stage1d_tasks(const StageArgs &A);
+int stage1d_batch_ctas();
 cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slotk, int nvt, int E, int NP,
                                    const int n[3], const double v0[3], const double dv[3], int *err,
                                    cudaStream_t s);
@@ -168,7 +175,7 @@ struct bgk_ctx {
     int64_t chunk_floats = 0;  // floats per pool slot
     // device buffers
     float *fA = nullptr, *pool = nullptr;
-    float *xi = nullptr, *wpsi = nullptr, *gmask = nullptr, *ghost = nullptr;
+    float *xi = nullptr, *mi = nullptr, *wpsi = nullptr, *gmask = nullptr, *ghost = nullptr;
     int *slotk_d = nullptr;
     float *partial = nullptr, *param = nullptr;
     // all-FP64 form
@@ -238,7 +245,12 @@ cudaError_t dalloc(bgk_ctx *c, T **p, size_t n)
 StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
 {
     StageArgs A{};
-    A.xi = c->xi;
+    A.mi = c->mi;
+    for (int d = 0; d < 3; d++) {
+        A.vc[d] = (float)(c->vlo[d] + 0.5 * (c->nv[d] - 1) * c->dv[d]);
+        A.vs[d] = (float)(0.5 * c->dv[d]);
+    }
+    A.viso = c->dv[0] == c->dv[1] && c->dv[0] == c->dv[2];
     A.wpsi = c->wpsi;
     A.gmask = c->gmask;
     A.ghost = c->ghost;
@@ -249,6 +261,7 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.partial = c->partial;
     A.ops = c->ops;
     A.mesh = c->mesh;
+    A.n1 = c->N1;
     A.vt0 = ch.vt0;
     A.nvt = ch.nvt;
     A.G = c->G;
@@ -257,6 +270,24 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.npts = (int)c->npts;
     A.inv_tau = (float)(1.0 / c->tau);
     return A;
+}
+
+// Shu-Osher stage st (0, 1, 2) of step dt in FP32: b = 1, 1/4, 2/3 and an = 1 - b (exact), the
+// Maxwellian weight kg = b dt / tau and kb = b - kg, rounded so that kb + kg = b exactly (Sterbenz's
+// lemma makes b - kg or b - kb exact for dt / tau <= 2). With inexact sums a state equal to f^n and
+// to its Maxwellian would gain the sum's rounding (about 3e-8 for 1/3 + 2/3) at every stage.
+void stage_coeffs(StageArgs &A, int st, double dt, double tau)
+{
+    static const float bb[3] = {1.f, 0.25f, (float)(2.0 / 3.0)};
+    const float b = bb[st];
+    A.b = b;
+    A.an = 1.f - b;
+    A.dt = (float)dt;
+    A.inv_tau = (float)(1.0 / tau);
+    const float kg0 = (float)((double)b * dt / tau);
+    const float kb = b - kg0;
+    A.kb = kb;
+    A.kg = b - kb;
 }
 
 float *chunk_ptr(bgk_ctx *c, float *base, int vt0) { return base + (int64_t)vt0 * c->E * c->NP * kWarp; }
@@ -453,8 +484,6 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
 // One SSP-RK3 step: three stages, each over all chunks, each followed by the Newton solve.
 int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
 {
-    static const float an[3] = {0.f, 0.75f, 1.f / 3.f};
-    static const float bb[3] = {1.f, 0.25f, 2.f / 3.f};
     const int C = (int)c->chunks.size();
     std::vector<int> slot1(C), slot2(C);
     for (int q = 0; q < C; q++) {
@@ -494,9 +523,7 @@ int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
                 A.fn = Aq;
                 A.dst = Aq;
             }
-            A.an = an[st];
-            A.b = bb[st];
-            A.dt = (float)dt;
+            stage_coeffs(A, st, dt, c->tau);
             int64_t real = 0;
             for (int v = ch.vt0 * kWarp; v < (ch.vt0 + ch.nvt) * kWarp; v++)
                 real += c->slotk[v] >= 0;
@@ -542,7 +569,7 @@ void bgk_destroy(bgk_ctx *c)
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
     }
-    void *bufs[] = {c->fA, c->pool, c->xi, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
+    void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
                     c->fpar64, c->w64};
@@ -697,7 +724,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     const int64_t fA = (int64_t)c->nvt * E * c->NP * kWarp;
     const int64_t need = (fA + (int64_t)(c->chunks.size() + 1) * c->chunk_floats) * c->esize +
                          (int64_t)c->max_groups * 5 * c->npts * 4 + c->npts * (5 * 8 * 3 + kParamStride * 4) +
-                         (int64_t)c->nslots * 4 * 16;
+                         (int64_t)c->nslots * 4 * 20;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
         return bail(BGK_ECUDA, "cudaMemGetInfo failed (no CUDA device?)");
@@ -723,6 +750,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         AL(c->pool, (c->chunks.size() + 1) * c->chunk_floats);
     }
     AL(c->xi, 3 * c->nslots);
+    AL(c->mi, 3 * c->nslots);
     AL(c->wpsi, 5 * c->nslots);
     AL(c->gmask, c->nslots);
     AL(c->ghost, 6 * c->nslots);
@@ -750,7 +778,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     AL(c->err, 1);
 #undef AL
     // velocity tables
-    std::vector<float> xi(3 * c->nslots), wpsi(5 * c->nslots), gm(c->nslots), gh(6 * c->nslots, 0.f);
+    std::vector<float> xi(3 * c->nslots), mi(3 * c->nslots), wpsi(5 * c->nslots), gm(c->nslots), gh(6 * c->nslots, 0.f);
     std::vector<double> xi64(3 * c->nslots), wpsi64(5 * c->nslots), gh64(6 * c->nslots, 0.0), w64h(c->nslots);
     std::vector<float> w32h(c->nslots);
     double win[6] = {0, 0, 0, 0, 0, 0};
@@ -767,13 +795,23 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
             w *= (kk[d] == 0 || kk[d] == c->nv[d] - 1) ? 0.5 * c->dv[d] : c->dv[d];
             xi[d * c->nslots + s] = (float)v[d];
             xi64[d * c->nslots + s] = v[d];
+            mi[d * c->nslots + s] = (float)(2 * kk[d] - (c->nv[d] - 1));
         }
         if (!real)
             w = 0.0;
         const int vt = s / kWarp, l = s % kWarp;
         const double ps[5] = {1.0, v[0], v[1], v[2], 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])};
+        // FP32 kernels: exact index-basis weights W (1, m, sum_d r_d m_d^2) (see index_to_moments)
+        double W = real ? 1.0 : 0.0, m[3], mr = 0.0;
+        for (int d = 0; d < 3; d++) {
+            if (kk[d] == 0 || kk[d] == c->nv[d] - 1)
+                W *= 0.5;
+            m[d] = 2.0 * kk[d] - (c->nv[d] - 1);
+            mr += (double)index_r(c->dv[d], c->dv[0]) * m[d] * m[d];
+        }
+        const double pi[5] = {1.0, m[0], m[1], m[2], mr};
         for (int q = 0; q < 5; q++) {
-            wpsi[((int64_t)vt * 5 + q) * kWarp + l] = (float)(w * ps[q]);
+            wpsi[((int64_t)vt * 5 + q) * kWarp + l] = (float)(W * pi[q]);
             wpsi64[(int64_t)s * 5 + q] = w * ps[q];
         }
         gm[s] = real ? 1.f : 0.f;
@@ -799,6 +837,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     if ((c->w32 && (rc = cudaMemcpy(c->w32, w32h.data(), w32h.size() * 4, cudaMemcpyHostToDevice))) ||
         (c->w64 && (rc = cudaMemcpy(c->w64, w64h.data(), w64h.size() * 8, cudaMemcpyHostToDevice))) ||
         (rc = cudaMemcpy(c->xi, xi.data(), xi.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemcpy(c->mi, mi.data(), mi.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->wpsi, wpsi.data(), wpsi.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->gmask, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->ghost, gh.data(), gh.size() * 4, cudaMemcpyHostToDevice)) ||
@@ -1090,9 +1129,7 @@ int bgk_autotune(bgk_ctx *c, int *g_out)
                 A.src = c->pool + (int64_t)q * c->chunk_floats;
                 A.fn = chunk_ptr(c, c->fA, ch.vt0);
                 A.dst = c->pool + (int64_t)(q == 0 ? C : q - 1) * c->chunk_floats;
-                A.an = 0.75f;
-                A.b = 0.25f;
-                A.dt = (float)(0.1 * c->tau);
+                stage_coeffs(A, 1, 0.1 * c->tau, c->tau);
                 if (q == 0 && C > 1)
                     A.dst = c->pool + (int64_t)C * c->chunk_floats;
                 CK(launch_stage(A, c->p, 0, ch.oct, c->stream));
@@ -1142,6 +1179,461 @@ int bgk_timing(bgk_ctx *c, double *stage_ms, int64_t *stage_launches, double *ne
             sm += ms;
             sl++;
             by += c->evs[q].bytes;
+        } else {
+            nm += ms;
+            nl++;
+        }
+    }
+    if (stage_ms)
+        *stage_ms = sm;
+    if (stage_launches)
+        *stage_launches = sl;
+    if (newton_ms)
+        *newton_ms = nm;
+    if (newton_launches)
+        *newton_launches = nl;
+    if (stage_alg_bytes)
+        *stage_alg_bytes = sl ? by / sl : 0.0;
+    return BGK_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------------
+// Batches of independent line-element problems: one persistent stage launch and one Newton launch per
+// RK stage over all members, the whole step captured in one CUDA graph.
+
+struct bgk_batch {
+    int n = 0;
+    std::vector<bgk_ctx *> probs;
+    StageArgs *d_args = nullptr;    // [3][n] stage arguments of every member
+    NewtonArgs *d_nargs = nullptr;  // [n]
+    int *d_task_start = nullptr;    // [n + 1] task prefix sums (the same for the three stages)
+    int *d_pt_start = nullptr;      // [n + 1] point prefix sums
+    int *d_counter = nullptr;       // work counter of the persistent launch
+    int *err = nullptr;             // status word shared by the members' Newton solves
+    int total_tasks = 0, total_pts = 0, ctas = 0;
+    std::vector<double> dt;         // time step of every member in the device arguments
+    std::vector<int> G;             // task length of every member in the device arguments
+    double alg_bytes[3] = {0, 0, 0};
+    cudaStream_t stream = nullptr, own = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::string last;
+    int sticky = 0;
+    bool timing = false;
+    std::vector<bgk_ctx::Ev> evs;
+    size_t nev = 0;
+};
+
+namespace {
+
+int bfail(bgk_batch *b, int code, const std::string &msg)
+{
+    b->last = msg;
+    return code;
+}
+
+#define BK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return bfail(b, BGK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Build and upload the members' stage and Newton arguments for time steps dt (one chunk per member:
+// stage 1 A -> slot 0, stage 2 slot 0 (+ A) -> slot 1, stage 3 slot 1 (+ A) -> A in place).
+int batch_upload(bgk_batch *b, const double *dt)
+{
+    const int n = b->n;
+    std::vector<StageArgs> sa(3 * (size_t)n);
+    std::vector<NewtonArgs> na(n);
+    std::vector<int> ts(n + 1, 0), ps(n + 1, 0);
+    for (int s = 0; s < 3; s++)
+        b->alg_bytes[s] = 0.0;
+    for (int q = 0; q < n; q++) {
+        bgk_ctx *c = b->probs[q];
+        const Chunk &ch = c->chunks[0];
+        float *Aq = c->fA, *s1 = c->pool, *s2 = c->pool + c->chunk_floats;
+        int64_t real = 0;
+        for (int v = 0; v < c->nslots; v++)
+            real += c->slotk[v] >= 0;
+        for (int st = 0; st < 3; st++) {
+            StageArgs A = stage_args(c, ch);
+            A.src = st == 0 ? Aq : (st == 1 ? s1 : s2);
+            A.fn = st == 0 ? nullptr : Aq;
+            A.dst = st == 0 ? s1 : (st == 1 ? s2 : Aq);
+            stage_coeffs(A, st, dt[q], c->tau);
+            sa[(size_t)st * n + q] = A;
+            b->alg_bytes[st] += (double)real * c->npts * sizeof(float) * (st == 0 ? 2 : 3);
+        }
+        NewtonArgs N = newton_args(c, 0);
+        N.err = b->err;
+        na[q] = N;
+        const int64_t t = ts[q] + (int64_t)stage1d_tasks(sa[q]);
+        const int64_t pt = ps[q] + c->npts;
+        if (t > INT32_MAX / 2 || pt > INT32_MAX / 2)
+            return bfail(b, BGK_EINVAL, "batch too large");
+        ts[q + 1] = (int)t;
+        ps[q + 1] = (int)pt;
+        b->dt[q] = dt[q];
+        b->G[q] = c->G;
+    }
+    b->total_tasks = ts[n];
+    b->total_pts = ps[n];
+    BK(cudaMemcpyAsync(b->d_args, sa.data(), sa.size() * sizeof(StageArgs), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_nargs, na.data(), na.size() * sizeof(NewtonArgs), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_task_start, ts.data(), ts.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_pt_start, ps.data(), ps.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
+    return BGK_OK;
+}
+
+void bev_begin(bgk_batch *b, int kind, double bytes)
+{
+    if (!b->timing)
+        return;
+    if (b->nev == b->evs.size()) {
+        bgk_ctx::Ev ev{};
+        cudaEventCreate(&ev.a);
+        cudaEventCreate(&ev.b);
+        b->evs.push_back(ev);
+    }
+    b->evs[b->nev].kind = kind;
+    b->evs[b->nev].bytes = bytes;
+    cudaEventRecord(b->evs[b->nev].a, b->stream);
+}
+
+void bev_end(bgk_batch *b)
+{
+    if (!b->timing)
+        return;
+    cudaEventRecord(b->evs[b->nev].b, b->stream);
+    b->nev++;
+}
+
+// One SSP-RK3 step of every member: per stage one persistent stage launch and one Newton launch.
+int batch_enqueue(bgk_batch *b, cudaStream_t s)
+{
+    for (int st = 0; st < 3; st++) {
+        bev_begin(b, 0, b->alg_bytes[st]);
+        BK(launch_stage1d_batch(b->d_args + (size_t)st * b->n, b->d_task_start, b->n, b->d_counter, b->ctas, s));
+        bev_end(b);
+        bev_begin(b, 1, 0.0);
+        BK(launch_newton_batch(b->d_nargs, b->d_pt_start, b->n, b->total_pts, s));
+        bev_end(b);
+    }
+    return BGK_OK;
+}
+
+int batch_status(bgk_batch *b)
+{
+    int e = 0;
+    BK(cudaStreamSynchronize(b->stream));
+    BK(cudaMemcpy(&e, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e)
+        for (bgk_ctx *c : b->probs)
+            c->sticky |= e;  // the members' states are no longer valid either
+    b->sticky |= e;
+    if (b->sticky & kErrDomain)
+        return bfail(b, BGK_EDOMAIN, "non-physical state (rho <= 0, theta <= 0 or NaN) met on the device");
+    if (b->sticky & kErrNewton)
+        return bfail(b, BGK_ENEWTON, "conservative-Maxwellian Newton solve did not converge at some point");
+    return BGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bgk_batch_last_error(const bgk_batch *b) { return b ? b->last.c_str() : "null batch"; }
+
+void bgk_batch_destroy(bgk_batch *b)
+{
+    if (!b)
+        return;
+    if (b->stream)
+        cudaStreamSynchronize(b->stream);
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    for (auto &ev : b->evs) {
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    if (b->ev)
+        cudaEventDestroy(b->ev);
+    void *bufs[] = {b->d_args, b->d_nargs, b->d_task_start, b->d_pt_start, b->d_counter, b->err};
+    for (void *p : bufs)
+        if (p)
+            cudaFree(p);
+    if (b->own)
+        cudaStreamDestroy(b->own);
+    delete b;
+}
+
+int bgk_batch_create(int n, bgk_ctx *const *probs, bgk_batch **out)
+{
+    if (!out)
+        return BGK_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !probs)
+        return BGK_EINVAL;
+    bgk_batch *b = new bgk_batch();
+    auto bail = [&](int code, const std::string &msg) {
+        fprintf(stderr, "bgk_batch_create: %s\n", msg.c_str());
+        bgk_batch_destroy(b);
+        return code;
+    };
+    std::vector<const bgk_ctx *> seen;
+    for (int q = 0; q < n; q++) {
+        bgk_ctx *c = probs[q];
+        if (!c)
+            return bail(BGK_EINVAL, "null member");
+        if (c->prec != BGK_FP32_SPLIT || c->dim != 1 || c->p > 3)
+            return bail(BGK_EINVAL, "members must be FP32-split line problems (dim = 1) with p <= 3");
+        if (c->chunks.size() != 1)
+            return bail(BGK_EINVAL, "members must be created with opts.chunks = 1");
+        if (c->sticky)
+            return bail(BGK_EINVAL, "a member holds a device error");
+        seen.push_back(c);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return bail(BGK_EINVAL, "a context appears twice");
+    b->n = n;
+    b->probs.assign(probs, probs + n);
+    b->dt.assign(n, -1.0);
+    b->G.assign(n, 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->d_args, 3 * (size_t)n * sizeof(StageArgs));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->d_nargs, (size_t)n * sizeof(NewtonArgs));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->d_task_start, (size_t)(n + 1) * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->d_pt_start, (size_t)(n + 1) * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->d_counter, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&b->err, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemset(b->err, 0, sizeof(int));
+    // the line operators of every degree present, for the constant table of the persistent launch
+    bool done[kMaxN1 + 1] = {false};
+    for (int q = 0; q < n && e == cudaSuccess; q++) {
+        const bgk_ctx *c = probs[q];
+        if (!done[c->N1])
+            e = set_batch_ops(c->N1, c->ops);
+        done[c->N1] = true;
+    }
+    if (e != cudaSuccess)
+        return bail(e == cudaErrorMemoryAllocation ? BGK_ENOMEM : BGK_ECUDA, cudaGetErrorString(e));
+    b->stream = b->own;
+    b->ctas = stage1d_batch_ctas();
+    *out = b;
+    return BGK_OK;
+}
+
+int bgk_batch_set_stream(bgk_batch *b, void *stream)
+{
+    if (!b)
+        return BGK_EINVAL;
+    b->stream = stream ? (cudaStream_t)stream : b->own;
+    return BGK_OK;
+}
+
+int bgk_batch_step(bgk_batch *b, const double *dt, int nsteps)
+{
+    if (!b || !dt || nsteps < 0)
+        return BGK_EINVAL;
+    for (int q = 0; q < b->n; q++)
+        if (!(dt[q] > 0.0) || !std::isfinite(dt[q]))
+            return bfail(b, BGK_EINVAL, "every time step must be positive and finite");
+    if (b->sticky)
+        return batch_status(b);
+    for (bgk_ctx *c : b->probs)
+        if (c->sticky)
+            return bfail(b, BGK_EINVAL, "a member holds a device error");
+    if (nsteps == 0)
+        return BGK_OK;
+    // the members' pending work (state set-up) comes first
+    for (bgk_ctx *c : b->probs) {
+        BK(cudaEventRecord(b->ev, c->stream));
+        BK(cudaStreamWaitEvent(b->stream, b->ev, 0));
+    }
+    bool stale = false;
+    for (int q = 0; q < b->n; q++)
+        stale = stale || b->dt[q] != dt[q] || b->G[q] != b->probs[q]->G;
+    if (stale) {
+        int rc = batch_upload(b, dt);
+        if (rc)
+            return rc;
+    }
+    if (b->timing) {
+        for (int k = 0; k < nsteps; k++) {
+            int rc = batch_enqueue(b, b->stream);
+            if (rc)
+                return rc;
+        }
+    } else {
+        if (!b->gexec) {  // the graph reads the device argument tables, so new time steps need no capture
+            cudaStream_t cap;
+            BK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(cap);
+                BK(e);
+            }
+            int rc = batch_enqueue(b, cap);
+            e = cudaStreamEndCapture(cap, &g);
+            cudaStreamDestroy(cap);
+            if (rc)
+                return rc;
+            BK(e);
+            e = cudaGraphInstantiate(&b->gexec, g, 0);
+            cudaGraphDestroy(g);
+            BK(e);
+        }
+        for (int k = 0; k < nsteps; k++)
+            BK(cudaGraphLaunch(b->gexec, b->stream));
+    }
+    // the members' later work (moments, their own steps) follows the batch
+    BK(cudaEventRecord(b->ev, b->stream));
+    for (bgk_ctx *c : b->probs)
+        BK(cudaStreamWaitEvent(c->stream, b->ev, 0));
+    return BGK_OK;
+}
+
+int bgk_batch_synchronize(bgk_batch *b)
+{
+    if (!b)
+        return BGK_EINVAL;
+    return batch_status(b);
+}
+
+int bgk_batch_autotune(bgk_batch *b)
+{
+    if (!b)
+        return BGK_EINVAL;
+    std::vector<double> dt(b->dt);
+    for (int q = 0; q < b->n; q++)
+        if (!(dt[q] > 0.0))
+            dt[q] = 0.1 * b->probs[q]->tau;  // any step: the timed stage's values are discarded
+    // classes of members with the same (degree, velocity grid)
+    std::vector<int> cls(b->n, -1);
+    std::vector<int> rep;
+    for (int q = 0; q < b->n; q++) {
+        const bgk_ctx *c = b->probs[q];
+        for (size_t k = 0; k < rep.size() && cls[q] < 0; k++) {
+            const bgk_ctx *r = b->probs[rep[k]];
+            if (r->p == c->p && r->nv[0] == c->nv[0] && r->nv[1] == c->nv[1] && r->nv[2] == c->nv[2])
+                cls[q] = (int)k;
+        }
+        if (cls[q] < 0) {
+            cls[q] = (int)rep.size();
+            rep.push_back(q);
+        }
+    }
+    cudaEvent_t e0, e1;
+    BK(cudaEventCreate(&e0));
+    BK(cudaEventCreate(&e1));
+    auto timed = [&](float &ms_out) -> int {
+        int rc = batch_upload(b, dt.data());
+        if (rc)
+            return rc;
+        float tot = 0.f;
+        for (int r = 0; r < 3; r++) {
+            // stage 2: reads slot 0 and f^n, writes slot 1 (f^n, the moments and equilibrium untouched)
+            BK(cudaEventRecord(e0, b->stream));
+            BK(launch_stage1d_batch(b->d_args + b->n, b->d_task_start, b->n, b->d_counter, b->ctas, b->stream));
+            BK(cudaEventRecord(e1, b->stream));
+            BK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BK(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0)
+                tot += ms;
+        }
+        ms_out = tot;
+        return BGK_OK;
+    };
+    for (bgk_ctx *c : b->probs) {
+        BK(cudaEventRecord(b->ev, c->stream));
+        BK(cudaStreamWaitEvent(b->stream, b->ev, 0));
+    }
+    for (size_t k = 0; k < rep.size(); k++) {
+        float best = 1e30f;
+        int bestG = b->probs[rep[k]]->G;
+        for (int G = kMinTuneG; G <= 16; G *= 2) {
+            for (int q = 0; q < b->n; q++)
+                if (cls[q] == (int)k)
+                    set_task_length(b->probs[q], G);
+            float ms = 0.f;
+            int rc = timed(ms);
+            if (rc)
+                return rc;
+            if (ms < best) {
+                best = ms;
+                bestG = G;
+            }
+        }
+        for (int q = 0; q < b->n; q++)
+            if (cls[q] == (int)k)
+                set_task_length(b->probs[q], bestG);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::fill(b->G.begin(), b->G.end(), 0);  // re-upload with the chosen lengths on the next step
+    return BGK_OK;
+}
+
+int bgk_batch_info(const bgk_batch *b, int64_t *npoints, int64_t *ndof, int64_t *tasks)
+{
+    if (!b)
+        return BGK_EINVAL;
+    int64_t np = 0, nd = 0, nt = 0;
+    for (const bgk_ctx *c : b->probs) {
+        np += c->npts;
+        nd += c->npts * c->nvel;
+        const int nEB = (c->E + kWarpsPerCta - 1) / kWarpsPerCta;
+        nt += (int64_t)nEB * ((c->chunks[0].nvt + c->G - 1) / c->G);
+    }
+    if (npoints)
+        *npoints = np;
+    if (ndof)
+        *ndof = nd;
+    if (tasks)
+        *tasks = nt;
+    return BGK_OK;
+}
+
+int bgk_batch_set_timing(bgk_batch *b, int on)
+{
+    if (!b)
+        return BGK_EINVAL;
+    b->timing = on != 0;
+    b->nev = 0;
+    return BGK_OK;
+}
+
+int bgk_batch_timing(bgk_batch *b, double *stage_ms, int64_t *stage_launches, double *newton_ms,
+                     int64_t *newton_launches, double *stage_alg_bytes)
+{
+    if (!b)
+        return BGK_EINVAL;
+    BK(cudaStreamSynchronize(b->stream));
+    double sm = 0, nm = 0, by = 0;
+    int64_t sl = 0, nl = 0;
+    for (size_t q = 0; q < b->nev; q++) {
+        float ms = 0.f;
+        BK(cudaEventElapsedTime(&ms, b->evs[q].a, b->evs[q].b));
+        if (b->evs[q].kind == 0) {
+            sm += ms;
+            sl++;
+            by += b->evs[q].bytes;
         } else {
             nm += ms;
             nl++;

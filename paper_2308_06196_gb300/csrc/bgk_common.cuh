@@ -16,6 +16,7 @@ constexpr int kWarp = 32;
 constexpr int kWarpsPerCta = 4;   // elements per CTA in the stage kernel
 constexpr int kMaxN1 = 8;         // nodes per direction (p <= 7)
 constexpr int kParamStride = 8;   // floats per point in the BGK parameter table
+constexpr float kExp2Magic = 12582912.0f;  // 1.5 * 2^23, the rounding constant of the stage kernels' 2^x
 
 // error bits of the device status word
 constexpr int kErrDomain = 1;
@@ -46,17 +47,25 @@ struct StageArgs {
     const float *src;    // f_s of this chunk: [nvt_chunk][E][NP][32]
     const float *fn;     // f^n of this chunk (same layout), null in stage 1
     float *dst;          // stage output of this chunk (may alias fn: in-place update of f^n)
-    const float *xi;     // [3][nslots] velocity components of every device slot
+    const float *mi;     // [3][nslots] centred grid index m_d = 2 k_d - (n_d - 1) of every device slot
+                         // (an integer, exact in FP32): xi_d = vc[d] + vs[d] m_d
     const float *wpsi;   // [nvt][5][32] w * (1, xi, |xi|^2/2), 0 on padded slots
     const float *gmask;  // [nslots] 1 for real velocities, 0 for padding
     const float *ghost;  // [6][nslots] Dirichlet ghost values (sampled Maxwellian), or null
-    const float *param;  // [n_x][8] BGK exponent b0..b4 of every point: g = exp2(b0 + b.xi + b4|xi|^2)
+    const float *param;  // [n_x][8] BGK exponent of every point in the grid index m:
+                         //   g = 2^j exp2(a + sum_d b_d m_d + e),  j integer,
+                         // (a, b_x, b_y, b_z, p4, p5, p6, kExp2Magic + j) with, when viso (one spacing
+                         // on all axes), e = p4 |m|^2 + p5 |m|^2 (p4 + p5 = q in two FP32 parts, p6 = 0),
+                         // otherwise e = p4 m_x^2 + p5 m_y^2 + p6 m_z^2
     const float *rhow;   // [6][nfmax][N1^2] diffuse-wall density per wall face point, or null
     const float *fpar;   // [n_x][8] body-force source polynomial q0..q4: S = g (q0 + q.xi + q4|xi|^2), or null
     int nfmax;           // face elements per face slot of rhow
+    float vc[3], vs[3];  // velocity grid centre and half spacing per axis
+    int viso;            // 1: one velocity spacing on all axes
     float *partial;      // [ngroups_total][5][n_x] moment partial sums of the stage output
     Ops ops;
     Mesh mesh;
+    int n1;              // nodes per direction (p + 1)
     int vt0;             // first global tile of the chunk
     int nvt;             // tiles in the chunk
     int G;               // tiles per warp task
@@ -65,6 +74,9 @@ struct StageArgs {
     int npts;            // n_x
     float an, b;         // Shu-Osher coefficients: out = an f^n + b (f_s + dt L(f_s))
     float dt, inv_tau;
+    float kb, kg;        // b (1 - dt / tau) and b dt / tau: the weights of f_s and of the Maxwellian.
+                         // Rounded so that an + b = 1 and kb + kg = b hold exactly in FP32, so a state
+                         // equal to f^n and to its Maxwellian is kept up to unbiased rounding.
 };
 
 struct NewtonArgs {
@@ -137,6 +149,32 @@ struct WallArgs {
     double lm[kMaxN1], lp[kMaxN1];
     void *rhow;            // out: float or double [6][nfmax][N1^2]
 };
+
+// Moment weights of the FP32 stage kernels in the grid-index basis. With W = w / (dv_x dv_y dv_z)
+// (1, 1/2, 1/4 or 1/8 on the trapezoid grid) and m_d = 2 k_d - (n_d - 1) the centred index
+// (xi_d = c_d + s_d m_d, s_d = dv_d / 2), the kernels accumulate
+//   mu = sum_k W_k (1, m_x, m_y, m_z, r_x m_x^2 + r_y m_y^2 + r_z m_z^2) f_k,  r_d = (s_d / s_x)^2 in FP32,
+// whose weights are exact FP32 numbers (r_d = 1 on grids with one spacing), so the only FP32 error of
+// the moments is the summation's. index_to_moments turns mu into Q = sum_k w_k psi_k f_k (Eq. 2).
+__host__ __device__ inline float index_r(double dv_d, double dv_x)
+{
+    return (float)((dv_d / dv_x) * (dv_d / dv_x));
+}
+
+__host__ __device__ inline void index_to_moments(const double (&mu)[5], const double v0[3], const double dv[3],
+                                                 const int n[3], double (&Q)[5])
+{
+    const double V = dv[0] * dv[1] * dv[2], s0 = 0.5 * dv[0];
+    double cs = 0.0, cm = 0.0;
+    Q[0] = V * mu[0];
+    for (int d = 0; d < 3; d++) {
+        const double sd = 0.5 * dv[d], cd = v0[d] + (n[d] - 1) * sd;
+        Q[1 + d] = V * (cd * mu[0] + sd * mu[1 + d]);
+        cs += cd * cd;
+        cm += cd * sd * mu[1 + d];
+    }
+    Q[4] = 0.5 * V * (cs * mu[0] + 2.0 * cm + s0 * s0 * mu[4]);
+}
 
 // Index of the face element of element (ec) on face direction d: the two other coordinates.
 __host__ __device__ inline int face_elem(const Mesh &m, const int ec[3], int d)

@@ -36,12 +36,11 @@ static __device__ __align__(256) float g_scratch[kScratchFloats];
 std::mutex g_mu;
 float *g_ptr[256] = {nullptr};
 
-// Partial moments sum_k w_k psi_k f[pt][k] over velocity group blockIdx.y of point blockIdx.x.
-// f is in the host order [npts][N_v] with k = kx + nx (ky + ny kz); the uniform grid and its
-// trapezoid weights are recomputed from (v0, dv, n), psi = (1, xi, |xi|^2 / 2).
+// Partial grid-index moments sum_k W_k (1, m, sum_d r_d m_d^2) f[pt][k] (the basis of the Newton
+// kernel's input, exact FP32 weights) over velocity group blockIdx.y of point blockIdx.x. f is in the
+// host order [npts][N_v] with k = kx + nx (ky + ny kz).
 __global__ void __launch_bounds__(256) k_noalloc_partials(const float *__restrict__ f, int npts, int nx, int ny,
-                                                          int nz, double v0x, double v0y, double v0z, double dvx,
-                                                          double dvy, double dvz, float *partial)
+                                                          int nz, float ry, float rz, float *partial)
 {
     const int pt = blockIdx.x, g = blockIdx.y;
     const int64_t nvel = (int64_t)nx * ny * nz;
@@ -50,15 +49,15 @@ __global__ void __launch_bounds__(256) k_noalloc_partials(const float *__restric
     float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         const int kx = (int)(k % nx), ky = (int)((k / nx) % ny), kz = (int)(k / ((int64_t)nx * ny));
-        const double x = v0x + kx * dvx, y = v0y + ky * dvy, z = v0z + kz * dvz;
-        const double w = ((kx == 0 || kx == nx - 1) ? 0.5 * dvx : dvx) * ((ky == 0 || ky == ny - 1) ? 0.5 * dvy : dvy) *
-                         ((kz == 0 || kz == nz - 1) ? 0.5 * dvz : dvz);
+        const float W = ((kx == 0 || kx == nx - 1) ? 0.5f : 1.f) * ((ky == 0 || ky == ny - 1) ? 0.5f : 1.f) *
+                        ((kz == 0 || kz == nz - 1) ? 0.5f : 1.f);
+        const float mx = (float)(2 * kx - (nx - 1)), my = (float)(2 * ky - (ny - 1)), mz = (float)(2 * kz - (nz - 1));
         const float v = __ldg(f + (int64_t)pt * nvel + k);
-        m[0] = fmaf((float)w, v, m[0]);
-        m[1] = fmaf((float)(w * x), v, m[1]);
-        m[2] = fmaf((float)(w * y), v, m[2]);
-        m[3] = fmaf((float)(w * z), v, m[3]);
-        m[4] = fmaf((float)(w * 0.5 * (x * x + y * y + z * z)), v, m[4]);
+        m[0] = fmaf(W, v, m[0]);
+        m[1] = fmaf(W * mx, v, m[1]);
+        m[2] = fmaf(W * my, v, m[2]);
+        m[3] = fmaf(W * mz, v, m[3]);
+        m[4] = fmaf(W * (mx * mx + ry * (my * my) + rz * (mz * mz)), v, m[4]);
     }
     __shared__ float red[8][5];
 #pragma unroll
@@ -133,8 +132,8 @@ extern "C" int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk
         dv[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
     }
     dim3 grid((unsigned)npts, (unsigned)ngroups);
-    k_noalloc_partials<<<grid, 256, 0, s>>>(d_f, (int)npts, vg->n[0], vg->n[1], vg->n[2], v0[0], v0[1], v0[2], dv[0],
-                                            dv[1], dv[2], partial);
+    k_noalloc_partials<<<grid, 256, 0, s>>>(d_f, (int)npts, vg->n[0], vg->n[1], vg->n[2], index_r(dv[1], dv[0]),
+                                            index_r(dv[2], dv[0]), partial);
     if (cudaGetLastError() != cudaSuccess)
         return BGK_ECUDA;
     NewtonArgs N{};

@@ -1,8 +1,9 @@
 // k_newton.cu -- per-point discretely-conservative Maxwellian (Sec. 2.1, text after Eq. 13).
 //
 // For every spatial point the kernel
-//   1. sums the FP32 partial moments of all velocity tasks exactly (double-float accumulation),
-//      giving Q = sum_k w_k psi_k f_k in FP64 (Eq. 2 with the trapezoid operator of Eq. 12),
+//   1. sums the FP32 partial moments of all velocity tasks exactly (double-float accumulation) and
+//      maps these grid-index moments to Q = sum_k w_k psi_k f_k in FP64 (Eq. 2 with the trapezoid
+//      operator of Eq. 12),
 //   2. finds the Maxwellian g at a perturbed state whose discrete moments equal Q. On the tensor
 //      velocity grid with tensor trapezoid weights, g factors into 1-D Gaussians, so every moment
 //      and every Jacobian entry sum_k w g psi psi^T is a product of 1-D sums S_d^m = sum_k w c^m A
@@ -14,7 +15,8 @@
 //          product recurrence outward from their peak: three FP64 exponentials per axis) and
 //          corrected with the FP32 Jacobian, which contracts the error by ~1e-6 per refinement.
 //   3. writes Q, the perturbed state (rho', U', theta') used as the next warm start, and the FP32
-//      exponent g = exp2(b0 + b . xi + b4 |xi|^2) that the stage kernel evaluates per velocity.
+//      exponent g = exp2(a + sum_d (b_d m_d + q_d m_d^2)) in the centred grid index m of the velocity
+//      (exact in FP32), which the stage kernel evaluates per velocity.
 // Points with rho <= 0, theta <= 0 or NaN moments set the domain bit of the status word; a Newton
 // correction that stays large sets the Newton bit. No thread waits on another.
 #include "bgk_common.cuh"
@@ -193,11 +195,8 @@ __device__ __forceinline__ void sums64(double ad, double beta, double c0, double
     }
 }
 
-__global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
+__device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
 {
-    const int pt = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pt >= A.npts)
-        return;
 
     // 1. moments: exact sum of the FP32 partials (or the FP64 moments of the all-FP64 form)
     double Q[5];
@@ -217,6 +216,10 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
         }
         Q[c] = (double)hi + (double)lo;
     }
+    if (!A.Qin) {  // the FP32 kernels sum in the grid-index basis
+        const double mu[5] = {Q[0], Q[1], Q[2], Q[3], Q[4]};
+        index_to_moments(mu, A.v0, A.dv, A.n, Q);
+    }
 #pragma unroll
     for (int c = 0; c < 5; c++)
         A.Q[(int64_t)pt * 5 + c] = Q[c];
@@ -228,7 +231,9 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
     if (!(rho > 0.0) || !(thc > 0.0) || !isfinite(rho) || !isfinite(thc)) {
         atomicOr(A.err, kErrDomain);
         par[0] = -1e30f;  // g = 0 at this point
-        par[1] = par[2] = par[3] = par[4] = 0.f;
+        for (int c = 1; c < kParamStride; c++)
+            par[c] = 0.f;
+        par[7] = kExp2Magic;
         if (A.param64)
             for (int c = 0; c < 5; c++)
                 A.param64[(int64_t)pt * 5 + c] = 0.0;
@@ -368,14 +373,38 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
     pp[2] = Up[1];
     pp[3] = Up[2];
     pp[4] = thp;
-    // ln g = lnC - |xi - U'|^2 / (2 theta') = lnC - |U'|^2/(2 theta') + U'.xi / theta' - |xi|^2 / (2 theta')
+    // stage-kernel exponent in the centred grid index m (xi_d = c_d + s_d m_d, c_d the grid centre,
+    // s_d half the spacing): log2 g = L2E (lnC - |xi - U'|^2 / (2 theta'))
+    //   = A + sum_d b_d m_d + sum_d q_d m_d^2, e_d = c_d - U'_d,
+    //   A = L2E (lnC - |e|^2 / (2 theta')), b_d = -L2E e_d s_d / theta', q_d = -L2E s_d^2 / (2 theta').
+    // The index is exact in FP32, so the kernel evaluates the Maxwellian of the exact discrete velocity
+    // set. A = j + a with j = rint(A) carried exactly in the rounding constant of the kernel's 2^x and
+    // a in [-1/2, 1/2]; on grids with one spacing q is written as two FP32 parts. Left in FP32, the
+    // roundings of A and q would scale every g of the point alike (a moment error near 1e-7 per
+    // solve, which the relaxation accumulates); split, they are below 1e-8.
     const double L2E = 1.4426950408889634;
     const double it2 = 1.0 / thp;
-    par[0] = (float)(L2E * (lnC - 0.5 * (Up[0] * Up[0] + Up[1] * Up[1] + Up[2] * Up[2]) * it2));
-    par[1] = (float)(L2E * Up[0] * it2);
-    par[2] = (float)(L2E * Up[1] * it2);
-    par[3] = (float)(L2E * Up[2] * it2);
-    par[4] = (float)(-0.5 * L2E * it2);
+    double e2 = 0.0;
+    for (int d = 0; d < 3; d++) {
+        const double sd = 0.5 * A.dv[d];
+        const double ed = A.v0[d] + (A.n[d] - 1) * sd - Up[d];
+        e2 += ed * ed;
+        par[1 + d] = (float)(-L2E * ed * sd * it2);
+    }
+    const double Aexp = L2E * (lnC - 0.5 * e2 * it2);
+    const double j = fmin(20.0, fmax(-20.0, rint(Aexp)));
+    par[0] = (float)(Aexp - j);
+    if (A.dv[0] == A.dv[1] && A.dv[0] == A.dv[2]) {
+        const double q = -0.5 * L2E * (0.25 * A.dv[0] * A.dv[0]) * it2;
+        const float qh = (float)q;
+        par[4] = qh;
+        par[5] = (float)(q - (double)qh);
+        par[6] = 0.f;
+    } else {
+        for (int d = 0; d < 3; d++)
+            par[4 + d] = (float)(-0.5 * L2E * (0.25 * A.dv[d] * A.dv[d]) * it2);
+    }
+    par[7] = kExp2Magic + (float)j;
     // body force: source S = g (beta . psi~) with M[g psi~ psi~^T] beta = M[S psi~] =
     // (0, rho F / s, rho (U - V) . F / s^2), whose raw moments are (0, rho F, rho U . F); written as
     // the polynomial q0 + q . xi + q4 |xi|^2 in the raw velocity
@@ -418,6 +447,40 @@ __global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
         p64[3] = Up[2];
         p64[4] = 0.5 * it2;
     }
+}
+
+__global__ void __launch_bounds__(128) k_newton(const NewtonArgs A)
+{
+    const int pt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pt < A.npts)
+        newton_point(A, pt);
+}
+
+// Batched solve over the points of many independent problems: thread per point, the problem found
+// by a binary search over the point prefix sums pt_start[0..n].
+__global__ void __launch_bounds__(128) k_newton_batch(const NewtonArgs *__restrict__ args,
+                                                      const int *__restrict__ pt_start, int n)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= pt_start[n])
+        return;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pt_start[mid] <= g)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    newton_point(args[lo], g - pt_start[lo]);
+}
+
+cudaError_t launch_newton_batch(const NewtonArgs *d_args, const int *d_pt_start, int n, int total_pts,
+                                cudaStream_t s)
+{
+    const int threads = 128;
+    k_newton_batch<<<(total_pts + threads - 1) / threads, threads, 0, s>>>(d_args, d_pt_start, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s)

@@ -34,8 +34,9 @@ struct Stage3Smem {
 
 // OCT in 0..7: every tile of the launch lies in that sign octant (bit d set: xi_d >= 0, the upwind
 // neighbour in direction d is on the low side); OCT = 8: the octant is read per tile.
-// GEN = 0: every face periodic and no body force (the lean form); GEN = 1: Dirichlet and diffuse-wall
-// faces and the body-force source.
+// GEN = 0: every face periodic, no body force and one velocity spacing on all axes (the lean form;
+// the Maxwellian exponent needs only the sum of the squared grid indices); GEN = 1: Dirichlet and
+// diffuse-wall faces, the body-force source and per-axis spacings.
 template <int N1, int MODE, int OCT, int GEN>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
 {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
 #pragma unroll
         for (int c = 0; c < 5; c++)
             ms[h][c] = 0ull;
-    const float kb = A.b * (1.f - A.dt * A.inv_tau);
+    const float kb = A.kb;
     const float bdt = A.b * A.dt;
 
     // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
@@ -115,12 +116,12 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             cp_wait<0>();
         }
         __syncwarp();
-        const float x0 = __ldg(A.xi + slot), x1 = __ldg(A.xi + A.nslots + slot), x2 = __ldg(A.xi + 2 * A.nslots + slot);
+        const float m0 = __ldg(A.mi + slot), m1 = __ldg(A.mi + A.nslots + slot), m2 = __ldg(A.mi + 2 * A.nslots + slot);
+        const float x0 = fmaf(A.vs[0], m0, A.vc[0]), x1 = fmaf(A.vs[1], m1, A.vc[1]), x2 = fmaf(A.vs[2], m2, A.vc[2]);
         float f[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++)
             f[q] = sm.tile[b][q + NQ * w][lane];
-        float o[NQ];
         if (MODE == 0) {
             const bool l0 = OCT < 8 ? (OCT & 1) != 0 : x0 >= 0.f;
             const bool l1 = OCT < 8 ? (OCT & 2) != 0 : x1 >= 0.f;
@@ -243,15 +244,21 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             __syncthreads();  // B2: z-sums complete
             // BGK source towards the conservative Maxwellian, Shu-Osher combination, store
             const float gm = __ldg(A.gmask + slot);
-            const float cg = bdt * A.inv_tau * gm, cf = bdt * gm;
+            const float cg = A.kg * gm, cf = bdt * gm;
             const float xs = x0 * x0 + x1 * x1 + x2 * x2;
+            // squared indices (exact); the lean form has one spacing on every axis and needs their sum
+            const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
+            const float u0 = (!GEN || A.viso) ? mms : mm0, u1 = (!GEN || A.viso) ? mms : mm1;
+            const float u2 = (!GEN || A.viso) ? 0.f : mm2;
             float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
                 const int i = q + NQ * w;
                 const float4 pb = *reinterpret_cast<const float4 *>(&sm.par[i][0]);
-                const float b4 = sm.par[i][4];
-                const float ex = fmaf(b4, xs, fmaf(pb.w, x2, fmaf(pb.z, x1, fmaf(pb.y, x0, pb.x))));
+                const float4 pq = *reinterpret_cast<const float4 *>(&sm.par[i][4]);
+                const float lin = fmaf(pb.w, m2, fmaf(pb.z, m1, fmaf(pb.y, m0, pb.x)));
+                const float ex = GEN ? fmaf(pq.x, u0, fmaf(pq.y, u1, fmaf(pq.z, u2, lin)))
+                                     : fmaf(pq.x, mms, fmaf(pq.y, mms, lin));
                 const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
                 float gc = cg;
                 if (GEN && A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
@@ -259,8 +266,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                     const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
                     gc = fmaf(cf, qv, cg);
                 }
-                o[q] = fmaf(gc, ex2(ex), a);
-                __stcs(dst + i * kWarp, o[q]);
+                const float o = fmaf(gc, exp2_fp32(ex, pq.w), a);
+                __stcs(dst + i * kWarp, o);
+                sm.wf[w][q][lane] = o;  // for the moments below (this warp's own rows)
             }
         } else {
             __syncthreads();  // B1 (same barrier sequence in both modes)
@@ -272,12 +280,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             __syncthreads();  // B2
 #pragma unroll
             for (int q = 0; q < NQ; q++)
-                o[q] = f[q];
+                sm.wf[w][q][lane] = f[q];
         }
         // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values
-#pragma unroll
-        for (int q = 0; q < NQ; q++)
-            sm.wf[w][q][lane] = o[q];
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < 8; k += 4) {
@@ -365,7 +370,8 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
 {
     if (mode == 1)
         return launch3<N1, 1, 8, 0>(A, s);
-    bool general = A.fpar != nullptr;
+    // the lean form: periodic faces, no force, one velocity spacing on all axes
+    bool general = A.fpar != nullptr || !A.viso;
     for (int f = 0; f < 6; f++)
         general = general || A.mesh.bc[f] != 0;
     return general ? launch3_oct<N1, 1>(A, oct, s) : launch3_oct<N1, 0>(A, oct, s);

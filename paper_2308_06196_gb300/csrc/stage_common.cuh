@@ -63,8 +63,6 @@ __device__ __forceinline__ void line_sums(float (&s)[N1], const float (&fl)[N1],
     }
 }
 
-// Upwind trace of one neighbour line v (difference form, exact for a constant state): a left
-// neighbour is evaluated at its +1 end (lp), a right neighbour at its -1 end (lm).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -77,14 +75,33 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N));
 }
 
-// 2^x on the special-function unit (inputs below -126 flush the result to 0)
-__device__ __forceinline__ float ex2(float x)
+// 2^(x + j) in FP32 arithmetic for an integer j carried in the rounding constant kmagic = 1.5 * 2^23 + j
+// (the BGK Maxwellian: j is the integer part of the point's exponent, x the velocity-dependent rest,
+// so the FP32 rounding of x is relative to a small number). x = n + r with n = rint(x) (the low bits of
+// x + kmagic hold n + j) and |r| <= 1/2; 2^r by a degree-6 polynomial fitted by weighted least squares
+// to 2^r on [-1/2, 1/2] in FP64 (coefficients from exp2_fit.py, rounded to FP32); 2^(n + j) added to
+// the exponent field. Relative error below 8e-8, with a mean over any unit interval of x below 1e-9:
+// the mean matters, because every relaxation step moves the moments of f by (dt / tau) times the mean
+// error of g, and the special-function unit's 2^x has a mean error near -5e-8. x is clamped at -100
+// (g below 2^(j - 100), of no weight); |j| <= 20 keeps n + j inside the normal range.
+__device__ __forceinline__ float exp2_fp32(float x, float kmagic)
 {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
+    x = fmaxf(x, -100.0f);
+    const float t = __fadd_rn(x, kmagic);
+    const float r = __fsub_rn(x, __fsub_rn(t, kmagic));
+    float p = 1.533757750e-04f;
+    p = fmaf(p, r, 1.339985989e-03f);
+    p = fmaf(p, r, 9.618519805e-03f);
+    p = fmaf(p, r, 5.550329015e-02f);
+    p = fmaf(p, r, 2.402264625e-01f);
+    p = fmaf(p, r, 6.931471825e-01f);
+    p = fmaf(p, r, 1.0f);
+    // the low bits of t hold n + j (two's complement); shifting them into the exponent field scales
+    return __int_as_float(__float_as_int(p) + (__float_as_int(t) << 23));
 }
 
+// Upwind trace of one neighbour line v (difference form, exact for a constant state): a left
+// neighbour is evaluated at its +1 end (lp), a right neighbour at its -1 end (lm).
 template <int N1, bool LEFT>
 __device__ __forceinline__ float trace_line(const float (&v)[N1], const Ops &op)
 {

@@ -31,6 +31,11 @@ CONFIGS = {
                     bc=((PERIODIC, PERIODIC), (WALL, WALL), (PERIODIC, PERIODIC)),
                     bc_state=(((0,) * 5, (0,) * 5), ((0, 0, 0, 0, 1.0), (0, 0, 0, 0, 1.0)), ((0,) * 5, (0,) * 5)),
                     force=(0.01, 0.0, 0.0)),
+    # ensemble of independent 1-D Sod shock tubes on [0, 1] (interface at x = 1/2, gas at rest, Dirichlet
+    # ends), drawn from one seed: elements U{16..128}, p U{2, 3}, velocity grid N^3 on [-8, 8]^3 with
+    # N in {12, 16, 24, 32}, (rho, T) of each side U[0.125, 1] x U[0.8, 1.25], tau log-uniform [1e-4, 1e-1]
+    "sod_ensemble": dict(members=256, seed=0, elements=(16, 128), degrees=(2, 3), nvs=(12, 16, 24, 32), vmax=8.0,
+                         rho=(0.125, 1.0), temp=(0.8, 1.25), tau=(1e-4, 1e-1), cfl=0.1, steps=20),
 }
 
 
@@ -75,6 +80,38 @@ def prim_channel(x: np.ndarray) -> np.ndarray:
     P = np.zeros((len(x), 5))
     P[:, 0] = 1.0
     P[:, 4] = 1.0
+    return P
+
+
+def sod_members(members: int = 256, seed: int = 0, elements=(16, 128), degrees=(2, 3), nvs=(12, 16, 24, 32),
+                vmax: float = 8.0, rho=(0.125, 1.0), temp=(0.8, 1.25), tau=(1e-4, 1e-1), **_) -> list:
+    """The seeded Sod ensemble: one dict per member with the Solver/Problem arguments (mesh_kwargs
+    form plus bc, bc_state) and its left/right states. Draw order per member: E, p, N, rho_L, T_L,
+    rho_R, T_R, log10 tau."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(members):
+        E = int(rng.integers(elements[0], elements[1] + 1))
+        p = int(rng.integers(degrees[0], degrees[1] + 1))
+        N = int(nvs[int(rng.integers(0, len(nvs)))])
+        rl, tl = rng.uniform(*rho), rng.uniform(*temp)
+        rr, tr = rng.uniform(*rho), rng.uniform(*temp)
+        t = 10.0 ** rng.uniform(math.log10(tau[0]), math.log10(tau[1]))
+        out.append(dict(dim=1, nelem=(E,), lo=(0.0,), hi=(1.0,), p=p, nv=(N, N, N), vlo=(-vmax,) * 3,
+                        vhi=(vmax,) * 3, tau=float(t),
+                        bc=((DIRICHLET, DIRICHLET), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC)),
+                        bc_state=(((rl, 0.0, 0.0, 0.0, tl), (rr, 0.0, 0.0, 0.0, tr)), ((0,) * 5, (0,) * 5),
+                                  ((0,) * 5, (0,) * 5)),
+                        left=(rl, tl), right=(rr, tr)))
+    return out
+
+
+def prim_sod(x: np.ndarray, left, right) -> np.ndarray:
+    """Gas at rest with (rho, T) = left for x < 1/2 and right otherwise."""
+    P = np.zeros((len(x), 5))
+    L = x[:, 0] < 0.5
+    P[:, 0] = np.where(L, left[0], right[0])
+    P[:, 4] = np.where(L, left[1], right[1])
     return P
 
 
