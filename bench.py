@@ -144,7 +144,7 @@ def run_oracle(steps: int, warmup: int):
     return dof * 3 * steps / sec, sec / steps, cores, dof, c
 
 
-def bench_batch(steps: int, warmup: int, stream, torch) -> dict:
+def bench_batch(steps: int, warmup: int, stream, torch, members: int = 0) -> dict:
     """The ensemble of independent 1-D Sod tubes (uneven mesh, degree and velocity grid) in one batch:
     one persistent stage launch and one Newton launch per RK stage, the step under a CUDA graph, tile
     lengths from the batch autotuner; then the same members stepped one after another through their
@@ -152,6 +152,8 @@ def bench_batch(steps: int, warmup: int, stream, torch) -> dict:
     from paper_2308_06196_gb300.bgk import Batch, Solver
 
     cb = W.config("sod_ensemble")
+    if members:
+        cb["members"] = members
     members = W.sod_members(**cb)
     sol = []
     for m in members:
@@ -214,6 +216,8 @@ def main():
                     help="steps of the plain all-FP64 form timed for the comparison (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="steps of the batched Sod ensemble (0: skip)")
+    ap.add_argument("--batch-members", type=int, default=0,
+                    help="members of the Sod ensemble (default: the workload's 256); smaller for profiling")
     ap.add_argument("--elements", type=int, default=0,
                     help="elements per direction (default: the workload's 16); smaller cases for profiling")
     args = ap.parse_args()
@@ -355,7 +359,7 @@ def main():
     batch = None
     if args.batch_steps > 0:
         s.close()  # the ensemble's own buffers replace the Taylor-Green ones
-        batch = bench_batch(args.batch_steps, warmup, stream, torch)
+        batch = bench_batch(args.batch_steps, warmup, stream, torch, args.batch_members)
 
     ms_t = torch.tensor([ms, graph_ms, e2e_ms], dtype=torch.float64, device="cuda")
     if dist:

@@ -171,12 +171,14 @@ struct bgk_ctx {
     // velocity plan
     int nvt = 0, nslots = 0, G = 1, ngroups = 0, max_groups = 0;
     std::vector<int> slotk;
+    std::vector<unsigned char> toct_h;  // sign octant of every tile
     std::vector<Chunk> chunks;
     int64_t chunk_floats = 0;  // floats per pool slot
     // device buffers
     float *fA = nullptr, *pool = nullptr;
     float *xi = nullptr, *mi = nullptr, *wpsi = nullptr, *gmask = nullptr, *ghost = nullptr;
     int *slotk_d = nullptr;
+    unsigned char *toct = nullptr;
     float *partial = nullptr, *param = nullptr;
     // all-FP64 form
     int prec = BGK_FP32_SPLIT;
@@ -246,6 +248,7 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
 {
     StageArgs A{};
     A.mi = c->mi;
+    A.toct = c->toct;
     for (int d = 0; d < 3; d++) {
         A.vc[d] = (float)(c->vlo[d] + 0.5 * (c->nv[d] - 1) * c->dv[d]);
         A.vs[d] = (float)(0.5 * c->dv[d]);
@@ -569,7 +572,7 @@ void bgk_destroy(bgk_ctx *c)
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
     }
-    void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
+    void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
                     c->fpar64, c->w64};
@@ -680,6 +683,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         while (c->slotk.size() % kWarp)
             c->slotk.push_back(-1);
         ch.nvt = (int)(c->slotk.size() / kWarp) - ch.vt0;
+        c->toct_h.insert(c->toct_h.end(), ch.nvt, (unsigned char)o);
         c->chunks.push_back(ch);
     }
     c->nvt = (int)(c->slotk.size() / kWarp);
@@ -751,6 +755,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     }
     AL(c->xi, 3 * c->nslots);
     AL(c->mi, 3 * c->nslots);
+    AL(c->toct, c->nvt);
     AL(c->wpsi, 5 * c->nslots);
     AL(c->gmask, c->nslots);
     AL(c->ghost, 6 * c->nslots);
@@ -838,6 +843,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         (c->w64 && (rc = cudaMemcpy(c->w64, w64h.data(), w64h.size() * 8, cudaMemcpyHostToDevice))) ||
         (rc = cudaMemcpy(c->xi, xi.data(), xi.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->mi, mi.data(), mi.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemcpy(c->toct, c->toct_h.data(), c->toct_h.size(), cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->wpsi, wpsi.data(), wpsi.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->gmask, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->ghost, gh.data(), gh.size() * 4, cudaMemcpyHostToDevice)) ||

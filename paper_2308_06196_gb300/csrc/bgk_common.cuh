@@ -51,6 +51,7 @@ struct StageArgs {
                          // (an integer, exact in FP32): xi_d = vc[d] + vs[d] m_d
     const float *wpsi;   // [nvt][5][32] w * (1, xi, |xi|^2/2), 0 on padded slots
     const float *gmask;  // [nslots] 1 for real velocities, 0 for padding
+    const unsigned char *toct;  // [nvt] sign octant of every tile (bit d: xi_d >= 0)
     const float *ghost;  // [6][nslots] Dirichlet ghost values (sampled Maxwellian), or null
     const float *param;  // [n_x][8] BGK exponent of every point in the grid index m:
                          //   g = 2^j exp2(a + sum_d b_d m_d + e),  j integer,

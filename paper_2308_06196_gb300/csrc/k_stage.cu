@@ -3,9 +3,9 @@
 //
 // One task = a block of kWarpsPerCta consecutive elements x a run of G velocity tiles (32 velocities
 // of one sign octant each); warp w of the CTA takes element w of the block. Lane l owns velocity l of
-// the tile and keeps the p+1 nodes of its element in registers. Per tile the warp
-//   1. loads f_s and f^n of its element (coalesced 128-byte lines, one per node; the next tile's
-//      values are prefetched while the current one is computed),
+// the tile. The CTA streams its tiles through a ring of shared slots with cp.async, several tiles
+// ahead. Per tile the warp
+//   1. reads f_s and f^n of its element from the slot (staged as coalesced 128-byte rows),
 //   2. adds the FR advection residual (Sec. 2.1, Eqs. 7-9): it reads the upwind neighbour element's
 //      line (same tile) and interpolates the neighbour's trace at the shared face, the interior trace
 //      being folded into the merged operator; a Dirichlet end supplies the sampled ghost value,
@@ -45,10 +45,43 @@ __device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane)
     }
 }
 
-// One task of the line-element stage. MODE 0: full stage. MODE 1: moments of src only (no advection,
-// no store). op: the FR operators of degree N1 - 1.
+constexpr int kLineDepth = 4;  // tiles in flight per CTA in the line-element stage
+
+// Shared staging of one tile of the line-element stage: f_s and f^n of the CTA's block of elements,
+// the upwind neighbour element just outside the block, and the tile's velocity tables.
+template <int N1>
+struct alignas(16) LineSlot {
+    float fs[kWarpsPerCta][N1][kWarp];
+    float fn[kWarpsPerCta][N1][kWarp];
+    float nb[N1][kWarp];
+    float mi[3][kWarp];
+    float wp[5][kWarp];
+    float gm[kWarp];
+};
+template <int N1>
+struct alignas(16) LineSmem {  // cp.async and the 16-byte parameter loads need 16-byte alignment
+    LineSlot<N1> s[kLineDepth];
+    // BGK exponents of the block's nodes by element and node pair, [element][pair][param][node of the
+    // pair], so that one 16-byte load gives two parameters of both nodes (an odd last pair repeats)
+    float par[kWarpsPerCta][(N1 + 1) / 2][kParamStride][2];
+};
+
+// Asynchronous copy of `rows` 128-byte rows from g to s by the CTA's threads (16 bytes per copy).
+__device__ __forceinline__ void copy_rows(float *s, const float *g, int rows)
+{
+    const int n = rows * (kWarp / 4);
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        cp_async16(s + 4 * k, g + 4 * k);
+}
+
+// One task of the line-element stage: a block of kWarpsPerCta consecutive elements (warp w takes
+// element eb + w) x a run of G tiles. The CTA streams the tiles through a kLineDepth-deep ring of
+// shared slots (cp.async, kLineDepth - 1 tiles ahead), so every warp reads its element, its upwind
+// neighbour (a sibling's element, or the staged outside neighbour) and the velocity tables from
+// shared memory. MODE 0: full stage. MODE 1: moments of src only (no advection, no store).
+// op: the FR operators of degree N1 - 1. Every thread of the CTA must call it (barriers).
 template <int N1, int MODE>
-__device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task, const Ops &op)
+__device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task, const Ops &op, LineSmem<N1> &sm)
 {
     constexpr int NP = N1;
     constexpr int NQ = (NP + 1) / 2;  // packed node pairs
@@ -57,32 +90,45 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
     const int E = A.mesh.nelem;
     const int nEB = (E + kWarpsPerCta - 1) / kWarpsPerCta;
     const int gl = task / nEB;
-    const int e = (task % nEB) * kWarpsPerCta + wid;
-    if (e >= E)
-        return;  // whole warp; the task uses no CTA-wide synchronisation
+    const int eb = (task % nEB) * kWarpsPerCta;
+    const int ne = min(kWarpsPerCta, E - eb);
+    const int e = eb + wid;
+    const bool active = e < E;
     const int vl0 = gl * A.G;
     const int vl1 = min(vl0 + A.G, A.nvt);
-    const int ec[3] = {e, 0, 0};
+    int ec[3] = {e, 0, 0};
     const int eL = upwind_neighbour(A.mesh, ec, 0, true), eR = upwind_neighbour(A.mesh, ec, 0, false);
-    const float *__restrict__ src = A.src;
-    const float *__restrict__ fnp = A.fn;
+    ec[0] = eb;
+    const int eoL = upwind_neighbour(A.mesh, ec, 0, true);  // outside neighbours of the block
+    ec[0] = eb + ne - 1;
+    const int eoR = upwind_neighbour(A.mesh, ec, 0, false);
+    const bool has_fn = MODE == 0 && A.fn != nullptr;
 
-    // BGK exponents of the element's nodes (the same for every lane)
-    float pb[NP][8];
+    auto prefetch = [&](int vl, int slot) {
+        LineSlot<N1> &S = sm.s[slot];
+        const int vt = A.vt0 + vl;
+        copy_rows(&S.fs[0][0][0], A.src + fidx(vl, eb, 0, 0, E, NP), ne * NP);
+        copy_rows(&S.wp[0][0], A.wpsi + (int64_t)vt * 5 * kWarp, 5);
+        if (MODE == 0) {
+            if (has_fn)
+                copy_rows(&S.fn[0][0][0], A.fn + fidx(vl, eb, 0, 0, E, NP), ne * NP);
+            const int eo = (__ldg(A.toct + vt) & 1) ? eoL : eoR;
+            if (eo >= 0)
+                copy_rows(&S.nb[0][0], A.src + fidx(vl, eo, 0, 0, E, NP), N1);
+            for (int d = 0; d < 3; d++)
+                copy_rows(&S.mi[d][0], A.mi + (int64_t)d * A.nslots + (int64_t)vt * kWarp, 1);
+            copy_rows(&S.gm[0], A.gmask + (int64_t)vt * kWarp, 1);
+        }
+    };
+
+    // BGK exponents of the block's nodes into shared memory (pair-interleaved); the first barrier of
+    // the tile loop orders these stores before their reads
     if (MODE == 0) {
-#pragma unroll
-        for (int i = 0; i < NP; i++) {
-            const float *q = A.param + ((int64_t)e * NP + i) * kParamStride;
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(q));
-            const float4 u = __ldg(reinterpret_cast<const float4 *>(q + 4));
-            pb[i][0] = v.x;
-            pb[i][1] = v.y;
-            pb[i][2] = v.z;
-            pb[i][3] = v.w;
-            pb[i][4] = u.x;
-            pb[i][5] = u.y;
-            pb[i][6] = u.z;
-            pb[i][7] = u.w;
+        const float *src = A.param + (int64_t)eb * NP * kParamStride;
+        for (int q = threadIdx.x; q < ne * NQ * 2 * kParamStride; q += blockDim.x) {
+            const int c = q % kParamStride, sl = (q / kParamStride) & 1, h = (q / (2 * kParamStride)) % NQ;
+            const int el = q / (2 * kParamStride * NQ);
+            sm.par[el][h][c][sl] = __ldg(src + (el * NP + min(2 * h + sl, NP - 1)) * kParamStride + c);
         }
     }
     const bool viso = A.viso != 0;
@@ -96,46 +142,55 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
     const float kb = A.kb;
     const float cdt = -A.mesh.inv_h2[0] * (A.b * A.dt);
     const float cgt = A.kg;
-    // f: f_s of the current tile; acc: f^n of the current tile (or 0), prefetched one tile ahead
-    float f[NP], acc[NP];
-    {
-        const int64_t b0 = fidx(vl0, e, 0, lane, E, NP);
+
 #pragma unroll
-        for (int i = 0; i < NP; i++) {
-            f[i] = __ldg(src + b0 + i * kWarp);
-            acc[i] = (MODE == 0 && fnp) ? __ldcs(fnp + b0 + i * kWarp) : 0.f;
-        }
+    for (int d = 0; d < kLineDepth - 1; d++) {
+        if (vl0 + d < vl1)
+            prefetch(vl0 + d, d);
+        cp_commit();
     }
     for (int vl = vl0; vl < vl1; vl++) {
+        const int it = vl - vl0;
+        cp_wait<kLineDepth - 2>();  // tile vl has landed (this thread's copies) ...
+        __syncthreads();            // ... for every thread; and every warp is done with tile vl - 1
+        {
+            const int vn = vl + kLineDepth - 1;
+            if (vn < vl1)
+                prefetch(vn, (it + kLineDepth - 1) % kLineDepth);  // the slot of tile vl - 1
+            cp_commit();
+        }
+        if (!active)
+            continue;
+        const LineSlot<N1> &S = sm.s[it % kLineDepth];
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
-        float nf[NP], nacc[NP];
-        if (vl + 1 < vl1) {
-            const int64_t b1 = fidx(vl + 1, e, 0, lane, E, NP);
-#pragma unroll
-            for (int i = 0; i < NP; i++) {
-                nf[i] = __ldg(src + b1 + i * kWarp);
-                nacc[i] = (MODE == 0 && fnp) ? __ldcs(fnp + b1 + i * kWarp) : 0.f;
-            }
-        }
         float o[NP];
         if (MODE == 0) {
-            const float m0 = __ldg(A.mi + slot), m1 = __ldg(A.mi + A.nslots + slot);
-            const float m2 = __ldg(A.mi + 2 * A.nslots + slot);
+            float f[NP];
+#pragma unroll
+            for (int i = 0; i < NP; i++)
+                f[i] = S.fs[wid][i][lane];
+            const float m0 = S.mi[0][lane], m1 = S.mi[1][lane], m2 = S.mi[2][lane];
             const float x0 = fmaf(A.vs[0], m0, A.vc[0]);
             // squared indices (exact) as the exponent's quadratic terms take them
             const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
-            const float u0 = viso ? mms : mm0, u1 = viso ? mms : mm1, u2 = viso ? 0.f : mm2;
-            const bool left = x0 >= 0.f;
+            const unsigned long long M0 = pack2(m0, m0), M1 = pack2(m1, m1), M2 = pack2(m2, m2);
+            const unsigned long long U0 = viso ? pack2(mms, mms) : pack2(mm0, mm0);
+            const unsigned long long U1 = viso ? U0 : pack2(mm1, mm1);
+            const unsigned long long U2 = viso ? 0ull : pack2(mm2, mm2);
+            // inflow side of the tile (one sign octant per tile)
+            const bool left = (__ldg(A.toct + vt) & 1) != 0;
             const int en = left ? eL : eR;
-            // upwind trace at the shared face
+            // upwind trace at the shared face: a sibling's element, the staged outside neighbour, or
+            // the Dirichlet ghost value
             float T;
             if (en >= 0) {
                 float v[N1];
-                const int64_t bn = fidx(vl, en, 0, lane, E, NP);
+                const int r = en - eb;
+                const float *vrow = (r >= 0 && r < ne) ? &S.fs[r][0][0] : &S.nb[0][0];
 #pragma unroll
                 for (int j = 0; j < N1; j++)
-                    v[j] = __ldg(src + bn + j * kWarp);
+                    v[j] = vrow[j * kWarp + lane];
                 T = left ? trace_line<N1, true>(v, op) : trace_line<N1, false>(v, op);
             } else {
                 T = __ldg(A.ghost + (left ? 0 : 1) * A.nslots + slot);
@@ -146,38 +201,49 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
             else
                 line_sums<N1, false>(sd, f, T, op);
             const float cd = cdt * x0;
-            const float cg = cgt * __ldg(A.gmask + slot);
+            const float cg = cgt * S.gm[lane];
             float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
 #pragma unroll
-            for (int i = 0; i < NP; i++) {
-                const float lin = fmaf(pb[i][3], m2, fmaf(pb[i][2], m1, fmaf(pb[i][1], m0, pb[i][0])));
-                const float ex = fmaf(pb[i][4], u0, fmaf(pb[i][5], u1, fmaf(pb[i][6], u2, lin)));
-                const float a = fmaf(cd, sd[i], fmaf(A.an, acc[i], kb * f[i]));
-                o[i] = fmaf(cg, exp2_fp32(ex, pb[i][7]), a);
-                __stcs(dst + i * kWarp, o[i]);
+            for (int h = 0; h < NQ; h++) {
+                const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[wid][h][0][0]);
+                const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];  // (c, c+1) of both nodes
+                const unsigned long long lin =
+                    ffma2(pack2(p23.z, p23.w), M2,
+                          ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
+                const unsigned long long ex =
+                    ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)));
+                float g[2];
+                exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
+#pragma unroll
+                for (int sl = 0; sl < 2; sl++) {
+                    const int i = 2 * h + sl;
+                    if (i < NP) {
+                        const float fnv = has_fn ? S.fn[wid][i][lane] : 0.f;
+                        const float a = fmaf(cd, sd[i], fmaf(A.an, fnv, kb * f[i]));
+                        o[i] = fmaf(cg, g[sl], a);
+                        __stcs(dst + i * kWarp, o[i]);
+                    }
+                }
             }
         } else {
 #pragma unroll
             for (int i = 0; i < NP; i++)
-                o[i] = f[i];
+                o[i] = S.fs[wid][i][lane];
         }
-        // moments of this tile, accumulated per lane: m[c][q] += w psi_c (o_2q, o_2q+1)
+        // moments of this tile, accumulated per lane: m[c][q] += W psi_c (o_2q, o_2q+1)
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            const float w = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+            const float w = S.wp[c][lane];
             const unsigned long long ww = pack2(w, w);
 #pragma unroll
             for (int q = 0; q < NQ; q++)
                 m[c][q] = ffma2(ww, pack2(o[2 * q], 2 * q + 1 < NP ? o[2 * q + 1] : 0.f), m[c][q]);
         }
-        if (vl + 1 < vl1) {
-#pragma unroll
-            for (int i = 0; i < NP; i++) {
-                f[i] = nf[i];
-                acc[i] = nacc[i];
-            }
-        }
     }
+    cp_wait<0>();
+    __syncthreads();  // the ring is free for the CTA's next task
+    if (!active)
+        return;
 
     // totals over the 32 velocities of every tile: value (c, i) at index c * NP + i
     float v[32];
@@ -189,7 +255,7 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
             float lo, hi;
-            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(m[c][q]));
+            unpack2(m[c][q], lo, hi);
             v[c * NP + 2 * q] = lo;
             if (2 * q + 1 < NP)
                 v[c * NP + 2 * q + 1] = hi;
@@ -202,19 +268,21 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
 }
 
 template <int N1, int MODE>
-__global__ void __launch_bounds__(kWarp *kWarpsPerCta) k_stage1d(const StageArgs A)
+__global__ void __launch_bounds__(kWarp *kWarpsPerCta, 5) k_stage1d(const StageArgs A)
 {
-    stage1d_task<N1, MODE>(A, blockIdx.x, A.ops);
+    __shared__ __align__(16) LineSmem<N1> sm;
+    stage1d_task<N1, MODE>(A, blockIdx.x, A.ops, sm);
 }
 
 // Batched line-element stages: one persistent launch over the tasks of many independent problems
 // (each with its own arguments, degree, mesh, velocity grid and task count). CTAs take tasks from an
 // atomic counter; a binary search over the task prefix sums finds the problem. The degree selects the
 // body; the FR operators of each degree come from constant memory.
-__global__ void __launch_bounds__(kWarp *kWarpsPerCta, 4)
+__global__ void __launch_bounds__(kWarp *kWarpsPerCta, 5)
     k_stage1d_batch(const StageArgs *__restrict__ args, const int *__restrict__ task_start, int n, int *counter)
 {
     __shared__ int s_item;
+    __shared__ __align__(16) LineSmem<4> sm;  // the largest degree of the batch (p = 3); smaller ones use its front
     const int total = task_start[n];
     for (;;) {
         __syncthreads();
@@ -235,9 +303,9 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, 4)
         const StageArgs &A = args[lo];
         const int task = item - __ldg(task_start + lo);
         switch (A.n1) {
-        case 2: stage1d_task<2, 0>(A, task, c_ops1d[2]); break;
-        case 3: stage1d_task<3, 0>(A, task, c_ops1d[3]); break;
-        case 4: stage1d_task<4, 0>(A, task, c_ops1d[4]); break;
+        case 2: stage1d_task<2, 0>(A, task, c_ops1d[2], *reinterpret_cast<LineSmem<2> *>(&sm)); break;
+        case 3: stage1d_task<3, 0>(A, task, c_ops1d[3], *reinterpret_cast<LineSmem<3> *>(&sm)); break;
+        case 4: stage1d_task<4, 0>(A, task, c_ops1d[4], sm); break;
         default: break;
         }
     }

@@ -27,7 +27,9 @@ struct Stage3Smem {
     float fnb[2][NP][kWarp];      // f^n of the element (each warp its own layer), double-buffered
     float zc[NP][kWarp];          // z-derivative sums, [node][lane]
     float wf[N1][16][36];         // per warp: its layer's stage output, [node][velocity] (16 rows)
-    float par[NP][kParamStride];  // BGK exponents of the element's points
+    // BGK exponents of the element's points by layer and node pair, [layer][pair][param][node of the
+    // pair], so that one 16-byte load gives two parameters of both nodes (odd layers repeat the last node)
+    float par[N1][(N1 * N1 + 1) / 2][kParamStride][2];
     float fpar[NP][kParamStride]; // body-force polynomials of the element's points (when a force acts)
     float wpsi[5][kWarp];         // w psi of the tile's velocities
 };
@@ -59,10 +61,14 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
     ec[2] = e / (A.mesh.ne[0] * A.mesh.ne[1]);
 
     if (MODE == 0) {
-        const float4 *src4 = reinterpret_cast<const float4 *>(A.param + (int64_t)e * NP * kParamStride);
-        float4 *dst4 = reinterpret_cast<float4 *>(&sm.par[0][0]);
-        for (int q = tid; q < NP * kParamStride / 4; q += NT)
-            dst4[q] = __ldg(src4 + q);
+        constexpr int NH = (NQ + 1) / 2;
+        const float *src = A.param + (int64_t)e * NP * kParamStride;
+        for (int q = tid; q < N1 * NH * 2 * kParamStride; q += NT) {
+            const int c = q % kParamStride, sl = (q / kParamStride) & 1, h = (q / (2 * kParamStride)) % NH;
+            const int lw = q / (2 * kParamStride * NH);
+            const int node = lw * NQ + min(2 * h + sl, NQ - 1);
+            sm.par[lw][h][c][sl] = __ldg(src + node * kParamStride + c);
+        }
         if (GEN && A.fpar) {
             const float4 *f4 = reinterpret_cast<const float4 *>(A.fpar + (int64_t)e * NP * kParamStride);
             float4 *d4 = reinterpret_cast<float4 *>(&sm.fpar[0][0]);
@@ -248,27 +254,43 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             const float xs = x0 * x0 + x1 * x1 + x2 * x2;
             // squared indices (exact); the lean form has one spacing on every axis and needs their sum
             const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
-            const float u0 = (!GEN || A.viso) ? mms : mm0, u1 = (!GEN || A.viso) ? mms : mm1;
-            const float u2 = (!GEN || A.viso) ? 0.f : mm2;
+            const bool iso = !GEN || A.viso;
+            const unsigned long long M0 = pack2(m0, m0), M1 = pack2(m1, m1), M2 = pack2(m2, m2);
+            const unsigned long long U0 = iso ? pack2(mms, mms) : pack2(mm0, mm0);
+            const unsigned long long U1 = iso ? U0 : pack2(mm1, mm1);
+            const unsigned long long U2 = iso ? 0ull : pack2(mm2, mm2);
             float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
+            // two nodes at a time: the exponent a + b.m + q |m|^2 (+ the low part of q) and the range
+            // reduction of 2^x in packed pairs
 #pragma unroll
-            for (int q = 0; q < NQ; q++) {
-                const int i = q + NQ * w;
-                const float4 pb = *reinterpret_cast<const float4 *>(&sm.par[i][0]);
-                const float4 pq = *reinterpret_cast<const float4 *>(&sm.par[i][4]);
-                const float lin = fmaf(pb.w, m2, fmaf(pb.z, m1, fmaf(pb.y, m0, pb.x)));
-                const float ex = GEN ? fmaf(pq.x, u0, fmaf(pq.y, u1, fmaf(pq.z, u2, lin)))
-                                     : fmaf(pq.x, mms, fmaf(pq.y, mms, lin));
-                const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
-                float gc = cg;
-                if (GEN && A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
-                    const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
-                    const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
-                    gc = fmaf(cf, qv, cg);
+            for (int h = 0; h < (NQ + 1) / 2; h++) {
+                const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[w][h][0][0]);
+                const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];  // (c, c+1) of both nodes
+                const unsigned long long lin =
+                    ffma2(pack2(p23.z, p23.w), M2,
+                          ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
+                const unsigned long long ex =
+                    GEN ? ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
+                        : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
+                float g[2];
+                exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
+#pragma unroll
+                for (int sl = 0; sl < 2; sl++) {
+                    const int q = 2 * h + sl;
+                    if (q >= NQ)
+                        break;
+                    const int i = q + NQ * w;
+                    const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
+                    float gc = cg;
+                    if (GEN && A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
+                        const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
+                        const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
+                        gc = fmaf(cf, qv, cg);
+                    }
+                    const float o = fmaf(gc, g[sl], a);
+                    __stcs(dst + i * kWarp, o);
+                    sm.wf[w][q][lane] = o;  // for the moments below (this warp's own rows)
                 }
-                const float o = fmaf(gc, exp2_fp32(ex, pq.w), a);
-                __stcs(dst + i * kWarp, o);
-                sm.wf[w][q][lane] = o;  // for the moments below (this warp's own rows)
             }
         } else {
             __syncthreads();  // B1 (same barrier sequence in both modes)

@@ -25,6 +25,23 @@ __device__ __forceinline__ float sum2(unsigned long long v)
     return lo + hi;
 }
 
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 // Upwind neighbour of element (ec) in direction d: returns its index, or -1 when the face is a
 // non-periodic domain boundary (then the ghost table supplies the upwind value).
 __device__ __forceinline__ int upwind_neighbour(const Mesh &m, const int ec[3], int d, bool left)
@@ -98,6 +115,35 @@ __device__ __forceinline__ float exp2_fp32(float x, float kmagic)
     p = fmaf(p, r, 1.0f);
     // the low bits of t hold n + j (two's complement); shifting them into the exponent field scales
     return __int_as_float(__float_as_int(p) + (__float_as_int(t) << 23));
+}
+
+// exp2_fp32 of two values at once: the range reduction in packed FP32 pairs, the polynomial per value
+// (its coefficients as immediates). x holds the two arguments, kmagic their two rounding constants.
+__device__ __forceinline__ void exp2_fp32x2(unsigned long long x, unsigned long long kmagic, float &y0, float &y1)
+{
+    float x0, x1;
+    unpack2(x, x0, x1);
+    const unsigned long long xc = pack2(fmaxf(x0, -100.0f), fmaxf(x1, -100.0f));
+    const unsigned long long t = fadd2(xc, kmagic);
+    const unsigned long long r = fsub2(xc, fsub2(t, kmagic));
+    float r0, r1, t0, t1;
+    unpack2(r, r0, r1);
+    unpack2(t, t0, t1);
+    float p0 = 1.533757750e-04f, p1 = 1.533757750e-04f;
+    p0 = fmaf(p0, r0, 1.339985989e-03f);
+    p1 = fmaf(p1, r1, 1.339985989e-03f);
+    p0 = fmaf(p0, r0, 9.618519805e-03f);
+    p1 = fmaf(p1, r1, 9.618519805e-03f);
+    p0 = fmaf(p0, r0, 5.550329015e-02f);
+    p1 = fmaf(p1, r1, 5.550329015e-02f);
+    p0 = fmaf(p0, r0, 2.402264625e-01f);
+    p1 = fmaf(p1, r1, 2.402264625e-01f);
+    p0 = fmaf(p0, r0, 6.931471825e-01f);
+    p1 = fmaf(p1, r1, 6.931471825e-01f);
+    p0 = fmaf(p0, r0, 1.0f);
+    p1 = fmaf(p1, r1, 1.0f);
+    y0 = __int_as_float(__float_as_int(p0) + (__float_as_int(t0) << 23));
+    y1 = __int_as_float(__float_as_int(p1) + (__float_as_int(t1) << 23));
 }
 
 // Upwind trace of one neighbour line v (difference form, exact for a constant state): a left
