@@ -20,17 +20,17 @@ namespace bgk {
 // the layers and are read from a shared copy of the element tile. The z-upwind traces are split
 // over the warps (warp w interpolates the z-lines with iy = w) and shared the same way.
 // ------------------------------------------------------------------------------------------------
-template <int N1>
+template <int N1, int GEN>
 struct Stage3Smem {
     static constexpr int NP = N1 * N1 * N1;
     float tile[2][NP][kWarp];     // f_s of the element, [node][lane], double-buffered (cp.async)
-    float fnb[2][NP][kWarp];      // f^n of the element (each warp its own layer), double-buffered
+    float fnb[NP][kWarp];         // f^n of the element (each warp its own layer), refilled after use
     float zc[NP][kWarp];          // z-derivative sums, [node][lane]
     float wf[N1][16][36];         // per warp: its layer's stage output, [node][velocity] (16 rows)
     // BGK exponents of the element's points by layer and node pair, [layer][pair][param][node of the
     // pair], so that one 16-byte load gives two parameters of both nodes (odd layers repeat the last node)
     float par[N1][(N1 * N1 + 1) / 2][kParamStride][2];
-    float fpar[NP][kParamStride]; // body-force polynomials of the element's points (when a force acts)
+    float fpar[GEN ? NP : 1][kParamStride];  // body-force polynomials of the element's points (general form)
     float wpsi[5][kWarp];         // w psi of the tile's velocities
 };
 
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
     constexpr int NQ = N1 * N1;      // nodes per layer
     constexpr int NP = NQ * N1;
     constexpr int NT = kWarp * N1;   // threads
-    using Sm = Stage3Smem<N1>;
+    using Sm = Stage3Smem<N1, GEN>;
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm &sm = *reinterpret_cast<Sm *>(smraw);
 
@@ -92,16 +92,20 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
     // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
     // 128 bytes, contiguous in global and shared memory
     const bool has_fn = MODE == 0 && A.fn != nullptr;
+    constexpr int NCH = NQ * kWarp / 4;  // 16-byte chunks of one layer
     auto prefetch = [&](int vl, int b) {
-        constexpr int NCH = NQ * kWarp / 4;  // 16-byte chunks of one layer
         const float4 *gs = reinterpret_cast<const float4 *>(A.src + fidx(vl, e, NQ * w, 0, E, NP));
         float4 *ss = reinterpret_cast<float4 *>(&sm.tile[b][NQ * w][0]);
 #pragma unroll
         for (int m = lane; m < NCH; m += kWarp)
             cp_async16(ss + m, gs + m);
+        cp_commit();
+    };
+    // f^n of this warp's layer: one buffer, refilled for the next tile once this tile has read it
+    auto prefetch_fn = [&](int vl) {
         if (has_fn) {
             const float4 *gf = reinterpret_cast<const float4 *>(A.fn + fidx(vl, e, NQ * w, 0, E, NP));
-            float4 *sf = reinterpret_cast<float4 *>(&sm.fnb[b][NQ * w][0]);
+            float4 *sf = reinterpret_cast<float4 *>(&sm.fnb[NQ * w][0]);
 #pragma unroll
             for (int m = lane; m < NCH; m += kWarp)
                 cp_async16(sf + m, gf + m);
@@ -109,12 +113,14 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
         cp_commit();
     };
     prefetch(vl0, 0);
+    prefetch_fn(vl0);
 
     for (int vl = vl0; vl < vl1; vl++) {
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
         const int b = (vl - vl0) & 1;
-        // the other buffer was last read before the previous tile's B2, which every warp has passed
+        // the other buffer was last read before the previous tile's B2, which every warp has passed;
+        // pending groups: tile vl, f^n vl (issued last tile), then tile vl + 1
         if (vl + 1 < vl1) {
             prefetch(vl + 1, b ^ 1);
             cp_wait<1>();
@@ -136,12 +142,17 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             if (has_fn) {
 #pragma unroll
                 for (int q = 0; q < NQ; q++)
-                    acc[q] = sm.fnb[b][q + NQ * w][lane];
+                    acc[q] = sm.fnb[q + NQ * w][lane];
             } else {
 #pragma unroll
                 for (int q = 0; q < NQ; q++)
                     acc[q] = 0.f;
             }
+            __syncwarp();  // every lane has read its f^n rows before they are refilled
+            if (vl + 1 < vl1)
+                prefetch_fn(vl + 1);
+            else
+                cp_commit();  // keep the group count per tile fixed
             // upwind neighbour values: x-lines and y-lines of layer w, z-lines of slice iy = w
             float vx[N1][N1], vy[N1][N1], vz[N1][N1];
             const int enx = upwind_neighbour(A.mesh, ec, 0, l0);
@@ -162,14 +173,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
 #pragma unroll
                     for (int j = 0; j < N1; j++)
                         vy[ix][j] = __ldg(nb + (ix + N1 * j + NQ * w) * kWarp);
-            }
-            if (enz >= 0) {
-                const float *nb = A.src + fidx(vl, enz, 0, lane, E, NP);
-#pragma unroll
-                for (int ix = 0; ix < N1; ix++)
-#pragma unroll
-                    for (int j = 0; j < N1; j++)
-                        vz[ix][j] = __ldg(nb + (ix + N1 * w + NQ * j) * kWarp);
             }
             // acc = an f^n + b (1 - dt/tau) f_s, then x and y lines from registers
 #pragma unroll
@@ -223,6 +226,16 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
+            }
+            // the z-neighbour lines (slice iy = w) are loaded only now, so that their registers are
+            // not live across the x and y lines; the barrier covers part of their latency
+            if (enz >= 0) {
+                const float *nb = A.src + fidx(vl, enz, 0, lane, E, NP);
+#pragma unroll
+                for (int ix = 0; ix < N1; ix++)
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        vz[ix][j] = __ldg(nb + (ix + N1 * w + NQ * j) * kWarp);
             }
             __syncthreads();  // B1: the element tile is complete
             if (w == 0) {
@@ -350,20 +363,20 @@ template <int N1, int MODE, int OCT, int GEN>
 cudaError_t launch3(const StageArgs &A, cudaStream_t s)
 {
     const int ngroups = (A.nvt + A.G - 1) / A.G;
-    k_stage3<N1, MODE, OCT, GEN><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3Smem<N1>), s>>>(A);
+    k_stage3<N1, MODE, OCT, GEN><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3Smem<N1, GEN>), s>>>(A);
     return cudaGetLastError();
 }
 
 template <int N1>
 cudaError_t prepare3()
 {
-    const int smem = (int)sizeof(Stage3Smem<N1>);
-    cudaError_t e = cudaFuncSetAttribute(k_stage3<N1, 1, 8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int s0 = (int)sizeof(Stage3Smem<N1, 0>), s1 = (int)sizeof(Stage3Smem<N1, 1>);
+    cudaError_t e = cudaFuncSetAttribute(k_stage3<N1, 1, 8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0);
 #define BGK_P3(O)                                                                                         \
     if (e == cudaSuccess)                                                                                 \
-        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0); \
     if (e == cudaSuccess)                                                                                 \
-        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
     BGK_P3(0) BGK_P3(1) BGK_P3(2) BGK_P3(3) BGK_P3(4) BGK_P3(5) BGK_P3(6) BGK_P3(7) BGK_P3(8)
 #undef BGK_P3
     return e;
