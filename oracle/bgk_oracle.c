@@ -49,6 +49,8 @@ struct orc_ctx {
     double *ghost;          /* [6][nvel]: Dirichlet ghost Maxwellian, or unit-density wall Maxwellian */
     double newton_tol;
     int newton_max;
+    int continuous;         /* 1: g is the sampled continuous Maxwellian of Q (no Newton; ablation) */
+    int limiter;            /* 1: Zhang-Shu positivity limiter on every stage output */
 };
 
 /* ------------------------------------------------------------------------------------------ */
@@ -341,6 +343,8 @@ static int newton_point(const orc_ctx *c, const double *Q, double *P, int *iters
         *resid = INFINITY;
     if (!(rho > 0) || !(theta > 0) || !isfinite(rho) || !isfinite(theta))
         return -1;
+    if (c->continuous)  /* the state of Q itself: the equilibrium that Sec. 2.1 shows is not conservative */
+        return 0;
     double s[5] = {rho, rho * sqrt(theta), rho * sqrt(theta), rho * sqrt(theta), fabs(Q[4])};
     double G[5], J[25];
     newton_eval(c, P, Q, G, J);
@@ -504,6 +508,49 @@ void oracle_set_newton(orc_ctx *c, double tol, int max_it)
 {
     c->newton_tol = tol;
     c->newton_max = max_it;
+}
+
+void oracle_set_maxwellian(orc_ctx *c, int continuous) { c->continuous = continuous != 0; }
+
+void oracle_set_limiter(orc_ctx *c, int on) { c->limiter = on != 0; }
+
+/* Zhang-Shu positivity limiter (Sec. 2.1, Eqs. 10-11), per element and velocity: with the element mean
+ * fbar = sum_i W_i f_i / sum_i W_i (tensor Gauss-Legendre weights W) and fmin = min_i f_i, every node value
+ * becomes fbar + beta (f_i - fbar), beta = min(|fbar / (fbar - fmin)|, 1), when some f_i < 0. */
+int oracle_limit(const orc_ctx *c, double *f)
+{
+    const int n1 = c->n1, np = c->np;
+    double W[MAXN * MAXN * MAXN], Wsum = 0.0;
+    for (int i = 0; i < np; i++) {
+        W[i] = c->wg[i % n1];
+        if (c->dim >= 2)
+            W[i] *= c->wg[(i / n1) % n1];
+        if (c->dim >= 3)
+            W[i] *= c->wg[i / (n1 * n1)];
+        Wsum += W[i];
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < c->nelem; e++)
+        for (int64_t k = 0; k < c->nvel; k++) {
+            double fbar = 0.0, fmin = INFINITY;
+            for (int i = 0; i < np; i++) {
+                const double v = f[(e * np + i) * c->nvel + k];
+                fbar += W[i] * v;
+                if (v < fmin)
+                    fmin = v;
+            }
+            fbar /= Wsum;
+            if (!(fmin < 0.0))
+                continue;
+            double beta = fabs(fbar / (fbar - fmin));
+            if (beta > 1.0)
+                beta = 1.0;
+            for (int i = 0; i < np; i++) {
+                double *v = &f[(e * np + i) * c->nvel + k];
+                *v = fbar + beta * (*v - fbar);
+            }
+        }
+    return 0;
 }
 
 /* element coordinates (ex, ey, ez) <-> index, x fastest */
@@ -794,14 +841,20 @@ int oracle_step(orc_ctx *c, double dt, int nsteps)
 #pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; q++)
             f1[q] = f[q] + dt * L[q];
+        if (c->limiter)
+            oracle_limit(c, f1);
         fails += -oracle_rhs(c, f1, L);
 #pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; q++)
             f2[q] = 0.75 * f[q] + 0.25 * (f1[q] + dt * L[q]);
+        if (c->limiter)
+            oracle_limit(c, f2);
         fails += -oracle_rhs(c, f2, L);
 #pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; q++)
             f[q] = (1.0 / 3.0) * f[q] + (2.0 / 3.0) * (f2[q] + dt * L[q]);
+        if (c->limiter)
+            oracle_limit(c, f);
     }
     free(f1);
     free(f2);

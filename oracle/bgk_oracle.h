@@ -101,6 +101,17 @@ double oracle_dt(const orc_ctx *c, double cfl);
 /* Newton tolerance and iteration cap used by the conservative Maxwellian (defaults 1e-13, 50). */
 void oracle_set_newton(orc_ctx *c, double tol, int max_it);
 
+/* Equilibrium of the BGK source: 0 (default) the discretely-conservative Maxwellian (Sec. 2.1, text
+ * after Eq. 13); 1 the sampled continuous Maxwellian of the moments Q, which Sec. 2.1 (Eq. 13) shows is
+ * not conservative on the discrete grid (the ablation of the method). */
+void oracle_set_maxwellian(orc_ctx *c, int continuous);
+
+/* Zhang-Shu positivity limiter (Sec. 2.1, Eqs. 10-11) on every RK stage output: off by default. */
+void oracle_set_limiter(orc_ctx *c, int on);
+
+/* Apply the limiter to f[n_x][N_v] in place (element mean with the tensor Gauss-Legendre weights). */
+int oracle_limit(const orc_ctx *c, double *f);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,9 @@ def lib():
             L.oracle_dt.restype = C.c_double
             L.oracle_dt.argtypes = [C.c_void_p, C.c_double]
             L.oracle_set_newton.argtypes = [C.c_void_p, C.c_double, C.c_int]
+            L.oracle_set_maxwellian.argtypes = [C.c_void_p, C.c_int]
+            L.oracle_set_limiter.argtypes = [C.c_void_p, C.c_int]
+            L.oracle_limit.argtypes = [C.c_void_p, dp]
             _lib = L
     return _lib
 
@@ -214,3 +217,16 @@ class Problem:
 
     def set_newton(self, tol, max_it):
         lib().oracle_set_newton(self.h, float(tol), int(max_it))
+
+    def set_maxwellian(self, continuous):
+        """False: the discretely-conservative Maxwellian; True: the continuous one of Q (ablation)."""
+        lib().oracle_set_maxwellian(self.h, int(bool(continuous)))
+
+    def set_limiter(self, on):
+        lib().oracle_set_limiter(self.h, int(bool(on)))
+
+    def limit(self, f):
+        """The positivity limiter applied to a copy of f [n_x, N_v]."""
+        a = np.ascontiguousarray(f, dtype=np.float64).reshape(self.npts, self.nvel).copy()
+        lib().oracle_limit(self.h, _d(a))
+        return a
