@@ -79,10 +79,18 @@ typedef struct {
                                 exactly those of -F . grad_xi f */
     int newton_max_it;       /* FP32 Newton iterations per solve, <= 0: default (2 warm, 12 cold) */
     double newton_tol;       /* reserved (the FP64 refinement fixes the final accuracy) */
-    int limiter;             /* reserved: positivity limiter (Eqs. 10-11) is not on this path */
+    int limiter;             /* 1: Zhang-Shu positivity limiter (Sec. 2.1, Eqs. 10-11) on every stage output,
+                                per element and velocity: towards the Gauss-Legendre-weighted element mean
+                                where a node value is negative. Keeps element means (so conservation). */
     int chunks;              /* velocity chunks per stage, 0 = automatic */
     int vtiles_per_task;     /* 32-velocity tiles per warp task, 0 = automatic */
+    int maxwellian;          /* BGK_MAXWELLIAN_CONSERVATIVE (0, the method) or BGK_MAXWELLIAN_CONTINUOUS
+                                (the ablation: g = the sampled continuous Maxwellian of the moments, whose
+                                discrete moments differ from them, Sec. 2.1, Eq. 13) */
 } bgk_opts;
+
+#define BGK_MAXWELLIAN_CONSERVATIVE 0
+#define BGK_MAXWELLIAN_CONTINUOUS 1
 
 /* Create a problem on the current CUDA device: plans the velocity tiles, builds the FR operators
  * (Eqs. 7-8) in FP64 on the host and allocates every device buffer. p in [1, 3] for dim = 3 and

@@ -17,6 +17,7 @@ from . import _build
 BGK_OK, BGK_EINVAL, BGK_ENOMEM, BGK_ECUDA, BGK_ENEWTON, BGK_EDOMAIN, BGK_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 BC_PERIODIC, BC_DIRICHLET, BC_DIFFUSE_WALL = 0, 1, 2
 FP32_SPLIT, FP64 = 0, 1
+MAXWELLIAN_CONSERVATIVE, MAXWELLIAN_CONTINUOUS = 0, 1
 
 # every symbol include/bgk.h declares
 SYMBOLS = (
@@ -41,7 +42,7 @@ class bgk_vgrid(C.Structure):
 class bgk_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("body_force", C.c_double * 3), ("newton_max_it", C.c_int),
                 ("newton_tol", C.c_double), ("limiter", C.c_int), ("chunks", C.c_int),
-                ("vtiles_per_task", C.c_int)]
+                ("vtiles_per_task", C.c_int), ("maxwellian", C.c_int)]
 
 
 class BgkError(RuntimeError):
@@ -140,16 +141,19 @@ def make_vgrid(n, lo, hi) -> bgk_vgrid:
     return v
 
 
-def make_opts(precision=FP32_SPLIT, body_force=(0.0, 0.0, 0.0), newton_max_it=0, chunks=0, vtiles_per_task=0):
+def make_opts(precision=FP32_SPLIT, body_force=(0.0, 0.0, 0.0), newton_max_it=0, chunks=0, vtiles_per_task=0,
+              limiter=False, maxwellian=0):
+    """maxwellian: MAXWELLIAN_CONSERVATIVE (the method) or MAXWELLIAN_CONTINUOUS (the ablation)."""
     o = bgk_opts()
     o.precision = precision
     for d in range(3):
         o.body_force[d] = float(body_force[d])
     o.newton_max_it = newton_max_it
     o.newton_tol = 0.0
-    o.limiter = 0
+    o.limiter = int(bool(limiter))
     o.chunks = chunks
     o.vtiles_per_task = vtiles_per_task
+    o.maxwellian = int(maxwellian)
     return o
 
 

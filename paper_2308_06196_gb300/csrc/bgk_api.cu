@@ -36,6 +36,7 @@ cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slot
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
 cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s);
+cudaError_t launch_limit64(double *f, int nvt, int E, int NP, int N1, int dim, const Ops64 &ops, cudaStream_t s);
 cudaError_t launch_wall(const WallArgs &A, bool fp64, const void *w, const void *xi, cudaStream_t s);
 cudaError_t launch_moments64(const Moments64Args &A, cudaStream_t s);
 cudaError_t launch_init64(double *f, const double *prim, const double *xi, const float *gmask, int nvt, int E, int NP,
@@ -131,6 +132,7 @@ void build_ops(int p, Ops &op, Ops64 &o64, double *xg_out)
         o64.lp[i] = lp[i];
         o64.gl[i] = gl[i];
         o64.gr[i] = gr[i];
+        o64.wq[i] = 0.5 * W[i];
     }
     for (int i = 0; i < n; i++) {
         for (int j = 0; j < n; j++) {
@@ -141,6 +143,7 @@ void build_ops(int p, Ops &op, Ops64 &o64, double *xg_out)
         op.gr[i] = (float)gr[i];
         op.lm[i] = (float)lm[i];
         op.lp[i] = (float)lp[i];
+        op.wq[i] = (float)(0.5 * W[i]);
         xg_out[i] = x[i];
     }
 }
@@ -272,6 +275,7 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.nslots = c->nslots;
     A.npts = (int)c->npts;
     A.inv_tau = (float)(1.0 / c->tau);
+    A.limiter = c->opts.limiter != 0;
     return A;
 }
 
@@ -306,6 +310,7 @@ NewtonArgs newton_args(bgk_ctx *c, int cold)
     N.param = c->param;
     N.err = c->err;
     N.cold = cold;
+    N.continuous = c->opts.maxwellian == BGK_MAXWELLIAN_CONTINUOUS;
     N.it32 = c->opts.newton_max_it > 0 ? c->opts.newton_max_it : 2;
     N.it64 = 1;
     if (c->prec == BGK_FP64) {  // FP64 moments from k64_moments; FP64 Maxwellian parameters out
@@ -471,6 +476,8 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
                 real += c->slotk[v] >= 0;
             ev_begin(c, 0, (double)real * c->npts * sizeof(double) * (st == 0 ? 2 : 3));
             CK(launch_stage64(A, s));
+            if (c->opts.limiter)
+                CK(launch_limit64(A.dst, ch.nvt, c->E, c->NP, c->N1, c->dim, c->ops64, s));
             ev_end(c);
             M.base[q] = A.dst;
             M.vt0[q] = ch.vt0;
@@ -602,6 +609,8 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         c->opts = *opts;
     if (c->opts.precision != BGK_FP32_SPLIT && c->opts.precision != BGK_FP64)
         return bail(BGK_EINVAL, "precision must be BGK_FP32_SPLIT or BGK_FP64");
+    if (c->opts.maxwellian != BGK_MAXWELLIAN_CONSERVATIVE && c->opts.maxwellian != BGK_MAXWELLIAN_CONTINUOUS)
+        return bail(BGK_EINVAL, "maxwellian must be BGK_MAXWELLIAN_CONSERVATIVE or BGK_MAXWELLIAN_CONTINUOUS");
     c->prec = c->opts.precision;
     c->esize = c->prec == BGK_FP64 ? 8 : 4;
     c->dim = mesh->dim;

@@ -32,6 +32,7 @@ struct Ops {
     float DR[kMaxN1][kMaxN1];
     float gl[kMaxN1], gr[kMaxN1];
     float lm[kMaxN1], lp[kMaxN1];
+    float wq[kMaxN1];    // Gauss-Legendre weights / 2 (they sum to 1): the element mean of the limiter
 };
 
 struct Mesh {
@@ -75,6 +76,7 @@ struct StageArgs {
     int npts;            // n_x
     float an, b;         // Shu-Osher coefficients: out = an f^n + b (f_s + dt L(f_s))
     float dt, inv_tau;
+    int limiter;         // 1: Zhang-Shu positivity limiter on the stage output (Sec. 2.1, Eqs. 10-11)
     float kb, kg;        // b (1 - dt / tau) and b dt / tau: the weights of f_s and of the Maxwellian.
                          // Rounded so that an + b = 1 and kb + kg = b hold exactly in FP32, so a state
                          // equal to f^n and to its Maxwellian is kept up to unbiased rounding.
@@ -94,6 +96,7 @@ struct NewtonArgs {
     float *param;          // [n_x][8] stage-kernel exponent (out)
     int *err;              // status word (atomicOr)
     int cold;              // 1: ignore prim and start from the continuous state of Q
+    int continuous;        // 1: no solve, g = the continuous Maxwellian of Q (ablation)
     int it32;              // FP32 Newton iterations
     int it64;              // FP64 refinements
     // 1-D velocity grids: xi_k = v0[d] + k dv[d], k < n[d]; trapezoid weights
@@ -106,6 +109,7 @@ struct Ops64 {
     double D[kMaxN1][kMaxN1];
     double lm[kMaxN1], lp[kMaxN1];
     double gl[kMaxN1], gr[kMaxN1];
+    double wq[kMaxN1];  // Gauss-Legendre weights / 2
 };
 
 // One launch of the plain FP64 stage kernel over one velocity chunk (thread per degree of freedom).

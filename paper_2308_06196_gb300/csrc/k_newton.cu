@@ -243,7 +243,7 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     // 2. starting state (V, s^2) and target moments in the centred, scaled basis psi~ = (1, c, |c|^2/2)
     double V[3] = {u[0], u[1], u[2]}, th0 = thc, rh0 = rho;
     bool warm = false;
-    if (!A.cold) {
+    if (!A.cold && !A.continuous) {
         const double *pp = A.prim + (int64_t)pt * 5;
         if (pp[0] > 0.0 && pp[4] > 0.0 && isfinite(pp[0] + pp[1] + pp[2] + pp[3] + pp[4])) {
             rh0 = pp[0];
@@ -271,87 +271,90 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
         dvs[d] = A.dv[d];
     }
 
-    // FP32 Newton iterations until the step is below FP32 resolution (it32 minimum, 30 maximum)
-    float J[5][5];
-    bool haveJ = false;
-    const int it32min = warm ? A.it32 : max(A.it32, 4);
-    for (int it = 0; it < 30; it++) {
-        float S[3][5];
-#pragma unroll
-        for (int d = 0; d < 3; d++)
-            sums32((float)al[1 + d], (float)(-al[4]), (float)c0[d], (float)h[d], A.n[d], (float)dvs[d], S[d]);
-        float M[5];
-        assemble<float>(S, expf((float)al[0]), M, J);
-        haveJ = true;
-        float r[5], dx[5], Jw[5][5];
-#pragma unroll
-        for (int m = 0; m < 5; m++) {
-            r[m] = (float)(Qt[m] - (double)M[m]);
-#pragma unroll
-            for (int q = 0; q < 5; q++)
-                Jw[m][q] = J[m][q];
-        }
-        if (!solve5<float>(Jw, r, dx)) {
-            haveJ = false;
-            break;
-        }
-        // keep the Gaussian decaying: halve the step while beta would drop below 0.05
-        float lam = 1.f;
-        while (-(al[4] + lam * dx[4]) < 0.05 && lam > 1e-3f)
-            lam *= 0.5f;
-        float step = 0.f;
-#pragma unroll
-        for (int m = 0; m < 5; m++) {
-            al[m] += (double)(lam * dx[m]);
-            step = fmaxf(step, fabsf(lam * dx[m]));
-        }
-        if (it + 1 >= it32min && step < 2e-6f)
-            break;
-    }
-    if (!haveJ) {
-        atomicOr(A.err, kErrNewton);
-        return;
-    }
-
-    // FP64 refinements with the FP32 Jacobian of the last iteration, until the correction is at
-    // FP64 resolution (it64 minimum, 4 maximum)
+    // the ablation (continuous Maxwellian of Q) stops here: alpha = the starting state itself
     double corr = 0.0;
-    const int it64min = warm ? A.it64 : max(A.it64, 2);
-    for (int it = 0; it < 4; it++) {
-        double S[3][5];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            double s3[3];
-            sums64<3>(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], s3);
-            S[d][0] = s3[0];
-            S[d][1] = s3[1];
-            S[d][2] = s3[2];
-            S[d][3] = S[d][4] = 0.0;
+    if (!A.continuous) {
+        // FP32 Newton iterations until the step is below FP32 resolution (it32 minimum, 30 maximum)
+        float J[5][5];
+        bool haveJ = false;
+        const int it32min = warm ? A.it32 : max(A.it32, 4);
+        for (int it = 0; it < 30; it++) {
+            float S[3][5];
+    #pragma unroll
+            for (int d = 0; d < 3; d++)
+                sums32((float)al[1 + d], (float)(-al[4]), (float)c0[d], (float)h[d], A.n[d], (float)dvs[d], S[d]);
+            float M[5];
+            assemble<float>(S, expf((float)al[0]), M, J);
+            haveJ = true;
+            float r[5], dx[5], Jw[5][5];
+    #pragma unroll
+            for (int m = 0; m < 5; m++) {
+                r[m] = (float)(Qt[m] - (double)M[m]);
+    #pragma unroll
+                for (int q = 0; q < 5; q++)
+                    Jw[m][q] = J[m][q];
+            }
+            if (!solve5<float>(Jw, r, dx)) {
+                haveJ = false;
+                break;
+            }
+            // keep the Gaussian decaying: halve the step while beta would drop below 0.05
+            float lam = 1.f;
+            while (-(al[4] + lam * dx[4]) < 0.05 && lam > 1e-3f)
+                lam *= 0.5f;
+            float step = 0.f;
+    #pragma unroll
+            for (int m = 0; m < 5; m++) {
+                al[m] += (double)(lam * dx[m]);
+                step = fmaxf(step, fabsf(lam * dx[m]));
+            }
+            if (it + 1 >= it32min && step < 2e-6f)
+                break;
         }
-        double M[5];
-        assemble<double>(S, exp(al[0]), M, nullptr);
-        double r[5], dx[5], Jd[5][5];
-#pragma unroll
-        for (int m = 0; m < 5; m++) {
-            r[m] = Qt[m] - M[m];
-#pragma unroll
-            for (int q = 0; q < 5; q++)
-                Jd[m][q] = (double)J[m][q];
-        }
-        if (!solve5<double>(Jd, r, dx)) {
+        if (!haveJ) {
             atomicOr(A.err, kErrNewton);
             return;
         }
-        corr = 0.0;
-#pragma unroll
-        for (int m = 0; m < 5; m++) {
-            al[m] += dx[m];
-            corr = fmax(corr, fabs(dx[m]));
+
+        // FP64 refinements with the FP32 Jacobian of the last iteration, until the correction is at
+        // FP64 resolution (it64 minimum, 4 maximum)
+        const int it64min = warm ? A.it64 : max(A.it64, 2);
+        for (int it = 0; it < 4; it++) {
+            double S[3][5];
+    #pragma unroll
+            for (int d = 0; d < 3; d++) {
+                double s3[3];
+                sums64<3>(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], s3);
+                S[d][0] = s3[0];
+                S[d][1] = s3[1];
+                S[d][2] = s3[2];
+                S[d][3] = S[d][4] = 0.0;
+            }
+            double M[5];
+            assemble<double>(S, exp(al[0]), M, nullptr);
+            double r[5], dx[5], Jd[5][5];
+    #pragma unroll
+            for (int m = 0; m < 5; m++) {
+                r[m] = Qt[m] - M[m];
+    #pragma unroll
+                for (int q = 0; q < 5; q++)
+                    Jd[m][q] = (double)J[m][q];
+            }
+            if (!solve5<double>(Jd, r, dx)) {
+                atomicOr(A.err, kErrNewton);
+                return;
+            }
+            corr = 0.0;
+    #pragma unroll
+            for (int m = 0; m < 5; m++) {
+                al[m] += dx[m];
+                corr = fmax(corr, fabs(dx[m]));
+            }
+            // the FP32 Jacobian contracts the error by ~1e-6 per refinement: after a correction below
+            // 1e-6 the residual is at FP64 resolution
+            if (it + 1 >= it64min && corr < 1e-6)
+                break;
         }
-        // the FP32 Jacobian contracts the error by ~1e-6 per refinement: after a correction below
-        // 1e-6 the residual is at FP64 resolution
-        if (it + 1 >= it64min && corr < 1e-6)
-            break;
     }
     const double beta = -al[4];
     if (!(beta > 0.0) || !isfinite(al[0] + al[1] + al[2] + al[3]) || corr >= 1e-6) {

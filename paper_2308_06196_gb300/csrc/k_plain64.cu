@@ -156,6 +156,44 @@ __global__ void k64_convert(double *f, double *st, const int *slotk, int nvt, in
 
 static int grid_for(int64_t n, int threads) { return (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 32); }
 
+// Zhang-Shu positivity limiter on the FP64 stage output (Sec. 2.1, Eqs. 10-11): thread per
+// (tile, element, lane); the element mean uses the Gauss-Legendre weights of the nodes.
+__global__ void __launch_bounds__(256) k64_limit(double *f, int nvt, int E, int NP, int N1, int dim, Ops64 ops)
+{
+    const int64_t n = (int64_t)nvt * E * kWarp;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(q % kWarp);
+        const int64_t ve = q / kWarp;  // (tile, element)
+        double *b = f + ve * NP * kWarp + lane;
+        double mean = 0.0, wsum = 0.0, mn = b[0];
+        for (int i = 0; i < NP; i++) {
+            double w = ops.wq[i % N1];
+            if (dim >= 2)
+                w *= ops.wq[(i / N1) % N1];
+            if (dim >= 3)
+                w *= ops.wq[i / (N1 * N1)];
+            const double v = b[(int64_t)i * kWarp];
+            mean += w * v;
+            wsum += w;
+            mn = fmin(mn, v);
+        }
+        mean /= wsum;
+        if (!(mn < 0.0))
+            continue;
+        const double beta = fmin(fabs(mean / (mean - mn)), 1.0);
+        for (int i = 0; i < NP; i++)
+            b[(int64_t)i * kWarp] = mean + beta * (b[(int64_t)i * kWarp] - mean);
+    }
+}
+
+cudaError_t launch_limit64(double *f, int nvt, int E, int NP, int N1, int dim, const Ops64 &ops, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nvt * E * kWarp;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k64_limit<<<blocks, 256, 0, s>>>(f, nvt, E, NP, N1, dim, ops);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s)
 {
     const int64_t n = (int64_t)A.nvt * A.mesh.nelem * A.NP * kWarp;

@@ -221,10 +221,28 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
                         const float fnv = has_fn ? S.fn[wid][i][lane] : 0.f;
                         const float a = fmaf(cd, sd[i], fmaf(A.an, fnv, kb * f[i]));
                         o[i] = fmaf(cg, g[sl], a);
-                        __stcs(dst + i * kWarp, o[i]);
                     }
                 }
             }
+            if (A.limiter) {
+                // Zhang-Shu (Sec. 2.1, Eqs. 10-11): contract towards the element mean where a node
+                // value of this velocity is negative
+                float mean = 0.f, mn = o[0];
+#pragma unroll
+                for (int i = 0; i < NP; i++) {
+                    mean = fmaf(op.wq[i], o[i], mean);
+                    mn = fminf(mn, o[i]);
+                }
+                if (mn < 0.f) {
+                    const float beta = fminf(fabsf(mean / (mean - mn)), 1.f);
+#pragma unroll
+                    for (int i = 0; i < NP; i++)
+                        o[i] = fmaf(beta, o[i] - mean, mean);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NP; i++)
+                __stcs(dst + i * kWarp, o[i]);
         } else {
 #pragma unroll
             for (int i = 0; i < NP; i++)

@@ -31,6 +31,7 @@ struct Stage3Smem {
     // pair], so that one 16-byte load gives two parameters of both nodes (odd layers repeat the last node)
     float par[N1][(N1 * N1 + 1) / 2][kParamStride][2];
     float fpar[GEN ? NP : 1][kParamStride];  // body-force polynomials of the element's points (general form)
+    float lim[GEN ? 2 : 1][GEN ? N1 : 1][kWarp];  // positivity limiter: per-layer weighted sums and minima
     float wpsi[5][kWarp];         // w psi of the tile's velocities
 };
 
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             const unsigned long long U1 = iso ? U0 : pack2(mm1, mm1);
             const unsigned long long U2 = iso ? 0ull : pack2(mm2, mm2);
             float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
+            float lsum = 0.f, lmin = 3.4e38f;  // limiter: this layer's weighted sum and minimum
             // two nodes at a time: the exponent a + b.m + q |m|^2 (+ the low part of q) and the range
             // reduction of 2^x in packed pairs
 #pragma unroll
@@ -301,8 +303,36 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                         gc = fmaf(cf, qv, cg);
                     }
                     const float o = fmaf(gc, g[sl], a);
-                    __stcs(dst + i * kWarp, o);
+                    if (GEN && A.limiter) {  // stored after the limiter below
+                        lsum = fmaf(A.ops.wq[q % N1] * A.ops.wq[q / N1], o, lsum);
+                        lmin = fminf(lmin, o);
+                    } else {
+                        __stcs(dst + i * kWarp, o);
+                    }
                     sm.wf[w][q][lane] = o;  // for the moments below (this warp's own rows)
+                }
+            }
+            if (GEN && A.limiter) {
+                // Zhang-Shu (Sec. 2.1, Eqs. 10-11): element mean and minimum of every velocity over
+                // the four layers, then the contraction of the values of this warp's layer
+                sm.lim[0][w][lane] = A.ops.wq[w] * lsum;
+                sm.lim[1][w][lane] = lmin;
+                __syncthreads();  // B3 (the general form only)
+                float mean = 0.f, mn = sm.lim[1][0][lane];
+#pragma unroll
+                for (int lw = 0; lw < N1; lw++) {
+                    mean += sm.lim[0][lw][lane];
+                    mn = fminf(mn, sm.lim[1][lw][lane]);
+                }
+                const float beta = mn < 0.f ? fminf(fabsf(mean / (mean - mn)), 1.f) : 1.f;
+#pragma unroll
+                for (int q = 0; q < NQ; q++) {
+                    float o = sm.wf[w][q][lane];
+                    if (mn < 0.f) {
+                        o = fmaf(beta, o - mean, mean);
+                        sm.wf[w][q][lane] = o;
+                    }
+                    __stcs(dst + (q + NQ * w) * kWarp, o);
                 }
             }
         } else {
@@ -405,8 +435,8 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
 {
     if (mode == 1)
         return launch3<N1, 1, 8, 0>(A, s);
-    // the lean form: periodic faces, no force, one velocity spacing on all axes
-    bool general = A.fpar != nullptr || !A.viso;
+    // the lean form: periodic faces, no force, no limiter, one velocity spacing on all axes
+    bool general = A.fpar != nullptr || !A.viso || A.limiter;
     for (int f = 0; f < 6; f++)
         general = general || A.mesh.bc[f] != 0;
     return general ? launch3_oct<N1, 1>(A, oct, s) : launch3_oct<N1, 0>(A, oct, s);
