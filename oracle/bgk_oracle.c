@@ -50,6 +50,7 @@ struct orc_ctx {
     double newton_tol;
     int newton_max;
     int continuous;         /* 1: g is the sampled continuous Maxwellian of Q (no Newton; ablation) */
+    double mu_ref, mu_omega; /* mu_ref > 0: tau = mu / P per point, mu = mu_ref theta^omega (Sec. 2, Eq. 5) */
     int limiter;            /* 1: Zhang-Shu positivity limiter on every stage output */
 };
 
@@ -514,6 +515,12 @@ void oracle_set_maxwellian(orc_ctx *c, int continuous) { c->continuous = continu
 
 void oracle_set_limiter(orc_ctx *c, int on) { c->limiter = on != 0; }
 
+void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega)
+{
+    c->mu_ref = mu_ref;
+    c->mu_omega = omega;
+}
+
 /* Zhang-Shu positivity limiter (Sec. 2.1, Eqs. 10-11), per element and velocity: with the element mean
  * fbar = sum_i W_i f_i / sum_i W_i (tensor Gauss-Legendre weights W) and fmin = min_i f_i, every node value
  * becomes fbar + beta (f_i - fbar), beta = min(|fbar / (fbar - fmin)|, 1), when some f_i < 0. */
@@ -803,10 +810,17 @@ int oracle_rhs(const orc_ctx *c, const double *f, double *L)
                 continue;
             }
         }
+        /* collision time: the constant tau, or mu(theta) / P of this point's state (P = rho theta) */
+        double tau = c->tau;
+        if (c->mu_ref > 0.0) {
+            const double rho = Q[0];
+            const double th = (2.0 / 3.0) * (Q[4] / rho - 0.5 * (Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]) / (rho * rho));
+            tau = c->mu_ref * pow(th, c->mu_omega) / (rho * th);
+        }
         for (int64_t k = 0; k < c->nvel; k++) {
             double g = maxwellian(P[0], P + 1, P[4], c->xi + 3 * k);
             if (c->collide)
-                Lp[k] += (g - fp[k]) / c->tau;
+                Lp[k] += (g - fp[k]) / tau;
             if (c->has_force) {
                 double psi[5], s = 0.0;
                 psi_of(c->xi + 3 * k, psi);

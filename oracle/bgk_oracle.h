@@ -109,6 +109,11 @@ void oracle_set_maxwellian(orc_ctx *c, int continuous);
 /* Zhang-Shu positivity limiter (Sec. 2.1, Eqs. 10-11) on every RK stage output: off by default. */
 void oracle_set_limiter(orc_ctx *c, int on);
 
+/* Variable collision time (Sec. 2, Eq. 5): with mu_ref > 0 every point relaxes with tau = mu / P,
+ * mu = mu_ref theta^omega (a power law, reference temperature 1) and P = rho theta of the point's
+ * moments; mu_ref <= 0 restores the constant tau given at creation (which must stay > 0). */
+void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega);
+
 /* Apply the limiter to f[n_x][N_v] in place (element mean with the tensor Gauss-Legendre weights). */
 int oracle_limit(const orc_ctx *c, double *f);
 

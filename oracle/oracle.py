@@ -72,6 +72,7 @@ def lib():
             L.oracle_set_maxwellian.argtypes = [C.c_void_p, C.c_int]
             L.oracle_set_limiter.argtypes = [C.c_void_p, C.c_int]
             L.oracle_limit.argtypes = [C.c_void_p, dp]
+            L.oracle_set_viscosity.argtypes = [C.c_void_p, C.c_double, C.c_double]
             _lib = L
     return _lib
 
@@ -221,6 +222,10 @@ class Problem:
     def set_maxwellian(self, continuous):
         """False: the discretely-conservative Maxwellian; True: the continuous one of Q (ablation)."""
         lib().oracle_set_maxwellian(self.h, int(bool(continuous)))
+
+    def set_viscosity(self, mu_ref, omega):
+        """tau = mu_ref theta^omega / (rho theta) per point (mu_ref <= 0: the constant tau)."""
+        lib().oracle_set_viscosity(self.h, float(mu_ref), float(omega))
 
     def set_limiter(self, on):
         lib().oracle_set_limiter(self.h, int(bool(on)))

@@ -175,3 +175,56 @@ def test_conservative_state_tends_to_the_moments_state():
         gaps.append(np.abs(P - state_of(Q)).max())
     assert gaps[1] < gaps[0] and gaps[2] < gaps[1] and gaps[3] < gaps[2]
     assert gaps[3] < 1e-6 * gaps[0]
+
+
+# ------------------------------------------------------------------------------------------------
+# variable collision time tau = mu(theta) / P (Sec. 2, Eq. 5)
+
+
+@pytest.mark.parametrize("rho,th", [(1.0, 1.0), (0.3, 1.6)])
+def test_variable_tau_space_homogeneous_closed_form(rho, th):
+    # a uniform non-equilibrium state keeps its moments, hence its tau = mu_ref theta^omega / P;
+    # the Shu-Osher steps of the linear relaxation then give f_n = M + (f_0 - M) R(-dt/tau)^n with
+    # R(z) = 1 + z + z^2/2 + z^3/6 exactly
+    mu_ref, omega = 2e-3, 0.81
+    pr = orc.Problem(1, [1], [0.0], [1.0], 1, (12, 12, 12), (-7.0,) * 3, (7.0,) * 3, 1.0)
+    a = pr.sample_maxwellian([rho, 0.3, 0.0, 0.0, th])
+    b = pr.sample_maxwellian([0.2 * rho, -1.0, 0.5, 0.0, 0.5 * th])
+    f0 = a + b
+    Q = pr.moments(np.tile(f0, (pr.npts, 1)))[0]
+    state = state_of(Q[None])[0]  # the mixture's (rho, U, theta): P = rho theta of it
+    tau = mu_ref * state[4] ** omega / (state[0] * state[4])
+    pr.set_newton(1e-14, 50)
+    P, _, _, bad = pr.conservative_maxwellian(Q[None])
+    assert bad == 0
+    M = pr.sample_maxwellian(P[0])
+    pr.set_f(np.tile(f0, (pr.npts, 1)))
+    pr.set_viscosity(mu_ref, omega)
+    dt, n = 0.4 * tau, 7
+    pr.step(dt, n)
+    z = -dt / tau
+    R = 1 + z + z * z / 2 + z**3 / 6
+    exact = M + (f0 - M) * R**n
+    assert np.abs(pr.get_f()[0] - exact).max() <= 1e-12 * f0.max()
+
+
+def test_variable_tau_differs_between_states_and_conserves():
+    # a periodic line with a density step: tau varies along the line (1 / rho), the totals stay
+    # constant to round-off
+    p, ne = 2, 6
+    pr = orc.Problem(1, [ne], [0.0], [1.0], p, (10, 10, 10), (-6.0,) * 3, (6.0,) * 3, 1.0)
+    x = pr.points()[:, 0]
+    P = np.zeros((pr.npts, 5))
+    P[:, 0] = np.where(x < 0.5, 1.0, 0.25)
+    P[:, 1] = 0.2
+    P[:, 4] = np.where(x < 0.5, 1.0, 1.5)
+    pr.set_state(P)
+    pr.set_viscosity(5e-3, 0.75)
+    _, w = orc.gauss_legendre(p + 1)
+
+    def tot(Q):
+        return (Q.reshape(ne, p + 1, 5) * w[None, :, None]).sum((0, 1))
+
+    T0 = tot(pr.moments())
+    pr.step(2e-3, 30)
+    assert np.abs(tot(pr.moments()) - T0).max() <= 1e-12 * np.abs(T0).max()
