@@ -87,6 +87,11 @@ typedef struct {
     int maxwellian;          /* BGK_MAXWELLIAN_CONSERVATIVE (0, the method) or BGK_MAXWELLIAN_CONTINUOUS
                                 (the ablation: g = the sampled continuous Maxwellian of the moments, whose
                                 discrete moments differ from them, Sec. 2.1, Eq. 13) */
+    double mu_ref;           /* > 0: variable collision time tau = mu / P per point (Sec. 2, Eq. 5) with the
+                                power law mu = mu_ref theta^mu_omega (reference temperature 1) and P = rho
+                                theta of the point's moments at every stage; the tau argument of bgk_create
+                                is then unused. FP32-split form: one velocity spacing on all axes. */
+    double mu_omega;
 } bgk_opts;
 
 #define BGK_MAXWELLIAN_CONSERVATIVE 0
@@ -141,7 +146,8 @@ int bgk_equilibrium(bgk_ctx *ctx, double *prim_out);
 /* Wait for the context's stream and return the sticky device status. */
 int bgk_synchronize(bgk_ctx *ctx);
 
-/* Explicit step size min(cfl / max_k sum_d |xi_kd| / h_d, tau). */
+/* Explicit step size min(cfl / max_k sum_d |xi_kd| / h_d, tau); with a variable collision time, the
+ * smallest tau of the current state (synchronises). */
 double bgk_dt(const bgk_ctx *ctx, double cfl);
 
 /* Tile-shape autotuner: times the stage kernel for several task lengths (32-velocity tiles per warp

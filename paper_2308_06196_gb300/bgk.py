@@ -42,7 +42,8 @@ class bgk_vgrid(C.Structure):
 class bgk_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("body_force", C.c_double * 3), ("newton_max_it", C.c_int),
                 ("newton_tol", C.c_double), ("limiter", C.c_int), ("chunks", C.c_int),
-                ("vtiles_per_task", C.c_int), ("maxwellian", C.c_int)]
+                ("vtiles_per_task", C.c_int), ("maxwellian", C.c_int), ("mu_ref", C.c_double),
+                ("mu_omega", C.c_double)]
 
 
 class BgkError(RuntimeError):
@@ -142,7 +143,7 @@ def make_vgrid(n, lo, hi) -> bgk_vgrid:
 
 
 def make_opts(precision=FP32_SPLIT, body_force=(0.0, 0.0, 0.0), newton_max_it=0, chunks=0, vtiles_per_task=0,
-              limiter=False, maxwellian=0):
+              limiter=False, maxwellian=0, mu_ref=0.0, mu_omega=0.0):
     """maxwellian: MAXWELLIAN_CONSERVATIVE (the method) or MAXWELLIAN_CONTINUOUS (the ablation)."""
     o = bgk_opts()
     o.precision = precision
@@ -154,6 +155,8 @@ def make_opts(precision=FP32_SPLIT, body_force=(0.0, 0.0, 0.0), newton_max_it=0,
     o.chunks = chunks
     o.vtiles_per_task = vtiles_per_task
     o.maxwellian = int(maxwellian)
+    o.mu_ref = float(mu_ref)
+    o.mu_omega = float(mu_omega)
     return o
 
 

@@ -195,6 +195,7 @@ struct bgk_ctx {
     double *rhow64 = nullptr, *fpar64 = nullptr, *w64 = nullptr;
     Ops64 ops64{};
     double *Q = nullptr, *prim = nullptr, *prim_in = nullptr;
+    double *itau64 = nullptr;  // per-point 1/tau of the FP64 form (variable collision time)
     int *err = nullptr;
     int64_t bytes = 0;
     Ops ops{};
@@ -276,6 +277,7 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.npts = (int)c->npts;
     A.inv_tau = (float)(1.0 / c->tau);
     A.limiter = c->opts.limiter != 0;
+    A.vtau = c->opts.mu_ref > 0.0;
     return A;
 }
 
@@ -311,6 +313,9 @@ NewtonArgs newton_args(bgk_ctx *c, int cold)
     N.err = c->err;
     N.cold = cold;
     N.continuous = c->opts.maxwellian == BGK_MAXWELLIAN_CONTINUOUS;
+    N.mu_ref = c->opts.mu_ref;
+    N.mu_omega = c->opts.mu_omega;
+    N.itau64 = c->itau64;
     N.it32 = c->opts.newton_max_it > 0 ? c->opts.newton_max_it : 2;
     N.it64 = 1;
     if (c->prec == BGK_FP64) {  // FP64 moments from k64_moments; FP64 Maxwellian parameters out
@@ -471,6 +476,7 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
             A.b = bb[st];
             A.dt = dt;
             A.inv_tau = 1.0 / c->tau;
+            A.itau = c->itau64;
             int64_t real = 0;
             for (int v = ch.vt0 * kWarp; v < (ch.vt0 + ch.nvt) * kWarp; v++)
                 real += c->slotk[v] >= 0;
@@ -582,7 +588,7 @@ void bgk_destroy(bgk_ctx *c)
     void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
-                    c->fpar64, c->w64};
+                    c->fpar64, c->w64, c->itau64};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -609,6 +615,8 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         c->opts = *opts;
     if (c->opts.precision != BGK_FP32_SPLIT && c->opts.precision != BGK_FP64)
         return bail(BGK_EINVAL, "precision must be BGK_FP32_SPLIT or BGK_FP64");
+    if (c->opts.mu_ref > 0.0 && !(std::isfinite(c->opts.mu_ref) && std::isfinite(c->opts.mu_omega)))
+        return bail(BGK_EINVAL, "mu_ref and mu_omega must be finite");
     if (c->opts.maxwellian != BGK_MAXWELLIAN_CONSERVATIVE && c->opts.maxwellian != BGK_MAXWELLIAN_CONTINUOUS)
         return bail(BGK_EINVAL, "maxwellian must be BGK_MAXWELLIAN_CONSERVATIVE or BGK_MAXWELLIAN_CONTINUOUS");
     c->prec = c->opts.precision;
@@ -668,6 +676,8 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         c->vlo[d] = vg->lo[d];
         c->dv[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
     }
+    if (c->opts.mu_ref > 0.0 && c->prec == BGK_FP32_SPLIT && !(c->dv[0] == c->dv[1] && c->dv[0] == c->dv[2]))
+        return bail(BGK_EINVAL, "a variable collision time needs one velocity spacing on all axes (FP32-split form)");
     c->nvel = (int64_t)c->nv[0] * c->nv[1] * c->nv[2];
     c->tau = tau;
     build_ops(p, c->ops, c->ops64, c->xg);
@@ -758,6 +768,8 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         AL(c->wpsi64, 5 * c->nslots);
         AL(c->ghost64, 6 * c->nslots);
         AL(c->par64, c->npts * 5);
+        if (c->opts.mu_ref > 0.0)
+            AL(c->itau64, c->npts);
     } else {
         AL(c->fA, fA);
         AL(c->pool, (c->chunks.size() + 1) * c->chunk_floats);
@@ -1083,7 +1095,20 @@ double bgk_dt(const bgk_ctx *c, double cfl)
             s += fabs(c->vlo[d] + kk[d] * c->dv[d]) / c->h[d];
         smax = std::max(smax, s);
     }
-    return std::min(cfl / smax, c->tau);
+    double tmin = c->tau;
+    if (c->opts.mu_ref > 0.0) {  // the smallest collision time of the current state
+        std::vector<double> Q(c->npts * 5);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+            cudaMemcpy(Q.data(), c->Q, Q.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return -1.0;
+        tmin = INFINITY;
+        for (int64_t i = 0; i < c->npts; i++) {
+            const double *q = &Q[i * 5];
+            const double rho = q[0], th = (2.0 / 3.0) * (q[4] / rho - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (rho * rho));
+            tmin = std::min(tmin, c->opts.mu_ref * pow(th, c->opts.mu_omega) / (rho * th));
+        }
+    }
+    return std::min(cfl / smax, tmin);
 }
 
 // Tile-shape autotuner: tiles per task G, per (mesh, degree, velocity grid), cached for the process.

@@ -77,6 +77,7 @@ struct StageArgs {
     float an, b;         // Shu-Osher coefficients: out = an f^n + b (f_s + dt L(f_s))
     float dt, inv_tau;
     int limiter;         // 1: Zhang-Shu positivity limiter on the stage output (Sec. 2.1, Eqs. 10-11)
+    int vtau;            // 1: per-point 1/tau in param slot 6 (variable collision time, one spacing only)
     float kb, kg;        // b (1 - dt / tau) and b dt / tau: the weights of f_s and of the Maxwellian.
                          // Rounded so that an + b = 1 and kb + kg = b hold exactly in FP32, so a state
                          // equal to f^n and to its Maxwellian is kept up to unbiased rounding.
@@ -97,6 +98,9 @@ struct NewtonArgs {
     int *err;              // status word (atomicOr)
     int cold;              // 1: ignore prim and start from the continuous state of Q
     int continuous;        // 1: no solve, g = the continuous Maxwellian of Q (ablation)
+    double mu_ref, mu_omega;  // mu_ref > 0: 1/tau = P / (mu_ref theta^omega) per point (Sec. 2, Eq. 5),
+                              // written to param slot 6 (FP32 kernels) and to itau64 (FP64 form)
+    double *itau64;           // [n_x] 1/tau of the plain FP64 form, or null
     int it32;              // FP32 Newton iterations
     int it64;              // FP64 refinements
     // 1-D velocity grids: xi_k = v0[d] + k dv[d], k < n[d]; trapezoid weights
@@ -129,6 +133,7 @@ struct Stage64Args {
     int N1, NP;
     int vt0, nvt, nslots;
     double an, b, dt, inv_tau;
+    const double *itau;    // [n_x] per-point 1/tau (variable collision time), or null: inv_tau
 };
 
 // FP64 moments of the stage output over all chunks (warp per point).

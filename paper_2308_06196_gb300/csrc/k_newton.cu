@@ -408,6 +408,12 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
             par[4 + d] = (float)(-0.5 * L2E * (0.25 * A.dv[d] * A.dv[d]) * it2);
     }
     par[7] = kExp2Magic + (float)j;
+    if (A.mu_ref > 0.0) {  // variable collision time of this point's state: 1/tau = rho theta / mu(theta)
+        const double itau = rho * thc / (A.mu_ref * pow(thc, A.mu_omega));
+        par[6] = (float)itau;
+        if (A.itau64)
+            A.itau64[pt] = itau;
+    }
     // body force: source S = g (beta . psi~) with M[g psi~ psi~^T] beta = M[S psi~] =
     // (0, rho F / s, rho (U - V) . F / s^2), whose raw moments are (0, rho F, rho U . F); written as
     // the polynomial q0 + q . xi + q4 |xi|^2 in the raw velocity

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k64_stage(const Stage64Args A)
         const double *p = A.par + ((int64_t)e * NP + i) * 5;
         const double r2 = (xi[0] - p[1]) * (xi[0] - p[1]) + (xi[1] - p[2]) * (xi[1] - p[2]) + (xi[2] - p[3]) * (xi[2] - p[3]);
         const double g = A.gmask[slot] * p[0] * exp(-r2 * p[4]);
-        double src = (g - fs) * A.inv_tau;
+        double src = (g - fs) * (A.itau ? A.itau[(int64_t)e * NP + i] : A.inv_tau);
         if (A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
             const double *q = A.fpar + ((int64_t)e * NP + i) * 5;
             src += g * (q[0] + q[1] * xi[0] + q[2] * xi[1] + q[3] * xi[2] + q[4] * (xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]));

@@ -140,7 +140,8 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
             m[c][q] = 0ull;
 
     const float kb = A.kb;
-    const float cdt = -A.mesh.inv_h2[0] * (A.b * A.dt);
+    const float bdt = A.b * A.dt;
+    const float cdt = -A.mesh.inv_h2[0] * bdt;
     const float cgt = A.kg;
 
 #pragma unroll
@@ -214,13 +215,19 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
                     ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)));
                 float g[2];
                 exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
+                const float itau[2] = {p67.x, p67.y};  // variable collision time: 1/tau of both nodes
 #pragma unroll
                 for (int sl = 0; sl < 2; sl++) {
                     const int i = 2 * h + sl;
                     if (i < NP) {
                         const float fnv = has_fn ? S.fn[wid][i][lane] : 0.f;
-                        const float a = fmaf(cd, sd[i], fmaf(A.an, fnv, kb * f[i]));
-                        o[i] = fmaf(cg, g[sl], a);
+                        float kbi = kb, cgi = cg;
+                        if (A.vtau) {  // per-node weights, rounded so that kb + kg = b exactly
+                            kbi = __fsub_rn(A.b, __fmul_rn(bdt, itau[sl]));
+                            cgi = __fsub_rn(A.b, kbi) * S.gm[lane];
+                        }
+                        const float a = fmaf(cd, sd[i], fmaf(A.an, fnv, kbi * f[i]));
+                        o[i] = fmaf(cgi, g[sl], a);
                     }
                 }
             }

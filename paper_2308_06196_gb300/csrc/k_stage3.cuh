@@ -177,8 +177,12 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             }
             // acc = an f^n + b (1 - dt/tau) f_s, then x and y lines from registers
 #pragma unroll
-            for (int q = 0; q < NQ; q++)
-                acc[q] = fmaf(A.an, acc[q], kb * f[q]);
+            for (int q = 0; q < NQ; q++) {
+                float kbq = kb;
+                if (GEN && A.vtau)  // variable collision time: b (1 - dt/tau) of this node, see below
+                    kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
+                acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
+            }
             const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt,
                         cz = -A.mesh.inv_h2[2] * x2 * bdt;
             // upwind value on a non-periodic face: the Dirichlet ghost Maxwellian, or the diffuse-wall
@@ -297,6 +301,10 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                     const int i = q + NQ * w;
                     const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
                     float gc = cg;
+                    if (GEN && A.vtau) {  // kg = b - kb exactly, kb as in the accumulator above
+                        const float itau = sl == 0 ? p67.x : p67.y;
+                        gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
+                    }
                     if (GEN && A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
                         const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
                         const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
@@ -435,8 +443,8 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
 {
     if (mode == 1)
         return launch3<N1, 1, 8, 0>(A, s);
-    // the lean form: periodic faces, no force, no limiter, one velocity spacing on all axes
-    bool general = A.fpar != nullptr || !A.viso || A.limiter;
+    // the lean form: periodic faces, no force, no limiter, constant tau, one velocity spacing on all axes
+    bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
     for (int f = 0; f < 6; f++)
         general = general || A.mesh.bc[f] != 0;
     return general ? launch3_oct<N1, 1>(A, oct, s) : launch3_oct<N1, 0>(A, oct, s);

@@ -1,6 +1,7 @@
 """The widened rows on the GPU against the FP64 oracle: the Zhang-Shu positivity limiter (Sec. 2.1,
-Eqs. 10-11) in the line kernel, the general hexahedral kernel and the plain all-FP64 form, and the
-non-conservative ablation (the continuous Maxwellian of the moments, Sec. 2.1, Eq. 13)."""
+Eqs. 10-11) in the line kernel, the general hexahedral kernel and the plain all-FP64 form, the
+non-conservative ablation (the continuous Maxwellian of the moments, Sec. 2.1, Eq. 13) and the
+variable collision time tau = mu(theta) / P (Sec. 2, Eq. 5)."""
 import numpy as np
 import pytest
 
@@ -129,3 +130,23 @@ def test_batch_with_limiter_equals_members_alone():
     for q, (xa, xb) in enumerate(zip(alone, batched)):
         assert rel(xb.moments(), xa.moments()) <= 1e-6, q
     b.close()
+
+
+def test_variable_tau_line_and_hexahedra():
+    # tau = mu(theta) / P varies along a Sod tube: line kernel (FP32-split), general hexahedral kernel
+    # (FP32-split) and the FP64 form against the oracle
+    bc, bcs = tube()
+    for dim, ne, p, N, precision, tol in ((1, [10], 3, 12, 0, 1e-5), (3, [4, 2, 2], 2, 8, 0, 1e-5),
+                                          (3, [4, 2, 2], 2, 8, 1, 1e-10)):
+        extra = dict(chunks=1) if dim == 1 else {}
+        s, pr = make(dim, ne, p, N, 7.0, 1.0, bc, bcs, precision=precision, mu_ref=2e-3, mu_omega=0.81, **extra)
+        pr.set_viscosity(2e-3, 0.81)
+        prim = W.prim_sod(pr.points(), (1.0, 1.0), (0.125, 0.8))
+        s.set_state(prim)
+        pr.set_state(prim)
+        dt = min(pr.dt(0.1), s.dt(0.1))
+        assert dt < 1.0  # the state's smallest tau, not the unused constant
+        s.step(dt, 6)
+        pr.step(dt, 6)
+        assert rel(s.moments(), pr.moments()) < tol, (dim, precision)
+        assert rel(s.get_f(), pr.get_f()) < tol, (dim, precision)
