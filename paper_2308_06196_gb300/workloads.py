@@ -31,6 +31,13 @@ CONFIGS = {
                     bc=((PERIODIC, PERIODIC), (WALL, WALL), (PERIODIC, PERIODIC)),
                     bc_state=(((0,) * 5, (0,) * 5), ((0, 0, 0, 0, 1.0), (0, 0, 0, 0, 1.0)), ((0,) * 5, (0,) * 5)),
                     force=(0.01, 0.0, 0.0)),
+    # Mach-5 normal shock in a square duct: 128 x 8 x 8 hexahedra at p = 2 on [0, 16] x [0, 1]^2 (cubic
+    # elements), periodic y and z, Dirichlet x-ends with the upstream / downstream states, 48^3
+    # velocities on [-14, 14]^3, tau = 5e-4; the step at x = 8. The positivity limiter is on: without
+    # it the p = 2 solution undershoots at the shock and some point's moments stop admitting a
+    # Maxwellian within a few steps (in FP32 and FP64 alike)
+    "mach5": dict(dim=3, nelem=(128, 8, 8), lo=(0.0,) * 3, hi=(16.0, 1.0, 1.0), p=2, nv=(48, 48, 48),
+                  vlo=(-14.0,) * 3, vhi=(14.0,) * 3, tau=5e-4, cfl=0.1, steps=20, mach=5.0, limiter=True),
     # ensemble of independent 1-D Sod shock tubes on [0, 1] (interface at x = 1/2, gas at rest, Dirichlet
     # ends), drawn from one seed: elements U{16..128}, p U{2, 3}, velocity grid N^3 on [-8, 8]^3 with
     # N in {12, 16, 24, 32}, (rho, T) of each side U[0.125, 1] x U[0.8, 1.25], tau log-uniform [1e-4, 1e-1]
@@ -104,6 +111,36 @@ def sod_members(members: int = 256, seed: int = 0, elements=(16, 128), degrees=(
                                   ((0,) * 5, (0,) * 5)),
                         left=(rl, tl), right=(rr, tr)))
     return out
+
+
+def rankine_hugoniot(mach: float, gamma: float = 5.0 / 3.0):
+    """Upstream (rho, u, T) = (1, M sqrt(gamma), 1) and the downstream state of the normal shock that is
+    steady in this frame: rho2 = (gamma+1) M^2 / ((gamma-1) M^2 + 2), p2 = 1 + 2 gamma (M^2 - 1) / (gamma+1),
+    u2 = u1 / rho2, T2 = p2 / rho2 (R = 1)."""
+    u1 = mach * math.sqrt(gamma)
+    r2 = (gamma + 1.0) * mach**2 / ((gamma - 1.0) * mach**2 + 2.0)
+    p2 = 1.0 + 2.0 * gamma * (mach**2 - 1.0) / (gamma + 1.0)
+    return (1.0, u1, 1.0), (r2, u1 / r2, p2 / r2)
+
+
+def mach5_bc(c: dict):
+    """Boundary kinds and states of the duct: Dirichlet x-ends (upstream, downstream), periodic y, z."""
+    (r1, u1, t1), (r2, u2, t2) = rankine_hugoniot(c["mach"])
+    bc = ((DIRICHLET, DIRICHLET), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC))
+    bcs = (((r1, u1, 0.0, 0.0, t1), (r2, u2, 0.0, 0.0, t2)), ((0,) * 5, (0,) * 5), ((0,) * 5, (0,) * 5))
+    return bc, bcs
+
+
+def prim_mach5(x: np.ndarray, c: dict) -> np.ndarray:
+    """The Rankine-Hugoniot step at the middle of the duct."""
+    (r1, u1, t1), (r2, u2, t2) = rankine_hugoniot(c["mach"])
+    xm = 0.5 * (c["lo"][0] + c["hi"][0])
+    up = x[:, 0] < xm
+    P = np.zeros((len(x), 5))
+    P[:, 0] = np.where(up, r1, r2)
+    P[:, 1] = np.where(up, u1, u2)
+    P[:, 4] = np.where(up, t1, t2)
+    return P
 
 
 def prim_sod(x: np.ndarray, left, right) -> np.ndarray:
