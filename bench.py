@@ -204,6 +204,128 @@ def bench_batch(steps: int, warmup: int, stream, torch, members: int = 0) -> dic
     return out
 
 
+def timed_steps(s, dt, steps, warmup, stream, torch):
+    """ms per step through the graph, and the stage timing of the same number of steps."""
+    s.step(dt, warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(dt, steps)
+    e1.record(stream)
+    s.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.set_timing(True)
+    s.step(dt, steps)
+    tm = s.timing()
+    s.set_timing(False)
+    s.synchronize()
+    stage_avg = tm["stage_ms"] / max(1, tm["stage_launches"])
+    return ms, {"stage_avg_ms": stage_avg, "stage_achieved_gbs": tm["stage_alg_bytes"] / (stage_avg * 1e-3) / 1e9,
+                "newton_avg_ms": tm["newton_ms"] / max(1, tm["newton_launches"])}
+
+
+def bench_mach5(steps: int, warmup: int, stream, torch) -> dict:
+    """The Mach-5 duct at full size in the FP32-split form (positivity limiter on, general kernel),
+    then the plain all-FP64 form on the one-element-wide duct of the same x-mesh for the same steps:
+    the flow is y/z-homogeneous, so the two must agree; their moments' largest scaled difference."""
+    from paper_2308_06196_gb300.bgk import FP64, Solver
+
+    c = W.config("mach5")
+    bc, bcs = W.mach5_bc(c)
+    k = W.mesh_kwargs(c)
+    s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"], bc=bc,
+               bc_state=bcs, limiter=c["limiter"])
+    s.set_stream(stream.cuda_stream)
+    prim = W.prim_mach5(s.points(), c)
+    s.set_state(prim)
+    g = s.autotune()
+    dt = s.dt(c["cfl"])
+    ms, st = timed_steps(s, dt, steps, warmup, stream, torch)
+    total = warmup + 2 * steps
+    Q = s.moments()
+    dof, npts = s.ndof, s.npts
+    s.close()
+    ne, n1 = c["nelem"], c["p"] + 1
+    Qx = Q.reshape(ne[2], ne[1], ne[0], n1, n1, n1, 5).transpose(2, 5, 0, 1, 3, 4, 6).reshape(ne[0], n1, -1, 5)
+    hy = (c["hi"][1] - c["lo"][1]) / ne[1]
+    c64 = dict(c, nelem=(ne[0], 1, 1), hi=(c["hi"][0], hy, hy))
+    k64 = W.mesh_kwargs(c64)
+    s64 = Solver(k64["dim"], k64["nelem"], k64["lo"], k64["hi"], k64["p"], k64["nv"], k64["vlo"], k64["vhi"],
+                 k64["tau"], bc=bc, bc_state=bcs, limiter=c["limiter"], precision=FP64)
+    s64.set_stream(stream.cuda_stream)
+    s64.set_state(W.prim_mach5(s64.points(), c64))
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s64.step(dt, 1)
+    torch.cuda.synchronize()
+    h0.record(stream)
+    s64.step(dt, total - 1)
+    h1.record(stream)
+    Q64 = s64.moments().reshape(ne[0], n1, n1, n1, 5)[:, 0, 0, :, :]
+    ms64 = h0.elapsed_time(h1) / (total - 1)
+    dof64 = s64.ndof
+    s64.close()
+    rho = Q64[..., 0]
+    th = (2.0 / 3.0) * (Q64[..., 4] / rho - 0.5 * (Q64[..., 1:4] ** 2).sum(-1) / rho**2)
+    scale = np.array([rho.max()] + [(rho * np.sqrt(th)).max()] * 3 + [Q64[..., 4].max()])
+    homog = float(np.abs(Qx - Qx[:, :, :1]).max())
+    err = float((np.abs(Qx[:, :, 0, :] - Q64) / scale).max())
+    return {"workload": "mach5", "dof": dof, "n_x": npts, "value": dof * 3 / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, **st, "tiles_per_task": g, "limiter": True, "steps_compared": total,
+            "yz_homogeneity_max_abs_diff": homog,
+            "fp64_narrow_duct": {"dof": dof64, "value": dof64 * 3 / (ms64 * 1e-3), "unit": UNIT,
+                                 "ms_per_step": ms64, "moments_max_rel_diff_fp32_split": err}}
+
+
+def bench_variants(steps: int, warmup: int, stream, torch, k: dict, prim_dev, dt: float) -> dict:
+    """The Taylor-Green workload with the widened rows switched on one at a time: the positivity
+    limiter and the variable collision time (both in the general hexahedral kernel), and the
+    continuous-Maxwellian ablation (no Newton solve)."""
+    from paper_2308_06196_gb300.bgk import MAXWELLIAN_CONTINUOUS, Solver
+
+    out = {}
+    for name, opts in (("limiter", dict(limiter=True)),
+                       ("variable_tau", dict(mu_ref=1e-3, mu_omega=0.81)),
+                       ("continuous_maxwellian", dict(maxwellian=MAXWELLIAN_CONTINUOUS))):
+        s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"], **opts)
+        s.set_stream(stream.cuda_stream)
+        s.set_state(prim_dev)
+        s.autotune()
+        ms, st = timed_steps(s, min(dt, s.dt(0.1)), steps, warmup, stream, torch)
+        out[name] = {"value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, **st}
+        s.close()
+    return out
+
+
+def bench_ablation() -> dict:
+    """The paper's central claim (Sec. 2.1, Eq. 13 and the text after it), measured: the drift of the
+    total mass and energy of a periodic 3-D box after 20 steps with the discretely-conservative
+    Maxwellian and with the sampled continuous one, for velocity grids of 8^3, 12^3 and 16^3."""
+    from paper_2308_06196_gb300.bgk import MAXWELLIAN_CONTINUOUS, MAXWELLIAN_CONSERVATIVE, Solver
+
+    # the discrete spatial integral: tensor Gauss-Legendre weights of the p = 2 nodes (x fastest)
+    w = np.polynomial.legendre.leggauss(3)[1]
+    Wn = np.einsum("i,j,k->kji", w, w, w).ravel()
+
+    def total(Q):
+        return (Q.reshape(-1, Wn.size, 5) * Wn[None, :, None]).sum((0, 1))
+
+    out = {}
+    for N in (8, 12, 16):
+        row = {}
+        for name, mode in (("conservative", MAXWELLIAN_CONSERVATIVE), ("continuous", MAXWELLIAN_CONTINUOUS)):
+            s = Solver(3, [4, 4, 4], [0.0] * 3, [1.0] * 3, 2, (N, N, N), (-5.0,) * 3, (5.0,) * 3, 5e-3,
+                       maxwellian=mode)
+            s.set_state(W.smooth_prim(s.points(), 3, seed=1, amp=0.3))
+            Q0 = total(s.moments())
+            s.step(s.dt(0.1), 20)
+            d = np.abs(total(s.moments()) - Q0)
+            row[name] = float(max(d[0] / abs(Q0[0]), d[4] / abs(Q0[4])))
+            s.close()
+        out[f"N{N}"] = row
+    return {"workload": "periodic box 4^3 hex p=2, tau=5e-3, 20 steps", "metric": "max relative drift of total "
+            "mass and energy", **out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +338,10 @@ def main():
                     help="steps of the plain all-FP64 form timed for the comparison (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="steps of the batched Sod ensemble (0: skip)")
+    ap.add_argument("--mach5-steps", type=int, default=3, help="steps of the Mach-5 duct (0: skip)")
+    ap.add_argument("--variant-steps", type=int, default=3,
+                    help="steps of the Taylor-Green variants: limiter, variable tau, ablation (0: skip)")
+    ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--batch-members", type=int, default=0,
                     help="members of the Sod ensemble (default: the workload's 256); smaller for profiling")
     ap.add_argument("--elements", type=int, default=0,
@@ -356,10 +482,17 @@ def main():
                 "moments_max_rel_diff_fp32_split": err}
         s64.close()
 
+    s.close()  # the other workloads' buffers replace the Taylor-Green ones
+    variants = None
+    if args.variant_steps > 0 and world == 1:
+        variants = bench_variants(args.variant_steps, warmup, stream, torch, k, prim_dev, dt)
     batch = None
     if args.batch_steps > 0:
-        s.close()  # the ensemble's own buffers replace the Taylor-Green ones
         batch = bench_batch(args.batch_steps, warmup, stream, torch, args.batch_members)
+    mach5 = None
+    if args.mach5_steps > 0 and world == 1:
+        mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch)
+    ablation = None if (args.no_ablation or world > 1) else bench_ablation()
 
     ms_t = torch.tensor([ms, graph_ms, e2e_ms], dtype=torch.float64, device="cuda")
     if dist:
@@ -407,6 +540,9 @@ def main():
         "gpu_launches": launches,
         "fp64_form": None if fp64 is None else dict(fp64, speedup_of_fp32_split=value / world / fp64["value"]),
         "batched": batch,
+        "mach5": mach5,
+        "variants": variants,
+        "ablation": ablation,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

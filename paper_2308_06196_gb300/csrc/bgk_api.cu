@@ -877,6 +877,10 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         (c->prec != BGK_FP64 && (rc = cudaMemset(c->fA, 0, fA * 4))) || (rc = cudaMemset(c->err, 0, 4)) ||
         (rc = cudaMemset(c->prim, 0, c->npts * 5 * 8)) || (rc = cudaMemset(c->param, 0, c->npts * kParamStride * 4)))
         return bail(BGK_ECUDA, std::string("device set-up copy failed: ") + cudaGetErrorString(rc));
+    // the set-up memsets may still run on the legacy stream, which work on a non-blocking stream
+    // (the context's own, or the caller's) does not wait for: finish them here
+    if ((rc = cudaDeviceSynchronize()) != cudaSuccess)
+        return bail(BGK_ECUDA, std::string("device set-up failed: ") + cudaGetErrorString(rc));
     if (prepare_stage(c->dim, p) != cudaSuccess)
         return bail(BGK_ECUDA, "stage kernel attribute set-up failed");
     if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess)
@@ -1461,6 +1465,8 @@ int bgk_batch_create(int n, bgk_ctx *const *probs, bgk_batch **out)
         e = cudaMalloc((void **)&b->err, sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemset(b->err, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();  // the memset on the legacy stream, before any non-blocking stream's work
     // the line operators of every degree present, for the constant table of the persistent launch
     bool done[kMaxN1 + 1] = {false};
     for (int q = 0; q < n && e == cudaSuccess; q++) {
