@@ -204,6 +204,21 @@ def bench_batch(steps: int, warmup: int, stream, torch, members: int = 0) -> dic
     return out
 
 
+def max_over_ranks(values, dist, device):
+    """Each timing's maximum over all ranks: the slowest replica sets the job's time."""
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_value(dof_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job DOF-stage updates per second: every rank steps its own replica of the workload."""
+    return dof_per_rank * 3 * world / (ms_per_step * 1e-3)
+
+
 def timed_steps(s, dt, steps, warmup, stream, torch):
     """ms per step through the graph, and the stage timing of the same number of steps."""
     s.step(dt, warmup)
@@ -494,13 +509,9 @@ def main():
         mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch)
     ablation = None if (args.no_ablation or world > 1) else bench_ablation()
 
-    ms_t = torch.tensor([ms, graph_ms, e2e_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms, graph_ms, e2e_ms = ms_t.tolist()
-    nrep = world
-    value = dof * 3 * nrep / (ms * 1e-3)
-    e2e_value = dof * 3 * nrep / (e2e_ms * 1e-3)
+    ms, graph_ms, e2e_ms = max_over_ranks([ms, graph_ms, e2e_ms], dist, "cuda")
+    value = job_value(dof, world, ms)
+    e2e_value = job_value(dof, world, e2e_ms)
 
     stage_avg_ms = tm["stage_ms"] / max(1, tm["stage_launches"])
     achieved = tm["stage_alg_bytes"] / (stage_avg_ms * 1e-3) / 1e9
