@@ -66,14 +66,6 @@ struct alignas(16) LineSmem {  // cp.async and the 16-byte parameter loads need 
     float par[kWarpsPerCta][(N1 + 1) / 2][kParamStride][2];
 };
 
-// Asynchronous copy of `rows` 128-byte rows from g to s by the CTA's threads (16 bytes per copy).
-__device__ __forceinline__ void copy_rows(float *s, const float *g, int rows)
-{
-    const int n = rows * (kWarp / 4);
-    for (int k = threadIdx.x; k < n; k += blockDim.x)
-        cp_async16(s + 4 * k, g + 4 * k);
-}
-
 // One task of the line-element stage: a block of kWarpsPerCta consecutive elements (warp w takes
 // element eb + w) x a run of G tiles. The CTA streams the tiles through a kLineDepth-deep ring of
 // shared slots (cp.async, kLineDepth - 1 tiles ahead), so every warp reads its element, its upwind
@@ -104,20 +96,51 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
     const int eoR = upwind_neighbour(A.mesh, ec, 0, false);
     const bool has_fn = MODE == 0 && A.fn != nullptr;
 
+    // Copy plan of the task, fixed for all its tiles (16-byte chunks; a slot's rows nb, mi, wp, gm
+    // are contiguous in shared memory): the element block's f_s and f^n rows (stride tileA per tile)
+    // and at most one table chunk per thread: a row of the outside neighbour (its element depends on
+    // the tile's inflow side), of the grid index, of w psi or of the mask.
+    const int tid = threadIdx.x;
+    constexpr int CH = kWarp / 4;  // chunks per 128-byte row
+    const int nA = ne * NP * CH;
+    const int64_t tileA = (int64_t)E * NP * kWarp;
+    const float *gA = A.src + (int64_t)eb * NP * kWarp;
+    const float *gB = has_fn ? A.fn + (int64_t)eb * NP * kWarp : nullptr;
+    const float *gC = nullptr;
+    int64_t sC = 0;
+    int cnb = -1;  // >= 0: this thread copies chunk cnb of the outside neighbour's rows
+    if (MODE == 0) {
+        const int q = tid - N1 * CH;
+        if (tid < N1 * CH)
+            cnb = 4 * tid;
+        else if (q < 3 * CH) {
+            gC = A.mi + (int64_t)(q / CH) * A.nslots + (int64_t)A.vt0 * kWarp + 4 * (q % CH);
+            sC = kWarp;
+        } else if (q < 8 * CH) {
+            gC = A.wpsi + (int64_t)A.vt0 * 5 * kWarp + 4 * (q - 3 * CH);
+            sC = 5 * kWarp;
+        } else if (q < 9 * CH) {
+            gC = A.gmask + (int64_t)A.vt0 * kWarp + 4 * (q - 8 * CH);
+            sC = kWarp;
+        }
+    } else if (tid < 5 * CH) {  // moments only: the w psi rows
+        gC = A.wpsi + (int64_t)A.vt0 * 5 * kWarp + 4 * tid;
+        sC = 5 * kWarp;
+    }
     auto prefetch = [&](int vl, int slot) {
         LineSlot<N1> &S = sm.s[slot];
-        const int vt = A.vt0 + vl;
-        copy_rows(&S.fs[0][0][0], A.src + fidx(vl, eb, 0, 0, E, NP), ne * NP);
-        copy_rows(&S.wp[0][0], A.wpsi + (int64_t)vt * 5 * kWarp, 5);
-        if (MODE == 0) {
-            if (has_fn)
-                copy_rows(&S.fn[0][0][0], A.fn + fidx(vl, eb, 0, 0, E, NP), ne * NP);
-            const int eo = (__ldg(A.toct + vt) & 1) ? eoL : eoR;
+        for (int k = tid; k < nA; k += blockDim.x)
+            cp_async16(&S.fs[0][0][0] + 4 * k, gA + vl * tileA + 4 * k);
+        if (MODE == 0 && has_fn)
+            for (int k = tid; k < nA; k += blockDim.x)
+                cp_async16(&S.fn[0][0][0] + 4 * k, gB + vl * tileA + 4 * k);
+        float *tables = MODE == 0 ? &S.nb[0][0] : &S.wp[0][0];
+        if (cnb >= 0) {
+            const int eo = (__ldg(A.toct + A.vt0 + vl) & 1) ? eoL : eoR;
             if (eo >= 0)
-                copy_rows(&S.nb[0][0], A.src + fidx(vl, eo, 0, 0, E, NP), N1);
-            for (int d = 0; d < 3; d++)
-                copy_rows(&S.mi[d][0], A.mi + (int64_t)d * A.nslots + (int64_t)vt * kWarp, 1);
-            copy_rows(&S.gm[0], A.gmask + (int64_t)vt * kWarp, 1);
+                cp_async16(tables + cnb, A.src + fidx(vl, eo, 0, 0, E, NP) + cnb);
+        } else if (gC) {
+            cp_async16(tables + 4 * tid, gC + vl * sC);
         }
     };
 
