@@ -151,7 +151,7 @@ int bgk_synchronize(bgk_ctx *ctx);
 double bgk_dt(const bgk_ctx *ctx, double cfl);
 
 /* Tile-shape autotuner: times the stage kernel for several task lengths (32-velocity tiles per warp
- * task: 2, 4, 8, 16) on this context's own buffers, keeps the fastest for this context and caches it
+ * task: 2, 4, ..., 64) on this context's own buffers, keeps the fastest for this context and caches it
  * per (dim, degree, velocity grid, mesh, chunking) for the rest of the process. Does not change f,
  * the moments or the equilibrium; invalidates the captured graph. *g_out (may be NULL) receives the
  * chosen length (0 for the all-FP64 form, which has no task shape). */
@@ -186,8 +186,8 @@ int bgk_timing(bgk_ctx *ctx, double *stage_ms, int64_t *stage_launches, double *
  * bgk_batch_synchronize: waits for the batch stream and returns the status of all members' Newton
  *   solves (BGK_EDOMAIN / BGK_ENEWTON also become sticky in every member).
  * bgk_batch_autotune: the tile-shape autotuner of the batch: for every (degree, velocity grid) class
- *   of members in turn, times the persistent stage launch with the class's task length at 2, 4, 8
- *   and 16 tiles (the other classes fixed) and keeps the fastest. Changes no state.
+ *   of members in turn, times the persistent stage launch with the class's task length at 2, 4, ...,
+ *   64 tiles (the other classes fixed) and keeps the fastest. Changes no state.
  * bgk_batch_info: total points, degrees of freedom and stage tasks of the batch.
  * bgk_batch_set_timing / bgk_batch_timing: as bgk_set_timing / bgk_timing, for the batch launches.
  * ------------------------------------------------------------------------------------------- */

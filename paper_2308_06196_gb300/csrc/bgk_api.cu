@@ -1161,7 +1161,7 @@ int bgk_autotune(bgk_ctx *c, int *g_out)
     float best = 1e30f;
     int bestG = c->G;
     const int C = (int)c->chunks.size();
-    for (int G = kMinTuneG; G <= 16 && G <= std::max(kMinTuneG, maxc); G *= 2) {
+    for (int G = kMinTuneG; G <= 64 && G <= std::max(kMinTuneG, maxc); G *= 2) {
         set_task_length(c, G);
         float tot = 0.f;
         for (int rep = 0; rep < 3; rep++) {
@@ -1613,7 +1613,7 @@ int bgk_batch_autotune(bgk_batch *b)
     for (size_t k = 0; k < rep.size(); k++) {
         float best = 1e30f;
         int bestG = b->probs[rep[k]]->G;
-        for (int G = kMinTuneG; G <= 16; G *= 2) {
+        for (int G = kMinTuneG; G <= 64; G *= 2) {
             for (int q = 0; q < b->n; q++)
                 if (cls[q] == (int)k)
                     set_task_length(b->probs[q], G);

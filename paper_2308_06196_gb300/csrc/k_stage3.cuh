@@ -3,9 +3,12 @@
 #pragma once
 #include "stage_common.cuh"
 
-// Resident CTAs per SM the register allocation is sized for (p = 3 / p = 2 / p = 1).
+// Resident CTAs per SM the register allocation is sized for (p = 3 lean and general / p = 2 / p = 1).
 #ifndef BGK_STAGE3_MINCTAS_P3
-#define BGK_STAGE3_MINCTAS_P3 4
+#define BGK_STAGE3_MINCTAS_P3 5
+#endif
+#ifndef BGK_STAGE3_MINCTAS_P3_GEN
+#define BGK_STAGE3_MINCTAS_P3_GEN 4
 #endif
 #ifndef BGK_STAGE3_MINCTAS_P2
 #define BGK_STAGE3_MINCTAS_P2 6
@@ -26,7 +29,7 @@ struct Stage3Smem {
     float tile[2][NP][kWarp];     // f_s of the element, [node][lane], double-buffered (cp.async)
     float fnb[NP][kWarp];         // f^n of the element (each warp its own layer), refilled after use
     float zc[NP][kWarp];          // z-derivative sums, [node][lane]
-    float wf[N1][16][36];         // per warp: its layer's stage output, [node][velocity] (16 rows)
+    float msum[N1][10][kWarp];    // per warp and lane: running moment sums of its 2 nodes x 5 moments
     // BGK exponents of the element's points by layer and node pair, [layer][pair][param][node of the
     // pair], so that one 16-byte load gives two parameters of both nodes (odd layers repeat the last node)
     float par[N1][(N1 * N1 + 1) / 2][kParamStride][2];
@@ -41,7 +44,8 @@ struct Stage3Smem {
 // the Maxwellian exponent needs only the sum of the squared grid indices); GEN = 1: Dirichlet and
 // diffuse-wall faces, the body-force source and per-axis spacings.
 template <int N1, int MODE, int OCT, int GEN>
-__global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
+__global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTAS_P3_GEN : BGK_STAGE3_MINCTAS_P3)
+                                               : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
 {
     constexpr int NQ = N1 * N1;      // nodes per layer
     constexpr int NP = NQ * N1;
@@ -78,15 +82,15 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
         }
     }
     // moment sums: lane = (node pair np = lane / 4: layer nodes np and np + 8) x (velocity eighth
-    // kg = lane % 4: velocities 8 kg .. 8 kg + 7 of every tile); FP32 pairs over even/odd velocities,
-    // accumulated over the whole task and combined across the 4 lanes of a pair at the end
+    // kg = lane % 4: velocities 8 kg .. 8 kg + 7 of every tile); FP32 pairs over even/odd velocities
+    // per tile, added to running sums in shared memory (no registers held across the tile), combined
+    // across the 4 lanes of a pair at the end. The stage output of the warp's layer is transposed
+    // through the layer's own rows of the tile buffer, free once the z-lines have read them (B2), with
+    // the 4-float column groups of row q rotated by q mod 8 (conflict-free writes and reads).
     const int np = lane >> 2, kg = lane & 3;
-    unsigned long long ms[2][5];
 #pragma unroll
-    for (int h = 0; h < 2; h++)
-#pragma unroll
-        for (int c = 0; c < 5; c++)
-            ms[h][c] = 0ull;
+    for (int m = 0; m < 10; m++)
+        sm.msum[w][m][lane] = 0.f;
     const float kb = A.kb;
     const float bdt = A.b * A.dt;
 
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                     } else {
                         __stcs(dst + i * kWarp, o);
                     }
-                    sm.wf[w][q][lane] = o;  // for the moments below (this warp's own rows)
+                    sm.tile[b][q + NQ * w][lane ^ (4 * (q & 7))] = o;  // for the moments below
                 }
             }
             if (GEN && A.limiter) {
@@ -335,10 +339,11 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
                 const float beta = mn < 0.f ? fminf(fabsf(mean / (mean - mn)), 1.f) : 1.f;
 #pragma unroll
                 for (int q = 0; q < NQ; q++) {
-                    float o = sm.wf[w][q][lane];
+                    float &slot_o = sm.tile[b][q + NQ * w][lane ^ (4 * (q & 7))];
+                    float o = slot_o;
                     if (mn < 0.f) {
                         o = fmaf(beta, o - mean, mean);
-                        sm.wf[w][q][lane] = o;
+                        slot_o = o;
                     }
                     __stcs(dst + (q + NQ * w) * kWarp, o);
                 }
@@ -353,10 +358,16 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             __syncthreads();  // B2
 #pragma unroll
             for (int q = 0; q < NQ; q++)
-                sm.wf[w][q][lane] = f[q];
+                sm.tile[b][q + NQ * w][lane ^ (4 * (q & 7))] = f[q];
         }
         // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values
         __syncwarp();
+        unsigned long long pm[2][5];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int c = 0; c < 5; c++)
+                pm[h][c] = 0ull;
 #pragma unroll
         for (int k = 0; k < 8; k += 4) {
             const int kk = 8 * kg + k;
@@ -369,15 +380,21 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
             }
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const float4 v = *reinterpret_cast<const float4 *>(&sm.wf[w][np + 8 * h][kk]);
+                const int row = min(np + 8 * h, NQ - 1);  // rows past the layer: discarded below
+                const float4 v = *reinterpret_cast<const float4 *>(&sm.tile[b][row + NQ * w][kk ^ (4 * (row & 7))]);
                 const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
 #pragma unroll
                 for (int c = 0; c < 5; c++) {
-                    ms[h][c] = ffma2(wv[c][0], v01, ms[h][c]);
-                    ms[h][c] = ffma2(wv[c][1], v23, ms[h][c]);
+                    pm[h][c] = ffma2(wv[c][0], v01, pm[h][c]);
+                    pm[h][c] = ffma2(wv[c][1], v23, pm[h][c]);
                 }
             }
         }
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int c = 0; c < 5; c++)
+                sm.msum[w][5 * h + c][lane] += sum2(pm[h][c]);
         __syncwarp();
     }
     // partial moments of this task: combine the 4 velocity eighths of every node pair
@@ -387,7 +404,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3_MINCTAS_P3 : 
         const int q = np + 8 * h;
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            float x = sum2(ms[h][c]);
+            float x = sm.msum[w][5 * h + c][lane];
             x += __shfl_xor_sync(0xffffffffu, x, 1);
             x += __shfl_xor_sync(0xffffffffu, x, 2);
             if (kg == 0 && q < NQ)
