@@ -117,8 +117,8 @@ __device__ __forceinline__ float exp2_fp32(float x, float kmagic)
     return __int_as_float(__float_as_int(p) + (__float_as_int(t) << 23));
 }
 
-// exp2_fp32 of two values at once: the range reduction in packed FP32 pairs, the polynomial per value
-// (its coefficients as immediates). x holds the two arguments, kmagic their two rounding constants.
+// exp2_fp32 of two values at once, every step on packed FP32 pairs (the same coefficients, duplicated).
+// x holds the two arguments, kmagic their two rounding constants.
 __device__ __forceinline__ void exp2_fp32x2(unsigned long long x, unsigned long long kmagic, float &y0, float &y1)
 {
     float x0, x1;
@@ -126,22 +126,18 @@ __device__ __forceinline__ void exp2_fp32x2(unsigned long long x, unsigned long 
     const unsigned long long xc = pack2(fmaxf(x0, -100.0f), fmaxf(x1, -100.0f));
     const unsigned long long t = fadd2(xc, kmagic);
     const unsigned long long r = fsub2(xc, fsub2(t, kmagic));
-    float r0, r1, t0, t1;
-    unpack2(r, r0, r1);
+    float t0, t1;
     unpack2(t, t0, t1);
-    float p0 = 1.533757750e-04f, p1 = 1.533757750e-04f;
-    p0 = fmaf(p0, r0, 1.339985989e-03f);
-    p1 = fmaf(p1, r1, 1.339985989e-03f);
-    p0 = fmaf(p0, r0, 9.618519805e-03f);
-    p1 = fmaf(p1, r1, 9.618519805e-03f);
-    p0 = fmaf(p0, r0, 5.550329015e-02f);
-    p1 = fmaf(p1, r1, 5.550329015e-02f);
-    p0 = fmaf(p0, r0, 2.402264625e-01f);
-    p1 = fmaf(p1, r1, 2.402264625e-01f);
-    p0 = fmaf(p0, r0, 6.931471825e-01f);
-    p1 = fmaf(p1, r1, 6.931471825e-01f);
-    p0 = fmaf(p0, r0, 1.0f);
-    p1 = fmaf(p1, r1, 1.0f);
+    // the polynomial on the packed pair (coefficient pairs as 64-bit immediates)
+    unsigned long long pp = pack2(1.533757750e-04f, 1.533757750e-04f);
+    pp = ffma2(pp, r, pack2(1.339985989e-03f, 1.339985989e-03f));
+    pp = ffma2(pp, r, pack2(9.618519805e-03f, 9.618519805e-03f));
+    pp = ffma2(pp, r, pack2(5.550329015e-02f, 5.550329015e-02f));
+    pp = ffma2(pp, r, pack2(2.402264625e-01f, 2.402264625e-01f));
+    pp = ffma2(pp, r, pack2(6.931471825e-01f, 6.931471825e-01f));
+    pp = ffma2(pp, r, pack2(1.0f, 1.0f));
+    float p0, p1;
+    unpack2(pp, p0, p1);
     y0 = __int_as_float(__float_as_int(p0) + (__float_as_int(t0) << 23));
     y1 = __int_as_float(__float_as_int(p1) + (__float_as_int(t1) << 23));
 }

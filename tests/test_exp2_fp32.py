@@ -39,8 +39,19 @@ def exp2_emulated(x, c, j=0):
     return (bits & 0xFFFFFFFF).astype(np.uint32).view(np.float32)
 
 
+def pair_coefficients():
+    """The coefficients of the packed-pair version (exp2_fp32x2), in the same order (c0 .. c6)."""
+    s = open(SRC).read()
+    body = s[s.index("void exp2_fp32x2("):]
+    body = body[:body.index("unpack2(pp")]
+    vals = re.findall(r"pack2\(([0-9.e+-]+)f, ([0-9.e+-]+)f\)", body)
+    assert all(a == b for a, b in vals)
+    return np.array([float(a) for a, _ in vals][::-1], dtype=np.float32)
+
+
 def test_coefficients_are_the_fit():
     assert np.array_equal(kernel_coefficients(), exp2_fit.coefficients())
+    assert np.array_equal(pair_coefficients(), exp2_fit.coefficients())
 
 
 def test_error_and_mean_error():
