@@ -239,13 +239,17 @@ def timed_steps(s, dt, steps, warmup, stream, torch):
                 "newton_avg_ms": tm["newton_ms"] / max(1, tm["newton_launches"])}
 
 
-def bench_mach5(steps: int, warmup: int, stream, torch) -> dict:
+def bench_mach5(steps: int, warmup: int, stream, torch, yz_elements: int = 0) -> dict:
     """The Mach-5 duct at full size in the FP32-split form (positivity limiter on, general kernel),
     then the plain all-FP64 form on the one-element-wide duct of the same x-mesh for the same steps:
     the flow is y/z-homogeneous, so the two must agree; their moments' largest scaled difference."""
     from paper_2308_06196_gb300.bgk import FP64, Solver
 
     c = W.config("mach5")
+    if yz_elements:  # a narrower duct of the same element size (profiling)
+        ne = c["nelem"]
+        c = dict(c, nelem=(ne[0], yz_elements, yz_elements),
+                 hi=(c["hi"][0], c["hi"][1] * yz_elements / ne[1], c["hi"][2] * yz_elements / ne[2]))
     bc, bcs = W.mach5_bc(c)
     k = W.mesh_kwargs(c)
     s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"], bc=bc,
@@ -354,6 +358,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="steps of the batched Sod ensemble (0: skip)")
     ap.add_argument("--mach5-steps", type=int, default=3, help="steps of the Mach-5 duct (0: skip)")
+    ap.add_argument("--mach5-yz-elements", type=int, default=0,
+                    help="elements in y and z of the Mach-5 duct (default: the workload's 8); narrower for profiling")
     ap.add_argument("--variant-steps", type=int, default=3,
                     help="steps of the Taylor-Green variants: limiter, variable tau, ablation (0: skip)")
     ap.add_argument("--no-ablation", action="store_true")
@@ -506,7 +512,7 @@ def main():
         batch = bench_batch(args.batch_steps, warmup, stream, torch, args.batch_members)
     mach5 = None
     if args.mach5_steps > 0 and world == 1:
-        mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch)
+        mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch, args.mach5_yz_elements)
     ablation = None if (args.no_ablation or world > 1) else bench_ablation()
 
     ms, graph_ms, e2e_ms = max_over_ranks([ms, graph_ms, e2e_ms], dist, "cuda")
