@@ -80,6 +80,10 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
             for (int q = tid; q < NP * kParamStride / 4; q += NT)
                 d4[q] = __ldg(f4 + q);
         }
+        // the general form reads 1/tau of its layer (variable collision time) before the first
+        // tile's B1, from rows other warps loaded
+        if (GEN)
+            __syncthreads();
     }
     // moment sums: lane = (node pair np = lane / 4: layer nodes np and np + 8) x (velocity eighth
     // kg = lane % 4: velocities 8 kg .. 8 kg + 7 of every tile); FP32 pairs over even/odd velocities
