@@ -6,8 +6,11 @@
  * blocking, fusion or reordering. OpenMP only splits the outer loop over elements or points.
  *
  * Readings of the paper taken here (the paper is silent or ambiguous on each):
- *   - The Maxwellian exponent uses the velocity dimension m = 3 (Eq. 4 writes d/2).
- *   - Monatomic gas, gamma = 5/3, so P = rho*theta and E = rho|U|^2/2 + 3/2 rho theta (Eq. 4).
+ *   - The Maxwellian normalisation uses the velocity dimension m (Eq. 4 writes d/2): m = 3, or m = 2
+ *     when the third velocity axis has a single node (the two-dimensional velocity space of the
+ *     paper's planar cases, Sec. 2, m >= d).
+ *   - Monatomic gas, P = rho*theta and E = rho|U|^2/2 + (m/2) rho theta (Eq. 4); for m = 2 the third
+ *     momentum component is identically zero and the Newton unknown U'z is left out.
  *   - Velocity grid nodes include both endpoints; trapezoid weights; tensor product (Eq. 12).
  *   - Correction functions: left/right Radau polynomials (Huynh's g_DG), which recover nodal DG.
  *   - Interface flux points are the tensor Gauss-Legendre points of each face.
@@ -37,6 +40,7 @@ struct orc_ctx {
     int bc[6];
     double bcs[30];
     int nv[3];
+    int vdim;               /* velocity dimension m: 3, or 2 when nv[2] == 1 (no u_z) */
     int64_t nvel;
     double *xi;             /* [nvel][3] */
     double *w;              /* [nvel] */
@@ -160,6 +164,11 @@ int oracle_velocity_grid(const int *nv, const double *vlo, const double *vhi, do
 {
     double x1[3][256], w1[3][256];
     for (int d = 0; d < 3; d++) {
+        if (d == 2 && nv[2] == 1) {  /* m = 2: the u_z axis is absent (one node at 0, unit weight) */
+            x1[2][0] = 0.0;
+            w1[2][0] = 1.0;
+            continue;
+        }
         if (nv[d] < 2 || nv[d] > 256 || !(vhi[d] > vlo[d]))
             return -1;
         double dx = (vhi[d] - vlo[d]) / (nv[d] - 1);
@@ -184,13 +193,21 @@ int oracle_velocity_grid(const int *nv, const double *vlo, const double *vhi, do
 /* Maxwellian and moments (Sec. 2, Eqs. 2 and 4; Sec. 2.1, Eq. 12)                            */
 /* ------------------------------------------------------------------------------------------ */
 
-/* Continuous Maxwellian at velocity v for (rho, U, theta), velocity dimension 3. */
-static double maxwellian(double rho, const double *U, double theta, const double *v)
+/* Continuous Maxwellian at velocity v for (rho, U, theta) in velocity dimension m (Eq. 4); for
+ * m = 2 the third components of U and v take no part. */
+static double maxwellian(int m, double rho, const double *U, double theta, const double *v)
 {
     double r2 = 0.0;
-    for (int d = 0; d < 3; d++)
+    for (int d = 0; d < m; d++)
         r2 += (v[d] - U[d]) * (v[d] - U[d]);
-    return rho / pow(2.0 * ORC_PI * theta, 1.5) * exp(-r2 / (2.0 * theta));
+    return rho / pow(2.0 * ORC_PI * theta, 0.5 * m) * exp(-r2 / (2.0 * theta));
+}
+
+/* theta of the moments Q in velocity dimension m: E = rho |U|^2 / 2 + (m / 2) rho theta. */
+static double theta_of(int m, const double *Q)
+{
+    const double rho = Q[0];
+    return (2.0 / m) * (Q[4] / rho - 0.5 * (Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]) / (rho * rho));
 }
 
 static void psi_of(const double *v, double *psi)
@@ -232,7 +249,7 @@ int oracle_sample_maxwellian(const orc_ctx *c, const double *prim, double *g)
     if (!c || !prim || !g || !(prim[0] > 0) || !(prim[4] > 0))
         return -1;
     for (int64_t k = 0; k < c->nvel; k++)
-        g[k] = maxwellian(prim[0], prim + 1, prim[4], c->xi + 3 * k);
+        g[k] = maxwellian(c->vdim, prim[0], prim + 1, prim[4], c->xi + 3 * k);
     return 0;
 }
 
@@ -279,10 +296,32 @@ static int solve_dense(int n, const double *A_in, const double *b_in, double *x)
     return 0;
 }
 
+/* Solve the n x n system restricted to the unknowns of velocity dimension m (m = 2 leaves out the
+ * third momentum component, whose row and column vanish); x of a left-out unknown is 0. */
+static int solve_active(int m, const double *A, const double *b, double *x)
+{
+    if (m == 3)
+        return solve_dense(5, A, b, x);
+    static const int act[4] = {0, 1, 2, 4};
+    double As[16], bs[4], xs[4];
+    for (int r = 0; r < 4; r++) {
+        bs[r] = b[act[r]];
+        for (int q = 0; q < 4; q++)
+            As[r * 4 + q] = A[act[r] * 5 + act[q]];
+    }
+    if (solve_dense(4, As, bs, xs) != 0)
+        return -1;
+    for (int r = 0; r < 5; r++)
+        x[r] = 0.0;
+    for (int r = 0; r < 4; r++)
+        x[act[r]] = xs[r];
+    return 0;
+}
+
 /* Residual G(P) = sum_k w_k psi_k g_k(P) - Q and, when J is non-NULL, its Jacobian with respect to
  * P = (rho', U'x, U'y, U'z, theta'), written out from the closed-form derivatives of the Maxwellian:
  * dg/drho' = g / rho', dg/dU'_d = g (xi_d - U'_d) / theta', dg/dtheta' = g (|xi - U'|^2 / (2 theta'^2)
- * - 3 / (2 theta')). */
+ * - m / (2 theta')). */
 static void newton_eval(const orc_ctx *c, const double *P, const double *Q, double *G, double *J)
 {
     for (int m = 0; m < 5; m++)
@@ -292,19 +331,19 @@ static void newton_eval(const orc_ctx *c, const double *P, const double *Q, doub
             J[m] = 0.0;
     for (int64_t k = 0; k < c->nvel; k++) {
         const double *v = c->xi + 3 * k;
-        double g = maxwellian(P[0], P + 1, P[4], v);
+        double g = maxwellian(c->vdim, P[0], P + 1, P[4], v);
         double psi[5];
         psi_of(v, psi);
         for (int m = 0; m < 5; m++)
             G[m] += c->w[k] * psi[m] * g;
         if (J) {
-            double r2 = 0.0, dg[5];
-            for (int d = 0; d < 3; d++)
+            double r2 = 0.0, dg[5] = {0, 0, 0, 0, 0};
+            for (int d = 0; d < c->vdim; d++)
                 r2 += (v[d] - P[1 + d]) * (v[d] - P[1 + d]);
             dg[0] = g / P[0];
-            for (int d = 0; d < 3; d++)
+            for (int d = 0; d < c->vdim; d++)
                 dg[1 + d] = g * (v[d] - P[1 + d]) / P[4];
-            dg[4] = g * (r2 / (2.0 * P[4] * P[4]) - 1.5 / P[4]);
+            dg[4] = g * (r2 / (2.0 * P[4] * P[4]) - 0.5 * c->vdim / P[4]);
             for (int m = 0; m < 5; m++)
                 for (int n = 0; n < 5; n++)
                     J[m * 5 + n] += c->w[k] * psi[m] * dg[n];
@@ -331,7 +370,7 @@ static int newton_point(const orc_ctx *c, const double *Q, double *P, int *iters
     if (rho > 0) {
         for (int d = 0; d < 3; d++)
             U[d] = Q[1 + d] / rho;
-        theta = (2.0 / 3.0) * (Q[4] / rho - 0.5 * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]));
+        theta = theta_of(c->vdim, Q);
     }
     P[0] = rho;
     P[1] = U[0];
@@ -355,7 +394,7 @@ static int newton_point(const orc_ctx *c, const double *Q, double *P, int *iters
         double rhs[5], dP[5];
         for (int m = 0; m < 5; m++)
             rhs[m] = -G[m];
-        if (solve_dense(5, J, rhs, dP) != 0)
+        if (solve_active(c->vdim, J, rhs, dP) != 0)
             break;
         it++;
         /* full Newton step, halved only while it leaves the admissible set or raises the residual */
@@ -452,6 +491,11 @@ orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double
         c->bcs[i] = bc_state ? bc_state[i] : 0.0;
     for (int d = 0; d < 3; d++)
         c->nv[d] = nv[d];
+    c->vdim = nv[2] == 1 ? 2 : 3;
+    if (c->vdim < dim) {  /* the velocity space spans at least the physical space (m >= d) */
+        free(c);
+        return NULL;
+    }
     c->nvel = (int64_t)nv[0] * nv[1] * nv[2];
     c->xi = (double *)malloc(sizeof(double) * 3 * c->nvel);
     c->w = (double *)malloc(sizeof(double) * c->nvel);
@@ -482,7 +526,7 @@ orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double
                 return NULL;
             }
             for (int64_t k = 0; k < c->nvel; k++)
-                c->ghost[fc * c->nvel + k] = maxwellian(rho, s + 1, s[4], c->xi + 3 * k);
+                c->ghost[fc * c->nvel + k] = maxwellian(c->vdim, rho, s + 1, s[4], c->xi + 3 * k);
         } else if (c->bc[fc] != ORC_PERIODIC) {
             oracle_destroy(c);
             return NULL;
@@ -616,7 +660,7 @@ int oracle_set_state(orc_ctx *c, const double *prim)
             continue;
         }
         for (int64_t k = 0; k < c->nvel; k++)
-            c->f[i * c->nvel + k] = maxwellian(s[0], s + 1, s[4], c->xi + 3 * k);
+            c->f[i * c->nvel + k] = maxwellian(c->vdim, s[0], s + 1, s[4], c->xi + 3 * k);
     }
     return bad ? -2 : 0;
 }
@@ -794,7 +838,7 @@ int oracle_rhs(const orc_ctx *c, const double *f, double *L)
             /* (sum_k w g psi psi^T) beta = (0, rho F, rho U . F) */
             double A[25] = {0}, b[5];
             for (int64_t k = 0; k < c->nvel; k++) {
-                double g = maxwellian(P[0], P + 1, P[4], c->xi + 3 * k), psi[5];
+                double g = maxwellian(c->vdim, P[0], P + 1, P[4], c->xi + 3 * k), psi[5];
                 psi_of(c->xi + 3 * k, psi);
                 for (int m = 0; m < 5; m++)
                     for (int n = 0; n < 5; n++)
@@ -805,7 +849,7 @@ int oracle_rhs(const orc_ctx *c, const double *f, double *L)
             for (int d = 0; d < 3; d++)
                 b[1 + d] = rho * c->force[d];
             b[4] = Q[1] * c->force[0] + Q[2] * c->force[1] + Q[3] * c->force[2];
-            if (solve_dense(5, A, b, beta) != 0) {
+            if (solve_active(c->vdim, A, b, beta) != 0) {
                 bad++;
                 continue;
             }
@@ -814,11 +858,11 @@ int oracle_rhs(const orc_ctx *c, const double *f, double *L)
         double tau = c->tau;
         if (c->mu_ref > 0.0) {
             const double rho = Q[0];
-            const double th = (2.0 / 3.0) * (Q[4] / rho - 0.5 * (Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]) / (rho * rho));
+            const double th = theta_of(c->vdim, Q);
             tau = c->mu_ref * pow(th, c->mu_omega) / (rho * th);
         }
         for (int64_t k = 0; k < c->nvel; k++) {
-            double g = maxwellian(P[0], P + 1, P[4], c->xi + 3 * k);
+            double g = maxwellian(c->vdim, P[0], P + 1, P[4], c->xi + 3 * k);
             if (c->collide)
                 Lp[k] += (g - fp[k]) / tau;
             if (c->has_force) {

@@ -46,14 +46,19 @@ int oracle_gauss_legendre(int n, double *x, double *w);
 int oracle_fr_operators(int p, double *D, double *lm, double *lp, double *dgl, double *dgr);
 
 /* Uniform velocity grid, endpoints included, tensor trapezoid weights.
- * nv[3] nodes per axis on [vlo, vhi]; xi is [N_v][3], w is [N_v]. */
+ * nv[3] nodes per axis on [vlo, vhi]; xi is [N_v][3], w is [N_v]. nv[2] = 1 selects the
+ * two-dimensional velocity space (m = 2): the third components are 0, the weights are the 2-D ones
+ * and vlo[2], vhi[2] are not read. */
 int oracle_velocity_grid(const int *nv, const double *vlo, const double *vhi, double *xi, double *w);
 
 /* Create a problem. dim in {1,2,3}; nelem[dim], lo[dim], hi[dim] describe an affine structured mesh.
  * bc[2*d + side] is ORC_PERIODIC / ORC_DIRICHLET / ORC_WALL; bc_state[(2*d+side)*5 + c] holds
  * (rho, u, v, w, T) of a Dirichlet state or (unused, u_w, v_w, w_w, T_w) of a wall.
  * tau <= 0 or tau = +inf switches the collision term off (pure advection).
- * force[3] is a constant body force per unit mass (may be NULL). Returns NULL on error. */
+ * force[3] is a constant body force per unit mass (may be NULL). Returns NULL on error.
+ * Velocity dimension m = 3, or m = 2 when nv[2] = 1 (then dim <= 2; E = rho|U|^2/2 + rho theta, the
+ * third momentum component is identically 0 and the third velocity component of every state, of
+ * bc_state and of force is not used). */
 orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double *hi,
                        const int *bc, const double *bc_state, int p,
                        const int *nv, const double *vlo, const double *vhi,
