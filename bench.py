@@ -295,6 +295,49 @@ def bench_mach5(steps: int, warmup: int, stream, torch, yz_elements: int = 0) ->
                                  "ms_per_step": ms64, "moments_max_rel_diff_fp32_split": err}}
 
 
+def bench_planar(steps: int, warmup: int, stream, torch) -> dict:
+    """The transverse shear wave in the two-dimensional velocity space (m = 2) on a 65,536-element
+    periodic line in the FP32-split form, then the plain all-FP64 form for the same steps from the same
+    state: ms per step, the stage kernel's achieved bandwidth, and the two forms' largest scaled
+    moment difference."""
+    from paper_2308_06196_gb300.bgk import FP64, Solver
+
+    c = W.config("planar_shear")
+    k = W.mesh_kwargs(c)
+    out = {"workload": "planar_shear", "mesh": f"{c['nelem'][0]} line elements p={c['p']}, periodic",
+           "nv": list(c["nv"]), "velocity_dimension": 2}
+    Q = {}
+    for name, prec in (("fp32_split", 0), ("fp64", FP64)):
+        s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"],
+                   precision=prec)
+        s.set_stream(stream.cuda_stream)
+        s.set_state(W.prim_shear(s.points(), c["amp"]))
+        if prec == 0:
+            out["tiles_per_task"] = s.autotune()
+            dt = s.dt(c["cfl"])
+            ms, st = timed_steps(s, dt, steps, warmup, stream, torch)
+            n_total = warmup + 2 * steps
+            out.update({"dof": s.ndof, "value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, **st})
+        else:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.step(dt, 1)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.step(dt, n_total - 1)
+            e1.record(stream)
+            s.synchronize()
+            ms64 = e0.elapsed_time(e1) / (n_total - 1)
+            out["fp64"] = {"value": s.ndof * 3 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
+        Q[name] = s.moments()
+        s.close()
+    q32, q64 = Q["fp32_split"], Q["fp64"]
+    scale = np.array([np.abs(q64[:, 0]).max()] + [np.abs(q64[:, 0]).max()] * 3 + [np.abs(q64[:, 4]).max()])
+    out["steps_compared"] = n_total
+    out["moments_max_rel_diff_fp32_split"] = float((np.abs(q32 - q64).max(axis=0) / scale).max())
+    out["fp64"]["speedup_of_fp32_split"] = out["value"] / out["fp64"]["value"]
+    return out
+
+
 def bench_variants(steps: int, warmup: int, stream, torch, k: dict, prim_dev, dt: float) -> dict:
     """The Taylor-Green workload with the widened rows switched on one at a time: the positivity
     limiter and the variable collision time (both in the general hexahedral kernel), and the
@@ -363,6 +406,8 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=3,
                     help="steps of the Taylor-Green variants: limiter, variable tau, ablation (0: skip)")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--planar-steps", type=int, default=3,
+                    help="steps of the m = 2 planar shear workload (0: skip)")
     ap.add_argument("--batch-members", type=int, default=0,
                     help="members of the Sod ensemble (default: the workload's 256); smaller for profiling")
     ap.add_argument("--elements", type=int, default=0,
@@ -514,6 +559,9 @@ def main():
     if args.mach5_steps > 0 and world == 1:
         mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch, args.mach5_yz_elements)
     ablation = None if (args.no_ablation or world > 1) else bench_ablation()
+    planar = None
+    if args.planar_steps > 0 and world == 1:
+        planar = bench_planar(args.planar_steps, warmup, stream, torch)
 
     ms, graph_ms, e2e_ms = max_over_ranks([ms, graph_ms, e2e_ms], dist, "cuda")
     value = job_value(dof, world, ms)
@@ -560,6 +608,7 @@ def main():
         "mach5": mach5,
         "variants": variants,
         "ablation": ablation,
+        "planar": planar,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

@@ -67,6 +67,12 @@ typedef struct {
 
 /* Uniform velocity grid, n[d] >= 2 nodes per axis on [lo[d], hi[d]] with both endpoints included,
  * tensor-product trapezoid weights (Sec. 2.1, Eq. 12). */
+/* Uniform velocity grid, n[d] nodes on [lo[d], hi[d]] per axis, endpoints included, tensor trapezoid
+ * weights (Sec. 2.1, Eq. 12). n[2] = 1 selects the two-dimensional velocity space (velocity dimension
+ * m = 2, Sec. 2 with m >= d, so dim <= 2): velocities (u_x, u_y), the Maxwellian normalised by
+ * (2 pi theta)^(m/2) (Eq. 4), E = rho |U|^2 / 2 + (m/2) rho theta; lo[2] and hi[2] are not read, the
+ * third momentum component of Q is identically 0 and the third velocity component of every state
+ * (bgk_set_state, Dirichlet data) is not used. */
 typedef struct {
     int n[3];
     double lo[3], hi[3];
@@ -118,7 +124,7 @@ int bgk_info(const bgk_ctx *ctx, int64_t *npoints, int64_t *nvel, int64_t *ndof,
 /* Node coordinates x[n_x][3] (unused components 0), host. */
 int bgk_points(const bgk_ctx *ctx, double *x);
 
-/* Set f to the sampled continuous Maxwellian (Eq. 4, velocity dimension 3) of the primitive state
+/* Set f to the sampled continuous Maxwellian (Eq. 4, velocity dimension m) of the primitive state
  * prim[n_x][5] = (rho, u, v, w, T) (theta = T), then compute its moments and conservative
  * Maxwellian. Host array (synchronises) or device array (asynchronous) variant. */
 int bgk_set_state(bgk_ctx *ctx, const double *prim);

@@ -40,7 +40,7 @@ cudaError_t launch_limit64(double *f, int nvt, int E, int NP, int N1, int dim, c
 cudaError_t launch_wall(const WallArgs &A, bool fp64, const void *w, const void *xi, cudaStream_t s);
 cudaError_t launch_moments64(const Moments64Args &A, cudaStream_t s);
 cudaError_t launch_init64(double *f, const double *prim, const double *xi, const float *gmask, int nvt, int E, int NP,
-                          int nslots, int *err, cudaStream_t s);
+                          int nslots, int vdim, int *err, cudaStream_t s);
 cudaError_t launch_convert64(bool to_device, double *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
 }  // namespace bgk
@@ -148,10 +148,13 @@ void build_ops(int p, Ops &op, Ops64 &o64, double *xg_out)
     }
 }
 
-double maxwell(double rho, const double *U, double th, double vx, double vy, double vz)
+// Continuous Maxwellian (Eq. 4) in velocity dimension m (3, or 2: u_z and U_z take no part).
+double maxwell(int m, double rho, const double *U, double th, double vx, double vy, double vz)
 {
-    const double r2 = (vx - U[0]) * (vx - U[0]) + (vy - U[1]) * (vy - U[1]) + (vz - U[2]) * (vz - U[2]);
-    return rho * pow(2.0 * kPi * th, -1.5) * exp(-0.5 * r2 / th);
+    double r2 = (vx - U[0]) * (vx - U[0]) + (vy - U[1]) * (vy - U[1]);
+    if (m == 3)
+        r2 += (vz - U[2]) * (vz - U[2]);
+    return rho * pow(2.0 * kPi * th, -0.5 * m) * exp(-0.5 * r2 / th);
 }
 
 }  // namespace
@@ -167,6 +170,7 @@ struct bgk_ctx {
     double bcs[30] = {0};
     int nv[3] = {0, 0, 0};
     double vlo[3] = {0, 0, 0}, dv[3] = {0, 0, 0};
+    int vdim = 3;  // velocity dimension m: 3, or 2 when nv[2] = 1 (dv[2] then holds dv[0] as a placeholder)
     int64_t nvel = 0;
     double tau = 0;
     bgk_opts opts{};
@@ -331,6 +335,7 @@ NewtonArgs newton_args(bgk_ctx *c, int cold)
         N.dv[d] = c->dv[d];
         N.n[d] = c->nv[d];
     }
+    N.vdim = c->vdim;
     return N;
 }
 
@@ -669,12 +674,20 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         return bail(BGK_EINVAL, "too many points");
     c->E = (int)E;
     c->npts = E * c->NP;
-    for (int d = 0; d < 3; d++) {
+    c->vdim = vg->n[2] == 1 ? 2 : 3;
+    if (c->vdim == 2 && c->dim > 2)
+        return bail(BGK_EINVAL, "a two-dimensional velocity space (n[2] = 1) needs dim <= 2");
+    for (int d = 0; d < c->vdim; d++) {
         if (vg->n[d] < 2 || vg->n[d] > 4096 || !(vg->hi[d] > vg->lo[d]))
             return bail(BGK_EINVAL, "bad velocity grid");
         c->nv[d] = vg->n[d];
         c->vlo[d] = vg->lo[d];
         c->dv[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
+    }
+    if (c->vdim == 2) {  // the absent u_z axis: one node at 0 of unit weight
+        c->nv[2] = 1;
+        c->vlo[2] = 0.0;
+        c->dv[2] = c->dv[0];
     }
     if (c->opts.mu_ref > 0.0 && c->prec == BGK_FP32_SPLIT && !(c->dv[0] == c->dv[1] && c->dv[0] == c->dv[2]))
         return bail(BGK_EINVAL, "a variable collision time needs one velocity spacing on all axes (FP32-split form)");
@@ -818,7 +831,8 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         double v[3], w = 1.0;
         for (int d = 0; d < 3; d++) {
             v[d] = c->vlo[d] + kk[d] * c->dv[d];
-            w *= (kk[d] == 0 || kk[d] == c->nv[d] - 1) ? 0.5 * c->dv[d] : c->dv[d];
+            if (c->nv[d] > 1)
+                w *= end_factor(kk[d], c->nv[d]) * c->dv[d];
             xi[d * c->nslots + s] = (float)v[d];
             xi64[d * c->nslots + s] = v[d];
             mi[d * c->nslots + s] = (float)(2 * kk[d] - (c->nv[d] - 1));
@@ -830,8 +844,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         // FP32 kernels: exact index-basis weights W (1, m, sum_d r_d m_d^2) (see index_to_moments)
         double W = real ? 1.0 : 0.0, m[3], mr = 0.0;
         for (int d = 0; d < 3; d++) {
-            if (kk[d] == 0 || kk[d] == c->nv[d] - 1)
-                W *= 0.5;
+            W *= end_factor(kk[d], c->nv[d]);
             m[d] = 2.0 * kk[d] - (c->nv[d] - 1);
             mr += (double)index_r(c->dv[d], c->dv[0]) * m[d] * m[d];
         }
@@ -848,7 +861,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
                 // Dirichlet: the prescribed Maxwellian; diffuse wall: the unit-density wall Maxwellian
                 const double *st = c->bcs + 5 * q;
                 const double rho = c->bc[q] == BGK_BC_DIRICHLET ? st[0] : 1.0;
-                gh64[q * c->nslots + s] = maxwell(rho, st + 1, st[4], v[0], v[1], v[2]);
+                gh64[q * c->nslots + s] = maxwell(c->vdim, rho, st + 1, st[4], v[0], v[1], v[2]);
                 gh[q * c->nslots + s] = (float)gh64[q * c->nslots + s];
                 if (c->bc[q] == BGK_BC_DIFFUSE_WALL) {
                     const double un = (q & 1) ? v[q / 2] : -v[q / 2];  // xi . n_out
@@ -931,7 +944,8 @@ static int set_state_impl(bgk_ctx *c, const double *prim, cudaMemcpyKind kind)
 {
     CK(cudaMemcpyAsync(c->prim_in, prim, c->npts * 5 * sizeof(double), kind, c->stream));
     if (c->prec == BGK_FP64)
-        CK(launch_init64(c->fA64, c->prim_in, c->xi64, c->gmask, c->nvt, c->E, c->NP, c->nslots, c->err, c->stream));
+        CK(launch_init64(c->fA64, c->prim_in, c->xi64, c->gmask, c->nvt, c->E, c->NP, c->nslots, c->vdim, c->err,
+                         c->stream));
     else
         CK(launch_init_maxwellian(c->fA, c->prim_in, c->slotk_d, c->nvt, c->E, c->NP, c->nv, c->vlo, c->dv,
                                   c->err, c->stream));
@@ -1108,7 +1122,8 @@ double bgk_dt(const bgk_ctx *c, double cfl)
         tmin = INFINITY;
         for (int64_t i = 0; i < c->npts; i++) {
             const double *q = &Q[i * 5];
-            const double rho = q[0], th = (2.0 / 3.0) * (q[4] / rho - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (rho * rho));
+            const double rho = q[0],
+                         th = (2.0 / c->vdim) * (q[4] / rho - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (rho * rho));
             tmin = std::min(tmin, c->opts.mu_ref * pow(th, c->opts.mu_omega) / (rho * th));
         }
     }

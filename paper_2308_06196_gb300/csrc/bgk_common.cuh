@@ -103,9 +103,12 @@ struct NewtonArgs {
     double *itau64;           // [n_x] 1/tau of the plain FP64 form, or null
     int it32;              // FP32 Newton iterations
     int it64;              // FP64 refinements
-    // 1-D velocity grids: xi_k = v0[d] + k dv[d], k < n[d]; trapezoid weights
+    // 1-D velocity grids: xi_k = v0[d] + k dv[d], k < n[d]; trapezoid weights. An axis with one node
+    // (n[2] = 1: the two-dimensional velocity space, m = 2) has v0 = 0 and unit weight, and its dv is
+    // the x spacing (a placeholder that keeps the one-spacing forms of the exponent).
     double v0[3], dv[3];
     int n[3];
+    int vdim;              // velocity dimension m: 3, or 2 (no u_z, E = rho |U|^2 / 2 + rho theta)
 };
 
 // FR reference operators in FP64 for the plain all-FP64 form (Sec. 2.1, Eqs. 7-9).
@@ -166,6 +169,10 @@ struct WallArgs {
 //   mu = sum_k W_k (1, m_x, m_y, m_z, r_x m_x^2 + r_y m_y^2 + r_z m_z^2) f_k,  r_d = (s_d / s_x)^2 in FP32,
 // whose weights are exact FP32 numbers (r_d = 1 on grids with one spacing), so the only FP32 error of
 // the moments is the summation's. index_to_moments turns mu into Q = sum_k w_k psi_k f_k (Eq. 2).
+// Trapezoid end factor of index k on an axis of n nodes: 1/2 at both ends, 1 inside; 1 on an axis with
+// a single node (the absent u_z of the two-dimensional velocity space).
+__host__ __device__ inline double end_factor(int k, int n) { return n > 1 && (k == 0 || k == n - 1) ? 0.5 : 1.0; }
+
 __host__ __device__ inline float index_r(double dv_d, double dv_x)
 {
     return (float)((dv_d / dv_x) * (dv_d / dv_x));
@@ -174,7 +181,8 @@ __host__ __device__ inline float index_r(double dv_d, double dv_x)
 __host__ __device__ inline void index_to_moments(const double (&mu)[5], const double v0[3], const double dv[3],
                                                  const int n[3], double (&Q)[5])
 {
-    const double V = dv[0] * dv[1] * dv[2], s0 = 0.5 * dv[0];
+    // cell volume of the axes that have a spacing (an axis with one node has unit weight)
+    const double V = dv[0] * dv[1] * (n[2] > 1 ? dv[2] : 1.0), s0 = 0.5 * dv[0];
     double cs = 0.0, cm = 0.0;
     Q[0] = V * mu[0];
     for (int d = 0; d < 3; d++) {

@@ -49,8 +49,7 @@ __global__ void __launch_bounds__(256) k_noalloc_partials(const float *__restric
     float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         const int kx = (int)(k % nx), ky = (int)((k / nx) % ny), kz = (int)(k / ((int64_t)nx * ny));
-        const float W = ((kx == 0 || kx == nx - 1) ? 0.5f : 1.f) * ((ky == 0 || ky == ny - 1) ? 0.5f : 1.f) *
-                        ((kz == 0 || kz == nz - 1) ? 0.5f : 1.f);
+        const float W = (float)(end_factor(kx, nx) * end_factor(ky, ny) * end_factor(kz, nz));
         const float mx = (float)(2 * kx - (nx - 1)), my = (float)(2 * ky - (ny - 1)), mz = (float)(2 * kz - (nz - 1));
         const float v = __ldg(f + (int64_t)pt * nvel + k);
         m[0] = fmaf(W, v, m[0]);
@@ -85,7 +84,8 @@ extern "C" int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk
 {
     if (!d_f || !vg || !d_Q || !d_prim || npts < 1 || npts > (1 << 30))
         return BGK_EINVAL;
-    for (int d = 0; d < 3; d++)
+    const int vdim = vg->n[2] == 1 ? 2 : 3;  // n[2] = 1: the two-dimensional velocity space
+    for (int d = 0; d < vdim; d++)
         if (vg->n[d] < 2 || vg->n[d] > 4096 || !(vg->hi[d] > vg->lo[d]))
             return BGK_EINVAL;
     const int64_t nvel = (int64_t)vg->n[0] * vg->n[1] * vg->n[2];
@@ -127,9 +127,13 @@ extern "C" int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk
     if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
         return BGK_ECUDA;
     double v0[3], dv[3];
-    for (int d = 0; d < 3; d++) {
+    for (int d = 0; d < vdim; d++) {
         v0[d] = vg->lo[d];
         dv[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
+    }
+    if (vdim == 2) {  // one node at 0 of unit weight; dv[2] a placeholder equal to dv[0]
+        v0[2] = 0.0;
+        dv[2] = dv[0];
     }
     dim3 grid((unsigned)npts, (unsigned)ngroups);
     k_noalloc_partials<<<grid, 256, 0, s>>>(d_f, (int)npts, vg->n[0], vg->n[1], vg->n[2], index_r(dv[1], dv[0]),
@@ -152,6 +156,7 @@ extern "C" int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk
         N.dv[d] = dv[d];
         N.n[d] = vg->n[d];
     }
+    N.vdim = vdim;
     if (launch_newton(N, s) != cudaSuccess)
         return BGK_ECUDA;
     int h = 0;

@@ -107,9 +107,19 @@ __device__ __forceinline__ void assemble(const T (&S)[3][5], T e0, T (&M)[5], T 
     J[4][4] = e0 * T(0.25) * s4;
 }
 
-// 1-D sums in FP32: A(c) = exp(ad c - (beta/2) c^2) on c_k = c0 + k h, trapezoid weights dv (ends /2).
+// 1-D sums in FP32: A(c) = exp(ad c - (beta/2) c^2) on c_k = c0 + k h, trapezoid weights dv (ends /2);
+// an axis with one node (no u_z, m = 2) has the single weight 1.
 __device__ __forceinline__ void sums32(float ad, float beta, float c0, float h, int n, float dv, float (&S)[5])
 {
+    if (n == 1) {
+        const float t = __expf(c0 * fmaf(-0.5f * beta, c0, ad));
+        S[0] = t;
+        S[1] = t * c0;
+        S[2] = S[1] * c0;
+        S[3] = S[2] * c0;
+        S[4] = S[3] * c0;
+        return;
+    }
     for (int m = 0; m < 5; m++)
         S[m] = 0.f;
     for (int k = 0; k < n; k++) {
@@ -138,6 +148,13 @@ __device__ __forceinline__ void sums32(float ad, float beta, float c0, float h, 
 template <int M>
 __device__ __forceinline__ void sums64(double ad, double beta, double c0, double h, int n, double dv, double (&S)[M])
 {
+    if (n == 1) {  // one node of unit weight (no u_z, m = 2)
+        double t = exp(c0 * fma(-0.5 * beta, c0, ad));
+#pragma unroll
+        for (int m = 0; m < M; m++, t *= c0)
+            S[m] = t;
+        return;
+    }
     const double q1 = (ad - beta * c0) * h, q2 = -0.5 * beta * h * h;
     int kp = (int)rintf((float)(-q1) / (float)(2.0 * q2));
     kp = kp < 0 ? 0 : (kp > n - 1 ? n - 1 : kp);
@@ -226,7 +243,8 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
 
     const double rho = Q[0];
     const double u[3] = {Q[1] / rho, Q[2] / rho, Q[3] / rho};
-    const double thc = (2.0 / 3.0) * (Q[4] / rho - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    const double hm = 0.5 * A.vdim;  // E = rho |U|^2 / 2 + (m / 2) rho theta
+    const double thc = (Q[4] / rho - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) / hm;
     float *par = A.param + (int64_t)pt * kParamStride;
     if (!(rho > 0.0) || !(thc > 0.0) || !isfinite(rho) || !isfinite(thc)) {
         atomicOr(A.err, kErrDomain);
@@ -262,7 +280,7 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     Qt[4] = (Q[4] - (V[0] * Q[1] + V[1] * Q[2] + V[2] * Q[3]) + 0.5 * Q[0] * (V[0] * V[0] + V[1] * V[1] + V[2] * V[2])) * is * is;
 
     // alpha = (alpha_0, a_1, a_2, a_3, -beta): g = exp(alpha_0 + a . c - beta |c|^2 / 2)
-    double al[5] = {log(rh0) - 1.5 * log(2.0 * 3.14159265358979323846 * th0), 0.0, 0.0, 0.0, -1.0};
+    double al[5] = {log(rh0) - hm * log(2.0 * 3.14159265358979323846 * th0), 0.0, 0.0, 0.0, -1.0};
     double c0[3], h[3], dvs[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -286,6 +304,10 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
             float M[5];
             assemble<float>(S, expf((float)al[0]), M, J);
             haveJ = true;
+            if (A.vdim == 2) {  // no u_z: the a_3 row and column vanish; keep a_3 = 0
+                J[3][3] = 1.f;
+                M[3] = (float)Qt[3];
+            }
             float r[5], dx[5], Jw[5][5];
     #pragma unroll
             for (int m = 0; m < 5; m++) {
@@ -332,6 +354,8 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
             }
             double M[5];
             assemble<double>(S, exp(al[0]), M, nullptr);
+            if (A.vdim == 2)
+                M[3] = Qt[3];
             double r[5], dx[5], Jd[5][5];
     #pragma unroll
             for (int m = 0; m < 5; m++) {
@@ -368,8 +392,8 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     double Up[3];
     for (int d = 0; d < 3; d++)
         Up[d] = V[d] + s * a[d] / beta;
-    const double lnC = al[0] + 0.5 * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / beta;  // ln(rho' (2 pi theta')^-1.5)
-    const double rhop = exp(lnC) * pow(2.0 * 3.14159265358979323846 * thp, 1.5);
+    const double lnC = al[0] + 0.5 * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / beta;  // ln(rho' (2 pi theta')^-m/2)
+    const double rhop = exp(lnC) * pow(2.0 * 3.14159265358979323846 * thp, hm);
     double *pp = A.prim + (int64_t)pt * 5;
     pp[0] = rhop;
     pp[1] = Up[0];

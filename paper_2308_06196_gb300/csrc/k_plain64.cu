@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k64_moments(const Moments64Args A)
 
 // Sample the continuous Maxwellian of every point's primitive state into the FP64 layout.
 __global__ void k64_init(double *f, const double *prim, const double *xi, const float *gmask, int nvt, int E, int NP,
-                         int nslots, int *err)
+                         int nslots, int vdim, int *err)
 {
     const int64_t n = (int64_t)nvt * E * NP * kWarp;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
@@ -127,11 +127,11 @@ __global__ void k64_init(double *f, const double *prim, const double *xi, const 
             continue;
         }
         double r2 = 0.0;
-        for (int d = 0; d < 3; d++) {
+        for (int d = 0; d < vdim; d++) {  // m = 2: u_z and U_z take no part
             const double c = xi[d * nslots + slot] - s[1 + d];
             r2 += c * c;
         }
-        f[q] = gmask[slot] * s[0] * pow(2.0 * 3.14159265358979323846 * s[4], -1.5) * exp(-0.5 * r2 / s[4]);
+        f[q] = gmask[slot] * s[0] * pow(2.0 * 3.14159265358979323846 * s[4], -0.5 * vdim) * exp(-0.5 * r2 / s[4]);
     }
 }
 
@@ -208,10 +208,10 @@ cudaError_t launch_moments64(const Moments64Args &A, cudaStream_t s)
 }
 
 cudaError_t launch_init64(double *f, const double *prim, const double *xi, const float *gmask, int nvt, int E, int NP,
-                          int nslots, int *err, cudaStream_t s)
+                          int nslots, int vdim, int *err, cudaStream_t s)
 {
     const int64_t n = (int64_t)nvt * E * NP * kWarp;
-    k64_init<<<grid_for(n, 256), 256, 0, s>>>(f, prim, xi, gmask, nvt, E, NP, nslots, err);
+    k64_init<<<grid_for(n, 256), 256, 0, s>>>(f, prim, xi, gmask, nvt, E, NP, nslots, vdim, err);
     return cudaGetLastError();
 }
 

@@ -5,14 +5,15 @@
 
 namespace bgk {
 
-// Sample the continuous Maxwellian (Sec. 2, Eq. 4, velocity dimension 3) of every point's primitive
-// state into f. One CTA per element: the separable factors exp(-(xi_d - U_d)^2 / (2 theta)) of the
+// Sample the continuous Maxwellian (Sec. 2, Eq. 4, velocity dimension m = 3, or 2 when nz = 1: the
+// one z node has factor 1 and U_z takes no part) of every point's primitive state into f. One CTA per element: the separable factors exp(-(xi_d - U_d)^2 / (2 theta)) of the
 // element's points are computed once in FP64 and kept in shared memory as FP32, then every
 // (tile, node, lane) value is the product C * Ex * Ey * Ez. Writes 0 on padded slots.
 __global__ void k_init_maxwellian(float *__restrict__ f, const double *__restrict__ prim, const int *__restrict__ slotk,
                                   int nvt, int E, int NP, int nx, int ny, int nz, double v0x, double v0y,
                                   double v0z, double dvx, double dvy, double dvz, int *err)
 {
+    const double hm = nz == 1 ? 1.0 : 1.5;  // m / 2
     extern __shared__ float tab[];  // [NP][nx + ny + nz + 1]
     const int e = blockIdx.x;
     const int ntab = nx + ny + nz + 1;
@@ -28,11 +29,13 @@ __global__ void k_init_maxwellian(float *__restrict__ f, const double *__restric
         }
         double v;
         if (t == 0)
-            v = rho * pow(2.0 * 3.14159265358979323846 * th, -1.5);
+            v = rho * pow(2.0 * 3.14159265358979323846 * th, -hm);
         else if (t <= nx)
             v = exp(-0.5 * (v0x + (t - 1) * dvx - s[1]) * (v0x + (t - 1) * dvx - s[1]) / th);
         else if (t <= nx + ny)
             v = exp(-0.5 * (v0y + (t - 1 - nx) * dvy - s[2]) * (v0y + (t - 1 - nx) * dvy - s[2]) / th);
+        else if (nz == 1)
+            v = 1.0;
         else
             v = exp(-0.5 * (v0z + (t - 1 - nx - ny) * dvz - s[3]) * (v0z + (t - 1 - nx - ny) * dvz - s[3]) / th);
         tab[q] = (float)v;

@@ -41,6 +41,11 @@ CONFIGS = {
     # ensemble of independent 1-D Sod shock tubes on [0, 1] (interface at x = 1/2, gas at rest, Dirichlet
     # ends), drawn from one seed: elements U{16..128}, p U{2, 3}, velocity grid N^3 on [-8, 8]^3 with
     # N in {12, 16, 24, 32}, (rho, T) of each side U[0.125, 1] x U[0.8, 1.25], tau log-uniform [1e-4, 1e-1]
+    # transverse shear wave on a periodic line in the two-dimensional velocity space (m = 2: velocity grid
+    # N^2, the third axis one node): 65,536 elements at p = 3, 32^2 velocities on [-7, 7]^2, tau = 1e-3;
+    # u_y = 0.1 sin(2 pi x) decays by shear viscosity (1.1 GB per FP32 f array, larger than L2)
+    "planar_shear": dict(dim=1, nelem=(65536,), lo=(0.0,), hi=(1.0,), p=3, nv=(32, 32, 1), vlo=(-7.0, -7.0, 0.0),
+                         vhi=(7.0, 7.0, 0.0), tau=1e-3, cfl=0.1, steps=20, amp=0.1),
     "sod_ensemble": dict(members=256, seed=0, elements=(16, 128), degrees=(2, 3), nvs=(12, 16, 24, 32), vmax=8.0,
                          rho=(0.125, 1.0), temp=(0.8, 1.25), tau=(1e-4, 1e-1), cfl=0.1, steps=20),
 }
@@ -79,6 +84,15 @@ def prim_taylor_green(x: np.ndarray, mach: float = 0.1, gamma: float = 5.0 / 3.0
     P[:, 2] = -U0 * np.cos(X) * np.sin(Y) * np.cos(Z)
     pres = 1.0 + U0 * U0 / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
     P[:, 4] = pres / P[:, 0]
+    return P
+
+
+def prim_shear(x: np.ndarray, amp: float = 0.1) -> np.ndarray:
+    """rho = 1, T = 1, u = 0, v = amp sin(2 pi x): a transverse shear wave along x."""
+    P = np.zeros((len(x), 5))
+    P[:, 0] = 1.0
+    P[:, 2] = amp * np.sin(TWO_PI * x[:, 0])
+    P[:, 4] = 1.0
     return P
 
 

@@ -213,3 +213,40 @@ def test_euler_limit_sound_speed(m):
     # differ by 9 %, the tolerance is 1 %
     c = acoustic_speed(m)
     assert abs(c - math.sqrt((m + 2) / m)) <= 0.01 * math.sqrt((m + 2) / m), c
+
+
+def shear_decay_rate(m, tau=5e-3, t1=0.1, t2=0.5, amp=0.01):
+    """Decay rate of a small transverse shear wave v = amp sin(2 pi x) on a periodic unit line: the
+    amplitude of rho v's first sine mode at t1 and t2, both well past the initial layer of a few tau in
+    which the shear stress builds up from the equilibrium start."""
+    p, ne, L = 3, 8, 6.0
+    n = 16 if m == 2 else 12
+    nv = (n, n, 1) if m == 2 else (n, n, n)
+    pr = orc.Problem(1, [ne], [0.0], [1.0], p, nv, (-L,) * 3, (L,) * 3, tau)
+    x = pr.points()[:, 0]
+    prim = np.zeros((pr.npts, 5))
+    prim[:, 0] = 1.0
+    prim[:, 2] = amp * np.sin(2 * np.pi * x)
+    prim[:, 4] = 1.0
+    pr.set_state(prim)
+    _, wg = orc.gauss_legendre(p + 1)
+    wq = np.tile(wg, ne) / (2 * ne)
+
+    def mode():
+        return 2 * (wq * pr.moments()[:, 2] * np.sin(2 * np.pi * x)).sum()
+
+    dt = tau / math.ceil(tau / pr.dt(0.1))
+    pr.step(dt, int(round(t1 / dt)))
+    a1 = mode()
+    pr.step(dt, int(round((t2 - t1) / dt)))
+    return math.log(a1 / mode()) / (t2 - t1)
+
+
+@pytest.mark.parametrize("m", [2, 3])
+def test_shear_wave_decays_at_the_bgk_viscosity(m):
+    # Chapman-Enskog: the BGK model's shear viscosity is mu = tau P, so a transverse shear wave of wave
+    # number k decays at nu k^2 with nu = mu / rho = tau theta, in either velocity dimension (the
+    # Burnett-order correction is O((tau k)^2), below 1e-3 here)
+    tau, k = 5e-3, 2 * math.pi
+    rate = shear_decay_rate(m, tau)
+    assert abs(rate - tau * k * k) <= 0.005 * tau * k * k, rate

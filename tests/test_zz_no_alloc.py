@@ -64,3 +64,36 @@ def test_noalloc_rejects_oversized_request():
     rc = bgk.lib().bgk_equilibrium_noalloc(C.c_void_p(f_dev.data_ptr()), npts, C.byref(vg),
                                            C.c_void_p(Q_dev.data_ptr()), C.c_void_p(Q_dev.data_ptr()), None)
     assert rc == bgk.BGK_EINVAL
+
+
+def test_noalloc_planar_velocity_space():
+    # m = 2 (n[2] = 1): 24^2 velocities on a 3-element p = 3 line, against the regular path and the
+    # Newton property of the planar Maxwellian
+    import torch
+
+    _build.build()
+    from paper_2308_06196_gb300 import bgk
+
+    ne, p, n, L, tau = 3, 3, 24, 6.0, 0.05
+    grid = ((n, n, 1), (-L, -L, 0.0), (L, L, 0.0))
+    pr = orc.Problem(1, [ne], [0.0], [1.0], p, *grid, tau)
+    s = bgk.Solver(1, [ne], [0.0], [1.0], p, *grid, tau)
+    P0 = W.smooth_prim(pr.points(), 1, seed=41)
+    P0[:, 3] = 0.0
+    pr.set_state(P0)
+    f = pr.get_f() * W.noise((pr.npts, pr.nvel), seed=42, amp=0.1)
+    s.set_f(f)
+    Q_ref, P_ref = s.moments(), s.equilibrium()
+    f_dev = torch.tensor(f, dtype=torch.float32, device="cuda")
+    Q_dev = torch.full((pr.npts, 5), float("nan"), dtype=torch.float64, device="cuda")
+    P_dev = torch.full((pr.npts, 5), float("nan"), dtype=torch.float64, device="cuda")
+    assert bgk.equilibrium_noalloc(f_dev, *grid, Q_dev, P_dev) == 0
+    Q, P = Q_dev.cpu().numpy(), P_dev.cpu().numpy()
+    assert np.all(Q[:, 3] == 0.0)
+    assert np.abs(Q - Q_ref).max() <= 5e-7 * np.abs(Q_ref).max()
+    assert np.abs(P - P_ref).max() <= 5e-6 * np.abs(P_ref).max()
+    xi, w = pr.xi, pr.w
+    psi = np.stack([np.ones(len(xi)), xi[:, 0], xi[:, 1], 0 * xi[:, 0], 0.5 * (xi[:, :2] ** 2).sum(1)], 1)
+    for q, pp in zip(Q, P):
+        g = pp[0] / (2 * np.pi * pp[4]) * np.exp(-((xi[:, :2] - pp[1:3]) ** 2).sum(1) / (2 * pp[4]))
+        assert np.all(np.abs((w * g) @ psi - q) <= 1e-12 * np.abs(q).max())
