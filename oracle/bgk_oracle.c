@@ -22,6 +22,13 @@
  *     chosen per face point for zero net discrete mass flux.
  *   - Body force: source g * (beta . psi) with (sum_k w g psi psi^T) beta = (0, rho F, rho U.F),
  *     whose discrete moments are exactly those of -F . grad_xi f.
+ *   - Curvilinear hexahedra (optional, oracle_set_geometry): each element maps the reference cube by the
+ *     degree-p interpolant of its solution-node coordinates; the advection is the FR residual of the
+ *     reference-space flux (Ja^i . xi) f divided by J, with the metric terms Ja^i in Kopriva's
+ *     conservative curl form (which satisfies the discrete metric identities, so a constant state is
+ *     preserved) and a single-valued face normal (the mean of the two elements' interpolated Ja^i at
+ *     the face) in the upwind flux (Eq. 9 with u_n = Ja^i . xi). The limiter's element mean is then
+ *     J-weighted.
  */
 #include "bgk_oracle.h"
 
@@ -56,6 +63,11 @@ struct orc_ctx {
     int continuous;         /* 1: g is the sampled continuous Maxwellian of Q (no Newton; ablation) */
     double mu_ref, mu_omega; /* mu_ref > 0: tau = mu / P per point, mu = mu_ref theta^omega (Sec. 2, Eq. 5) */
     int limiter;            /* 1: Zhang-Shu positivity limiter on every stage output */
+    /* curvilinear geometry (NULL: the affine mesh of lo/hi) */
+    double *gx;             /* [npts][3] node coordinates */
+    double *Ja;             /* [npts][3][3] metric terms Ja^i_n (i: reference direction, n: component) */
+    double *Jd;             /* [npts] Jacobian determinant J */
+    double *fn;             /* [nelem][3][2][n1^2][3] common contravariant face normals (direction, side) */
 };
 
 /* ------------------------------------------------------------------------------------------ */
@@ -543,6 +555,10 @@ void oracle_destroy(orc_ctx *c)
     free(c->w);
     free(c->f);
     free(c->ghost);
+    free(c->gx);
+    free(c->Ja);
+    free(c->Jd);
+    free(c->fn);
     free(c);
 }
 
@@ -567,7 +583,8 @@ void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega)
 
 /* Zhang-Shu positivity limiter (Sec. 2.1, Eqs. 10-11), per element and velocity: with the element mean
  * fbar = sum_i W_i f_i / sum_i W_i (tensor Gauss-Legendre weights W) and fmin = min_i f_i, every node value
- * becomes fbar + beta (f_i - fbar), beta = min(|fbar / (fbar - fmin)|, 1), when some f_i < 0. */
+ * becomes fbar + beta (f_i - fbar), beta = min(|fbar / (fbar - fmin)|, 1), when some f_i < 0. On
+ * curvilinear elements the mean is over the physical element (weights W_i J_i). */
 int oracle_limit(const orc_ctx *c, double *f)
 {
     const int n1 = c->n1, np = c->np;
@@ -583,14 +600,19 @@ int oracle_limit(const orc_ctx *c, double *f)
 #pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < c->nelem; e++)
         for (int64_t k = 0; k < c->nvel; k++) {
-            double fbar = 0.0, fmin = INFINITY;
+            double fbar = 0.0, fmin = INFINITY, wsum = Wsum;
+            if (c->Jd) { /* curvilinear: the mean over the physical element, weights W J */
+                wsum = 0.0;
+                for (int i = 0; i < np; i++)
+                    wsum += W[i] * c->Jd[e * np + i];
+            }
             for (int i = 0; i < np; i++) {
                 const double v = f[(e * np + i) * c->nvel + k];
-                fbar += W[i] * v;
+                fbar += (c->Jd ? W[i] * c->Jd[e * np + i] : W[i]) * v;
                 if (v < fmin)
                     fmin = v;
             }
-            fbar /= Wsum;
+            fbar /= wsum;
             if (!(fmin < 0.0))
                 continue;
             double beta = fabs(fbar / (fbar - fmin));
@@ -630,6 +652,10 @@ int oracle_points(const orc_ctx *c, double *x)
 {
     if (!c || !x)
         return -1;
+    if (c->gx) {
+        memcpy(x, c->gx, sizeof(double) * 3 * c->npts);
+        return 0;
+    }
     for (int64_t e = 0; e < c->nelem; e++) {
         int ec[3];
         elem_coords(c, e, ec);
@@ -678,6 +704,151 @@ int oracle_get_f(const orc_ctx *c, double *f)
     if (!c || !f)
         return -1;
     memcpy(f, c->f, sizeof(double) * (size_t)(c->npts * c->nvel));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Curvilinear hexahedra: metric terms and face normals                                        */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Derivative along reference direction j of a nodal field u of one element, at every node. */
+static void ref_deriv(const orc_ctx *c, const double *u, int j, double *du)
+{
+    for (int i = 0; i < c->np; i++) {
+        int ic[3] = {i % c->n1, (i / c->n1) % c->n1, i / (c->n1 * c->n1)};
+        double s = 0.0;
+        for (int k = 0; k < c->n1; k++) {
+            int kc[3] = {ic[0], ic[1], ic[2]};
+            kc[j] = k;
+            s += c->D[ic[j] * c->n1 + k] * u[node_index(c, kc)];
+        }
+        du[i] = s;
+    }
+}
+
+/* Metric terms of one element from its node coordinates X[np][3]: Kopriva's conservative curl form
+ * Ja^i_n = -(curl_r V)_i with V_j = X_l dX_m/dr_j, (n, m, l) cyclic, every product interpolated at
+ * the nodes and differentiated with D; J = det(dX_n/dr_j). */
+static void element_metric(const orc_ctx *c, const double *X, double *Ja, double *J)
+{
+    const int np = c->np;
+    double *Xc = (double *)malloc(sizeof(double) * np * 4), *dX = (double *)malloc(sizeof(double) * 9 * np);
+    double *V = Xc + np, *dV = (double *)malloc(sizeof(double) * 9 * np);
+    for (int n = 0; n < 3; n++) {
+        for (int i = 0; i < np; i++)
+            Xc[i] = X[3 * i + n];
+        for (int j = 0; j < 3; j++)
+            ref_deriv(c, Xc, j, dX + (n * 3 + j) * np); /* dX[n][j] = dX_n / dr_j */
+    }
+    for (int n = 0; n < 3; n++) {
+        const int m = (n + 1) % 3, l = (n + 2) % 3;
+        /* V_j = X_l dX_m/dr_j and its derivatives dV[j][k] = d V_j / d r_k */
+        for (int j = 0; j < 3; j++) {
+            for (int i = 0; i < np; i++)
+                V[i] = X[3 * i + l] * dX[(m * 3 + j) * np + i];
+            for (int k = 0; k < 3; k++)
+                ref_deriv(c, V, k, dV + (j * 3 + k) * np);
+        }
+        for (int i = 0; i < np; i++) {
+            /* curl components: (dV3/dr2 - dV2/dr3, dV1/dr3 - dV3/dr1, dV2/dr1 - dV1/dr2) */
+            const double cu[3] = {dV[(2 * 3 + 1) * np + i] - dV[(1 * 3 + 2) * np + i],
+                                  dV[(0 * 3 + 2) * np + i] - dV[(2 * 3 + 0) * np + i],
+                                  dV[(1 * 3 + 0) * np + i] - dV[(0 * 3 + 1) * np + i]};
+            for (int r = 0; r < 3; r++)
+                Ja[(i * 3 + r) * 3 + n] = -cu[r];
+        }
+    }
+    for (int i = 0; i < np; i++) {
+        double M[3][3];
+        for (int n = 0; n < 3; n++)
+            for (int j = 0; j < 3; j++)
+                M[n][j] = dX[(n * 3 + j) * np + i];
+        J[i] = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+               M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    }
+    free(Xc);
+    free(dX);
+    free(dV);
+}
+
+/* Own element's Ja^d interpolated to face point ln of its face (d, side). */
+static void face_metric(const orc_ctx *c, int64_t e, int d, int side, int ln, double *N)
+{
+    int ic[3] = {0, 0, 0}, t = ln;
+    for (int q = 0; q < 3; q++) {
+        if (q == d)
+            continue;
+        ic[q] = t % c->n1;
+        t /= c->n1;
+    }
+    const double *l = side ? c->lp : c->lm;
+    N[0] = N[1] = N[2] = 0.0;
+    for (int j = 0; j < c->n1; j++) {
+        ic[d] = j;
+        const double *a = c->Ja + ((e * c->np + node_index(c, ic)) * 3 + d) * 3;
+        for (int n = 0; n < 3; n++)
+            N[n] += l[j] * a[n];
+    }
+}
+
+int oracle_set_geometry(orc_ctx *c, const double *x)
+{
+    if (!c || !x || c->dim != 3)
+        return -1;
+    for (int fc = 0; fc < 6; fc++)
+        if (c->bc[fc] == ORC_WALL)
+            return -1;
+    const int nf = c->n1 * c->n1;
+    c->gx = (double *)realloc(c->gx, sizeof(double) * 3 * c->npts);
+    c->Ja = (double *)realloc(c->Ja, sizeof(double) * 9 * c->npts);
+    c->Jd = (double *)realloc(c->Jd, sizeof(double) * c->npts);
+    c->fn = (double *)realloc(c->fn, sizeof(double) * (size_t)(c->nelem * 3 * 2 * nf * 3));
+    if (!c->gx || !c->Ja || !c->Jd || !c->fn)
+        return -1;
+    memcpy(c->gx, x, sizeof(double) * 3 * c->npts);
+    int bad = 0;
+    for (int64_t e = 0; e < c->nelem; e++) {
+        element_metric(c, x + 3 * e * c->np, c->Ja + 9 * e * c->np, c->Jd + e * c->np);
+        for (int i = 0; i < c->np; i++)
+            if (!(c->Jd[e * c->np + i] > 0.0))
+                bad++;
+    }
+    /* single-valued face normals: the mean of both elements' interpolated Ja^d on interior and periodic
+     * faces, the element's own on a boundary face */
+    for (int64_t e = 0; e < c->nelem; e++) {
+        int ec[3];
+        elem_coords(c, e, ec);
+        for (int d = 0; d < 3; d++)
+            for (int side = 0; side < 2; side++) {
+                int nc[3] = {ec[0], ec[1], ec[2]};
+                nc[d] += side ? 1 : -1;
+                const int outside = nc[d] < 0 || nc[d] >= c->ne[d];
+                const int periodic = c->bc[2 * d + side] == ORC_PERIODIC;
+                nc[d] = (nc[d] + c->ne[d]) % c->ne[d];
+                const int64_t en = elem_index(c, nc);
+                for (int ln = 0; ln < nf; ln++) {
+                    double N[3], Nn[3];
+                    face_metric(c, e, d, side, ln, N);
+                    if (!outside || periodic) {
+                        face_metric(c, en, d, 1 - side, ln, Nn);
+                        for (int n = 0; n < 3; n++)
+                            N[n] = 0.5 * (N[n] + Nn[n]);
+                    }
+                    memcpy(c->fn + ((((e * 3 + d) * 2 + side) * nf + ln) * 3), N, sizeof N);
+                }
+            }
+    }
+    return bad ? -2 : 0;
+}
+
+int oracle_metric(const orc_ctx *c, double *Ja, double *J)
+{
+    if (!c || !c->Ja)
+        return -1;
+    if (Ja)
+        memcpy(Ja, c->Ja, sizeof(double) * 9 * c->npts);
+    if (J)
+        memcpy(J, c->Jd, sizeof(double) * c->npts);
     return 0;
 }
 
@@ -745,10 +916,69 @@ static double wall_density(const orc_ctx *c, const double *f, int64_t e, int d, 
     return out / in;
 }
 
+/* The residual on curvilinear hexahedra: along every reference line of direction d, the nodal fluxes
+ * F_j = (Ja^d . xi) f_j, their derivative D F, and the FR correction with the upwind common flux of the
+ * face normal N (Eq. 9 with u_n = N . xi, positive in +r_d); R = -(sum_d dF_d) / J. */
+static int residual_curved(const orc_ctx *c, const double *f, double *R)
+{
+    const int n1 = c->n1, nf = n1 * n1;
+    memset(R, 0, sizeof(double) * (size_t)(c->npts * c->nvel));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < c->nelem; e++) {
+        int ec[3];
+        elem_coords(c, e, ec);
+        for (int d = 0; d < 3; d++)
+            for (int ln = 0; ln < nf; ln++) {
+                int ic[3] = {0, 0, 0}, t = ln;
+                for (int q = 0; q < 3; q++) {
+                    if (q == d)
+                        continue;
+                    ic[q] = t % n1;
+                    t /= n1;
+                }
+                int64_t pts[MAXN];
+                for (int j = 0; j < n1; j++) {
+                    int jc[3] = {ic[0], ic[1], ic[2]};
+                    jc[d] = j;
+                    pts[j] = e * c->np + node_index(c, jc);
+                }
+                const double *NL = c->fn + (((e * 3 + d) * 2 + 0) * nf + ln) * 3;
+                const double *NR = c->fn + (((e * 3 + d) * 2 + 1) * nf + ln) * 3;
+                for (int64_t k = 0; k < c->nvel; k++) {
+                    const double *v = c->xi + 3 * k;
+                    double fl[MAXN], F[MAXN], fL = 0.0, fR = 0.0, FL = 0.0, FR = 0.0;
+                    for (int j = 0; j < n1; j++) {
+                        const double *a = c->Ja + (pts[j] * 3 + d) * 3;
+                        fl[j] = f[pts[j] * c->nvel + k];
+                        F[j] = (a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) * fl[j];
+                        fL += c->lm[j] * fl[j];
+                        fR += c->lp[j] * fl[j];
+                        FL += c->lm[j] * F[j];
+                        FR += c->lp[j] * F[j];
+                    }
+                    const double uL = NL[0] * v[0] + NL[1] * v[1] + NL[2] * v[2];
+                    const double uR = NR[0] * v[0] + NR[1] * v[1] + NR[2] * v[2];
+                    const double FIL = uL > 0 ? uL * exterior_value(c, f, ec, d, 0, ic, k, 0.0) : uL * fL;
+                    const double FIR = uR > 0 ? uR * fR : uR * exterior_value(c, f, ec, d, 1, ic, k, 0.0);
+                    for (int i = 0; i < n1; i++) {
+                        double dF = 0.0;
+                        for (int j = 0; j < n1; j++)
+                            dF += c->D[i * n1 + j] * F[j];
+                        dF += (FIL - FL) * c->dgl[i] + (FIR - FR) * c->dgr[i];
+                        R[pts[i] * c->nvel + k] -= dF / c->Jd[pts[i]];
+                    }
+                }
+            }
+    }
+    return 0;
+}
+
 int oracle_residual(const orc_ctx *c, const double *f, double *R)
 {
     if (!c || !f || !R)
         return -1;
+    if (c->Ja)
+        return residual_curved(c, f, R);
     const int n1 = c->n1;
     memset(R, 0, sizeof(double) * (size_t)(c->npts * c->nvel));
 #pragma omp parallel for schedule(dynamic, 1)
@@ -929,6 +1159,21 @@ double oracle_dt(const orc_ctx *c, double cfl)
             s += fabs(c->xi[3 * k + d]) / c->h[d];
         if (s > smax)
             smax = s;
+    }
+    if (c->Ja) { /* curvilinear: max over nodes of sum_d |Ja^d . xi| / (2 J) (the affine value above) */
+        smax = 0.0;
+        for (int64_t i = 0; i < c->npts; i++)
+            for (int64_t k = 0; k < c->nvel; k++) {
+                const double *v = c->xi + 3 * k;
+                double s = 0.0;
+                for (int d = 0; d < 3; d++) {
+                    const double *a = c->Ja + (i * 3 + d) * 3;
+                    s += fabs(a[0] * v[0] + a[1] * v[1] + a[2] * v[2]);
+                }
+                s /= 2.0 * c->Jd[i];
+                if (s > smax)
+                    smax = s;
+            }
     }
     double dt = cfl / smax;
     if (c->collide && c->tau < dt)

@@ -119,6 +119,18 @@ void oracle_set_limiter(orc_ctx *c, int on);
  * moments; mu_ref <= 0 restores the constant tau given at creation (which must stay > 0). */
 void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega);
 
+/* Curvilinear hexahedra (dim = 3; no diffuse walls): x[n_x][3] are the physical coordinates of every
+ * solution node (point order as above); each element is the degree-p interpolant of its nodes. The
+ * metric terms Ja^i_n (Kopriva's conservative curl form) and J are computed here, the advection
+ * becomes the reference-space FR residual of (Ja^i . xi) f over J, with face normals averaged between
+ * the two elements of a face, the limiter's mean is J-weighted and oracle_dt uses the metric.
+ * Returns 0, -2 if some node has J <= 0, -1 on bad input. */
+int oracle_set_geometry(orc_ctx *c, const double *x);
+
+/* Metric terms Ja[n_x][3][3] (reference direction i, component n) and J[n_x] of the geometry set by
+ * oracle_set_geometry (either pointer may be NULL); -1 without a geometry. */
+int oracle_metric(const orc_ctx *c, double *Ja, double *J);
+
 /* Apply the limiter to f[n_x][N_v] in place (element mean with the tensor Gauss-Legendre weights). */
 int oracle_limit(const orc_ctx *c, double *f);
 

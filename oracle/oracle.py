@@ -73,6 +73,8 @@ def lib():
             L.oracle_set_limiter.argtypes = [C.c_void_p, C.c_int]
             L.oracle_limit.argtypes = [C.c_void_p, dp]
             L.oracle_set_viscosity.argtypes = [C.c_void_p, C.c_double, C.c_double]
+            L.oracle_set_geometry.argtypes = [C.c_void_p, dp]
+            L.oracle_metric.argtypes = [C.c_void_p, dp, dp]
             _lib = L
     return _lib
 
@@ -226,6 +228,20 @@ class Problem:
     def set_viscosity(self, mu_ref, omega):
         """tau = mu_ref theta^omega / (rho theta) per point (mu_ref <= 0: the constant tau)."""
         lib().oracle_set_viscosity(self.h, float(mu_ref), float(omega))
+
+    def set_geometry(self, x):
+        """Curvilinear hexahedra: physical coordinates x [n_x, 3] of every solution node."""
+        x = _f64(x, (self.npts, 3))
+        rc = lib().oracle_set_geometry(self.h, _d(x))
+        if rc != 0:
+            raise ValueError(f"oracle_set_geometry: {rc}")
+
+    def metric(self):
+        """(Ja [n_x, 3, 3] with Ja[:, i, n] = J d r_i / d x_n, J [n_x]) of the curvilinear geometry."""
+        Ja = np.zeros((self.npts, 3, 3))
+        J = np.zeros(self.npts)
+        assert lib().oracle_metric(self.h, _d(Ja), _d(J)) == 0
+        return Ja, J
 
     def set_limiter(self, on):
         lib().oracle_set_limiter(self.h, int(bool(on)))

@@ -196,6 +196,31 @@ def smooth_prim(x: np.ndarray, dim: int, seed: int = 0, amp: float = 0.2) -> np.
     return P
 
 
+def curved_nodes(x: np.ndarray, lo, hi, nelem, eps: float = 0.1, kind: str = "bump") -> np.ndarray:
+    """Physical coordinates of the solution nodes of a curvilinear hexahedral mesh, from the affine node
+    coordinates x [n, 3] of the box [lo, hi] with nelem elements per direction.
+
+    kind = "bump": X = x + eps (h_x b(y), h_y b(z), h_z b(x)) with b = 4 t (1 - t) of the element-local
+    coordinate t in [0, 1] of the other direction: quadratic in every element (exact at p >= 2),
+    continuous and periodic, faces curved, volume kept.
+    kind = "sine": X = x + eps (h_x s(y), h_y s(z), h_z s(x)) with s = sin(2 pi (t - lo) / L) over the
+    whole box: smooth and periodic but not polynomial per element."""
+    lo, hi, ne = np.asarray(lo, float), np.asarray(hi, float), np.asarray(nelem)
+    h = (hi - lo) / ne
+    X = np.array(x, dtype=float, copy=True)
+
+    def disp(d):
+        t = (x[:, d] - lo[d]) / h[d]
+        if kind == "bump":
+            tl = t - np.floor(t)
+            return 4.0 * tl * (1.0 - tl)
+        return np.sin(TWO_PI * (x[:, d] - lo[d]) / (hi[d] - lo[d]))
+
+    for d in range(3):
+        X[:, d] += eps * h[d] * disp((d + 1) % 3)
+    return X
+
+
 def noise(shape, seed: int = 0, amp: float = 0.05) -> np.ndarray:
     """Seeded multiplicative perturbation factors 1 + amp * U(-1, 1)."""
     rng = np.random.default_rng(seed)
