@@ -338,6 +338,28 @@ def bench_planar(steps: int, warmup: int, stream, torch) -> dict:
     return out
 
 
+def bench_curved(steps: int, warmup: int, stream, torch) -> dict:
+    """The Taylor-Green workload on curvilinear hexahedra: the box's solution nodes displaced by the
+    smooth periodic sine mapping (amplitude 0.3 element widths), metric terms from bgk_set_geometry,
+    the curvilinear stage kernel (per-lane upwinding, reference-space flux)."""
+    from paper_2308_06196_gb300.bgk import Solver
+
+    c = W.config(WORKLOAD)
+    k = W.mesh_kwargs(c)
+    s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
+    s.set_stream(stream.cuda_stream)
+    X = W.curved_nodes(s.points(), c["lo"], c["hi"], c["nelem"], 0.3, kind="sine")
+    s.set_geometry(X)
+    s.set_state(W.prim_field(WORKLOAD, X))
+    g = s.autotune()
+    dt = s.dt(c["cfl"])
+    ms, st = timed_steps(s, dt, steps, warmup, stream, torch)
+    out = {"workload": "taylor_green on curvilinear hexahedra (sine mapping, 0.3 h)", "dof": s.ndof,
+           "value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "dt": dt, "tiles_per_task": g, **st}
+    s.close()
+    return out
+
+
 def bench_variants(steps: int, warmup: int, stream, torch, k: dict, prim_dev, dt: float) -> dict:
     """The Taylor-Green workload with the widened rows switched on one at a time: the positivity
     limiter and the variable collision time (both in the general hexahedral kernel), and the
@@ -406,6 +428,8 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=3,
                     help="steps of the Taylor-Green variants: limiter, variable tau, ablation (0: skip)")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--curved-steps", type=int, default=3,
+                    help="steps of Taylor-Green on curvilinear hexahedra (0: skip)")
     ap.add_argument("--planar-steps", type=int, default=3,
                     help="steps of the m = 2 planar shear workload (0: skip)")
     ap.add_argument("--batch-members", type=int, default=0,
@@ -559,6 +583,9 @@ def main():
     if args.mach5_steps > 0 and world == 1:
         mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch, args.mach5_yz_elements)
     ablation = None if (args.no_ablation or world > 1) else bench_ablation()
+    curved = None
+    if args.curved_steps > 0 and world == 1:
+        curved = bench_curved(args.curved_steps, warmup, stream, torch)
     planar = None
     if args.planar_steps > 0 and world == 1:
         planar = bench_planar(args.planar_steps, warmup, stream, torch)
@@ -609,6 +636,7 @@ def main():
         "variants": variants,
         "ablation": ablation,
         "planar": planar,
+        "curved": curved,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

@@ -163,6 +163,18 @@ double bgk_dt(const bgk_ctx *ctx, double cfl);
  * chosen length (0 for the all-FP64 form, which has no task shape). */
 int bgk_autotune(bgk_ctx *ctx, int *g_out);
 
+/* Curvilinear hexahedra (the mapped elements of Sec. 2.1's FR on unstructured curved meshes; dim = 3,
+ * FP32-split form, no diffuse walls). x is host memory, FP64, [n_x][3]: the physical coordinates of
+ * every solution node in the point order of bgk_points (element-major, x-fastest; the mesh connectivity
+ * and periodicity stay those of bgk_create). Each element maps the reference cube by the degree-p
+ * interpolant of its nodes. The library computes in FP64 the metric terms Ja^i (Kopriva's conservative
+ * curl form, so a constant state is kept to round-off), J, and the face normals (the mean of the two
+ * elements' interpolated Ja^i on a shared face), and from then on advects the reference-space flux
+ * (Ja^i . xi) f / J with per-lane upwinding at every face point (Eq. 9 with u_n = Ja^i . xi). The
+ * limiter's element mean becomes J-weighted; bgk_points returns x; bgk_dt uses the metric. The state
+ * is kept. Returns BGK_EINVAL for another dim/precision, diffuse walls, or a node with J <= 0. */
+int bgk_set_geometry(bgk_ctx *ctx, const double *x);
+
 /* Launch timing: when on, bgk_step launches its kernels directly (not through the CUDA graph) and
  * brackets every stage and Newton launch with CUDA events on the context stream. bgk_timing()
  * synchronises and returns the summed milliseconds and launch counts since timing was switched on,

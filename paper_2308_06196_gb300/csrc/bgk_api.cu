@@ -200,6 +200,11 @@ struct bgk_ctx {
     Ops64 ops64{};
     double *Q = nullptr, *prim = nullptr, *prim_in = nullptr;
     double *itau64 = nullptr;  // per-point 1/tau of the FP64 form (variable collision time)
+    // curvilinear hexahedra (bgk_set_geometry)
+    float4 *met = nullptr, *fnm = nullptr;
+    float *iwj = nullptr;
+    std::vector<double> geom;  // node coordinates [n_x][3]
+    double curv_smax = 0.0;    // max over nodes and velocities of sum_d |Ja^d . xi| / (2 J)
     int *err = nullptr;
     int64_t bytes = 0;
     Ops ops{};
@@ -282,6 +287,9 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.inv_tau = (float)(1.0 / c->tau);
     A.limiter = c->opts.limiter != 0;
     A.vtau = c->opts.mu_ref > 0.0;
+    A.met = c->met;
+    A.fnm = c->fnm;
+    A.iwj = c->iwj;
     return A;
 }
 
@@ -593,7 +601,7 @@ void bgk_destroy(bgk_ctx *c)
     void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
-                    c->fpar64, c->w64, c->itau64};
+                    c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -930,6 +938,10 @@ int bgk_points(const bgk_ctx *c, double *x)
 {
     if (!c || !x)
         return BGK_EINVAL;
+    if (!c->geom.empty()) {
+        std::copy(c->geom.begin(), c->geom.end(), x);
+        return BGK_OK;
+    }
     for (int64_t pt = 0; pt < c->npts; pt++) {
         const int e = (int)(pt / c->NP), i = (int)(pt % c->NP);
         const int ec[3] = {e % c->ne[0], (e / c->ne[0]) % c->ne[1], e / (c->ne[0] * c->ne[1])};
@@ -1113,6 +1125,8 @@ double bgk_dt(const bgk_ctx *c, double cfl)
             s += fabs(c->vlo[d] + kk[d] * c->dv[d]) / c->h[d];
         smax = std::max(smax, s);
     }
+    if (c->met)  // curvilinear: the metric's transport speed in reference units (the affine value above)
+        smax = c->curv_smax;
     double tmin = c->tau;
     if (c->opts.mu_ref > 0.0) {  // the smallest collision time of the current state
         std::vector<double> Q(c->npts * 5);
@@ -1128,6 +1142,161 @@ double bgk_dt(const bgk_ctx *c, double cfl)
         }
     }
     return std::min(cfl / smax, tmin);
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// Curvilinear hexahedra. Every element maps the reference cube by the degree-p interpolant of its
+// solution-node coordinates. Metric terms (Kopriva's conservative curl form, so the discrete metric
+// identities hold and a constant state is kept): Ja^i_n = -(curl_r (X_l grad_r X_m))_i for (n, m, l)
+// cyclic, with every product taken at the nodes and differentiated with the FR derivative matrix.
+// Face normals: Ja^d interpolated to the face from both elements and averaged (single-valued, so the
+// upwind flux is conservative); a non-periodic boundary face keeps the element's own.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+// d/dr_j of a nodal field u[NP] (x fastest) with the FP64 derivative matrix
+void dref(const bgk_ctx *c, const double *u, int j, double *out)
+{
+    const int n = c->N1, stride = j == 0 ? 1 : (j == 1 ? n : n * n);
+    for (int i = 0; i < c->NP; i++) {
+        const int ij = (i / stride) % n, base = i - ij * stride;
+        double a = 0.0;
+        for (int k = 0; k < n; k++)
+            a += c->ops64.D[ij][k] * u[base + k * stride];
+        out[i] = a;
+    }
+}
+
+}  // namespace
+
+int bgk_set_geometry(bgk_ctx *c, const double *x)
+{
+    if (!c || !x)
+        return BGK_EINVAL;
+    if (c->dim != 3 || c->prec != BGK_FP32_SPLIT || c->has_wall)
+        return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3) in the FP32-split form "
+                                   "without diffuse walls");
+    const int NP = c->NP, N1 = c->N1, NQ = N1 * N1, E = c->E;
+    std::vector<double> Ja((size_t)c->npts * 9), J(c->npts);
+    std::vector<double> X(NP), dX(9 * (size_t)NP), V(NP), dV(9 * (size_t)NP);
+    int64_t bad = 0;
+    for (int e = 0; e < E; e++) {
+        const double *xe = x + (int64_t)e * NP * 3;
+        for (int n = 0; n < 3; n++) {  // dX[n][j] = dX_n / dr_j
+            for (int i = 0; i < NP; i++)
+                X[i] = xe[3 * i + n];
+            for (int j = 0; j < 3; j++)
+                dref(c, X.data(), j, &dX[(size_t)(3 * n + j) * NP]);
+        }
+        double *Je = &J[(size_t)e * NP], *Jae = &Ja[(size_t)e * NP * 9];
+        for (int i = 0; i < NP; i++) {
+            double M[3][3];
+            for (int n = 0; n < 3; n++)
+                for (int j = 0; j < 3; j++)
+                    M[n][j] = dX[(size_t)(3 * n + j) * NP + i];
+            Je[i] = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                    M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+            bad += !(Je[i] > 0.0);
+        }
+        for (int n = 0; n < 3; n++) {
+            const int m = (n + 1) % 3, l = (n + 2) % 3;
+            for (int j = 0; j < 3; j++) {  // V_j = X_l dX_m/dr_j; dV[j][k] = d V_j / d r_k
+                for (int i = 0; i < NP; i++)
+                    V[i] = xe[3 * i + l] * dX[(size_t)(3 * m + j) * NP + i];
+                for (int k = 0; k < 3; k++)
+                    dref(c, V.data(), k, &dV[(size_t)(3 * j + k) * NP]);
+            }
+            for (int i = 0; i < NP; i++) {
+                auto g = [&](int j, int k) { return dV[(size_t)(3 * j + k) * NP + i]; };
+                Jae[(size_t)i * 9 + 0 * 3 + n] = -(g(2, 1) - g(1, 2));
+                Jae[(size_t)i * 9 + 1 * 3 + n] = -(g(0, 2) - g(2, 0));
+                Jae[(size_t)i * 9 + 2 * 3 + n] = -(g(1, 0) - g(0, 1));
+            }
+        }
+    }
+    if (bad)
+        return fail(c, BGK_EINVAL, "curvilinear geometry: J <= 0 at " + std::to_string(bad) + " nodes");
+    // face normals [E][3][2][NQ] and the per-element sum of W J
+    auto own_face = [&](int e, int d, int side, int ln, double *Nv) {
+        const int a = ln % N1, bq = ln / N1;  // face point: the two other coordinates in increasing axis order
+        int ic[3];
+        Nv[0] = Nv[1] = Nv[2] = 0.0;
+        for (int j = 0; j < N1; j++) {
+            if (d == 0) { ic[0] = j; ic[1] = a; ic[2] = bq; }
+            else if (d == 1) { ic[0] = a; ic[1] = j; ic[2] = bq; }
+            else { ic[0] = a; ic[1] = bq; ic[2] = j; }
+            const int node = ic[0] + N1 * (ic[1] + N1 * ic[2]);
+            const double lj = side ? c->ops64.lp[j] : c->ops64.lm[j];
+            for (int n = 0; n < 3; n++)
+                Nv[n] += lj * Ja[((size_t)e * NP + node) * 9 + d * 3 + n];
+        }
+    };
+    std::vector<float4> met((size_t)E * NP * 3), fn((size_t)E * 6 * NQ);
+    std::vector<float> iwj(E);
+    for (int e = 0; e < E; e++) {
+        const int ec[3] = {e % c->ne[0], (e / c->ne[0]) % c->ne[1], e / (c->ne[0] * c->ne[1])};
+        double wj = 0.0;
+        for (int i = 0; i < NP; i++) {
+            const double W = c->ops64.wq[i % N1] * c->ops64.wq[(i / N1) % N1] * c->ops64.wq[i / NQ];
+            const double Jv = J[(size_t)e * NP + i];
+            const double *a = &Ja[((size_t)e * NP + i) * 9];
+            wj += W * Jv;
+            for (int d = 0; d < 3; d++)
+                met[((size_t)e * NP + i) * 3 + d] = make_float4((float)a[d * 3], (float)a[d * 3 + 1], (float)a[d * 3 + 2],
+                                                               (float)(d == 1 ? W * Jv : 1.0 / Jv));
+        }
+        iwj[e] = (float)(1.0 / wj);
+        for (int d = 0; d < 3; d++)
+            for (int side = 0; side < 2; side++) {
+                int nc[3] = {ec[0], ec[1], ec[2]};
+                nc[d] += side ? 1 : -1;
+                const bool outside = nc[d] < 0 || nc[d] >= c->ne[d];
+                const bool shared = !outside || c->bc[2 * d + side] == BGK_BC_PERIODIC;
+                nc[d] = (nc[d] + c->ne[d]) % c->ne[d];
+                const int en = nc[0] + c->ne[0] * (nc[1] + c->ne[1] * nc[2]);
+                for (int ln = 0; ln < NQ; ln++) {
+                    double Nv[3], Nn[3];
+                    own_face(e, d, side, ln, Nv);
+                    if (shared) {
+                        own_face(en, d, 1 - side, ln, Nn);
+                        for (int n = 0; n < 3; n++)
+                            Nv[n] = 0.5 * (Nv[n] + Nn[n]);
+                    }
+                    fn[(((size_t)e * 3 + d) * 2 + side) * NQ + ln] = make_float4((float)Nv[0], (float)Nv[1], (float)Nv[2], 0.f);
+                }
+            }
+    }
+    // stable-step speed: the maximum over a node's velocities of the convex sum_d |Ja^d . xi| is at a
+    // corner of the velocity box
+    double smax = 0.0;
+    for (int64_t i = 0; i < c->npts; i++)
+        for (int corner = 0; corner < 8; corner++) {
+            double v[3];
+            for (int d = 0; d < 3; d++)
+                v[d] = c->vlo[d] + ((corner >> d) & 1 ? (c->nv[d] - 1) * c->dv[d] : 0.0);
+            double sum = 0.0;
+            for (int d = 0; d < 3; d++) {
+                const double *a = &Ja[(size_t)i * 9 + d * 3];
+                sum += fabs(a[0] * v[0] + a[1] * v[1] + a[2] * v[2]);
+            }
+            smax = std::max(smax, sum / (2.0 * J[i]));
+        }
+    if (!c->met) {
+        CK(dalloc(c, &c->met, met.size()));
+        CK(dalloc(c, &c->fnm, fn.size()));
+        CK(dalloc(c, &c->iwj, iwj.size()));
+    }
+    CK(cudaMemcpy(c->met, met.data(), met.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->fnm, fn.data(), fn.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->iwj, iwj.data(), iwj.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->geom.assign(x, x + c->npts * 3);
+    c->curv_smax = smax;
+    if (c->gexec) {  // the captured launches carry the old arguments
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return BGK_OK;
 }
 
 // Tile-shape autotuner: tiles per task G, per (mesh, degree, velocity grid), cached for the process.
@@ -1159,7 +1328,8 @@ int bgk_autotune(bgk_ctx *c, int *g_out)
     }
     char key[256];
     snprintf(key, sizeof key, "%d/%d/%d,%d,%d/%d,%d,%d/%zu/%d", c->dim, c->p, c->nv[0], c->nv[1], c->nv[2], c->ne[0],
-             c->ne[1], c->ne[2], c->chunks.size(), (int)(c->has_wall || c->has_force || c->bc[0] || c->bc[2] || c->bc[4]));
+             c->ne[1], c->ne[2], c->chunks.size(),
+             (int)(c->has_wall || c->has_force || c->bc[0] || c->bc[2] || c->bc[4]) + 2 * (c->met != nullptr));
     for (auto &kv : g_tuned)
         if (kv.first == key) {
             set_task_length(c, kv.second);

@@ -81,6 +81,12 @@ struct StageArgs {
     float kb, kg;        // b (1 - dt / tau) and b dt / tau: the weights of f_s and of the Maxwellian.
                          // Rounded so that an + b = 1 and kb + kg = b hold exactly in FP32, so a state
                          // equal to f^n and to its Maxwellian is kept up to unbiased rounding.
+    // curvilinear hexahedra (null on the affine mesh):
+    const float4 *met;   // [E][NP][3] metric rows Ja^d (d = 0, 1, 2) of every node; .w of row 0 and row 2
+                         // = 1/J, .w of row 1 = W J (tensor Gauss-Legendre weight / 8 times J)
+    const float4 *fnm;   // [E][3][2][N1^2] shared contravariant face normal N (direction, low/high side,
+                         // face point); N . xi > 0 is flow towards +r_d
+    const float *iwj;    // [E] 1 / sum_i W_i J_i (the limiter's element mean over the physical element)
 };
 
 struct NewtonArgs {

@@ -38,12 +38,60 @@ struct Stage3Smem {
     float wpsi[5][kWarp];         // w psi of the tile's velocities
 };
 
+// Curvilinear hexahedra: the element's metric rows and face normals (see StageArgs), placed after the
+// stage's shared memory at a 16-byte boundary.
+template <int N1>
+struct CurvSmem {
+    float4 met[N1 * N1 * N1][3];
+    float4 fnm[3][2][N1 * N1];
+    float iwj;
+};
+
+template <int N1, int GEN, int CURV>
+constexpr int stage3_smem_bytes()
+{
+    return CURV ? (int)((sizeof(Stage3Smem<N1, GEN>) + 15) / 16 * 16 + sizeof(CurvSmem<N1>))
+                : (int)sizeof(Stage3Smem<N1, GEN>);
+}
+
+// Curvilinear line of direction d (Sec. 2.1, Eqs. 7-9 on the mapped element): with the nodal fluxes
+// F_j = u_j f_j (u_j = Ja^d . xi at node j), s_i = (D F)_i + gl'_i (F^I_L - F_L) + gr'_i (F^I_R - F_R)
+// = sum_j DL_ij F_j + gl'_i F^I_L + gr'_i (F^I_R - sum_j lp_j F_j), where F_L, F_R are the interpolated
+// traces of F and F^I the upwind common fluxes of the face normals' u_L, u_R (Eq. 9): the exterior trace
+// tL / tR where the face flow enters the element, the element's own trace of f where it leaves.
+template <int N1>
+__device__ __forceinline__ void curv_line(float (&sv)[N1], const float (&fl)[N1], const float (&u)[N1], float uL,
+                                          float uR, float tL, float tR, const Ops &op)
+{
+    float F[N1], oL = 0.f, oR = 0.f, FR = 0.f;
+#pragma unroll
+    for (int j = 0; j < N1; j++) {
+        F[j] = u[j] * fl[j];
+        oL = fmaf(op.lm[j], fl[j], oL);
+        oR = fmaf(op.lp[j], fl[j], oR);
+        FR = fmaf(op.lp[j], F[j], FR);
+    }
+    const float FIL = uL * (uL > 0.f ? tL : oL);
+    const float FIR = uR * (uR < 0.f ? tR : oR);
+    const float cR = FIR - FR;
+#pragma unroll
+    for (int i = 0; i < N1; i++) {
+        float a = fmaf(op.gl[i], FIL, op.gr[i] * cR);
+#pragma unroll
+        for (int j = 0; j < N1; j++)
+            a = fmaf(op.DL[i][j], F[j], a);
+        sv[i] = a;
+    }
+}
+
 // OCT in 0..7: every tile of the launch lies in that sign octant (bit d set: xi_d >= 0, the upwind
 // neighbour in direction d is on the low side); OCT = 8: the octant is read per tile.
 // GEN = 0: every face periodic, no body force and one velocity spacing on all axes (the lean form;
 // the Maxwellian exponent needs only the sum of the squared grid indices); GEN = 1: Dirichlet and
 // diffuse-wall faces, the body-force source and per-axis spacings.
-template <int N1, int MODE, int OCT, int GEN>
+// CURV = 1 (with GEN = 1, OCT = 8): curvilinear hexahedra, the reference-space flux (Ja^d . xi) f and
+// per-lane upwinding at every face point from the shared face normal.
+template <int N1, int MODE, int OCT, int GEN, int CURV = 0>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTAS_P3_GEN : BGK_STAGE3_MINCTAS_P3)
                                                : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
 {
@@ -53,6 +101,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     using Sm = Stage3Smem<N1, GEN>;
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm &sm = *reinterpret_cast<Sm *>(smraw);
+    CurvSmem<N1> &cs = *reinterpret_cast<CurvSmem<N1> *>(smraw + (sizeof(Sm) + 15) / 16 * 16);  // CURV only
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;  // w: this warp's z-layer and y-slice
     const int E = A.mesh.nelem;
@@ -79,6 +128,14 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
             float4 *d4 = reinterpret_cast<float4 *>(&sm.fpar[0][0]);
             for (int q = tid; q < NP * kParamStride / 4; q += NT)
                 d4[q] = __ldg(f4 + q);
+        }
+        if constexpr (CURV) {
+            for (int q = tid; q < NP * 3; q += NT)
+                (&cs.met[0][0])[q] = __ldg(A.met + (int64_t)e * NP * 3 + q);
+            for (int q = tid; q < 6 * NQ; q += NT)
+                (&cs.fnm[0][0][0])[q] = __ldg(A.fnm + (int64_t)e * 6 * NQ + q);
+            if (tid == 0)
+                cs.iwj = __ldg(A.iwj + e);
         }
         // the general form reads 1/tau of its layer (variable collision time) before the first
         // tile's B1, from rows other warps loaded
@@ -162,6 +219,118 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 prefetch_fn(vl + 1);
             else
                 cp_commit();  // keep the group count per tile fixed
+            const float cz = -A.mesh.inv_h2[2] * x2 * bdt;
+            if constexpr (CURV) {
+                // curvilinear: kb f_s as above, then the x- and y-lines of layer w with the metric
+#pragma unroll
+                for (int q = 0; q < NQ; q++) {
+                    float kbq = kb;
+                    if (A.vtau)
+                        kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
+                    acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
+                }
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    const int eL = upwind_neighbour(A.mesh, ec, d, true), eR = upwind_neighbour(A.mesh, ec, d, false);
+#pragma unroll
+                    for (int ln = 0; ln < N1; ln++) {
+                        float fl[N1], u[N1], sv[N1];
+                        int nd[N1];
+#pragma unroll
+                        for (int j = 0; j < N1; j++) {
+                            nd[j] = (d == 0 ? j + N1 * ln : ln + N1 * j) + NQ * w;
+                            fl[j] = f[nd[j] - NQ * w];
+                            const float4 m = cs.met[nd[j]][d];
+                            u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
+                        }
+                        const float4 nL = cs.fnm[d][0][ln + N1 * w], nR = cs.fnm[d][1][ln + N1 * w];
+                        const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
+                        const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
+                        float tL = 0.f, tR = 0.f;
+                        if (uL > 0.f) {  // inflow through the low face: the low neighbour's +1 trace or the ghost
+                            if (eL >= 0) {
+                                float v[N1];
+                                const float *nb = A.src + fidx(vl, eL, 0, lane, E, NP);
+#pragma unroll
+                                for (int j = 0; j < N1; j++)
+                                    v[j] = __ldg(nb + nd[j] * kWarp);
+                                tL = trace_line<N1, true>(v, A.ops);
+                            } else {
+                                tL = __ldg(A.ghost + (2 * d) * A.nslots + slot);
+                            }
+                        }
+                        if (uR < 0.f) {  // inflow through the high face
+                            if (eR >= 0) {
+                                float v[N1];
+                                const float *nb = A.src + fidx(vl, eR, 0, lane, E, NP);
+#pragma unroll
+                                for (int j = 0; j < N1; j++)
+                                    v[j] = __ldg(nb + nd[j] * kWarp);
+                                tR = trace_line<N1, false>(v, A.ops);
+                            } else {
+                                tR = __ldg(A.ghost + (2 * d + 1) * A.nslots + slot);
+                            }
+                        }
+                        curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
+#pragma unroll
+                        for (int j = 0; j < N1; j++)
+                            acc[nd[j] - NQ * w] = fmaf(-bdt * cs.met[nd[j]][0].w, sv[j], acc[nd[j] - NQ * w]);
+                    }
+                }
+                __syncthreads();  // B1: the element tile is complete
+                if (w == 0) {
+#pragma unroll
+                    for (int c = 0; c < 5; c++)
+                        sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+                }
+                // z-lines of slice iy = w (all layers) from the shared tile; unscaled sums to zc
+                const int eL = upwind_neighbour(A.mesh, ec, 2, true), eR = upwind_neighbour(A.mesh, ec, 2, false);
+#pragma unroll
+                for (int ln = 0; ln < N1; ln++) {
+                    float fl[N1], u[N1], sv[N1];
+                    int nd[N1];
+#pragma unroll
+                    for (int j = 0; j < N1; j++) {
+                        nd[j] = ln + N1 * w + NQ * j;
+                        fl[j] = sm.tile[b][nd[j]][lane];
+                        const float4 m = cs.met[nd[j]][2];
+                        u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
+                    }
+                    const float4 nL = cs.fnm[2][0][ln + N1 * w], nR = cs.fnm[2][1][ln + N1 * w];
+                    const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
+                    const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
+                    float tL = 0.f, tR = 0.f;
+                    if (uL > 0.f) {
+                        if (eL >= 0) {
+                            float v[N1];
+                            const float *nb = A.src + fidx(vl, eL, 0, lane, E, NP);
+#pragma unroll
+                            for (int j = 0; j < N1; j++)
+                                v[j] = __ldg(nb + nd[j] * kWarp);
+                            tL = trace_line<N1, true>(v, A.ops);
+                        } else {
+                            tL = __ldg(A.ghost + 4 * A.nslots + slot);
+                        }
+                    }
+                    if (uR < 0.f) {
+                        if (eR >= 0) {
+                            float v[N1];
+                            const float *nb = A.src + fidx(vl, eR, 0, lane, E, NP);
+#pragma unroll
+                            for (int j = 0; j < N1; j++)
+                                v[j] = __ldg(nb + nd[j] * kWarp);
+                            tR = trace_line<N1, false>(v, A.ops);
+                        } else {
+                            tR = __ldg(A.ghost + 5 * A.nslots + slot);
+                        }
+                    }
+                    curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        sm.zc[nd[j]][lane] = sv[j];
+                }
+                __syncthreads();  // B2: z-sums complete
+            } else {
             // upwind neighbour values: x-lines and y-lines of layer w, z-lines of slice iy = w
             float vx[N1][N1], vy[N1][N1], vz[N1][N1];
             const int enx = upwind_neighbour(A.mesh, ec, 0, l0);
@@ -191,8 +360,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
                 acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
             }
-            const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt,
-                        cz = -A.mesh.inv_h2[2] * x2 * bdt;
+            const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt;
             // upwind value on a non-periodic face: the Dirichlet ghost Maxwellian, or the diffuse-wall
             // Maxwellian scaled by the wall density of the face point (face point of every line of
             // this warp: its index + N1 * w)
@@ -274,6 +442,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     sm.zc[q + NQ * j][lane] = sv[j];
             }
             __syncthreads();  // B2: z-sums complete
+            }
             // BGK source towards the conservative Maxwellian, Shu-Osher combination, store
             const float gm = __ldg(A.gmask + slot);
             const float cg = A.kg * gm, cf = bdt * gm;
@@ -307,7 +476,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     if (q >= NQ)
                         break;
                     const int i = q + NQ * w;
-                    const float a = fmaf(cz, sm.zc[i][lane], acc[q]);
+                    const float a = CURV ? fmaf(-bdt * cs.met[i][0].w, sm.zc[i][lane], acc[q])
+                                         : fmaf(cz, sm.zc[i][lane], acc[q]);
                     float gc = cg;
                     if (GEN && A.vtau) {  // kg = b - kb exactly, kb as in the accumulator above
                         const float itau = sl == 0 ? p67.x : p67.y;
@@ -320,7 +490,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     }
                     const float o = fmaf(gc, g[sl], a);
                     if (GEN && A.limiter) {  // stored after the limiter below
-                        lsum = fmaf(A.ops.wq[q % N1] * A.ops.wq[q / N1], o, lsum);
+                        lsum = fmaf(CURV ? cs.met[i][1].w : A.ops.wq[q % N1] * A.ops.wq[q / N1], o, lsum);
                         lmin = fminf(lmin, o);
                     } else {
                         __stcs(dst + i * kWarp, o);
@@ -331,7 +501,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
             if (GEN && A.limiter) {
                 // Zhang-Shu (Sec. 2.1, Eqs. 10-11): element mean and minimum of every velocity over
                 // the four layers, then the contraction of the values of this warp's layer
-                sm.lim[0][w][lane] = A.ops.wq[w] * lsum;
+                sm.lim[0][w][lane] = CURV ? lsum : A.ops.wq[w] * lsum;
                 sm.lim[1][w][lane] = lmin;
                 __syncthreads();  // B3 (the general form only)
                 float mean = 0.f, mn = sm.lim[1][0][lane];
@@ -340,6 +510,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     mean += sm.lim[0][lw][lane];
                     mn = fminf(mn, sm.lim[1][lw][lane]);
                 }
+                if (CURV)  // the physical element's mean: weights W J over their sum
+                    mean *= cs.iwj;
                 const float beta = mn < 0.f ? fminf(fabsf(mean / (mean - mn)), 1.f) : 1.f;
 #pragma unroll
                 for (int q = 0; q < NQ; q++) {
@@ -418,11 +590,12 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
 }
 
 
-template <int N1, int MODE, int OCT, int GEN>
+template <int N1, int MODE, int OCT, int GEN, int CURV = 0>
 cudaError_t launch3(const StageArgs &A, cudaStream_t s)
 {
     const int ngroups = (A.nvt + A.G - 1) / A.G;
-    k_stage3<N1, MODE, OCT, GEN><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3Smem<N1, GEN>), s>>>(A);
+    k_stage3<N1, MODE, OCT, GEN, CURV>
+        <<<A.mesh.nelem * ngroups, kWarp * N1, stage3_smem_bytes<N1, GEN, CURV>(), s>>>(A);
     return cudaGetLastError();
 }
 
@@ -438,6 +611,9 @@ cudaError_t prepare3()
         e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
     BGK_P3(0) BGK_P3(1) BGK_P3(2) BGK_P3(3) BGK_P3(4) BGK_P3(5) BGK_P3(6) BGK_P3(7) BGK_P3(8)
 #undef BGK_P3
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 stage3_smem_bytes<N1, 1, 1>());
     return e;
 }
 
@@ -464,6 +640,8 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
 {
     if (mode == 1)
         return launch3<N1, 1, 8, 0>(A, s);
+    if (A.met)  // curvilinear hexahedra: the general form with the metric, upwind side per lane
+        return launch3<N1, 0, 8, 1, 1>(A, s);
     // the lean form: periodic faces, no force, no limiter, constant tau, one velocity spacing on all axes
     bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
     for (int f = 0; f < 6; f++)

@@ -1,0 +1,142 @@
+"""Curvilinear hexahedra on the GPU (bgk_set_geometry) against the FP64 oracle with the same node
+coordinates: the affine mesh given as coordinates, the quadratic bump mesh and the sine mesh (not
+polynomial per element), periodic and with Dirichlet ends, with the J-weighted limiter and the
+variable collision time; free stream and conservation of the J-weighted totals; rejected set-ups."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2308_06196_gb300 import _build, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def make(ne, p, n=6, L=4.0, tau=0.05, bc=None, bcs=None, kind="bump", eps=0.15, limiter=False, **opts):
+    from paper_2308_06196_gb300.bgk import Solver
+
+    lo, hi = (0.0,) * 3, (1.0,) * 3
+    s = Solver(3, list(ne), lo, hi, p, (n,) * 3, (-L,) * 3, (L,) * 3, tau, bc=bc, bc_state=bcs, limiter=limiter,
+               **opts)
+    pr = orc.Problem(3, list(ne), lo, hi, p, (n,) * 3, (-L,) * 3, (L,) * 3, tau,
+                     bc=None if bc is None else np.asarray(bc).reshape(6),
+                     bc_state=None if bcs is None else np.asarray(bcs, dtype=float).reshape(30))
+    pr.set_limiter(limiter)
+    x = pr.points()
+    X = x if kind == "affine" else W.curved_nodes(x, lo, hi, ne, eps, kind=kind)
+    s.set_geometry(X)
+    pr.set_geometry(X)
+    return s, pr, X
+
+
+def tube():
+    bc = [[W.DIRICHLET, W.DIRICHLET], [0, 0], [0, 0]]
+    bcs = np.zeros((3, 2, 5))
+    bcs[0, 0] = [1.0, 0.2, 0.0, 0.0, 1.0]
+    bcs[0, 1] = [0.5, 0.2, 0.0, 0.0, 0.9]
+    return bc, bcs
+
+
+def test_affine_coordinates_match_the_affine_kernel():
+    from paper_2308_06196_gb300.bgk import Solver
+
+    ne, p = (3, 2, 3), 2
+    s, pr, X = make(ne, p, kind="affine")
+    a = Solver(3, list(ne), (0.0,) * 3, (1.0,) * 3, p, (6,) * 3, (-4.0,) * 3, (4.0,) * 3, 0.05, limiter=True)
+    prim = W.smooth_prim(X, 3, seed=1)
+    for x in (s, a, pr):
+        x.set_state(prim)
+    dt = pr.dt(0.1)
+    assert abs(s.dt(0.1) - dt) <= 1e-14 * dt
+    s.step(dt, 3)
+    a.step(dt, 3)
+    pr.step(dt, 3)
+    assert rel(s.moments(), a.moments()) < 2e-6
+    assert rel(s.moments(), pr.moments()) < 1e-5
+    assert rel(s.get_f(), pr.get_f()) < 1e-5
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("opts", [dict(), dict(chunks=1, vtiles_per_task=1)])
+def test_bump_mesh_vs_oracle(p, opts):
+    # 3 x 2 x 3 elements (a ragged element count), 6^3 velocities (octants of 27: padded tiles); at p = 1
+    # the trilinear interpolant of the bump mesh is a different (still curved) mesh, the same on both sides
+    s, pr, X = make((3, 2, 3), p, **opts)
+    pr.set_state(W.smooth_prim(X, 3, seed=10 + p))
+    f = pr.get_f() * W.noise((pr.npts, pr.nvel), seed=20 + p, amp=0.05)
+    s.set_f(f)
+    pr.set_f(f.astype(np.float32).astype(np.float64))
+    dt = pr.dt(0.1)
+    s.step(dt, 3)
+    pr.step(dt, 3)
+    assert rel(s.get_f(), pr.get_f()) < 1e-5
+    assert rel(s.moments(), pr.moments()) < 1e-5
+
+
+def test_sine_mesh_tube_with_limiter_vs_oracle():
+    bc, bcs = tube()
+    s, pr, X = make((4, 2, 2), 2, n=8, L=5.0, tau=2e-3, bc=bc, bcs=bcs, kind="sine", eps=0.3, limiter=True)
+    prim = W.prim_sod(X, (1.0, 1.0), (0.25, 0.8))
+    s.set_state(prim)
+    pr.set_state(prim)
+    dt = pr.dt(0.1)
+    s.step(dt, 5)
+    pr.step(dt, 5)
+    assert rel(s.moments(), pr.moments()) < 1e-5
+    assert rel(s.get_f(), pr.get_f()) < 1e-5
+
+
+def test_variable_tau_on_a_curved_mesh_vs_oracle():
+    s, pr, X = make((3, 2, 2), 2, n=6, tau=1.0, mu_ref=2e-3, mu_omega=0.81)
+    pr.set_viscosity(2e-3, 0.81)
+    prim = W.smooth_prim(X, 3, seed=4, amp=0.3)
+    s.set_state(prim)
+    pr.set_state(prim)
+    dt = min(pr.dt(0.1), s.dt(0.1))
+    s.step(dt, 4)
+    pr.step(dt, 4)
+    assert rel(s.moments(), pr.moments()) < 1e-5
+
+
+def test_free_stream_and_conservation_on_a_curved_mesh():
+    ne, p = (2, 3, 2), 3
+    s, pr, X = make(ne, p, n=6, tau=1e30)
+    g = pr.sample_maxwellian([1.0, 0.2, -0.1, 0.3, 1.1]) * W.noise(pr.nvel, seed=3, amp=0.1)
+    F = np.tile(g, (s.npts, 1))
+    s.set_f(F)
+    s.step(1e-3, 10)
+    assert rel(s.get_f(), F.astype(np.float32).astype(np.float64)) < 2e-6
+    # J-weighted totals of a non-uniform state with collisions
+    s2, pr2, X2 = make(ne, p, n=6, tau=0.02, kind="sine", eps=0.3)
+    _, J = pr2.metric()
+    _, w = orc.gauss_legendre(p + 1)
+    Wn = np.einsum("i,j,k->kji", w, w, w).ravel()
+    WJ = (J.reshape(-1, Wn.size) * Wn).ravel()
+    s2.set_state(W.smooth_prim(X2, 3, seed=6, amp=0.2))
+    T0 = (s2.moments() * WJ[:, None]).sum(0)
+    s2.step(s2.dt(0.1), 50)
+    T1 = (s2.moments() * WJ[:, None]).sum(0)
+    assert np.abs(T1 - T0).max() <= 2e-6 * np.abs(T0).max()
+
+
+def test_rejected_setups():
+    from paper_2308_06196_gb300.bgk import BGK_EINVAL, FP64, BgkError, Solver
+
+    x = Solver(3, [2, 2, 2], (0.0,) * 3, (1.0,) * 3, 2, (6,) * 3, (-4.0,) * 3, (4.0,) * 3, 0.1, precision=FP64)
+    with pytest.raises(BgkError) as err:
+        x.set_geometry(x.points())
+    assert err.value.code == BGK_EINVAL
+    y = Solver(3, [2, 2, 2], (0.0,) * 3, (1.0,) * 3, 2, (6,) * 3, (-4.0,) * 3, (4.0,) * 3, 0.1)
+    X = y.points()
+    X[:27, 0] = X[:27, 0].max() + X[:27, 0].min() - X[:27, 0]  # element 0 mirrored in x: J < 0 there
+    with pytest.raises(BgkError) as err:
+        y.set_geometry(X)
+    assert err.value.code == BGK_EINVAL
