@@ -68,6 +68,10 @@ struct orc_ctx {
     double *Ja;             /* [npts][3][3] metric terms Ja^i_n (i: reference direction, n: component) */
     double *Jd;             /* [npts] Jacobian determinant J */
     double *fn;             /* [nelem][3][2][n1^2][3] common contravariant face normals (direction, side) */
+    /* unstructured connectivity (NULL: the structured element grid); per element and local face 2d+side */
+    int *cn;                /* neighbour element, or -1 - g at a boundary face with the ghost of face g */
+    int *cf;                /* the neighbour's local face 2d'+s' */
+    int *co;                /* orientation of the neighbour's face points (see oracle_set_connectivity) */
 };
 
 /* ------------------------------------------------------------------------------------------ */
@@ -559,6 +563,9 @@ void oracle_destroy(orc_ctx *c)
     free(c->Ja);
     free(c->Jd);
     free(c->fn);
+    free(c->cn);
+    free(c->cf);
+    free(c->co);
     free(c);
 }
 
@@ -791,6 +798,9 @@ static void face_metric(const orc_ctx *c, int64_t e, int d, int side, int ln, do
     }
 }
 
+static void face_normals(orc_ctx *c);
+static int64_t table_neighbour(const orc_ctx *c, int64_t e, int d, int side, const int *ic, int64_t *nodes, int *sp);
+
 int oracle_set_geometry(orc_ctx *c, const double *x)
 {
     if (!c || !x || c->dim != 3)
@@ -813,11 +823,51 @@ int oracle_set_geometry(orc_ctx *c, const double *x)
             if (!(c->Jd[e * c->np + i] > 0.0))
                 bad++;
     }
-    /* single-valued face normals: the mean of both elements' interpolated Ja^d on interior and periodic
-     * faces, the element's own on a boundary face */
+    face_normals(c);
+    return bad ? -2 : 0;
+}
+
+/* Single-valued face normals: the mean of both elements' interpolated Ja^d on interior and periodic
+ * faces (with the neighbour's own axis, face point and sign under unstructured connectivity), the
+ * element's own on a boundary face. */
+static void face_normals(orc_ctx *c)
+{
+    const int nf = c->n1 * c->n1;
     for (int64_t e = 0; e < c->nelem; e++) {
         int ec[3];
         elem_coords(c, e, ec);
+        if (c->cn) {
+            for (int d = 0; d < 3; d++)
+                for (int side = 0; side < 2; side++)
+                    for (int ln = 0; ln < nf; ln++) {
+                        int ic[3] = {0, 0, 0}, t = ln;
+                        for (int q = 0; q < 3; q++) {
+                            if (q == d)
+                                continue;
+                            ic[q] = t % c->n1;
+                            t /= c->n1;
+                        }
+                        double N[3], Nn[3];
+                        face_metric(c, e, d, side, ln, N);
+                        int64_t nodes[MAXN];
+                        int sp;
+                        const int64_t en = table_neighbour(c, e, d, side, ic, nodes, &sp);
+                        if (en >= 0) {
+                            /* the neighbour's Ja^{d'} interpolated to the shared face point; its +r_{d'}
+                             * points the same way as our +r_d when the faces have opposite sides */
+                            const int dn = c->cf[e * 6 + 2 * d + side] / 2;
+                            const double *l = sp ? c->lp : c->lm, sg = (sp != side) ? 1.0 : -1.0;
+                            Nn[0] = Nn[1] = Nn[2] = 0.0;
+                            for (int j = 0; j < c->n1; j++)
+                                for (int n = 0; n < 3; n++)
+                                    Nn[n] += l[j] * c->Ja[(nodes[j] * 3 + dn) * 3 + n];
+                            for (int n = 0; n < 3; n++)
+                                N[n] = 0.5 * (N[n] + sg * Nn[n]);
+                        }
+                        memcpy(c->fn + ((((e * 3 + d) * 2 + side) * nf + ln) * 3), N, sizeof N);
+                    }
+            continue;
+        }
         for (int d = 0; d < 3; d++)
             for (int side = 0; side < 2; side++) {
                 int nc[3] = {ec[0], ec[1], ec[2]};
@@ -838,7 +888,33 @@ int oracle_set_geometry(orc_ctx *c, const double *x)
                 }
             }
     }
-    return bad ? -2 : 0;
+}
+
+int oracle_set_connectivity(orc_ctx *c, const int *nbr, const int *nface, const int *orient)
+{
+    if (!c || !nbr || !nface || !orient || c->dim != 3)
+        return -1;
+    for (int fc = 0; fc < 6; fc++)
+        if (c->bc[fc] == ORC_WALL)
+            return -1;
+    for (int64_t q = 0; q < c->nelem * 6; q++) {
+        if (nbr[q] >= c->nelem || nbr[q] < -6 || nface[q] < 0 || nface[q] > 5 || orient[q] < 0 || orient[q] > 7)
+            return -1;
+        if (nbr[q] < 0 && c->bc[-1 - nbr[q]] != ORC_DIRICHLET)
+            return -1;
+    }
+    const size_t n = sizeof(int) * (size_t)(c->nelem * 6);
+    c->cn = (int *)realloc(c->cn, n);
+    c->cf = (int *)realloc(c->cf, n);
+    c->co = (int *)realloc(c->co, n);
+    if (!c->cn || !c->cf || !c->co)
+        return -1;
+    memcpy(c->cn, nbr, n);
+    memcpy(c->cf, nface, n);
+    memcpy(c->co, orient, n);
+    if (c->Ja)
+        face_normals(c);
+    return 0;
 }
 
 int oracle_metric(const orc_ctx *c, double *Ja, double *J)
@@ -861,9 +937,58 @@ int oracle_metric(const orc_ctx *c, double *Ja, double *J)
  * Periodic / interior faces: the neighbour's trace interpolated to the shared face.
  * Dirichlet: the ghost Maxwellian. Wall: rho_w * unit-density wall Maxwellian, rho_w from zero net
  * discrete mass flux through this face point (computed by the caller and passed as rho_w). */
+/* Face point of face (d, side) given by the node coordinates ic (ic[d] ignored) as (a, b): the coordinates
+ * along the two other axes in increasing order. */
+static void face_ab(int d, const int *ic, int *a, int *b)
+{
+    *a = ic[d == 0 ? 1 : 0];
+    *b = ic[d == 2 ? 1 : 2];
+}
+
+/* Unstructured connectivity: the neighbour across local face (d, side) of element e and, for the face
+ * point ic, the neighbour's nodes along its own normal axis d' (nodes[0..n1-1], from its low end) and
+ * the side s' of its shared face. Returns the neighbour element, or -1 - g at a boundary face. */
+static int64_t table_neighbour(const orc_ctx *c, int64_t e, int d, int side, const int *ic, int64_t *nodes, int *sp)
+{
+    const int fc = 2 * d + side;
+    const int en = c->cn[e * 6 + fc];
+    if (en < 0)
+        return en;
+    const int fcn = c->cf[e * 6 + fc], o = c->co[e * 6 + fc];
+    const int dn = fcn / 2;
+    int a, b;
+    face_ab(d, ic, &a, &b);
+    int an = (o & 1) ? b : a, bn = (o & 1) ? a : b;
+    if (o & 2)
+        an = c->n1 - 1 - an;
+    if (o & 4)
+        bn = c->n1 - 1 - bn;
+    int jc[3];
+    jc[dn == 0 ? 1 : 0] = an;
+    jc[dn == 2 ? 1 : 2] = bn;
+    for (int j = 0; j < c->n1; j++) {
+        jc[dn] = j;
+        nodes[j] = (int64_t)en * c->np + node_index(c, jc);
+    }
+    *sp = fcn & 1;
+    return en;
+}
+
 static double exterior_value(const orc_ctx *c, const double *f, const int *ec, int d, int side,
                              const int *ic, int64_t k, double rho_w)
 {
+    if (c->cn) { /* unstructured: the neighbour's trace at its shared face, or the boundary ghost */
+        int64_t nodes[MAXN];
+        int sp;
+        const int64_t en = table_neighbour(c, elem_index(c, ec), d, side, ic, nodes, &sp);
+        if (en < 0)
+            return c->ghost[(-1 - en) * c->nvel + k];
+        const double *l = sp ? c->lp : c->lm;
+        double t = 0.0;
+        for (int j = 0; j < c->n1; j++)
+            t += l[j] * f[nodes[j] * c->nvel + k];
+        return t;
+    }
     int nc[3] = {ec[0], ec[1], ec[2]};
     nc[d] += side ? 1 : -1;
     int fc = 2 * d + side;
@@ -979,6 +1104,8 @@ int oracle_residual(const orc_ctx *c, const double *f, double *R)
         return -1;
     if (c->Ja)
         return residual_curved(c, f, R);
+    if (c->cn) /* unstructured connectivity needs the node coordinates */
+        return -1;
     const int n1 = c->n1;
     memset(R, 0, sizeof(double) * (size_t)(c->npts * c->nvel));
 #pragma omp parallel for schedule(dynamic, 1)

@@ -127,6 +127,18 @@ void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega);
  * Returns 0, -2 if some node has J <= 0, -1 on bad input. */
 int oracle_set_geometry(orc_ctx *c, const double *x);
 
+/* Unstructured connectivity (dim = 3, Dirichlet or periodic data only): per element e and local face
+ * f = 2d + side (d the reference axis, side 0 = the r_d = -1 face), [nelem][6] arrays:
+ *   nbr[e][f]    the neighbour element, or -1 - g at a boundary face that takes the Dirichlet ghost of
+ *                the structured face g (whose bc must be ORC_DIRICHLET);
+ *   nface[e][f]  the neighbour's local face 2d' + s' that is shared;
+ *   orient[e][f] how face points match: with (a, b) the node coordinates of a face point along the two
+ *                other axes in increasing order, the neighbour's (a', b') is (b, a) if bit 0 is set,
+ *                else (a, b), then a' -> p - a' if bit 1, b' -> p - b' if bit 2.
+ * Replaces the structured element grid for the advection (which then needs oracle_set_geometry: the
+ * node coordinates carry every element's position and orientation). Returns 0 or -1. */
+int oracle_set_connectivity(orc_ctx *c, const int *nbr, const int *nface, const int *orient);
+
 /* Metric terms Ja[n_x][3][3] (reference direction i, component n) and J[n_x] of the geometry set by
  * oracle_set_geometry (either pointer may be NULL); -1 without a geometry. */
 int oracle_metric(const orc_ctx *c, double *Ja, double *J);

@@ -75,6 +75,7 @@ def lib():
             L.oracle_set_viscosity.argtypes = [C.c_void_p, C.c_double, C.c_double]
             L.oracle_set_geometry.argtypes = [C.c_void_p, dp]
             L.oracle_metric.argtypes = [C.c_void_p, dp, dp]
+            L.oracle_set_connectivity.argtypes = [C.c_void_p, ip, ip, ip]
             _lib = L
     return _lib
 
@@ -235,6 +236,13 @@ class Problem:
         rc = lib().oracle_set_geometry(self.h, _d(x))
         if rc != 0:
             raise ValueError(f"oracle_set_geometry: {rc}")
+
+    def set_connectivity(self, nbr, nface, orient):
+        """Unstructured connectivity: [nelem, 6] neighbour / shared face / orientation tables."""
+        a = [np.ascontiguousarray(t, dtype=np.int32).reshape(-1) for t in (nbr, nface, orient)]
+        rc = lib().oracle_set_connectivity(self.h, _i(a[0]), _i(a[1]), _i(a[2]))
+        if rc != 0:
+            raise ValueError(f"oracle_set_connectivity: {rc}")
 
     def metric(self):
         """(Ja [n_x, 3, 3] with Ja[:, i, n] = J d r_i / d x_n, J [n_x]) of the curvilinear geometry."""

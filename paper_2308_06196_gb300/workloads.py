@@ -221,6 +221,116 @@ def curved_nodes(x: np.ndarray, lo, hi, nelem, eps: float = 0.1, kind: str = "bu
     return X
 
 
+def _proper_rotations():
+    """The 24 rotations of the cube as (P, F): local axis k runs along structured axis P[k], reversed
+    when F[k]; determinant sign(P) (-1)^(number of flips) = +1."""
+    import itertools
+
+    out = []
+    for P in itertools.permutations(range(3)):
+        sgn = 1
+        for i in range(3):
+            for j in range(i + 1, 3):
+                if P[i] > P[j]:
+                    sgn = -sgn
+        for F in itertools.product((0, 1), repeat=3):
+            if sgn * (-1) ** sum(F) == 1:
+                out.append((P, F))
+    return out
+
+
+def unstructured_box(ne, p: int, bc=None, seed: int = 0) -> dict:
+    """A structured ne[0] x ne[1] x ne[2] hexahedral grid relabelled as an unstructured mesh: elements in
+    a seeded random order, each with a seeded random rotation of its local axes. Returns
+      node_map [E*NP]: (structured point index) of every new point (new element-major, local x fastest),
+      nbr, nface, orient [E, 6]: the connectivity tables of oracle_set_connectivity / bgk_set_connectivity
+    (bc[d][side] of the structured grid: 0 periodic, else a boundary face with the structured face's
+    ghost). Pure index bookkeeping: coordinates and states are carried over by node_map."""
+    rng = np.random.default_rng(seed)
+    ne = tuple(int(v) for v in ne)
+    E, n1 = ne[0] * ne[1] * ne[2], p + 1
+    NP = n1 ** 3
+    perm = rng.permutation(E)              # structured element -> new element
+    inv = np.argsort(perm)                 # new element -> structured element
+    rots = _proper_rotations()
+    rot = [rots[int(rng.integers(0, 24))] for _ in range(E)]  # per new element
+    bc = bc if bc is not None else ((0, 0), (0, 0), (0, 0))
+
+    def struct_ec(e):
+        return [e % ne[0], (e // ne[0]) % ne[1], e // (ne[0] * ne[1])]
+
+    def to_struct(loc, r):
+        P, F = r
+        T = [0, 0, 0]
+        for k in range(3):
+            T[P[k]] = (n1 - 1 - loc[k]) if F[k] else loc[k]
+        return T
+
+    def to_local(T, r):
+        P, F = r
+        return [(n1 - 1 - T[P[k]]) if F[k] else T[P[k]] for k in range(3)]
+
+    node_map = np.zeros(E * NP, dtype=np.int64)
+    for en in range(E):
+        es = int(inv[en])
+        for i in range(NP):
+            loc = [i % n1, (i // n1) % n1, i // (n1 * n1)]
+            T = to_struct(loc, rot[en])
+            node_map[en * NP + i] = es * NP + T[0] + n1 * (T[1] + n1 * T[2])
+    nbr = np.zeros((E, 6), dtype=np.int32)
+    nface = np.zeros((E, 6), dtype=np.int32)
+    orient = np.zeros((E, 6), dtype=np.int32)
+    for en in range(E):
+        es = int(inv[en])
+        P, F = rot[en]
+        for d in range(3):
+            o1, o2 = [q for q in range(3) if q != d]
+            for side in range(2):
+                D, S = P[d], side ^ F[d]
+                ec = struct_ec(es)
+                ec[D] += 1 if S else -1
+                if ec[D] < 0 or ec[D] >= ne[D]:
+                    if bc[D][S] != 0:
+                        nbr[en, 2 * d + side] = -1 - (2 * D + S)
+                        continue
+                    ec[D] %= ne[D]
+                ns = ec[0] + ne[0] * (ec[1] + ne[1] * ec[2])
+                nn = int(perm[ns])
+                Pn, Fn = rot[nn]
+                dn = list(Pn).index(D)
+                sn = (1 - S) ^ Fn[dn]
+                q1, q2 = [q for q in range(3) if q != dn]
+                pairs = []
+                for a in range(n1):
+                    for b in range(n1):
+                        loc = [0, 0, 0]
+                        loc[d], loc[o1], loc[o2] = side * (n1 - 1), a, b
+                        T = to_struct(loc, rot[en])
+                        T[D] = n1 - 1 - T[D]
+                        ln = to_local(T, rot[nn])
+                        pairs.append(((a, b), (ln[q1], ln[q2])))
+                code = None
+                for c in range(8):
+                    ok = True
+                    for (a, b), (a2, b2) in pairs:
+                        x, y = (b, a) if c & 1 else (a, b)
+                        if c & 2:
+                            x = n1 - 1 - x
+                        if c & 4:
+                            y = n1 - 1 - y
+                        if (x, y) != (a2, b2):
+                            ok = False
+                            break
+                    if ok:
+                        code = c
+                        break
+                assert code is not None
+                nbr[en, 2 * d + side] = nn
+                nface[en, 2 * d + side] = 2 * dn + sn
+                orient[en, 2 * d + side] = code
+    return dict(node_map=node_map, nbr=nbr, nface=nface, orient=orient, perm=perm)
+
+
 def noise(shape, seed: int = 0, amp: float = 0.05) -> np.ndarray:
     """Seeded multiplicative perturbation factors 1 + amp * U(-1, 1)."""
     rng = np.random.default_rng(seed)

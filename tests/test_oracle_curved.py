@@ -171,3 +171,54 @@ def test_limiter_keeps_the_physical_element_mean():
     neg = f.reshape(-1, Wn.size, pr.nvel).min(1) < 0
     ok = neg & (mean(f) >= 0)
     assert np.abs(g.reshape(-1, Wn.size, pr.nvel).min(1)[ok]).max() <= 1e-14
+
+
+# ------------------------------------------------------------------------------------------------
+# unstructured connectivity: the structured grid relabelled (random element order, every element's
+# local axes rotated at random) is the same discretisation, so it must reproduce the structured
+# result point for point; a wrong orientation bit, trace end or normal sign anywhere breaks this
+
+
+@pytest.mark.parametrize("kind,bc", [("bump", None), ("sine", "tube")])
+def test_unstructured_relabelling_reproduces_the_structured_mesh(kind, bc):
+    ne, p = (3, 2, 2), 2
+    bcs = None
+    if bc == "tube":
+        bc = np.array([[W.DIRICHLET, W.DIRICHLET], [0, 0], [0, 0]])
+        bcs = np.zeros((3, 2, 5))
+        bcs[0, 0] = [1.0, 0.3, 0.0, 0.0, 1.0]
+        bcs[0, 1] = [0.5, 0.3, 0.0, 0.0, 0.9]
+    u = W.unstructured_box(ne, p, bc=None if bc is None else bc.tolist(), seed=5)
+    kw = dict(bc=None if bc is None else bc.reshape(6), bc_state=None if bcs is None else bcs.reshape(30))
+    a, b = box(ne, p, n=6, L=4.0, tau=0.05, **kw), box(ne, p, n=6, L=4.0, tau=0.05, **kw)
+    X = W.curved_nodes(a.points(), (0, 0, 0), L3, ne, 0.3 if kind == "sine" else 0.15, kind=kind)
+    m = u["node_map"]
+    a.set_geometry(X)
+    b.set_connectivity(u["nbr"], u["nface"], u["orient"])
+    b.set_geometry(X[m])
+    assert b.dt(0.1) == pytest.approx(a.dt(0.1), rel=1e-13)
+    prim = W.smooth_prim(X, 3, seed=2)
+    a.set_state(prim)
+    f = a.get_f() * W.noise((a.npts, a.nvel), seed=3, amp=0.1)
+    Ra, Rb = a.residual(f), b.residual(f[m])
+    assert np.abs(Ra[m] - Rb).max() <= 1e-13 * np.abs(Ra).max()
+    a.set_f(f)
+    b.set_f(f[m])
+    a.set_limiter(True)
+    b.set_limiter(True)
+    a.step(0.01, 3)
+    b.step(0.01, 3)
+    assert np.abs(a.get_f()[m] - b.get_f()).max() <= 1e-13 * np.abs(a.get_f()).max()
+
+
+def test_unstructured_tables_are_validated():
+    pr = box((2, 2, 2), 2)
+    u = W.unstructured_box((2, 2, 2), 2, seed=1)
+    bad = u["orient"].copy()
+    bad[0, 0] = 9
+    with pytest.raises(ValueError):
+        pr.set_connectivity(u["nbr"], u["nface"], bad)
+    nb = u["nbr"].copy()
+    nb[0, 0] = -1  # a boundary face on a periodic grid: no Dirichlet ghost for it
+    with pytest.raises(ValueError):
+        pr.set_connectivity(nb, u["nface"], u["orient"])
