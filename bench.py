@@ -338,13 +338,15 @@ def bench_planar(steps: int, warmup: int, stream, torch) -> dict:
     return out
 
 
-def bench_curved(steps: int, warmup: int, stream, torch) -> dict:
+def bench_curved(steps: int, warmup: int, stream, torch, elements: int = 0) -> dict:
     """The Taylor-Green workload on curvilinear hexahedra: the box's solution nodes displaced by the
     smooth periodic sine mapping (amplitude 0.3 element widths), metric terms from bgk_set_geometry,
     the curvilinear stage kernel (per-lane upwinding, reference-space flux)."""
     from paper_2308_06196_gb300.bgk import Solver
 
     c = W.config(WORKLOAD)
+    if elements:  # fewer, larger elements on the same box (profiling)
+        c = W.config(WORKLOAD, nelem=(elements,) * 3)
     k = W.mesh_kwargs(c)
     s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
     s.set_stream(stream.cuda_stream)
@@ -585,7 +587,7 @@ def main():
     ablation = None if (args.no_ablation or world > 1) else bench_ablation()
     curved = None
     if args.curved_steps > 0 and world == 1:
-        curved = bench_curved(args.curved_steps, warmup, stream, torch)
+        curved = bench_curved(args.curved_steps, warmup, stream, torch, args.elements)
     planar = None
     if args.planar_steps > 0 and world == 1:
         planar = bench_planar(args.planar_steps, warmup, stream, torch)

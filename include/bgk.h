@@ -175,6 +175,20 @@ int bgk_autotune(bgk_ctx *ctx, int *g_out);
  * is kept. Returns BGK_EINVAL for another dim/precision, diffuse walls, or a node with J <= 0. */
 int bgk_set_geometry(bgk_ctx *ctx, const double *x);
 
+/* Unstructured hexahedral connectivity (with bgk_set_geometry, whose node coordinates then carry every
+ * element's position and local-axis orientation; dim = 3, FP32-split form, no diffuse walls). Host
+ * arrays [n_elements][6], indexed by element and local face f = 2d + side (reference axis d, side 0 the
+ * r_d = -1 face):
+ *   nbr[e][f]    the neighbour element, or -1 - g at a boundary face, which takes the Dirichlet ghost of
+ *                face g of bgk_create's boundary data (bc[g / 2][g % 2] must be BGK_BC_DIRICHLET);
+ *   nface[e][f]  the neighbour's local face 2d' + s' that is shared;
+ *   orient[e][f] the face-point match: for the face point with node coordinates (a, b) along our two
+ *                other axes (in increasing axis order) the neighbour's (a', b') is (b, a) if bit 0 is
+ *                set, else (a, b); then a' -> p - a' if bit 1, b' -> p - b' if bit 2.
+ * The element count stays that of bgk_create (its grid shape no longer matters for the advection).
+ * Recomputes the face normals when a geometry is already set. Returns BGK_EINVAL on a bad table. */
+int bgk_set_connectivity(bgk_ctx *ctx, const int *nbr, const int *nface, const int *orient);
+
 /* Launch timing: when on, bgk_step launches its kernels directly (not through the CUDA graph) and
  * brackets every stage and Newton launch with CUDA events on the context stream. bgk_timing()
  * synchronises and returns the summed milliseconds and launch counts since timing was switched on,

@@ -24,7 +24,7 @@ SYMBOLS = (
     "bgk_create", "bgk_destroy", "bgk_last_error", "bgk_set_stream", "bgk_info", "bgk_points",
     "bgk_set_state", "bgk_set_state_device", "bgk_set_f", "bgk_get_f", "bgk_step", "bgk_moments",
     "bgk_moments_device", "bgk_equilibrium", "bgk_synchronize", "bgk_dt", "bgk_set_timing", "bgk_timing",
-    "bgk_equilibrium_noalloc", "bgk_autotune", "bgk_set_geometry",
+    "bgk_equilibrium_noalloc", "bgk_autotune", "bgk_set_geometry", "bgk_set_connectivity",
     "bgk_batch_create", "bgk_batch_destroy", "bgk_batch_last_error", "bgk_batch_set_stream", "bgk_batch_step",
     "bgk_batch_synchronize", "bgk_batch_autotune", "bgk_batch_info", "bgk_batch_set_timing", "bgk_batch_timing",
 )
@@ -90,6 +90,7 @@ def lib():
             L.bgk_equilibrium_noalloc.argtypes = [vp, C.c_int64, C.POINTER(bgk_vgrid), vp, vp, vp]
             L.bgk_autotune.argtypes = [vp, C.POINTER(C.c_int)]
             L.bgk_set_geometry.argtypes = [vp, C.POINTER(C.c_double)]
+            L.bgk_set_connectivity.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.bgk_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
             L.bgk_batch_destroy.argtypes = [vp]
             L.bgk_batch_destroy.restype = None
@@ -217,6 +218,14 @@ class Solver:
         """Curvilinear hexahedra: physical coordinates x [n_x, 3] (FP64, host) of every solution node."""
         a = np.ascontiguousarray(x, dtype=np.float64).reshape(self.npts, 3)
         self._check(lib().bgk_set_geometry(self.h, _dptr(a)))
+
+    def set_connectivity(self, nbr, nface, orient):
+        """Unstructured hexahedral connectivity: [n_elements, 6] neighbour, shared-face and orientation
+        tables (host int arrays)."""
+        a = [np.ascontiguousarray(t, dtype=np.int32).reshape(-1) for t in (nbr, nface, orient)]
+        ip = C.POINTER(C.c_int)
+        self._check(lib().bgk_set_connectivity(self.h, a[0].ctypes.data_as(ip), a[1].ctypes.data_as(ip),
+                                               a[2].ctypes.data_as(ip)))
 
     def set_state(self, prim):
         """prim: numpy (host) or torch tensor [n_x, 5] (rho, u, v, w, T), FP64, host or CUDA."""

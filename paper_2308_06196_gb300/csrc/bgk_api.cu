@@ -203,6 +203,10 @@ struct bgk_ctx {
     // curvilinear hexahedra (bgk_set_geometry)
     float4 *met = nullptr, *fnm = nullptr;
     float *iwj = nullptr;
+    // unstructured connectivity (bgk_set_connectivity): host tables [E][6] and their device form
+    std::vector<int> cnbr, cface, corient;
+    int4 *ftab = nullptr;
+    unsigned char *fbase = nullptr;
     std::vector<double> geom;  // node coordinates [n_x][3]
     double curv_smax = 0.0;    // max over nodes and velocities of sum_d |Ja^d . xi| / (2 J)
     int *err = nullptr;
@@ -290,6 +294,8 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.met = c->met;
     A.fnm = c->fnm;
     A.iwj = c->iwj;
+    A.ftab = c->ftab;
+    A.fbase = c->fbase;
     return A;
 }
 
@@ -601,7 +607,7 @@ void bgk_destroy(bgk_ctx *c)
     void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
-                    c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj};
+                    c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -1170,6 +1176,59 @@ void dref(const bgk_ctx *c, const double *u, int j, double *out)
 
 }  // namespace
 
+int bgk_set_connectivity(bgk_ctx *c, const int *nbr, const int *nface, const int *orient)
+{
+    if (!c || !nbr || !nface || !orient)
+        return BGK_EINVAL;
+    if (c->dim != 3 || c->prec != BGK_FP32_SPLIT || c->has_wall)
+        return fail(c, BGK_EINVAL, "unstructured connectivity is built for hexahedra (dim = 3) in the FP32-split "
+                                   "form without diffuse walls");
+    const int E = c->E, N1 = c->N1, NQ = N1 * N1;
+    for (int64_t q = 0; q < (int64_t)E * 6; q++) {
+        if (nbr[q] >= E || nbr[q] < -6 || nface[q] < 0 || nface[q] > 5 || orient[q] < 0 || orient[q] > 7)
+            return fail(c, BGK_EINVAL, "connectivity table entry out of range at " + std::to_string(q));
+        if (nbr[q] < 0 && c->bc[-1 - nbr[q]] != BGK_BC_DIRICHLET)
+            return fail(c, BGK_EINVAL, "a boundary face must take the ghost of a Dirichlet face");
+    }
+    std::vector<int4> tab((size_t)E * 6);
+    std::vector<unsigned char> base((size_t)E * 6 * NQ);
+    for (int e = 0; e < E; e++)
+        for (int f = 0; f < 6; f++) {
+            const int q = e * 6 + f, dn = nface[q] / 2, o = orient[q];
+            const int stride = dn == 0 ? 1 : (dn == 1 ? N1 : NQ);
+            tab[q] = make_int4(nbr[q], stride, nface[q] % 2, 0);
+            // face point (a, b) of our face -> the neighbour's (a', b') along its other axes (increasing)
+            const int s1 = dn == 0 ? N1 : 1, s2 = dn == 2 ? N1 : NQ;
+            for (int ln = 0; ln < NQ; ln++) {
+                const int a = ln % N1, b = ln / N1;
+                int an = (o & 1) ? b : a, bn = (o & 1) ? a : b;
+                if (o & 2)
+                    an = N1 - 1 - an;
+                if (o & 4)
+                    bn = N1 - 1 - bn;
+                base[(size_t)q * NQ + ln] = (unsigned char)(an * s1 + bn * s2);
+            }
+        }
+    if (!c->ftab) {
+        CK(dalloc(c, &c->ftab, tab.size()));
+        CK(dalloc(c, &c->fbase, base.size()));
+    }
+    CK(cudaMemcpy(c->ftab, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->fbase, base.data(), base.size(), cudaMemcpyHostToDevice));
+    c->cnbr.assign(nbr, nbr + (size_t)E * 6);
+    c->cface.assign(nface, nface + (size_t)E * 6);
+    c->corient.assign(orient, orient + (size_t)E * 6);
+    if (!c->geom.empty()) {  // face normals follow the new neighbours
+        const std::vector<double> x = c->geom;
+        return bgk_set_geometry(c, x.data());
+    }
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return BGK_OK;
+}
+
 int bgk_set_geometry(bgk_ctx *c, const double *x)
 {
     if (!c || !x)
@@ -1252,16 +1311,33 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
                 int nc[3] = {ec[0], ec[1], ec[2]};
                 nc[d] += side ? 1 : -1;
                 const bool outside = nc[d] < 0 || nc[d] >= c->ne[d];
-                const bool shared = !outside || c->bc[2 * d + side] == BGK_BC_PERIODIC;
+                bool shared = !outside || c->bc[2 * d + side] == BGK_BC_PERIODIC;
                 nc[d] = (nc[d] + c->ne[d]) % c->ne[d];
-                const int en = nc[0] + c->ne[0] * (nc[1] + c->ne[1] * nc[2]);
+                int en = nc[0] + c->ne[0] * (nc[1] + c->ne[1] * nc[2]);
+                int dn = d, sn = 1 - side, orient = 0;
+                if (!c->cnbr.empty()) {  // unstructured: the table's neighbour, shared face and orientation
+                    en = c->cnbr[(size_t)e * 6 + 2 * d + side];
+                    shared = en >= 0;
+                    dn = c->cface[(size_t)e * 6 + 2 * d + side] / 2;
+                    sn = c->cface[(size_t)e * 6 + 2 * d + side] % 2;
+                    orient = c->corient[(size_t)e * 6 + 2 * d + side];
+                }
                 for (int ln = 0; ln < NQ; ln++) {
                     double Nv[3], Nn[3];
                     own_face(e, d, side, ln, Nv);
                     if (shared) {
-                        own_face(en, d, 1 - side, ln, Nn);
+                        // the neighbour's face point of ours, its Ja^{d'} there, and the sign that turns its
+                        // +r_{d'} into our +r_d (equal directions when the shared faces have opposite sides)
+                        int a = ln % N1, bq = ln / N1;
+                        int an = (orient & 1) ? bq : a, bn = (orient & 1) ? a : bq;
+                        if (orient & 2)
+                            an = N1 - 1 - an;
+                        if (orient & 4)
+                            bn = N1 - 1 - bn;
+                        own_face(en, dn, sn, an + N1 * bn, Nn);
+                        const double sg = sn != side ? 1.0 : -1.0;
                         for (int n = 0; n < 3; n++)
-                            Nv[n] = 0.5 * (Nv[n] + Nn[n]);
+                            Nv[n] = 0.5 * (Nv[n] + sg * Nn[n]);
                     }
                     fn[(((size_t)e * 3 + d) * 2 + side) * NQ + ln] = make_float4((float)Nv[0], (float)Nv[1], (float)Nv[2], 0.f);
                 }

@@ -87,6 +87,10 @@ struct StageArgs {
     const float4 *fnm;   // [E][3][2][N1^2] shared contravariant face normal N (direction, low/high side,
                          // face point); N . xi > 0 is flow towards +r_d
     const float *iwj;    // [E] 1 / sum_i W_i J_i (the limiter's element mean over the physical element)
+    // unstructured connectivity (null: the structured element grid), per element and local face 2d+side:
+    const int4 *ftab;    // [E][6] (neighbour element or -1 - g for the ghost of face g, node stride of the
+                         // neighbour's normal axis, side of its shared face (1: its +1 end), 0)
+    const unsigned char *fbase;  // [E][6][N1^2] the neighbour's first node on the line through each face point
 };
 
 struct NewtonArgs {

@@ -44,6 +44,8 @@ template <int N1>
 struct CurvSmem {
     float4 met[N1 * N1 * N1][3];
     float4 fnm[3][2][N1 * N1];
+    int4 ftab[6];                          // unstructured connectivity of the element (see StageArgs)
+    unsigned char fbase[6][N1 * N1];
     float iwj;
 };
 
@@ -136,6 +138,12 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 (&cs.fnm[0][0][0])[q] = __ldg(A.fnm + (int64_t)e * 6 * NQ + q);
             if (tid == 0)
                 cs.iwj = __ldg(A.iwj + e);
+            if (A.ftab) {
+                if (tid < 6)
+                    cs.ftab[tid] = __ldg(A.ftab + (int64_t)e * 6 + tid);
+                for (int q = tid; q < 6 * NQ; q += NT)
+                    (&cs.fbase[0][0])[q] = __ldg(A.fbase + (int64_t)e * 6 * NQ + q);
+            }
         }
         // the general form reads 1/tau of its layer (variable collision time) before the first
         // tile's B1, from rows other warps loaded
@@ -154,6 +162,32 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
         sm.msum[w][m][lane] = 0.f;
     const float kb = A.kb;
     const float bdt = A.b * A.dt;
+    // curvilinear: the exterior trace at face (d, side) for the face point fp of the line whose own nodes
+    // are nd (tile vl, this lane): the neighbour's interpolant at the shared face, or the face's ghost
+    auto exterior = [&](int vl, int slot, int d, int side, int fp, const int (&nd)[N1]) -> float {
+        int en, g, stride = 0, base = 0;
+        bool hi_end;  // the neighbour's shared face is its +1 end
+        if (A.ftab) {
+            const int4 t = cs.ftab[2 * d + side];
+            en = t.x;
+            g = -1 - t.x;
+            stride = t.y;
+            hi_end = t.z != 0;
+            base = cs.fbase[2 * d + side][fp];
+        } else {
+            en = upwind_neighbour(A.mesh, ec, d, side == 0);
+            g = 2 * d + side;
+            hi_end = side == 0;
+        }
+        if (en < 0)
+            return __ldg(A.ghost + (int64_t)g * A.nslots + slot);
+        float v[N1];
+        const float *nb = A.src + fidx(vl, en, 0, lane, E, NP);
+#pragma unroll
+        for (int j = 0; j < N1; j++)
+            v[j] = __ldg(nb + (A.ftab ? base + j * stride : nd[j]) * kWarp);
+        return hi_end ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
+    };
 
     // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
     // 128 bytes, contiguous in global and shared memory
@@ -231,7 +265,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 }
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    const int eL = upwind_neighbour(A.mesh, ec, d, true), eR = upwind_neighbour(A.mesh, ec, d, false);
 #pragma unroll
                     for (int ln = 0; ln < N1; ln++) {
                         float fl[N1], u[N1], sv[N1];
@@ -246,31 +279,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         const float4 nL = cs.fnm[d][0][ln + N1 * w], nR = cs.fnm[d][1][ln + N1 * w];
                         const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
                         const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
-                        float tL = 0.f, tR = 0.f;
-                        if (uL > 0.f) {  // inflow through the low face: the low neighbour's +1 trace or the ghost
-                            if (eL >= 0) {
-                                float v[N1];
-                                const float *nb = A.src + fidx(vl, eL, 0, lane, E, NP);
-#pragma unroll
-                                for (int j = 0; j < N1; j++)
-                                    v[j] = __ldg(nb + nd[j] * kWarp);
-                                tL = trace_line<N1, true>(v, A.ops);
-                            } else {
-                                tL = __ldg(A.ghost + (2 * d) * A.nslots + slot);
-                            }
-                        }
-                        if (uR < 0.f) {  // inflow through the high face
-                            if (eR >= 0) {
-                                float v[N1];
-                                const float *nb = A.src + fidx(vl, eR, 0, lane, E, NP);
-#pragma unroll
-                                for (int j = 0; j < N1; j++)
-                                    v[j] = __ldg(nb + nd[j] * kWarp);
-                                tR = trace_line<N1, false>(v, A.ops);
-                            } else {
-                                tR = __ldg(A.ghost + (2 * d + 1) * A.nslots + slot);
-                            }
-                        }
+                        // inflow through the low / high face: the exterior trace (predicated per lane)
+                        const float tL = uL > 0.f ? exterior(vl, slot, d, 0, ln + N1 * w, nd) : 0.f;
+                        const float tR = uR < 0.f ? exterior(vl, slot, d, 1, ln + N1 * w, nd) : 0.f;
                         curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
                         for (int j = 0; j < N1; j++)
@@ -284,7 +295,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
                 }
                 // z-lines of slice iy = w (all layers) from the shared tile; unscaled sums to zc
-                const int eL = upwind_neighbour(A.mesh, ec, 2, true), eR = upwind_neighbour(A.mesh, ec, 2, false);
 #pragma unroll
                 for (int ln = 0; ln < N1; ln++) {
                     float fl[N1], u[N1], sv[N1];
@@ -299,31 +309,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     const float4 nL = cs.fnm[2][0][ln + N1 * w], nR = cs.fnm[2][1][ln + N1 * w];
                     const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
                     const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
-                    float tL = 0.f, tR = 0.f;
-                    if (uL > 0.f) {
-                        if (eL >= 0) {
-                            float v[N1];
-                            const float *nb = A.src + fidx(vl, eL, 0, lane, E, NP);
-#pragma unroll
-                            for (int j = 0; j < N1; j++)
-                                v[j] = __ldg(nb + nd[j] * kWarp);
-                            tL = trace_line<N1, true>(v, A.ops);
-                        } else {
-                            tL = __ldg(A.ghost + 4 * A.nslots + slot);
-                        }
-                    }
-                    if (uR < 0.f) {
-                        if (eR >= 0) {
-                            float v[N1];
-                            const float *nb = A.src + fidx(vl, eR, 0, lane, E, NP);
-#pragma unroll
-                            for (int j = 0; j < N1; j++)
-                                v[j] = __ldg(nb + nd[j] * kWarp);
-                            tR = trace_line<N1, false>(v, A.ops);
-                        } else {
-                            tR = __ldg(A.ghost + 5 * A.nslots + slot);
-                        }
-                    }
+                    const float tL = uL > 0.f ? exterior(vl, slot, 2, 0, ln + N1 * w, nd) : 0.f;
+                    const float tR = uR < 0.f ? exterior(vl, slot, 2, 1, ln + N1 * w, nd) : 0.f;
                     curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
                     for (int j = 0; j < N1; j++)
