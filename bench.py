@@ -338,6 +338,26 @@ def bench_planar(steps: int, warmup: int, stream, torch) -> dict:
     return out
 
 
+def bench_quad(steps: int, warmup: int, stream, torch) -> dict:
+    """The planar Taylor-Green vortex on quadrilaterals (dim = 2) in the two-dimensional velocity space,
+    FP32-split form: ms per step and the quadrilateral stage kernel's achieved bandwidth."""
+    from paper_2308_06196_gb300.bgk import Solver
+
+    c = W.config("planar_tg")
+    k = W.mesh_kwargs(c)
+    s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
+    s.set_stream(stream.cuda_stream)
+    s.set_state(W.prim_planar_tg(s.points(), c["mach"]))
+    g = s.autotune()
+    dt = s.dt(c["cfl"])
+    ms, st = timed_steps(s, dt, steps, warmup, stream, torch)
+    out = {"workload": "planar_tg", "mesh": "128^2 quadrilaterals p=3 on [0,2pi]^2", "nv": list(c["nv"]),
+           "dof": s.ndof, "value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "dt": dt,
+           "tiles_per_task": g, **st}
+    s.close()
+    return out
+
+
 def bench_curved(steps: int, warmup: int, stream, torch, elements: int = 0) -> dict:
     """The Taylor-Green workload on curvilinear hexahedra: the box's solution nodes displaced by the
     smooth periodic sine mapping (amplitude 0.3 element widths), metric terms from bgk_set_geometry,
@@ -607,6 +627,7 @@ def main():
     planar = None
     if args.planar_steps > 0 and world == 1:
         planar = bench_planar(args.planar_steps, warmup, stream, torch)
+        planar["quadrilaterals"] = bench_quad(args.planar_steps, warmup, stream, torch)
 
     ms, graph_ms, e2e_ms = max_over_ranks([ms, graph_ms, e2e_ms], dist, "cuda")
     value = job_value(dof, world, ms)

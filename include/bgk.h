@@ -55,7 +55,7 @@ extern "C" {
 
 typedef struct bgk_ctx bgk_ctx;
 
-/* Structured affine mesh of line (dim = 1) or hexahedral (dim = 3) elements on [lo, hi].
+/* Structured affine mesh of line (dim = 1), quadrilateral (dim = 2) or hexahedral (dim = 3) elements on [lo, hi].
  * Only the first dim entries of nelem/lo/hi/bc/bc_state are read. The velocity space is always 3-D. */
 typedef struct {
     int dim;
@@ -104,7 +104,7 @@ typedef struct {
 #define BGK_MAXWELLIAN_CONTINUOUS 1
 
 /* Create a problem on the current CUDA device: plans the velocity tiles, builds the FR operators
- * (Eqs. 7-8) in FP64 on the host and allocates every device buffer. p in [1, 3] for dim = 3 and
+ * (Eqs. 7-8) in FP64 on the host and allocates every device buffer. p in [1, 3] for dim = 2, 3 and
  * [1, 5] for dim = 1; opts may be NULL. tau > 0 is the constant relaxation time (Eq. 3 with a fixed
  * tau). The state is zero until bgk_set_state/bgk_set_f. Returns BGK_ENOMEM, without allocating,
  * when the buffers would not fit in free device memory. */

@@ -641,10 +641,10 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     c->prec = c->opts.precision;
     c->esize = c->prec == BGK_FP64 ? 8 : 4;
     c->dim = mesh->dim;
-    if (c->dim != 1 && c->dim != 3)
-        return bail(BGK_EINVAL, "dim must be 1 or 3");
-    if (p < 1 || (c->dim == 3 && p > 3) || (c->dim == 1 && p > 5))
-        return bail(BGK_EINVAL, "p must be in [1, 3] (dim 3) or [1, 5] (dim 1)");
+    if (c->dim < 1 || c->dim > 3)
+        return bail(BGK_EINVAL, "dim must be 1, 2 or 3");
+    if (p < 1 || (c->dim >= 2 && p > 3) || (c->dim == 1 && p > 5))
+        return bail(BGK_EINVAL, "p must be in [1, 3] (dim 2, 3) or [1, 5] (dim 1)");
     if (!(tau > 0.0) || !std::isfinite(tau))
         return bail(BGK_EINVAL, "tau must be positive and finite");
     for (int d = 0; d < 3; d++) {
@@ -657,7 +657,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         return bail(BGK_EINVAL, "the body-force source is built for hexahedral meshes (dim = 3)");
     c->p = p;
     c->N1 = p + 1;
-    c->NP = c->dim == 1 ? c->N1 : c->N1 * c->N1 * c->N1;
+    c->NP = c->dim == 1 ? c->N1 : (c->dim == 2 ? c->N1 * c->N1 : c->N1 * c->N1 * c->N1);
     int64_t E = 1;
     for (int d = 0; d < 3; d++) {
         if (d < c->dim) {

@@ -399,6 +399,7 @@ cudaError_t prepare_stage3_p3();
 cudaError_t launch_stage3_p1(const StageArgs &A, int mode, int oct, cudaStream_t s);
 cudaError_t launch_stage3_p2(const StageArgs &A, int mode, int oct, cudaStream_t s);
 cudaError_t launch_stage3_p3(const StageArgs &A, int mode, int oct, cudaStream_t s);
+cudaError_t launch_stage2(const StageArgs &A, int p, int mode, int oct, cudaStream_t s);
 
 template <int N1>
 static cudaError_t launch_1d(const StageArgs &A, int mode, cudaStream_t s)
@@ -422,6 +423,8 @@ cudaError_t prepare_stage(int dim, int p)
         }
     } else if (dim == 1 && p >= 1 && p <= 5) {
         return cudaSuccess;  // the line kernels use static shared memory only
+    } else if (dim == 2 && p >= 1 && p <= 3) {
+        return cudaSuccess;  // so do the quadrilateral kernels
     }
     return cudaErrorInvalidValue;
 }
@@ -436,6 +439,8 @@ cudaError_t launch_stage(const StageArgs &A, int p, int mode, int oct, cudaStrea
         case 2: return launch_stage3_p2(A, mode, oct, s);
         case 3: return launch_stage3_p3(A, mode, oct, s);
         }
+    } else if (A.mesh.dim == 2) {
+        return launch_stage2(A, p, mode, oct, s);
     } else if (A.mesh.dim == 1) {
         switch (p) {
         case 1: return launch_1d<2>(A, mode, s);

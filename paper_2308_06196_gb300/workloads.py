@@ -46,6 +46,10 @@ CONFIGS = {
     # u_y = 0.1 sin(2 pi x) decays by shear viscosity (1.1 GB per FP32 f array, larger than L2)
     "planar_shear": dict(dim=1, nelem=(65536,), lo=(0.0,), hi=(1.0,), p=3, nv=(32, 32, 1), vlo=(-7.0, -7.0, 0.0),
                          vhi=(7.0, 7.0, 0.0), tau=1e-3, cfl=0.1, steps=20, amp=0.1),
+    # planar Taylor-Green vortex on quadrilaterals (dim = 2) in the two-dimensional velocity space: [0, 2 pi]^2,
+    # 128^2 elements at p = 3 (262,144 points), 32^2 velocities on [-7, 7]^2, Ma 0.1, tau = 1e-3
+    "planar_tg": dict(dim=2, nelem=(128, 128), lo=(0.0, 0.0), hi=(TWO_PI, TWO_PI), p=3, nv=(32, 32, 1),
+                      vlo=(-7.0, -7.0, 0.0), vhi=(7.0, 7.0, 0.0), tau=1e-3, cfl=0.1, steps=20, mach=0.1),
     "sod_ensemble": dict(members=256, seed=0, elements=(16, 128), degrees=(2, 3), nvs=(12, 16, 24, 32), vmax=8.0,
                          rho=(0.125, 1.0), temp=(0.8, 1.25), tau=(1e-4, 1e-1), cfl=0.1, steps=20),
 }
@@ -93,6 +97,19 @@ def prim_shear(x: np.ndarray, amp: float = 0.1) -> np.ndarray:
     P[:, 0] = 1.0
     P[:, 2] = amp * np.sin(TWO_PI * x[:, 0])
     P[:, 4] = 1.0
+    return P
+
+
+def prim_planar_tg(x: np.ndarray, mach: float = 0.1, gamma: float = 2.0) -> np.ndarray:
+    """Planar Taylor-Green vortex (gamma = 2 for the two-dimensional velocity space): rho = 1,
+    U0 = Ma sqrt(gamma), u = U0 sin x cos y, v = -U0 cos x sin y, p = 1 + U0^2 / 4 (cos 2x + cos 2y), T = p."""
+    U0 = mach * math.sqrt(gamma)
+    X, Y = x[:, 0], x[:, 1]
+    P = np.zeros((len(x), 5))
+    P[:, 0] = 1.0
+    P[:, 1] = U0 * np.sin(X) * np.cos(Y)
+    P[:, 2] = -U0 * np.cos(X) * np.sin(Y)
+    P[:, 4] = 1.0 + U0 * U0 / 4.0 * (np.cos(2 * X) + np.cos(2 * Y))
     return P
 
 

@@ -16,7 +16,7 @@ def make(dim, ne, p, nv=(2, 2, 2), vl=1.0, tau=INF, lo=None, hi=None, bc=None, b
     return orc.Problem(dim, list(ne), lo, hi, p, nv, (-vl,) * 3, (vl,) * 3, tau, bc=bc, bc_state=bc_state)
 
 
-@pytest.mark.parametrize("dim,p", [(1, 1), (1, 3), (1, 5), (3, 1), (3, 2), (3, 3)])
+@pytest.mark.parametrize("dim,p", [(1, 1), (1, 3), (1, 5), (2, 2), (2, 3), (3, 1), (3, 2), (3, 3)])
 def test_free_stream_preserved(dim, p):
     ne = [5] if dim == 1 else [3, 2, 2]
     pr = make(dim, ne, p, nv=(4, 3, 5), vl=5.0)
@@ -143,3 +143,23 @@ def test_3d_equals_1d_for_x_only_data():
     # map every 3-D point to the 1-D point with the same x-node
     idx = np.array([np.argmin(np.abs(x1 - xx)) for xx in x3])
     assert np.allclose(f3, f1[idx], atol=1e-13, rtol=1e-12)
+
+
+def test_2d_equals_1d_for_x_only_data():
+    # quadrilaterals (dim = 2, 3-D velocity space): a state that varies only in x, periodic in y,
+    # evolves as the line problem
+    p, ne = 3, 4
+    kw = dict(nv=(4, 4, 4), vl=3.0, tau=0.05)
+    p1, p2 = make(1, [ne], p, **kw), make(2, [ne, 3], p, **kw)
+
+    def prim(x):
+        s = np.sin(2 * np.pi * x)
+        return np.stack([1 + 0.2 * s, 0.1 * np.cos(2 * np.pi * x), 0.05 * s, 0 * x, 1 + 0.1 * s], 1)
+
+    x1, x2 = p1.points()[:, 0], p2.points()[:, 0]
+    p1.set_state(prim(x1))
+    p2.set_state(prim(x2))
+    p1.step(0.01, 3)
+    p2.step(0.01, 3)
+    idx = np.array([np.argmin(np.abs(x1 - xx)) for xx in x2])
+    assert np.allclose(p2.get_f(), p1.get_f()[idx], atol=1e-13, rtol=1e-12)
