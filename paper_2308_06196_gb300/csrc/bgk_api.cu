@@ -327,6 +327,7 @@ NewtonArgs newton_args(bgk_ctx *c, int cold)
     N.npts = (int)c->npts;
     N.Q = c->Q;
     N.prim = c->prim;
+    N.lnc_form = 1;  // bgk_equilibrium turns lnC into rho' on the host
     N.param = c->param;
     N.err = c->err;
     N.cold = cold;
@@ -1109,7 +1110,13 @@ int bgk_equilibrium(bgk_ctx *c, double *prim_out)
     if (!c || !prim_out)
         return BGK_EINVAL;
     CK(cudaMemcpyAsync(prim_out, c->prim, c->npts * 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    return read_status(c);
+    const int rc = read_status(c);
+    // the Newton kernel keeps lnC = ln(rho' (2 pi theta')^(-m/2)) as its warm start: rho' from it
+    for (int64_t i = 0; i < c->npts; i++) {
+        double *pp = prim_out + i * 5;
+        pp[0] = pp[4] > 0.0 ? exp(pp[0]) * pow(2.0 * kPi * pp[4], 0.5 * c->vdim) : 0.0;
+    }
+    return rc;
 }
 
 int bgk_synchronize(bgk_ctx *c)

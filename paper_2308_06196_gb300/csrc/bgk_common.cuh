@@ -103,7 +103,9 @@ struct NewtonArgs {
     int ngroups;
     int npts;
     double *Q;             // [n_x][5] moments (out)
-    double *prim;          // [n_x][5] perturbed state rho', U', theta' (in: warm start, out)
+    double *prim;          // [n_x][5] perturbed state rho', U', theta' (in: warm start, out); with lnc_form
+                           // slot 0 holds lnC = ln(rho' (2 pi theta')^(-m/2)) instead of rho'
+    int lnc_form;          // 1: prim in the lnC form above (no logarithm or exponential per solve)
     float *param;          // [n_x][8] stage-kernel exponent (out)
     int *err;              // status word (atomicOr)
     int cold;              // 1: ignore prim and start from the continuous state of Q

@@ -261,10 +261,12 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     // 2. starting state (V, s^2) and target moments in the centred, scaled basis psi~ = (1, c, |c|^2/2)
     double V[3] = {u[0], u[1], u[2]}, th0 = thc, rh0 = rho;
     bool warm = false;
+    double lnc0 = 0.0;  // warm start in the lnC form: alpha_0 of the centred basis directly
     if (!A.cold && !A.continuous) {
         const double *pp = A.prim + (int64_t)pt * 5;
-        if (pp[0] > 0.0 && pp[4] > 0.0 && isfinite(pp[0] + pp[1] + pp[2] + pp[3] + pp[4])) {
+        if ((A.lnc_form || pp[0] > 0.0) && pp[4] > 0.0 && isfinite(pp[0] + pp[1] + pp[2] + pp[3] + pp[4])) {
             rh0 = pp[0];
+            lnc0 = pp[0];
             V[0] = pp[1];
             V[1] = pp[2];
             V[2] = pp[3];
@@ -280,7 +282,8 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     Qt[4] = (Q[4] - (V[0] * Q[1] + V[1] * Q[2] + V[2] * Q[3]) + 0.5 * Q[0] * (V[0] * V[0] + V[1] * V[1] + V[2] * V[2])) * is * is;
 
     // alpha = (alpha_0, a_1, a_2, a_3, -beta): g = exp(alpha_0 + a . c - beta |c|^2 / 2)
-    double al[5] = {log(rh0) - hm * log(2.0 * 3.14159265358979323846 * th0), 0.0, 0.0, 0.0, -1.0};
+    double al[5] = {warm && A.lnc_form ? lnc0 : log(rh0) - hm * log(2.0 * 3.14159265358979323846 * th0), 0.0, 0.0,
+                    0.0, -1.0};
     double c0[3], h[3], dvs[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -356,23 +359,25 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
             assemble<double>(S, exp(al[0]), M, nullptr);
             if (A.vdim == 2)
                 M[3] = Qt[3];
-            double r[5], dx[5], Jd[5][5];
+            // the FP64 residual, solved with the FP32 Jacobian in FP32: the correction only needs FP32
+            // relative accuracy (iterative refinement)
+            float r[5], dx[5], Jw[5][5];
     #pragma unroll
             for (int m = 0; m < 5; m++) {
-                r[m] = Qt[m] - M[m];
+                r[m] = (float)(Qt[m] - M[m]);
     #pragma unroll
                 for (int q = 0; q < 5; q++)
-                    Jd[m][q] = (double)J[m][q];
+                    Jw[m][q] = J[m][q];
             }
-            if (!solve5<double>(Jd, r, dx)) {
+            if (!solve5<float>(Jw, r, dx)) {
                 atomicOr(A.err, kErrNewton);
                 return;
             }
             corr = 0.0;
     #pragma unroll
             for (int m = 0; m < 5; m++) {
-                al[m] += dx[m];
-                corr = fmax(corr, fabs(dx[m]));
+                al[m] += (double)dx[m];
+                corr = fmax(corr, fabs((double)dx[m]));
             }
             // the FP32 Jacobian contracts the error by ~1e-6 per refinement: after a correction below
             // 1e-6 the residual is at FP64 resolution
@@ -393,9 +398,8 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     for (int d = 0; d < 3; d++)
         Up[d] = V[d] + s * a[d] / beta;
     const double lnC = al[0] + 0.5 * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / beta;  // ln(rho' (2 pi theta')^-m/2)
-    const double rhop = exp(lnC) * pow(2.0 * 3.14159265358979323846 * thp, hm);
     double *pp = A.prim + (int64_t)pt * 5;
-    pp[0] = rhop;
+    pp[0] = A.lnc_form ? lnC : exp(lnC) * pow(2.0 * 3.14159265358979323846 * thp, hm);
     pp[1] = Up[0];
     pp[2] = Up[1];
     pp[3] = Up[2];
