@@ -338,12 +338,14 @@ def bench_planar(steps: int, warmup: int, stream, torch) -> dict:
     return out
 
 
-def bench_quad(steps: int, warmup: int, stream, torch) -> dict:
+def bench_quad(steps: int, warmup: int, stream, torch, elements: int = 0) -> dict:
     """The planar Taylor-Green vortex on quadrilaterals (dim = 2) in the two-dimensional velocity space,
     FP32-split form: ms per step and the quadrilateral stage kernel's achieved bandwidth."""
     from paper_2308_06196_gb300.bgk import Solver
 
     c = W.config("planar_tg")
+    if elements:  # fewer, larger elements on the same box (profiling)
+        c = W.config("planar_tg", nelem=(elements, elements))
     k = W.mesh_kwargs(c)
     s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
     s.set_stream(stream.cuda_stream)
@@ -351,7 +353,7 @@ def bench_quad(steps: int, warmup: int, stream, torch) -> dict:
     g = s.autotune()
     dt = s.dt(c["cfl"])
     ms, st = timed_steps(s, dt, steps, warmup, stream, torch)
-    out = {"workload": "planar_tg", "mesh": "128^2 quadrilaterals p=3 on [0,2pi]^2", "nv": list(c["nv"]),
+    out = {"workload": "planar_tg", "mesh": f"{c['nelem'][0]}^2 quadrilaterals p=3 on [0,2pi]^2", "nv": list(c["nv"]),
            "dof": s.ndof, "value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "dt": dt,
            "tiles_per_task": g, **st}
     s.close()
@@ -468,6 +470,10 @@ def main():
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--curved-steps", type=int, default=3,
                     help="steps of Taylor-Green on curvilinear hexahedra (0: skip)")
+    ap.add_argument("--quad-elements", type=int, default=0,
+                    help="elements per direction of the planar Taylor-Green quadrilaterals (default 128)")
+    ap.add_argument("--no-planar-line", action="store_true",
+                    help="skip the line-element planar shear wave (profiling the quadrilaterals alone)")
     ap.add_argument("--planar-steps", type=int, default=3,
                     help="steps of the m = 2 planar shear workload (0: skip)")
     ap.add_argument("--batch-members", type=int, default=0,
@@ -626,8 +632,8 @@ def main():
         curved = bench_curved(args.curved_steps, warmup, stream, torch, args.elements)
     planar = None
     if args.planar_steps > 0 and world == 1:
-        planar = bench_planar(args.planar_steps, warmup, stream, torch)
-        planar["quadrilaterals"] = bench_quad(args.planar_steps, warmup, stream, torch)
+        planar = {} if args.no_planar_line else bench_planar(args.planar_steps, warmup, stream, torch)
+        planar["quadrilaterals"] = bench_quad(args.planar_steps, warmup, stream, torch, args.quad_elements)
 
     ms, graph_ms, e2e_ms = max_over_ranks([ms, graph_ms, e2e_ms], dist, "cuda")
     value = job_value(dof, world, ms)
