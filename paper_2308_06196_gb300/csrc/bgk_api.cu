@@ -30,9 +30,9 @@ cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int *d_task_star
 cudaError_t set_batch_ops(int n1, const Ops &op);
 int stage1d_tasks(const StageArgs &A);
 int stage1d_batch_ctas();
-cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slotk, int nvt, int E, int NP,
-                                   const int n[3], const double v0[3], const double dv[3], int *err,
-                                   cudaStream_t s);
+cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi, const float *gmask, int nslots,
+                                   int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
+                                   int *err, cudaStream_t s);
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
 cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s);
@@ -966,8 +966,8 @@ static int set_state_impl(bgk_ctx *c, const double *prim, cudaMemcpyKind kind)
         CK(launch_init64(c->fA64, c->prim_in, c->xi64, c->gmask, c->nvt, c->E, c->NP, c->nslots, c->vdim, c->err,
                          c->stream));
     else
-        CK(launch_init_maxwellian(c->fA, c->prim_in, c->slotk_d, c->nvt, c->E, c->NP, c->nv, c->vlo, c->dv,
-                                  c->err, c->stream));
+        CK(launch_init_maxwellian(c->fA, c->prim_in, c->mi, c->gmask, c->nslots, c->nvt, c->E, c->NP, c->nv, c->vlo,
+                                  c->dv, c->err, c->stream));
     return prologue(c, c->stream);
 }
 

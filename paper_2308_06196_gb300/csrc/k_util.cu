@@ -6,12 +6,22 @@
 namespace bgk {
 
 // Sample the continuous Maxwellian (Sec. 2, Eq. 4, velocity dimension m = 3, or 2 when nz = 1: the
-// one z node has factor 1 and U_z takes no part) of every point's primitive state into f. One CTA per element: the separable factors exp(-(xi_d - U_d)^2 / (2 theta)) of the
-// element's points are computed once in FP64 and kept in shared memory as FP32, then every
+// one z node has factor 1 and U_z takes no part) of every point's primitive state into f. One CTA per
+// element: the separable factors exp(-(xi_d - U_d)^2 / (2 theta)) of the element's points are tabulated
+// once in shared memory as FP32 (the exponent in FP64, split into an integer power of two and a
+// remainder in [-1/2, 1/2] whose 2^r is taken in FP32: within a few FP32 ulp at any exponent), then every
 // (tile, node, lane) value is the product C * Ex * Ey * Ez. Writes 0 on padded slots.
-__global__ void k_init_maxwellian(float *__restrict__ f, const double *__restrict__ prim, const int *__restrict__ slotk,
-                                  int nvt, int E, int NP, int nx, int ny, int nz, double v0x, double v0y,
-                                  double v0z, double dvx, double dvy, double dvz, int *err)
+__device__ __forceinline__ float exp_split(double x)
+{
+    const double y = x * 1.4426950408889634;  // log2(e)
+    const double n = rint(y);
+    return ldexpf(exp2f((float)(y - n)), (int)n);
+}
+
+__global__ void k_init_maxwellian(float *__restrict__ f, const double *__restrict__ prim, const float *__restrict__ mi,
+                                  const float *__restrict__ gmask, int nslots, int nvt, int E, int NP, int nx, int ny,
+                                  int nz, double v0x, double v0y, double v0z, double dvx, double dvy, double dvz,
+                                  int *err)
 {
     const double hm = nz == 1 ? 1.0 : 1.5;  // m / 2
     extern __shared__ float tab[];  // [NP][nx + ny + nz + 1]
@@ -27,27 +37,35 @@ __global__ void k_init_maxwellian(float *__restrict__ f, const double *__restric
                 atomicOr(err, kErrDomain);
             continue;
         }
-        double v;
-        if (t == 0)
-            v = rho * pow(2.0 * 3.14159265358979323846 * th, -hm);
-        else if (t <= nx)
-            v = exp(-0.5 * (v0x + (t - 1) * dvx - s[1]) * (v0x + (t - 1) * dvx - s[1]) / th);
-        else if (t <= nx + ny)
-            v = exp(-0.5 * (v0y + (t - 1 - nx) * dvy - s[2]) * (v0y + (t - 1 - nx) * dvy - s[2]) / th);
-        else if (nz == 1)
-            v = 1.0;
-        else
-            v = exp(-0.5 * (v0z + (t - 1 - nx - ny) * dvz - s[3]) * (v0z + (t - 1 - nx - ny) * dvz - s[3]) / th);
-        tab[q] = (float)v;
+        float v;
+        if (t == 0) {
+            v = (float)(rho * pow(2.0 * 3.14159265358979323846 * th, -hm));
+        } else if (t <= nx) {
+            const double c = v0x + (t - 1) * dvx - s[1];
+            v = exp_split(-0.5 * c * c / th);
+        } else if (t <= nx + ny) {
+            const double c = v0y + (t - 1 - nx) * dvy - s[2];
+            v = exp_split(-0.5 * c * c / th);
+        } else if (nz == 1) {
+            v = 1.f;
+        } else {
+            const double c = v0z + (t - 1 - nx - ny) * dvz - s[3];
+            v = exp_split(-0.5 * c * c / th);
+        }
+        tab[q] = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int vt = 0; vt < nvt; vt++) {
-        const int k = __ldg(slotk + vt * kWarp + lane);
-        const int kx = k % nx, ky = (k / nx) % ny, kz = k / (nx * ny);
+        // grid indices k_d = (m_d + n_d - 1) / 2 of the slot from the centred index table (exact)
+        const int slot = vt * kWarp + lane;
+        const int kx = __float2int_rn(0.5f * (__ldg(mi + slot) + (float)(nx - 1)));
+        const int ky = __float2int_rn(0.5f * (__ldg(mi + nslots + slot) + (float)(ny - 1)));
+        const int kz = __float2int_rn(0.5f * (__ldg(mi + 2 * nslots + slot) + (float)(nz - 1)));
+        const float gm = __ldg(gmask + slot);
         for (int i = w; i < NP; i += nw) {
             const float *t = tab + i * ntab;
-            const float v = k < 0 ? 0.f : t[0] * t[1 + kx] * t[1 + nx + ky] * t[1 + nx + ny + kz];
+            const float v = gm * (t[0] * t[1 + kx] * t[1 + nx + ky] * t[1 + nx + ny + kz]);
             __stcs(f + fidx(vt, e, i, lane, E, NP), v);
         }
     }
@@ -85,16 +103,16 @@ __global__ void k_gather_f(double *__restrict__ st, const float *__restrict__ f,
     }
 }
 
-cudaError_t launch_init_maxwellian(float *f, const double *prim, const int *slotk, int nvt, int E, int NP,
-                                   const int n[3], const double v0[3], const double dv[3], int *err,
-                                   cudaStream_t s)
+cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi, const float *gmask, int nslots,
+                                   int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
+                                   int *err, cudaStream_t s)
 {
     const int smem = NP * (n[0] + n[1] + n[2] + 1) * (int)sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_init_maxwellian, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
-    k_init_maxwellian<<<E, 256, smem, s>>>(f, prim, slotk, nvt, E, NP, n[0], n[1], n[2], v0[0], v0[1], v0[2],
-                                           dv[0], dv[1], dv[2], err);
+    k_init_maxwellian<<<E, 256, smem, s>>>(f, prim, mi, gmask, nslots, nvt, E, NP, n[0], n[1], n[2], v0[0], v0[1],
+                                           v0[2], dv[0], dv[1], dv[2], err);
     return cudaGetLastError();
 }
 
