@@ -32,7 +32,7 @@ int stage1d_tasks(const StageArgs &A);
 int stage1d_batch_ctas();
 cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi, const float *gmask, int nslots,
                                    int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
-                                   int *err, cudaStream_t s);
+                                   int *err, double *Q, cudaStream_t s);
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
 cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s);
@@ -393,7 +393,9 @@ Moments64Args moments64_args(bgk_ctx *c)
 }
 
 // Moments + conservative Maxwellian of the current f^n (after set_state / set_f).
-int prologue(bgk_ctx *c, cudaStream_t s)
+// Moments of the state f^n and its conservative Maxwellian; have_q: Q was formed with the state (the
+// initial sampling's separable moments), only the Newton solve is left.
+int prologue(bgk_ctx *c, cudaStream_t s, bool have_q = false)
 {
     if (c->prec == BGK_FP64) {
         Moments64Args M = moments64_args(c);
@@ -404,6 +406,12 @@ int prologue(bgk_ctx *c, cudaStream_t s)
         }
         CK(launch_moments64(M, s));
         CK(launch_newton(newton_args(c, 1), s));
+        return BGK_OK;
+    }
+    if (have_q) {
+        NewtonArgs N = newton_args(c, 1);
+        N.Qin = c->Q;
+        CK(launch_newton(N, s));
         return BGK_OK;
     }
     for (const Chunk &ch : c->chunks) {
@@ -967,8 +975,8 @@ static int set_state_impl(bgk_ctx *c, const double *prim, cudaMemcpyKind kind)
                          c->stream));
     else
         CK(launch_init_maxwellian(c->fA, c->prim_in, c->mi, c->gmask, c->nslots, c->nvt, c->E, c->NP, c->nv, c->vlo,
-                                  c->dv, c->err, c->stream));
-    return prologue(c, c->stream);
+                                  c->dv, c->err, c->Q, c->stream));
+    return prologue(c, c->stream, c->prec != BGK_FP64);
 }
 
 int bgk_set_state(bgk_ctx *c, const double *prim)

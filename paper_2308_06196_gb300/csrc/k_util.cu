@@ -11,6 +11,9 @@ namespace bgk {
 // once in shared memory as FP32 (the exponent in FP64, split into an integer power of two and a
 // remainder in [-1/2, 1/2] whose 2^r is taken in FP32: within a few FP32 ulp at any exponent), then every
 // (tile, node, lane) value is the product C * Ex * Ey * Ez. Writes 0 on padded slots.
+// Q (when not null): the discrete moments (Eq. 2 with Eq. 12) of every point's sampled Maxwellian in
+// FP64, from the 1-D trapezoid sums of its tabulated factors (the grid is a tensor product): they differ
+// from the moments of the stored FP32 values only by the rounding of the products.
 __device__ __forceinline__ float exp_split(double x)
 {
     const double y = x * 1.4426950408889634;  // log2(e)
@@ -21,7 +24,7 @@ __device__ __forceinline__ float exp_split(double x)
 __global__ void k_init_maxwellian(float *__restrict__ f, const double *__restrict__ prim, const float *__restrict__ mi,
                                   const float *__restrict__ gmask, int nslots, int nvt, int E, int NP, int nx, int ny,
                                   int nz, double v0x, double v0y, double v0z, double dvx, double dvy, double dvz,
-                                  int *err)
+                                  int *err, double *__restrict__ Q)
 {
     const double hm = nz == 1 ? 1.0 : 1.5;  // m / 2
     extern __shared__ float tab[];  // [NP][nx + ny + nz + 1]
@@ -55,6 +58,36 @@ __global__ void k_init_maxwellian(float *__restrict__ f, const double *__restric
         tab[q] = v;
     }
     __syncthreads();
+    if (Q)
+        for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+            const float *t = tab + i * ntab;
+            const int n[3] = {nx, ny, nz};
+            const double v0[3] = {v0x, v0y, v0z}, dv[3] = {dvx, dvy, dvz};
+            double S[3][3];
+            int off = 1;
+            for (int d = 0; d < 3; d++) {
+                S[d][0] = S[d][1] = S[d][2] = 0.0;
+                if (n[d] == 1) {  // the absent u_z: one node at 0 of unit weight
+                    S[d][0] = (double)t[off];
+                } else {
+                    for (int k = 0; k < n[d]; k++) {
+                        const double x = v0[d] + k * dv[d];
+                        const double a = (k == 0 || k == n[d] - 1 ? 0.5 * dv[d] : dv[d]) * (double)t[off + k];
+                        S[d][0] += a;
+                        S[d][1] = fma(x, a, S[d][1]);
+                        S[d][2] = fma(x * x, a, S[d][2]);
+                    }
+                }
+                off += n[d];
+            }
+            const double C = (double)t[0];
+            double *q = Q + ((int64_t)e * NP + i) * 5;
+            q[0] = C * S[0][0] * S[1][0] * S[2][0];
+            q[1] = C * S[0][1] * S[1][0] * S[2][0];
+            q[2] = C * S[0][0] * S[1][1] * S[2][0];
+            q[3] = C * S[0][0] * S[1][0] * S[2][1];
+            q[4] = 0.5 * C * (S[0][2] * S[1][0] * S[2][0] + S[0][0] * S[1][2] * S[2][0] + S[0][0] * S[1][0] * S[2][2]);
+        }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int vt = 0; vt < nvt; vt++) {
         // grid indices k_d = (m_d + n_d - 1) / 2 of the slot from the centred index table (exact)
@@ -105,14 +138,14 @@ __global__ void k_gather_f(double *__restrict__ st, const float *__restrict__ f,
 
 cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi, const float *gmask, int nslots,
                                    int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
-                                   int *err, cudaStream_t s)
+                                   int *err, double *Q, cudaStream_t s)
 {
     const int smem = NP * (n[0] + n[1] + n[2] + 1) * (int)sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_init_maxwellian, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
     k_init_maxwellian<<<E, 256, smem, s>>>(f, prim, mi, gmask, nslots, nvt, E, NP, n[0], n[1], n[2], v0[0], v0[1],
-                                           v0[2], dv[0], dv[1], dv[2], err);
+                                           v0[2], dv[0], dv[1], dv[2], err, Q);
     return cudaGetLastError();
 }
 
