@@ -91,8 +91,10 @@ __device__ __forceinline__ void curv_line(float (&sv)[N1], const float (&fl)[N1]
 // GEN = 0: every face periodic, no body force and one velocity spacing on all axes (the lean form;
 // the Maxwellian exponent needs only the sum of the squared grid indices); GEN = 1: Dirichlet and
 // diffuse-wall faces, the body-force source and per-axis spacings.
-// CURV = 1 (with GEN = 1, OCT = 8): curvilinear hexahedra, the reference-space flux (Ja^d . xi) f and
-// per-lane upwinding at every face point from the shared face normal.
+// CURV = 1 (with GEN = 1, OCT = 8): curvilinear hexahedra on the structured element grid, the
+// reference-space flux (Ja^d . xi) f and per-lane upwinding at every face point from the shared face
+// normal; CURV = 2: the same with unstructured connectivity (the element's neighbours, their shared
+// faces and face-point orientations from its connectivity row).
 template <int N1, int MODE, int OCT, int GEN, int CURV = 0>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTAS_P3_GEN : BGK_STAGE3_MINCTAS_P3)
                                                : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 (&cs.fnm[0][0][0])[q] = __ldg(A.fnm + (int64_t)e * 6 * NQ + q);
             if (tid == 0)
                 cs.iwj = __ldg(A.iwj + e);
-            if (A.ftab) {
+            if (CURV == 2) {
                 if (tid < 6)
                     cs.ftab[tid] = __ldg(A.ftab + (int64_t)e * 6 + tid);
                 for (int q = tid; q < 6 * NQ; q += NT)
@@ -164,29 +166,29 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     const float bdt = A.b * A.dt;
     // curvilinear: the exterior trace at face (d, side) for the face point fp of the line whose own nodes
     // are nd (tile vl, this lane): the neighbour's interpolant at the shared face, or the face's ghost
-    auto exterior = [&](int vl, int slot, int d, int side, int fp, const int (&nd)[N1]) -> float {
-        int en, g, stride = 0, base = 0;
-        bool hi_end;  // the neighbour's shared face is its +1 end
-        if (A.ftab) {
-            const int4 t = cs.ftab[2 * d + side];
-            en = t.x;
-            g = -1 - t.x;
-            stride = t.y;
-            hi_end = t.z != 0;
-            base = cs.fbase[2 * d + side][fp];
-        } else {
-            en = upwind_neighbour(A.mesh, ec, d, side == 0);
-            g = 2 * d + side;
-            hi_end = side == 0;
-        }
-        if (en < 0)
-            return __ldg(A.ghost + (int64_t)g * A.nslots + slot);
+    // exterior trace at face (d, side), face point fp, from the connectivity row (CURV = 2)
+    auto exterior = [&](int vl, int slot, int d, int side, int fp) -> float {
+        const int4 t = cs.ftab[2 * d + side];  // (neighbour or -1 - ghost face, stride, its +1 end, 0)
+        if (t.x < 0)
+            return __ldg(A.ghost + (int64_t)(-1 - t.x) * A.nslots + slot);
+        const int base = cs.fbase[2 * d + side][fp];
         float v[N1];
+        const float *nb = A.src + fidx(vl, t.x, 0, lane, E, NP);
+#pragma unroll
+        for (int j = 0; j < N1; j++)
+            v[j] = __ldg(nb + (base + j * t.y) * kWarp);
+        return t.z ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
+    };
+    // the structured grid's neighbour en: its values on the line through our nodes nd (CURV = 1)
+    auto nbline = [&](int vl, int en, const int (&nd)[N1]) {
+        struct Line {
+            float v[N1];
+        } r;
         const float *nb = A.src + fidx(vl, en, 0, lane, E, NP);
 #pragma unroll
         for (int j = 0; j < N1; j++)
-            v[j] = __ldg(nb + (A.ftab ? base + j * stride : nd[j]) * kWarp);
-        return hi_end ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
+            r.v[j] = __ldg(nb + nd[j] * kWarp);
+        return r;
     };
 
     // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
@@ -265,6 +267,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 }
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
+                    const int eL = CURV == 1 ? upwind_neighbour(A.mesh, ec, d, true) : 0;
+                    const int eR = CURV == 1 ? upwind_neighbour(A.mesh, ec, d, false) : 0;
 #pragma unroll
                     for (int ln = 0; ln < N1; ln++) {
                         float fl[N1], u[N1], sv[N1];
@@ -280,8 +284,23 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
                         const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
                         // inflow through the low / high face: the exterior trace (predicated per lane)
-                        const float tL = uL > 0.f ? exterior(vl, slot, d, 0, ln + N1 * w, nd) : 0.f;
-                        const float tR = uR < 0.f ? exterior(vl, slot, d, 1, ln + N1 * w, nd) : 0.f;
+                        float tL = 0.f, tR = 0.f;
+                        if (uL > 0.f) {
+                            if (CURV == 2)
+                                tL = exterior(vl, slot, d, 0, ln + N1 * w);
+                            else if (eL >= 0)
+                                tL = trace_line<N1, true>(nbline(vl, eL, nd).v, A.ops);
+                            else
+                                tL = __ldg(A.ghost + (2 * d) * A.nslots + slot);
+                        }
+                        if (uR < 0.f) {
+                            if (CURV == 2)
+                                tR = exterior(vl, slot, d, 1, ln + N1 * w);
+                            else if (eR >= 0)
+                                tR = trace_line<N1, false>(nbline(vl, eR, nd).v, A.ops);
+                            else
+                                tR = __ldg(A.ghost + (2 * d + 1) * A.nslots + slot);
+                        }
                         curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
                         for (int j = 0; j < N1; j++)
@@ -295,6 +314,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
                 }
                 // z-lines of slice iy = w (all layers) from the shared tile; unscaled sums to zc
+                const int eL = CURV == 1 ? upwind_neighbour(A.mesh, ec, 2, true) : 0;
+                const int eR = CURV == 1 ? upwind_neighbour(A.mesh, ec, 2, false) : 0;
 #pragma unroll
                 for (int ln = 0; ln < N1; ln++) {
                     float fl[N1], u[N1], sv[N1];
@@ -309,8 +330,23 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     const float4 nL = cs.fnm[2][0][ln + N1 * w], nR = cs.fnm[2][1][ln + N1 * w];
                     const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
                     const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
-                    const float tL = uL > 0.f ? exterior(vl, slot, 2, 0, ln + N1 * w, nd) : 0.f;
-                    const float tR = uR < 0.f ? exterior(vl, slot, 2, 1, ln + N1 * w, nd) : 0.f;
+                    float tL = 0.f, tR = 0.f;
+                    if (uL > 0.f) {
+                        if (CURV == 2)
+                            tL = exterior(vl, slot, 2, 0, ln + N1 * w);
+                        else if (eL >= 0)
+                            tL = trace_line<N1, true>(nbline(vl, eL, nd).v, A.ops);
+                        else
+                            tL = __ldg(A.ghost + 4 * A.nslots + slot);
+                    }
+                    if (uR < 0.f) {
+                        if (CURV == 2)
+                            tR = exterior(vl, slot, 2, 1, ln + N1 * w);
+                        else if (eR >= 0)
+                            tR = trace_line<N1, false>(nbline(vl, eR, nd).v, A.ops);
+                        else
+                            tR = __ldg(A.ghost + 5 * A.nslots + slot);
+                    }
                     curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
                     for (int j = 0; j < N1; j++)
@@ -601,6 +637,10 @@ cudaError_t prepare3()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stage3_smem_bytes<N1, 1, 1>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 stage3_smem_bytes<N1, 1, 2>());
+
     return e;
 }
 
@@ -628,7 +668,7 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
     if (mode == 1)
         return launch3<N1, 1, 8, 0>(A, s);
     if (A.met)  // curvilinear hexahedra: the general form with the metric, upwind side per lane
-        return launch3<N1, 0, 8, 1, 1>(A, s);
+        return A.ftab ? launch3<N1, 0, 8, 1, 2>(A, s) : launch3<N1, 0, 8, 1, 1>(A, s);
     // the lean form: periodic faces, no force, no limiter, constant tau, one velocity spacing on all axes
     bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
     for (int f = 0; f < 6; f++)
