@@ -395,21 +395,23 @@ def bench_curved(steps: int, warmup: int, stream, torch, elements: int = 0) -> d
            "value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "dt": dt, "tiles_per_task": g, **st}
     Q = s.moments()
     s.close()
-    # the same mesh as an unstructured one: seeded random element order and local-axis rotations,
-    # table-driven neighbours; the same steps must give the same moments up to FP32 rounding
-    u = W.unstructured_box(c["nelem"], c["p"], seed=0)
-    m = u["node_map"]
-    s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
-    s.set_stream(stream.cuda_stream)
-    s.set_connectivity(u["nbr"], u["nface"], u["orient"])
-    s.set_geometry(X[m])
-    s.set_state(W.prim_field(WORKLOAD, X[m]))
-    s.autotune()
-    ms_u, st_u = timed_steps(s, dt, steps, warmup, stream, torch)
-    Qu = s.moments()
-    s.close()
-    out["unstructured"] = {"value": s.ndof * 3 / (ms_u * 1e-3), "unit": UNIT, "ms_per_step": ms_u, **st_u,
-                           "moments_max_rel_diff_vs_structured": float(np.abs(Qu - Q[m]).max() / np.abs(Q).max())}
+    # the same mesh as an unstructured one (table-driven neighbours): every element's local axes rotated
+    # at random, in the grid's own element order (as a locality-ordered mesh) and in a random order (no
+    # locality at all); the same steps must give the same moments up to FP32 rounding
+    for name, shuffle in (("unstructured", False), ("unstructured_random_order", True)):
+        u = W.unstructured_box(c["nelem"], c["p"], seed=0, shuffle=shuffle)
+        m = u["node_map"]
+        s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
+        s.set_stream(stream.cuda_stream)
+        s.set_connectivity(u["nbr"], u["nface"], u["orient"])
+        s.set_geometry(X[m])
+        s.set_state(W.prim_field(WORKLOAD, X[m]))
+        s.autotune()
+        ms_u, st_u = timed_steps(s, dt, steps, warmup, stream, torch)
+        Qu = s.moments()
+        s.close()
+        out[name] = {"value": s.ndof * 3 / (ms_u * 1e-3), "unit": UNIT, "ms_per_step": ms_u, **st_u,
+                     "moments_max_rel_diff_vs_structured": float(np.abs(Qu - Q[m]).max() / np.abs(Q).max())}
     return out
 
 

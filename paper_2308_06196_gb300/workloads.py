@@ -256,9 +256,10 @@ def _proper_rotations():
     return out
 
 
-def unstructured_box(ne, p: int, bc=None, seed: int = 0) -> dict:
+def unstructured_box(ne, p: int, bc=None, seed: int = 0, shuffle: bool = True) -> dict:
     """A structured ne[0] x ne[1] x ne[2] hexahedral grid relabelled as an unstructured mesh: elements in
-    a seeded random order, each with a seeded random rotation of its local axes. Returns
+    a seeded random order (or the grid's own order with shuffle=False, as a locality-ordered mesh would
+    have), each with a seeded random rotation of its local axes. Returns
       node_map [E*NP]: (structured point index) of every new point (new element-major, local x fastest),
       nbr, nface, orient [E, 6]: the connectivity tables of oracle_set_connectivity / bgk_set_connectivity
     (bc[d][side] of the structured grid: 0 periodic, else a boundary face with the structured face's
@@ -267,7 +268,7 @@ def unstructured_box(ne, p: int, bc=None, seed: int = 0) -> dict:
     ne = tuple(int(v) for v in ne)
     E, n1 = ne[0] * ne[1] * ne[2], p + 1
     NP = n1 ** 3
-    perm = rng.permutation(E)              # structured element -> new element
+    perm = rng.permutation(E) if shuffle else np.arange(E)  # structured element -> new element
     inv = np.argsort(perm)                 # new element -> structured element
     rots = _proper_rotations()
     rot = [rots[int(rng.integers(0, 24))] for _ in range(E)]  # per new element
