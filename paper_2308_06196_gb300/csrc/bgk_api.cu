@@ -1056,6 +1056,8 @@ int bgk_step(bgk_ctx *c, double dt, int nsteps)
 {
     if (!c || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
         return BGK_EINVAL;
+    if (c->ftab && !c->met)  // a connectivity table means nothing without the elements' node coordinates
+        return fail(c, BGK_EINVAL, "unstructured connectivity needs bgk_set_geometry before stepping");
     if (c->sticky)
         return read_status(c);
     if (nsteps == 0)
@@ -1420,7 +1422,8 @@ int bgk_autotune(bgk_ctx *c, int *g_out)
     char key[256];
     snprintf(key, sizeof key, "%d/%d/%d,%d,%d/%d,%d,%d/%zu/%d", c->dim, c->p, c->nv[0], c->nv[1], c->nv[2], c->ne[0],
              c->ne[1], c->ne[2], c->chunks.size(),
-             (int)(c->has_wall || c->has_force || c->bc[0] || c->bc[2] || c->bc[4]) + 2 * (c->met != nullptr));
+             (int)(c->has_wall || c->has_force || c->bc[0] || c->bc[2] || c->bc[4]) + 2 * (c->met != nullptr) +
+                 4 * (c->ftab != nullptr));
     for (auto &kv : g_tuned)
         if (kv.first == key) {
             set_task_length(c, kv.second);

@@ -186,3 +186,9 @@ def test_unstructured_table_rejected():
     with pytest.raises(BgkError) as err:
         x.set_connectivity(bad, u["nface"], u["orient"])
     assert err.value.code == BGK_EINVAL
+    # a valid table without the node coordinates cannot be stepped
+    x.set_connectivity(u["nbr"], u["nface"], u["orient"])
+    x.set_state(W.smooth_prim(x.points(), 3, seed=2))
+    with pytest.raises(BgkError) as err:
+        x.step(1e-3, 1)
+    assert err.value.code == BGK_EINVAL
