@@ -805,9 +805,10 @@ int oracle_set_geometry(orc_ctx *c, const double *x)
 {
     if (!c || !x || c->dim != 3)
         return -1;
-    for (int fc = 0; fc < 6; fc++)
-        if (c->bc[fc] == ORC_WALL)
-            return -1;
+    if (c->cn)  /* walls of an unstructured mesh would need boundary faces of their own */
+        for (int fc = 0; fc < 6; fc++)
+            if (c->bc[fc] == ORC_WALL)
+                return -1;
     const int nf = c->n1 * c->n1;
     c->gx = (double *)realloc(c->gx, sizeof(double) * 3 * c->npts);
     c->Ja = (double *)realloc(c->Ja, sizeof(double) * 9 * c->npts);
@@ -1041,6 +1042,26 @@ static double wall_density(const orc_ctx *c, const double *f, int64_t e, int d, 
     return out / in;
 }
 
+/* Diffuse-wall density at a face point of a curved wall: as wall_density, with the outward unit normal
+ * n = +-N / |N| of the face normal N at the point (N points towards +r_d, outward on the high face). */
+static double wall_density_curved(const orc_ctx *c, const double *f, int64_t e, int d, int side, const int *ic,
+                                  const double *N)
+{
+    const int fc = 2 * d + side;
+    const double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]), sg = side ? 1.0 : -1.0;
+    const double n[3] = {sg * N[0] / nn, sg * N[1] / nn, sg * N[2] / nn};
+    double out = 0.0, in = 0.0;
+    for (int64_t k = 0; k < c->nvel; k++) {
+        const double *v = c->xi + 3 * k;
+        const double un = n[0] * v[0] + n[1] * v[1] + n[2] * v[2]; /* xi . n_out */
+        if (un > 0)
+            out += c->w[k] * un * interior_trace(c, f, e, d, side, ic, k);
+        else if (un < 0)
+            in += c->w[k] * (-un) * c->ghost[fc * c->nvel + k];
+    }
+    return out / in;
+}
+
 /* The residual on curvilinear hexahedra: along every reference line of direction d, the nodal fluxes
  * F_j = (Ja^d . xi) f_j, their derivative D F, and the FR correction with the upwind common flux of the
  * face normal N (Eq. 9 with u_n = N . xi, positive in +r_d); R = -(sum_d dF_d) / J. */
@@ -1069,6 +1090,14 @@ static int residual_curved(const orc_ctx *c, const double *f, double *R)
                 }
                 const double *NL = c->fn + (((e * 3 + d) * 2 + 0) * nf + ln) * 3;
                 const double *NR = c->fn + (((e * 3 + d) * 2 + 1) * nf + ln) * 3;
+                /* wall densities of the line's two faces, if they are walls */
+                double rw[2] = {0.0, 0.0};
+                if (!c->cn)
+                    for (int side = 0; side < 2; side++) {
+                        const int edge = side ? (ec[d] == c->ne[d] - 1) : (ec[d] == 0);
+                        if (edge && c->bc[2 * d + side] == ORC_WALL)
+                            rw[side] = wall_density_curved(c, f, e, d, side, ic, side ? NR : NL);
+                    }
                 for (int64_t k = 0; k < c->nvel; k++) {
                     const double *v = c->xi + 3 * k;
                     double fl[MAXN], F[MAXN], fL = 0.0, fR = 0.0, FL = 0.0, FR = 0.0;
@@ -1083,8 +1112,8 @@ static int residual_curved(const orc_ctx *c, const double *f, double *R)
                     }
                     const double uL = NL[0] * v[0] + NL[1] * v[1] + NL[2] * v[2];
                     const double uR = NR[0] * v[0] + NR[1] * v[1] + NR[2] * v[2];
-                    const double FIL = uL > 0 ? uL * exterior_value(c, f, ec, d, 0, ic, k, 0.0) : uL * fL;
-                    const double FIR = uR > 0 ? uR * fR : uR * exterior_value(c, f, ec, d, 1, ic, k, 0.0);
+                    const double FIL = uL > 0 ? uL * exterior_value(c, f, ec, d, 0, ic, k, rw[0]) : uL * fL;
+                    const double FIR = uR > 0 ? uR * fR : uR * exterior_value(c, f, ec, d, 1, ic, k, rw[1]);
                     for (int i = 0; i < n1; i++) {
                         double dF = 0.0;
                         for (int j = 0; j < n1; j++)

@@ -119,7 +119,9 @@ void oracle_set_limiter(orc_ctx *c, int on);
  * moments; mu_ref <= 0 restores the constant tau given at creation (which must stay > 0). */
 void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega);
 
-/* Curvilinear hexahedra (dim = 3; no diffuse walls): x[n_x][3] are the physical coordinates of every
+/* Curvilinear hexahedra (dim = 3; diffuse walls on the structured element grid only, with the wall
+ * density of every face point set by zero net mass flux through the curved face's own normal there):
+ * x[n_x][3] are the physical coordinates of every
  * solution node (point order as above); each element is the degree-p interpolant of its nodes. The
  * metric terms Ja^i_n (Kopriva's conservative curl form) and J are computed here, the advection
  * becomes the reference-space FR residual of (Ja^i . xi) f over J, with face normals averaged between
