@@ -203,6 +203,7 @@ struct bgk_ctx {
     // curvilinear hexahedra (bgk_set_geometry)
     float4 *met = nullptr, *fnm = nullptr;
     float *iwj = nullptr;
+    double *wn64 = nullptr;  // outward unit normals of the curved wall face points [6][nfmax][N1^2][4]
     // unstructured connectivity (bgk_set_connectivity): host tables [E][6] and their device form
     std::vector<int> cnbr, cface, corient;
     int4 *ftab = nullptr;
@@ -449,6 +450,8 @@ int enqueue_wall(bgk_ctx *c, const std::vector<const void *> &src, cudaStream_t 
     }
     const bool f64 = c->prec == BGK_FP64;
     W.rhow = f64 ? (void *)c->rhow64 : (void *)c->rhow32;
+    W.wn = c->wn64;  // curved walls (FP32-split form only)
+    W.ghost = c->ghost;
     CK(launch_wall(W, f64, f64 ? (const void *)c->w64 : (const void *)c->w32,
                    f64 ? (const void *)c->xi64 : (const void *)c->xi, s));
     return BGK_OK;
@@ -616,7 +619,7 @@ void bgk_destroy(bgk_ctx *c)
     void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
-                    c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase};
+                    c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase, c->wn64};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -1250,9 +1253,9 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
 {
     if (!c || !x)
         return BGK_EINVAL;
-    if (c->dim != 3 || c->prec != BGK_FP32_SPLIT || c->has_wall)
-        return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3) in the FP32-split form "
-                                   "without diffuse walls");
+    if (c->dim != 3 || c->prec != BGK_FP32_SPLIT || (c->has_wall && !c->cnbr.empty()))
+        return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3) in the FP32-split form, "
+                                   "diffuse walls on the structured element grid only");
     const int NP = c->NP, N1 = c->N1, NQ = N1 * N1, E = c->E;
     std::vector<double> Ja((size_t)c->npts * 9), J(c->npts);
     std::vector<double> X(NP), dX(9 * (size_t)NP), V(NP), dV(9 * (size_t)NP);
@@ -1309,6 +1312,7 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
         }
     };
     std::vector<float4> met((size_t)E * NP * 3), fn((size_t)E * 6 * NQ);
+    std::vector<double> wn(c->has_wall ? (size_t)6 * c->nfmax * NQ * 4 : 0, 0.0);  // curved wall normals
     std::vector<float> iwj(E);
     for (int e = 0; e < E; e++) {
         const int ec[3] = {e % c->ne[0], (e / c->ne[0]) % c->ne[1], e / (c->ne[0] * c->ne[1])};
@@ -1357,6 +1361,15 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
                             Nv[n] = 0.5 * (Nv[n] + sg * Nn[n]);
                     }
                     fn[(((size_t)e * 3 + d) * 2 + side) * NQ + ln] = make_float4((float)Nv[0], (float)Nv[1], (float)Nv[2], 0.f);
+                    if (!shared && c->bc[2 * d + side] == BGK_BC_DIFFUSE_WALL) {
+                        // outward unit normal of the wall face point, at the wall kernel's face element index
+                        const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
+                        const int fe = ec[o1] + c->ne[o1] * ec[o2];
+                        const double nn = sqrt(Nv[0] * Nv[0] + Nv[1] * Nv[1] + Nv[2] * Nv[2]), sg = side ? 1.0 : -1.0;
+                        double *o = &wn[(((size_t)(2 * d + side) * c->nfmax + fe) * NQ + ln) * 4];
+                        for (int n = 0; n < 3; n++)
+                            o[n] = sg * Nv[n] / nn;
+                    }
                 }
             }
     }
@@ -1383,6 +1396,11 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
     CK(cudaMemcpy(c->met, met.data(), met.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->fnm, fn.data(), fn.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->iwj, iwj.data(), iwj.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (c->has_wall) {
+        if (!c->wn64)
+            CK(dalloc(c, &c->wn64, wn.size()));
+        CK(cudaMemcpy(c->wn64, wn.data(), wn.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
     c->geom.assign(x, x + c->npts * 3);
     c->curv_smax = smax;
     if (c->gexec) {  // the captured launches carry the old arguments

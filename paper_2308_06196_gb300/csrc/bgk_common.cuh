@@ -173,6 +173,11 @@ struct WallArgs {
     int N1, NP, nfmax;
     double lm[kMaxN1], lp[kMaxN1];
     void *rhow;            // out: float or double [6][nfmax][N1^2]
+    // curved walls (FP32-split form): the outward unit normal of every wall face point, [6][nfmax][N1^2][4]
+    // (FP64), or null on affine faces; with it both sums run per face point over all velocities, the
+    // incoming one with the unit-density wall Maxwellian ghost[6][nslots]
+    const double *wn;
+    const float *ghost;
 };
 
 // Moment weights of the FP32 stage kernels in the grid-index basis. With W = w / (dv_x dv_y dv_z)

@@ -179,6 +179,10 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
             v[j] = __ldg(nb + (base + j * t.y) * kWarp);
         return t.z ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
     };
+    // wall density of face point fp of the element's boundary face g (a diffuse wall), else 1 (CURV = 1)
+    auto wall_rho = [&](int g, int d, int fp) -> float {
+        return A.mesh.bc[g] == 2 ? __ldg(A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + fp) : 1.f;
+    };
     // the structured grid's neighbour en: its values on the line through our nodes nd (CURV = 1)
     auto nbline = [&](int vl, int en, const int (&nd)[N1]) {
         struct Line {
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                             else if (eL >= 0)
                                 tL = trace_line<N1, true>(nbline(vl, eL, nd).v, A.ops);
                             else
-                                tL = __ldg(A.ghost + (2 * d) * A.nslots + slot);
+                                tL = __ldg(A.ghost + (2 * d) * A.nslots + slot) * wall_rho(2 * d, d, ln + N1 * w);
                         }
                         if (uR < 0.f) {
                             if (CURV == 2)
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                             else if (eR >= 0)
                                 tR = trace_line<N1, false>(nbline(vl, eR, nd).v, A.ops);
                             else
-                                tR = __ldg(A.ghost + (2 * d + 1) * A.nslots + slot);
+                                tR = __ldg(A.ghost + (2 * d + 1) * A.nslots + slot) * wall_rho(2 * d + 1, d, ln + N1 * w);
                         }
                         curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         else if (eL >= 0)
                             tL = trace_line<N1, true>(nbline(vl, eL, nd).v, A.ops);
                         else
-                            tL = __ldg(A.ghost + 4 * A.nslots + slot);
+                            tL = __ldg(A.ghost + 4 * A.nslots + slot) * wall_rho(4, 2, ln + N1 * w);
                     }
                     if (uR < 0.f) {
                         if (CURV == 2)
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         else if (eR >= 0)
                             tR = trace_line<N1, false>(nbline(vl, eR, nd).v, A.ops);
                         else
-                            tR = __ldg(A.ghost + 5 * A.nslots + slot);
+                            tR = __ldg(A.ghost + 5 * A.nslots + slot) * wall_rho(5, 2, ln + N1 * w);
                     }
                     curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll

@@ -7,7 +7,9 @@
 // lets out) and M_w the unit-density Maxwellian of the wall (the denominator is fixed per face and
 // precomputed on the host). One warp per face point; lanes run over the outgoing velocities of the
 // stage source, accumulating in FP64. T is the storage type of f (float or double); the quadrature
-// weights and velocities are those the moments use (FP32 tables for the FP32 form).
+// weights and velocities are those the moments use (FP32 tables for the FP32 form). On curved walls
+// the normal changes from point to point: both sums are then taken per face point, over all
+// velocities, with the outward unit normal of the point.
 #include "bgk_common.cuh"
 
 namespace bgk {
@@ -18,7 +20,7 @@ __global__ void __launch_bounds__(256) k_wall(const WallArgs A, const W *w, cons
     const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     const int N1 = A.N1, NQ = N1 * N1, NP = A.NP, E = A.mesh.nelem;
     const int f = gw / (A.nfmax * NQ);
-    if (f >= 6 || A.inv_in[f] == 0.0)
+    if (f >= 6 || (A.inv_in[f] == 0.0 && !(A.wn && A.mesh.bc[f] == 2)))
         return;  // whole warp
     const int fe = (gw / NQ) % A.nfmax, fnode = gw % NQ;
     const int d = f >> 1, side = f & 1;
@@ -36,6 +38,34 @@ __global__ void __launch_bounds__(256) k_wall(const WallArgs A, const W *w, cons
     nc[d] = 0;
     const int n0 = nc[0] + N1 * (nc[1] + N1 * nc[2]);
     const int stride = d == 0 ? 1 : (d == 1 ? N1 : NQ);
+    if (A.wn) {  // curved wall: per-point normal, both sums here
+        const double *n = A.wn + (((int64_t)f * A.nfmax + fe) * NQ + fnode) * 4;
+        double out = 0.0, in = 0.0;
+        for (int c = 0; c < A.nchunks; c++) {
+            const T *src = static_cast<const T *>(A.src[c]);
+            for (int vl = 0; vl < A.nvt[c]; vl++) {
+                const int slot = (A.vt0[c] + vl) * kWarp + lane;
+                const double un = n[0] * (double)xi[slot] + n[1] * (double)xi[(int64_t)A.nslots + slot] +
+                                  n[2] * (double)xi[2 * (int64_t)A.nslots + slot];
+                if (un > 0.0) {
+                    const T *b = src + fidx(vl, e, n0, lane, E, NP);
+                    double t = 0.0;
+                    for (int j = 0; j < N1; j++)
+                        t += (side ? A.lp[j] : A.lm[j]) * (double)b[(int64_t)j * stride * kWarp];
+                    out += (double)w[slot] * un * t;
+                } else if (un < 0.0) {
+                    in -= (double)w[slot] * un * (double)A.ghost[(int64_t)f * A.nslots + slot];
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            out += __shfl_xor_sync(0xffffffffu, out, o);
+            in += __shfl_xor_sync(0xffffffffu, in, o);
+        }
+        if (lane == 0)
+            static_cast<T *>(A.rhow)[((int64_t)f * A.nfmax + fe) * NQ + fnode] = (T)(out / in);
+        return;
+    }
     double sum = 0.0;
     for (int c = 0; c < A.nchunks; c++) {
         const int oc = A.oct[c];
