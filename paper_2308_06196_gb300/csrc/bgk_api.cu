@@ -36,7 +36,8 @@ cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
 cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s);
-cudaError_t launch_limit64(double *f, int nvt, int E, int NP, int N1, int dim, const Ops64 &ops, cudaStream_t s);
+cudaError_t launch_limit64(double *f, int nvt, int E, int NP, int N1, int dim, const Ops64 &ops, const double *ijac,
+                           cudaStream_t s);
 cudaError_t launch_wall(const WallArgs &A, bool fp64, const void *w, const void *xi, cudaStream_t s);
 cudaError_t launch_moments64(const Moments64Args &A, cudaStream_t s);
 cudaError_t launch_init64(double *f, const double *prim, const double *xi, const float *gmask, int nvt, int E, int NP,
@@ -204,6 +205,7 @@ struct bgk_ctx {
     float4 *met = nullptr, *fnm = nullptr;
     float *iwj = nullptr;
     double *wn64 = nullptr;  // outward unit normals of the curved wall face points [6][nfmax][N1^2][4]
+    double *ja64 = nullptr, *ijac64 = nullptr, *fnm64 = nullptr;  // the same metric in FP64 (all-FP64 form)
     // unstructured connectivity (bgk_set_connectivity): host tables [E][6] and their device form
     std::vector<int> cnbr, cface, corient;
     int4 *ftab = nullptr;
@@ -450,8 +452,8 @@ int enqueue_wall(bgk_ctx *c, const std::vector<const void *> &src, cudaStream_t 
     }
     const bool f64 = c->prec == BGK_FP64;
     W.rhow = f64 ? (void *)c->rhow64 : (void *)c->rhow32;
-    W.wn = c->wn64;  // curved walls (FP32-split form only)
-    W.ghost = c->ghost;
+    W.wn = c->wn64;  // curved walls
+    W.ghost = f64 ? (const void *)c->ghost64 : (const void *)c->ghost;
     CK(launch_wall(W, f64, f64 ? (const void *)c->w64 : (const void *)c->w32,
                    f64 ? (const void *)c->xi64 : (const void *)c->xi, s));
     return BGK_OK;
@@ -508,13 +510,18 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
             A.dt = dt;
             A.inv_tau = 1.0 / c->tau;
             A.itau = c->itau64;
+            A.ja = c->ja64;  // curvilinear hexahedra (null on the affine mesh)
+            A.ijac = c->ijac64;
+            A.fnm = c->fnm64;
+            A.ftab = c->ftab;
+            A.fbase = c->fbase;
             int64_t real = 0;
             for (int v = ch.vt0 * kWarp; v < (ch.vt0 + ch.nvt) * kWarp; v++)
                 real += c->slotk[v] >= 0;
             ev_begin(c, 0, (double)real * c->npts * sizeof(double) * (st == 0 ? 2 : 3));
             CK(launch_stage64(A, s));
             if (c->opts.limiter)
-                CK(launch_limit64(A.dst, ch.nvt, c->E, c->NP, c->N1, c->dim, c->ops64, s));
+                CK(launch_limit64(A.dst, ch.nvt, c->E, c->NP, c->N1, c->dim, c->ops64, c->ijac64, s));
             ev_end(c);
             M.base[q] = A.dst;
             M.vt0[q] = ch.vt0;
@@ -619,7 +626,8 @@ void bgk_destroy(bgk_ctx *c)
     void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
-                    c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase, c->wn64};
+                    c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase, c->wn64,
+                    c->ja64, c->ijac64, c->fnm64};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -1200,9 +1208,8 @@ int bgk_set_connectivity(bgk_ctx *c, const int *nbr, const int *nface, const int
 {
     if (!c || !nbr || !nface || !orient)
         return BGK_EINVAL;
-    if (c->dim != 3 || c->prec != BGK_FP32_SPLIT || c->has_wall)
-        return fail(c, BGK_EINVAL, "unstructured connectivity is built for hexahedra (dim = 3) in the FP32-split "
-                                   "form without diffuse walls");
+    if (c->dim != 3 || c->has_wall)
+        return fail(c, BGK_EINVAL, "unstructured connectivity is built for hexahedra (dim = 3) without diffuse walls");
     const int E = c->E, N1 = c->N1, NQ = N1 * N1;
     for (int64_t q = 0; q < (int64_t)E * 6; q++) {
         if (nbr[q] >= E || nbr[q] < -6 || nface[q] < 0 || nface[q] > 5 || orient[q] < 0 || orient[q] > 7)
@@ -1253,9 +1260,9 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
 {
     if (!c || !x)
         return BGK_EINVAL;
-    if (c->dim != 3 || c->prec != BGK_FP32_SPLIT || (c->has_wall && !c->cnbr.empty()))
-        return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3) in the FP32-split form, "
-                                   "diffuse walls on the structured element grid only");
+    if (c->dim != 3 || (c->has_wall && !c->cnbr.empty()))
+        return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3), diffuse walls on the "
+                                   "structured element grid only");
     const int NP = c->NP, N1 = c->N1, NQ = N1 * N1, E = c->E;
     std::vector<double> Ja((size_t)c->npts * 9), J(c->npts);
     std::vector<double> X(NP), dX(9 * (size_t)NP), V(NP), dV(9 * (size_t)NP);
@@ -1313,6 +1320,7 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
     };
     std::vector<float4> met((size_t)E * NP * 3), fn((size_t)E * 6 * NQ);
     std::vector<double> wn(c->has_wall ? (size_t)6 * c->nfmax * NQ * 4 : 0, 0.0);  // curved wall normals
+    std::vector<double> fn64_src((size_t)E * 6 * NQ * 3);                           // face normals in FP64
     std::vector<float> iwj(E);
     for (int e = 0; e < E; e++) {
         const int ec[3] = {e % c->ne[0], (e / c->ne[0]) % c->ne[1], e / (c->ne[0] * c->ne[1])};
@@ -1361,6 +1369,8 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
                             Nv[n] = 0.5 * (Nv[n] + sg * Nn[n]);
                     }
                     fn[(((size_t)e * 3 + d) * 2 + side) * NQ + ln] = make_float4((float)Nv[0], (float)Nv[1], (float)Nv[2], 0.f);
+                    for (int n = 0; n < 3; n++)
+                        fn64_src[((((size_t)e * 3 + d) * 2 + side) * NQ + ln) * 3 + n] = Nv[n];
                     if (!shared && c->bc[2 * d + side] == BGK_BC_DIFFUSE_WALL) {
                         // outward unit normal of the wall face point, at the wall kernel's face element index
                         const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
@@ -1400,6 +1410,22 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
         if (!c->wn64)
             CK(dalloc(c, &c->wn64, wn.size()));
         CK(cudaMemcpy(c->wn64, wn.data(), wn.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (c->prec == BGK_FP64) {  // the all-FP64 form reads the metric, 1/J and the face normals in FP64
+        std::vector<double> ij(c->npts), fn64((size_t)E * 6 * NQ * 3);
+        for (int64_t i = 0; i < c->npts; i++)
+            ij[i] = 1.0 / J[i];
+        for (size_t q = 0; q < fn.size(); q++)
+            for (int n = 0; n < 3; n++)
+                fn64[q * 3 + n] = fn64_src[q * 3 + n];
+        if (!c->ja64) {
+            CK(dalloc(c, &c->ja64, Ja.size()));
+            CK(dalloc(c, &c->ijac64, ij.size()));
+            CK(dalloc(c, &c->fnm64, fn64.size()));
+        }
+        CK(cudaMemcpy(c->ja64, Ja.data(), Ja.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->ijac64, ij.data(), ij.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->fnm64, fn64.data(), fn64.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
     c->geom.assign(x, x + c->npts * 3);
     c->curv_smax = smax;

@@ -149,6 +149,12 @@ struct Stage64Args {
     int vt0, nvt, nslots;
     double an, b, dt, inv_tau;
     const double *itau;    // [n_x] per-point 1/tau (variable collision time), or null: inv_tau
+    // curvilinear hexahedra (null on the affine mesh): the metric rows Ja^d of every node [n_x][3][3]
+    // with 1/J [n_x], the shared face normals [E][3][2][N1^2][3], and the unstructured connectivity
+    // (the FP32 form's tables: int4 [E][6] and the neighbour's first node per face point), or null
+    const double *ja, *ijac, *fnm;
+    const int4 *ftab;
+    const unsigned char *fbase;
 };
 
 // FP64 moments of the stage output over all chunks (warp per point).
@@ -177,7 +183,7 @@ struct WallArgs {
     // (FP64), or null on affine faces; with it both sums run per face point over all velocities, the
     // incoming one with the unit-density wall Maxwellian ghost[6][nslots]
     const double *wn;
-    const float *ghost;
+    const void *ghost;     // float or double, as the storage type of f
 };
 
 // Moment weights of the FP32 stage kernels in the grid-index basis. With W = w / (dv_x dv_y dv_z)

@@ -14,6 +14,86 @@
 
 namespace bgk {
 
+// The exterior trace at face (d, side) of element e for the face point fp of the line whose own first
+// node is i0 (stride along d): the neighbour's interpolant at the shared face (structured grid or the
+// connectivity table), or the face's ghost (times the wall density on a diffuse wall).
+__device__ double exterior64(const Stage64Args &A, int vl, int e, const int ec[3], int d, int side, int fp, int i0,
+                             int lane, int slot)
+{
+    const int N1 = A.N1, NQ = N1 * N1, E = A.mesh.nelem, NP = A.NP;
+    const int stride = d == 0 ? 1 : (d == 1 ? N1 : NQ);
+    int en, g, base, str;
+    bool hi;  // the neighbour's shared face is its +1 end
+    if (A.ftab) {
+        const int4 t = A.ftab[(int64_t)e * 6 + 2 * d + side];
+        en = t.x;
+        g = -1 - t.x;
+        str = t.y;
+        hi = t.z != 0;
+        base = A.fbase[((int64_t)e * 6 + 2 * d + side) * NQ + fp];
+    } else {
+        int nc[3] = {ec[0], ec[1], ec[2]};
+        nc[d] += side ? 1 : -1;
+        g = 2 * d + side;
+        en = -1;
+        if (nc[d] < 0 || nc[d] >= A.mesh.ne[d]) {
+            if (A.mesh.bc[g] == 0)
+                nc[d] = (nc[d] + A.mesh.ne[d]) % A.mesh.ne[d];
+        }
+        if (nc[d] >= 0 && nc[d] < A.mesh.ne[d])
+            en = nc[0] + A.mesh.ne[0] * (nc[1] + A.mesh.ne[1] * nc[2]);
+        str = stride;
+        hi = side == 0;
+        base = i0;
+    }
+    if (en < 0) {
+        double up = A.ghost[(int64_t)g * A.nslots + slot];
+        if (A.mesh.bc[g] == 2)
+            up *= A.rhow[((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + fp];
+        return up;
+    }
+    double t = 0.0;
+    for (int j = 0; j < N1; j++)
+        t += (hi ? A.ops.lp[j] : A.ops.lm[j]) * A.src[fidx(vl, en, base + j * str, lane, E, NP)];
+    return t;
+}
+
+// Curvilinear residual of one degree of freedom (node i of element e, one velocity): per direction the
+// nodal fluxes F_j = (Ja^d(node_j) . xi) f_j along the line, D F, and the FR corrections with the upwind
+// common fluxes of the shared face normals at both ends; -(sum over directions) / J.
+__device__ double curved_residual64(const Stage64Args &A, int vl, int e, int i, int lane, int slot, const int ec[3],
+                                    const int ic[3], const double xi[3])
+{
+    const int N1 = A.N1, NQ = N1 * N1, E = A.mesh.nelem, NP = A.NP;
+    double R = 0.0;
+    for (int d = 0; d < 3; d++) {
+        const int stride = d == 0 ? 1 : (d == 1 ? N1 : NQ);
+        const int i0 = i - ic[d] * stride;
+        const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
+        const int fp = ic[o1] + N1 * ic[o2];
+        double dsum = 0.0, FL = 0.0, FR = 0.0, fL = 0.0, fR = 0.0;
+        for (int j = 0; j < N1; j++) {
+            const int node = i0 + j * stride;
+            const double *ja = A.ja + (((int64_t)e * NP + node) * 3 + d) * 3;
+            const double fj = A.src[fidx(vl, e, node, lane, E, NP)];
+            const double Fj = (ja[0] * xi[0] + ja[1] * xi[1] + ja[2] * xi[2]) * fj;
+            dsum += A.ops.D[ic[d]][j] * Fj;
+            FL += A.ops.lm[j] * Fj;
+            FR += A.ops.lp[j] * Fj;
+            fL += A.ops.lm[j] * fj;
+            fR += A.ops.lp[j] * fj;
+        }
+        const double *nL = A.fnm + ((((int64_t)e * 3 + d) * 2 + 0) * NQ + fp) * 3;
+        const double *nR = A.fnm + ((((int64_t)e * 3 + d) * 2 + 1) * NQ + fp) * 3;
+        const double uL = nL[0] * xi[0] + nL[1] * xi[1] + nL[2] * xi[2];
+        const double uR = nR[0] * xi[0] + nR[1] * xi[1] + nR[2] * xi[2];
+        const double FIL = uL > 0.0 ? uL * exterior64(A, vl, e, ec, d, 0, fp, i0, lane, slot) : uL * fL;
+        const double FIR = uR < 0.0 ? uR * exterior64(A, vl, e, ec, d, 1, fp, i0, lane, slot) : uR * fR;
+        R -= dsum + (FIL - FL) * A.ops.gl[ic[d]] + (FIR - FR) * A.ops.gr[ic[d]];
+    }
+    return R * A.ijac[(int64_t)e * NP + i];
+}
+
 __global__ void __launch_bounds__(256) k64_stage(const Stage64Args A)
 {
     const int NP = A.NP, N1 = A.N1, E = A.mesh.nelem, dim = A.mesh.dim;
@@ -31,6 +111,10 @@ __global__ void __launch_bounds__(256) k64_stage(const Stage64Args A)
         double xi[3];
         for (int d = 0; d < 3; d++)
             xi[d] = A.xi[d * A.nslots + slot];
+        if (A.ja) {  // curvilinear hexahedra: the reference-space flux (Ja^d . xi) f over J
+            R = curved_residual64(A, vl, e, i, lane, slot, ec, ic, xi);
+            goto have_R;
+        }
         for (int d = 0; d < dim; d++) {
             const double a = xi[d];
             const bool left = a >= 0.0;
@@ -69,6 +153,7 @@ __global__ void __launch_bounds__(256) k64_stage(const Stage64Args A)
             const double corr = (left ? A.ops.gl[ic[d]] : A.ops.gr[ic[d]]) * (a * up - a * tr);
             R -= (2.0 / A.h[d]) * (a * dsum + corr);
         }
+    have_R:
         // conservative Maxwellian of this point, BGK relaxation and the Shu-Osher combination
         const double *p = A.par + ((int64_t)e * NP + i) * 5;
         const double r2 = (xi[0] - p[1]) * (xi[0] - p[1]) + (xi[1] - p[2]) * (xi[1] - p[2]) + (xi[2] - p[3]) * (xi[2] - p[3]);
@@ -158,7 +243,8 @@ static int grid_for(int64_t n, int threads) { return (int)std::min<int64_t>((n +
 
 // Zhang-Shu positivity limiter on the FP64 stage output (Sec. 2.1, Eqs. 10-11): thread per
 // (tile, element, lane); the element mean uses the Gauss-Legendre weights of the nodes.
-__global__ void __launch_bounds__(256) k64_limit(double *f, int nvt, int E, int NP, int N1, int dim, Ops64 ops)
+__global__ void __launch_bounds__(256) k64_limit(double *f, int nvt, int E, int NP, int N1, int dim, Ops64 ops,
+                                                 const double *ijac)
 {
     const int64_t n = (int64_t)nvt * E * kWarp;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
@@ -172,6 +258,8 @@ __global__ void __launch_bounds__(256) k64_limit(double *f, int nvt, int E, int 
                 w *= ops.wq[(i / N1) % N1];
             if (dim >= 3)
                 w *= ops.wq[i / (N1 * N1)];
+            if (ijac)  // curvilinear: the physical element's mean (weights W J)
+                w /= ijac[(ve % E) * NP + i];
             const double v = b[(int64_t)i * kWarp];
             mean += w * v;
             wsum += w;
@@ -186,11 +274,12 @@ __global__ void __launch_bounds__(256) k64_limit(double *f, int nvt, int E, int 
     }
 }
 
-cudaError_t launch_limit64(double *f, int nvt, int E, int NP, int N1, int dim, const Ops64 &ops, cudaStream_t s)
+cudaError_t launch_limit64(double *f, int nvt, int E, int NP, int N1, int dim, const Ops64 &ops, const double *ijac,
+                           cudaStream_t s)
 {
     const int64_t n = (int64_t)nvt * E * kWarp;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-    k64_limit<<<blocks, 256, 0, s>>>(f, nvt, E, NP, N1, dim, ops);
+    k64_limit<<<blocks, 256, 0, s>>>(f, nvt, E, NP, N1, dim, ops, ijac);
     return cudaGetLastError();
 }
 

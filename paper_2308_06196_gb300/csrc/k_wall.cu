@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_wall(const WallArgs A, const W *w, cons
                         t += (side ? A.lp[j] : A.lm[j]) * (double)b[(int64_t)j * stride * kWarp];
                     out += (double)w[slot] * un * t;
                 } else if (un < 0.0) {
-                    in -= (double)w[slot] * un * (double)A.ghost[(int64_t)f * A.nslots + slot];
+                    in -= (double)w[slot] * un * (double)static_cast<const T *>(A.ghost)[(int64_t)f * A.nslots + slot];
                 }
             }
         }

@@ -128,9 +128,9 @@ def test_free_stream_and_conservation_on_a_curved_mesh():
 
 
 def test_rejected_setups():
-    from paper_2308_06196_gb300.bgk import BGK_EINVAL, FP64, BgkError, Solver
+    from paper_2308_06196_gb300.bgk import BGK_EINVAL, BgkError, Solver
 
-    x = Solver(3, [2, 2, 2], (0.0,) * 3, (1.0,) * 3, 2, (6,) * 3, (-4.0,) * 3, (4.0,) * 3, 0.1, precision=FP64)
+    x = Solver(2, [2, 2], (0.0,) * 2, (1.0,) * 2, 2, (6,) * 3, (-4.0,) * 3, (4.0,) * 3, 0.1)  # quadrilaterals
     with pytest.raises(BgkError) as err:
         x.set_geometry(x.points())
     assert err.value.code == BGK_EINVAL
@@ -219,3 +219,41 @@ def test_curved_walls_vs_oracle_and_mass():
     assert rel(s.moments(), pr.moments()) < 1e-5
     assert rel(s.get_f(), pr.get_f()) < 1e-5
     assert abs((s.moments()[:, 0] * WJ).sum() - M0) <= 2e-6 * M0
+
+
+@pytest.mark.parametrize("case", ["bump", "sine_tube_limiter", "unstructured", "walls"])
+def test_all_fp64_form_on_curved_meshes(case):
+    # the plain all-FP64 form with the metric terms: against the oracle to 1e-10
+    from paper_2308_06196_gb300.bgk import FP64, Solver
+
+    ne, p, n, L, tau = (3, 2, 2), 2, 6, 4.0, 0.05
+    bc = bcs = None
+    kind, eps, limiter = "bump", 0.15, False
+    if case == "sine_tube_limiter":
+        bc, bcs = tube()
+        kind, eps, limiter, tau = "sine", 0.3, True, 2e-3
+    if case == "walls":
+        bc = [[0, 0], [W.WALL, W.WALL], [0, 0]]
+        bcs = np.zeros((3, 2, 5))
+        bcs[1, 0] = [0, 0.0, 0.0, 0.0, 1.0]
+        bcs[1, 1] = [0, 0.2, 0.0, 0.0, 1.0]
+        kind, eps, tau = "sine", 0.3, 0.02
+    s, pr, X = make(ne, p, n=n, L=L, tau=tau, bc=bc, bcs=bcs, kind=kind, eps=eps, limiter=limiter,
+                    precision=FP64)
+    if case == "unstructured":  # the same mesh relabelled and rotated, both sides on the same tables
+        u = W.unstructured_box(ne, p, seed=3)
+        m = u["node_map"]
+        s = Solver(3, list(ne), (0.0,) * 3, (1.0,) * 3, p, (n,) * 3, (-L,) * 3, (L,) * 3, tau, precision=FP64)
+        pr = orc.Problem(3, list(ne), [0.0] * 3, [1.0] * 3, p, (n,) * 3, (-L,) * 3, (L,) * 3, tau)
+        for x in (s, pr):
+            x.set_connectivity(u["nbr"], u["nface"], u["orient"])
+            x.set_geometry(X[m])
+        X = X[m]
+    prim = W.prim_sod(X, (1.0, 1.0), (0.25, 0.8)) if case == "sine_tube_limiter" else W.smooth_prim(X, 3, seed=8)
+    s.set_state(prim)
+    pr.set_state(prim)
+    dt = pr.dt(0.1)
+    s.step(dt, 4)
+    pr.step(dt, 4)
+    assert rel(s.moments(), pr.moments()) < 1e-10
+    assert rel(s.get_f(), pr.get_f()) < 1e-10
