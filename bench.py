@@ -395,6 +395,30 @@ def bench_curved(steps: int, warmup: int, stream, torch, elements: int = 0) -> d
            "value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "dt": dt, "tiles_per_task": g, **st}
     Q = s.moments()
     s.close()
+    # the plain all-FP64 form on the same curved mesh for the same steps from the same state: its time
+    # and the largest scaled moment difference (full-size parity of the curvilinear kernel)
+    from paper_2308_06196_gb300.bgk import FP64
+
+    n_total = warmup + 2 * steps
+    s64 = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"], precision=FP64)
+    s64.set_stream(stream.cuda_stream)
+    s64.set_geometry(X)
+    s64.set_state(W.prim_field(WORKLOAD, X))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s64.step(dt, 1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s64.step(dt, n_total - 1)
+    e1.record(stream)
+    Q64 = s64.moments()
+    ms64 = e0.elapsed_time(e1) / (n_total - 1)
+    s64.close()
+    rho = Q64[:, 0]
+    th = (2.0 / 3.0) * (Q64[:, 4] / rho - 0.5 * (Q64[:, 1:4] ** 2).sum(1) / rho**2)
+    scale = np.array([rho.max()] + [(rho * np.sqrt(th)).max()] * 3 + [np.abs(Q64[:, 4]).max()])
+    out["fp64"] = {"value": out["dof"] * 3 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                   "steps_compared": n_total,
+                   "moments_max_rel_diff_fp32_split": float((np.abs(Q - Q64).max(axis=0) / scale).max())}
     # the same mesh as an unstructured one (table-driven neighbours): every element's local axes rotated
     # at random, in the grid's own element order (as a locality-ordered mesh) and in a random order (no
     # locality at all); the same steps must give the same moments up to FP32 rounding
