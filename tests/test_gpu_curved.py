@@ -257,3 +257,21 @@ def test_all_fp64_form_on_curved_meshes(case):
     pr.step(dt, 4)
     assert rel(s.moments(), pr.moments()) < 1e-10
     assert rel(s.get_f(), pr.get_f()) < 1e-10
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-10)])
+def test_dirichlet_in_z_on_the_bump_mesh(precision, tol):
+    # the z face pair (the z-lines' ghosts) on a curved mesh
+    bc = [[0, 0], [0, 0], [W.DIRICHLET, W.DIRICHLET]]
+    bcs = np.zeros((3, 2, 5))
+    bcs[2, 0] = [1.0, 0.0, 0.0, 0.2, 1.0]
+    bcs[2, 1] = [0.5, 0.0, 0.1, 0.0, 0.9]
+    s, pr, X = make((2, 2, 3), 2, n=6, tau=0.02, bc=bc, bcs=bcs, precision=precision)
+    prim = W.smooth_prim(X, 3, seed=13, amp=0.2)
+    s.set_state(prim)
+    pr.set_state(prim)
+    dt = pr.dt(0.1)
+    s.step(dt, 4)
+    pr.step(dt, 4)
+    assert rel(s.moments(), pr.moments()) < tol
+    assert rel(s.get_f(), pr.get_f()) < tol

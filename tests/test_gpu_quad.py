@@ -135,3 +135,20 @@ def test_y_independent_state_is_the_line():
     s2.step(dt, 10)
     idx = np.array([np.argmin(np.abs(x1[:, 0] - xx)) for xx in x2[:, 0]])
     assert rel(s2.moments(), s1.moments()[idx]) < 2e-6
+
+
+def test_dirichlet_in_y_vs_oracle():
+    # the other face pair: Dirichlet data at y = 0 and y = 1, periodic in x
+    bc = [[0, 0], [W.DIRICHLET, W.DIRICHLET], [0, 0]]
+    bcs = np.zeros((3, 2, 5))
+    bcs[1, 0] = [1.0, 0.1, 0.0, 0.0, 1.0]
+    bcs[1, 1] = [0.4, 0.0, -0.1, 0.0, 0.9]
+    s, pr = make((3, 5), 2, n=8, L=5.0, tau=0.01, m=3, bc=bc, bcs=bcs)
+    prim = prim2(pr.points(), 11, 3)
+    s.set_state(prim)
+    pr.set_state(prim)
+    dt = pr.dt(0.1)
+    s.step(dt, 4)
+    pr.step(dt, 4)
+    assert rel(s.moments(), pr.moments()) < 1e-5
+    assert rel(s.get_f(), pr.get_f()) < 1e-5
