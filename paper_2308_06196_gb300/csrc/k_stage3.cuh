@@ -221,6 +221,13 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     prefetch(vl0, 0);
     prefetch_fn(vl0);
 
+    // upwind neighbours of a launch that lies in one sign octant: the same for every tile of the task
+    int en_oct[3] = {0, 0, 0};
+    if (OCT < 8)
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            en_oct[d] = upwind_neighbour(A.mesh, ec, d, ((OCT >> d) & 1) != 0);
+
     for (int vl = vl0; vl < vl1; vl++) {
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
@@ -360,9 +367,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
             } else {
             // upwind neighbour values: x-lines and y-lines of layer w, z-lines of slice iy = w
             float vx[N1][N1], vy[N1][N1], vz[N1][N1];
-            const int enx = upwind_neighbour(A.mesh, ec, 0, l0);
-            const int eny = upwind_neighbour(A.mesh, ec, 1, l1);
-            const int enz = upwind_neighbour(A.mesh, ec, 2, l2);
+            const int enx = OCT < 8 ? en_oct[0] : upwind_neighbour(A.mesh, ec, 0, l0);
+            const int eny = OCT < 8 ? en_oct[1] : upwind_neighbour(A.mesh, ec, 1, l1);
+            const int enz = OCT < 8 ? en_oct[2] : upwind_neighbour(A.mesh, ec, 2, l2);
             if (enx >= 0) {
                 const float *nb = A.src + fidx(vl, enx, 0, lane, E, NP);
 #pragma unroll
