@@ -805,10 +805,6 @@ int oracle_set_geometry(orc_ctx *c, const double *x)
 {
     if (!c || !x || c->dim != 3)
         return -1;
-    if (c->cn)  /* walls of an unstructured mesh would need boundary faces of their own */
-        for (int fc = 0; fc < 6; fc++)
-            if (c->bc[fc] == ORC_WALL)
-                return -1;
     const int nf = c->n1 * c->n1;
     c->gx = (double *)realloc(c->gx, sizeof(double) * 3 * c->npts);
     c->Ja = (double *)realloc(c->Ja, sizeof(double) * 9 * c->npts);
@@ -895,13 +891,10 @@ int oracle_set_connectivity(orc_ctx *c, const int *nbr, const int *nface, const 
 {
     if (!c || !nbr || !nface || !orient || c->dim != 3)
         return -1;
-    for (int fc = 0; fc < 6; fc++)
-        if (c->bc[fc] == ORC_WALL)
-            return -1;
     for (int64_t q = 0; q < c->nelem * 6; q++) {
         if (nbr[q] >= c->nelem || nbr[q] < -6 || nface[q] < 0 || nface[q] > 5 || orient[q] < 0 || orient[q] > 7)
             return -1;
-        if (nbr[q] < 0 && c->bc[-1 - nbr[q]] != ORC_DIRICHLET)
+        if (nbr[q] < 0 && c->bc[-1 - nbr[q]] != ORC_DIRICHLET && c->bc[-1 - nbr[q]] != ORC_WALL)
             return -1;
     }
     const size_t n = sizeof(int) * (size_t)(c->nelem * 6);
@@ -982,8 +975,8 @@ static double exterior_value(const orc_ctx *c, const double *f, const int *ec, i
         int64_t nodes[MAXN];
         int sp;
         const int64_t en = table_neighbour(c, elem_index(c, ec), d, side, ic, nodes, &sp);
-        if (en < 0)
-            return c->ghost[(-1 - en) * c->nvel + k];
+        if (en < 0) /* a boundary face: the ghost of its class, times the wall density on a wall */
+            return (c->bc[-1 - en] == ORC_WALL ? rho_w : 1.0) * c->ghost[(-1 - en) * c->nvel + k];
         const double *l = sp ? c->lp : c->lm;
         double t = 0.0;
         for (int j = 0; j < c->n1; j++)
@@ -1043,11 +1036,11 @@ static double wall_density(const orc_ctx *c, const double *f, int64_t e, int d, 
 }
 
 /* Diffuse-wall density at a face point of a curved wall: as wall_density, with the outward unit normal
- * n = +-N / |N| of the face normal N at the point (N points towards +r_d, outward on the high face). */
+ * n = +-N / |N| of the face normal N at the point (N points towards +r_d, outward on the high face);
+ * fc: the wall's boundary data (its structured face). */
 static double wall_density_curved(const orc_ctx *c, const double *f, int64_t e, int d, int side, const int *ic,
-                                  const double *N)
+                                  const double *N, int fc)
 {
-    const int fc = 2 * d + side;
     const double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]), sg = side ? 1.0 : -1.0;
     const double n[3] = {sg * N[0] / nn, sg * N[1] / nn, sg * N[2] / nn};
     double out = 0.0, in = 0.0;
@@ -1092,12 +1085,19 @@ static int residual_curved(const orc_ctx *c, const double *f, double *R)
                 const double *NR = c->fn + (((e * 3 + d) * 2 + 1) * nf + ln) * 3;
                 /* wall densities of the line's two faces, if they are walls */
                 double rw[2] = {0.0, 0.0};
-                if (!c->cn)
-                    for (int side = 0; side < 2; side++) {
+                for (int side = 0; side < 2; side++) {
+                    int wall, g = 2 * d + side;
+                    if (c->cn) { /* a boundary face whose ghost class is a wall */
+                        const int en = c->cn[e * 6 + 2 * d + side];
+                        g = -1 - en;
+                        wall = en < 0 && c->bc[g] == ORC_WALL;
+                    } else {
                         const int edge = side ? (ec[d] == c->ne[d] - 1) : (ec[d] == 0);
-                        if (edge && c->bc[2 * d + side] == ORC_WALL)
-                            rw[side] = wall_density_curved(c, f, e, d, side, ic, side ? NR : NL);
+                        wall = edge && c->bc[g] == ORC_WALL;
                     }
+                    if (wall)
+                        rw[side] = wall_density_curved(c, f, e, d, side, ic, side ? NR : NL, g);
+                }
                 for (int64_t k = 0; k < c->nvel; k++) {
                     const double *v = c->xi + 3 * k;
                     double fl[MAXN], F[MAXN], fL = 0.0, fR = 0.0, FL = 0.0, FR = 0.0;

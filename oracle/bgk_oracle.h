@@ -119,8 +119,8 @@ void oracle_set_limiter(orc_ctx *c, int on);
  * moments; mu_ref <= 0 restores the constant tau given at creation (which must stay > 0). */
 void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega);
 
-/* Curvilinear hexahedra (dim = 3; diffuse walls on the structured element grid only, with the wall
- * density of every face point set by zero net mass flux through the curved face's own normal there):
+/* Curvilinear hexahedra (dim = 3; on a diffuse wall the wall density of every face point is set by
+ * zero net mass flux through the curved face's own normal there):
  * x[n_x][3] are the physical coordinates of every
  * solution node (point order as above); each element is the degree-p interpolant of its nodes. The
  * metric terms Ja^i_n (Kopriva's conservative curl form) and J are computed here, the advection
@@ -129,10 +129,10 @@ void oracle_set_viscosity(orc_ctx *c, double mu_ref, double omega);
  * Returns 0, -2 if some node has J <= 0, -1 on bad input. */
 int oracle_set_geometry(orc_ctx *c, const double *x);
 
-/* Unstructured connectivity (dim = 3, Dirichlet or periodic data only): per element e and local face
+/* Unstructured connectivity (dim = 3): per element e and local face
  * f = 2d + side (d the reference axis, side 0 = the r_d = -1 face), [nelem][6] arrays:
- *   nbr[e][f]    the neighbour element, or -1 - g at a boundary face that takes the Dirichlet ghost of
- *                the structured face g (whose bc must be ORC_DIRICHLET);
+ *   nbr[e][f]    the neighbour element, or -1 - g at a boundary face that takes the boundary data of
+ *                the structured face g (whose bc must be ORC_DIRICHLET or ORC_WALL);
  *   nface[e][f]  the neighbour's local face 2d' + s' that is shared;
  *   orient[e][f] how face points match: with (a, b) the node coordinates of a face point along the two
  *                other axes in increasing order, the neighbour's (a', b') is (b, a) if bit 0 is set,

@@ -219,7 +219,7 @@ def test_unstructured_tables_are_validated():
     with pytest.raises(ValueError):
         pr.set_connectivity(u["nbr"], u["nface"], bad)
     nb = u["nbr"].copy()
-    nb[0, 0] = -1  # a boundary face on a periodic grid: no Dirichlet ghost for it
+    nb[0, 0] = -1  # a boundary face on a periodic grid: no Dirichlet or wall data for it
     with pytest.raises(ValueError):
         pr.set_connectivity(nb, u["nface"], u["orient"])
 
@@ -264,3 +264,25 @@ def test_curved_walls_conserve_mass():
     T1 = (pr.moments() * WJ[:, None]).sum(0)
     assert abs(T1[0] - T0[0]) <= 1e-12 * T0[0]
     assert abs(T1[1] - T0[1]) > 1e-6 * T0[0]  # the moving wall drags the gas
+
+
+def test_unstructured_walls_reproduce_the_structured_channel():
+    # the wavy-walled channel (moving upper wall) relabelled and rotated: the walls are boundary faces of
+    # the tables, in whatever local face they fall; point for point equal to the structured run
+    ne, p = (3, 3, 2), 2
+    bcw = [[0, 0], [orc.WALL, orc.WALL], [0, 0]]
+    u = W.unstructured_box(ne, p, bc=bcw, seed=9)
+    m = u["node_map"]
+    a, b = channel(ne, p, tau=0.02), channel(ne, p, tau=0.02)
+    X = W.curved_nodes(a.points(), (0, 0, 0), L3, ne, 0.3, kind="sine")
+    a.set_geometry(X)
+    b.set_connectivity(u["nbr"], u["nface"], u["orient"])
+    b.set_geometry(X[m])
+    a.set_state(W.smooth_prim(X, 3, seed=6, amp=0.2))
+    f = a.get_f()
+    b.set_f(f[m])
+    Ra, Rb = a.residual(f), b.residual(f[m])
+    assert np.abs(Ra[m] - Rb).max() <= 1e-13 * np.abs(Ra).max()
+    a.step(0.01, 3)
+    b.step(0.01, 3)
+    assert np.abs(a.get_f()[m] - b.get_f()).max() <= 1e-13 * np.abs(a.get_f()).max()
