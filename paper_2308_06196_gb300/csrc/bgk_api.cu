@@ -210,6 +210,14 @@ struct bgk_ctx {
     std::vector<int> cnbr, cface, corient;
     int4 *ftab = nullptr;
     unsigned char *fbase = nullptr;
+    // diffuse walls of an unstructured mesh: the list of its wall faces (element, local face, class, 0),
+    // each face's index in it (or -1) by element and local face, normals and wall densities
+    std::vector<int4> wlist_h;
+    std::vector<int> wall_idx;
+    int4 *wlist = nullptr;
+    double *wnu = nullptr;
+    float *rhowu32 = nullptr;
+    double *rhowu64 = nullptr;
     std::vector<double> geom;  // node coordinates [n_x][3]
     double curv_smax = 0.0;    // max over nodes and velocities of sum_d |Ja^d . xi| / (2 J)
     int *err = nullptr;
@@ -299,6 +307,7 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.iwj = c->iwj;
     A.ftab = c->ftab;
     A.fbase = c->fbase;
+    A.rhowu = c->rhowu32;
     return A;
 }
 
@@ -454,6 +463,12 @@ int enqueue_wall(bgk_ctx *c, const std::vector<const void *> &src, cudaStream_t 
     W.rhow = f64 ? (void *)c->rhow64 : (void *)c->rhow32;
     W.wn = c->wn64;  // curved walls
     W.ghost = f64 ? (const void *)c->ghost64 : (const void *)c->ghost;
+    if (!c->wlist_h.empty()) {  // walls of an unstructured mesh: their own list instead of the grid's faces
+        W.wlist = c->wlist;
+        W.nwall = (int)c->wlist_h.size();
+        W.wnu = c->wnu;
+        W.rhowu = f64 ? (void *)c->rhowu64 : (void *)c->rhowu32;
+    }
     CK(launch_wall(W, f64, f64 ? (const void *)c->w64 : (const void *)c->w32,
                    f64 ? (const void *)c->xi64 : (const void *)c->xi, s));
     return BGK_OK;
@@ -515,6 +530,7 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
             A.fnm = c->fnm64;
             A.ftab = c->ftab;
             A.fbase = c->fbase;
+            A.rhowu = c->rhowu64;
             int64_t real = 0;
             for (int v = ch.vt0 * kWarp; v < (ch.vt0 + ch.nvt) * kWarp; v++)
                 real += c->slotk[v] >= 0;
@@ -627,7 +643,7 @@ void bgk_destroy(bgk_ctx *c)
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
                     c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase, c->wn64,
-                    c->ja64, c->ijac64, c->fnm64};
+                    c->ja64, c->ijac64, c->fnm64, c->wlist, c->wnu, c->rhowu32, c->rhowu64};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -1208,22 +1224,30 @@ int bgk_set_connectivity(bgk_ctx *c, const int *nbr, const int *nface, const int
 {
     if (!c || !nbr || !nface || !orient)
         return BGK_EINVAL;
-    if (c->dim != 3 || c->has_wall)
-        return fail(c, BGK_EINVAL, "unstructured connectivity is built for hexahedra (dim = 3) without diffuse walls");
+    if (c->dim != 3)
+        return fail(c, BGK_EINVAL, "unstructured connectivity is built for hexahedra (dim = 3)");
     const int E = c->E, N1 = c->N1, NQ = N1 * N1;
     for (int64_t q = 0; q < (int64_t)E * 6; q++) {
         if (nbr[q] >= E || nbr[q] < -6 || nface[q] < 0 || nface[q] > 5 || orient[q] < 0 || orient[q] > 7)
             return fail(c, BGK_EINVAL, "connectivity table entry out of range at " + std::to_string(q));
-        if (nbr[q] < 0 && c->bc[-1 - nbr[q]] != BGK_BC_DIRICHLET)
-            return fail(c, BGK_EINVAL, "a boundary face must take the ghost of a Dirichlet face");
+        if (nbr[q] < 0 && c->bc[-1 - nbr[q]] != BGK_BC_DIRICHLET && c->bc[-1 - nbr[q]] != BGK_BC_DIFFUSE_WALL)
+            return fail(c, BGK_EINVAL, "a boundary face must take the data of a Dirichlet or diffuse-wall face");
     }
     std::vector<int4> tab((size_t)E * 6);
     std::vector<unsigned char> base((size_t)E * 6 * NQ);
+    c->wlist_h.clear();
+    c->wall_idx.assign((size_t)E * 6, -1);
     for (int e = 0; e < E; e++)
         for (int f = 0; f < 6; f++) {
             const int q = e * 6 + f, dn = nface[q] / 2, o = orient[q];
             const int stride = dn == 0 ? 1 : (dn == 1 ? N1 : NQ);
-            tab[q] = make_int4(nbr[q], stride, nface[q] % 2, 0);
+            int wi = -1;
+            if (nbr[q] < 0 && c->bc[-1 - nbr[q]] == BGK_BC_DIFFUSE_WALL) {
+                wi = (int)c->wlist_h.size();
+                c->wlist_h.push_back(make_int4(e, f, -1 - nbr[q], 0));
+            }
+            c->wall_idx[q] = wi;
+            tab[q] = make_int4(nbr[q], stride, nface[q] % 2, wi);
             // face point (a, b) of our face -> the neighbour's (a', b') along its other axes (increasing)
             const int s1 = dn == 0 ? N1 : 1, s2 = dn == 2 ? N1 : NQ;
             for (int ln = 0; ln < NQ; ln++) {
@@ -1242,6 +1266,27 @@ int bgk_set_connectivity(bgk_ctx *c, const int *nbr, const int *nface, const int
     }
     CK(cudaMemcpy(c->ftab, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->fbase, base.data(), base.size(), cudaMemcpyHostToDevice));
+    if (!c->wlist_h.empty()) {  // the wall-face list, its normals (set with the geometry) and densities
+        const size_t nw = c->wlist_h.size();
+        if (c->wlist) {
+            cudaFree(c->wlist);
+            cudaFree(c->wnu);
+            cudaFree(c->rhowu32);
+            cudaFree(c->rhowu64);
+            c->wlist = nullptr;
+            c->wnu = nullptr;
+            c->rhowu32 = nullptr;
+            c->rhowu64 = nullptr;
+        }
+        CK(dalloc(c, &c->wlist, nw));
+        CK(dalloc(c, &c->wnu, nw * NQ * 4));
+        CK(cudaMemset(c->wnu, 0, nw * NQ * 4 * sizeof(double)));
+        if (c->prec == BGK_FP64)
+            CK(dalloc(c, &c->rhowu64, nw * NQ));
+        else
+            CK(dalloc(c, &c->rhowu32, nw * NQ));
+        CK(cudaMemcpy(c->wlist, c->wlist_h.data(), nw * sizeof(int4), cudaMemcpyHostToDevice));
+    }
     c->cnbr.assign(nbr, nbr + (size_t)E * 6);
     c->cface.assign(nface, nface + (size_t)E * 6);
     c->corient.assign(orient, orient + (size_t)E * 6);
@@ -1260,9 +1305,8 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
 {
     if (!c || !x)
         return BGK_EINVAL;
-    if (c->dim != 3 || (c->has_wall && !c->cnbr.empty()))
-        return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3), diffuse walls on the "
-                                   "structured element grid only");
+    if (c->dim != 3)
+        return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3)");
     const int NP = c->NP, N1 = c->N1, NQ = N1 * N1, E = c->E;
     std::vector<double> Ja((size_t)c->npts * 9), J(c->npts);
     std::vector<double> X(NP), dX(9 * (size_t)NP), V(NP), dV(9 * (size_t)NP);
@@ -1321,6 +1365,7 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
     std::vector<float4> met((size_t)E * NP * 3), fn((size_t)E * 6 * NQ);
     std::vector<double> wn(c->has_wall ? (size_t)6 * c->nfmax * NQ * 4 : 0, 0.0);  // curved wall normals
     std::vector<double> fn64_src((size_t)E * 6 * NQ * 3);                           // face normals in FP64
+    std::vector<double> wnu(c->wlist_h.size() * NQ * 4, 0.0);                        // unstructured wall normals
     std::vector<float> iwj(E);
     for (int e = 0; e < E; e++) {
         const int ec[3] = {e % c->ne[0], (e / c->ne[0]) % c->ne[1], e / (c->ne[0] * c->ne[1])};
@@ -1371,7 +1416,13 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
                     fn[(((size_t)e * 3 + d) * 2 + side) * NQ + ln] = make_float4((float)Nv[0], (float)Nv[1], (float)Nv[2], 0.f);
                     for (int n = 0; n < 3; n++)
                         fn64_src[((((size_t)e * 3 + d) * 2 + side) * NQ + ln) * 3 + n] = Nv[n];
-                    if (!shared && c->bc[2 * d + side] == BGK_BC_DIFFUSE_WALL) {
+                    const int wi = c->wall_idx.empty() ? -1 : c->wall_idx[(size_t)e * 6 + 2 * d + side];
+                    if (wi >= 0) {  // a wall face of the unstructured mesh: its outward unit normal
+                        const double nn = sqrt(Nv[0] * Nv[0] + Nv[1] * Nv[1] + Nv[2] * Nv[2]), sg = side ? 1.0 : -1.0;
+                        for (int n = 0; n < 3; n++)
+                            wnu[((size_t)wi * NQ + ln) * 4 + n] = sg * Nv[n] / nn;
+                    }
+                    if (c->cnbr.empty() && !shared && c->bc[2 * d + side] == BGK_BC_DIFFUSE_WALL) {
                         // outward unit normal of the wall face point, at the wall kernel's face element index
                         const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
                         const int fe = ec[o1] + c->ne[o1] * ec[o2];
@@ -1406,11 +1457,13 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
     CK(cudaMemcpy(c->met, met.data(), met.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->fnm, fn.data(), fn.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->iwj, iwj.data(), iwj.size() * sizeof(float), cudaMemcpyHostToDevice));
-    if (c->has_wall) {
+    if (c->has_wall && c->cnbr.empty()) {
         if (!c->wn64)
             CK(dalloc(c, &c->wn64, wn.size()));
         CK(cudaMemcpy(c->wn64, wn.data(), wn.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
+    if (!wnu.empty())
+        CK(cudaMemcpy(c->wnu, wnu.data(), wnu.size() * sizeof(double), cudaMemcpyHostToDevice));
     if (c->prec == BGK_FP64) {  // the all-FP64 form reads the metric, 1/J and the face normals in FP64
         std::vector<double> ij(c->npts), fn64((size_t)E * 6 * NQ * 3);
         for (int64_t i = 0; i < c->npts; i++)

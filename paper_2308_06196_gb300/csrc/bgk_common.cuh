@@ -89,7 +89,9 @@ struct StageArgs {
     const float *iwj;    // [E] 1 / sum_i W_i J_i (the limiter's element mean over the physical element)
     // unstructured connectivity (null: the structured element grid), per element and local face 2d+side:
     const int4 *ftab;    // [E][6] (neighbour element or -1 - g for the ghost of face g, node stride of the
-                         // neighbour's normal axis, side of its shared face (1: its +1 end), 0)
+                         // neighbour's normal axis, side of its shared face (1: its +1 end), index of
+                         // the face in the wall list when it is a diffuse wall, else -1)
+    const float *rhowu;  // [nwall][N1^2] wall densities of the unstructured mesh's wall faces, or null
     const unsigned char *fbase;  // [E][6][N1^2] the neighbour's first node on the line through each face point
 };
 
@@ -155,6 +157,7 @@ struct Stage64Args {
     const double *ja, *ijac, *fnm;
     const int4 *ftab;
     const unsigned char *fbase;
+    const double *rhowu;   // [nwall][N1^2] wall densities of the unstructured mesh's wall faces, or null
 };
 
 // FP64 moments of the stage output over all chunks (warp per point).
@@ -184,6 +187,12 @@ struct WallArgs {
     // incoming one with the unit-density wall Maxwellian ghost[6][nslots]
     const double *wn;
     const void *ghost;     // float or double, as the storage type of f
+    // walls of an unstructured mesh: the list of wall faces (element, local face 2d+side, boundary class
+    // g, 0), their outward unit normals [nwall][N1^2][4] and the densities out [nwall][N1^2]
+    const int4 *wlist;
+    int nwall;
+    const double *wnu;
+    void *rhowu;
 };
 
 // Moment weights of the FP32 stage kernels in the grid-index basis. With W = w / (dv_x dv_y dv_z)

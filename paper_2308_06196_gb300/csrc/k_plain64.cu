@@ -22,7 +22,7 @@ __device__ double exterior64(const Stage64Args &A, int vl, int e, const int ec[3
 {
     const int N1 = A.N1, NQ = N1 * N1, E = A.mesh.nelem, NP = A.NP;
     const int stride = d == 0 ? 1 : (d == 1 ? N1 : NQ);
-    int en, g, base, str;
+    int en, g, base, str, wall = -1;
     bool hi;  // the neighbour's shared face is its +1 end
     if (A.ftab) {
         const int4 t = A.ftab[(int64_t)e * 6 + 2 * d + side];
@@ -30,6 +30,7 @@ __device__ double exterior64(const Stage64Args &A, int vl, int e, const int ec[3
         g = -1 - t.x;
         str = t.y;
         hi = t.z != 0;
+        wall = t.w;
         base = A.fbase[((int64_t)e * 6 + 2 * d + side) * NQ + fp];
     } else {
         int nc[3] = {ec[0], ec[1], ec[2]};
@@ -48,8 +49,12 @@ __device__ double exterior64(const Stage64Args &A, int vl, int e, const int ec[3
     }
     if (en < 0) {
         double up = A.ghost[(int64_t)g * A.nslots + slot];
-        if (A.mesh.bc[g] == 2)
+        if (A.ftab) {
+            if (wall >= 0)  // a wall face of the unstructured mesh
+                up *= A.rhowu[(int64_t)wall * NQ + fp];
+        } else if (A.mesh.bc[g] == 2) {
             up *= A.rhow[((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + fp];
+        }
         return up;
     }
     double t = 0.0;

@@ -168,9 +168,11 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     // are nd (tile vl, this lane): the neighbour's interpolant at the shared face, or the face's ghost
     // exterior trace at face (d, side), face point fp, from the connectivity row (CURV = 2)
     auto exterior = [&](int vl, int slot, int d, int side, int fp) -> float {
-        const int4 t = cs.ftab[2 * d + side];  // (neighbour or -1 - ghost face, stride, its +1 end, 0)
-        if (t.x < 0)
-            return __ldg(A.ghost + (int64_t)(-1 - t.x) * A.nslots + slot);
+        const int4 t = cs.ftab[2 * d + side];  // (neighbour or -1 - ghost face, stride, its +1 end, wall)
+        if (t.x < 0) {  // boundary: the ghost of its class, times the wall density of this point on a wall
+            const float gv = __ldg(A.ghost + (int64_t)(-1 - t.x) * A.nslots + slot);
+            return t.w >= 0 ? gv * __ldg(A.rhowu + (int64_t)t.w * NQ + fp) : gv;
+        }
         const int base = cs.fbase[2 * d + side][fp];
         float v[N1];
         const float *nb = A.src + fidx(vl, t.x, 0, lane, E, NP);
