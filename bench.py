@@ -109,6 +109,9 @@ def stage_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300's nominal HBM3e bandwidth, for context beside the measured copy peak
+
+
 def stage_source_sha():
     """Hash of the sources of the hexahedral stage kernel (the counters are void once they change)."""
     h = hashlib.sha256()
@@ -707,6 +710,7 @@ def main():
                    "graph_ms_per_step": graph_ms, "tiles_per_task": tiles_per_task},
         "roofline": {"bound": "hbm", "kernel": "k_stage", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "alg_bytes_per_launch": tm["stage_alg_bytes"], "avg_launch_ms": stage_avg_ms,
                      "stage_share": tm["stage_ms"] / (tm["stage_ms"] + tm["newton_ms"]),
                      "newton_avg_ms": tm["newton_ms"] / max(1, tm["newton_launches"])},
