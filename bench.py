@@ -354,6 +354,53 @@ def bench_planar(steps: int, warmup: int, stream, torch) -> dict:
     return out
 
 
+def bench_channel(steps: int, warmup: int, stream, torch) -> dict:
+    """The rarefied channel at full size (32 x 16 x 4 hexahedra at p = 2, 32^3 velocities, diffuse
+    isothermal walls in y, body force 0.01 in x, Kn = 0.1) in the FP32-split form (general kernel: wall
+    ghosts with their per-point densities, the force source), then the plain all-FP64 form for the same
+    steps from the same state: ms per step, the stage kernel's achieved bandwidth and the two forms'
+    largest scaled moment difference."""
+    from paper_2308_06196_gb300.bgk import FP64, Solver
+
+    c = W.config("channel")
+    k = W.mesh_kwargs(c)
+    out = {"workload": "channel", "mesh": "32x16x4 hex p=2 on [0,2]x[0,1]x[0,0.25], diffuse walls in y",
+           "nv": list(c["nv"]), "tau": c["tau"], "force": list(c["force"])}
+    Q = {}
+    for name, prec in (("fp32_split", 0), ("fp64", FP64)):
+        s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"],
+                   bc=c["bc"], bc_state=c["bc_state"], body_force=c["force"], precision=prec)
+        s.set_stream(stream.cuda_stream)
+        s.set_state(W.prim_field("channel", s.points()))
+        if prec == 0:
+            out["tiles_per_task"] = s.autotune()
+            dt = s.dt(c["cfl"])
+            ms, st = timed_steps(s, dt, steps, warmup, stream, torch)
+            n_total = warmup + 2 * steps
+            out.update({"dof": s.ndof, "dt": dt, "value": s.ndof * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                        **st})
+        else:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.step(dt, 1)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.step(dt, n_total - 1)
+            e1.record(stream)
+            s.synchronize()
+            ms64 = e0.elapsed_time(e1) / (n_total - 1)
+            out["fp64"] = {"value": s.ndof * 3 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64}
+        Q[name] = s.moments()
+        s.close()
+    q32, q64 = Q["fp32_split"], Q["fp64"]
+    rho = q64[:, 0]
+    th = (2.0 / 3.0) * (q64[:, 4] / rho - 0.5 * (q64[:, 1:4] ** 2).sum(-1) / rho**2)
+    scale = np.array([rho.max()] + [(rho * np.sqrt(th)).max()] * 3 + [q64[:, 4].max()])
+    out["steps_compared"] = n_total
+    out["moments_max_rel_diff_fp32_split"] = float((np.abs(q32 - q64).max(axis=0) / scale).max())
+    out["fp64"]["speedup_of_fp32_split"] = out["value"] / out["fp64"]["value"]
+    return out
+
+
 def bench_quad(steps: int, warmup: int, stream, torch, elements: int = 0) -> dict:
     """The planar Taylor-Green vortex on quadrilaterals (dim = 2) in the two-dimensional velocity space,
     FP32-split form: ms per step and the quadrilateral stage kernel's achieved bandwidth."""
@@ -510,6 +557,8 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=3,
                     help="steps of the Taylor-Green variants: limiter, variable tau, ablation (0: skip)")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--channel-steps", type=int, default=3,
+                    help="steps of the full-size channel, FP32-split and all-FP64 (0: skip)")
     ap.add_argument("--curved-steps", type=int, default=3,
                     help="steps of Taylor-Green on curvilinear hexahedra (0: skip)")
     ap.add_argument("--quad-elements", type=int, default=0,
@@ -669,6 +718,9 @@ def main():
     if args.mach5_steps > 0 and world == 1:
         mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch, args.mach5_yz_elements)
     ablation = None if (args.no_ablation or world > 1) else bench_ablation()
+    channel = None
+    if args.channel_steps > 0 and world == 1:
+        channel = bench_channel(args.channel_steps, warmup, stream, torch)
     curved = None
     if args.curved_steps > 0 and world == 1:
         curved = bench_curved(args.curved_steps, warmup, stream, torch, args.elements)
@@ -724,6 +776,7 @@ def main():
         "variants": variants,
         "ablation": ablation,
         "planar": planar,
+        "channel": channel,
         "curved": curved,
         "clocks": clk.summary(),
     }

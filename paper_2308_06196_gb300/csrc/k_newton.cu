@@ -12,7 +12,9 @@
 //      5 x 5 Jacobian well conditioned.
 //        - FP32 Newton iterations (closed-form Jacobian) bring alpha to FP32 accuracy;
 //        - FP64 refinement: the residual is evaluated in FP64 (the 1-D Gaussians by an exact
-//          product recurrence outward from their peak: three FP64 exponentials per axis) and
+//          product recurrence outward from their peak, relative to the peak value: one FP64
+//          exponential per axis, one for the ratio factor of equally spaced axes, and one for
+//          alpha_0 with the three peak values) and
 //          corrected with the FP32 Jacobian, which contracts the error by ~1e-6 per refinement.
 //   3. writes Q, the perturbed state (rho', U', theta') used as the next warm start, and the FP32
 //      exponent g = exp2(a + sum_d (b_d m_d + q_d m_d^2)) in the centred grid index m of the velocity
@@ -243,30 +245,31 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b)
     return {r, __fsub_rn(e, __fsub_rn(r, s))};
 }
 
-// The refinement's 1-D sums S0..S2 as sums64<3>, with the recurrence and the sums in double-float: the
-// three exponentials of the recurrence (peak value, first ratio, ratio factor) in FP64, every node in
-// FP32 pairs. Relative error about 1e-13 (checked against FP64 sums), far below what one refinement
+// The refinement's 1-D sums S0..S2 as sums64<3>, with the recurrence and the sums in double-float, and
+// relative to the peak node: returns ln A(kp) = q(kp) and S_m / A(kp). Every moment and Jacobian entry is
+// a product of one 1-D sum per axis, so the three peak values join exp(alpha_0) in one exponential. The
+// ratio factor E2 = exp(-beta h^2) comes from the caller (one exponential for all axes of equal
+// spacing), the first ratio exp(q1 + q2 (2 kp + 1)) is the one FP64 exponential per axis; every node is
+// in FP32 pairs. Relative error about 1e-13 (checked against FP64 sums), far below what one refinement
 // with the FP32 Jacobian needs.
-__device__ __forceinline__ void sums_df(double ad, double beta, double c0, double h, int n, double dv, double (&S)[3])
+__device__ __forceinline__ double sums_df(double ad, double beta, double c0, double h, int n, double dv, double E2,
+                                          double (&S)[3])
 {
     if (n == 1) {  // one node of unit weight (no u_z, m = 2)
-        const double t = exp(c0 * fma(-0.5 * beta, c0, ad));
-        S[0] = t;
-        S[1] = t * c0;
-        S[2] = S[1] * c0;
-        return;
+        S[0] = 1.0;
+        S[1] = c0;
+        S[2] = c0 * c0;
+        return c0 * fma(-0.5 * beta, c0, ad);
     }
     const double q1 = (ad - beta * c0) * h, q2 = -0.5 * beta * h * h;
     int kp = (int)rintf((float)(-q1) / (float)(2.0 * q2));
     kp = kp < 0 ? 0 : (kp > n - 1 ? n - 1 : kp);
     const double cp = fma((double)kp, h, c0);
-    const double Ap = exp(cp * fma(-0.5 * beta, cp, ad));
-    const double E2 = exp(2.0 * q2);
     const double rp = exp(q1 + q2 * (2.0 * kp + 1.0));
     const dfl e2 = df_from(E2), hd = df_from(h), hm = df_from(-h);
     dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
-    // upward from the peak (inclusive); unit weights, the trapezoid ends are corrected below
-    dfl Ak = df_from(Ap), r = df_from(rp), c = df_from(cp), Aend = Ak, cend = c;
+    // upward from the peak (inclusive, value 1); unit weights, the trapezoid ends are corrected below
+    dfl Ak = {1.f, 0.f}, r = df_from(rp), c = df_from(cp), Aend = Ak, cend = c;
     for (int k = kp; k < n; k++) {
         const dfl cA = df_mul(c, Ak);
         s0 = df_add(s0, Ak);
@@ -279,7 +282,7 @@ __device__ __forceinline__ void sums_df(double ad, double beta, double c0, doubl
         c = df_add(c, hd);
     }
     // downward from the peak (exclusive): A(k-1) = A(k) d(k), d(k) = E2 / r(k), d(k-1) = d(k) E2
-    Ak = df_from(Ap);
+    Ak = {1.f, 0.f};
     c = df_from(cp);
     dfl dk = df_from(E2 / rp), A0 = Ak, c0e = c;
     for (int k = kp - 1; k >= 0; k--) {
@@ -297,6 +300,7 @@ __device__ __forceinline__ void sums_df(double ad, double beta, double c0, doubl
     S[0] = (df_val(s0) - 0.5 * (a0 + ae)) * dv;
     S[1] = (df_val(s1) - 0.5 * (x0 * a0 + xe * ae)) * dv;
     S[2] = (df_val(s2) - 0.5 * (x0 * x0 * a0 + xe * xe * ae)) * dv;
+    return cp * fma(-0.5 * beta, cp, ad);
 }
 
 __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
@@ -328,10 +332,10 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     for (int c = 0; c < 5; c++)
         A.Q[(int64_t)pt * 5 + c] = Q[c];
 
-    const double rho = Q[0];
-    const double u[3] = {Q[1] / rho, Q[2] / rho, Q[3] / rho};
+    const double rho = Q[0], irho = 1.0 / rho;
+    const double u[3] = {Q[1] * irho, Q[2] * irho, Q[3] * irho};
     const double hm = 0.5 * A.vdim;  // E = rho |U|^2 / 2 + (m / 2) rho theta
-    const double thc = (Q[4] / rho - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) / hm;
+    const double thc = (Q[4] * irho - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) * (A.vdim == 2 ? 1.0 : 2.0 / 3.0);
     float *par = A.param + (int64_t)pt * kParamStride;
     if (!(rho > 0.0) || !(thc > 0.0) || !isfinite(rho) || !isfinite(thc)) {
         atomicOr(A.err, kErrDomain);
@@ -448,18 +452,21 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
         // FP64 resolution (it64 minimum, 4 maximum)
         const int it64min = warm ? A.it64 : max(A.it64, 2);
         for (int it = 0; it < 4; it++) {
-            double S[3][5];
+            double S[3][5], E2[3], lnp = 0.0;
+    #pragma unroll
+            for (int d = 0; d < 3; d++)
+                E2[d] = d > 0 && h[d] == h[d - 1] ? E2[d - 1] : exp(al[4] * h[d] * h[d]);
     #pragma unroll
             for (int d = 0; d < 3; d++) {
                 double s3[3];
-                sums_df(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], s3);
+                lnp += sums_df(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], E2[d], s3);
                 S[d][0] = s3[0];
                 S[d][1] = s3[1];
                 S[d][2] = s3[2];
                 S[d][3] = S[d][4] = 0.0;
             }
             double M[5];
-            assemble<double>(S, exp(al[0]), M, nullptr);
+            assemble<double>(S, exp(al[0] + lnp), M, nullptr);  // the peaks' factors with alpha_0
             if (A.vdim == 2)
                 M[3] = Qt[3];
             // the FP64 residual, solved with the FP32 Jacobian in FP32: the correction only needs FP32
@@ -496,11 +503,12 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
 
     // 3. outputs: perturbed state and the stage kernel's exponent in the raw velocity
     const double a[3] = {al[1], al[2], al[3]};
-    const double thp = th0 / beta;  // s^2 / beta
+    const double ib = 1.0 / beta;
+    const double thp = th0 * ib;  // s^2 / beta
     double Up[3];
     for (int d = 0; d < 3; d++)
-        Up[d] = V[d] + s * a[d] / beta;
-    const double lnC = al[0] + 0.5 * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / beta;  // ln(rho' (2 pi theta')^-m/2)
+        Up[d] = V[d] + s * a[d] * ib;
+    const double lnC = al[0] + 0.5 * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * ib;  // ln(rho' (2 pi theta')^-m/2)
     double *pp = A.prim + (int64_t)pt * 5;
     pp[0] = A.lnc_form ? lnC : exp(lnC) * pow(2.0 * 3.14159265358979323846 * thp, hm);
     pp[1] = Up[0];
@@ -517,7 +525,7 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     // roundings of A and q would scale every g of the point alike (a moment error near 1e-7 per
     // solve, which the relaxation accumulates); split, they are below 1e-8.
     const double L2E = 1.4426950408889634;
-    const double it2 = 1.0 / thp;
+    const double it2 = beta * is * is;  // 1 / theta' = beta / s^2
     double e2 = 0.0;
     for (int d = 0; d < 3; d++) {
         const double sd = 0.5 * A.dv[d];
