@@ -458,10 +458,22 @@ int enqueue_wall(bgk_ctx *c, const std::vector<const void *> &src, cudaStream_t 
     for (int j = 0; j < c->N1; j++) {
         W.lm[j] = c->ops64.lm[j];
         W.lp[j] = c->ops64.lp[j];
+        W.lmf[j] = (float)c->ops64.lm[j];
+        W.lpf[j] = (float)c->ops64.lp[j];
     }
     const bool f64 = c->prec == BGK_FP64;
     W.rhow = f64 ? (void *)c->rhow64 : (void *)c->rhow32;
     W.wn = c->wn64;  // curved walls
+    W.nwf = 0;
+    W.wfstart[0] = 0;
+    for (int f = 0; f < 6; f++) {
+        if (c->inv_in[f] == 0.0 && !(c->wn64 && c->mesh.bc[f] == BGK_BC_DIFFUSE_WALL))
+            continue;
+        const int d = f >> 1, o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
+        W.wf[W.nwf] = f;
+        W.wfstart[W.nwf + 1] = W.wfstart[W.nwf] + c->mesh.ne[o1] * c->mesh.ne[o2] * c->N1 * c->N1;
+        W.nwf++;
+    }
     W.ghost = f64 ? (const void *)c->ghost64 : (const void *)c->ghost;
     if (!c->wlist_h.empty()) {  // walls of an unstructured mesh: their own list instead of the grid's faces
         W.wlist = c->wlist;

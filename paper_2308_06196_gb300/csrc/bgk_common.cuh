@@ -181,6 +181,10 @@ struct WallArgs {
     Mesh mesh;
     int N1, NP, nfmax;
     double lm[kMaxN1], lp[kMaxN1];
+    float lmf[kMaxN1], lpf[kMaxN1];  // the same in FP32 (the FP32-split form's traces)
+    // the structured mesh's wall faces: nwf faces wf[q], whose face points are CTAs wfstart[q] ..
+    // wfstart[q + 1] - 1 of the launch
+    int nwf, wf[6], wfstart[7];
     void *rhow;            // out: float or double [6][nfmax][N1^2]
     // curved walls (FP32-split form): the outward unit normal of every wall face point, [6][nfmax][N1^2][4]
     // (FP64), or null on affine faces; with it both sums run per face point over all velocities, the

@@ -5,28 +5,72 @@
 // through that point vanishes: rho_w = sum_{xi . n_out > 0} w |xi_n| f_trace / sum_{xi . n_out < 0}
 // w |xi_n| M_w, where f_trace is the element's own interpolant at the face (the value the FR scheme
 // lets out) and M_w the unit-density Maxwellian of the wall (the denominator is fixed per face and
-// precomputed on the host). One warp per face point; lanes run over the outgoing velocities of the
-// stage source, accumulating in FP64. T is the storage type of f (float or double); the quadrature
-// weights and velocities are those the moments use (FP32 tables for the FP32 form). On curved walls
-// the normal changes from point to point: both sums are then taken per face point, over all
-// velocities, with the outward unit normal of the point.
+// precomputed on the host). One CTA per face point: its warps take every fourth velocity tile, lanes
+// run over the tile's outgoing velocities, and the warps' sums are added in a fixed order. T is the
+// storage type of f (float or double); the quadrature weights and velocities are those the moments use
+// (FP32 tables for the FP32 form). The all-FP64 form sums in FP64; the FP32-split form forms the terms
+// in FP32 and sums them in double-float. On curved walls the normal changes from point to point: both
+// sums are then taken per face point, over all velocities, with the outward unit normal of the point
+// (in FP64). The walls of an unstructured mesh have a kernel of their own, one warp per face point.
 #include "bgk_common.cuh"
 
 namespace bgk {
 
-template <typename T, typename W>
-__global__ void __launch_bounds__(256) k_wall(const WallArgs A, const W *w, const W *xi)
+// Sum of one face point's flux terms. The all-FP64 form accumulates in FP64; the FP32-split form forms
+// each term in FP32 (the precision of the stage kernel's own outgoing flux) and accumulates it in
+// double-float, the running FP32 sum and its exact two-sum errors, about 1e-12 relative over any number
+// of terms at FP32 throughput.
+template <typename T>
+struct WallAcc {
+    double s = 0.0;
+    __device__ void add(double x) { s += x; }
+    __device__ double val() const { return s; }
+};
+template <>
+struct WallAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ void add(float x)
+    {
+        const float t = __fadd_rn(hi, x), bb = __fsub_rn(t, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+        hi = t;
+    }
+    __device__ double val() const { return (double)hi + (double)lo; }
+};
+
+constexpr int kWallWarps = 4;  // warps per face point: tiles vl = w, w + 4, ... of every chunk
+
+// a double from every warp of the CTA, added in warp order (deterministic); the result in thread 0
+__device__ __forceinline__ double wall_cta_sum(double v, double *red)
 {
-    const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kWallWarps; q++)
+            s += red[q];
+    __syncthreads();
+    return s;
+}
+
+// One CTA of kWallWarps warps per face point of the structured mesh (a whole CTA returns together).
+template <typename T, typename W>
+__global__ void __launch_bounds__(kWallWarps * 32) k_wall(const WallArgs A, const W *w, const W *xi)
+{
+    __shared__ double red[kWallWarps];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int N1 = A.N1, NQ = N1 * N1, NP = A.NP, E = A.mesh.nelem;
-    const int f = gw / (A.nfmax * NQ);
-    if (f >= 6 || (A.inv_in[f] == 0.0 && !(A.wn && A.mesh.bc[f] == 2)))
-        return;  // whole warp
-    const int fe = (gw / NQ) % A.nfmax, fnode = gw % NQ;
+    int q = 0;  // the wall face of this CTA's face point
+    while (q + 1 < A.nwf && (int)blockIdx.x >= A.wfstart[q + 1])
+        q++;
+    const int f = A.wf[q], gp = (int)blockIdx.x - A.wfstart[q];
+    const int fe = gp / NQ, fnode = gp % NQ;
     const int d = f >> 1, side = f & 1;
     const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;  // the two in-face directions
-    if (fe >= A.mesh.ne[o1] * A.mesh.ne[o2])
-        return;
     int ec[3];
     ec[d] = side ? A.mesh.ne[d] - 1 : 0;
     ec[o1] = fe % A.mesh.ne[o1];
@@ -38,12 +82,12 @@ __global__ void __launch_bounds__(256) k_wall(const WallArgs A, const W *w, cons
     nc[d] = 0;
     const int n0 = nc[0] + N1 * (nc[1] + N1 * nc[2]);
     const int stride = d == 0 ? 1 : (d == 1 ? N1 : NQ);
-    if (A.wn) {  // curved wall: per-point normal, both sums here
+    if (A.wn) {  // curved wall: per-point normal, both sums here (FP64)
         const double *n = A.wn + (((int64_t)f * A.nfmax + fe) * NQ + fnode) * 4;
         double out = 0.0, in = 0.0;
         for (int c = 0; c < A.nchunks; c++) {
             const T *src = static_cast<const T *>(A.src[c]);
-            for (int vl = 0; vl < A.nvt[c]; vl++) {
+            for (int vl = wq; vl < A.nvt[c]; vl += kWallWarps) {
                 const int slot = (A.vt0[c] + vl) * kWarp + lane;
                 const double un = n[0] * (double)xi[slot] + n[1] * (double)xi[(int64_t)A.nslots + slot] +
                                   n[2] * (double)xi[2 * (int64_t)A.nslots + slot];
@@ -58,35 +102,40 @@ __global__ void __launch_bounds__(256) k_wall(const WallArgs A, const W *w, cons
                 }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            out += __shfl_xor_sync(0xffffffffu, out, o);
-            in += __shfl_xor_sync(0xffffffffu, in, o);
-        }
-        if (lane == 0)
+        out = wall_cta_sum(out, red);
+        in = wall_cta_sum(in, red);
+        if (threadIdx.x == 0)
             static_cast<T *>(A.rhow)[((int64_t)f * A.nfmax + fe) * NQ + fnode] = (T)(out / in);
         return;
     }
-    double sum = 0.0;
+    T l[kMaxN1];
+#pragma unroll
+    for (int j = 0; j < kMaxN1; j++)
+        l[j] = sizeof(T) == 4 ? (T)(side ? A.lpf[j] : A.lmf[j]) : (T)(side ? A.lp[j] : A.lm[j]);
+    WallAcc<T> acc;
     for (int c = 0; c < A.nchunks; c++) {
         const int oc = A.oct[c];
         if (oc < 8 && ((oc >> d) & 1) != side)
             continue;  // no outgoing velocity in this chunk
         const T *src = static_cast<const T *>(A.src[c]);
-        for (int vl = 0; vl < A.nvt[c]; vl++) {
+        // branch-free body (the term of a velocity that does not leave is selected away), so that the
+        // unrolled iterations' loads are in flight together
+#pragma unroll 4
+        for (int vl = wq; vl < A.nvt[c]; vl += kWallWarps) {
             const int slot = (A.vt0[c] + vl) * kWarp + lane;
-            const double xn = (double)xi[(int64_t)d * A.nslots + slot];
-            if (side ? !(xn > 0.0) : !(xn < 0.0))
-                continue;
+            const T xn = (T)xi[(int64_t)d * A.nslots + slot];
             const T *b = src + fidx(vl, e, n0, lane, E, NP);
-            double t = 0.0;
-            for (int j = 0; j < N1; j++)
-                t += (side ? A.lp[j] : A.lm[j]) * (double)b[(int64_t)j * stride * kWarp];
-            sum += (double)w[slot] * fabs(xn) * t;
+            T t = T(0);  // the element's own trace, in the storage precision
+#pragma unroll
+            for (int j = 0; j < kMaxN1; j++)
+                if (j < N1)
+                    t += l[j] * b[(int64_t)j * stride * kWarp];
+            const bool leaves = side ? xn > T(0) : xn < T(0);
+            acc.add(leaves ? (T)w[slot] * (xn < T(0) ? -xn : xn) * t : T(0));
         }
     }
-    for (int o = 16; o > 0; o >>= 1)
-        sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0)
+    const double sum = wall_cta_sum(acc.val(), red);
+    if (threadIdx.x == 0)
         static_cast<T *>(A.rhow)[((int64_t)f * A.nfmax + fe) * NQ + fnode] = (T)(sum * A.inv_in[f]);
 }
 
@@ -148,12 +197,15 @@ cudaError_t launch_wall(const WallArgs &A, bool fp64, const void *w, const void 
             k_wall_list<float, float><<<blocks, 256, 0, s>>>(A, static_cast<const float *>(w), static_cast<const float *>(xi));
         return cudaGetLastError();
     }
-    const int64_t warps = 6ll * A.nfmax * A.N1 * A.N1;
-    const int blocks = (int)((warps * kWarp + 255) / 256);
+    const int blocks = A.wfstart[A.nwf];  // one CTA per wall face point
+    if (blocks == 0)
+        return cudaSuccess;
     if (fp64)
-        k_wall<double, double><<<blocks, 256, 0, s>>>(A, static_cast<const double *>(w), static_cast<const double *>(xi));
+        k_wall<double, double>
+            <<<blocks, kWallWarps * 32, 0, s>>>(A, static_cast<const double *>(w), static_cast<const double *>(xi));
     else
-        k_wall<float, float><<<blocks, 256, 0, s>>>(A, static_cast<const float *>(w), static_cast<const float *>(xi));
+        k_wall<float, float>
+            <<<blocks, kWallWarps * 32, 0, s>>>(A, static_cast<const float *>(w), static_cast<const float *>(xi));
     return cudaGetLastError();
 }
 
