@@ -4,6 +4,10 @@
 #include "stage_common.cuh"
 
 // Resident CTAs per SM the register allocation is sized for (p = 3 lean and general / p = 2 / p = 1).
+// The register file is split over the SM's four schedulers, so a CTA of 3 warps (p = 2) at 96
+// registers packs only 6 per SM (18 warps); at 80 registers 8 fit (24 warps), and the p = 2 stage runs
+// 8-11 % faster despite a few bytes of spills in the general form. The p = 3 general form at 5 CTAs
+// (96 registers) spills about 100 bytes and runs 13-17 % slower than at 4 (128 registers).
 #ifndef BGK_STAGE3_MINCTAS_P3
 #define BGK_STAGE3_MINCTAS_P3 5
 #endif
@@ -11,7 +15,7 @@
 #define BGK_STAGE3_MINCTAS_P3_GEN 4
 #endif
 #ifndef BGK_STAGE3_MINCTAS_P2
-#define BGK_STAGE3_MINCTAS_P2 6
+#define BGK_STAGE3_MINCTAS_P2 8
 #endif
 
 namespace bgk {
