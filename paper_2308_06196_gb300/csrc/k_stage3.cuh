@@ -189,16 +189,15 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     auto wall_rho = [&](int g, int d, int fp) -> float {
         return A.mesh.bc[g] == 2 ? __ldg(A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + fp) : 1.f;
     };
-    // the structured grid's neighbour en: its values on the line through our nodes nd (CURV = 1)
-    auto nbline = [&](int vl, int en, const int (&nd)[N1]) {
-        struct Line {
-            float v[N1];
-        } r;
-        const float *nb = A.src + fidx(vl, en, 0, lane, E, NP);
+    // the structured grid's neighbour en: the upwind trace of its line through our nodes n0 + j st
+    // (CURV = 1); left: the neighbour lies on the low side (its +1 end)
+    auto nbtrace = [&](int vl, int en, int n0, int st, bool left) -> float {
+        float v[N1];
+        const float *nb = A.src + fidx(vl, en, n0, lane, E, NP);
 #pragma unroll
         for (int j = 0; j < N1; j++)
-            r.v[j] = __ldg(nb + nd[j] * kWarp);
-        return r;
+            v[j] = __ldg(nb + j * st * kWarp);
+        return left ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
     };
 
     // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
@@ -289,11 +288,12 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
 #pragma unroll
                     for (int ln = 0; ln < N1; ln++) {
                         float fl[N1], u[N1], sv[N1];
-                        int nd[N1];
+                        int nd[N1], qi[N1];  // element node and in-layer node (compile-time) of the line
 #pragma unroll
                         for (int j = 0; j < N1; j++) {
-                            nd[j] = (d == 0 ? j + N1 * ln : ln + N1 * j) + NQ * w;
-                            fl[j] = f[nd[j] - NQ * w];
+                            qi[j] = d == 0 ? j + N1 * ln : ln + N1 * j;
+                            nd[j] = qi[j] + NQ * w;
+                            fl[j] = f[qi[j]];
                             const float4 m = cs.met[nd[j]][d];
                             u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
                         }
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                             if (CURV == 2)
                                 tL = exterior(vl, slot, d, 0, ln + N1 * w);
                             else if (eL >= 0)
-                                tL = trace_line<N1, true>(nbline(vl, eL, nd).v, A.ops);
+                                tL = nbtrace(vl, eL, nd[0], nd[1] - nd[0], true);
                             else
                                 tL = __ldg(A.ghost + (2 * d) * A.nslots + slot) * wall_rho(2 * d, d, ln + N1 * w);
                         }
@@ -314,14 +314,14 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                             if (CURV == 2)
                                 tR = exterior(vl, slot, d, 1, ln + N1 * w);
                             else if (eR >= 0)
-                                tR = trace_line<N1, false>(nbline(vl, eR, nd).v, A.ops);
+                                tR = nbtrace(vl, eR, nd[0], nd[1] - nd[0], false);
                             else
                                 tR = __ldg(A.ghost + (2 * d + 1) * A.nslots + slot) * wall_rho(2 * d + 1, d, ln + N1 * w);
                         }
                         curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
                         for (int j = 0; j < N1; j++)
-                            acc[nd[j] - NQ * w] = fmaf(-bdt * cs.met[nd[j]][0].w, sv[j], acc[nd[j] - NQ * w]);
+                            acc[qi[j]] = fmaf(-bdt * cs.met[nd[j]][0].w, sv[j], acc[qi[j]]);
                     }
                 }
                 __syncthreads();  // B1: the element tile is complete
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         if (CURV == 2)
                             tL = exterior(vl, slot, 2, 0, ln + N1 * w);
                         else if (eL >= 0)
-                            tL = trace_line<N1, true>(nbline(vl, eL, nd).v, A.ops);
+                            tL = nbtrace(vl, eL, nd[0], NQ, true);
                         else
                             tL = __ldg(A.ghost + 4 * A.nslots + slot) * wall_rho(4, 2, ln + N1 * w);
                     }
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         if (CURV == 2)
                             tR = exterior(vl, slot, 2, 1, ln + N1 * w);
                         else if (eR >= 0)
-                            tR = trace_line<N1, false>(nbline(vl, eR, nd).v, A.ops);
+                            tR = nbtrace(vl, eR, nd[0], NQ, false);
                         else
                             tR = __ldg(A.ghost + 5 * A.nslots + slot) * wall_rho(5, 2, ln + N1 * w);
                     }
