@@ -139,6 +139,7 @@ void build_ops(int p, Ops &op, Ops64 &o64, double *xg_out)
         for (int j = 0; j < n; j++) {
             op.DL[i][j] = (float)(D[i][j] - gl[i] * lm[j]);
             op.DR[i][j] = (float)(D[i][j] - gr[i] * lp[j]);
+            op.DM[i][j] = (float)(D[i][j] - gl[i] * lm[j] - gr[i] * lp[j]);
         }
         op.gl[i] = (float)gl[i];
         op.gr[i] = (float)gr[i];

@@ -30,6 +30,7 @@ constexpr int kErrNewton = 2;
 struct Ops {
     float DL[kMaxN1][kMaxN1];
     float DR[kMaxN1][kMaxN1];
+    float DM[kMaxN1][kMaxN1];  // D - gl (x) lm - gr (x) lp: both interior traces folded in (curvilinear)
     float gl[kMaxN1], gr[kMaxN1];
     float lm[kMaxN1], lp[kMaxN1];
     float wq[kMaxN1];    // Gauss-Legendre weights / 2 (they sum to 1): the element mean of the limiter

@@ -62,30 +62,29 @@ constexpr int stage3_smem_bytes()
 
 // Curvilinear line of direction d (Sec. 2.1, Eqs. 7-9 on the mapped element): with the nodal fluxes
 // F_j = u_j f_j (u_j = Ja^d . xi at node j), s_i = (D F)_i + gl'_i (F^I_L - F_L) + gr'_i (F^I_R - F_R)
-// = sum_j DL_ij F_j + gl'_i F^I_L + gr'_i (F^I_R - sum_j lp_j F_j), where F_L, F_R are the interpolated
-// traces of F and F^I the upwind common fluxes of the face normals' u_L, u_R (Eq. 9): the exterior trace
-// tL / tR where the face flow enters the element, the element's own trace of f where it leaves.
+// = sum_j DM_ij F_j + gl'_i F^I_L + gr'_i F^I_R, where F_L, F_R are the interpolated traces of F (folded
+// into DM = D - gl' (x) lm - gr' (x) lp) and F^I the upwind common fluxes of the face normals' u_L, u_R
+// (Eq. 9): the exterior trace tL / tR where the face flow enters the element, the element's own trace
+// of f where it leaves.
 template <int N1>
 __device__ __forceinline__ void curv_line(float (&sv)[N1], const float (&fl)[N1], const float (&u)[N1], float uL,
                                           float uR, float tL, float tR, const Ops &op)
 {
-    float F[N1], oL = 0.f, oR = 0.f, FR = 0.f;
+    float F[N1], oL = 0.f, oR = 0.f;
 #pragma unroll
     for (int j = 0; j < N1; j++) {
         F[j] = u[j] * fl[j];
         oL = fmaf(op.lm[j], fl[j], oL);
         oR = fmaf(op.lp[j], fl[j], oR);
-        FR = fmaf(op.lp[j], F[j], FR);
     }
     const float FIL = uL * (uL > 0.f ? tL : oL);
     const float FIR = uR * (uR < 0.f ? tR : oR);
-    const float cR = FIR - FR;
 #pragma unroll
     for (int i = 0; i < N1; i++) {
-        float a = fmaf(op.gl[i], FIL, op.gr[i] * cR);
+        float a = fmaf(op.gl[i], FIL, op.gr[i] * FIR);
 #pragma unroll
         for (int j = 0; j < N1; j++)
-            a = fmaf(op.DL[i][j], F[j], a);
+            a = fmaf(op.DM[i][j], F[j], a);
         sv[i] = a;
     }
 }
