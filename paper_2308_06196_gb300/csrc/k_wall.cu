@@ -11,7 +11,7 @@
 // (FP32 tables for the FP32 form). The all-FP64 form sums in FP64; the FP32-split form forms the terms
 // in FP32 and sums them in double-float. On curved walls the normal changes from point to point: both
 // sums are then taken per face point, over all velocities, with the outward unit normal of the point
-// (in FP64). The walls of an unstructured mesh have a kernel of their own, one warp per face point.
+// (in FP64). The walls of an unstructured mesh have a kernel of their own over their list.
 #include "bgk_common.cuh"
 
 namespace bgk {
@@ -57,6 +57,39 @@ __device__ __forceinline__ double wall_cta_sum(double v, double *red)
     return s;
 }
 
+// Both sums of a face point with its own outward unit normal n (curved walls and the walls of an
+// unstructured mesh), in FP64: the outgoing flux of the element's trace along its normal line (nodes
+// n0 + j stride of element e, its +1 end when side = 1) and the incoming flux of the unit-density wall
+// Maxwellian ghost[g]. This warp takes tiles wq, wq + kWallWarps, ...; returns rho_w in thread 0.
+template <typename T, typename W>
+__device__ double curved_wall_density(const WallArgs &A, const W *w, const W *xi, const double *n, int e, int side,
+                                      int n0, int stride, int g, double *red)
+{
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int N1 = A.N1, NP = A.NP, E = A.mesh.nelem;
+    double out = 0.0, in = 0.0;
+    for (int c = 0; c < A.nchunks; c++) {
+        const T *src = static_cast<const T *>(A.src[c]);
+        for (int vl = wq; vl < A.nvt[c]; vl += kWallWarps) {
+            const int slot = (A.vt0[c] + vl) * kWarp + lane;
+            const double un = n[0] * (double)xi[slot] + n[1] * (double)xi[(int64_t)A.nslots + slot] +
+                              n[2] * (double)xi[2 * (int64_t)A.nslots + slot];
+            if (un > 0.0) {
+                const T *b = src + fidx(vl, e, n0, lane, E, NP);
+                double t = 0.0;
+                for (int j = 0; j < N1; j++)
+                    t += (side ? A.lp[j] : A.lm[j]) * (double)b[(int64_t)j * stride * kWarp];
+                out += (double)w[slot] * un * t;
+            } else if (un < 0.0) {
+                in -= (double)w[slot] * un * (double)static_cast<const T *>(A.ghost)[(int64_t)g * A.nslots + slot];
+            }
+        }
+    }
+    out = wall_cta_sum(out, red);
+    in = wall_cta_sum(in, red);
+    return out / in;
+}
+
 // One CTA of kWallWarps warps per face point of the structured mesh (a whole CTA returns together).
 template <typename T, typename W>
 __global__ void __launch_bounds__(kWallWarps * 32) k_wall(const WallArgs A, const W *w, const W *xi)
@@ -84,28 +117,9 @@ __global__ void __launch_bounds__(kWallWarps * 32) k_wall(const WallArgs A, cons
     const int stride = d == 0 ? 1 : (d == 1 ? N1 : NQ);
     if (A.wn) {  // curved wall: per-point normal, both sums here (FP64)
         const double *n = A.wn + (((int64_t)f * A.nfmax + fe) * NQ + fnode) * 4;
-        double out = 0.0, in = 0.0;
-        for (int c = 0; c < A.nchunks; c++) {
-            const T *src = static_cast<const T *>(A.src[c]);
-            for (int vl = wq; vl < A.nvt[c]; vl += kWallWarps) {
-                const int slot = (A.vt0[c] + vl) * kWarp + lane;
-                const double un = n[0] * (double)xi[slot] + n[1] * (double)xi[(int64_t)A.nslots + slot] +
-                                  n[2] * (double)xi[2 * (int64_t)A.nslots + slot];
-                if (un > 0.0) {
-                    const T *b = src + fidx(vl, e, n0, lane, E, NP);
-                    double t = 0.0;
-                    for (int j = 0; j < N1; j++)
-                        t += (side ? A.lp[j] : A.lm[j]) * (double)b[(int64_t)j * stride * kWarp];
-                    out += (double)w[slot] * un * t;
-                } else if (un < 0.0) {
-                    in -= (double)w[slot] * un * (double)static_cast<const T *>(A.ghost)[(int64_t)f * A.nslots + slot];
-                }
-            }
-        }
-        out = wall_cta_sum(out, red);
-        in = wall_cta_sum(in, red);
+        const double rw = curved_wall_density<T, W>(A, w, xi, n, e, side, n0, stride, f, red);
         if (threadIdx.x == 0)
-            static_cast<T *>(A.rhow)[((int64_t)f * A.nfmax + fe) * NQ + fnode] = (T)(out / in);
+            static_cast<T *>(A.rhow)[((int64_t)f * A.nfmax + fe) * NQ + fnode] = (T)rw;
         return;
     }
     T l[kMaxN1];
@@ -139,16 +153,15 @@ __global__ void __launch_bounds__(kWallWarps * 32) k_wall(const WallArgs A, cons
         static_cast<T *>(A.rhow)[((int64_t)f * A.nfmax + fe) * NQ + fnode] = (T)(sum * A.inv_in[f]);
 }
 
-// The wall faces of an unstructured mesh (from its list, one warp per face point): the same zero-net-
-// mass-flux density with the face point's own outward normal, both sums over all velocities.
+// The wall faces of an unstructured mesh (from its list, one CTA of kWallWarps warps per face point):
+// the same zero-net-mass-flux density with the face point's own outward normal, both sums over all
+// velocities.
 template <typename T, typename W>
-__global__ void __launch_bounds__(256) k_wall_list(const WallArgs A, const W *w, const W *xi)
+__global__ void __launch_bounds__(kWallWarps * 32) k_wall_list(const WallArgs A, const W *w, const W *xi)
 {
-    const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    const int N1 = A.N1, NQ = N1 * N1, NP = A.NP, E = A.mesh.nelem;
-    if (gw >= A.nwall * NQ)
-        return;  // whole warp
-    const int idx = gw / NQ, fnode = gw % NQ;
+    __shared__ double red[kWallWarps];
+    const int N1 = A.N1, NQ = N1 * N1;
+    const int idx = (int)blockIdx.x / NQ, fnode = (int)blockIdx.x % NQ;
     const int4 wf = A.wlist[idx];
     const int e = wf.x, d = wf.y >> 1, side = wf.y & 1, g = wf.z;
     const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
@@ -159,42 +172,23 @@ __global__ void __launch_bounds__(256) k_wall_list(const WallArgs A, const W *w,
     const int n0 = nc[0] + N1 * (nc[1] + N1 * nc[2]);
     const int stride = d == 0 ? 1 : (d == 1 ? N1 : NQ);
     const double *n = A.wnu + ((int64_t)idx * NQ + fnode) * 4;
-    double out = 0.0, in = 0.0;
-    for (int c = 0; c < A.nchunks; c++) {
-        const T *src = static_cast<const T *>(A.src[c]);
-        for (int vl = 0; vl < A.nvt[c]; vl++) {
-            const int slot = (A.vt0[c] + vl) * kWarp + lane;
-            const double un = n[0] * (double)xi[slot] + n[1] * (double)xi[(int64_t)A.nslots + slot] +
-                              n[2] * (double)xi[2 * (int64_t)A.nslots + slot];
-            if (un > 0.0) {
-                const T *b = src + fidx(vl, e, n0, lane, E, NP);
-                double t = 0.0;
-                for (int j = 0; j < N1; j++)
-                    t += (side ? A.lp[j] : A.lm[j]) * (double)b[(int64_t)j * stride * kWarp];
-                out += (double)w[slot] * un * t;
-            } else if (un < 0.0) {
-                in -= (double)w[slot] * un * (double)static_cast<const T *>(A.ghost)[(int64_t)g * A.nslots + slot];
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        out += __shfl_xor_sync(0xffffffffu, out, o);
-        in += __shfl_xor_sync(0xffffffffu, in, o);
-    }
-    if (lane == 0)
-        static_cast<T *>(A.rhowu)[(int64_t)idx * NQ + fnode] = (T)(out / in);
+    const double rw = curved_wall_density<T, W>(A, w, xi, n, e, side, n0, stride, g, red);
+    if (threadIdx.x == 0)
+        static_cast<T *>(A.rhowu)[(int64_t)idx * NQ + fnode] = (T)rw;
 }
 
 cudaError_t launch_wall(const WallArgs &A, bool fp64, const void *w, const void *xi, cudaStream_t s)
 {
-    if (A.wlist) {  // unstructured mesh: its wall-face list
-        const int64_t warps = (int64_t)A.nwall * A.N1 * A.N1;
-        const int blocks = (int)((warps * kWarp + 255) / 256);
+    if (A.wlist) {  // unstructured mesh: its wall-face list, one CTA per face point
+        const int blocks = A.nwall * A.N1 * A.N1;
+        if (blocks == 0)
+            return cudaSuccess;
         if (fp64)
             k_wall_list<double, double>
-                <<<blocks, 256, 0, s>>>(A, static_cast<const double *>(w), static_cast<const double *>(xi));
+                <<<blocks, kWallWarps * 32, 0, s>>>(A, static_cast<const double *>(w), static_cast<const double *>(xi));
         else
-            k_wall_list<float, float><<<blocks, 256, 0, s>>>(A, static_cast<const float *>(w), static_cast<const float *>(xi));
+            k_wall_list<float, float>
+                <<<blocks, kWallWarps * 32, 0, s>>>(A, static_cast<const float *>(w), static_cast<const float *>(xi));
         return cudaGetLastError();
     }
     const int blocks = A.wfstart[A.nwf];  // one CTA per wall face point
