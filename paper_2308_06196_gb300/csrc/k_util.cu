@@ -21,41 +21,46 @@ __device__ __forceinline__ float exp_split(double x)
     return ldexpf(exp2f((float)(y - n)), (int)n);
 }
 
-__global__ void k_init_maxwellian(float *__restrict__ f, const double *__restrict__ prim, const float *__restrict__ mi,
-                                  const float *__restrict__ gmask, int nslots, int nvt, int E, int NP, int nx, int ny,
-                                  int nz, double v0x, double v0y, double v0z, double dvx, double dvy, double dvz,
-                                  int *err, double *__restrict__ Q)
+__global__ void __launch_bounds__(256, 4)
+    k_init_maxwellian(float *__restrict__ f, const double *__restrict__ prim, const float *__restrict__ mi,
+                      const float *__restrict__ gmask, int nslots, int nvt, int E, int NP, int nx, int ny, int nz,
+                      double v0x, double v0y, double v0z, double dvx, double dvy, double dvz, int *err,
+                      double *__restrict__ Q)
 {
     const double hm = nz == 1 ? 1.0 : 1.5;  // m / 2
-    extern __shared__ float tab[];  // [NP][nx + ny + nz + 1]
+    extern __shared__ double ith[];          // [NP] -1 / (2 theta) of the element's points, then
+    float *tab = reinterpret_cast<float *>(ith + NP);  // [NP][nx + ny + nz + 1]
     const int e = blockIdx.x;
     const int ntab = nx + ny + nz + 1;
-    for (int q = threadIdx.x; q < NP * ntab; q += blockDim.x) {
-        const int i = q / ntab, t = q % ntab;
+    // per point: the normalisation rho (2 pi theta)^(-m/2) and -1 / (2 theta) (one division per point)
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
         const double *s = prim + ((int64_t)e * NP + i) * 5;
         const double rho = s[0], th = s[4];
-        if (!(rho > 0.0) || !(th > 0.0)) {
-            tab[q] = 0.f;
-            if (t == 0)
-                atomicOr(err, kErrDomain);
-            continue;
-        }
+        const bool ok = rho > 0.0 && th > 0.0;
+        if (!ok)
+            atomicOr(err, kErrDomain);
+        ith[i] = ok ? -0.5 / th : 0.0;
+        tab[i * ntab] = ok ? (float)(rho * pow(2.0 * 3.14159265358979323846 * th, -hm)) : 0.f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NP * (ntab - 1); q += blockDim.x) {
+        const int i = q / (ntab - 1), t = 1 + q % (ntab - 1);
+        const double *s = prim + ((int64_t)e * NP + i) * 5;
+        const double a = ith[i];
         float v;
-        if (t == 0) {
-            v = (float)(rho * pow(2.0 * 3.14159265358979323846 * th, -hm));
-        } else if (t <= nx) {
+        if (t <= nx) {
             const double c = v0x + (t - 1) * dvx - s[1];
-            v = exp_split(-0.5 * c * c / th);
+            v = exp_split(a * c * c);
         } else if (t <= nx + ny) {
             const double c = v0y + (t - 1 - nx) * dvy - s[2];
-            v = exp_split(-0.5 * c * c / th);
+            v = exp_split(a * c * c);
         } else if (nz == 1) {
             v = 1.f;
         } else {
             const double c = v0z + (t - 1 - nx - ny) * dvz - s[3];
-            v = exp_split(-0.5 * c * c / th);
+            v = exp_split(a * c * c);
         }
-        tab[q] = v;
+        tab[i * ntab + t] = a == 0.0 ? 0.f : v;
     }
     __syncthreads();
     if (Q)
@@ -89,17 +94,34 @@ __global__ void k_init_maxwellian(float *__restrict__ f, const double *__restric
             q[4] = 0.5 * C * (S[0][2] * S[1][0] * S[2][0] + S[0][0] * S[1][2] * S[2][0] + S[0][0] * S[1][0] * S[2][2]);
         }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int vt = 0; vt < nvt; vt++) {
-        // grid indices k_d = (m_d + n_d - 1) / 2 of the slot from the centred index table (exact)
+    // the tile's table columns (1 + k_x, 1 + n_x + k_y, 1 + n_x + n_y + k_z) from the centred index table
+    // (k_d = (m_d + n_d - 1) / 2, exact) and its mask; the next tile's are loaded while this one is written
+    auto slot_cols = [&](int vt, int &cx, int &cy, int &cz, float &gm) {
         const int slot = vt * kWarp + lane;
-        const int kx = __float2int_rn(0.5f * (__ldg(mi + slot) + (float)(nx - 1)));
-        const int ky = __float2int_rn(0.5f * (__ldg(mi + nslots + slot) + (float)(ny - 1)));
-        const int kz = __float2int_rn(0.5f * (__ldg(mi + 2 * nslots + slot) + (float)(nz - 1)));
-        const float gm = __ldg(gmask + slot);
+        cx = 1 + __float2int_rn(0.5f * (__ldg(mi + slot) + (float)(nx - 1)));
+        cy = 1 + nx + __float2int_rn(0.5f * (__ldg(mi + nslots + slot) + (float)(ny - 1)));
+        cz = 1 + nx + ny + __float2int_rn(0.5f * (__ldg(mi + 2 * nslots + slot) + (float)(nz - 1)));
+        gm = __ldg(gmask + slot);
+    };
+    int cx, cy, cz;
+    float gm;
+    slot_cols(0, cx, cy, cz, gm);
+    for (int vt = 0; vt < nvt; vt++) {
+        int nx_, ny_, nz_;
+        float ngm;
+        if (vt + 1 < nvt)
+            slot_cols(vt + 1, nx_, ny_, nz_, ngm);
+        float *dst = f + fidx(vt, e, 0, lane, E, NP);
+#pragma unroll 4
         for (int i = w; i < NP; i += nw) {
             const float *t = tab + i * ntab;
-            const float v = gm * (t[0] * t[1 + kx] * t[1 + nx + ky] * t[1 + nx + ny + kz]);
-            __stcs(f + fidx(vt, e, i, lane, E, NP), v);
+            __stcs(dst + i * kWarp, gm * (t[0] * t[cx] * t[cy] * t[cz]));
+        }
+        if (vt + 1 < nvt) {
+            cx = nx_;
+            cy = ny_;
+            cz = nz_;
+            gm = ngm;
         }
     }
 }
@@ -140,7 +162,7 @@ cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi
                                    int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
                                    int *err, double *Q, cudaStream_t s)
 {
-    const int smem = NP * (n[0] + n[1] + n[2] + 1) * (int)sizeof(float);
+    const int smem = NP * (int)sizeof(double) + NP * (n[0] + n[1] + n[2] + 1) * (int)sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_init_maxwellian, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
