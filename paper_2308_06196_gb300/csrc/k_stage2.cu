@@ -21,8 +21,14 @@ struct alignas(16) QuadSmem {
     float wpsi[5][kWarp];                      // w psi of the tile's velocities
 };
 
+// Resident CTAs per SM the register allocation is sized for: 5 (96 registers); 6 (80 registers, a few
+// bytes of spills) runs 3 % slower on the planar Taylor-Green quadrilaterals.
+#ifndef BGK_STAGE2_MINCTAS
+#define BGK_STAGE2_MINCTAS 5
+#endif
+
 template <int N1, int MODE, int OCT>
-__global__ void __launch_bounds__(kWarp *kWarpsPerCta, 5) k_stage2(const StageArgs A)
+__global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_stage2(const StageArgs A)
 {
     constexpr int NQ = N1 * N1;
     constexpr int NCH = NQ * kWarp / 4;  // 16-byte chunks of one element tile
