@@ -162,6 +162,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     // through the layer's own rows of the tile buffer, free once the z-lines have read them (B2), with
     // the 4-float column groups of row q rotated by q mod 8 (conflict-free writes and reads).
     const int np = lane >> 2, kg = lane & 3;
+    // the second half of the rows (np + 8) exists only for layers of more than 8 nodes. Every row is
+    // summed in the same order, so equal rows give bit-equal moments (a y/z-homogeneous state stays so).
+    constexpr int NHR = NQ > 8 ? 2 : 1;
 #pragma unroll
     for (int m = 0; m < 10; m++)
         sm.msum[w][m][lane] = 0.f;
@@ -590,11 +593,11 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
             for (int q = 0; q < NQ; q++)
                 sm.tile[b][q + NQ * w][lane ^ (4 * (q & 7))] = f[q];
         }
-        // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values
+        // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values (rows np + 8 h)
         __syncwarp();
         unsigned long long pm[2][5];
 #pragma unroll
-        for (int h = 0; h < 2; h++)
+        for (int h = 0; h < NHR; h++)
 #pragma unroll
             for (int c = 0; c < 5; c++)
                 pm[h][c] = 0ull;
@@ -609,7 +612,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 wv[c][1] = pack2(w4.z, w4.w);
             }
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
+            for (int h = 0; h < NHR; h++) {
                 const int row = min(np + 8 * h, NQ - 1);  // rows past the layer: discarded below
                 const float4 v = *reinterpret_cast<const float4 *>(&sm.tile[b][row + NQ * w][kk ^ (4 * (row & 7))]);
                 const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; h++)
+        for (int h = 0; h < NHR; h++)
 #pragma unroll
             for (int c = 0; c < 5; c++)
                 sm.msum[w][5 * h + c][lane] += sum2(pm[h][c]);
@@ -630,7 +633,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     // partial moments of this task: combine the 4 velocity eighths of every node pair
     const int grp = A.group0 + gl;
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < NHR; h++) {
         const int q = np + 8 * h;
 #pragma unroll
         for (int c = 0; c < 5; c++) {
