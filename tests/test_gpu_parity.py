@@ -380,6 +380,26 @@ def test_channel_mass_conserved_momentum_driven(fp64):
     assert abs(G2[0] - G0[0]) <= (1e-12 if fp64 else 2e-6) * G0[0]
 
 
+@pytest.mark.parametrize("fp64", [False, True])
+def test_general_form_reruns_are_bit_identical(fp64):
+    # walls (their densities summed over 4 warps in a fixed order), body force, limiter and variable tau:
+    # two fresh contexts on the same input give the same f and moments, bit for bit
+    from paper_2308_06196_gb300.bgk import FP64, FP32_SPLIT
+
+    c = small_channel(force=(0.05, 0.02, 0.0))
+    f = random_f(oracle_problem(c), seed=51)
+    runs = []
+    for _ in range(2):
+        s = solver(c, precision=FP64 if fp64 else FP32_SPLIT, limiter=True, mu_ref=2e-2, mu_omega=0.81)
+        s.set_f(f)
+        dt = s.dt(0.1)
+        s.step(dt, 3)
+        runs.append((s.get_f(), s.moments()))
+        s.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+
+
 def test_autotune_keeps_results():
     # the autotuner only changes the task shape: the same step gives the same moments (the grouping of
     # the FP32 partial sums changes, so agreement is to FP32 summation order, not bitwise)
