@@ -65,10 +65,11 @@ typedef struct {
     double bc_state[3][2][5];  /* Dirichlet: rho,u,v,w,T.  Wall: (unused),u_w,v_w,w_w,T_w */
 } bgk_mesh;
 
-/* Uniform velocity grid, n[d] >= 2 nodes per axis on [lo[d], hi[d]] with both endpoints included,
- * tensor-product trapezoid weights (Sec. 2.1, Eq. 12). */
-/* Uniform velocity grid, n[d] nodes on [lo[d], hi[d]] per axis, endpoints included, tensor trapezoid
- * weights (Sec. 2.1, Eq. 12). n[2] = 1 selects the two-dimensional velocity space (velocity dimension
+/* Uniform velocity grid, n[d] >= 2 nodes on [lo[d], hi[d]] per axis, endpoints included, tensor
+ * trapezoid weights (Sec. 2.1, Eq. 12); at least one axis needs 3 or more nodes (on two nodes every
+ * function of xi_d is affine in xi_d, so with two on every axis |xi|^2 is a combination of 1 and xi,
+ * the energy moment depends on the others and the conservative Maxwellian is not unique: BGK_EINVAL).
+ * n[2] = 1 selects the two-dimensional velocity space (velocity dimension
  * m = 2, Sec. 2 with m >= d, so dim <= 2): velocities (u_x, u_y), the Maxwellian normalised by
  * (2 pi theta)^(m/2) (Eq. 4), E = rho |U|^2 / 2 + (m/2) rho theta; lo[2] and hi[2] are not read, the
  * third momentum component of Q is identically 0 and the third velocity component of every state

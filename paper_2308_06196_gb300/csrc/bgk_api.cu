@@ -747,6 +747,12 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         c->vlo[d] = vg->lo[d];
         c->dv[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
     }
+    bool all_two = true;  // on two nodes every function of xi_d is affine in xi_d, so with two on every
+    for (int d = 0; d < c->vdim; d++)  // axis |xi|^2 is a combination of 1 and xi: E is not independent
+        all_two = all_two && vg->n[d] == 2;
+    if (all_two)
+        return bail(BGK_EINVAL, "the velocity grid needs 3 or more nodes on some axis (with 2 on every axis "
+                                "the energy moment depends on the others and the Maxwellian is not unique)");
     if (c->vdim == 2) {  // the absent u_z axis: one node at 0 of unit weight
         c->nv[2] = 1;
         c->vlo[2] = 0.0;

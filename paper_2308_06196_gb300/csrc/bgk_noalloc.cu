@@ -85,9 +85,14 @@ extern "C" int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk
     if (!d_f || !vg || !d_Q || !d_prim || npts < 1 || npts > (1 << 30))
         return BGK_EINVAL;
     const int vdim = vg->n[2] == 1 ? 2 : 3;  // n[2] = 1: the two-dimensional velocity space
-    for (int d = 0; d < vdim; d++)
+    bool all_two = true;  // two nodes on every axis: the energy moment depends on the others
+    for (int d = 0; d < vdim; d++) {
         if (vg->n[d] < 2 || vg->n[d] > 4096 || !(vg->hi[d] > vg->lo[d]))
             return BGK_EINVAL;
+        all_two = all_two && vg->n[d] == 2;
+    }
+    if (all_two)
+        return BGK_EINVAL;
     const int64_t nvel = (int64_t)vg->n[0] * vg->n[1] * vg->n[2];
     const int64_t ng64 = (nvel + kGroupVel - 1) / kGroupVel;
     if (ng64 > 65535) {

@@ -252,3 +252,14 @@ def test_body_force_source_moments():
     MS = S @ (a.w[:, None] * psi(a.xi))
     ref = np.stack([0 * Q[:, 0], Q[:, 0] * F[0], Q[:, 0] * F[1], Q[:, 0] * F[2], Q[:, 1:4] @ F], 1)
     assert np.allclose(MS, ref, atol=1e-13, rtol=1e-10)
+
+
+@pytest.mark.parametrize("nv,rank", [((2, 2, 2), 4), ((2, 2, 3), 5), ((2, 3, 2), 5), ((3, 3, 3), 5)])
+def test_moment_functions_independent_only_with_three_nodes_on_some_axis(nv, rank):
+    # (1, xi, |xi|^2 / 2) on the grid nodes: on two nodes every function of xi_d is affine in xi_d, so
+    # with two on every axis |xi|^2 is a combination of 1 and xi (rank 4, the Maxwellian of given moments
+    # is not unique and the library rejects the grid); one axis of three restores rank 5. Asymmetric
+    # extents, so the dependence is not a symmetry accident.
+    xi, _ = orc.velocity_grid(nv, (-4.0, -3.0, -2.0), (4.0, 5.0, 2.0))
+    psi = np.column_stack([np.ones(len(xi)), xi, 0.5 * (xi**2).sum(1)])
+    assert np.linalg.matrix_rank(psi) == rank
