@@ -3,8 +3,9 @@
 One "step" is one SSP-RK3 step (three stages) over the whole Taylor-Green workload: 16^3 hexahedra
 at p = 3 (262,144 points) x 24^3 velocities (13,824) = 3.62e9 degrees of freedom; each stage
 advects every velocity, relaxes towards the conservative Maxwellian and recomputes moments and the
-Newton solve. value = n_x * N_v * 3 / (seconds per step). f (14.5 GB per array) is far larger than
-L2, so no flush is needed between steps.
+Newton solve. value = n_x * N_v * 3 / (seconds per step), timed over K steps of the captured CUDA graph;
+a second pass of K steps launched directly, with CUDA events around every launch, gives the roofline's
+per-launch durations. f (14.5 GB per array) is far larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
