@@ -61,7 +61,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -641,28 +641,27 @@ def main():
     barrier()
 
     # timed region: K steps through the captured CUDA graph (the library's stepping path), CUDA events
-    # on the library's stream, clocks sampled meanwhile
+    # on the library's stream; then the same K steps launched directly, every stage and Newton launch
+    # bracketed by CUDA events on its stream (the per-launch durations of the roofline). Clocks are
+    # sampled during both.
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.set_state(prim_dev)
     barrier()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         barrier()
         g0.record(stream)
         s.step(dt, args.steps)
         g1.record(stream)
         barrier()
+        s.set_state(prim_dev)
+        barrier()
+        s.set_timing(True)
+        e0.record(stream)
+        s.step(dt, args.steps)
+        e1.record(stream)
+        barrier()
     ms = g0.elapsed_time(g1) / args.steps
-
-    # the same K steps launched directly, every stage and Newton launch bracketed by CUDA events on its
-    # stream: the per-launch durations of the roofline
-    s.set_state(prim_dev)
-    barrier()
-    s.set_timing(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(dt, args.steps)
-    e1.record(stream)
-    barrier()
     tm = s.timing()
     s.set_timing(False)
     s.synchronize()
