@@ -32,7 +32,7 @@ int stage1d_tasks(const StageArgs &A);
 int stage1d_batch_ctas();
 cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi, const float *gmask, int nslots,
                                    int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
-                                   int *err, double *Q, cudaStream_t s);
+                                   int *err, double *Q, double *warm, cudaStream_t s);
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
 cudaError_t launch_stage64(const Stage64Args &A, cudaStream_t s);
@@ -405,9 +405,9 @@ Moments64Args moments64_args(bgk_ctx *c)
     return M;
 }
 
-// Moments + conservative Maxwellian of the current f^n (after set_state / set_f).
-// Moments of the state f^n and its conservative Maxwellian; have_q: Q was formed with the state (the
-// initial sampling's separable moments), only the Newton solve is left.
+// Moments of the state f^n and its conservative Maxwellian (after bgk_set_state / bgk_set_f). have_q:
+// Q was formed with the state (the initial sampling's separable moments) and the Newton solve starts
+// from the sampled Maxwellian itself; otherwise a moments pass over f and a cold solve.
 int prologue(bgk_ctx *c, cudaStream_t s, bool have_q = false)
 {
     if (c->prec == BGK_FP64) {
@@ -421,8 +421,8 @@ int prologue(bgk_ctx *c, cudaStream_t s, bool have_q = false)
         CK(launch_newton(newton_args(c, 1), s));
         return BGK_OK;
     }
-    if (have_q) {
-        NewtonArgs N = newton_args(c, 1);
+    if (have_q) {  // after bgk_set_state: the moments and the warm start are the sampled Maxwellian's
+        NewtonArgs N = newton_args(c, 0);
         N.Qin = c->Q;
         CK(launch_newton(N, s));
         return BGK_OK;
@@ -1021,7 +1021,7 @@ static int set_state_impl(bgk_ctx *c, const double *prim, cudaMemcpyKind kind)
                          c->stream));
     else
         CK(launch_init_maxwellian(c->fA, c->prim_in, c->mi, c->gmask, c->nslots, c->nvt, c->E, c->NP, c->nv, c->vlo,
-                                  c->dv, c->err, c->Q, c->stream));
+                                  c->dv, c->err, c->Q, c->prim, c->stream));
     return prologue(c, c->stream, c->prec != BGK_FP64);
 }
 

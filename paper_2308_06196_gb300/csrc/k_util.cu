@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256, BGK_INIT_MINCTAS)
     k_init_maxwellian(float *__restrict__ f, const double *__restrict__ prim, const float *__restrict__ mi,
                       const float *__restrict__ gmask, int nslots, int nvt, int E, int NP, int nx, int ny, int nz,
                       double v0x, double v0y, double v0z, double dvx, double dvy, double dvz, int *err,
-                      double *__restrict__ Q)
+                      double *__restrict__ Q, double *__restrict__ warm)
 {
     const double hm = nz == 1 ? 1.0 : 1.5;  // m / 2
     extern __shared__ double ith[];          // [NP] -1 / (2 theta) of the element's points, then
@@ -45,7 +45,16 @@ __global__ void __launch_bounds__(256, BGK_INIT_MINCTAS)
         if (!ok)
             atomicOr(err, kErrDomain);
         ith[i] = ok ? -0.5 / th : 0.0;
-        tab[i * ntab] = ok ? (float)(rho * pow(2.0 * 3.14159265358979323846 * th, -hm)) : 0.f;
+        const double C = rho * pow(2.0 * 3.14159265358979323846 * th, -hm);
+        tab[i * ntab] = ok ? (float)C : 0.f;
+        if (warm && ok) {  // the first Newton solve's start: this Maxwellian, (ln C, U, theta)
+            double *wp = warm + ((int64_t)e * NP + i) * 5;
+            wp[0] = log(C);
+            wp[1] = s[1];
+            wp[2] = s[2];
+            wp[3] = nz == 1 ? 0.0 : s[3];
+            wp[4] = th;
+        }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NP * (ntab - 1); q += blockDim.x) {
@@ -165,14 +174,14 @@ __global__ void k_gather_f(double *__restrict__ st, const float *__restrict__ f,
 
 cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi, const float *gmask, int nslots,
                                    int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
-                                   int *err, double *Q, cudaStream_t s)
+                                   int *err, double *Q, double *warm, cudaStream_t s)
 {
     const int smem = NP * (int)sizeof(double) + NP * (n[0] + n[1] + n[2] + 1) * (int)sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_init_maxwellian, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess)
         return e;
     k_init_maxwellian<<<E, 256, smem, s>>>(f, prim, mi, gmask, nslots, nvt, E, NP, n[0], n[1], n[2], v0[0], v0[1],
-                                           v0[2], dv[0], dv[1], dv[2], err, Q);
+                                           v0[2], dv[0], dv[1], dv[2], err, Q, warm);
     return cudaGetLastError();
 }
 
