@@ -56,7 +56,8 @@ extern "C" {
 typedef struct bgk_ctx bgk_ctx;
 
 /* Structured affine mesh of line (dim = 1), quadrilateral (dim = 2) or hexahedral (dim = 3) elements on [lo, hi].
- * Only the first dim entries of nelem/lo/hi/bc/bc_state are read. The velocity space is always 3-D. */
+ * Only the first dim entries of nelem/lo/hi/bc/bc_state are read. The velocity space is 3-D unless the
+ * velocity grid has n[2] = 1 (see bgk_vgrid). */
 typedef struct {
     int dim;
     int nelem[3];
@@ -127,18 +128,24 @@ int bgk_points(const bgk_ctx *ctx, double *x);
 
 /* Set f to the sampled continuous Maxwellian (Eq. 4, velocity dimension m) of the primitive state
  * prim[n_x][5] = (rho, u, v, w, T) (theta = T), then compute its moments and conservative
- * Maxwellian. Host array (synchronises) or device array (asynchronous) variant. */
+ * Maxwellian. Host array (synchronises) or device array (asynchronous) variant. A point with
+ * rho <= 0, T <= 0 or NaN makes the context's status BGK_EDOMAIN (returned by the host variant, by
+ * the device variant's next synchronising call). */
 int bgk_set_state(bgk_ctx *ctx, const double *prim);
 int bgk_set_state_device(bgk_ctx *ctx, const double *d_prim);
 
-/* Copy the distribution function in or out as f[n_x][N_v] FP64 (host; synchronises). */
+/* Copy the distribution function in or out as f[n_x][N_v] FP64 (host; synchronises). bgk_set_f then
+ * computes the moments and conservative Maxwellian of the new f (a point of non-positive density:
+ * BGK_EDOMAIN, sticky). */
 int bgk_set_f(bgk_ctx *ctx, const double *f);
 int bgk_get_f(bgk_ctx *ctx, double *f);
 
 /* Enqueue nsteps SSP-RK3 steps of size dt. Each step is three stages; each stage advects every
  * velocity (Eqs. 7-9), applies the BGK relaxation towards the conservative Maxwellian of the
  * stage's input (Eq. 3) and combines the Shu-Osher stage, then recomputes the moments and the
- * conservative Maxwellian of its output. Asynchronous on the context stream. */
+ * conservative Maxwellian of its output. Asynchronous on the context stream. BGK_EINVAL for
+ * nsteps < 0 or a dt that is not positive and finite, and for connectivity tables without node
+ * coordinates; a sticky device status from earlier work is returned instead of enqueuing. */
 int bgk_step(bgk_ctx *ctx, double dt, int nsteps);
 
 /* Moments Q[n_x][5] = (rho, rho u, rho v, rho w, E) of the current f (Eq. 2 with Eq. 12).
