@@ -165,30 +165,33 @@ int bgk_synchronize(bgk_ctx *ctx);
 double bgk_dt(const bgk_ctx *ctx, double cfl);
 
 /* Tile-shape autotuner: times the stage kernel for several task lengths (32-velocity tiles per warp
- * task: 2, 4, ..., 64) on this context's own buffers, keeps the fastest for this context and caches it
+ * task: 2, 4, ..., 64, and the lengths that split the longest velocity chunk into 1, 2, 3, 4, 6, 8,
+ * 12 or 16 equal tasks) on this context's own buffers, keeps the fastest for this context and caches it
  * per (dim, degree, velocity grid, mesh, chunking) for the rest of the process. Does not change f,
  * the moments or the equilibrium; invalidates the captured graph. *g_out (may be NULL) receives the
  * chosen length (0 for the all-FP64 form, which has no task shape). */
 int bgk_autotune(bgk_ctx *ctx, int *g_out);
 
 /* Curvilinear hexahedra (the mapped elements of Sec. 2.1's FR on unstructured curved meshes; dim = 3,
- * FP32-split form, no diffuse walls). x is host memory, FP64, [n_x][3]: the physical coordinates of
+ * both precision forms, every boundary kind). x is host memory, FP64, [n_x][3]: the physical coordinates of
  * every solution node in the point order of bgk_points (element-major, x-fastest; the mesh connectivity
  * and periodicity stay those of bgk_create). Each element maps the reference cube by the degree-p
  * interpolant of its nodes. The library computes in FP64 the metric terms Ja^i (Kopriva's conservative
  * curl form, so a constant state is kept to round-off), J, and the face normals (the mean of the two
  * elements' interpolated Ja^i on a shared face), and from then on advects the reference-space flux
  * (Ja^i . xi) f / J with per-lane upwinding at every face point (Eq. 9 with u_n = Ja^i . xi). The
- * limiter's element mean becomes J-weighted; bgk_points returns x; bgk_dt uses the metric. The state
- * is kept. Returns BGK_EINVAL for another dim/precision, diffuse walls, or a node with J <= 0. */
+ * limiter's element mean becomes J-weighted; on a diffuse wall every face point's density makes the
+ * net discrete mass flux through its own outward unit normal vanish; bgk_points returns x; bgk_dt uses
+ * the metric. The state is kept. Returns BGK_EINVAL for dim != 3 or a node with J <= 0. */
 int bgk_set_geometry(bgk_ctx *ctx, const double *x);
 
 /* Unstructured hexahedral connectivity (with bgk_set_geometry, whose node coordinates then carry every
- * element's position and local-axis orientation; dim = 3, FP32-split form, no diffuse walls). Host
+ * element's position and local-axis orientation; dim = 3, both precision forms). Host
  * arrays [n_elements][6], indexed by element and local face f = 2d + side (reference axis d, side 0 the
  * r_d = -1 face):
- *   nbr[e][f]    the neighbour element, or -1 - g at a boundary face, which takes the Dirichlet ghost of
- *                face g of bgk_create's boundary data (bc[g / 2][g % 2] must be BGK_BC_DIRICHLET);
+ *   nbr[e][f]    the neighbour element, or -1 - g at a boundary face, which takes the boundary data of
+ *                face g of bgk_create (bc[g / 2][g % 2] must be BGK_BC_DIRICHLET or BGK_BC_DIFFUSE_WALL;
+ *                a wall face gets its own wall density per face point);
  *   nface[e][f]  the neighbour's local face 2d' + s' that is shared;
  *   orient[e][f] the face-point match: for the face point with node coordinates (a, b) along our two
  *                other axes (in increasing axis order) the neighbour's (a', b') is (b, a) if bit 0 is

@@ -1556,7 +1556,19 @@ int bgk_autotune(bgk_ctx *c, int *g_out)
     float best = 1e30f;
     int bestG = c->G;
     const int C = (int)c->chunks.size();
-    for (int G = kMinTuneG; G <= 64 && G <= std::max(kMinTuneG, maxc); G *= 2) {
+    // task lengths: powers of two, and the lengths that split the longest chunk into k equal tasks (no
+    // short last task per element)
+    std::vector<int> cands;
+    for (int G = kMinTuneG; G <= 64 && G <= std::max(kMinTuneG, maxc); G *= 2)
+        cands.push_back(G);
+    for (int k : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        const int G = (maxc + k - 1) / k;
+        if (G >= kMinTuneG && G <= 64)
+            cands.push_back(G);
+    }
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    for (int G : cands) {
         set_task_length(c, G);
         float tot = 0.f;
         for (int rep = 0; rep < 3; rep++) {
