@@ -229,8 +229,8 @@ int bgk_timing(bgk_ctx *ctx, double *stage_ms, int64_t *stage_launches, double *
  * bgk_batch_synchronize: waits for the batch stream and returns the status of all members' Newton
  *   solves (BGK_EDOMAIN / BGK_ENEWTON also become sticky in every member).
  * bgk_batch_autotune: the tile-shape autotuner of the batch: for every (degree, velocity grid) class
- *   of members in turn, times the persistent stage launch with the class's task length at 2, 4, ...,
- *   64 tiles (the other classes fixed) and keeps the fastest. Changes no state.
+ *   of members in turn, times the persistent stage launch with the class's task length at the
+ *   lengths bgk_autotune tries (the other classes fixed) and keeps the fastest. Changes no state.
  * bgk_batch_info: total points, degrees of freedom and stage tasks of the batch.
  * bgk_batch_set_timing / bgk_batch_timing: as bgk_set_timing / bgk_timing, for the batch launches.
  * ------------------------------------------------------------------------------------------- */

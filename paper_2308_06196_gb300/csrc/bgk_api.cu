@@ -1511,6 +1511,23 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
 // Tile-shape autotuner: tiles per task G, per (mesh, degree, velocity grid), cached for the process.
 static std::vector<std::pair<std::string, int>> g_tuned;
 
+// Task lengths the autotuners try for chunks of at most maxc tiles: the powers of two from kMinTuneG to
+// 64, and the lengths that split the longest chunk into k equal tasks (no short last task per element).
+static std::vector<int> task_length_candidates(int maxc)
+{
+    std::vector<int> cands;
+    for (int G = kMinTuneG; G <= 64 && G <= std::max(kMinTuneG, maxc); G *= 2)
+        cands.push_back(G);
+    for (int k : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        const int G = (maxc + k - 1) / k;
+        if (G >= kMinTuneG && G <= 64)
+            cands.push_back(G);
+    }
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    return cands;
+}
+
 static void set_task_length(bgk_ctx *c, int G)
 {
     c->G = G;
@@ -1556,19 +1573,7 @@ int bgk_autotune(bgk_ctx *c, int *g_out)
     float best = 1e30f;
     int bestG = c->G;
     const int C = (int)c->chunks.size();
-    // task lengths: powers of two, and the lengths that split the longest chunk into k equal tasks (no
-    // short last task per element)
-    std::vector<int> cands;
-    for (int G = kMinTuneG; G <= 64 && G <= std::max(kMinTuneG, maxc); G *= 2)
-        cands.push_back(G);
-    for (int k : {1, 2, 3, 4, 6, 8, 12, 16}) {
-        const int G = (maxc + k - 1) / k;
-        if (G >= kMinTuneG && G <= 64)
-            cands.push_back(G);
-    }
-    std::sort(cands.begin(), cands.end());
-    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
-    for (int G : cands) {
+    for (int G : task_length_candidates(maxc)) {
         set_task_length(c, G);
         float tot = 0.f;
         for (int rep = 0; rep < 3; rep++) {
@@ -2020,7 +2025,10 @@ int bgk_batch_autotune(bgk_batch *b)
     for (size_t k = 0; k < rep.size(); k++) {
         float best = 1e30f;
         int bestG = b->probs[rep[k]]->G;
-        for (int G = kMinTuneG; G <= 64; G *= 2) {
+        int maxc = 0;  // the class's longest chunk (members with the same degree and velocity grid)
+        for (const Chunk &ch : b->probs[rep[k]]->chunks)
+            maxc = std::max(maxc, ch.nvt);
+        for (int G : task_length_candidates(maxc)) {
             for (int q = 0; q < b->n; q++)
                 if (cls[q] == (int)k)
                     set_task_length(b->probs[q], G);
