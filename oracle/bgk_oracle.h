@@ -17,6 +17,19 @@
  *     found by Newton's method with a closed-form Jacobian so that its discrete moments equal Q
  *     (Sec. 2.1, the text after Eq. 13).
  *   - The BGK relaxation (g - f)/tau (Sec. 2, Eq. 3) and explicit SSP-RK3 time stepping (Sec. 2.2).
+ *   - The Zhang-Shu positivity limiter of every stage output (Sec. 2.1, Eqs. 10-11), a power-law
+ *     viscosity giving tau per point (Sec. 2, Eq. 5), and the ablation's continuous Maxwellian of Q
+ *     (Sec. 2.1, Eq. 13) in place of the conservative one.
+ *   - Boundaries: Dirichlet Maxwellian ghosts, diffuse walls whose density per face point gives zero
+ *     net discrete mass flux, and the body-force source projected on the equilibrium.
+ *   - Meshes: line, quadrilateral and hexahedral elements (dim = 1, 2, 3); curvilinear hexahedra from
+ *     node coordinates (metric terms in Kopriva's conservative curl form, upwinding on the shared face
+ *     normal); unstructured hexahedral connectivity (neighbour, shared-face and orientation tables).
+ *   - The two-dimensional velocity space (m = 2, a velocity grid with one node on its third axis).
+ * Every part is pinned by the CPU tests against what the paper and the mathematics fix (closed forms,
+ * invariants, an independent second formulation, brute force on small inputs); the Sod and Mach-5
+ * shock structures have no closed form, so beyond agreement with the oracle their physics is parity
+ * unpinned.
  *
  * Conventions: all arrays are FP64 and caller-owned. Point order = element-major (element index
  * x-fastest), then node index x-fastest. Velocity order k = kx + nx*(ky + ny*kz). f is [n_x][N_v].
