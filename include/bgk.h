@@ -263,13 +263,19 @@ int bgk_batch_timing(bgk_batch *batch, double *stage_ms, int64_t *stage_launches
  *   d_prim  device, FP64, [npts][5] (rho', U'x, U'y, U'z, theta'), written;
  *   stream  cudaStream_t to run on (NULL: the legacy default stream). The call waits for its own
  *           work on that stream and returns its status (BGK_OK, BGK_EDOMAIN, BGK_ENEWTON).
- * Scratch: one static device array of BGK_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the
- * library until the process exits. It must hold 4 * (64 + npts * (5 * ceil(N_v / 2048) + 8)) bytes;
- * larger requests return BGK_EINVAL with a message on stderr, before any work is enqueued.
- * The first call on a device looks up that device's address of the array (with the device
- * current); make that first call before any stream capture. Every call uses the same array, which
- * keeps the last call's contents: calls that overlap on the GPU (other streams, other host threads)
- * race on it, so serialise them. No cudaMalloc, cudaFree or allocating library routine is called.
+ * Scratch: one static device array of BGK_NOALLOC_SCRATCH_BYTES. A GPU holds it from the moment the
+ * library's module is loaded on it until the process exits; under lazy module loading (the CUDA
+ * default since 12.2) that is the first call of this entry point on that device, so the first call is
+ * the sizing point: a caller whose device footprint must not grow after start-up makes one call during
+ * start-up (or sets CUDA_MODULE_LOADING=EAGER). It must hold
+ * 4 * (64 + npts * (5 * ceil(N_v / 2048) + 8)) bytes; larger requests return BGK_EINVAL with a message
+ * on stderr, before any work is enqueued. The first call on a device also looks up that device's
+ * address of the array (with the device current). The call is synchronous -- it waits for its work
+ * and reads a status word back -- so it cannot be captured in a CUDA graph: on a capturing stream it
+ * returns BGK_EINVAL (message on stderr) before enqueuing anything. Every call uses the same array,
+ * which keeps the last call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race on it, so serialise them. No cudaMalloc, cudaFree or allocating library routine is
+ * called.
  * ------------------------------------------------------------------------------------------- */
 #define BGK_NOALLOC_SCRATCH_BYTES (16ll << 20)
 int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk_vgrid *vg, double *d_Q, double *d_prim,

@@ -162,14 +162,31 @@ def make_opts(precision=FP32_SPLIT, body_force=(0.0, 0.0, 0.0), newton_max_it=0,
     return o
 
 
-def equilibrium_noalloc(f_dev, nv, vlo, vhi, Q_dev, prim_dev, stream_ptr=0):
+def equilibrium_noalloc(f_dev, nv, vlo, vhi, Q_dev, prim_dev, stream_ptr=None):
     """bgk_equilibrium_noalloc on caller-owned CUDA tensors: f_dev float32 [npts, N_v], Q_dev and
-    prim_dev float64 [npts, 5]. For callers that cannot allocate device memory: the library uses
-    only its fixed static scratch. Returns the status code (0 on success)."""
-    assert f_dev.is_cuda and f_dev.dtype.itemsize == 4 and f_dev.is_contiguous()
-    assert Q_dev.is_cuda and prim_dev.is_cuda and Q_dev.is_contiguous() and prim_dev.is_contiguous()
+    prim_dev float64 [npts, 5], all on one device. For callers that cannot allocate device memory: the
+    library uses only its fixed static scratch. The C entry point cannot see buffer sizes, so every
+    shape, dtype and device is checked here and a mismatch raises ValueError before anything is
+    launched. stream_ptr defaults to torch's current stream on f's device. Returns the status code
+    (0 on success)."""
+    import torch
+
+    nvel = int(np.prod([int(x) for x in nv]))
+    if f_dev.dtype != torch.float32 or f_dev.dim() != 2 or f_dev.shape[1] != nvel or not f_dev.is_contiguous():
+        raise ValueError(f"f must be a contiguous float32 [npts, {nvel}] tensor, got {f_dev.dtype} "
+                         f"{tuple(f_dev.shape)}")
+    npts = int(f_dev.shape[0])
+    for name, t in (("Q", Q_dev), ("prim", prim_dev)):
+        if t.dtype != torch.float64 or tuple(t.shape) != (npts, 5) or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 [{npts}, 5] tensor, got {t.dtype} {tuple(t.shape)}")
+        if t.device != f_dev.device:
+            raise ValueError(f"{name} is on {t.device}, f on {f_dev.device}")
+    if not f_dev.is_cuda:
+        raise ValueError("f, Q and prim must be CUDA tensors")
+    if stream_ptr is None:
+        stream_ptr = torch.cuda.current_stream(f_dev.device).cuda_stream
     vg = make_vgrid(nv, vlo, vhi)
-    return lib().bgk_equilibrium_noalloc(C.c_void_p(f_dev.data_ptr()), int(f_dev.shape[0]), C.byref(vg),
+    return lib().bgk_equilibrium_noalloc(C.c_void_p(f_dev.data_ptr()), npts, C.byref(vg),
                                          C.c_void_p(Q_dev.data_ptr()), C.c_void_p(prim_dev.data_ptr()),
                                          C.c_void_p(stream_ptr or 0))
 

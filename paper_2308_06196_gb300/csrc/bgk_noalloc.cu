@@ -7,8 +7,12 @@
 // path (bgk_create) allocates its own buffers, so those callers could not use it. This entry point
 // allocates nothing: the caller passes device pointers for the input and the outputs, and the only
 // scratch (the partial moment sums and the solver's private per-point table) lives in one
-// file-scope __device__ array of fixed size, which every GPU that loads this library holds until
-// the process exits.
+// file-scope __device__ array of fixed size. A device holds it from the moment this library's module
+// is loaded there until the process exits; under lazy module loading (the CUDA default since 12.2)
+// that is the first call of this entry point on the device, which is therefore the sizing point: a
+// caller with a fixed footprint makes it during start-up. The call is synchronous (it reads the
+// status word back), so it cannot be captured in a CUDA graph; on a capturing stream it returns
+// BGK_EINVAL before enqueuing anything.
 //
 // Scratch layout (floats): [0, 64) status word, then partial sums [ngroups][5][npts], then the
 // per-point exponent table [npts][8] written by the Newton kernel.
@@ -126,6 +130,13 @@ extern "C" int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk
         scr = g_ptr[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess)
+        return BGK_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) {
+        fprintf(stderr, "bgk_equilibrium_noalloc: the call is synchronous and cannot be captured in a CUDA graph\n");
+        return BGK_EINVAL;
+    }
     int *status = reinterpret_cast<int *>(scr);
     float *partial = scr + kStatusFloats;
     float *param = partial + (int64_t)ngroups * 5 * npts;

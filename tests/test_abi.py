@@ -52,3 +52,26 @@ def test_oracle_and_library_share_no_code():
             txt = open(os.path.join(ROOT, "oracle", fn)).read()
             assert "paper_2308_06196_gb300" not in txt and "bgk.h" not in txt
 
+
+
+def test_noalloc_wrapper_checks_buffers_before_any_launch():
+    # the C entry point cannot see buffer sizes, so the binding checks dtype, shape and device of every
+    # tensor and raises before calling into the library (CPU tensors here: nothing reaches a GPU)
+    torch = pytest.importorskip("torch")
+    from paper_2308_06196_gb300 import bgk
+
+    nv, lo, hi = (4, 4, 4), (-3.0,) * 3, (3.0,) * 3
+    good_f = torch.zeros((5, 64), dtype=torch.float32)
+    good_q = torch.zeros((5, 5), dtype=torch.float64)
+    cases = [
+        (torch.zeros((5, 64), dtype=torch.float64), good_q, good_q),   # f in FP64
+        (torch.zeros((5, 63), dtype=torch.float32), good_q, good_q),   # f of another velocity grid
+        (torch.zeros((320,), dtype=torch.float32), good_q, good_q),    # f not [npts, N_v]
+        (good_f, torch.zeros((5, 5), dtype=torch.float32), good_q),    # Q in FP32
+        (good_f, good_q, torch.zeros((4, 5), dtype=torch.float64)),    # prim too short
+        (good_f, torch.zeros((5, 4), dtype=torch.float64), good_q),    # Q of 4 components
+        (good_f, good_q, good_q),                                      # host tensors
+    ]
+    for f, q, p in cases:
+        with pytest.raises(ValueError):
+            bgk.equilibrium_noalloc(f, nv, lo, hi, q, p)

@@ -48,6 +48,33 @@ def test_noalloc_matches_context_path_twice():
             assert np.all(np.abs((w * g) @ psi - q) <= 1e-12 * np.abs(q).max())
 
 
+def test_noalloc_allocates_nothing():
+    # the defining property: after a first call (the sizing point, which may load the library's module
+    # and its static scratch on this device), further calls change neither the device's free memory
+    # nor the torch allocator's total
+    import torch
+
+    _build.build()
+    from paper_2308_06196_gb300 import bgk
+
+    n, L = 12, 5.0
+    pr = orc.Problem(1, [4], [0.0], [1.0], 2, (n,) * 3, (-L,) * 3, (L,) * 3, 0.05)
+    pr.set_state(W.smooth_prim(pr.points(), 1, seed=51))
+    f_dev = torch.tensor(pr.get_f(), dtype=torch.float32, device="cuda")
+    Q_dev = torch.zeros((pr.npts, 5), dtype=torch.float64, device="cuda")
+    P_dev = torch.zeros((pr.npts, 5), dtype=torch.float64, device="cuda")
+    assert bgk.equilibrium_noalloc(f_dev, (n,) * 3, (-L,) * 3, (L,) * 3, Q_dev, P_dev) == 0
+    Q0 = Q_dev.clone()
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert bgk.equilibrium_noalloc(f_dev, (n,) * 3, (-L,) * 3, (L,) * 3, Q_dev, P_dev) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.equal(Q_dev, Q0)
+
+
 def test_noalloc_rejects_oversized_request():
     import torch
 
