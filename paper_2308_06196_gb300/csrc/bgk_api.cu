@@ -186,6 +186,7 @@ struct bgk_ctx {
     // device buffers
     float *fA = nullptr, *pool = nullptr;
     float *xi = nullptr, *mi = nullptr, *wpsi = nullptr, *gmask = nullptr, *ghost = nullptr;
+    float *vtab = nullptr;  // [nvt][5][32]: m_x, m_y, m_z, W and W sum_d r_d m_d^2 of every slot, by tile
     int *slotk_d = nullptr;
     unsigned char *toct = nullptr;
     float *partial = nullptr, *param = nullptr;
@@ -284,6 +285,7 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     }
     A.viso = c->dv[0] == c->dv[1] && c->dv[0] == c->dv[2];
     A.wpsi = c->wpsi;
+    A.vtab = c->vtab;
     A.gmask = c->gmask;
     A.ghost = c->ghost;
     A.param = c->param;
@@ -309,6 +311,7 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.ftab = c->ftab;
     A.fbase = c->fbase;
     A.rhowu = c->rhowu32;
+    A.err = c->err;
     return A;
 }
 
@@ -631,6 +634,8 @@ int read_status(bgk_ctx *c)
         return fail(c, BGK_EDOMAIN, "non-physical state (rho <= 0, theta <= 0 or NaN) met on the device");
     if (c->sticky & kErrNewton)
         return fail(c, BGK_ENEWTON, "conservative-Maxwellian Newton solve did not converge at some point");
+    if (c->sticky & kErrTimeout)
+        return fail(c, BGK_ETIMEOUT, "a bounded device wait for an asynchronous copy gave up");
     return BGK_OK;
 }
 
@@ -652,7 +657,7 @@ void bgk_destroy(bgk_ctx *c)
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
     }
-    void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
+    void *bufs[] = {c->fA, c->pool, c->xi, c->mi, c->vtab, c->toct, c->wpsi, c->gmask, c->ghost, c->slotk_d, c->partial,
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
                     c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase, c->wn64,
@@ -829,7 +834,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     const int64_t fA = (int64_t)c->nvt * E * c->NP * kWarp;
     const int64_t need = (fA + (int64_t)(c->chunks.size() + 1) * c->chunk_floats) * c->esize +
                          (int64_t)c->max_groups * 5 * c->npts * 4 + c->npts * (5 * 8 * 3 + kParamStride * 4) +
-                         (int64_t)c->nslots * 4 * 20;
+                         (int64_t)c->nslots * 4 * 25;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
         return bail(BGK_ECUDA, "cudaMemGetInfo failed (no CUDA device?)");
@@ -860,6 +865,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     AL(c->mi, 3 * c->nslots);
     AL(c->toct, c->nvt);
     AL(c->wpsi, 5 * c->nslots);
+    AL(c->vtab, 5 * c->nslots);
     AL(c->gmask, c->nslots);
     AL(c->ghost, 6 * c->nslots);
     AL(c->slotk_d, c->nslots);
@@ -887,6 +893,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
 #undef AL
     // velocity tables
     std::vector<float> xi(3 * c->nslots), mi(3 * c->nslots), wpsi(5 * c->nslots), gm(c->nslots), gh(6 * c->nslots, 0.f);
+    std::vector<float> vtab(5 * c->nslots);
     std::vector<double> xi64(3 * c->nslots), wpsi64(5 * c->nslots), gh64(6 * c->nslots, 0.0), w64h(c->nslots);
     std::vector<float> w32h(c->nslots);
     double win[6] = {0, 0, 0, 0, 0, 0};
@@ -922,6 +929,10 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
             wpsi[((int64_t)vt * 5 + q) * kWarp + l] = (float)(W * pi[q]);
             wpsi64[(int64_t)s * 5 + q] = w * ps[q];
         }
+        for (int d = 0; d < 3; d++)
+            vtab[((int64_t)vt * 5 + d) * kWarp + l] = (float)m[d];
+        vtab[((int64_t)vt * 5 + 3) * kWarp + l] = (float)(W * pi[0]);
+        vtab[((int64_t)vt * 5 + 4) * kWarp + l] = (float)(W * pi[4]);
         gm[s] = real ? 1.f : 0.f;
         w32h[s] = (float)w;
         w64h[s] = w;
@@ -948,6 +959,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         (rc = cudaMemcpy(c->mi, mi.data(), mi.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->toct, c->toct_h.data(), c->toct_h.size(), cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->wpsi, wpsi.data(), wpsi.size() * 4, cudaMemcpyHostToDevice)) ||
+        (rc = cudaMemcpy(c->vtab, vtab.data(), vtab.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->gmask, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->ghost, gh.data(), gh.size() * 4, cudaMemcpyHostToDevice)) ||
         (rc = cudaMemcpy(c->slotk_d, c->slotk.data(), c->slotk.size() * 4, cudaMemcpyHostToDevice)) ||

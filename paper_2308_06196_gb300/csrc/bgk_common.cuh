@@ -21,6 +21,7 @@ constexpr float kExp2Magic = 12582912.0f;  // 1.5 * 2^23, the rounding constant 
 // error bits of the device status word
 constexpr int kErrDomain = 1;
 constexpr int kErrNewton = 2;
+constexpr int kErrTimeout = 4;  // a bounded device wait (an asynchronous copy's barrier) gave up
 
 // FR reference operators on [-1, 1] in FP32 (Sec. 2.1, Eqs. 7-9), merged for the upwind side:
 //   left inflow  (xi_d > 0): d_i = sum_{j>=1} DL[i][j] (f_j - f_0) + gl[i] (t_up - f_0)
@@ -52,6 +53,8 @@ struct StageArgs {
     const float *mi;     // [3][nslots] centred grid index m_d = 2 k_d - (n_d - 1) of every device slot
                          // (an integer, exact in FP32): xi_d = vc[d] + vs[d] m_d
     const float *wpsi;   // [nvt][5][32] w * (1, xi, |xi|^2/2), 0 on padded slots
+    const float *vtab;   // [nvt][5][32] m_x, m_y, m_z, W, W sum_d r_d m_d^2 (rows 1 and 5 of the index-basis
+                         // weights): the per-tile velocity table of the staged hexahedral kernel
     const float *gmask;  // [nslots] 1 for real velocities, 0 for padding
     const unsigned char *toct;  // [nvt] sign octant of every tile (bit d: xi_d >= 0)
     const float *ghost;  // [6][nslots] Dirichlet ghost values (sampled Maxwellian), or null
@@ -94,6 +97,7 @@ struct StageArgs {
                          // the face in the wall list when it is a diffuse wall, else -1)
     const float *rhowu;  // [nwall][N1^2] wall densities of the unstructured mesh's wall faces, or null
     const unsigned char *fbase;  // [E][6][N1^2] the neighbour's first node on the line through each face point
+    int *err;            // device status word (atomicOr of the kErr* bits)
 };
 
 struct NewtonArgs {

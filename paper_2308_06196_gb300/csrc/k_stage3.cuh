@@ -1,6 +1,7 @@
 // k_stage3.cuh -- the fused SSP-RK3 stage kernel for hexahedra (FP32-split form); instantiated per
 // degree in k_stage3_p*.cu so the octant variants compile in parallel.
 #pragma once
+#include "k_stage3s.cuh"
 #include "stage_common.cuh"
 
 // Resident CTAs per SM the register allocation is sized for (p = 3 lean and general / p = 2 / p = 1).
@@ -659,15 +660,10 @@ cudaError_t launch3(const StageArgs &A, cudaStream_t s)
 template <int N1>
 cudaError_t prepare3()
 {
-    const int s0 = (int)sizeof(Stage3Smem<N1, 0>), s1 = (int)sizeof(Stage3Smem<N1, 1>);
+    const int s0 = (int)sizeof(Stage3Smem<N1, 0>);
     cudaError_t e = cudaFuncSetAttribute(k_stage3<N1, 1, 8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0);
-#define BGK_P3(O)                                                                                         \
-    if (e == cudaSuccess)                                                                                 \
-        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0); \
-    if (e == cudaSuccess)                                                                                 \
-        e = cudaFuncSetAttribute(k_stage3<N1, 0, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-    BGK_P3(0) BGK_P3(1) BGK_P3(2) BGK_P3(3) BGK_P3(4) BGK_P3(5) BGK_P3(6) BGK_P3(7) BGK_P3(8)
-#undef BGK_P3
+    if (e == cudaSuccess)
+        e = prepare3s<N1>();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stage3_smem_bytes<N1, 1, 1>());
@@ -676,22 +672,6 @@ cudaError_t prepare3()
                                  stage3_smem_bytes<N1, 1, 2>());
 
     return e;
-}
-
-template <int N1, int GEN>
-cudaError_t launch3_oct(const StageArgs &A, int oct, cudaStream_t s)
-{
-    switch (oct) {
-    case 0: return launch3<N1, 0, 0, GEN>(A, s);
-    case 1: return launch3<N1, 0, 1, GEN>(A, s);
-    case 2: return launch3<N1, 0, 2, GEN>(A, s);
-    case 3: return launch3<N1, 0, 3, GEN>(A, s);
-    case 4: return launch3<N1, 0, 4, GEN>(A, s);
-    case 5: return launch3<N1, 0, 5, GEN>(A, s);
-    case 6: return launch3<N1, 0, 6, GEN>(A, s);
-    case 7: return launch3<N1, 0, 7, GEN>(A, s);
-    default: return launch3<N1, 0, 8, GEN>(A, s);
-    }
 }
 
 // mode 0: stage of octant oct (8 = mixed octants), lean (all periodic, no force) or general form;
@@ -707,7 +687,7 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
     bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
     for (int f = 0; f < 6; f++)
         general = general || A.mesh.bc[f] != 0;
-    return general ? launch3_oct<N1, 1>(A, oct, s) : launch3_oct<N1, 0>(A, oct, s);
+    return general ? launch3s_oct<N1, 1>(A, oct, s) : launch3s_oct<N1, 0>(A, oct, s);
 }
 
 }  // namespace bgk

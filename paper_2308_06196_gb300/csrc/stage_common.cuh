@@ -155,3 +155,71 @@ __device__ __forceinline__ float trace_line(const float (&v)[N1], const Ops &op)
 }
 
 }  // namespace bgk
+
+namespace bgk {
+
+// ------------------------------------------------------------------------------------------------
+// Bulk asynchronous copies (global -> this CTA's shared memory) completed on an mbarrier. One lane
+// arms the barrier with the bytes it is about to copy and issues the copies; every lane that reads
+// the data waits on the barrier's phase first. Source and destination are 16-byte aligned and every
+// size is a multiple of 16 bytes (rows of 32 floats).
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// makes barrier initialisations visible to the asynchronous (bulk-copy) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this thread's earlier generic-proxy shared-memory accesses before later bulk copies
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// the same with a suspend-time hint: a thread whose phase is not complete sleeps in hardware until it
+// completes or hint_ns nanoseconds pass, instead of spinning on issue slots
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of phase `parity`: one plain test, then up to 10^4 sleeping tries of
+// at most 100 us each (about a second in all). After that the timeout bit of the status word is set,
+// so that a copy that never lands cannot hang the GPU; the kernel carries on with whatever the buffer
+// holds (its results are then void and the host reports BGK_ETIMEOUT).
+__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *err)
+{
+    if (mbar_try_wait(bar, parity))
+        return;
+    for (int i = 0; i < 10000; i++)
+        if (mbar_try_wait_sleep(bar, parity, 100000u))
+            return;
+    if (err)
+        atomicOr(err, kErrTimeout);
+}
+
+}  // namespace bgk
