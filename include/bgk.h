@@ -209,6 +209,14 @@ int bgk_set_timing(bgk_ctx *ctx, int on);
 int bgk_timing(bgk_ctx *ctx, double *stage_ms, int64_t *stage_launches, double *newton_ms,
                int64_t *newton_launches, double *stage_alg_bytes);
 
+/* Accuracy measurement between two forms of one discretisation (e.g. the FP32-split form against the
+ * all-FP64 form of the same mesh, degree and velocity grid, Sec. 2.1 Eqs. 7-13): the largest
+ * |f_a - f_b| and the largest |f_b| over every real degree of freedom of the current states, computed
+ * on the device. Waits for b's stream, runs on a's stream and synchronises it. The two contexts must
+ * have the same element count, degree and velocity plan (else BGK_EINVAL); either may be in either
+ * precision. Allocates and frees 16 bytes of device memory per call. */
+int bgk_f_distance(bgk_ctx *a, bgk_ctx *b, double *max_abs_diff, double *max_abs_b);
+
 /* ---------------------------------------------------------------------------------------------
  * Batches of independent problems. The paper runs one problem at a time; the method's steps are
  * the same per member (Sec. 2.1-2.2), only scheduled together: each RK stage of every member runs

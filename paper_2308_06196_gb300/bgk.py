@@ -24,7 +24,7 @@ SYMBOLS = (
     "bgk_create", "bgk_destroy", "bgk_last_error", "bgk_set_stream", "bgk_info", "bgk_points",
     "bgk_set_state", "bgk_set_state_device", "bgk_set_f", "bgk_get_f", "bgk_step", "bgk_moments",
     "bgk_moments_device", "bgk_equilibrium", "bgk_synchronize", "bgk_dt", "bgk_set_timing", "bgk_timing",
-    "bgk_equilibrium_noalloc", "bgk_autotune", "bgk_set_geometry", "bgk_set_connectivity",
+    "bgk_equilibrium_noalloc", "bgk_autotune", "bgk_set_geometry", "bgk_set_connectivity", "bgk_f_distance",
     "bgk_batch_create", "bgk_batch_destroy", "bgk_batch_last_error", "bgk_batch_set_stream", "bgk_batch_step",
     "bgk_batch_synchronize", "bgk_batch_autotune", "bgk_batch_info", "bgk_batch_set_timing", "bgk_batch_timing",
 )
@@ -89,6 +89,7 @@ def lib():
             L.bgk_timing.argtypes = [vp, dp, i64p, dp, i64p, dp]
             L.bgk_equilibrium_noalloc.argtypes = [vp, C.c_int64, C.POINTER(bgk_vgrid), vp, vp, vp]
             L.bgk_autotune.argtypes = [vp, C.POINTER(C.c_int)]
+            L.bgk_f_distance.argtypes = [vp, vp, dp, dp]
             L.bgk_set_geometry.argtypes = [vp, C.POINTER(C.c_double)]
             L.bgk_set_connectivity.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.bgk_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
@@ -300,6 +301,12 @@ class Solver:
 
     def set_timing(self, on):
         self._check(lib().bgk_set_timing(self.h, int(bool(on))))
+
+    def f_distance(self, other):
+        """(max |f_self - f_other|, max |f_other|) over every real degree of freedom, on the device."""
+        d, m = C.c_double(), C.c_double()
+        self._check(lib().bgk_f_distance(self.h, other.h, C.byref(d), C.byref(m)))
+        return d.value, m.value
 
     def timing(self):
         sm, nm, by = C.c_double(), C.c_double(), C.c_double()

@@ -44,6 +44,8 @@ cudaError_t launch_init64(double *f, const double *prim, const double *xi, const
                           int nslots, int vdim, int *err, cudaStream_t s);
 cudaError_t launch_convert64(bool to_device, double *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s);
+cudaError_t launch_f_distance(const void *a, bool a64, const void *b, bool b64, const int *slotk, int nvt, int E,
+                              int NP, unsigned long long *out, cudaStream_t s);
 }  // namespace bgk
 
 using namespace bgk;
@@ -1108,6 +1110,32 @@ int bgk_get_f(bgk_ctx *c, double *f)
     if (!c || !f)
         return BGK_EINVAL;
     return convert_impl(c, f, false);
+}
+
+int bgk_f_distance(bgk_ctx *a, bgk_ctx *b, double *max_abs_diff, double *max_abs_b)
+{
+    if (!a || !b || !max_abs_diff || !max_abs_b)
+        return BGK_EINVAL;
+    if (a->E != b->E || a->NP != b->NP || a->nvt != b->nvt || a->nvel != b->nvel || a->slotk != b->slotk)
+        return fail(a, BGK_EINVAL, "bgk_f_distance: the two contexts have different meshes or velocity plans");
+    bgk_ctx *c = a;  // errors are reported on a
+    // both contexts' work before the comparison: b's stream first, then a's, which runs the kernel
+    CK(cudaStreamSynchronize(b->stream));
+    unsigned long long *d = nullptr, h[2] = {0, 0};
+    CK(cudaMalloc(&d, sizeof(h)));
+    cudaError_t e = launch_f_distance(a->prec == BGK_FP64 ? (const void *)a->fA64 : (const void *)a->fA,
+                                      a->prec == BGK_FP64, b->prec == BGK_FP64 ? (const void *)b->fA64 : (const void *)b->fA,
+                                      b->prec == BGK_FP64, a->slotk_d, a->nvt, a->E, a->NP, d, a->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, a->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(a->stream);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return cuda_fail(a, e, "bgk_f_distance");
+    std::memcpy(max_abs_diff, &h[0], sizeof(double));
+    std::memcpy(max_abs_b, &h[1], sizeof(double));
+    return BGK_OK;
 }
 
 int bgk_step(bgk_ctx *c, double dt, int nsteps)

@@ -121,9 +121,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
     // warp one short code path: lane 0 the warp's f_s layer, lanes RZ .. RZ + N1 - 1 the z-upwind
     // neighbour's row groups j = lane - RZ of the warp's z-line slice (rows ix + N1 w + NQ j, landing as
     // ix + N1 j), lane RFN the warp's layer of f^n, lanes RX and RY the x- and y-upwind neighbours' layer
-    // w; lane 0 of warp 0 also the tile's velocity table. A role lane keeps the source of its copy at
+    // w; lane RT of warp 0 the tile's velocity table. A role lane keeps the source of its copy at
     // tile 0 and adds the tile stride; a boundary face (no neighbour) gives only the barrier's arrival.
-    constexpr int RZ = 1, RFN = N1 + 1, RX = N1 + 2, RY = N1 + 3;
+    constexpr int RZ = 1, RFN = N1 + 1, RX = N1 + 2, RY = N1 + 3, RT = N1 + 4;
     const int64_t tstride = (int64_t)E * NP * kWarp;  // floats between consecutive tiles of one element
     auto role_src = [&](const int (&en)[3]) -> const float * {
         if (lane == 0)
@@ -276,18 +276,13 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             }
             const float bx = rwx ? gx * __ldg(rwx + iy) : gx;
             if (l0)
-                line_sums<N1, true>(sv, fl, enx >= 0 ? trace_line<N1, true>(v, A.ops) : bx, A.ops);
+                line_sums_jump<N1, true>(sv, fl, enx >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0], A.ops);
             else
-                line_sums<N1, false>(sv, fl, enx >= 0 ? trace_line<N1, false>(v, A.ops) : bx, A.ops);
+                line_sums_jump<N1, false>(sv, fl, enx >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bx - fl[N1 - 1],
+                                          A.ops);
 #pragma unroll
             for (int j = 0; j < N1; j++)
                 acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
-        }
-        // slot kx is consumed: the next tile's f^n lands there
-        __syncwarp();
-        if (lane == RFN && more && has_fn) {
-            fence_proxy_async();
-            issue_layer(csrc, vl + 1, kx);
         }
         wait(2 + ky);
 #pragma unroll
@@ -300,27 +295,21 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             }
             const float by = rwy ? gy * __ldg(rwy + ix) : gy;
             if (l1)
-                line_sums<N1, true>(sv, fl, eny >= 0 ? trace_line<N1, true>(v, A.ops) : by, A.ops);
+                line_sums_jump<N1, true>(sv, fl, eny >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : by - fl[0], A.ops);
             else
-                line_sums<N1, false>(sv, fl, eny >= 0 ? trace_line<N1, false>(v, A.ops) : by, A.ops);
+                line_sums_jump<N1, false>(sv, fl, eny >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : by - fl[N1 - 1],
+                                          A.ops);
 #pragma unroll
             for (int j = 0; j < N1; j++)
                 acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
         }
-        // slot ky is consumed: the next tile's x-neighbour layer lands there
+        // slots kx and ky are consumed: the next tile's f^n and x-neighbour layer land there
         __syncwarp();
-        if (lane == RX && more) {
+        if (more && ((lane == RFN && has_fn) || lane == RX)) {
             fence_proxy_async();
-            issue_layer(OCT < 8 ? csrc : role_src(enn), vl + 1, ky);
+            issue_layer(lane == RX && OCT == 8 ? role_src(enn) : csrc, vl + 1, lane == RX ? ky : kx);
         }
         __syncthreads();  // B1: every layer of the element tile has landed (each warp waited for its own)
-        // every warp is done with the other table buffer (the previous tile's): the next tile's tables
-        if (w == 0 && lane == 0 && more) {
-            fence_proxy_async();
-            mbar_arrive_expect_tx(tbar(b ^ 1), kTabRows * kRow);
-            bulk_g2s(smem_u32(&sm.tab[b ^ 1][0][0]), A.vtab + (int64_t)(vt + 1) * kTabRows * kWarp,
-                     kTabRows * kRow, tbar(b ^ 1));
-        }
         // z-lines of slice iy = w (all layers) from the shared tile, the upwind trace from the staged
         // neighbour rows; each line's derivative sums overwrite the rows it read
         wait(2 + ka);
@@ -335,18 +324,26 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             }
             const float bz = rwz ? gz * __ldg(rwz + ix) : gz;
             if (l2)
-                line_sums<N1, true>(sv, fl, enz >= 0 ? trace_line<N1, true>(v, A.ops) : bz, A.ops);
+                line_sums_jump<N1, true>(sv, fl, enz >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bz - fl[0], A.ops);
             else
-                line_sums<N1, false>(sv, fl, enz >= 0 ? trace_line<N1, false>(v, A.ops) : bz, A.ops);
+                line_sums_jump<N1, false>(sv, fl, enz >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bz - fl[N1 - 1],
+                                          A.ops);
 #pragma unroll
             for (int j = 0; j < N1; j++)
                 sm.fs[b][q + NQ * j][lane] = sv[j];
         }
-        // slot ka is consumed: the next tile's y-neighbour layer lands there
+        // slot ka is consumed: the next tile's y-neighbour layer lands there; warp 0 also brings the next
+        // tile's velocity table into the other table buffer, which every warp is done with (B1)
         __syncwarp();
-        if (lane == RY && more) {
+        if (more && (lane == RY || (w == 0 && lane == RT))) {
             fence_proxy_async();
-            issue_layer(OCT < 8 ? csrc : role_src(enn), vl + 1, ka);
+            if (lane == RY) {
+                issue_layer(OCT < 8 ? csrc : role_src(enn), vl + 1, ka);
+            } else {
+                mbar_arrive_expect_tx(tbar(b ^ 1), kTabRows * kRow);
+                bulk_g2s(smem_u32(&sm.tab[b ^ 1][0][0]), A.vtab + (int64_t)(vt + 1) * kTabRows * kWarp,
+                         kTabRows * kRow, tbar(b ^ 1));
+            }
         }
         __syncthreads();  // B2: z-sums complete
 #pragma unroll

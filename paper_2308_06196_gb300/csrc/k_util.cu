@@ -185,6 +185,55 @@ cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi
     return cudaGetLastError();
 }
 
+// Largest |a - b| and |b| over the real slots of two distributions stored in the same tile layout
+// (each FP32 or FP64): out[0], out[1] hold the bit patterns of the two non-negative doubles, which
+// order like the unsigned integers (atomicMax).
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) k_f_distance(const TA *__restrict__ a, const TB *__restrict__ b,
+                                                    const int *__restrict__ slotk, int64_t n, int per_tile,
+                                                    unsigned long long *out)
+{
+    double d = 0.0, m = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int lane = (int)(q % kWarp);
+        const int vt = (int)(q / per_tile);
+        if (__ldg(slotk + vt * kWarp + lane) < 0)
+            continue;
+        const double x = (double)a[q], y = (double)b[q];
+        d = fmax(d, fabs(x - y));
+        m = fmax(m, fabs(y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(d));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+cudaError_t launch_f_distance(const void *a, bool a64, const void *b, bool b64, const int *slotk, int nvt, int E,
+                              int NP, unsigned long long *out, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nvt * E * NP * kWarp;
+    const int per_tile = E * NP * kWarp;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess)
+        return e;
+    if (a64 && b64)
+        k_f_distance<<<blocks, threads, 0, s>>>((const double *)a, (const double *)b, slotk, n, per_tile, out);
+    else if (a64)
+        k_f_distance<<<blocks, threads, 0, s>>>((const double *)a, (const float *)b, slotk, n, per_tile, out);
+    else if (b64)
+        k_f_distance<<<blocks, threads, 0, s>>>((const float *)a, (const double *)b, slotk, n, per_tile, out);
+    else
+        k_f_distance<<<blocks, threads, 0, s>>>((const float *)a, (const float *)b, slotk, n, per_tile, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_convert_f(bool to_device, float *f, double *st, const int *slotk, int nvt, int E, int NP,
                              int64_t nvel, int p0, int npt, cudaStream_t s)
 {

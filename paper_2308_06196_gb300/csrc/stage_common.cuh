@@ -80,6 +80,40 @@ __device__ __forceinline__ void line_sums(float (&s)[N1], const float (&fl)[N1],
     }
 }
 
+// line_sums with the jump tr = T - f_R at the inflow face given (see trace_jump)
+template <int N1, bool LEFT>
+__device__ __forceinline__ void line_sums_jump(float (&s)[N1], const float (&fl)[N1], float tr, const Ops &op)
+{
+    constexpr int R = LEFT ? 0 : N1 - 1;
+    const float fr = fl[R];
+    float G[N1];
+#pragma unroll
+    for (int j = 0; j < N1; j++)
+        G[j] = fl[j] - fr;
+#pragma unroll
+    for (int i = 0; i < N1; i++) {
+        float v = (LEFT ? op.gl[i] : op.gr[i]) * tr;
+#pragma unroll
+        for (int j = 0; j < N1; j++)
+            if (j != R)
+                v = fmaf(LEFT ? op.DL[i][j] : op.DR[i][j], G[j], v);
+        s[i] = v;
+    }
+}
+
+// The jump T - f_R between the upwind neighbour line v's trace (a left neighbour at its +1 end, a right
+// one at its -1 end) and this line's inflow value fr, in difference form: (v_0 - f_R) + sum_{j>=1}
+// l_j (v_j - v_0), exactly 0 when both lines hold one constant.
+template <int N1, bool LEFT>
+__device__ __forceinline__ float trace_jump(const float (&v)[N1], float fr, const Ops &op)
+{
+    float t = v[0] - fr;
+#pragma unroll
+    for (int j = 1; j < N1; j++)
+        t = fmaf(LEFT ? op.lp[j] : op.lm[j], v[j] - v[0], t);
+    return t;
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
