@@ -540,6 +540,183 @@ def bench_ablation() -> dict:
             "mass and energy", **out}
 
 
+def moment_scales(Q):
+    """Component scales of the moment distance: rho for mass, rho sqrt(theta) for momentum (a component
+    of the mean velocity can vanish identically), E for energy; theta with the velocity dimension 3."""
+    rho = Q[:, 0]
+    th = (2.0 / 3.0) * (Q[:, 4] / rho - 0.5 * (Q[:, 1:4] ** 2).sum(1) / rho**2)
+    return np.array([rho.max()] + [(rho * np.sqrt(th)).max()] * 3 + [np.abs(Q[:, 4]).max()])
+
+
+def pair_accuracy(make, prim_fn, steps: int, dt_cfl: float, stream, torch) -> dict:
+    """One workload in the FP32-split and the all-FP64 form from the same state for the same steps:
+    both forms' ms per step, and the FP32-split form's distance from the FP64 one in the moments
+    (largest scaled component difference) and in f (max |f32 - f64| / max |f64|, on the device)."""
+    from paper_2308_06196_gb300.bgk import FP64
+
+    out = {}
+    sol = {}
+    for name, prec in (("fp32_split", 0), ("fp64", FP64)):
+        s = make(prec)
+        s.set_stream(stream.cuda_stream)
+        s.set_state(prim_fn(s.points()))
+        if prec == 0:
+            s.autotune()
+        dt = s.dt(dt_cfl) if name == "fp32_split" else out["dt"]
+        out["dt"] = dt
+        s.step(dt, 1)  # graph capture, timed with the rest below as part of the run
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(dt, steps - 1)
+        e1.record(stream)
+        s.synchronize()
+        out[f"{name}_ms_per_step"] = e0.elapsed_time(e1) / max(1, steps - 1)
+        sol[name] = s
+    Q32, Q64 = sol["fp32_split"].moments(), sol["fp64"].moments()
+    df, fm = sol["fp32_split"].f_distance(sol["fp64"])
+    out.update({"dof": sol["fp64"].ndof, "steps": steps,
+                "moments_max_rel_diff": float((np.abs(Q32 - Q64).max(axis=0) / moment_scales(Q64)).max()),
+                "f_max_abs_diff_rel": df / fm,
+                "speedup_of_fp32_split": out["fp64_ms_per_step"] / out["fp32_split_ms_per_step"]})
+    for s in sol.values():
+        s.close()
+    return out
+
+
+def bench_accuracy(steps: int, stream, torch, sod_oracle_members: int = 3) -> dict:
+    """The FP32-split form's accuracy after `steps` RK steps, per workload, against the all-FP64 GPU form
+    (and, for the line workloads, the FP64 CPU oracle), with the time per step of both forms:
+    the Taylor-Green box and the channel at full size; the Mach-5 duct on its one-element-wide form
+    (y/z-homogeneous, so it stands for the full duct, whose own moments are compared with the FP64 duct
+    too); the Sod ensemble as one FP32-split batch against its members one after another in the FP64 form,
+    and a few members against the oracle; the 1-D periodic workload against the oracle."""
+    from paper_2308_06196_gb300.bgk import FP64, Batch, Solver
+
+    res = {"steps": steps, "tolerance_moments": 1e-5}
+    c = W.config("taylor_green")
+    k = W.mesh_kwargs(c)
+    res["taylor_green"] = pair_accuracy(
+        lambda prec: Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"],
+                            precision=prec), lambda x: W.prim_field("taylor_green", x), steps, c["cfl"], stream, torch)
+    c = W.config("channel")
+    k = W.mesh_kwargs(c)
+    res["channel"] = pair_accuracy(
+        lambda prec: Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"],
+                            bc=c["bc"], bc_state=c["bc_state"], body_force=c["force"], precision=prec),
+        lambda x: W.prim_field("channel", x), steps, c["cfl"], stream, torch)
+    # Mach 5: the one-element-wide duct in both forms, then the full duct (FP32-split) against it
+    c = W.config("mach5")
+    bc, bcs = W.mach5_bc(c)
+    ne = c["nelem"]
+    hy = (c["hi"][1] - c["lo"][1]) / ne[1]
+    cn = dict(c, nelem=(ne[0], 1, 1), hi=(c["hi"][0], hy, hy))
+    kn = W.mesh_kwargs(cn)
+    m5 = pair_accuracy(
+        lambda prec: Solver(kn["dim"], kn["nelem"], kn["lo"], kn["hi"], kn["p"], kn["nv"], kn["vlo"], kn["vhi"],
+                            kn["tau"], bc=bc, bc_state=bcs, limiter=True, precision=prec),
+        lambda x: W.prim_mach5(x, cn), steps, c["cfl"], stream, torch)
+    m5["mesh"] = f"{ne[0]}x1x1 hex p=2 (the duct's y/z-homogeneous form)"
+    k = W.mesh_kwargs(c)
+    s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"], bc=bc,
+               bc_state=bcs, limiter=True)
+    s.set_stream(stream.cuda_stream)
+    s.set_state(W.prim_mach5(s.points(), c))
+    s.autotune()
+    s.step(m5["dt"], steps)
+    Q = s.moments()
+    s.close()
+    n1 = c["p"] + 1
+    Qx = Q.reshape(ne[2], ne[1], ne[0], n1, n1, n1, 5).transpose(2, 5, 0, 1, 3, 4, 6).reshape(ne[0], n1, -1, 5)
+    s64 = Solver(kn["dim"], kn["nelem"], kn["lo"], kn["hi"], kn["p"], kn["nv"], kn["vlo"], kn["vhi"], kn["tau"],
+                 bc=bc, bc_state=bcs, limiter=True, precision=FP64)
+    s64.set_stream(stream.cuda_stream)
+    s64.set_state(W.prim_mach5(s64.points(), cn))
+    s64.step(m5["dt"], steps)
+    Q64 = s64.moments().reshape(ne[0], n1, n1, n1, 5)[:, 0, 0, :, :]
+    s64.close()
+    m5["full_duct_moments_max_rel_diff"] = float(
+        (np.abs(Qx - Q64[:, :, None, :]).max(axis=(0, 1, 2)) / moment_scales(Q64.reshape(-1, 5))).max())
+    m5["full_duct_yz_homogeneity_max_abs_diff"] = float(np.abs(Qx - Qx[:, :, :1]).max())
+    res["mach5"] = m5
+    # Sod ensemble: one FP32-split batch, the members one after another in the FP64 form, a few against the oracle
+    cb = W.config("sod_ensemble")
+    members = W.sod_members(**cb)
+    sol, sol64 = [], []
+    for m in members:
+        km = W.mesh_kwargs(m)
+        for prec, lst in ((0, sol), (FP64, sol64)):
+            sm = Solver(km["dim"], km["nelem"], km["lo"], km["hi"], km["p"], km["nv"], km["vlo"], km["vhi"],
+                        km["tau"], bc=m["bc"], bc_state=m["bc_state"], chunks=1, precision=prec)
+            sm.set_stream(stream.cuda_stream)
+            sm.set_state(W.prim_sod(sm.points(), m["left"], m["right"]))
+            lst.append(sm)
+    dts = [sm.dt(cb["cfl"]) for sm in sol]
+    b = Batch(sol)
+    b.set_stream(stream.cuda_stream)
+    b.autotune()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.step(dts, 1)
+    b.synchronize()
+    e0.record(stream)
+    b.step(dts, steps - 1)
+    e1.record(stream)
+    b.synchronize()
+    ms32 = e0.elapsed_time(e1) / max(1, steps - 1)
+    for sm, dt in zip(sol64, dts):
+        sm.step(dt, 1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for sm, dt in zip(sol64, dts):
+        sm.step(dt, steps - 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / max(1, steps - 1)
+    dq = 0.0
+    for sm, sm64 in zip(sol, sol64):
+        q32, q64 = sm.moments(), sm64.moments()
+        dq = max(dq, float((np.abs(q32 - q64).max(axis=0) / moment_scales(q64)).max()))
+    sod = {"members": len(members), "steps": steps, "batched_fp32_split_ms_per_step": ms32,
+           "fp64_members_one_after_another_ms_per_step": ms64, "speedup_of_batched_fp32_split": ms64 / ms32,
+           "moments_max_rel_diff_vs_fp64": dq}
+    from oracle import oracle as orc
+
+    do = 0.0
+    for q in range(sod_oracle_members):
+        m = members[q]
+        km = W.mesh_kwargs(m)
+        pr = orc.Problem(km["dim"], km["nelem"], km["lo"], km["hi"], km["p"], km["nv"], km["vlo"], km["vhi"],
+                         km["tau"], bc=np.asarray(m["bc"]).reshape(6), bc_state=np.asarray(m["bc_state"]).reshape(6, 5))
+        pr.set_state(W.prim_sod(pr.points(), m["left"], m["right"]))
+        pr.step(dts[q], steps)
+        qo = pr.moments()
+        do = max(do, float((np.abs(sol[q].moments() - qo).max(axis=0) / moment_scales(qo)).max()))
+    sod["oracle_members"] = sod_oracle_members
+    sod["moments_max_rel_diff_vs_oracle"] = do
+    b.close()
+    for sm in sol + sol64:
+        sm.close()
+    res["sod_ensemble"] = sod
+    # the 1-D periodic workload against the oracle (moments and f)
+    c = W.config("periodic1d")
+    k = W.mesh_kwargs(c)
+    s = Solver(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
+    pr = orc.Problem(k["dim"], k["nelem"], k["lo"], k["hi"], k["p"], k["nv"], k["vlo"], k["vhi"], k["tau"])
+    prim = W.prim_field("periodic1d", pr.points())
+    s.set_state(prim)
+    pr.set_state(prim)
+    dt = pr.dt(c["cfl"])
+    s.step(dt, steps)
+    pr.step(dt, steps)
+    Qg, Qo = s.moments(), pr.moments()
+    fg, fo = s.get_f(), pr.get_f()
+    s.close()
+    res["periodic1d"] = {"steps": steps, "dt": dt,
+                         "moments_max_rel_diff_vs_oracle": float((np.abs(Qg - Qo).max(axis=0) / moment_scales(Qo)).max()),
+                         "f_max_abs_diff_rel_vs_oracle": float(np.abs(fg - fo).max() / np.abs(fo).max())}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,6 +747,10 @@ def main():
                     help="steps of the m = 2 planar shear workload (0: skip)")
     ap.add_argument("--batch-members", type=int, default=0,
                     help="members of the Sod ensemble (default: the workload's 256); smaller for profiling")
+    ap.add_argument("--accuracy-steps", type=int, default=0,
+                    help="steps of the per-workload accuracy comparison of the FP32-split form against the "
+                         "all-FP64 GPU form and the oracle (0: skip; 100 is the stated tolerance's horizon, "
+                         "about 10 minutes)")
     ap.add_argument("--elements", type=int, default=0,
                     help="elements per direction (default: the workload's 16); smaller cases for profiling")
     args = ap.parse_args()
@@ -720,6 +901,9 @@ def main():
     if args.mach5_steps > 0 and world == 1:
         mach5 = bench_mach5(args.mach5_steps, warmup, stream, torch, args.mach5_yz_elements)
     ablation = None if (args.no_ablation or world > 1) else bench_ablation()
+    accuracy = None
+    if args.accuracy_steps > 0 and world == 1:
+        accuracy = bench_accuracy(args.accuracy_steps, stream, torch)
     channel = None
     if args.channel_steps > 0 and world == 1:
         channel = bench_channel(args.channel_steps, warmup, stream, torch)
@@ -762,7 +946,7 @@ def main():
                    "dof": dof, "tau": c["tau"], "dt": dt, "precision": "f32 storage+advection, f64 Newton",
                    "l2": "inputs larger than L2 (14.5 GB per f array)", "parallelism": f"replicas x{world}",
                    "event_timed_ms_per_step": event_ms, "tiles_per_task": tiles_per_task},
-        "roofline": {"bound": "hbm", "kernel": "k_stage", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": "k_stage3s", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "alg_bytes_per_launch": tm["stage_alg_bytes"], "avg_launch_ms": stage_avg_ms,
@@ -780,6 +964,7 @@ def main():
         "planar": planar,
         "channel": channel,
         "curved": curved,
+        "accuracy": accuracy,
         "clocks": clk.summary(),
     }
     print(json.dumps(line))

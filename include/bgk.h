@@ -49,6 +49,9 @@ extern "C" {
 #define BGK_BC_DIRICHLET 1     /* ghost = sampled continuous Maxwellian of bc_state (rho,u,v,w,T) */
 #define BGK_BC_DIFFUSE_WALL 2  /* ghost = rho_w * M(T_w, U_w), rho_w per face point for zero net discrete
                                   mass flux, recomputed every stage (hexahedral meshes, dim = 3) */
+#define BGK_BC_EXCHANGE 3      /* an x face shared with a neighbouring subdomain of a partitioned mesh: the
+                                  exterior values come from a halo (bgk_set_halo); affine hexahedra in the
+                                  FP32-split form; such a context steps by bgk_stage */
 
 #define BGK_FP32_SPLIT 0
 #define BGK_FP64 1
@@ -208,6 +211,27 @@ int bgk_set_connectivity(bgk_ctx *ctx, const int *nbr, const int *nface, const i
 int bgk_set_timing(bgk_ctx *ctx, int on);
 int bgk_timing(bgk_ctx *ctx, double *stage_ms, int64_t *stage_launches, double *newton_ms,
                int64_t *newton_launches, double *stage_alg_bytes);
+
+/* ---------------------------------------------------------------------------------------------
+ * Spatial domain decomposition (a mesh cut into slabs along x). The upwind common flux (Sec. 2.1,
+ * Eq. 9) is the only coupling between elements, so a slab needs, before every RK stage, only its
+ * x-neighbours' element layers next to the shared faces. For a context with BGK_BC_EXCHANGE x faces:
+ * bgk_halo_floats: the floats of one halo, nvt * ne_y * ne_z * (p+1)^3 * 32 (velocity tiles of 32
+ *   slots, face elements y + ne_y z, nodes, slots: the library's tile layout of f);
+ * bgk_halo_pack: enqueues, on the context stream, copies of the element layers next to the lo and hi x
+ *   faces of the source of stage `stage` (0: f^n, 1 and 2: the previous stages' outputs) into the device
+ *   buffers d_lo, d_hi (caller-owned, halo_floats each; either may be NULL), for the neighbours;
+ * bgk_set_halo: the device buffer holding the neighbour's layer across face 0 (lo) or 1 (hi), read by
+ *   the stage kernel from then on (caller-owned, kept valid while stages run; NULL: the context's own
+ *   zero halo);
+ * bgk_stage: enqueues stage `stage` of an SSP-RK3 step of size dt (the three stages in order make one
+ *   bgk_step; asynchronous on the context stream). Any FP32-split context may step this way; one with
+ *   exchange faces must (bgk_step refuses it), with the halos refreshed before every stage.
+ * ------------------------------------------------------------------------------------------- */
+int bgk_halo_floats(const bgk_ctx *ctx, int64_t *nfloats);
+int bgk_halo_pack(bgk_ctx *ctx, int stage, float *d_lo, float *d_hi);
+int bgk_set_halo(bgk_ctx *ctx, int face, const float *d_halo);
+int bgk_stage(bgk_ctx *ctx, double dt, int stage);
 
 /* Accuracy measurement between two forms of one discretisation (e.g. the FP32-split form against the
  * all-FP64 form of the same mesh, degree and velocity grid, Sec. 2.1 Eqs. 7-13): the largest

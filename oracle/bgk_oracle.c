@@ -58,6 +58,8 @@ struct orc_ctx {
     double xg[MAXN], wg[MAXN], D[MAXN * MAXN], lm[MAXN], lp[MAXN], dgl[MAXN], dgr[MAXN];
     double *f;              /* [npts][nvel] */
     double *ghost;          /* [6][nvel]: Dirichlet ghost Maxwellian, or unit-density wall Maxwellian */
+    double *halo[6];        /* exchange faces: the neighbouring subdomain's element layer [nface][np][nvel] */
+    double *sf1, *sf2;      /* stage sources of oracle_stage (allocated on first use) */
     double newton_tol;
     int newton_max;
     int continuous;         /* 1: g is the sampled continuous Maxwellian of Q (no Newton; ablation) */
@@ -475,6 +477,17 @@ static int64_t ipow(int b, int e)
     return r;
 }
 
+/* Elements on a face of direction d (the product of the other two directions' counts) and the index
+ * of element ec among them: the other two coordinates, lower direction fastest. */
+static int64_t face_count(const orc_ctx *c, int d)
+{
+    return d == 0 ? (int64_t)c->ne[1] * c->ne[2] : (d == 1 ? (int64_t)c->ne[0] * c->ne[2] : (int64_t)c->ne[0] * c->ne[1]);
+}
+static int64_t face_index(const orc_ctx *c, const int *ec, int d)
+{
+    return d == 0 ? ec[1] + (int64_t)c->ne[1] * ec[2] : (d == 1 ? ec[0] + (int64_t)c->ne[0] * ec[2] : ec[0] + (int64_t)c->ne[0] * ec[1]);
+}
+
 orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double *hi, const int *bc,
                        const double *bc_state, int p, const int *nv, const double *vlo,
                        const double *vhi, double tau, const double *force)
@@ -543,6 +556,12 @@ orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double
             }
             for (int64_t k = 0; k < c->nvel; k++)
                 c->ghost[fc * c->nvel + k] = maxwellian(c->vdim, rho, s + 1, s[4], c->xi + 3 * k);
+        } else if (c->bc[fc] == ORC_EXCHANGE) {
+            c->halo[fc] = (double *)calloc((size_t)(face_count(c, fc / 2) * c->np * c->nvel), sizeof(double));
+            if (!c->halo[fc]) {
+                oracle_destroy(c);
+                return NULL;
+            }
         } else if (c->bc[fc] != ORC_PERIODIC) {
             oracle_destroy(c);
             return NULL;
@@ -566,6 +585,10 @@ void oracle_destroy(orc_ctx *c)
     free(c->cn);
     free(c->cf);
     free(c->co);
+    for (int fc = 0; fc < 6; fc++)
+        free(c->halo[fc]);
+    free(c->sf1);
+    free(c->sf2);
     free(c);
 }
 
@@ -801,8 +824,18 @@ static void face_metric(const orc_ctx *c, int64_t e, int d, int side, int ln, do
 static void face_normals(orc_ctx *c);
 static int64_t table_neighbour(const orc_ctx *c, int64_t e, int d, int side, const int *ic, int64_t *nodes, int *sp);
 
+static int has_exchange(const orc_ctx *c)
+{
+    for (int fc = 0; fc < 6; fc++)
+        if (c->bc[fc] == ORC_EXCHANGE)
+            return 1;
+    return 0;
+}
+
 int oracle_set_geometry(orc_ctx *c, const double *x)
 {
+    if (c && has_exchange(c)) /* exchange faces are on the structured affine mesh only */
+        return -1;
     if (!c || !x || c->dim != 3)
         return -1;
     const int nf = c->n1 * c->n1;
@@ -889,6 +922,8 @@ static void face_normals(orc_ctx *c)
 
 int oracle_set_connectivity(orc_ctx *c, const int *nbr, const int *nface, const int *orient)
 {
+    if (c && has_exchange(c))
+        return -1;
     if (!c || !nbr || !nface || !orient || c->dim != 3)
         return -1;
     for (int64_t q = 0; q < c->nelem * 6; q++) {
@@ -991,6 +1026,19 @@ static double exterior_value(const orc_ctx *c, const double *f, const int *ec, i
             return c->ghost[fc * c->nvel + k];
         if (c->bc[fc] == ORC_WALL)
             return rho_w * c->ghost[fc * c->nvel + k];
+        if (c->bc[fc] == ORC_EXCHANGE) {
+            /* the neighbouring subdomain's element across the face, from its halo layer: its trace at
+             * the shared face, as for a neighbour inside the mesh */
+            const double *l = side ? c->lm : c->lp;
+            const double *hl = c->halo[fc] + face_index(c, ec, d) * c->np * c->nvel;
+            double t = 0.0;
+            int jc[3] = {ic[0], ic[1], ic[2]};
+            for (int j = 0; j < c->n1; j++) {
+                jc[d] = j;
+                t += l[j] * hl[(int64_t)node_index(c, jc) * c->nvel + k];
+            }
+            return t;
+        }
         nc[d] = (nc[d] + c->ne[d]) % c->ne[d];
     }
     int64_t en = elem_index(c, nc);
@@ -1304,6 +1352,81 @@ int oracle_step(orc_ctx *c, double dt, int nsteps)
     free(f2);
     free(L);
     return fails ? -fails : 0;
+}
+
+/* One Shu-Osher stage of the SSP-RK3 step of oracle_step, with the same arithmetic: stage 0 forms
+ * f1 = f + dt L(f), stage 1 f2 = 3/4 f + 1/4 (f1 + dt L(f1)), stage 2 f = 1/3 f + 2/3 (f2 + dt L(f2)),
+ * the limiter after each when it is on. Three calls in order equal one oracle_step; between them the
+ * caller may refresh exchange halos from the other subdomains' stage sources (oracle_pack_halo). */
+int oracle_stage(orc_ctx *c, double dt, int stage)
+{
+    if (!c || stage < 0 || stage > 2)
+        return -1;
+    size_t n = (size_t)(c->npts * c->nvel);
+    if (!c->sf1)
+        c->sf1 = (double *)malloc(sizeof(double) * n);
+    if (!c->sf2)
+        c->sf2 = (double *)malloc(sizeof(double) * n);
+    double *L = (double *)malloc(sizeof(double) * n);
+    if (!c->sf1 || !c->sf2 || !L) {
+        free(L);
+        return -1;
+    }
+    double *f = c->f, *f1 = c->sf1, *f2 = c->sf2;
+    int fails = 0;
+    if (stage == 0) {
+        fails += -oracle_rhs(c, f, L);
+#pragma omp parallel for schedule(static)
+        for (size_t q = 0; q < n; q++)
+            f1[q] = f[q] + dt * L[q];
+        if (c->limiter)
+            oracle_limit(c, f1);
+    } else if (stage == 1) {
+        fails += -oracle_rhs(c, f1, L);
+#pragma omp parallel for schedule(static)
+        for (size_t q = 0; q < n; q++)
+            f2[q] = 0.75 * f[q] + 0.25 * (f1[q] + dt * L[q]);
+        if (c->limiter)
+            oracle_limit(c, f2);
+    } else {
+        fails += -oracle_rhs(c, f2, L);
+#pragma omp parallel for schedule(static)
+        for (size_t q = 0; q < n; q++)
+            f[q] = (1.0 / 3.0) * f[q] + (2.0 / 3.0) * (f2[q] + dt * L[q]);
+        if (c->limiter)
+            oracle_limit(c, f);
+    }
+    free(L);
+    return fails ? -fails : 0;
+}
+
+/* The element layer next to face fc (2 d + side) of the source of stage `stage` (0: f, 1: f1, 2: f2):
+ * out[face_index][node][velocity], the data a neighbouring subdomain takes as the halo of its opposite
+ * face. */
+int oracle_pack_halo(const orc_ctx *c, int fc, int stage, double *out)
+{
+    if (!c || fc < 0 || fc >= 2 * c->dim || stage < 0 || stage > 2 || !out || (stage > 0 && !(stage == 1 ? c->sf1 : c->sf2)))
+        return -1;
+    const double *src = stage == 0 ? c->f : (stage == 1 ? c->sf1 : c->sf2);
+    const int d = fc / 2, side = fc % 2;
+    for (int64_t e = 0; e < c->nelem; e++) {
+        int ec[3];
+        elem_coords(c, e, ec);
+        if (ec[d] != (side ? c->ne[d] - 1 : 0))
+            continue;
+        memcpy(out + face_index(c, ec, d) * c->np * c->nvel, src + e * c->np * c->nvel,
+               sizeof(double) * (size_t)(c->np * c->nvel));
+    }
+    return 0;
+}
+
+/* The halo of exchange face fc: in[face_index][node][velocity] (copied). */
+int oracle_set_halo(orc_ctx *c, int fc, const double *in)
+{
+    if (!c || fc < 0 || fc >= 6 || !c->halo[fc] || !in)
+        return -1;
+    memcpy(c->halo[fc], in, sizeof(double) * (size_t)(face_count(c, fc / 2) * c->np * c->nvel));
+    return 0;
 }
 
 double oracle_dt(const orc_ctx *c, double cfl)

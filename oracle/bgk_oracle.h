@@ -46,6 +46,9 @@ extern "C" {
 #define ORC_PERIODIC 0
 #define ORC_DIRICHLET 1
 #define ORC_WALL 2
+/* a face shared with a neighbouring subdomain of a partitioned mesh: its exterior values come from a
+ * halo, the neighbour's element layer next to the shared face (oracle_set_halo) */
+#define ORC_EXCHANGE 3
 
 typedef struct orc_ctx orc_ctx;
 
@@ -65,7 +68,7 @@ int oracle_fr_operators(int p, double *D, double *lm, double *lp, double *dgl, d
 int oracle_velocity_grid(const int *nv, const double *vlo, const double *vhi, double *xi, double *w);
 
 /* Create a problem. dim in {1,2,3}; nelem[dim], lo[dim], hi[dim] describe an affine structured mesh.
- * bc[2*d + side] is ORC_PERIODIC / ORC_DIRICHLET / ORC_WALL; bc_state[(2*d+side)*5 + c] holds
+ * bc[2*d + side] is ORC_PERIODIC / ORC_DIRICHLET / ORC_WALL / ORC_EXCHANGE; bc_state[(2*d+side)*5 + c] holds
  * (rho, u, v, w, T) of a Dirichlet state or (unused, u_w, v_w, w_w, T_w) of a wall.
  * tau <= 0 or tau = +inf switches the collision term off (pure advection).
  * force[3] is a constant body force per unit mass (may be NULL). Returns NULL on error.
@@ -77,6 +80,17 @@ orc_ctx *oracle_create(int dim, const int *nelem, const double *lo, const double
                        const int *nv, const double *vlo, const double *vhi,
                        double tau, const double *force);
 void oracle_destroy(orc_ctx *c);
+
+/* Partitioned meshes (spatial domain decomposition; the upwind common flux of Sec. 2.1, Eq. 9, is the
+ * only coupling between elements, so a subdomain needs, per RK stage, only its neighbours' element
+ * layers next to the shared faces). oracle_stage runs one Shu-Osher stage (0, 1, 2) of the step of
+ * oracle_step with the same arithmetic; oracle_pack_halo writes the element layer next to face fc of
+ * the source of a stage, out[face element][node][velocity] (face elements: the two other coordinates,
+ * the lower direction fastest); oracle_set_halo sets the halo of an ORC_EXCHANGE face (same layout).
+ * Exchange faces need the structured affine mesh (no oracle_set_geometry / oracle_set_connectivity). */
+int oracle_stage(orc_ctx *c, double dt, int stage);
+int oracle_pack_halo(const orc_ctx *c, int fc, int stage, double *out);
+int oracle_set_halo(orc_ctx *c, int fc, const double *in);
 int64_t oracle_npoints(const orc_ctx *c);
 int64_t oracle_nvel(const orc_ctx *c);
 

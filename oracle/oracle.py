@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liborc.so")
 SRC = os.path.join(HERE, "bgk_oracle.c")
 
-PERIODIC, DIRICHLET, WALL = 0, 1, 2
+PERIODIC, DIRICHLET, WALL, EXCHANGE = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -76,6 +76,9 @@ def lib():
             L.oracle_set_geometry.argtypes = [C.c_void_p, dp]
             L.oracle_metric.argtypes = [C.c_void_p, dp, dp]
             L.oracle_set_connectivity.argtypes = [C.c_void_p, ip, ip, ip]
+            L.oracle_stage.argtypes = [C.c_void_p, C.c_double, C.c_int]
+            L.oracle_pack_halo.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
+            L.oracle_set_halo.argtypes = [C.c_void_p, C.c_int, dp]
             _lib = L
     return _lib
 
@@ -250,6 +253,30 @@ class Problem:
         J = np.zeros(self.npts)
         assert lib().oracle_metric(self.h, _d(Ja), _d(J)) == 0
         return Ja, J
+
+    def face_elements(self, fc):
+        """Elements on face fc = 2 d + side (the product of the other directions' counts)."""
+        ne = [max(1, int(n)) for n in self._keep[0]]
+        d = fc // 2
+        return int(np.prod([ne[q] for q in range(3) if q != d]))
+
+    def stage(self, dt, stage):
+        """One Shu-Osher stage (0, 1, 2) of oracle_step's RK3 step."""
+        rc = lib().oracle_stage(self.h, float(dt), int(stage))
+        if rc != 0:
+            raise RuntimeError(f"oracle_stage: {rc}")
+
+    def pack_halo(self, fc, stage):
+        """The element layer next to face fc of the source of `stage`: [face element][node][velocity]."""
+        nel = int(np.prod([max(1, int(n)) for n in self._keep[0]]))
+        out = np.zeros((self.face_elements(fc), self.npts // nel, self.nvel))
+        assert lib().oracle_pack_halo(self.h, int(fc), int(stage), _d(out)) == 0
+        return out
+
+    def set_halo(self, fc, halo):
+        """The halo of exchange face fc, [face element][node][velocity]."""
+        a = _f64(halo)
+        assert lib().oracle_set_halo(self.h, int(fc), _d(a)) == 0
 
     def set_limiter(self, on):
         lib().oracle_set_limiter(self.h, int(bool(on)))

@@ -15,7 +15,7 @@ import numpy as np
 from . import _build
 
 BGK_OK, BGK_EINVAL, BGK_ENOMEM, BGK_ECUDA, BGK_ENEWTON, BGK_EDOMAIN, BGK_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-BC_PERIODIC, BC_DIRICHLET, BC_DIFFUSE_WALL = 0, 1, 2
+BC_PERIODIC, BC_DIRICHLET, BC_DIFFUSE_WALL, BC_EXCHANGE = 0, 1, 2, 3
 FP32_SPLIT, FP64 = 0, 1
 MAXWELLIAN_CONSERVATIVE, MAXWELLIAN_CONTINUOUS = 0, 1
 
@@ -25,6 +25,7 @@ SYMBOLS = (
     "bgk_set_state", "bgk_set_state_device", "bgk_set_f", "bgk_get_f", "bgk_step", "bgk_moments",
     "bgk_moments_device", "bgk_equilibrium", "bgk_synchronize", "bgk_dt", "bgk_set_timing", "bgk_timing",
     "bgk_equilibrium_noalloc", "bgk_autotune", "bgk_set_geometry", "bgk_set_connectivity", "bgk_f_distance",
+    "bgk_halo_floats", "bgk_halo_pack", "bgk_set_halo", "bgk_stage",
     "bgk_batch_create", "bgk_batch_destroy", "bgk_batch_last_error", "bgk_batch_set_stream", "bgk_batch_step",
     "bgk_batch_synchronize", "bgk_batch_autotune", "bgk_batch_info", "bgk_batch_set_timing", "bgk_batch_timing",
 )
@@ -90,6 +91,10 @@ def lib():
             L.bgk_equilibrium_noalloc.argtypes = [vp, C.c_int64, C.POINTER(bgk_vgrid), vp, vp, vp]
             L.bgk_autotune.argtypes = [vp, C.POINTER(C.c_int)]
             L.bgk_f_distance.argtypes = [vp, vp, dp, dp]
+            L.bgk_halo_floats.argtypes = [vp, i64p]
+            L.bgk_halo_pack.argtypes = [vp, C.c_int, vp, vp]
+            L.bgk_set_halo.argtypes = [vp, C.c_int, vp]
+            L.bgk_stage.argtypes = [vp, C.c_double, C.c_int]
             L.bgk_set_geometry.argtypes = [vp, C.POINTER(C.c_double)]
             L.bgk_set_connectivity.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.bgk_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
@@ -301,6 +306,33 @@ class Solver:
 
     def set_timing(self, on):
         self._check(lib().bgk_set_timing(self.h, int(bool(on))))
+
+    def halo_floats(self):
+        n = C.c_int64()
+        self._check(lib().bgk_halo_floats(self.h, C.byref(n)))
+        return n.value
+
+    def halo_pack(self, stage, lo=None, hi=None):
+        """Enqueue copies of the element layers next to the lo / hi x faces of the source of `stage`
+        into the float32 CUDA tensors lo, hi (halo_floats() each; either may be None)."""
+        for t in (lo, hi):
+            if t is not None:
+                assert t.is_cuda and t.dtype.itemsize == 4 and t.is_contiguous() and t.numel() >= self.halo_floats()
+        self._check(lib().bgk_halo_pack(self.h, int(stage), C.c_void_p(lo.data_ptr() if lo is not None else 0),
+                                        C.c_void_p(hi.data_ptr() if hi is not None else 0)))
+
+    def set_halo(self, face, t):
+        """The neighbour's layer across x face 0 (lo) or 1 (hi): a float32 CUDA tensor of halo_floats(),
+        read by the stage kernel while it is set (None: the context's own zero halo)."""
+        if t is not None:
+            assert t.is_cuda and t.dtype.itemsize == 4 and t.is_contiguous() and t.numel() >= self.halo_floats()
+        self._halo = getattr(self, "_halo", [None, None])
+        self._halo[face] = t  # kept alive while the library reads it
+        self._check(lib().bgk_set_halo(self.h, int(face), C.c_void_p(t.data_ptr() if t is not None else 0)))
+
+    def stage(self, dt, stage):
+        """Enqueue stage `stage` (0, 1, 2) of one SSP-RK3 step."""
+        self._check(lib().bgk_stage(self.h, float(dt), int(stage)))
 
     def f_distance(self, other):
         """(max |f_self - f_other|, max |f_other|) over every real degree of freedom, on the device."""

@@ -197,6 +197,11 @@ struct bgk_ctx {
     double *fA64 = nullptr, *pool64 = nullptr, *xi64 = nullptr, *wpsi64 = nullptr, *ghost64 = nullptr, *par64 = nullptr;
     // diffuse walls and body force
     bool has_wall = false, has_force = false;
+    // exchange faces (x faces shared with a neighbouring subdomain): the halos, [nvt][E_face][NP][32]
+    bool has_exchange = false;
+    int64_t halo_floats = 0;
+    float *halo_own[2] = {nullptr, nullptr};   // library-owned halos (zeros until bgk_set_halo)
+    const float *halo[2] = {nullptr, nullptr}; // the halos the stage kernel reads (lo, hi x face)
     double force[3] = {0, 0, 0};
     double inv_in[6] = {0, 0, 0, 0, 0, 0};
     int nfmax = 0;
@@ -314,6 +319,9 @@ StageArgs stage_args(bgk_ctx *c, const Chunk &ch)
     A.fbase = c->fbase;
     A.rhowu = c->rhowu32;
     A.err = c->err;
+    A.halo[0] = c->halo[0];
+    A.halo[1] = c->halo[1];
+    A.eface = c->ne[1] * c->ne[2];
     return A;
 }
 
@@ -569,6 +577,8 @@ int enqueue_step64(bgk_ctx *c, double dt, cudaStream_t s, const std::vector<int>
     return BGK_OK;
 }
 
+int enqueue_stage(bgk_ctx *c, double dt, int st, cudaStream_t s);
+
 // One SSP-RK3 step: three stages, each over all chunks, each followed by the Newton solve.
 int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
 {
@@ -581,6 +591,44 @@ int enqueue_step(bgk_ctx *c, double dt, cudaStream_t s)
     if (c->prec == BGK_FP64)
         return enqueue_step64(c, dt, s, slot1, slot2);
     for (int st = 0; st < 3; st++) {
+        int rc = enqueue_stage(c, dt, st, s);
+        if (rc)
+            return rc;
+    }
+    return BGK_OK;
+}
+
+// Pool slots of the FP32-split stage outputs: chunk q's stage-1 output in slot q, its stage-2 output in
+// slot q - 1 (slot C for chunk 0), which chunk q - 1 has read by then.
+void stage_slots(const bgk_ctx *c, std::vector<int> &slot1, std::vector<int> &slot2)
+{
+    const int C = (int)c->chunks.size();
+    slot1.resize(C);
+    slot2.resize(C);
+    for (int q = 0; q < C; q++) {
+        slot1[q] = q;
+        slot2[q] = q == 0 ? C : q - 1;
+    }
+}
+
+// The source of stage st (0, 1, 2) of chunk q (FP32-split form): f^n, the stage-1 or the stage-2 output.
+float *stage_source(bgk_ctx *c, int q, int st)
+{
+    std::vector<int> slot1, slot2;
+    stage_slots(c, slot1, slot2);
+    if (st == 0)
+        return chunk_ptr(c, c->fA, c->chunks[q].vt0);
+    return c->pool + (int64_t)(st == 1 ? slot1[q] : slot2[q]) * c->chunk_floats;
+}
+
+// Stage st of one SSP-RK3 step of the FP32-split form: the wall densities of the stage source, the stage
+// kernel over every chunk, the Newton solve of the stage output.
+int enqueue_stage(bgk_ctx *c, double dt, int st, cudaStream_t s)
+{
+    const int C = (int)c->chunks.size();
+    std::vector<int> slot1, slot2;
+    stage_slots(c, slot1, slot2);
+    {
         if (c->has_wall) {
             std::vector<const void *> srcs(C);
             for (int q = 0; q < C; q++) {
@@ -663,7 +711,8 @@ void bgk_destroy(bgk_ctx *c)
                     c->param, c->Q, c->prim, c->prim_in, c->err, c->fA64, c->pool64, c->xi64,
                     c->wpsi64, c->ghost64, c->par64, c->rhow32, c->fpar32, c->w32, c->rhow64,
                     c->fpar64, c->w64, c->itau64, c->met, c->fnm, c->iwj, c->ftab, c->fbase, c->wn64,
-                    c->ja64, c->ijac64, c->fnm64, c->wlist, c->wnu, c->rhowu32, c->rhowu64};
+                    c->ja64, c->ijac64, c->fnm64, c->wlist, c->wnu, c->rhowu32, c->rhowu64,
+                    c->halo_own[0], c->halo_own[1]};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -724,8 +773,14 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
                 return bail(BGK_EINVAL, "bad mesh extent");
             for (int s = 0; s < 2; s++) {
                 const int b = mesh->bc[d][s];
-                if (b != BGK_BC_PERIODIC && b != BGK_BC_DIRICHLET && b != BGK_BC_DIFFUSE_WALL)
+                if (b != BGK_BC_PERIODIC && b != BGK_BC_DIRICHLET && b != BGK_BC_DIFFUSE_WALL &&
+                    b != BGK_BC_EXCHANGE)
                     return bail(BGK_EINVAL, "unknown boundary kind");
+                if (b == BGK_BC_EXCHANGE && (d != 0 || c->dim != 3 || c->prec != BGK_FP32_SPLIT))
+                    return bail(BGK_EINVAL, "exchange faces are built for the x faces of hexahedral meshes in the "
+                                            "FP32-split form");
+                if (b == BGK_BC_EXCHANGE)
+                    c->has_exchange = true;
                 if (b == BGK_BC_DIFFUSE_WALL && c->dim != 3)
                     return bail(BGK_EINVAL, "diffuse walls are built for hexahedral meshes (dim = 3)");
                 if (b == BGK_BC_DIFFUSE_WALL)
@@ -836,7 +891,8 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     const int64_t fA = (int64_t)c->nvt * E * c->NP * kWarp;
     const int64_t need = (fA + (int64_t)(c->chunks.size() + 1) * c->chunk_floats) * c->esize +
                          (int64_t)c->max_groups * 5 * c->npts * 4 + c->npts * (5 * 8 * 3 + kParamStride * 4) +
-                         (int64_t)c->nslots * 4 * 25;
+                         (int64_t)c->nslots * 4 * 25 +
+                         (c->has_exchange ? 2 * (int64_t)c->nvt * c->ne[1] * c->ne[2] * c->NP * kWarp * 4 : 0);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
         return bail(BGK_ECUDA, "cudaMemGetInfo failed (no CUDA device?)");
@@ -868,6 +924,14 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
     AL(c->toct, c->nvt);
     AL(c->wpsi, 5 * c->nslots);
     AL(c->vtab, 5 * c->nslots);
+    if (c->has_exchange) {  // halos of the exchange faces, zero until bgk_set_halo
+        c->halo_floats = (int64_t)c->nvt * c->ne[1] * c->ne[2] * c->NP * kWarp;
+        for (int f = 0; f < 2; f++)
+            if (c->bc[f] == BGK_BC_EXCHANGE) {
+                AL(c->halo_own[f], c->halo_floats);
+                c->halo[f] = c->halo_own[f];
+            }
+    }
     AL(c->gmask, c->nslots);
     AL(c->ghost, 6 * c->nslots);
     AL(c->slotk_d, c->nslots);
@@ -939,7 +1003,7 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         w32h[s] = (float)w;
         w64h[s] = w;
         for (int q = 0; q < 6; q++)
-            if (q / 2 < c->dim && c->bc[q] != BGK_BC_PERIODIC && real) {
+            if (q / 2 < c->dim && (c->bc[q] == BGK_BC_DIRICHLET || c->bc[q] == BGK_BC_DIFFUSE_WALL) && real) {
                 // Dirichlet: the prescribed Maxwellian; diffuse wall: the unit-density wall Maxwellian
                 const double *st = c->bcs + 5 * q;
                 const double rho = c->bc[q] == BGK_BC_DIRICHLET ? st[0] : 1.0;
@@ -1138,12 +1202,71 @@ int bgk_f_distance(bgk_ctx *a, bgk_ctx *b, double *max_abs_diff, double *max_abs
     return BGK_OK;
 }
 
+int bgk_halo_floats(const bgk_ctx *c, int64_t *nfloats)
+{
+    if (!c || !nfloats)
+        return BGK_EINVAL;
+    *nfloats = c->halo_floats;
+    return BGK_OK;
+}
+
+int bgk_set_halo(bgk_ctx *c, int face, const float *d_halo)
+{
+    if (!c || face < 0 || face > 1)
+        return BGK_EINVAL;
+    if (c->bc[face] != BGK_BC_EXCHANGE)
+        return fail(c, BGK_EINVAL, "bgk_set_halo: the face is not an exchange face");
+    c->halo[face] = d_halo ? d_halo : c->halo_own[face];
+    return BGK_OK;
+}
+
+int bgk_halo_pack(bgk_ctx *c, int stage, float *d_lo, float *d_hi)
+{
+    if (!c || stage < 0 || stage > 2)
+        return BGK_EINVAL;
+    if (!c->has_exchange || c->prec != BGK_FP32_SPLIT)
+        return fail(c, BGK_EINVAL, "bgk_halo_pack: no exchange faces");
+    const size_t row = (size_t)c->NP * kWarp * sizeof(float);  // one element of one tile
+    const int ef = c->ne[1] * c->ne[2];
+    for (int side = 0; side < 2; side++) {
+        float *dst = side ? d_hi : d_lo;
+        if (!dst)
+            continue;
+        const int ex = side ? c->ne[0] - 1 : 0;
+        for (int q = 0; q < (int)c->chunks.size(); q++) {
+            // rows (tile, face element) of the chunk's stage source: element ex + ne_x r of tile vt, at a
+            // uniform pitch of ne_x elements
+            const float *src = stage_source(c, q, stage) + (int64_t)ex * c->NP * kWarp;
+            float *d = dst + (int64_t)c->chunks[q].vt0 * ef * c->NP * kWarp;
+            CK(cudaMemcpy2DAsync(d, row, src, row * c->ne[0], row, (size_t)c->chunks[q].nvt * ef,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+        }
+    }
+    return BGK_OK;
+}
+
+int bgk_stage(bgk_ctx *c, double dt, int stage)
+{
+    if (!c || stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt))
+        return BGK_EINVAL;
+    if (c->prec != BGK_FP32_SPLIT)
+        return fail(c, BGK_EINVAL, "bgk_stage is built for the FP32-split form");
+    if (c->ftab && !c->met)
+        return fail(c, BGK_EINVAL, "unstructured connectivity needs bgk_set_geometry before stepping");
+    if (c->sticky)
+        return read_status(c);
+    return enqueue_stage(c, dt, stage, c->stream);
+}
+
 int bgk_step(bgk_ctx *c, double dt, int nsteps)
 {
     if (!c || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
         return BGK_EINVAL;
     if (c->ftab && !c->met)  // a connectivity table means nothing without the elements' node coordinates
         return fail(c, BGK_EINVAL, "unstructured connectivity needs bgk_set_geometry before stepping");
+    if (c->has_exchange)  // the halos must be refreshed between the stages
+        return fail(c, BGK_EINVAL, "a context with exchange faces steps by bgk_stage, with a halo exchange before "
+                                   "every stage");
     if (c->sticky)
         return read_status(c);
     if (nsteps == 0)
@@ -1283,6 +1406,8 @@ int bgk_set_connectivity(bgk_ctx *c, const int *nbr, const int *nface, const int
 {
     if (!c || !nbr || !nface || !orient)
         return BGK_EINVAL;
+    if (c->has_exchange)
+        return fail(c, BGK_EINVAL, "exchange faces are built for the affine structured mesh");
     if (c->dim != 3)
         return fail(c, BGK_EINVAL, "unstructured connectivity is built for hexahedra (dim = 3)");
     const int E = c->E, N1 = c->N1, NQ = N1 * N1;
@@ -1364,6 +1489,8 @@ int bgk_set_geometry(bgk_ctx *c, const double *x)
 {
     if (!c || !x)
         return BGK_EINVAL;
+    if (c->has_exchange)
+        return fail(c, BGK_EINVAL, "exchange faces are built for the affine structured mesh");
     if (c->dim != 3)
         return fail(c, BGK_EINVAL, "curvilinear geometry is built for hexahedra (dim = 3)");
     const int NP = c->NP, N1 = c->N1, NQ = N1 * N1, E = c->E;

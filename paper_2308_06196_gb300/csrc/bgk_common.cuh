@@ -98,6 +98,10 @@ struct StageArgs {
     const float *rhowu;  // [nwall][N1^2] wall densities of the unstructured mesh's wall faces, or null
     const unsigned char *fbase;  // [E][6][N1^2] the neighbour's first node on the line through each face point
     int *err;            // device status word (atomicOr of the kErr* bits)
+    // exchange faces (x faces shared with a neighbouring subdomain): the neighbours' element layers next
+    // to the lo and hi x faces, [nvt_total][eface][NP][32] (face element = y + ne_y z), or null
+    const float *halo[2];
+    int eface;           // elements on an x face (ne_y ne_z)
 };
 
 struct NewtonArgs {

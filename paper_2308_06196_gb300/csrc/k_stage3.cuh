@@ -1,5 +1,6 @@
-// k_stage3.cuh -- the fused SSP-RK3 stage kernel for hexahedra (FP32-split form); instantiated per
-// degree in k_stage3_p*.cu so the octant variants compile in parallel.
+// k_stage3.cuh -- the fused SSP-RK3 stage kernel of curvilinear hexahedra (FP32-split form) and the
+// moments-only pass of every hexahedral mesh; affine hexahedra step in k_stage3s.cuh. Instantiated per
+// degree in k_stage3_p*.cu.
 #pragma once
 #include "k_stage3s.cuh"
 #include "stage_common.cuh"
@@ -22,11 +23,11 @@
 namespace bgk {
 
 // ------------------------------------------------------------------------------------------------
-// Hexahedra: one CTA per (element, run of G tiles), one warp per z-layer of the element's nodes.
-// Lane l owns velocity l of the tile. A warp keeps its layer's N1^2 values (f_s, the accumulator and
-// the x/y neighbour lines) in registers, so x and y derivatives are register-local; the z-lines cross
-// the layers and are read from a shared copy of the element tile. The z-upwind traces are split
-// over the warps (warp w interpolates the z-lines with iy = w) and shared the same way.
+// Curvilinear hexahedra: one CTA per (element, run of G tiles), one warp per z-layer of the element's
+// nodes, lane l = velocity l of the tile. A warp keeps its layer's values (f_s and the accumulator) in
+// registers, so the r- and s-lines are register-local; the t-lines cross the layers and are read from a
+// shared copy of the element tile, their sums shared the same way. Exterior traces are loaded per lane
+// where the face flow enters (N . xi decides per lane and face point).
 // ------------------------------------------------------------------------------------------------
 template <int N1, int GEN>
 struct Stage3Smem {
@@ -103,6 +104,7 @@ template <int N1, int MODE, int OCT, int GEN, int CURV = 0>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTAS_P3_GEN : BGK_STAGE3_MINCTAS_P3)
                                                : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
 {
+    static_assert(MODE == 1 || CURV, "affine hexahedra step in k_stage3s");
     constexpr int NQ = N1 * N1;      // nodes per layer
     constexpr int NP = NQ * N1;
     constexpr int NT = kWarp * N1;   // threads
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     ec[1] = (e / A.mesh.ne[0]) % A.mesh.ne[1];
     ec[2] = e / (A.mesh.ne[0] * A.mesh.ne[1]);
 
-    if (MODE == 0) {
+    if constexpr (MODE == 0) {
         constexpr int NH = (NQ + 1) / 2;
         const float *src = A.param + (int64_t)e * NP * kParamStride;
         for (int q = tid; q < N1 * NH * 2 * kParamStride; q += NT) {
@@ -229,39 +231,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
     prefetch(vl0, 0);
     prefetch_fn(vl0);
 
-    // upwind neighbours of a launch that lies in one sign octant: the same for every tile of the task
-    int en_oct[3] = {0, 0, 0};
-    if (OCT < 8)
-#pragma unroll
-        for (int d = 0; d < 3; d++)
-            en_oct[d] = upwind_neighbour(A.mesh, ec, d, ((OCT >> d) & 1) != 0);
-    // upwind neighbour values of the x-lines and y-lines of layer w (affine elements). In a one-octant
-    // launch of the general form the next tile's lines are loaded before this tile's moment pass, whose
-    // registers they share, so that their L2 latency is spent there and not at the start of the next
-    // tile (1 % faster; the lean form is 3 % slower this way, its register budget being tighter).
-    constexpr bool kAheadXY = GEN && !CURV && OCT < 8;
-    float vx[N1][N1], vy[N1][N1];
-    auto load_xy = [&](int vl, int enx, int eny) {
-        if (enx >= 0) {
-            const float *nb = A.src + fidx(vl, enx, 0, lane, E, NP);
-#pragma unroll
-            for (int iy = 0; iy < N1; iy++)
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    vx[iy][j] = __ldg(nb + (j + N1 * iy + NQ * w) * kWarp);
-        }
-        if (eny >= 0) {
-            const float *nb = A.src + fidx(vl, eny, 0, lane, E, NP);
-#pragma unroll
-            for (int ix = 0; ix < N1; ix++)
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    vy[ix][j] = __ldg(nb + (ix + N1 * j + NQ * w) * kWarp);
-        }
-    };
-    if (MODE == 0 && kAheadXY)
-        load_xy(vl0, en_oct[0], en_oct[1]);
-
     for (int vl = vl0; vl < vl1; vl++) {
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
@@ -281,10 +250,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
 #pragma unroll
         for (int q = 0; q < NQ; q++)
             f[q] = sm.tile[b][q + NQ * w][lane];
-        if (MODE == 0) {
-            const bool l0 = OCT < 8 ? (OCT & 1) != 0 : x0 >= 0.f;
-            const bool l1 = OCT < 8 ? (OCT & 2) != 0 : x1 >= 0.f;
-            const bool l2 = OCT < 8 ? (OCT & 4) != 0 : x2 >= 0.f;
+        if constexpr (MODE == 0) {
             float acc[NQ];
             if (has_fn) {
 #pragma unroll
@@ -399,105 +365,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         sm.zc[nd[j]][lane] = sv[j];
                 }
                 __syncthreads();  // B2: z-sums complete
-            } else {
-            // upwind neighbour values: x-lines and y-lines of layer w (loaded ahead in a one-octant
-            // launch of the general form), z-lines of slice iy = w
-            float vz[N1][N1];
-            const int enx = OCT < 8 ? en_oct[0] : upwind_neighbour(A.mesh, ec, 0, l0);
-            const int eny = OCT < 8 ? en_oct[1] : upwind_neighbour(A.mesh, ec, 1, l1);
-            const int enz = OCT < 8 ? en_oct[2] : upwind_neighbour(A.mesh, ec, 2, l2);
-            if (!kAheadXY)
-                load_xy(vl, enx, eny);
-            // acc = an f^n + b (1 - dt/tau) f_s, then x and y lines from registers
-#pragma unroll
-            for (int q = 0; q < NQ; q++) {
-                float kbq = kb;
-                if (GEN && A.vtau)  // variable collision time: b (1 - dt/tau) of this node, see below
-                    kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
-                acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
-            }
-            const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt;
-            // upwind value on a non-periodic face: the Dirichlet ghost Maxwellian, or the diffuse-wall
-            // Maxwellian scaled by the wall density of the face point (face point of every line of
-            // this warp: its index + N1 * w)
-            const int fx = 0 + (l0 ? 0 : 1), fy = 2 + (l1 ? 0 : 1), fz = 4 + (l2 ? 0 : 1);
-            float gx = 0.f, gy = 0.f, gz = 0.f;
-            const float *rwx = nullptr, *rwy = nullptr, *rwz = nullptr;
-            if (GEN) {
-                gx = enx >= 0 ? 0.f : __ldg(A.ghost + fx * A.nslots + slot);
-                gy = eny >= 0 ? 0.f : __ldg(A.ghost + fy * A.nslots + slot);
-                gz = enz >= 0 ? 0.f : __ldg(A.ghost + fz * A.nslots + slot);
-                if (enx < 0 && A.mesh.bc[fx] == 2)
-                    rwx = A.rhow + ((int64_t)fx * A.nfmax + face_elem(A.mesh, ec, 0)) * NQ + N1 * w;
-                if (eny < 0 && A.mesh.bc[fy] == 2)
-                    rwy = A.rhow + ((int64_t)fy * A.nfmax + face_elem(A.mesh, ec, 1)) * NQ + N1 * w;
-                if (enz < 0 && A.mesh.bc[fz] == 2)
-                    rwz = A.rhow + ((int64_t)fz * A.nfmax + face_elem(A.mesh, ec, 2)) * NQ + N1 * w;
-            }
-#pragma unroll
-            for (int iy = 0; iy < N1; iy++) {
-                float fl[N1], sv[N1];
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    fl[j] = f[j + N1 * iy];
-                const float bx = rwx ? gx * __ldg(rwx + iy) : gx;
-                if (l0)
-                    line_sums<N1, true>(sv, fl, enx >= 0 ? trace_line<N1, true>(vx[iy], A.ops) : bx, A.ops);
-                else
-                    line_sums<N1, false>(sv, fl, enx >= 0 ? trace_line<N1, false>(vx[iy], A.ops) : bx, A.ops);
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
-            }
-#pragma unroll
-            for (int ix = 0; ix < N1; ix++) {
-                float fl[N1], sv[N1];
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    fl[j] = f[ix + N1 * j];
-                const float by = rwy ? gy * __ldg(rwy + ix) : gy;
-                if (l1)
-                    line_sums<N1, true>(sv, fl, eny >= 0 ? trace_line<N1, true>(vy[ix], A.ops) : by, A.ops);
-                else
-                    line_sums<N1, false>(sv, fl, eny >= 0 ? trace_line<N1, false>(vy[ix], A.ops) : by, A.ops);
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
-            }
-            // the z-neighbour lines (slice iy = w) are loaded only now, so that their registers are
-            // not live across the x and y lines; the barrier covers part of their latency
-            if (enz >= 0) {
-                const float *nb = A.src + fidx(vl, enz, 0, lane, E, NP);
-#pragma unroll
-                for (int ix = 0; ix < N1; ix++)
-#pragma unroll
-                    for (int j = 0; j < N1; j++)
-                        vz[ix][j] = __ldg(nb + (ix + N1 * w + NQ * j) * kWarp);
-            }
-            __syncthreads();  // B1: the element tile is complete
-            if (w == 0) {
-#pragma unroll
-                for (int c = 0; c < 5; c++)
-                    sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
-            }
-            // z-lines of slice iy = w (all layers), from the shared tile; results to zc
-#pragma unroll
-            for (int ix = 0; ix < N1; ix++) {
-                const int q = ix + N1 * w;
-                float fl[N1], sv[N1];
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    fl[j] = sm.tile[b][q + NQ * j][lane];
-                const float bz = rwz ? gz * __ldg(rwz + ix) : gz;
-                if (l2)
-                    line_sums<N1, true>(sv, fl, enz >= 0 ? trace_line<N1, true>(vz[ix], A.ops) : bz, A.ops);
-                else
-                    line_sums<N1, false>(sv, fl, enz >= 0 ? trace_line<N1, false>(vz[ix], A.ops) : bz, A.ops);
-#pragma unroll
-                for (int j = 0; j < N1; j++)
-                    sm.zc[q + NQ * j][lane] = sv[j];
-            }
-            __syncthreads();  // B2: z-sums complete
             }
             // BGK source towards the conservative Maxwellian, Shu-Osher combination, store
             const float gm = __ldg(A.gmask + slot);
@@ -580,8 +447,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     __stcs(dst + (q + NQ * w) * kWarp, o);
                 }
             }
-            if (kAheadXY && vl + 1 < vl1)  // the next tile's x/y neighbour lines (see load_xy)
-                load_xy(vl + 1, en_oct[0], en_oct[1]);
         } else {
             __syncthreads();  // B1 (same barrier sequence in both modes)
             if (w == 0) {
@@ -685,8 +550,8 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
         return A.ftab ? launch3<N1, 0, 8, 1, 2>(A, s) : launch3<N1, 0, 8, 1, 1>(A, s);
     // the lean form: periodic faces, no force, no limiter, constant tau, one velocity spacing on all axes
     bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
-    for (int f = 0; f < 6; f++)
-        general = general || A.mesh.bc[f] != 0;
+    for (int f = 0; f < 6; f++)  // Dirichlet or wall faces (exchange faces need only the neighbour's source)
+        general = general || A.mesh.bc[f] == 1 || A.mesh.bc[f] == 2;
     return general ? launch3s_oct<N1, 1>(A, oct, s) : launch3s_oct<N1, 0>(A, oct, s);
 }
 

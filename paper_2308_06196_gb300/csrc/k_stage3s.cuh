@@ -123,9 +123,19 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
     // ix + N1 j), lane RFN the warp's layer of f^n, lanes RX and RY the x- and y-upwind neighbours' layer
     // w; lane RT of warp 0 the tile's velocity table. A role lane keeps the source of its copy at
     // tile 0 and adds the tile stride; a boundary face (no neighbour) gives only the barrier's arrival.
+    // Across an exchange face the x-upwind neighbour is the element of the face's halo (the neighbouring
+    // subdomain's layer, [tile][face element][node][lane]), whose tiles are eface elements apart.
     constexpr int RZ = 1, RFN = N1 + 1, RX = N1 + 2, RY = N1 + 3, RT = N1 + 4;
     const int64_t tstride = (int64_t)E * NP * kWarp;  // floats between consecutive tiles of one element
-    auto role_src = [&](const int (&en)[3]) -> const float * {
+    const int64_t hstride = (int64_t)A.eface * NP * kWarp;
+    int64_t cstride = tstride;  // this lane's stride (hstride for a halo source)
+    auto role_src = [&](const int (&en)[3], int oct) -> const float * {
+        cstride = tstride;
+        if (lane == RX && en[0] == kHaloNeighbour) {
+            cstride = hstride;
+            const int64_t r = ec[1] + (int64_t)A.mesh.ne[1] * ec[2];
+            return A.halo[(oct & 1) ? 0 : 1] + (((int64_t)A.vt0 * A.eface + r) * NP + NQ * w) * kWarp;
+        }
         if (lane == 0)
             return A.src + fidx(0, e, NQ * w, 0, E, NP);
         if (lane >= RZ && lane < RZ + N1)
@@ -145,12 +155,12 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         const uint32_t bb = bar(2 + k);
         mbar_arrive_expect_tx(bb, csrc ? kSlot : 0);
         if (csrc)
-            bulk_g2s(sl0 + k * kSlot, csrc + vl * tstride, kSlot, bb);
+            bulk_g2s(sl0 + k * kSlot, csrc + vl * cstride, kSlot, bb);
     };
 
     int en[3];
     nbrs(vl0, en);
-    const float *csrc = role_src(en);  // this lane's copy source at tile 0 (neighbours of one-octant tasks)
+    const float *csrc = role_src(en, OCT < 8 ? OCT : (int)__ldg(A.toct + A.vt0 + vl0));  // at tile 0
     if (lane == 0) {
         mbar_arrive_expect_tx(bar(0), kSlot);
         bulk_g2s(fs0, csrc + vl0 * tstride, kSlot, bar(0));
@@ -230,7 +240,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         // slot ka is consumed: the z-neighbour's slice lands there
         __syncwarp();
         if (lane >= RZ && lane < RZ + N1) {
-            const float *zs = OCT < 8 ? csrc : role_src(en);
+            const float *zs = OCT < 8 ? csrc : role_src(en, oct);
             const uint32_t bb = bar(2 + ka);
             fence_proxy_async();
             if (lane == RZ)
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         float gx = 0.f, gy = 0.f, gz = 0.f;
         const float *rwx = nullptr, *rwy = nullptr, *rwz = nullptr;
         if (GEN) {
-            gx = enx >= 0 ? 0.f : __ldg(A.ghost + fx * A.nslots + slot);
+            gx = enx != -1 ? 0.f : __ldg(A.ghost + fx * A.nslots + slot);
             gy = eny >= 0 ? 0.f : __ldg(A.ghost + fy * A.nslots + slot);
             gz = enz >= 0 ? 0.f : __ldg(A.ghost + fz * A.nslots + slot);
             if (enx < 0 && A.mesh.bc[fx] == 2)
@@ -276,9 +286,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             }
             const float bx = rwx ? gx * __ldg(rwx + iy) : gx;
             if (l0)
-                line_sums_jump<N1, true>(sv, fl, enx >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0], A.ops);
+                line_sums_jump<N1, true>(sv, fl, enx != -1 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0], A.ops);
             else
-                line_sums_jump<N1, false>(sv, fl, enx >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bx - fl[N1 - 1],
+                line_sums_jump<N1, false>(sv, fl, enx != -1 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bx - fl[N1 - 1],
                                           A.ops);
 #pragma unroll
             for (int j = 0; j < N1; j++)
@@ -307,7 +317,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         __syncwarp();
         if (more && ((lane == RFN && has_fn) || lane == RX)) {
             fence_proxy_async();
-            issue_layer(lane == RX && OCT == 8 ? role_src(enn) : csrc, vl + 1, lane == RX ? ky : kx);
+            issue_layer(lane == RX && OCT == 8 ? role_src(enn, (int)__ldg(A.toct + vt + 1)) : csrc, vl + 1,
+                        lane == RX ? ky : kx);
         }
         __syncthreads();  // B1: every layer of the element tile has landed (each warp waited for its own)
         // z-lines of slice iy = w (all layers) from the shared tile, the upwind trace from the staged
@@ -338,7 +349,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         if (more && (lane == RY || (w == 0 && lane == RT))) {
             fence_proxy_async();
             if (lane == RY) {
-                issue_layer(OCT < 8 ? csrc : role_src(enn), vl + 1, ka);
+                issue_layer(OCT < 8 ? csrc : role_src(enn, (int)__ldg(A.toct + vt + 1)), vl + 1, ka);
             } else {
                 mbar_arrive_expect_tx(tbar(b ^ 1), kTabRows * kRow);
                 bulk_g2s(smem_u32(&sm.tab[b ^ 1][0][0]), A.vtab + (int64_t)(vt + 1) * kTabRows * kWarp,

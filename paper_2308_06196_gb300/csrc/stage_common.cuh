@@ -42,14 +42,19 @@ __device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-// Upwind neighbour of element (ec) in direction d: returns its index, or -1 when the face is a
-// non-periodic domain boundary (then the ghost table supplies the upwind value).
+// Upwind neighbour of element (ec) in direction d: returns its index, -1 when the face is a Dirichlet or
+// diffuse-wall boundary (then the ghost table supplies the upwind value), or kHaloNeighbour when it is
+// an exchange face (the neighbour is the element across it in the halo of that face).
+constexpr int kHaloNeighbour = -2;
 __device__ __forceinline__ int upwind_neighbour(const Mesh &m, const int ec[3], int d, bool left)
 {
     int c[3] = {ec[0], ec[1], ec[2]};
     c[d] += left ? -1 : 1;
     if (c[d] < 0 || c[d] >= m.ne[d]) {
-        if (m.bc[2 * d + (left ? 0 : 1)] != 0)
+        const int b = m.bc[2 * d + (left ? 0 : 1)];
+        if (b == 3)
+            return kHaloNeighbour;
+        if (b != 0)
             return -1;
         c[d] = (c[d] + m.ne[d]) % m.ne[d];
     }
