@@ -3,6 +3,7 @@
 // degree in k_stage3_p*.cu.
 #pragma once
 #include "k_stage3s.cuh"
+#include "k_stage3w.cuh"
 #include "stage_common.cuh"
 
 // Resident CTAs per SM the register allocation is sized for (p = 3 lean and general / p = 2 / p = 1).
@@ -527,8 +528,13 @@ cudaError_t prepare3()
 {
     const int s0 = (int)sizeof(Stage3Smem<N1, 0>);
     cudaError_t e = cudaFuncSetAttribute(k_stage3<N1, 1, 8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0);
-    if (e == cudaSuccess)
-        e = prepare3s<N1>();
+    if constexpr (N1 <= 3) {
+        if (e == cudaSuccess)
+            e = prepare3w<N1>();
+    } else {
+        if (e == cudaSuccess)
+            e = prepare3s<N1>();
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stage3_smem_bytes<N1, 1, 1>());
@@ -552,7 +558,10 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
     bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
     for (int f = 0; f < 6; f++)  // Dirichlet or wall faces (exchange faces need only the neighbour's source)
         general = general || A.mesh.bc[f] == 1 || A.mesh.bc[f] == 2;
-    return general ? launch3s_oct<N1, 1>(A, oct, s) : launch3s_oct<N1, 0>(A, oct, s);
+    if constexpr (N1 <= 3)  // p <= 2: one warp per element
+        return general ? launch3w_oct<N1, 1>(A, oct, s) : launch3w_oct<N1, 0>(A, oct, s);
+    else
+        return general ? launch3s_oct<N1, 1>(A, oct, s) : launch3s_oct<N1, 0>(A, oct, s);
 }
 
 }  // namespace bgk
