@@ -5,7 +5,10 @@
 #include "stage_common.cuh"
 
 #ifndef BGK_STAGE3W_WARPS
-#define BGK_STAGE3W_WARPS 2  // elements (warps) per CTA
+#define BGK_STAGE3W_WARPS 1  // elements (warps) per CTA
+#endif
+#ifndef BGK_STAGE3W_MINCTAS_P2
+#define BGK_STAGE3W_MINCTAS_P2 13  // resident CTAs per SM the register allocation is sized for (p = 2)
 #endif
 
 namespace bgk {
@@ -19,28 +22,28 @@ namespace bgk {
 // the per-tile work that does not grow with the nodes (barrier waits, copy issue, the velocity table,
 // the moment pass's row layout) is spread over 27 nodes instead of 9.
 // Shared memory per warp (bulk copies, the warp's own mbarriers):
-//   fs[2]  f_s of the element, double-buffered: tile t lands in fs[t & 1] and is read into registers
-//          at the start of the tile, the next tile lands in the other buffer meanwhile; fs[t & 1] then
-//          takes the tile's output, transposed, for the moment sums;
+//   fs     f_s of the element: read into registers at the start of the tile, after which the next
+//          tile's f_s lands there;
 //   sl[3]  three rotating slots of one element each, as k_stage3s: at tile t slot t mod 3 holds f^n,
 //          slot t+1 the x-upwind neighbour and slot t+2 the y-upwind neighbour; slot t mod 3 then takes
-//          the z-upwind neighbour (read by the z-lines) and each slot the next tile's copies as soon as
-//          it is consumed;
+//          the z-upwind neighbour (read by the z-lines), then the tile's output, transposed, for the
+//          moment sums; each slot takes the next tile's copies as soon as it is consumed;
 //   tab[2] the tile's velocity table (grid indices, W, energy weight), with f_s on its barrier.
 // ------------------------------------------------------------------------------------------------
 template <int N1, int GEN>
 struct __align__(16) Stage3wWarp {  // a multiple of 16 bytes, so every warp's copy targets stay aligned
     static constexpr int NP = N1 * N1 * N1;
-    float fs[2][NP][kWarp];
+    float fs[NP][kWarp];
     float sl[3][NP][kWarp];
     float tab[2][5][kWarp];
     float par[(NP + 1) / 2][kParamStride][2];  // BGK exponents by node pair (the last pair repeats node NP-1)
     float fpar[GEN ? NP : 1][GEN ? kParamStride : 1];
-    unsigned long long bar[5];  // fs[0], fs[1], sl[0..2]
+    unsigned long long bar[5];  // fs and the table of tile parity 0 and 1, sl[0..2]
 };
 
 template <int N1, int OCT, int GEN>
-__global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k_stage3w(const StageArgs A)
+__global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE3W_MINCTAS_P2 : 16))
+    k_stage3w(const StageArgs A)
 {
     constexpr int NQ = N1 * N1;
     constexpr int NP = NQ * N1;
@@ -119,11 +122,11 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k
         }
         return nullptr;
     };
-    const uint32_t fs0 = smem_u32(&sm.fs[0][0][0]), sl0 = smem_u32(&sm.sl[0][0][0]);
+    const uint32_t fs0 = smem_u32(&sm.fs[0][0]), sl0 = smem_u32(&sm.sl[0][0][0]);
     constexpr uint32_t kElem = NP * kRow;
     auto issue_fs = [&](const float *csrc, int vl, int b) {  // lane 0
         mbar_arrive_expect_tx(bar(b), kElem + 5 * kRow);
-        bulk_g2s(fs0 + b * kElem, csrc + vl * tstride, kElem, bar(b));
+        bulk_g2s(fs0, csrc + vl * tstride, kElem, bar(b));
         bulk_g2s(smem_u32(&sm.tab[b][0][0]), A.vtab + (int64_t)(A.vt0 + vl) * 5 * kWarp, 5 * kRow, bar(b));
     };
     auto issue_elem = [&](const float *csrc, int vl, int k) {  // role lanes
@@ -173,12 +176,6 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k
         if (OCT == 8 && vl + 1 < vl1)
             nbrs(vl + 1, enn);
         const bool more = vl + 1 < vl1;
-        // the other buffer last held the previous tile's output, read by this warp's moment pass
-        __syncwarp();
-        if (lane == 0 && more) {
-            fence_proxy_async();
-            issue_fs(csrc, vl + 1, b ^ 1);
-        }
         const int oct = OCT < 8 ? OCT : (int)__ldg(A.toct + vt);
         const bool l0 = (oct & 1) != 0, l1 = (oct & 2) != 0, l2 = (oct & 4) != 0;
         const int enx = en[0], eny = en[1], enz = en[2];
@@ -189,7 +186,13 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k
         float f[NP];
 #pragma unroll
         for (int q = 0; q < NP; q++)
-            f[q] = sm.fs[b][q][lane];
+            f[q] = sm.fs[q][lane];
+        // f_s is in registers: the next tile's lands in fs
+        __syncwarp();
+        if (lane == 0 && more) {
+            fence_proxy_async();
+            issue_fs(csrc, vl + 1, b ^ 1);
+        }
         float acc[NP];
         if (has_fn) {
             wait(2 + ka);
@@ -301,12 +304,6 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k
             for (int j = 0; j < N1; j++)
                 acc[q + NQ * j] = fmaf(cz, sv[j], acc[q + NQ * j]);
         }
-        // slot ka is consumed: the next tile's y-neighbour lands there
-        __syncwarp();
-        if (lane == RY && more) {
-            fence_proxy_async();
-            issue_elem(OCT < 8 ? csrc : role_src(enn, (int)__ldg(A.toct + vt + 1)), vl + 1, ka);
-        }
         // BGK source towards the conservative Maxwellian, Shu-Osher combination (as k_stage3s)
         const float gm = sm.tab[b][3][lane] != 0.f ? 1.f : 0.f;
         const float cg = A.kg * gm, cf = bdt * gm;
@@ -369,10 +366,11 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k
                     acc[q] = fmaf(beta, acc[q] - mean, mean);
             }
         }
+        __syncwarp();  // every lane's z-lines have read slot ka before it takes the output
 #pragma unroll
         for (int q = 0; q < NP; q++) {
             __stcs(dst + q * kWarp, acc[q]);
-            sm.fs[b][q][lane ^ (4 * (q & 7))] = acc[q];  // for the moments below
+            sm.sl[ka][q][lane ^ (4 * (q & 7))] = acc[q];  // for the moments below (slot ka is consumed)
         }
         // moments of the element's nodes (Eq. 2 with Eq. 12) of the stored values (rows np + 8 h)
         __syncwarp();
@@ -403,7 +401,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k
 #pragma unroll
             for (int h = 0; h < NHR; h++) {
                 const int row = min(np + 8 * h, NP - 1);  // rows past the element: discarded below
-                const float4 v = *reinterpret_cast<const float4 *>(&sm.fs[b][row][kk ^ (4 * (row & 7))]);
+                const float4 v = *reinterpret_cast<const float4 *>(&sm.sl[ka][row][kk ^ (4 * (row & 7))]);
                 const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
 #pragma unroll
                 for (int c = 0; c < 5; c++) {
@@ -417,6 +415,12 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? 5 : 8)) k
 #pragma unroll
             for (int c = 0; c < 5; c++)
                 msum[h][c] += sum2(pm[h][c]);
+        // slot ka is read: the next tile's y-neighbour lands there
+        __syncwarp();
+        if (lane == RY && more) {
+            fence_proxy_async();
+            issue_elem(OCT < 8 ? csrc : role_src(enn, (int)__ldg(A.toct + vt + 1)), vl + 1, ka);
+        }
 #pragma unroll
         for (int d = 0; d < 3; d++)
             en[d] = enn[d];
