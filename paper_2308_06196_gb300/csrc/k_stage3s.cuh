@@ -275,43 +275,96 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             if (enz < 0 && A.mesh.bc[fz] == 2)
                 rwz = A.rhow + ((int64_t)fz * A.nfmax + face_elem(A.mesh, ec, 2)) * NQ + N1 * w;
         }
+        // The three line directions. Where the upwind neighbour of the line ends is an element (not a
+        // Dirichlet or wall ghost) and N1 is even, two adjacent lines run at a time on packed pairs.
+        constexpr bool kPair = N1 % 2 == 0;
         wait(2 + kx);
+        if (kPair && enx != -1) {
 #pragma unroll
-        for (int iy = 0; iy < N1; iy++) {
-            float fl[N1], sv[N1], v[N1];
+            for (int iy = 0; iy < N1; iy += 2) {
+                unsigned long long fl[N1], sv[N1], v[N1];
 #pragma unroll
-            for (int j = 0; j < N1; j++) {
-                fl[j] = f[j + N1 * iy];
-                v[j] = sm.sl[w][kx][j + N1 * iy][lane];
+                for (int j = 0; j < N1; j++) {
+                    fl[j] = pack2(f[j + N1 * iy], f[j + N1 * iy + N1]);
+                    v[j] = pack2(sm.sl[w][kx][j + N1 * iy][lane], sm.sl[w][kx][j + N1 * iy + N1][lane]);
+                }
+                if (l0)
+                    line_sums_jump2<N1, true>(sv, fl, trace_jump2<N1, true>(v, fl[0], A.ops), A.ops);
+                else
+                    line_sums_jump2<N1, false>(sv, fl, trace_jump2<N1, false>(v, fl[N1 - 1], A.ops), A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++) {
+                    float lo, hi;
+                    unpack2(sv[j], lo, hi);
+                    acc[j + N1 * iy] = fmaf(cx, lo, acc[j + N1 * iy]);
+                    acc[j + N1 * iy + N1] = fmaf(cx, hi, acc[j + N1 * iy + N1]);
+                }
             }
-            const float bx = rwx ? gx * __ldg(rwx + iy) : gx;
-            if (l0)
-                line_sums_jump<N1, true>(sv, fl, enx != -1 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0], A.ops);
-            else
-                line_sums_jump<N1, false>(sv, fl, enx != -1 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bx - fl[N1 - 1],
-                                          A.ops);
+        } else {
 #pragma unroll
-            for (int j = 0; j < N1; j++)
-                acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
+            for (int iy = 0; iy < N1; iy++) {
+                float fl[N1], sv[N1], v[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++) {
+                    fl[j] = f[j + N1 * iy];
+                    v[j] = sm.sl[w][kx][j + N1 * iy][lane];
+                }
+                const float bx = rwx ? gx * __ldg(rwx + iy) : gx;
+                if (l0)
+                    line_sums_jump<N1, true>(sv, fl, enx != -1 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0],
+                                             A.ops);
+                else
+                    line_sums_jump<N1, false>(sv, fl,
+                                              enx != -1 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bx - fl[N1 - 1],
+                                              A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
+            }
         }
         wait(2 + ky);
+        if (kPair && eny >= 0) {
 #pragma unroll
-        for (int ix = 0; ix < N1; ix++) {
-            float fl[N1], sv[N1], v[N1];
+            for (int ix = 0; ix < N1; ix += 2) {
+                unsigned long long fl[N1], sv[N1], v[N1];
 #pragma unroll
-            for (int j = 0; j < N1; j++) {
-                fl[j] = f[ix + N1 * j];
-                v[j] = sm.sl[w][ky][ix + N1 * j][lane];
+                for (int j = 0; j < N1; j++) {
+                    fl[j] = pack2(f[ix + N1 * j], f[ix + 1 + N1 * j]);
+                    v[j] = pack2(sm.sl[w][ky][ix + N1 * j][lane], sm.sl[w][ky][ix + 1 + N1 * j][lane]);
+                }
+                if (l1)
+                    line_sums_jump2<N1, true>(sv, fl, trace_jump2<N1, true>(v, fl[0], A.ops), A.ops);
+                else
+                    line_sums_jump2<N1, false>(sv, fl, trace_jump2<N1, false>(v, fl[N1 - 1], A.ops), A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++) {
+                    float lo, hi;
+                    unpack2(sv[j], lo, hi);
+                    acc[ix + N1 * j] = fmaf(cy, lo, acc[ix + N1 * j]);
+                    acc[ix + 1 + N1 * j] = fmaf(cy, hi, acc[ix + 1 + N1 * j]);
+                }
             }
-            const float by = rwy ? gy * __ldg(rwy + ix) : gy;
-            if (l1)
-                line_sums_jump<N1, true>(sv, fl, eny >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : by - fl[0], A.ops);
-            else
-                line_sums_jump<N1, false>(sv, fl, eny >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : by - fl[N1 - 1],
-                                          A.ops);
+        } else {
 #pragma unroll
-            for (int j = 0; j < N1; j++)
-                acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
+            for (int ix = 0; ix < N1; ix++) {
+                float fl[N1], sv[N1], v[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++) {
+                    fl[j] = f[ix + N1 * j];
+                    v[j] = sm.sl[w][ky][ix + N1 * j][lane];
+                }
+                const float by = rwy ? gy * __ldg(rwy + ix) : gy;
+                if (l1)
+                    line_sums_jump<N1, true>(sv, fl, eny >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : by - fl[0],
+                                             A.ops);
+                else
+                    line_sums_jump<N1, false>(sv, fl,
+                                              eny >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : by - fl[N1 - 1],
+                                              A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
+            }
         }
         // slots kx and ky are consumed: the next tile's f^n and x-neighbour layer land there
         __syncwarp();
@@ -324,24 +377,50 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         // z-lines of slice iy = w (all layers) from the shared tile, the upwind trace from the staged
         // neighbour rows; each line's derivative sums overwrite the rows it read
         wait(2 + ka);
+        if (kPair && enz >= 0) {
 #pragma unroll
-        for (int ix = 0; ix < N1; ix++) {
-            const int q = ix + N1 * w;
-            float fl[N1], sv[N1], v[N1];
+            for (int ix = 0; ix < N1; ix += 2) {
+                const int q = ix + N1 * w;
+                unsigned long long fl[N1], sv[N1], v[N1];
 #pragma unroll
-            for (int j = 0; j < N1; j++) {
-                fl[j] = sm.fs[b][q + NQ * j][lane];
-                v[j] = sm.sl[w][ka][ix + N1 * j][lane];
+                for (int j = 0; j < N1; j++) {
+                    fl[j] = pack2(sm.fs[b][q + NQ * j][lane], sm.fs[b][q + 1 + NQ * j][lane]);
+                    v[j] = pack2(sm.sl[w][ka][ix + N1 * j][lane], sm.sl[w][ka][ix + 1 + N1 * j][lane]);
+                }
+                if (l2)
+                    line_sums_jump2<N1, true>(sv, fl, trace_jump2<N1, true>(v, fl[0], A.ops), A.ops);
+                else
+                    line_sums_jump2<N1, false>(sv, fl, trace_jump2<N1, false>(v, fl[N1 - 1], A.ops), A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++) {
+                    float lo, hi;
+                    unpack2(sv[j], lo, hi);
+                    sm.fs[b][q + NQ * j][lane] = lo;
+                    sm.fs[b][q + 1 + NQ * j][lane] = hi;
+                }
             }
-            const float bz = rwz ? gz * __ldg(rwz + ix) : gz;
-            if (l2)
-                line_sums_jump<N1, true>(sv, fl, enz >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bz - fl[0], A.ops);
-            else
-                line_sums_jump<N1, false>(sv, fl, enz >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bz - fl[N1 - 1],
-                                          A.ops);
+        } else {
 #pragma unroll
-            for (int j = 0; j < N1; j++)
-                sm.fs[b][q + NQ * j][lane] = sv[j];
+            for (int ix = 0; ix < N1; ix++) {
+                const int q = ix + N1 * w;
+                float fl[N1], sv[N1], v[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++) {
+                    fl[j] = sm.fs[b][q + NQ * j][lane];
+                    v[j] = sm.sl[w][ka][ix + N1 * j][lane];
+                }
+                const float bz = rwz ? gz * __ldg(rwz + ix) : gz;
+                if (l2)
+                    line_sums_jump<N1, true>(sv, fl, enz >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bz - fl[0],
+                                             A.ops);
+                else
+                    line_sums_jump<N1, false>(sv, fl,
+                                              enz >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bz - fl[N1 - 1],
+                                              A.ops);
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    sm.fs[b][q + NQ * j][lane] = sv[j];
+            }
         }
         // slot ka is consumed: the next tile's y-neighbour layer lands there; warp 0 also brings the next
         // tile's velocity table into the other table buffer, which every warp is done with (B1)

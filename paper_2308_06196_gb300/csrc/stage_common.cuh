@@ -37,6 +37,12 @@ __device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsign
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
 {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
@@ -117,6 +123,41 @@ __device__ __forceinline__ float trace_jump(const float (&v)[N1], float fr, cons
     for (int j = 1; j < N1; j++)
         t = fmaf(LEFT ? op.lp[j] : op.lm[j], v[j] - v[0], t);
     return t;
+}
+
+// line_sums_jump and trace_jump on two lines at once (the two halves of packed FP32 pairs), for lines
+// of one direction that share the operator: every step is one f32x2 instruction on both lines.
+__device__ __forceinline__ unsigned long long dup2(float c) { return pack2(c, c); }
+
+template <int N1, bool LEFT>
+__device__ __forceinline__ unsigned long long trace_jump2(const unsigned long long (&v)[N1], unsigned long long fr,
+                                                          const Ops &op)
+{
+    unsigned long long t = fsub2(v[0], fr);
+#pragma unroll
+    for (int j = 1; j < N1; j++)
+        t = ffma2(dup2(LEFT ? op.lp[j] : op.lm[j]), fsub2(v[j], v[0]), t);
+    return t;
+}
+
+template <int N1, bool LEFT>
+__device__ __forceinline__ void line_sums_jump2(unsigned long long (&s)[N1], const unsigned long long (&fl)[N1],
+                                                unsigned long long tr, const Ops &op)
+{
+    constexpr int R = LEFT ? 0 : N1 - 1;
+    unsigned long long G[N1];
+#pragma unroll
+    for (int j = 0; j < N1; j++)
+        G[j] = fsub2(fl[j], fl[R]);
+#pragma unroll
+    for (int i = 0; i < N1; i++) {
+        unsigned long long v = fmul2(dup2(LEFT ? op.gl[i] : op.gr[i]), tr);
+#pragma unroll
+        for (int j = 0; j < N1; j++)
+            if (j != R)
+                v = ffma2(dup2(LEFT ? op.DL[i][j] : op.DR[i][j]), G[j], v);
+        s[i] = v;
+    }
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
