@@ -116,7 +116,7 @@ NOMINAL_HBM_GBS = 7900.0  # GB300's nominal HBM3e bandwidth, for context beside 
 def stage_source_sha():
     """Hash of the sources of the hexahedral stage kernel (the counters are void once they change)."""
     h = hashlib.sha256()
-    for fn in ("k_stage3.cuh", "stage_common.cuh", "bgk_common.cuh"):
+    for fn in ("k_stage3s.cuh", "stage_common.cuh", "bgk_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2308_06196_gb300", "csrc", fn), "rb").read())
     return h.hexdigest()
 

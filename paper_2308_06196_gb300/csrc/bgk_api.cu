@@ -839,10 +839,42 @@ int bgk_create(const bgk_mesh *mesh, int p, const bgk_vgrid *vg, double tau, con
         Chunk ch{};
         ch.oct = o;
         ch.vt0 = (int)(c->slotk.size() / kWarp);
+        std::vector<int> ks;
+        ks.reserve(n);
         for (int kz : Z)
             for (int ky : Y)
                 for (int kx : X)
-                    c->slotk.push_back(kx + c->nv[0] * (ky + c->nv[1] * kz));
+                    ks.push_back(kx + c->nv[0] * (ky + c->nv[1] * kz));
+        if (c->dim == 3 && c->nv[0] > 1 && c->nv[1] > 1 && c->nv[2] > 1) {
+            // velocities with one component small against another first: on curved hexahedra these are
+            // the ones whose flow may enter an element through the face its octant does not make upwind
+            // (a face normal tilted against the small component), so they fill a few tiles of their own
+            // instead of a few lanes of every tile. Affine meshes are indifferent to the order.
+            auto ratio = [&](int k) {
+                double a[3];
+                const int kk[3] = {k % c->nv[0], (k / c->nv[0]) % c->nv[1], k / (c->nv[0] * c->nv[1])};
+                for (int d = 0; d < 3; d++)
+                    a[d] = std::fabs(c->vlo[d] + kk[d] * c->dv[d]);
+                double r = 1e300;
+                for (int d = 0; d < 3; d++) {
+                    const double other = std::max(a[(d + 1) % 3], a[(d + 2) % 3]);
+                    if (other > 0.0)
+                        r = std::min(r, a[d] / other);
+                }
+                return r;
+            };
+            std::vector<double> key(ks.size());
+            std::vector<int> order(ks.size());
+            for (size_t i = 0; i < ks.size(); i++) {
+                key[i] = ratio(ks[i]);
+                order[i] = (int)i;
+            }
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+            for (int i : order)
+                c->slotk.push_back(ks[i]);
+        } else {
+            c->slotk.insert(c->slotk.end(), ks.begin(), ks.end());
+        }
         while (c->slotk.size() % kWarp)
             c->slotk.push_back(-1);
         ch.nvt = (int)(c->slotk.size() / kWarp) - ch.vt0;
@@ -2226,8 +2258,7 @@ int bgk_batch_info(const bgk_batch *b, int64_t *npoints, int64_t *ndof, int64_t 
     for (const bgk_ctx *c : b->probs) {
         np += c->npts;
         nd += c->npts * c->nvel;
-        const int nEB = (c->E + kWarpsPerCta - 1) / kWarpsPerCta;
-        nt += (int64_t)nEB * ((c->chunks[0].nvt + c->G - 1) / c->G);
+        nt += stage1d_tasks(stage_args(const_cast<bgk_ctx *>(c), c->chunks[0]));
     }
     if (npoints)
         *npoints = np;

@@ -29,207 +29,197 @@ namespace bgk {
 // FR operators of the line kernel for each p + 1 (they depend on p only), read by the batched launch.
 __constant__ Ops c_ops1d[kMaxN1 + 1];
 
-// Sum of V <= 32 per-lane values over the warp, one total per lane: after the call, lane l of the
-// warp holds sum over lanes of v[l] (v padded with zeros to 32). Five halving exchange steps.
-__device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane)
+// Elements per task of the line kernels: a run of K = 16 / N1 consecutive elements, so that a warp
+// holds at most 16 nodes of every velocity of its tile.
+template <int N1>
+__host__ __device__ constexpr int line_run()
 {
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const bool up = lane & s;
-#pragma unroll
-        for (int j = 0; j < s; j++) {
-            const float send = up ? v[j] : v[j + s];
-            const float keep = up ? v[j + s] : v[j];
-            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-        }
-    }
+    return 16 / N1;
 }
 
-constexpr int kLineDepth = 4;  // tiles in flight per CTA in the line-element stage
-
-// Shared staging of one tile of the line-element stage: f_s and f^n of the CTA's block of elements,
-// the upwind neighbour element just outside the block, and the tile's velocity tables.
+// Shared memory of one warp of the line kernels (bulk copies, the warp's own mbarriers). Per buffer
+// b (tile parity): fs the run's f_s rows between the rows of its two outside neighbours (only the
+// upwind one is copied; the right one's rows follow the run's last real element), fn its f^n rows,
+// tab the tile's velocity table. The barriers come first, at the same place for every N1 (the batched
+// launch steps problems of different degrees through one warp's storage).
 template <int N1>
-struct alignas(16) LineSlot {
-    float fs[kWarpsPerCta][N1][kWarp];
-    float fn[kWarpsPerCta][N1][kWarp];
-    float nb[N1][kWarp];
-    float mi[3][kWarp];
-    float wp[5][kWarp];
-    float gm[kWarp];
-};
-template <int N1>
-struct alignas(16) LineSmem {  // cp.async and the 16-byte parameter loads need 16-byte alignment
-    LineSlot<N1> s[kLineDepth];
-    // BGK exponents of the block's nodes by element and node pair, [element][pair][param][node of the
-    // pair], so that one 16-byte load gives two parameters of both nodes (an odd last pair repeats)
-    float par[kWarpsPerCta][(N1 + 1) / 2][kParamStride][2];
+struct __align__(16) LineWarp {
+    static constexpr int K = line_run<N1>(), NW = K * N1;
+    unsigned long long bar[2];
+    float fs[2][NW + 2 * N1][kWarp];
+    float fn[2][NW][kWarp];
+    float tab[2][5][kWarp];
+    float par[(NW + 1) / 2][kParamStride][2];  // BGK exponents of the run's nodes by pair
 };
 
-// One task of the line-element stage: a block of kWarpsPerCta consecutive elements (warp w takes
-// element eb + w) x a run of G tiles. The CTA streams the tiles through a kLineDepth-deep ring of
-// shared slots (cp.async, kLineDepth - 1 tiles ahead), so every warp reads its element, its upwind
-// neighbour (a sibling's element, or the staged outside neighbour) and the velocity tables from
-// shared memory. MODE 0: full stage. MODE 1: moments of src only (no advection, no store).
-// op: the FR operators of degree N1 - 1. Every thread of the CTA must call it (barriers).
+#ifndef BGK_LINE_WARPS
+#define BGK_LINE_WARPS 4  // warps (independent tasks) per CTA of the line kernels
+#endif
+#ifndef BGK_LINE_MINCTAS
+#define BGK_LINE_MINCTAS 4
+#endif
+
+// One task of the line-element stage: the run of elements eb .. eb + ne - 1 x a run of G velocity
+// tiles, on one warp with no barrier shared with other warps. Lane l owns velocity l of the tile. The
+// next tile's f_s, f^n, upwind outside neighbour and velocity table are in flight (one bulk copy each,
+// issued by lanes 0-3 on one mbarrier) while this tile is computed. Per tile the warp
+//   1. forms every element's FR advection residual (Sec. 2.1, Eqs. 7-9) from its line and the upwind
+//      trace: the neighbouring element's interpolant at the shared face (a run element's or the
+//      staged outside neighbour's), or the Dirichlet ghost value at a boundary end;
+//   2. evaluates the conservative Maxwellian g = 2^j exp2(a + sum_d (b_d m_d + q_d m_d^2)) of every node
+//      (m = the exact centred grid index of the velocity) from the per-point exponent the Newton kernel
+//      wrote (Sec. 2.1, text after Eq. 13), applies the BGK relaxation (Eq. 3), the Shu-Osher
+//      combination of the stage (Sec. 2.2) and, if on, the positivity limiter (Eqs. 10-11); stores
+//      f_{s+1};
+//   3. transposes the output through the consumed f_s rows and accumulates the moments W psi f_{s+1}
+//      (Eq. 2 with Eq. 12): lane = (row np = lane / 4 of every group of 8 nodes) x (velocity eighth
+//      kg = lane % 4), running sums in registers, combined over the 4 lanes of a row at the end and
+//      written as the task's FP32 partial; the Newton kernel sums the partials of all tasks exactly.
+// MODE 0: full stage. MODE 1: moments of src only (no advection, no store). ph: the phase parity
+// bits of the warp's two barriers, carried across the tasks a warp runs.
 template <int N1, int MODE>
-__device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task, const Ops &op, LineSmem<N1> &sm)
+__device__ __forceinline__ void line_task(const StageArgs &A, const int task, const Ops &op, LineWarp<N1> &sm,
+                                          uint32_t &ph)
 {
     constexpr int NP = N1;
-    constexpr int NQ = (NP + 1) / 2;  // packed node pairs
-    static_assert(5 * NP <= 32, "one (moment, node) total per lane");
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int K = LineWarp<N1>::K, NW = LineWarp<N1>::NW;
+    constexpr int NH = (NW + 1) / 2;
+    constexpr int NHR = (NW + 7) / 8;
+    constexpr uint32_t kRow = kWarp * sizeof(float);
+    const int lane = threadIdx.x & 31;
     const int E = A.mesh.nelem;
-    const int nEB = (E + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int nEB = (E + K - 1) / K;
     const int gl = task / nEB;
-    const int eb = (task % nEB) * kWarpsPerCta;
-    const int ne = min(kWarpsPerCta, E - eb);
-    const int e = eb + wid;
-    const bool active = e < E;
+    const int eb = (task % nEB) * K;
+    const int ne = min(K, E - eb);
+    const int nr = ne * N1;  // real rows of the run
     const int vl0 = gl * A.G;
     const int vl1 = min(vl0 + A.G, A.nvt);
-    int ec[3] = {e, 0, 0};
-    const int eL = upwind_neighbour(A.mesh, ec, 0, true), eR = upwind_neighbour(A.mesh, ec, 0, false);
-    ec[0] = eb;
-    const int eoL = upwind_neighbour(A.mesh, ec, 0, true);  // outside neighbours of the block
+    int ec[3] = {eb, 0, 0};
+    const int enL = upwind_neighbour(A.mesh, ec, 0, true);  // outside neighbours of the run
     ec[0] = eb + ne - 1;
-    const int eoR = upwind_neighbour(A.mesh, ec, 0, false);
+    const int enR = upwind_neighbour(A.mesh, ec, 0, false);
     const bool has_fn = MODE == 0 && A.fn != nullptr;
 
-    // Copy plan of the task, fixed for all its tiles (16-byte chunks; a slot's rows nb, mi, wp, gm
-    // are contiguous in shared memory): the element block's f_s and f^n rows (stride tileA per tile)
-    // and at most one table chunk per thread: a row of the outside neighbour (its element depends on
-    // the tile's inflow side), of the grid index, of w psi or of the mask.
-    const int tid = threadIdx.x;
-    constexpr int CH = kWarp / 4;  // chunks per 128-byte row
-    const int nA = ne * NP * CH;
-    const int64_t tileA = (int64_t)E * NP * kWarp;
-    const float *gA = A.src + (int64_t)eb * NP * kWarp;
-    const float *gB = has_fn ? A.fn + (int64_t)eb * NP * kWarp : nullptr;
-    const float *gC = nullptr;
-    int64_t sC = 0;
-    int cnb = -1;  // >= 0: this thread copies chunk cnb of the outside neighbour's rows
-    if (MODE == 0) {
-        const int q = tid - N1 * CH;
-        if (tid < N1 * CH)
-            cnb = 4 * tid;
-        else if (q < 3 * CH) {
-            gC = A.mi + (int64_t)(q / CH) * A.nslots + (int64_t)A.vt0 * kWarp + 4 * (q % CH);
-            sC = kWarp;
-        } else if (q < 8 * CH) {
-            gC = A.wpsi + (int64_t)A.vt0 * 5 * kWarp + 4 * (q - 3 * CH);
-            sC = 5 * kWarp;
-        } else if (q < 9 * CH) {
-            gC = A.gmask + (int64_t)A.vt0 * kWarp + 4 * (q - 8 * CH);
-            sC = kWarp;
-        }
-    } else if (tid < 5 * CH) {  // moments only: the w psi rows
-        gC = A.wpsi + (int64_t)A.vt0 * 5 * kWarp + 4 * tid;
-        sC = 5 * kWarp;
-    }
-    auto prefetch = [&](int vl, int slot) {
-        LineSlot<N1> &S = sm.s[slot];
-        for (int k = tid; k < nA; k += blockDim.x)
-            cp_async16(&S.fs[0][0][0] + 4 * k, gA + vl * tileA + 4 * k);
-        if (MODE == 0 && has_fn)
-            for (int k = tid; k < nA; k += blockDim.x)
-                cp_async16(&S.fn[0][0][0] + 4 * k, gB + vl * tileA + 4 * k);
-        float *tables = MODE == 0 ? &S.nb[0][0] : &S.wp[0][0];
-        if (cnb >= 0) {
-            const int eo = (__ldg(A.toct + A.vt0 + vl) & 1) ? eoL : eoR;
-            if (eo >= 0)
-                cp_async16(tables + cnb, A.src + fidx(vl, eo, 0, 0, E, NP) + cnb);
-        } else if (gC) {
-            cp_async16(tables + 4 * tid, gC + vl * sC);
-        }
-    };
-
-    // BGK exponents of the block's nodes into shared memory (pair-interleaved); the first barrier of
-    // the tile loop orders these stores before their reads
+    __syncwarp();  // the previous task of this warp is done with the exponents and both buffers
     if (MODE == 0) {
         const float *src = A.param + (int64_t)eb * NP * kParamStride;
-        for (int q = threadIdx.x; q < ne * NQ * 2 * kParamStride; q += blockDim.x) {
-            const int c = q % kParamStride, sl = (q / kParamStride) & 1, h = (q / (2 * kParamStride)) % NQ;
-            const int el = q / (2 * kParamStride * NQ);
-            sm.par[el][h][c][sl] = __ldg(src + (el * NP + min(2 * h + sl, NP - 1)) * kParamStride + c);
+        for (int q = lane; q < NH * 2 * kParamStride; q += kWarp) {
+            const int c = q % kParamStride, s2 = (q / kParamStride) & 1, h = q / (2 * kParamStride);
+            sm.par[h][c][s2] = __ldg(src + min(2 * h + s2, nr - 1) * kParamStride + c);
         }
     }
-    const bool viso = A.viso != 0;
-    unsigned long long m[5][NQ];
-#pragma unroll
-    for (int c = 0; c < 5; c++)
-#pragma unroll
-        for (int q = 0; q < NQ; q++)
-            m[c][q] = 0ull;
+    const int64_t tstride = (int64_t)E * NP * kWarp;
+    const float *runsrc = A.src + fidx(0, eb, 0, 0, E, NP);
+    const float *fnsrc = has_fn ? A.fn + fidx(0, eb, 0, 0, E, NP) : nullptr;
+    const uint32_t bar0 = smem_u32(&sm.bar[0]);
+    // the copies of tile vl into buffer b: lane 0 announces the bytes, lanes 0-3 issue one copy each
+    auto issue = [&](int vl, int b) {
+        const bool left = (__ldg(A.toct + A.vt0 + vl) & 1) != 0;
+        const int en = left ? enL : enR;
+        const bool nb = MODE == 0 && en >= 0;
+        const uint32_t bb = bar0 + 8u * (uint32_t)b;
+        if (lane == 0)
+            mbar_arrive_expect_tx(bb, (uint32_t)(nr * (has_fn ? 2 : 1) + (nb ? N1 : 0) + 5) * kRow);
+        __syncwarp();
+        if (lane == 0)
+            bulk_g2s(smem_u32(&sm.fs[b][N1][0]), runsrc + vl * tstride, nr * kRow, bb);
+        else if (lane == 1 && has_fn)
+            bulk_g2s(smem_u32(&sm.fn[b][0][0]), fnsrc + vl * tstride, nr * kRow, bb);
+        else if (lane == 2 && nb)
+            bulk_g2s(smem_u32(&sm.fs[b][left ? 0 : N1 + nr][0]), A.src + fidx(vl, en, 0, 0, E, NP), N1 * kRow, bb);
+        else if (lane == 3)
+            bulk_g2s(smem_u32(&sm.tab[b][0][0]), A.vtab + (int64_t)(A.vt0 + vl) * 5 * kWarp, 5 * kRow, bb);
+    };
+    if (vl0 < vl1) {
+        fence_proxy_async();
+        issue(vl0, 0);
+    }
 
+    const int np = lane >> 2, kg = lane & 3;
+    float msum[NHR][5];
+#pragma unroll
+    for (int h = 0; h < NHR; h++)
+#pragma unroll
+        for (int c = 0; c < 5; c++)
+            msum[h][c] = 0.f;
+    const bool viso = A.viso != 0;
     const float kb = A.kb;
     const float bdt = A.b * A.dt;
     const float cdt = -A.mesh.inv_h2[0] * bdt;
-    const float cgt = A.kg;
 
-#pragma unroll
-    for (int d = 0; d < kLineDepth - 1; d++) {
-        if (vl0 + d < vl1)
-            prefetch(vl0 + d, d);
-        cp_commit();
-    }
     for (int vl = vl0; vl < vl1; vl++) {
-        const int it = vl - vl0;
-        cp_wait<kLineDepth - 2>();  // tile vl has landed (this thread's copies) ...
-        __syncthreads();            // ... for every thread; and every warp is done with tile vl - 1
-        {
-            const int vn = vl + kLineDepth - 1;
-            if (vn < vl1)
-                prefetch(vn, (it + kLineDepth - 1) % kLineDepth);  // the slot of tile vl - 1
-            cp_commit();
+        const int b = (vl - vl0) & 1;
+        if (vl + 1 < vl1) {  // buffer b ^ 1 was consumed by the previous tile (its moment pass)
+            __syncwarp();
+            fence_proxy_async();
+            issue(vl + 1, b ^ 1);
         }
-        if (!active)
-            continue;
-        const LineSlot<N1> &S = sm.s[it % kLineDepth];
+        mbar_wait(bar0 + 8u * (uint32_t)b, (ph >> b) & 1, A.err);
+        ph ^= 1u << b;
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
-        float o[NP];
+        float acc[NW];
         if (MODE == 0) {
-            float f[NP];
-#pragma unroll
-            for (int i = 0; i < NP; i++)
-                f[i] = S.fs[wid][i][lane];
-            const float m0 = S.mi[0][lane], m1 = S.mi[1][lane], m2 = S.mi[2][lane];
+            const bool left = (__ldg(A.toct + vt) & 1) != 0;
+            const float m0 = sm.tab[b][0][lane], m1 = sm.tab[b][1][lane], m2 = sm.tab[b][2][lane];
             const float x0 = fmaf(A.vs[0], m0, A.vc[0]);
-            // squared indices (exact) as the exponent's quadratic terms take them
+            const float cd = cdt * x0;
+            const float gm = sm.tab[b][3][lane] != 0.f ? 1.f : 0.f;  // the padding mask
+            const float cg = A.kg * gm;
+            // 1. advection of every element of the run: acc = an f^n + kb f_s + cd (line sums)
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if (k >= ne)
+                    break;
+                float fl[N1], v[N1], sd[N1];
+#pragma unroll
+                for (int j = 0; j < N1; j++)
+                    fl[j] = sm.fs[b][N1 + k * N1 + j][lane];
+                if (left) {
+                    float T;
+                    if (k > 0 || enL >= 0) {
+#pragma unroll
+                        for (int j = 0; j < N1; j++)
+                            v[j] = sm.fs[b][k * N1 + j][lane];
+                        T = trace_line<N1, true>(v, op);
+                    } else {
+                        T = __ldg(A.ghost + slot);
+                    }
+                    line_sums<N1, true>(sd, fl, T, op);
+                } else {
+                    float T;
+                    if (k < ne - 1 || enR >= 0) {
+#pragma unroll
+                        for (int j = 0; j < N1; j++)
+                            v[j] = sm.fs[b][N1 + (k + 1) * N1 + j][lane];
+                        T = trace_line<N1, false>(v, op);
+                    } else {
+                        T = __ldg(A.ghost + A.nslots + slot);
+                    }
+                    line_sums<N1, false>(sd, fl, T, op);
+                }
+#pragma unroll
+                for (int j = 0; j < N1; j++) {
+                    const int r = k * N1 + j;
+                    const float fnv = has_fn ? sm.fn[b][r][lane] : 0.f;
+                    float kbi = kb;
+                    if (A.vtau)  // per-node weights, rounded so that kb + kg = b exactly
+                        kbi = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[r / 2][6][r % 2]));
+                    acc[r] = fmaf(cd, sd[j], fmaf(A.an, fnv, kbi * fl[j]));
+                }
+            }
+            // 2. BGK source towards the conservative Maxwellian, two nodes at a time
             const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
             const unsigned long long M0 = pack2(m0, m0), M1 = pack2(m1, m1), M2 = pack2(m2, m2);
             const unsigned long long U0 = viso ? pack2(mms, mms) : pack2(mm0, mm0);
             const unsigned long long U1 = viso ? U0 : pack2(mm1, mm1);
             const unsigned long long U2 = viso ? 0ull : pack2(mm2, mm2);
-            // inflow side of the tile (one sign octant per tile)
-            const bool left = (__ldg(A.toct + vt) & 1) != 0;
-            const int en = left ? eL : eR;
-            // upwind trace at the shared face: a sibling's element, the staged outside neighbour, or
-            // the Dirichlet ghost value
-            float T;
-            if (en >= 0) {
-                float v[N1];
-                const int r = en - eb;
-                const float *vrow = (r >= 0 && r < ne) ? &S.fs[r][0][0] : &S.nb[0][0];
 #pragma unroll
-                for (int j = 0; j < N1; j++)
-                    v[j] = vrow[j * kWarp + lane];
-                T = left ? trace_line<N1, true>(v, op) : trace_line<N1, false>(v, op);
-            } else {
-                T = __ldg(A.ghost + (left ? 0 : 1) * A.nslots + slot);
-            }
-            float sd[N1];
-            if (left)
-                line_sums<N1, true>(sd, f, T, op);
-            else
-                line_sums<N1, false>(sd, f, T, op);
-            const float cd = cdt * x0;
-            const float cg = cgt * S.gm[lane];
-            float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
-#pragma unroll
-            for (int h = 0; h < NQ; h++) {
-                const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[wid][h][0][0]);
+            for (int h = 0; h < NH; h++) {
+                if (2 * h >= nr)
+                    break;
+                const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[h][0][0]);
                 const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];  // (c, c+1) of both nodes
                 const unsigned long long lin =
                     ffma2(pack2(p23.z, p23.w), M2,
@@ -238,112 +228,179 @@ __device__ __forceinline__ void stage1d_task(const StageArgs &A, const int task,
                     ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)));
                 float g[2];
                 exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
-                const float itau[2] = {p67.x, p67.y};  // variable collision time: 1/tau of both nodes
 #pragma unroll
-                for (int sl = 0; sl < 2; sl++) {
-                    const int i = 2 * h + sl;
-                    if (i < NP) {
-                        const float fnv = has_fn ? S.fn[wid][i][lane] : 0.f;
-                        float kbi = kb, cgi = cg;
-                        if (A.vtau) {  // per-node weights, rounded so that kb + kg = b exactly
-                            kbi = __fsub_rn(A.b, __fmul_rn(bdt, itau[sl]));
-                            cgi = __fsub_rn(A.b, kbi) * S.gm[lane];
-                        }
-                        const float a = fmaf(cd, sd[i], fmaf(A.an, fnv, kbi * f[i]));
-                        o[i] = fmaf(cgi, g[sl], a);
+                for (int s2 = 0; s2 < 2; s2++) {
+                    const int r = 2 * h + s2;
+                    if (r >= NW)
+                        break;
+                    float cgi = cg;
+                    if (A.vtau) {
+                        const float kbi = __fsub_rn(A.b, __fmul_rn(bdt, s2 == 0 ? p67.x : p67.y));
+                        cgi = __fsub_rn(A.b, kbi) * gm;
                     }
+                    acc[r] = fmaf(cgi, g[s2], acc[r]);
                 }
             }
             if (A.limiter) {
                 // Zhang-Shu (Sec. 2.1, Eqs. 10-11): contract towards the element mean where a node
                 // value of this velocity is negative
-                float mean = 0.f, mn = o[0];
 #pragma unroll
-                for (int i = 0; i < NP; i++) {
-                    mean = fmaf(op.wq[i], o[i], mean);
-                    mn = fminf(mn, o[i]);
+                for (int k = 0; k < K; k++) {
+                    if (k >= ne)
+                        break;
+                    float mean = 0.f, mn = acc[k * N1];
+#pragma unroll
+                    for (int j = 0; j < N1; j++) {
+                        mean = fmaf(op.wq[j], acc[k * N1 + j], mean);
+                        mn = fminf(mn, acc[k * N1 + j]);
+                    }
+                    if (mn < 0.f) {
+                        const float beta = fminf(fabsf(mean / (mean - mn)), 1.f);
+#pragma unroll
+                        for (int j = 0; j < N1; j++)
+                            acc[k * N1 + j] = fmaf(beta, acc[k * N1 + j] - mean, mean);
+                    }
                 }
-                if (mn < 0.f) {
-                    const float beta = fminf(fabsf(mean / (mean - mn)), 1.f);
+            }
+            float *dst = A.dst + fidx(vl, eb, 0, lane, E, NP);
 #pragma unroll
-                    for (int i = 0; i < NP; i++)
-                        o[i] = fmaf(beta, o[i] - mean, mean);
+            for (int r = 0; r < NW; r++)
+                if (r < nr)
+                    __stcs(dst + r * kWarp, acc[r]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < NW; r++)
+                acc[r] = r < nr ? sm.fs[b][N1 + r][lane] : 0.f;
+        }
+        // 3. moments of the run's nodes of the stored values: the output transposed through the f_s
+        // rows (every lane has read its own column of them), 4-float groups of row r rotated by r mod 8
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < NW; r++)
+            if (r < nr)
+                sm.fs[b][N1 + r][lane ^ (4 * (r & 7))] = acc[r];
+        __syncwarp();
+        unsigned long long pm[NHR][5];
+#pragma unroll
+        for (int h = 0; h < NHR; h++)
+#pragma unroll
+            for (int c = 0; c < 5; c++)
+                pm[h][c] = 0ull;
+#pragma unroll
+        for (int k = 0; k < 8; k += 4) {
+            const int kk = 8 * kg + k;
+            unsigned long long wv[5][2];
+            {
+                const float4 W4 = *reinterpret_cast<const float4 *>(&sm.tab[b][3][kk]);
+                const float4 E4 = *reinterpret_cast<const float4 *>(&sm.tab[b][4][kk]);
+                wv[0][0] = pack2(W4.x, W4.y);
+                wv[0][1] = pack2(W4.z, W4.w);
+                wv[4][0] = pack2(E4.x, E4.y);
+                wv[4][1] = pack2(E4.z, E4.w);
+#pragma unroll
+                for (int d = 0; d < 3; d++) {  // W m_d: a power of two times an integer, exact
+                    const float4 M4 = *reinterpret_cast<const float4 *>(&sm.tab[b][d][kk]);
+                    wv[1 + d][0] = pack2(W4.x * M4.x, W4.y * M4.y);
+                    wv[1 + d][1] = pack2(W4.z * M4.z, W4.w * M4.w);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < NP; i++)
-                __stcs(dst + i * kWarp, o[i]);
-        } else {
+            for (int h = 0; h < NHR; h++) {
+                const int row = min(np + 8 * h, nr - 1);  // rows past the run: discarded below
+                const float4 v = *reinterpret_cast<const float4 *>(&sm.fs[b][N1 + row][kk ^ (4 * (row & 7))]);
+                const unsigned long long v01 = pack2(v.x, v.y), v23 = pack2(v.z, v.w);
 #pragma unroll
-            for (int i = 0; i < NP; i++)
-                o[i] = S.fs[wid][i][lane];
+                for (int c = 0; c < 5; c++) {
+                    pm[h][c] = ffma2(wv[c][0], v01, pm[h][c]);
+                    pm[h][c] = ffma2(wv[c][1], v23, pm[h][c]);
+                }
+            }
         }
-        // moments of this tile, accumulated per lane: m[c][q] += W psi_c (o_2q, o_2q+1)
+#pragma unroll
+        for (int h = 0; h < NHR; h++)
+#pragma unroll
+            for (int c = 0; c < 5; c++)
+                msum[h][c] += sum2(pm[h][c]);
+    }
+    // partial moments of this task: combine the 4 velocity eighths of every row
+    const int grp = A.group0 + gl;
+#pragma unroll
+    for (int h = 0; h < NHR; h++) {
+        const int row = np + 8 * h;
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            const float w = S.wp[c][lane];
-            const unsigned long long ww = pack2(w, w);
-#pragma unroll
-            for (int q = 0; q < NQ; q++)
-                m[c][q] = ffma2(ww, pack2(o[2 * q], 2 * q + 1 < NP ? o[2 * q + 1] : 0.f), m[c][q]);
+            float x = msum[h][c];
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            if (kg == 0 && row < nr)
+                A.partial[((int64_t)grp * 5 + c) * A.npts + (int64_t)eb * NP + row] = x;
         }
-    }
-    cp_wait<0>();
-    __syncthreads();  // the ring is free for the CTA's next task
-    if (!active)
-        return;
-
-    // totals over the 32 velocities of every tile: value (c, i) at index c * NP + i
-    float v[32];
-#pragma unroll
-    for (int j = 0; j < 32; j++)
-        v[j] = 0.f;
-#pragma unroll
-    for (int c = 0; c < 5; c++)
-#pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            float lo, hi;
-            unpack2(m[c][q], lo, hi);
-            v[c * NP + 2 * q] = lo;
-            if (2 * q + 1 < NP)
-                v[c * NP + 2 * q + 1] = hi;
-        }
-    transpose_reduce(v, lane);
-    if (lane < 5 * NP) {
-        const int c = lane / NP, i = lane - c * NP;
-        A.partial[((int64_t)(A.group0 + gl) * 5 + c) * A.npts + (int64_t)e * NP + i] = v[0];
     }
 }
 
-// Resident CTAs per SM the register allocation of the line kernels is sized for: 6 (80 registers, no
-// spills) runs the planar shear wave's stage 5 % faster than 5 (96 registers); the batch is the same.
-#ifndef BGK_STAGE1D_MINCTAS
-#define BGK_STAGE1D_MINCTAS 6
-#endif
+// Tasks of one line-element launch of A (the batch prefix sums use the same count).
+template <int N1>
+__host__ __device__ int line_tasks(const StageArgs &A)
+{
+    constexpr int K = line_run<N1>();
+    return ((A.mesh.nelem + K - 1) / K) * ((A.nvt + A.G - 1) / A.G);
+}
+
+int stage1d_tasks(const StageArgs &A)
+{
+    switch (A.n1) {
+    case 2: return line_tasks<2>(A);
+    case 3: return line_tasks<3>(A);
+    case 4: return line_tasks<4>(A);
+    case 5: return line_tasks<5>(A);
+    case 6: return line_tasks<6>(A);
+    }
+    return 0;
+}
+
+__device__ __forceinline__ void line_init_barriers(uint32_t bar0)
+{
+    if ((threadIdx.x & 31) == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8u, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+}
 
 template <int N1, int MODE>
-__global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE1D_MINCTAS) k_stage1d(const StageArgs A)
+__global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS) k_stage1d(const StageArgs A)
 {
-    __shared__ __align__(16) LineSmem<N1> sm;
-    stage1d_task<N1, MODE>(A, blockIdx.x, A.ops, sm);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int w = threadIdx.x >> 5;
+    const int task = blockIdx.x * BGK_LINE_WARPS + w;
+    if (task >= line_tasks<N1>(A))  // no barrier below involves other warps
+        return;
+    LineWarp<N1> &sm = reinterpret_cast<LineWarp<N1> *>(smraw)[w];
+    line_init_barriers(smem_u32(&sm.bar[0]));
+    uint32_t ph = 0;
+    line_task<N1, MODE>(A, task, A.ops, sm, ph);
 }
 
 // Batched line-element stages: one persistent launch over the tasks of many independent problems
-// (each with its own arguments, degree, mesh, velocity grid and task count). CTAs take tasks from an
-// atomic counter; a binary search over the task prefix sums finds the problem. The degree selects the
-// body; the FR operators of each degree come from constant memory.
-__global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE1D_MINCTAS)
+// (each with its own arguments, degree, mesh, velocity grid and task count). Every warp takes tasks
+// from an atomic counter on its own; a binary search over the task prefix sums finds the problem.
+// The degree selects the body (its storage is the front of the p = 3 layout, barriers first); the FR
+// operators of each degree come from constant memory.
+__global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS)
     k_stage1d_batch(const StageArgs *__restrict__ args, const int *__restrict__ task_start, int n, int *counter)
 {
-    __shared__ int s_item;
-    __shared__ __align__(16) LineSmem<4> sm;  // the largest degree of the batch (p = 3); smaller ones use its front
-    const int total = task_start[n];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    LineWarp<4> &sm = reinterpret_cast<LineWarp<4> *>(smraw)[w];
+    line_init_barriers(smem_u32(&sm.bar[0]));
+    uint32_t ph = 0;
+    const int total = __ldg(task_start + n);
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0)
-            s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int item = s_item;
+        int item = 0;
+        if (lane == 0)
+            item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total)
             break;
         int lo = 0, hi = n;
@@ -357,20 +414,17 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE1D_MINCTAS)
         const StageArgs &A = args[lo];
         const int task = item - __ldg(task_start + lo);
         switch (A.n1) {
-        case 2: stage1d_task<2, 0>(A, task, c_ops1d[2], *reinterpret_cast<LineSmem<2> *>(&sm)); break;
-        case 3: stage1d_task<3, 0>(A, task, c_ops1d[3], *reinterpret_cast<LineSmem<3> *>(&sm)); break;
-        case 4: stage1d_task<4, 0>(A, task, c_ops1d[4], sm); break;
+        case 2: line_task<2, 0>(A, task, c_ops1d[2], *reinterpret_cast<LineWarp<2> *>(&sm), ph); break;
+        case 3: line_task<3, 0>(A, task, c_ops1d[3], *reinterpret_cast<LineWarp<3> *>(&sm), ph); break;
+        case 4: line_task<4, 0>(A, task, c_ops1d[4], sm, ph); break;
         default: break;
         }
     }
 }
-
-// Tasks of one line-element launch of A (the batch prefix sums use the same count).
-int stage1d_tasks(const StageArgs &A)
-{
-    const int nEB = (A.mesh.nelem + kWarpsPerCta - 1) / kWarpsPerCta;
-    return nEB * ((A.nvt + A.G - 1) / A.G);
-}
+static_assert(sizeof(LineWarp<2>) <= sizeof(LineWarp<4>) && sizeof(LineWarp<3>) <= sizeof(LineWarp<4>),
+              "the batched launch keeps every degree in the p = 3 layout");
+static_assert(BGK_LINE_WARPS * sizeof(LineWarp<5>) <= 48 * 1024 && BGK_LINE_WARPS * sizeof(LineWarp<4>) <= 48 * 1024,
+              "the line kernels stay within the default dynamic shared memory");
 
 // Copy the line operators of degree n1 - 1 into the constant table of the batched launch.
 cudaError_t set_batch_ops(int n1, const Ops &op)
@@ -385,7 +439,8 @@ cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int *d_task_star
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
     if (e != cudaSuccess)
         return e;
-    k_stage1d_batch<<<ctas, kWarp * kWarpsPerCta, 0, s>>>(d_args, d_task_start, n, d_counter);
+    k_stage1d_batch<<<ctas, kWarp * BGK_LINE_WARPS, BGK_LINE_WARPS * sizeof(LineWarp<4>), s>>>(d_args, d_task_start,
+                                                                                                n, d_counter);
     return cudaGetLastError();
 }
 
@@ -395,7 +450,8 @@ int stage1d_batch_ctas()
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage1d_batch, kWarp * kWarpsPerCta, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage1d_batch, kWarp * BGK_LINE_WARPS,
+                                                  BGK_LINE_WARPS * sizeof(LineWarp<4>));
     return nsm * (per > 0 ? per : 1);
 }
 
@@ -410,11 +466,12 @@ cudaError_t launch_stage2(const StageArgs &A, int p, int mode, int oct, cudaStre
 template <int N1>
 static cudaError_t launch_1d(const StageArgs &A, int mode, cudaStream_t s)
 {
-    const int ntask = stage1d_tasks(A);
+    const int ctas = (line_tasks<N1>(A) + BGK_LINE_WARPS - 1) / BGK_LINE_WARPS;
+    const size_t smem = BGK_LINE_WARPS * sizeof(LineWarp<N1>);
     if (mode == 0)
-        k_stage1d<N1, 0><<<ntask, kWarp * kWarpsPerCta, 0, s>>>(A);
+        k_stage1d<N1, 0><<<ctas, kWarp * BGK_LINE_WARPS, smem, s>>>(A);
     else
-        k_stage1d<N1, 1><<<ntask, kWarp * kWarpsPerCta, 0, s>>>(A);
+        k_stage1d<N1, 1><<<ctas, kWarp * BGK_LINE_WARPS, smem, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // moments-only pass of every hexahedral mesh; affine hexahedra step in k_stage3s.cuh. Instantiated per
 // degree in k_stage3_p*.cu.
 #pragma once
+#include "k_stage3c.cuh"
 #include "k_stage3s.cuh"
 #include "k_stage3w.cuh"
 #include "stage_common.cuh"
@@ -536,8 +537,7 @@ cudaError_t prepare3()
             e = prepare3s<N1>();
     }
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 stage3_smem_bytes<N1, 1, 1>());
+        e = prepare3c<N1>();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stage3_smem_bytes<N1, 1, 2>());
@@ -553,7 +553,7 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
     if (mode == 1)
         return launch3<N1, 1, 8, 0>(A, s);
     if (A.met)  // curvilinear hexahedra: the general form with the metric, upwind side per lane
-        return A.ftab ? launch3<N1, 0, 8, 1, 2>(A, s) : launch3<N1, 0, 8, 1, 1>(A, s);
+        return A.ftab ? launch3<N1, 0, 8, 1, 2>(A, s) : launch3c<N1>(A, s);
     // the lean form: periodic faces, no force, no limiter, constant tau, one velocity spacing on all axes
     bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
     for (int f = 0; f < 6; f++)  // Dirichlet or wall faces (exchange faces need only the neighbour's source)
