@@ -245,31 +245,85 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b)
     return {r, __fsub_rn(e, __fsub_rn(r, s))};
 }
 
-// The refinement's 1-D sums S0..S2 as sums64<3>, with the recurrence and the sums in double-float, and
-// relative to the peak node: returns ln A(kp) = q(kp) and S_m / A(kp). Every moment and Jacobian entry is
-// a product of one 1-D sum per axis, so the three peak values join exp(alpha_0) in one exponential. The
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+// a * b for a float b
+__device__ __forceinline__ dfl df_mulf(dfl a, float b)
+{
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ __forceinline__ dfl df_scale(dfl a, float b) { return {a.hi * b, a.lo * b}; }  // b a power of two
+// a / b: the FP32 quotient of the high parts, corrected once with the double-float remainder
+__device__ __forceinline__ dfl df_div(dfl a, dfl b)
+{
+    const float r = __frcp_rn(b.hi);
+    const float q1 = __fmul_rn(a.hi, r);
+    const dfl t = df_sub(a, df_mulf(b, q1));
+    const float q2 = __fmul_rn(t.hi, r);
+    const float s = __fadd_rn(q1, q2);
+    return {s, __fsub_rn(q2, __fsub_rn(s, q1))};
+}
+
+// e^x in double-float FP32 arithmetic, relative error about 1e-14 for |x| <= 10 (checked against a
+// 60-digit reference over [-10, 10]; the refinement's arguments are the log-ratios of neighbouring
+// Gaussian nodes and the peak value, all well inside). x = n ln 2 + r with n = rint(x / ln 2) and
+// |r| <= ln 2 / 2: ln 2 in three FP32 parts, the first with 12 significant bits so that n ln2_1 and
+// x - n ln2_1 are exact; e^r by its Taylor series to degree 11 (truncation below 1e-15 at |r| = 0.35),
+// Horner in double-float with the coefficients 1/k! as FP32 pairs; the result scaled by 2^n. Larger
+// arguments take the FP64 exponential.
+__device__ __forceinline__ dfl df_exp(dfl x)
+{
+    if (!(fabsf(x.hi) <= 10.f))
+        return df_from(exp((double)x.hi + (double)x.lo));
+    constexpr float kLn2a = 6.931152344e-01f, kLn2b = 3.194618330e-05f, kLn2c = 1.646594970e-12f;
+    constexpr float kCh[12] = {1.0f, 1.0f, 0.5f, 0.1666666716337204f, 0.0416666679084301f, 0.008333333767950535f,
+                               0.0013888889225199819f, 0.00019841270113829523f, 2.4801587642286904e-05f,
+                               2.7557318844628753e-06f, 2.755731998149713e-07f, 2.5052107943679403e-08f};
+    constexpr float kCl[12] = {0.0f, 0.0f, 0.0f, -4.967053879312289e-09f, -1.2417634698280722e-09f,
+                               -4.34617203337595e-10f, -3.3631094437103215e-11f, -2.725596874933456e-12f,
+                               -3.40699609366682e-13f, 3.793571224297229e-14f, -7.575112209051195e-15f,
+                               4.4176230446483665e-16f};
+    const float n = rintf(x.hi * 1.44269504089f);
+    const float t = __fmaf_rn(-n, kLn2a, x.hi);  // exact
+    dfl r = df_add({t, 0.f}, {x.lo, 0.f});
+    r = df_add(r, df_mulf({-kLn2b, -kLn2c}, n));
+    dfl p = {kCh[11], kCl[11]};
+#pragma unroll
+    for (int k = 10; k >= 0; k--)
+        p = df_add(df_mul(p, r), {kCh[k], kCl[k]});
+    const float sc = __int_as_float(((int)n + 127) << 23);  // 2^n, |n| <= 15
+    return {p.hi * sc, p.lo * sc};
+}
+
+// The refinement's 1-D sums S0..S2 of one axis in double-float, relative to the peak node: returns
+// ln A(kp) = q(kp) and S_m / A(kp) (sums64<3>'s recurrence). Every moment and Jacobian entry is a
+// product of one 1-D sum per axis, so the three peak values join exp(alpha_0) in one exponential. The
 // ratio factor E2 = exp(-beta h^2) comes from the caller (one exponential for all axes of equal
-// spacing), the first ratio exp(q1 + q2 (2 kp + 1)) is the one FP64 exponential per axis; every node is
-// in FP32 pairs. Relative error about 1e-13 (checked against FP64 sums), far below what one refinement
-// with the FP32 Jacobian needs.
-__device__ __forceinline__ double sums_df(double ad, double beta, double c0, double h, int n, double dv, double E2,
-                                          double (&S)[3])
+// spacing); the first ratio exp(q1 + q2 (2 kp + 1)) is one exponential per axis; the downward ratio
+// E2 / rp a division. Relative error about 1e-13, far below what one refinement with the FP32 Jacobian
+// needs.
+__device__ __forceinline__ dfl sums_dd(dfl ad, dfl beta, dfl c0, dfl h, int n, dfl dv, dfl E2, dfl (&S)[3])
 {
     if (n == 1) {  // one node of unit weight (no u_z, m = 2)
-        S[0] = 1.0;
+        S[0] = {1.f, 0.f};
         S[1] = c0;
-        S[2] = c0 * c0;
-        return c0 * fma(-0.5 * beta, c0, ad);
+        S[2] = df_mul(c0, c0);
+        return df_mul(c0, df_sub(ad, df_mulf(df_mul(beta, c0), 0.5f)));
     }
-    const double q1 = (ad - beta * c0) * h, q2 = -0.5 * beta * h * h;
-    int kp = (int)rintf((float)(-q1) / (float)(2.0 * q2));
+    const dfl q1 = df_mul(df_sub(ad, df_mul(beta, c0)), h);
+    const dfl q2 = df_mulf(df_mul(beta, df_mul(h, h)), -0.5f);
+    int kp = (int)rintf(-q1.hi / (2.f * q2.hi));
     kp = kp < 0 ? 0 : (kp > n - 1 ? n - 1 : kp);
-    const double cp = fma((double)kp, h, c0);
-    const double rp = exp(q1 + q2 * (2.0 * kp + 1.0));
-    const dfl e2 = df_from(E2), hd = df_from(h), hm = df_from(-h);
+    const dfl cp = df_add(c0, df_mulf(h, (float)kp));
+    const dfl rp = df_exp(df_add(q1, df_mulf(q2, (float)(2 * kp + 1))));
+    const dfl hm = df_neg(h);
     dfl s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
     // upward from the peak (inclusive, value 1); unit weights, the trapezoid ends are corrected below
-    dfl Ak = {1.f, 0.f}, r = df_from(rp), c = df_from(cp), Aend = Ak, cend = c;
+    dfl Ak = {1.f, 0.f}, r = rp, c = cp, Aend = Ak, cend = c;
     for (int k = kp; k < n; k++) {
         const dfl cA = df_mul(c, Ak);
         s0 = df_add(s0, Ak);
@@ -278,16 +332,16 @@ __device__ __forceinline__ double sums_df(double ad, double beta, double c0, dou
         Aend = Ak;
         cend = c;
         Ak = df_mul(Ak, r);
-        r = df_mul(r, e2);
-        c = df_add(c, hd);
+        r = df_mul(r, E2);
+        c = df_add(c, h);
     }
     // downward from the peak (exclusive): A(k-1) = A(k) d(k), d(k) = E2 / r(k), d(k-1) = d(k) E2
     Ak = {1.f, 0.f};
-    c = df_from(cp);
-    dfl dk = df_from(E2 / rp), A0 = Ak, c0e = c;
+    c = cp;
+    dfl dk = df_div(E2, rp), A0 = Ak, c0e = c;
     for (int k = kp - 1; k >= 0; k--) {
         Ak = df_mul(Ak, dk);
-        dk = df_mul(dk, e2);
+        dk = df_mul(dk, E2);
         c = df_add(c, hm);
         const dfl cA = df_mul(c, Ak);
         s0 = df_add(s0, Ak);
@@ -296,11 +350,24 @@ __device__ __forceinline__ double sums_df(double ad, double beta, double c0, dou
         A0 = Ak;
         c0e = c;
     }
-    const double a0 = df_val(A0), ae = df_val(Aend), x0 = df_val(c0e), xe = df_val(cend);
-    S[0] = (df_val(s0) - 0.5 * (a0 + ae)) * dv;
-    S[1] = (df_val(s1) - 0.5 * (x0 * a0 + xe * ae)) * dv;
-    S[2] = (df_val(s2) - 0.5 * (x0 * x0 * a0 + xe * xe * ae)) * dv;
-    return cp * fma(-0.5 * beta, cp, ad);
+    // trapezoid: half weight at both ends (k = 0 and k = n - 1)
+    const dfl xa0 = df_mul(c0e, A0), xae = df_mul(cend, Aend);
+    S[0] = df_mul(df_sub(s0, df_scale(df_add(A0, Aend), 0.5f)), dv);
+    S[1] = df_mul(df_sub(s1, df_scale(df_add(xa0, xae), 0.5f)), dv);
+    S[2] = df_mul(df_sub(s2, df_scale(df_add(df_mul(c0e, xa0), df_mul(cend, xae)), 0.5f)), dv);
+    return df_mul(cp, df_sub(ad, df_mulf(df_mul(beta, cp), 0.5f)));
+}
+
+// The moments M[g psi~] (5) of assemble() from double-float 1-D sums S[d][0..2], scaled by e0.
+__device__ __forceinline__ void assemble_dd(const dfl (&S)[3][3], dfl e0, dfl (&M)[5])
+{
+    const dfl o0[3] = {df_mul(S[1][0], S[2][0]), df_mul(S[0][0], S[2][0]), df_mul(S[0][0], S[1][0])};
+    M[0] = df_mul(e0, df_mul(S[0][0], o0[0]));
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        M[1 + d] = df_mul(e0, df_mul(S[d][1], o0[d]));
+    const dfl m4 = df_add(df_add(df_mul(S[0][2], o0[0]), df_mul(S[1][2], o0[1])), df_mul(S[2][2], o0[2]));
+    M[4] = df_mul(e0, df_scale(m4, 0.5f));
 }
 
 __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
@@ -391,17 +458,31 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
         float J[5][5];
         bool haveJ = false;
         const int it32min = warm ? A.it32 : max(A.it32, 4);
-        float a0[5], da[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Qf[5], c0f[3], hf[3], dvf[3];
+        // the targets, grid and starting alpha as double-float pairs (the refinement's operands); their
+        // high parts are the FP32 loop's (alpha_1..3 = 0 and alpha_4 = -1 are exact)
+        dfl ald[5], Qd[5], c0d[3], hd[3], dvd[3];
     #pragma unroll
         for (int m = 0; m < 5; m++) {
-            a0[m] = (float)al[m];
-            Qf[m] = (float)Qt[m];
+            ald[m] = m == 0 ? df_from(al[0]) : dfl{(float)al[m], 0.f};
+            Qd[m] = df_from(Qt[m]);
         }
     #pragma unroll
         for (int d = 0; d < 3; d++) {
-            c0f[d] = (float)c0[d];
-            hf[d] = (float)h[d];
-            dvf[d] = (float)dvs[d];
+            c0d[d] = df_from(c0[d]);
+            hd[d] = df_from(h[d]);
+            dvd[d] = df_from(dvs[d]);
+        }
+        float a0[5], da[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Qf[5], c0f[3], hf[3], dvf[3];
+    #pragma unroll
+        for (int m = 0; m < 5; m++) {
+            a0[m] = ald[m].hi;
+            Qf[m] = Qd[m].hi;
+        }
+    #pragma unroll
+        for (int d = 0; d < 3; d++) {
+            c0f[d] = c0d[d].hi;
+            hf[d] = hd[d].hi;
+            dvf[d] = dvd[d].hi;
         }
         for (int it = 0; it < 30; it++) {
             float S[3][5];
@@ -442,39 +523,40 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
         }
     #pragma unroll
         for (int m = 0; m < 5; m++)
-            al[m] += (double)da[m];
+            ald[m] = df_add(ald[m], {da[m], 0.f});
         if (!haveJ) {
             atomicOr(A.err, kErrNewton);
             return;
         }
 
-        // FP64 refinements with the FP32 Jacobian of the last iteration, until the correction is at
-        // FP64 resolution (it64 minimum, 4 maximum)
+        // Refinements to FP64 accuracy with the FP32 Jacobian of the last iteration, until the correction
+        // is at FP64 resolution (it64 minimum, 4 maximum). The residual Q - M(alpha) is formed in
+        // double-float FP32 arithmetic (about 1e-13 relative): alpha, the targets and the grid in FP32
+        // pairs, the 1-D Gaussian sums by the product recurrence, the exponentials by df_exp. GB300's
+        // FP64 rate is 1/60 of its FP32 rate, and the same residual in FP64 took 58 % of this kernel.
         const int it64min = warm ? A.it64 : max(A.it64, 2);
         for (int it = 0; it < 4; it++) {
-            double S[3][5], E2[3], lnp = 0.0;
+            dfl S[3][3], E2[3], lnp = {0.f, 0.f};
+            const dfl beta = df_neg(ald[4]);
     #pragma unroll
             for (int d = 0; d < 3; d++)
-                E2[d] = d > 0 && h[d] == h[d - 1] ? E2[d - 1] : exp(al[4] * h[d] * h[d]);
+                E2[d] = d > 0 && hd[d].hi == hd[d - 1].hi && hd[d].lo == hd[d - 1].lo
+                            ? E2[d - 1]
+                            : df_exp(df_mul(ald[4], df_mul(hd[d], hd[d])));
     #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                double s3[3];
-                lnp += sums_df(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], E2[d], s3);
-                S[d][0] = s3[0];
-                S[d][1] = s3[1];
-                S[d][2] = s3[2];
-                S[d][3] = S[d][4] = 0.0;
-            }
-            double M[5];
-            assemble<double>(S, exp(al[0] + lnp), M, nullptr);  // the peaks' factors with alpha_0
+            for (int d = 0; d < 3; d++)
+                lnp = df_add(lnp, sums_dd(ald[1 + d], beta, c0d[d], hd[d], A.n[d], dvd[d], E2[d], S[d]));
+            dfl M[5];
+            assemble_dd(S, df_exp(df_add(ald[0], lnp)), M);  // the peaks' factors with alpha_0
             if (A.vdim == 2)
-                M[3] = Qt[3];
-            // the FP64 residual, solved with the FP32 Jacobian in FP32: the correction only needs FP32
+                M[3] = Qd[3];
+            // the residual, solved with the FP32 Jacobian in FP32: the correction only needs FP32
             // relative accuracy (iterative refinement)
             float r[5], dx[5], Jw[5][5];
     #pragma unroll
             for (int m = 0; m < 5; m++) {
-                r[m] = (float)(Qt[m] - M[m]);
+                const dfl t = df_sub(Qd[m], M[m]);
+                r[m] = t.hi + t.lo;
     #pragma unroll
                 for (int q = 0; q < 5; q++)
                     Jw[m][q] = J[m][q];
@@ -483,17 +565,21 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
                 atomicOr(A.err, kErrNewton);
                 return;
             }
-            corr = 0.0;
+            float cf = 0.f;
     #pragma unroll
             for (int m = 0; m < 5; m++) {
-                al[m] += (double)dx[m];
-                corr = fmax(corr, fabs((double)dx[m]));
+                ald[m] = df_add(ald[m], {dx[m], 0.f});
+                cf = fmaxf(cf, fabsf(dx[m]));
             }
+            corr = cf;
             // the FP32 Jacobian contracts the error by ~1e-6 per refinement: after a correction below
             // 1e-6 the residual is at FP64 resolution
-            if (it + 1 >= it64min && corr < 1e-6)
+            if (it + 1 >= it64min && cf < 1e-6f)
                 break;
         }
+    #pragma unroll
+        for (int m = 0; m < 5; m++)
+            al[m] = df_val(ald[m]);
     }
     const double beta = -al[4];
     if (!(beta > 0.0) || !isfinite(al[0] + al[1] + al[2] + al[3]) || corr >= 1e-6) {
