@@ -371,11 +371,8 @@ NewtonArgs newton_args(bgk_ctx *c, int cold)
         N.force[d] = c->force[d];
     N.fpar = c->fpar32;
     N.fpar64 = c->fpar64;
-    for (int d = 0; d < 3; d++) {
-        N.v0[d] = c->vlo[d];
-        N.dv[d] = c->dv[d];
-        N.n[d] = c->nv[d];
-    }
+    for (int d = 0; d < 3; d++)
+        newton_axis(N, d, c->vlo[d], c->dv[d], c->nv[d]);
     N.vdim = c->vdim;
     return N;
 }

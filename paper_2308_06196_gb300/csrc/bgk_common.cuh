@@ -130,9 +130,22 @@ struct NewtonArgs {
     // (n[2] = 1: the two-dimensional velocity space, m = 2) has v0 = 0 and unit weight, and its dv is
     // the x spacing (a placeholder that keeps the one-spacing forms of the exponent).
     double v0[3], dv[3];
+    float v0h[3], v0l[3], dvh[3], dvl[3];  // v0 and dv as double-float pairs (hi + lo)
     int n[3];
     int vdim;              // velocity dimension m: 3, or 2 (no u_z, E = rho |U|^2 / 2 + rho theta)
 };
+
+// Axis d of the Newton solve's velocity grid: first node v0, spacing dv, n nodes (with the FP32 pairs).
+inline void newton_axis(NewtonArgs &N, int d, double v0, double dv, int n)
+{
+    N.v0[d] = v0;
+    N.dv[d] = dv;
+    N.n[d] = n;
+    N.v0h[d] = (float)v0;
+    N.v0l[d] = (float)(v0 - (double)N.v0h[d]);
+    N.dvh[d] = (float)dv;
+    N.dvl[d] = (float)(dv - (double)N.dvh[d]);
+}
 
 // FR reference operators in FP64 for the plain all-FP64 form (Sec. 2.1, Eqs. 7-9).
 struct Ops64 {

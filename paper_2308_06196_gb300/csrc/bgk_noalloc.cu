@@ -167,11 +167,8 @@ extern "C" int bgk_equilibrium_noalloc(const float *d_f, int64_t npts, const bgk
     N.cold = 1;
     N.it32 = 2;
     N.it64 = 1;
-    for (int d = 0; d < 3; d++) {
-        N.v0[d] = v0[d];
-        N.dv[d] = dv[d];
-        N.n[d] = vg->n[d];
-    }
+    for (int d = 0; d < 3; d++)
+        newton_axis(N, d, v0[d], dv[d], vg->n[d]);
     N.vdim = vdim;
     if (launch_newton(N, s) != cudaSuccess)
         return BGK_ECUDA;

@@ -432,7 +432,7 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
             warm = true;
         }
     }
-    const double s = sqrt(th0), is = 1.0 / s;
+    const double is = rsqrt(th0), s = th0 * is;
     double Qt[5];
     Qt[0] = Q[0];
     for (int d = 0; d < 3; d++)
@@ -442,12 +442,17 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     // alpha = (alpha_0, a_1, a_2, a_3, -beta): g = exp(alpha_0 + a . c - beta |c|^2 / 2)
     double al[5] = {warm && A.lnc_form ? lnc0 : log(rh0) - hm * log(2.0 * 3.14159265358979323846 * th0), 0.0, 0.0,
                     0.0, -1.0};
-    double c0[3], h[3], dvs[3];
+    // the grid in the centred, scaled basis, c_k = c0 + k h: in double-float FP32 pairs (the grid's own
+    // pairs come with the arguments), with FP32 high parts for the FP32 iterations
+    dfl c0d[3], hd[3], dvd[3];
+    {
+        const dfl isd = df_from(is);
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        c0[d] = (A.v0[d] - V[d]) * is;
-        h[d] = A.dv[d] * is;
-        dvs[d] = A.dv[d];
+        for (int d = 0; d < 3; d++) {
+            dvd[d] = {A.dvh[d], A.dvl[d]};
+            c0d[d] = df_mul(df_sub({A.v0h[d], A.v0l[d]}, df_from(V[d])), isd);
+            hd[d] = df_mul(dvd[d], isd);
+        }
     }
 
     // the ablation (continuous Maxwellian of Q) stops here: alpha = the starting state itself
@@ -460,17 +465,11 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
         const int it32min = warm ? A.it32 : max(A.it32, 4);
         // the targets, grid and starting alpha as double-float pairs (the refinement's operands); their
         // high parts are the FP32 loop's (alpha_1..3 = 0 and alpha_4 = -1 are exact)
-        dfl ald[5], Qd[5], c0d[3], hd[3], dvd[3];
+        dfl ald[5], Qd[5];
     #pragma unroll
         for (int m = 0; m < 5; m++) {
             ald[m] = m == 0 ? df_from(al[0]) : dfl{(float)al[m], 0.f};
             Qd[m] = df_from(Qt[m]);
-        }
-    #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            c0d[d] = df_from(c0[d]);
-            hd[d] = df_from(h[d]);
-            dvd[d] = df_from(dvs[d]);
         }
         float a0[5], da[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Qf[5], c0f[3], hf[3], dvf[3];
     #pragma unroll
@@ -646,7 +645,7 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
         double S[3][5];
 #pragma unroll
         for (int d = 0; d < 3; d++)
-            sums64<5>(al[1 + d], -al[4], c0[d], h[d], A.n[d], dvs[d], S[d]);
+            sums64<5>(al[1 + d], -al[4], df_val(c0d[d]), df_val(hd[d]), A.n[d], A.dv[d], S[d]);
         double M[5], J[5][5], r[5], b[5];
         assemble<double>(S, exp(al[0]), M, J);
         r[0] = 0.0;
@@ -683,11 +682,16 @@ __device__ __forceinline__ void newton_point(const NewtonArgs &A, const int pt)
     }
 }
 
-// Resident CTAs of 128 threads per SM the register allocation is sized for: 4 (128 registers, a few
-// bytes of spills) runs 4 % faster than the compiler's own choice (up to 176 registers, 3 CTAs); the
-// solve is bound by the FP64 pipe, which more resident warps keep busier.
+// Resident CTAs of 128 threads per SM the register allocation is sized for. The solve is bound by the
+// latency of its FP32 and FP64 chains and by the FP64 pipe, which more resident warps keep busier:
+// 8 CTAs (64 registers, spilling to L1) run the 262,144-point solves of the planar and Taylor-Green
+// workloads 10-17 % faster than 4 (128 registers); the batched solve, whose arguments come from
+// global memory, runs best at 4.
 #ifndef BGK_NEWTON_MINCTAS
-#define BGK_NEWTON_MINCTAS 4
+#define BGK_NEWTON_MINCTAS 8
+#endif
+#ifndef BGK_NEWTON_BATCH_MINCTAS
+#define BGK_NEWTON_BATCH_MINCTAS 4
 #endif
 
 __global__ void __launch_bounds__(128, BGK_NEWTON_MINCTAS) k_newton(const NewtonArgs A)
@@ -699,7 +703,7 @@ __global__ void __launch_bounds__(128, BGK_NEWTON_MINCTAS) k_newton(const Newton
 
 // Batched solve over the points of many independent problems: thread per point, the problem found
 // by a binary search over the point prefix sums pt_start[0..n].
-__global__ void __launch_bounds__(128, BGK_NEWTON_MINCTAS) k_newton_batch(const NewtonArgs *__restrict__ args,
+__global__ void __launch_bounds__(128, BGK_NEWTON_BATCH_MINCTAS) k_newton_batch(const NewtonArgs *__restrict__ args,
                                                       const int *__restrict__ pt_start, int n)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;

@@ -552,12 +552,12 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
 {
     if (mode == 1)
         return launch3<N1, 1, 8, 0>(A, s);
-    if (A.met)  // curvilinear hexahedra: the general form with the metric, upwind side per lane
-        return A.ftab ? launch3<N1, 0, 8, 1, 2>(A, s) : launch3c<N1>(A, s);
     // the lean form: periodic faces, no force, no limiter, constant tau, one velocity spacing on all axes
     bool general = A.fpar != nullptr || !A.viso || A.limiter || A.vtau;
     for (int f = 0; f < 6; f++)  // Dirichlet or wall faces (exchange faces need only the neighbour's source)
         general = general || A.mesh.bc[f] == 1 || A.mesh.bc[f] == 2;
+    if (A.met)  // curvilinear hexahedra: the metric, the upwind side per lane
+        return A.ftab ? launch3<N1, 0, 8, 1, 2>(A, s) : (general ? launch3c<N1, 1>(A, s) : launch3c<N1, 0>(A, s));
     if constexpr (N1 <= 3)  // p <= 2: one warp per element
         return general ? launch3w_oct<N1, 1>(A, oct, s) : launch3w_oct<N1, 0>(A, oct, s);
     else

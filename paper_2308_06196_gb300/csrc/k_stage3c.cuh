@@ -24,15 +24,15 @@ namespace bgk {
 // every lane. A lane whose flow enters through the other face (a normal tilted against a small xi_d)
 // reads that neighbour's trace from global memory; where no lane of the warp does, nothing is read.
 // ------------------------------------------------------------------------------------------------
-template <int N1>
+template <int N1, int GEN>
 struct Stage3cSmem {
     static constexpr int NP = N1 * N1 * N1, NQ = N1 * N1;
     float fs[2][NP][kWarp];
     float sl[N1][3][NQ][kWarp];
     float tab[2][kTabRows][kWarp];
     float par[N1][(NQ + 1) / 2][kParamStride][2];  // BGK exponents by layer and node pair (see k_stage3s)
-    float fpar[NP][kParamStride];
-    float lim[2][N1][kWarp];
+    float fpar[GEN ? NP : 1][GEN ? kParamStride : 4];
+    float lim[GEN ? 2 : 1][GEN ? N1 : 1][GEN ? kWarp : 4];
     float4 met[NP][3];      // metric rows Ja^d; .w of row 0 = -b dt / J (the line sums' factor), of row 1 = W J
     float4 fnm[3][2][NQ];   // shared face normals (direction, low/high side, face point)
     float iwj;              // 1 / sum_i W_i J_i
@@ -66,14 +66,17 @@ __device__ __forceinline__ void curv_line_c(float (&sv)[N1], const float (&fl)[N
     }
 }
 
-template <int N1>
+// GEN = 0: every face periodic, no body force, no limiter, constant tau and one velocity spacing on all
+// axes (the lean form of k_stage3s); GEN = 1: Dirichlet and diffuse-wall ghosts, the force source, the
+// limiter, variable tau and per-axis spacings.
+template <int N1, int GEN>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 : (N1 == 3 ? 6 : 8))) k_stage3c(const StageArgs A)
 {
     constexpr int NQ = N1 * N1;
     constexpr int NP = NQ * N1;
     constexpr int NT = kWarp * N1;
     constexpr uint32_t kRow = kWarp * sizeof(float);
-    using Sm = Stage3cSmem<N1>;
+    using Sm = Stage3cSmem<N1, GEN>;
     extern __shared__ __align__(16) unsigned char smraw[];
     Sm &sm = *reinterpret_cast<Sm *>(smraw);
 
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
             const int node = lw * NQ + min(2 * h + sl, NQ - 1);
             sm.par[lw][h][c][sl] = __ldg(src + node * kParamStride + c);
         }
-        if (A.fpar) {
+        if (GEN && A.fpar) {
             const float4 *f4 = reinterpret_cast<const float4 *>(A.fpar + (int64_t)e * NP * kParamStride);
             float4 *d4 = reinterpret_cast<float4 *>(&sm.fpar[0][0]);
             for (int q = tid; q < NP * kParamStride / 4; q += NT)
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
             float kbq = kb;
-            if (A.vtau)
+            if (GEN && A.vtau)
                 kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
             acc[q] = fmaf(A.an, acc[q], kbq * sm.fs[b][q + NQ * w][lane]);
         }
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
             if (__any_sync(0xffffffffu, far)) {
                 const int g = 2 * d + (lo ? 1 : 0);
                 const int eo = upwind_neighbour(A.mesh, ec, d, !lo);
-                if (eo >= 0) {
+                if (!GEN || eo >= 0) {
                     const float *nb = A.src + fidx(vl, eo, 0, lane, E, NP);
                     float v[N1][N1];
 #pragma unroll
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
             }
             float gS = 0.f;  // the staged side's ghost value on a boundary face
             const float *rwS = nullptr;
-            if (es < 0) {
+            if (GEN && es < 0) {
                 const int g = 2 * d + (lo ? 0 : 1);
                 gS = __ldg(A.ghost + (int64_t)g * A.nslots + slot);
                 if (A.mesh.bc[g] == 2)
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                     const float4 m = sm.met[node(ln, j)][d];
                     u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
                 }
-                const float tS = es >= 0 ? trace(v, cS) : (rwS ? gS * __ldg(rwS + ln) : gS);
+                const float tS = !GEN || es >= 0 ? trace(v, cS) : (rwS ? gS * __ldg(rwS + ln) : gS);
                 curv_line_c<N1>(sv, fl, u, uL[ln], uR[ln], lo ? tS : tF[ln], lo ? tF[ln] : tS, A.ops);
 #pragma unroll
                 for (int j = 0; j < N1; j++) {
@@ -381,7 +384,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
         const float cg = A.kg * gm, cf = bdt * gm;
         const float xs = x0 * x0 + x1 * x1 + x2 * x2;
         const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
-        const bool iso = A.viso;
+        const bool iso = !GEN || A.viso;
         const unsigned long long M0 = pack2(m0, m0), M1 = pack2(m1, m1), M2 = pack2(m2, m2);
         const unsigned long long U0 = iso ? pack2(mms, mms) : pack2(mm0, mm0);
         const unsigned long long U1 = iso ? U0 : pack2(mm1, mm1);
@@ -396,7 +399,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                 ffma2(pack2(p23.z, p23.w), M2,
                       ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
             const unsigned long long ex =
-                ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)));
+                GEN ? ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
+                    : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
             float g[2];
             exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
 #pragma unroll
@@ -407,17 +411,17 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                 const int i = q + NQ * w;
                 const float a = acc[q];
                 float gc = cg;
-                if (A.vtau) {
+                if (GEN && A.vtau) {
                     const float itau = sl == 0 ? p67.x : p67.y;
                     gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
                 }
-                if (A.fpar) {
+                if (GEN && A.fpar) {
                     const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
                     const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
                     gc = fmaf(cf, qv, cg);
                 }
                 const float o = fmaf(gc, g[sl], a);
-                if (A.limiter) {
+                if (GEN && A.limiter) {
                     lsum = fmaf(sm.met[i][1].w, o, lsum);
                     lmin = fminf(lmin, o);
                 } else {
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                 sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))] = o;
             }
         }
-        if (A.limiter) {
+        if (GEN && A.limiter) {
             // Zhang-Shu (Sec. 2.1, Eqs. 10-11) over the physical element: weights W J over their sum
             sm.lim[0][w][lane] = lsum;
             sm.lim[1][w][lane] = lmin;
@@ -516,14 +520,19 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
 template <int N1>
 cudaError_t prepare3c()
 {
-    return cudaFuncSetAttribute(k_stage3c<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Stage3cSmem<N1>));
+    cudaError_t e = cudaFuncSetAttribute(k_stage3c<N1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Stage3cSmem<N1, 0>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stage3c<N1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(Stage3cSmem<N1, 1>));
+    return e;
 }
 
-template <int N1>
+template <int N1, int GEN>
 cudaError_t launch3c(const StageArgs &A, cudaStream_t s)
 {
     const int ngroups = (A.nvt + A.G - 1) / A.G;
-    k_stage3c<N1><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3cSmem<N1>), s>>>(A);
+    k_stage3c<N1, GEN><<<A.mesh.nelem * ngroups, kWarp * N1, sizeof(Stage3cSmem<N1, GEN>), s>>>(A);
     return cudaGetLastError();
 }
 
