@@ -1,17 +1,17 @@
-// k_stage3.cuh -- the fused SSP-RK3 stage kernel of curvilinear hexahedra (FP32-split form) and the
-// moments-only pass of every hexahedral mesh; affine hexahedra step in k_stage3s.cuh. Instantiated per
-// degree in k_stage3_p*.cu.
+// k_stage3.cuh -- the fused SSP-RK3 stage kernel of curvilinear hexahedra with unstructured
+// connectivity (FP32-split form), the moments-only pass of every hexahedral mesh, and the dispatch of
+// the hexahedral stage kernels: affine hexahedra step in k_stage3s.cuh (k_stage3w.cuh at p <= 2),
+// curvilinear hexahedra on the structured element grid in k_stage3c.cuh. Instantiated per degree in
+// k_stage3_p*.cu.
 #pragma once
 #include "k_stage3c.cuh"
 #include "k_stage3s.cuh"
 #include "k_stage3w.cuh"
 #include "stage_common.cuh"
 
-// Resident CTAs per SM the register allocation is sized for (p = 3 lean and general / p = 2 / p = 1).
-// The register file is split over the SM's four schedulers, so a CTA of 3 warps (p = 2) at 96
-// registers packs only 6 per SM (18 warps); at 80 registers 8 fit (24 warps), and the p = 2 stage runs
-// 8-11 % faster despite a few bytes of spills in the general form. The p = 3 general form at 5 CTAs
-// (96 registers) spills about 100 bytes and runs 13-17 % slower than at 4 (128 registers).
+// Resident CTAs per SM the register allocation is sized for (p = 3 moments-only pass / p = 3 with
+// the curvilinear advection / p = 2). The register file is split over the SM's four schedulers, so a
+// CTA of 3 warps (p = 2) at 80 registers packs 8 per SM (24 warps).
 #ifndef BGK_STAGE3_MINCTAS_P3
 #define BGK_STAGE3_MINCTAS_P3 5
 #endif
@@ -25,11 +25,13 @@
 namespace bgk {
 
 // ------------------------------------------------------------------------------------------------
-// Curvilinear hexahedra: one CTA per (element, run of G tiles), one warp per z-layer of the element's
-// nodes, lane l = velocity l of the tile. A warp keeps its layer's values (f_s and the accumulator) in
-// registers, so the r- and s-lines are register-local; the t-lines cross the layers and are read from a
-// shared copy of the element tile, their sums shared the same way. Exterior traces are loaded per lane
-// where the face flow enters (N . xi decides per lane and face point).
+// Curvilinear hexahedra with unstructured connectivity: one CTA per (element, run of G tiles), one warp
+// per z-layer of the element's nodes, lane l = velocity l of the tile. A warp keeps its layer's values
+// (f_s and the accumulator) in registers, so the r- and s-lines are register-local; the t-lines cross
+// the layers and are read from a shared copy of the element tile, their sums shared the same way.
+// Exterior traces are loaded per lane where the face flow enters (N . xi decides per lane and face
+// point): a neighbour's line through a face point may run along any of its axes, so its rows are not
+// one contiguous layer to stage.
 // ------------------------------------------------------------------------------------------------
 template <int N1, int GEN>
 struct Stage3Smem {
@@ -98,15 +100,15 @@ __device__ __forceinline__ void curv_line(float (&sv)[N1], const float (&fl)[N1]
 // GEN = 0: every face periodic, no body force and one velocity spacing on all axes (the lean form;
 // the Maxwellian exponent needs only the sum of the squared grid indices); GEN = 1: Dirichlet and
 // diffuse-wall faces, the body-force source and per-axis spacings.
-// CURV = 1 (with GEN = 1, OCT = 8): curvilinear hexahedra on the structured element grid, the
+// CURV = 2 (with GEN = 1, OCT = 8): curvilinear hexahedra with unstructured connectivity, the
 // reference-space flux (Ja^d . xi) f and per-lane upwinding at every face point from the shared face
-// normal; CURV = 2: the same with unstructured connectivity (the element's neighbours, their shared
-// faces and face-point orientations from its connectivity row).
+// normal, the element's neighbours, their shared faces and face-point orientations from its
+// connectivity row (curvilinear hexahedra on the structured element grid step in k_stage3c.cuh).
 template <int N1, int MODE, int OCT, int GEN, int CURV = 0>
 __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTAS_P3_GEN : BGK_STAGE3_MINCTAS_P3)
                                                : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
 {
-    static_assert(MODE == 1 || CURV, "affine hexahedra step in k_stage3s");
+    static_assert(MODE == 1 || CURV == 2, "affine hexahedra step in k_stage3s, structured curvilinear ones in k_stage3c");
     constexpr int NQ = N1 * N1;      // nodes per layer
     constexpr int NP = NQ * N1;
     constexpr int NT = kWarp * N1;   // threads
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 (&cs.fnm[0][0][0])[q] = __ldg(A.fnm + (int64_t)e * 6 * NQ + q);
             if (tid == 0)
                 cs.iwj = __ldg(A.iwj + e);
-            if (CURV == 2) {
+            {
                 if (tid < 6)
                     cs.ftab[tid] = __ldg(A.ftab + (int64_t)e * 6 + tid);
                 for (int q = tid; q < 6 * NQ; q += NT)
@@ -191,20 +193,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
         for (int j = 0; j < N1; j++)
             v[j] = __ldg(nb + (base + j * t.y) * kWarp);
         return t.z ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
-    };
-    // wall density of face point fp of the element's boundary face g (a diffuse wall), else 1 (CURV = 1)
-    auto wall_rho = [&](int g, int d, int fp) -> float {
-        return A.mesh.bc[g] == 2 ? __ldg(A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + fp) : 1.f;
-    };
-    // the structured grid's neighbour en: the upwind trace of its line through our nodes n0 + j st
-    // (CURV = 1); left: the neighbour lies on the low side (its +1 end)
-    auto nbtrace = [&](int vl, int en, int n0, int st, bool left) -> float {
-        float v[N1];
-        const float *nb = A.src + fidx(vl, en, n0, lane, E, NP);
-#pragma unroll
-        for (int j = 0; j < N1; j++)
-            v[j] = __ldg(nb + j * st * kWarp);
-        return left ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
     };
 
     // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
@@ -280,8 +268,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 }
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    const int eL = CURV == 1 ? upwind_neighbour(A.mesh, ec, d, true) : 0;
-                    const int eR = CURV == 1 ? upwind_neighbour(A.mesh, ec, d, false) : 0;
 #pragma unroll
                     for (int ln = 0; ln < N1; ln++) {
                         float fl[N1], u[N1], sv[N1];
@@ -299,22 +285,10 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
                         // inflow through the low / high face: the exterior trace (predicated per lane)
                         float tL = 0.f, tR = 0.f;
-                        if (uL > 0.f) {
-                            if (CURV == 2)
-                                tL = exterior(vl, slot, d, 0, ln + N1 * w);
-                            else if (eL >= 0)
-                                tL = nbtrace(vl, eL, nd[0], nd[1] - nd[0], true);
-                            else
-                                tL = __ldg(A.ghost + (2 * d) * A.nslots + slot) * wall_rho(2 * d, d, ln + N1 * w);
-                        }
-                        if (uR < 0.f) {
-                            if (CURV == 2)
-                                tR = exterior(vl, slot, d, 1, ln + N1 * w);
-                            else if (eR >= 0)
-                                tR = nbtrace(vl, eR, nd[0], nd[1] - nd[0], false);
-                            else
-                                tR = __ldg(A.ghost + (2 * d + 1) * A.nslots + slot) * wall_rho(2 * d + 1, d, ln + N1 * w);
-                        }
+                        if (uL > 0.f)
+                            tL = exterior(vl, slot, d, 0, ln + N1 * w);
+                        if (uR < 0.f)
+                            tR = exterior(vl, slot, d, 1, ln + N1 * w);
                         curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
                         for (int j = 0; j < N1; j++)
@@ -328,8 +302,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
                 }
                 // z-lines of slice iy = w (all layers) from the shared tile; unscaled sums to zc
-                const int eL = CURV == 1 ? upwind_neighbour(A.mesh, ec, 2, true) : 0;
-                const int eR = CURV == 1 ? upwind_neighbour(A.mesh, ec, 2, false) : 0;
 #pragma unroll
                 for (int ln = 0; ln < N1; ln++) {
                     float fl[N1], u[N1], sv[N1];
@@ -345,22 +317,10 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
                     const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
                     float tL = 0.f, tR = 0.f;
-                    if (uL > 0.f) {
-                        if (CURV == 2)
-                            tL = exterior(vl, slot, 2, 0, ln + N1 * w);
-                        else if (eL >= 0)
-                            tL = nbtrace(vl, eL, nd[0], NQ, true);
-                        else
-                            tL = __ldg(A.ghost + 4 * A.nslots + slot) * wall_rho(4, 2, ln + N1 * w);
-                    }
-                    if (uR < 0.f) {
-                        if (CURV == 2)
-                            tR = exterior(vl, slot, 2, 1, ln + N1 * w);
-                        else if (eR >= 0)
-                            tR = nbtrace(vl, eR, nd[0], NQ, false);
-                        else
-                            tR = __ldg(A.ghost + 5 * A.nslots + slot) * wall_rho(5, 2, ln + N1 * w);
-                    }
+                    if (uL > 0.f)
+                        tL = exterior(vl, slot, 2, 0, ln + N1 * w);
+                    if (uR < 0.f)
+                        tR = exterior(vl, slot, 2, 1, ln + N1 * w);
                     curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
 #pragma unroll
                     for (int j = 0; j < N1; j++)
