@@ -177,22 +177,40 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
         sm.msum[w][m][lane] = 0.f;
     const float kb = A.kb;
     const float bdt = A.b * A.dt;
-    // curvilinear: the exterior trace at face (d, side) for the face point fp of the line whose own nodes
-    // are nd (tile vl, this lane): the neighbour's interpolant at the shared face, or the face's ghost
-    // exterior trace at face (d, side), face point fp, from the connectivity row (CURV = 2)
-    auto exterior = [&](int vl, int slot, int d, int side, int fp) -> float {
-        const int4 t = cs.ftab[2 * d + side];  // (neighbour or -1 - ghost face, stride, its +1 end, wall)
-        if (t.x < 0) {  // boundary: the ghost of its class, times the wall density of this point on a wall
-            const float gv = __ldg(A.ghost + (int64_t)(-1 - t.x) * A.nslots + slot);
-            return t.w >= 0 ? gv * __ldg(A.rhowu + (int64_t)t.w * NQ + fp) : gv;
-        }
-        const int base = cs.fbase[2 * d + side][fp];
-        float v[N1];
-        const float *nb = A.src + fidx(vl, t.x, 0, lane, E, NP);
+    // Exterior traces through face (d, side) of the connectivity row for the N1 lines of this warp whose
+    // face points are fp0 + ln, where the lane's flow enters (need[ln]), 0 elsewhere: the neighbour's
+    // interpolant at the shared face (its line through the face point: first node and stride from the
+    // row), or the face's ghost value (times the wall density of the point on a wall). The loads of all
+    // lines are in flight together, and nothing is read where no lane of the warp needs a value.
+    auto exteriors = [&](int vl, int slot, int d, int side, int fp0, const bool(&need)[N1], float(&t)[N1]) {
+        bool any = false;
 #pragma unroll
-        for (int j = 0; j < N1; j++)
-            v[j] = __ldg(nb + (base + j * t.y) * kWarp);
-        return t.z ? trace_line<N1, true>(v, A.ops) : trace_line<N1, false>(v, A.ops);
+        for (int ln = 0; ln < N1; ln++) {
+            t[ln] = 0.f;
+            any = any || need[ln];
+        }
+        if (!__any_sync(0xffffffffu, any))
+            return;
+        const int4 tb = cs.ftab[2 * d + side];
+        if (tb.x < 0) {
+            const float gv = __ldg(A.ghost + (int64_t)(-1 - tb.x) * A.nslots + slot);
+#pragma unroll
+            for (int ln = 0; ln < N1; ln++)
+                t[ln] = tb.w >= 0 ? gv * __ldg(A.rhowu + (int64_t)tb.w * NQ + fp0 + ln) : gv;
+            return;
+        }
+        const float *nb = A.src + fidx(vl, tb.x, 0, lane, E, NP);
+        float v[N1][N1];
+#pragma unroll
+        for (int ln = 0; ln < N1; ln++) {
+            const int base = cs.fbase[2 * d + side][fp0 + ln];
+#pragma unroll
+            for (int j = 0; j < N1; j++)
+                v[ln][j] = need[ln] ? __ldg(nb + (base + j * tb.y) * kWarp) : 0.f;
+        }
+#pragma unroll
+        for (int ln = 0; ln < N1; ln++)
+            t[ln] = tb.z ? trace_line<N1, true>(v[ln], A.ops) : trace_line<N1, false>(v[ln], A.ops);
     };
 
     // asynchronous copy of this warp's layer of f_s (and f^n) of tile vl into buffer b: NQ rows of
@@ -268,6 +286,19 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                 }
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
+                    // face-normal speeds of the warp's lines, then the exterior traces where the flow enters
+                    float uLs[N1], uRs[N1], tLs[N1], tRs[N1];
+                    bool inL[N1], inR[N1];
+#pragma unroll
+                    for (int ln = 0; ln < N1; ln++) {
+                        const float4 nL = cs.fnm[d][0][ln + N1 * w], nR = cs.fnm[d][1][ln + N1 * w];
+                        uLs[ln] = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
+                        uRs[ln] = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
+                        inL[ln] = uLs[ln] > 0.f;
+                        inR[ln] = uRs[ln] < 0.f;
+                    }
+                    exteriors(vl, slot, d, 0, N1 * w, inL, tLs);
+                    exteriors(vl, slot, d, 1, N1 * w, inR, tRs);
 #pragma unroll
                     for (int ln = 0; ln < N1; ln++) {
                         float fl[N1], u[N1], sv[N1];
@@ -280,16 +311,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                             const float4 m = cs.met[nd[j]][d];
                             u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
                         }
-                        const float4 nL = cs.fnm[d][0][ln + N1 * w], nR = cs.fnm[d][1][ln + N1 * w];
-                        const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
-                        const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
-                        // inflow through the low / high face: the exterior trace (predicated per lane)
-                        float tL = 0.f, tR = 0.f;
-                        if (uL > 0.f)
-                            tL = exterior(vl, slot, d, 0, ln + N1 * w);
-                        if (uR < 0.f)
-                            tR = exterior(vl, slot, d, 1, ln + N1 * w);
-                        curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
+                        curv_line<N1>(sv, fl, u, uLs[ln], uRs[ln], tLs[ln], tRs[ln], A.ops);
 #pragma unroll
                         for (int j = 0; j < N1; j++)
                             acc[qi[j]] = fmaf(-bdt * cs.met[nd[j]][0].w, sv[j], acc[qi[j]]);
@@ -302,6 +324,18 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
                 }
                 // z-lines of slice iy = w (all layers) from the shared tile; unscaled sums to zc
+                float uLs[N1], uRs[N1], tLs[N1], tRs[N1];
+                bool inL[N1], inR[N1];
+#pragma unroll
+                for (int ln = 0; ln < N1; ln++) {
+                    const float4 nL = cs.fnm[2][0][ln + N1 * w], nR = cs.fnm[2][1][ln + N1 * w];
+                    uLs[ln] = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
+                    uRs[ln] = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
+                    inL[ln] = uLs[ln] > 0.f;
+                    inR[ln] = uRs[ln] < 0.f;
+                }
+                exteriors(vl, slot, 2, 0, N1 * w, inL, tLs);
+                exteriors(vl, slot, 2, 1, N1 * w, inR, tRs);
 #pragma unroll
                 for (int ln = 0; ln < N1; ln++) {
                     float fl[N1], u[N1], sv[N1];
@@ -313,15 +347,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                         const float4 m = cs.met[nd[j]][2];
                         u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
                     }
-                    const float4 nL = cs.fnm[2][0][ln + N1 * w], nR = cs.fnm[2][1][ln + N1 * w];
-                    const float uL = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
-                    const float uR = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
-                    float tL = 0.f, tR = 0.f;
-                    if (uL > 0.f)
-                        tL = exterior(vl, slot, 2, 0, ln + N1 * w);
-                    if (uR < 0.f)
-                        tR = exterior(vl, slot, 2, 1, ln + N1 * w);
-                    curv_line<N1>(sv, fl, u, uL, uR, tL, tR, A.ops);
+                    curv_line<N1>(sv, fl, u, uLs[ln], uRs[ln], tLs[ln], tRs[ln], A.ops);
 #pragma unroll
                     for (int j = 0; j < N1; j++)
                         sm.zc[nd[j]][lane] = sv[j];
