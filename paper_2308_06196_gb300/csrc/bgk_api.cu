@@ -25,7 +25,7 @@ cudaError_t prepare_stage(int dim, int p);
 cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s);
 cudaError_t launch_newton_batch(const NewtonArgs *d_args, const int *d_pt_start, int n, int total_pts,
                                 cudaStream_t s);
-cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int *d_task_start, int n, int *d_counter,
+cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int2 *d_task_member, int *d_counter,
                                  int ctas, cudaStream_t s);
 cudaError_t set_batch_ops(int n1, const Ops &op);
 int stage1d_tasks(const StageArgs &A);
@@ -1860,7 +1860,8 @@ struct bgk_batch {
     std::vector<bgk_ctx *> probs;
     StageArgs *d_args = nullptr;    // [3][n] stage arguments of every member
     NewtonArgs *d_nargs = nullptr;  // [n]
-    int *d_task_start = nullptr;    // [n + 1] task prefix sums (the same for the three stages)
+    int2 *d_task_member = nullptr;  // [total_tasks] (member, its task index) of every stage task
+    int task_cap = 0;               // capacity of d_task_member
     int *d_pt_start = nullptr;      // [n + 1] point prefix sums
     int *d_counter = nullptr;       // work counter of the persistent launch
     int *err = nullptr;             // status word shared by the members' Newton solves
@@ -1933,9 +1934,28 @@ int batch_upload(bgk_batch *b, const double *dt)
     }
     b->total_tasks = ts[n];
     b->total_pts = ps[n];
+    std::vector<int2> tm((size_t)ts[n]);
+    for (int q = 0; q < n; q++)
+        for (int k = ts[q]; k < ts[q + 1]; k++)
+            tm[k] = make_int2(q, k - ts[q]);
+    if (ts[n] > b->task_cap) {  // a larger table: the captured step graph holds the old one's address
+        BK(cudaStreamSynchronize(b->stream));
+        if (b->d_task_member)
+            BK(cudaFree(b->d_task_member));
+        b->d_task_member = nullptr;
+        b->task_cap = 0;
+        BK(cudaMalloc((void **)&b->d_task_member, (size_t)ts[n] * sizeof(int2)));
+        b->task_cap = ts[n];
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+    }
+    const int counter[2] = {0, ts[n]};
     BK(cudaMemcpyAsync(b->d_args, sa.data(), sa.size() * sizeof(StageArgs), cudaMemcpyHostToDevice, b->stream));
     BK(cudaMemcpyAsync(b->d_nargs, na.data(), na.size() * sizeof(NewtonArgs), cudaMemcpyHostToDevice, b->stream));
-    BK(cudaMemcpyAsync(b->d_task_start, ts.data(), ts.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_task_member, tm.data(), tm.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, b->stream));
     BK(cudaMemcpyAsync(b->d_pt_start, ps.data(), ps.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BK(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
     return BGK_OK;
@@ -1969,7 +1989,7 @@ int batch_enqueue(bgk_batch *b, cudaStream_t s)
 {
     for (int st = 0; st < 3; st++) {
         bev_begin(b, 0, b->alg_bytes[st]);
-        BK(launch_stage1d_batch(b->d_args + (size_t)st * b->n, b->d_task_start, b->n, b->d_counter, b->ctas, s));
+        BK(launch_stage1d_batch(b->d_args + (size_t)st * b->n, b->d_task_member, b->d_counter, b->ctas, s));
         bev_end(b);
         bev_begin(b, 1, 0.0);
         BK(launch_newton_batch(b->d_nargs, b->d_pt_start, b->n, b->total_pts, s));
@@ -2014,7 +2034,7 @@ void bgk_batch_destroy(bgk_batch *b)
     }
     if (b->ev)
         cudaEventDestroy(b->ev);
-    void *bufs[] = {b->d_args, b->d_nargs, b->d_task_start, b->d_pt_start, b->d_counter, b->err};
+    void *bufs[] = {b->d_args, b->d_nargs, b->d_task_member, b->d_pt_start, b->d_counter, b->err};
     for (void *p : bufs)
         if (p)
             cudaFree(p);
@@ -2064,11 +2084,9 @@ int bgk_batch_create(int n, bgk_ctx *const *probs, bgk_batch **out)
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&b->d_nargs, (size_t)n * sizeof(NewtonArgs));
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&b->d_task_start, (size_t)(n + 1) * sizeof(int));
-    if (e == cudaSuccess)
         e = cudaMalloc((void **)&b->d_pt_start, (size_t)(n + 1) * sizeof(int));
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&b->d_counter, sizeof(int));
+        e = cudaMalloc((void **)&b->d_counter, 2 * sizeof(int));
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&b->err, sizeof(int));
     if (e == cudaSuccess)
@@ -2203,7 +2221,7 @@ int bgk_batch_autotune(bgk_batch *b)
         for (int r = 0; r < 3; r++) {
             // stage 2: reads slot 0 and f^n, writes slot 1 (f^n, the moments and equilibrium untouched)
             BK(cudaEventRecord(e0, b->stream));
-            BK(launch_stage1d_batch(b->d_args + b->n, b->d_task_start, b->n, b->d_counter, b->ctas, b->stream));
+            BK(launch_stage1d_batch(b->d_args + b->n, b->d_task_member, b->d_counter, b->ctas, b->stream));
             BK(cudaEventRecord(e1, b->stream));
             BK(cudaEventSynchronize(e1));
             float ms = 0.f;

@@ -384,18 +384,19 @@ __global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS) k_sta
 
 // Batched line-element stages: one persistent launch over the tasks of many independent problems
 // (each with its own arguments, degree, mesh, velocity grid and task count). Every warp takes tasks
-// from an atomic counter on its own; a binary search over the task prefix sums finds the problem.
+// from an atomic counter on its own (counter[0]; counter[1] holds the number of tasks); one load from
+// the task table gives the task's problem and its task index there.
 // The degree selects the body (its storage is the front of the p = 3 layout, barriers first); the FR
 // operators of each degree come from constant memory.
 __global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS)
-    k_stage1d_batch(const StageArgs *__restrict__ args, const int *__restrict__ task_start, int n, int *counter)
+    k_stage1d_batch(const StageArgs *__restrict__ args, const int2 *__restrict__ task_member, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     LineWarp<4> &sm = reinterpret_cast<LineWarp<4> *>(smraw)[w];
     line_init_barriers(smem_u32(&sm.bar[0]));
     uint32_t ph = 0;
-    const int total = __ldg(task_start + n);
+    const int total = *reinterpret_cast<volatile int *>(counter + 1);
     for (;;) {
         int item = 0;
         if (lane == 0)
@@ -403,16 +404,9 @@ __global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS)
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total)
             break;
-        int lo = 0, hi = n;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(task_start + mid) <= item)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const StageArgs &A = args[lo];
-        const int task = item - __ldg(task_start + lo);
+        const int2 tm = __ldg(task_member + item);  // (member, its task index)
+        const StageArgs &A = args[tm.x];
+        const int task = tm.y;
         switch (A.n1) {
         case 2: line_task<2, 0>(A, task, c_ops1d[2], *reinterpret_cast<LineWarp<2> *>(&sm), ph); break;
         case 3: line_task<3, 0>(A, task, c_ops1d[3], *reinterpret_cast<LineWarp<3> *>(&sm), ph); break;
@@ -433,14 +427,14 @@ cudaError_t set_batch_ops(int n1, const Ops &op)
 }
 
 // The work counter is reset in the same stream before every launch (a captured memset node).
-cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int *d_task_start, int n, int *d_counter,
-                                 int ctas, cudaStream_t s)
+cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int2 *d_task_member, int *d_counter, int ctas,
+                                 cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
     if (e != cudaSuccess)
         return e;
-    k_stage1d_batch<<<ctas, kWarp * BGK_LINE_WARPS, BGK_LINE_WARPS * sizeof(LineWarp<4>), s>>>(d_args, d_task_start,
-                                                                                                n, d_counter);
+    k_stage1d_batch<<<ctas, kWarp * BGK_LINE_WARPS, BGK_LINE_WARPS * sizeof(LineWarp<4>), s>>>(d_args, d_task_member,
+                                                                                                d_counter);
     return cudaGetLastError();
 }
 

@@ -100,12 +100,12 @@ __device__ __forceinline__ void curv_line(float (&sv)[N1], const float (&fl)[N1]
 // GEN = 0: every face periodic, no body force and one velocity spacing on all axes (the lean form;
 // the Maxwellian exponent needs only the sum of the squared grid indices); GEN = 1: Dirichlet and
 // diffuse-wall faces, the body-force source and per-axis spacings.
-// CURV = 2 (with GEN = 1, OCT = 8): curvilinear hexahedra with unstructured connectivity, the
+// CURV = 2 (OCT = 8; lean or general form): curvilinear hexahedra with unstructured connectivity, the
 // reference-space flux (Ja^d . xi) f and per-lane upwinding at every face point from the shared face
 // normal, the element's neighbours, their shared faces and face-point orientations from its
 // connectivity row (curvilinear hexahedra on the structured element grid step in k_stage3c.cuh).
 template <int N1, int MODE, int OCT, int GEN, int CURV = 0>
-__global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTAS_P3_GEN : BGK_STAGE3_MINCTAS_P3)
+__global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE3_MINCTAS_P3_GEN : BGK_STAGE3_MINCTAS_P3)
                                                : (N1 == 3 ? BGK_STAGE3_MINCTAS_P2 : 8))) k_stage3(const StageArgs A)
 {
     static_assert(MODE == 1 || CURV == 2, "affine hexahedra step in k_stage3s, structured curvilinear ones in k_stage3c");
@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
                     (&cs.fbase[0][0])[q] = __ldg(A.fbase + (int64_t)e * 6 * NQ + q);
             }
         }
-        // the general form reads 1/tau of its layer (variable collision time) before the first
-        // tile's B1, from rows other warps loaded
-        if (GEN)
+        // the general form reads 1/tau of its layer (variable collision time), and the curvilinear lines
+        // the metric, normals and connectivity, before the first tile's B1, from rows other warps loaded
+        if (GEN || CURV)
             __syncthreads();
     }
     // moment sums: lane = (node pair np = lane / 4: layer nodes np and np + 8) x (velocity eighth
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3_MINCTA
 #pragma unroll
                 for (int q = 0; q < NQ; q++) {
                     float kbq = kb;
-                    if (A.vtau)
+                    if (GEN && A.vtau)
                         kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
                     acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
                 }
@@ -527,6 +527,9 @@ cudaError_t prepare3()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stage3_smem_bytes<N1, 1, 2>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stage3<N1, 0, 8, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 stage3_smem_bytes<N1, 0, 2>());
 
     return e;
 }
@@ -543,7 +546,8 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
     for (int f = 0; f < 6; f++)  // Dirichlet or wall faces (exchange faces need only the neighbour's source)
         general = general || A.mesh.bc[f] == 1 || A.mesh.bc[f] == 2;
     if (A.met)  // curvilinear hexahedra: the metric, the upwind side per lane
-        return A.ftab ? launch3<N1, 0, 8, 1, 2>(A, s) : (general ? launch3c<N1, 1>(A, s) : launch3c<N1, 0>(A, s));
+        return A.ftab ? (general ? launch3<N1, 0, 8, 1, 2>(A, s) : launch3<N1, 0, 8, 0, 2>(A, s))
+                      : (general ? launch3c<N1, 1>(A, s) : launch3c<N1, 0>(A, s));
     if constexpr (N1 <= 3)  // p <= 2: one warp per element
         return general ? launch3w_oct<N1, 1>(A, oct, s) : launch3w_oct<N1, 0>(A, oct, s);
     else
