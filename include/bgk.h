@@ -244,9 +244,9 @@ int bgk_f_distance(bgk_ctx *a, bgk_ctx *b, double *max_abs_diff, double *max_abs
 /* ---------------------------------------------------------------------------------------------
  * Batches of independent problems. The paper runs one problem at a time; the method's steps are
  * the same per member (Sec. 2.1-2.2), only scheduled together: each RK stage of every member runs
- * in one persistent stage launch (CTAs take (member, element block, tile run) tasks from an atomic
- * work counter, reset by a memset in the same stream) followed by one Newton launch over all
- * members' points, and one step of all members is captured in one CUDA graph.
+ * in one persistent stage launch per degree present (warps take (member, element run, tile run)
+ * tasks from an atomic work counter, reset by a memset in the same stream) followed by one Newton
+ * launch over all members' points, and one step of all members is captured in one CUDA graph.
  *
  * bgk_batch_create: members are n distinct contexts created on the current device with
  *   precision BGK_FP32_SPLIT, dim = 1, p <= 3 and opts.chunks = 1 (the three stage buffers of a

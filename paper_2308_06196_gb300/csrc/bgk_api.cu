@@ -25,11 +25,11 @@ cudaError_t prepare_stage(int dim, int p);
 cudaError_t launch_newton(const NewtonArgs &A, cudaStream_t s);
 cudaError_t launch_newton_batch(const NewtonArgs *d_args, const int *d_pt_start, int n, int total_pts,
                                 cudaStream_t s);
-cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int2 *d_task_member, int *d_counter,
+cudaError_t launch_stage1d_batch(int n1, const StageArgs *d_args, const int2 *d_task_member, int *d_block,
                                  int ctas, cudaStream_t s);
 cudaError_t set_batch_ops(int n1, const Ops &op);
 int stage1d_tasks(const StageArgs &A);
-int stage1d_batch_ctas();
+int stage1d_batch_ctas(int n1);
 cudaError_t launch_init_maxwellian(float *f, const double *prim, const float *mi, const float *gmask, int nslots,
                                    int nvt, int E, int NP, const int n[3], const double v0[3], const double dv[3],
                                    int *err, double *Q, double *warm, cudaStream_t s);
@@ -1852,8 +1852,8 @@ int bgk_timing(bgk_ctx *c, double *stage_ms, int64_t *stage_launches, double *ne
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------------
-// Batches of independent line-element problems: one persistent stage launch and one Newton launch per
-// RK stage over all members, the whole step captured in one CUDA graph.
+// Batches of independent line-element problems: per RK stage one persistent stage launch per degree
+// present and one Newton launch over all members, the whole step captured in one CUDA graph.
 
 struct bgk_batch {
     int n = 0;
@@ -1863,9 +1863,10 @@ struct bgk_batch {
     int2 *d_task_member = nullptr;  // [total_tasks] (member, its task index) of every stage task
     int task_cap = 0;               // capacity of d_task_member
     int *d_pt_start = nullptr;      // [n + 1] point prefix sums
-    int *d_counter = nullptr;       // work counter of the persistent launch
+    int *d_counter = nullptr;       // [kMaxN1 + 1][4] per degree: work counter, first task, end (persistent launches)
     int *err = nullptr;             // status word shared by the members' Newton solves
-    int total_tasks = 0, total_pts = 0, ctas = 0;
+    int total_tasks = 0, total_pts = 0;
+    int ctas[kMaxN1 + 1] = {0};     // CTAs of each degree's launch, 0 where the batch has no member of that degree
     std::vector<double> dt;         // time step of every member in the device arguments
     std::vector<int> G;             // task length of every member in the device arguments
     double alg_bytes[3] = {0, 0, 0};
@@ -1934,10 +1935,18 @@ int batch_upload(bgk_batch *b, const double *dt)
     }
     b->total_tasks = ts[n];
     b->total_pts = ps[n];
-    std::vector<int2> tm((size_t)ts[n]);
-    for (int q = 0; q < n; q++)
-        for (int k = ts[q]; k < ts[q + 1]; k++)
-            tm[k] = make_int2(q, k - ts[q]);
+    // the task table degree by degree: one persistent launch per degree takes its range
+    std::vector<int2> tm;
+    tm.reserve((size_t)ts[n]);
+    std::vector<int> block(4 * (kMaxN1 + 1), 0);
+    for (int n1 = 0; n1 <= kMaxN1; n1++) {
+        block[4 * n1 + 1] = (int)tm.size();
+        for (int q = 0; q < n; q++)
+            if (b->probs[q]->N1 == n1)
+                for (int k = 0; k < ts[q + 1] - ts[q]; k++)
+                    tm.push_back(make_int2(q, k));
+        block[4 * n1 + 2] = (int)tm.size();
+    }
     if (ts[n] > b->task_cap) {  // a larger table: the captured step graph holds the old one's address
         BK(cudaStreamSynchronize(b->stream));
         if (b->d_task_member)
@@ -1951,11 +1960,10 @@ int batch_upload(bgk_batch *b, const double *dt)
             b->gexec = nullptr;
         }
     }
-    const int counter[2] = {0, ts[n]};
     BK(cudaMemcpyAsync(b->d_args, sa.data(), sa.size() * sizeof(StageArgs), cudaMemcpyHostToDevice, b->stream));
     BK(cudaMemcpyAsync(b->d_nargs, na.data(), na.size() * sizeof(NewtonArgs), cudaMemcpyHostToDevice, b->stream));
     BK(cudaMemcpyAsync(b->d_task_member, tm.data(), tm.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
-    BK(cudaMemcpyAsync(b->d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_counter, block.data(), block.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BK(cudaMemcpyAsync(b->d_pt_start, ps.data(), ps.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BK(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
     return BGK_OK;
@@ -1984,12 +1992,16 @@ void bev_end(bgk_batch *b)
     b->nev++;
 }
 
-// One SSP-RK3 step of every member: per stage one persistent stage launch and one Newton launch.
+// One SSP-RK3 step of every member: per stage one persistent stage launch per degree and one Newton
+// launch.
 int batch_enqueue(bgk_batch *b, cudaStream_t s)
 {
     for (int st = 0; st < 3; st++) {
         bev_begin(b, 0, b->alg_bytes[st]);
-        BK(launch_stage1d_batch(b->d_args + (size_t)st * b->n, b->d_task_member, b->d_counter, b->ctas, s));
+        for (int n1 = 0; n1 <= kMaxN1; n1++)
+            if (b->ctas[n1])
+                BK(launch_stage1d_batch(n1, b->d_args + (size_t)st * b->n, b->d_task_member, b->d_counter + 4 * n1,
+                                        b->ctas[n1], s));
         bev_end(b);
         bev_begin(b, 1, 0.0);
         BK(launch_newton_batch(b->d_nargs, b->d_pt_start, b->n, b->total_pts, s));
@@ -2086,14 +2098,14 @@ int bgk_batch_create(int n, bgk_ctx *const *probs, bgk_batch **out)
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&b->d_pt_start, (size_t)(n + 1) * sizeof(int));
     if (e == cudaSuccess)
-        e = cudaMalloc((void **)&b->d_counter, 2 * sizeof(int));
+        e = cudaMalloc((void **)&b->d_counter, 4 * (kMaxN1 + 1) * sizeof(int));
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&b->err, sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemset(b->err, 0, sizeof(int));
     if (e == cudaSuccess)
         e = cudaDeviceSynchronize();  // the memset on the legacy stream, before any non-blocking stream's work
-    // the line operators of every degree present, for the constant table of the persistent launch
+    // the line operators of every degree present, for the constant table of the persistent launches
     bool done[kMaxN1 + 1] = {false};
     for (int q = 0; q < n && e == cudaSuccess; q++) {
         const bgk_ctx *c = probs[q];
@@ -2104,7 +2116,8 @@ int bgk_batch_create(int n, bgk_ctx *const *probs, bgk_batch **out)
     if (e != cudaSuccess)
         return bail(e == cudaErrorMemoryAllocation ? BGK_ENOMEM : BGK_ECUDA, cudaGetErrorString(e));
     b->stream = b->own;
-    b->ctas = stage1d_batch_ctas();
+    for (int n1 = 0; n1 <= kMaxN1; n1++)  // one persistent launch per degree present
+        b->ctas[n1] = done[n1] ? stage1d_batch_ctas(n1) : 0;
     *out = b;
     return BGK_OK;
 }
@@ -2221,7 +2234,10 @@ int bgk_batch_autotune(bgk_batch *b)
         for (int r = 0; r < 3; r++) {
             // stage 2: reads slot 0 and f^n, writes slot 1 (f^n, the moments and equilibrium untouched)
             BK(cudaEventRecord(e0, b->stream));
-            BK(launch_stage1d_batch(b->d_args + b->n, b->d_task_member, b->d_counter, b->ctas, b->stream));
+            for (int n1 = 0; n1 <= kMaxN1; n1++)
+                if (b->ctas[n1])
+                    BK(launch_stage1d_batch(n1, b->d_args + b->n, b->d_task_member, b->d_counter + 4 * n1, b->ctas[n1],
+                                            b->stream));
             BK(cudaEventRecord(e1, b->stream));
             BK(cudaEventSynchronize(e1));
             float ms = 0.f;

@@ -1,23 +1,10 @@
 // k_stage.cu -- the fused SSP-RK3 stage kernel of the line-element (1-D in space, 3-D in velocity)
 // form, FP32-split, its batched persistent variant, and the dispatch of all stage kernels.
 //
-// One task = a block of kWarpsPerCta consecutive elements x a run of G velocity tiles (32 velocities
-// of one sign octant each); warp w of the CTA takes element w of the block. Lane l owns velocity l of
-// the tile. The CTA streams its tiles through a ring of shared slots with cp.async, several tiles
-// ahead. Per tile the warp
-//   1. reads f_s and f^n of its element from the slot (staged as coalesced 128-byte rows),
-//   2. adds the FR advection residual (Sec. 2.1, Eqs. 7-9): it reads the upwind neighbour element's
-//      line (same tile) and interpolates the neighbour's trace at the shared face, the interior trace
-//      being folded into the merged operator; a Dirichlet end supplies the sampled ghost value,
-//   3. evaluates the conservative Maxwellian g = 2^j exp2(a + sum_d (b_d m_d + q_d m_d^2)) of every node
-//      (m = the exact centred grid index of the velocity) from the per-point exponent the Newton kernel
-//      wrote (Sec. 2.1, text after Eq. 13), applies the BGK
-//      relaxation (Eq. 3) and the Shu-Osher combination of the stage (Sec. 2.2), stores f_{s+1},
-//   4. accumulates w_k psi_k f_{s+1} (Eq. 2 with Eq. 12) per lane, node and moment (two nodes per
-//      packed FP32 pair).
-// At the end of the task a transpose-reduction over the 32 lanes leaves one (moment, node) total per
-// lane, written as the task's FP32 partial; the Newton kernel sums the partials of all tasks exactly
-// (double-float) before solving for the next stage's Maxwellian.
+// One task = a run of consecutive elements (at most 16 nodes) x a run of G velocity tiles (32
+// velocities of one sign octant each), on one warp: lane l owns velocity l of the tile. The warp
+// streams its tiles through two shared buffers with bulk asynchronous copies on its own mbarriers,
+// one tile ahead, and shares no barrier with any other warp (see line_task).
 //
 // The stage never reads what another task of the same launch writes: it reads f_s (source), f^n,
 // the BGK exponent table and the ghost table, and writes only its own part of the destination and
@@ -382,70 +369,78 @@ __global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS) k_sta
     line_task<N1, MODE>(A, task, A.ops, sm, ph);
 }
 
-// Batched line-element stages: one persistent launch over the tasks of many independent problems
-// (each with its own arguments, degree, mesh, velocity grid and task count). Every warp takes tasks
-// from an atomic counter on its own (counter[0]; counter[1] holds the number of tasks); one load from
-// the task table gives the task's problem and its task index there.
-// The degree selects the body (its storage is the front of the p = 3 layout, barriers first); the FR
-// operators of each degree come from constant memory.
+// Batched line-element stages: one persistent launch per degree over the tasks of that degree's
+// problems (each with its own arguments, mesh, velocity grid and task count), so every launch runs one
+// body. The task table lists the tasks degree by degree; block = {counter, first task, end}: every warp
+// takes tasks from the counter on its own, and one load from the table gives the task's problem and its
+// task index there. The FR operators of each degree come from constant memory.
+template <int N1>
 __global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS)
-    k_stage1d_batch(const StageArgs *__restrict__ args, const int2 *__restrict__ task_member, int *counter)
+    k_stage1d_batch(const StageArgs *__restrict__ args, const int2 *__restrict__ task_member, int *block)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    LineWarp<4> &sm = reinterpret_cast<LineWarp<4> *>(smraw)[w];
+    LineWarp<N1> &sm = reinterpret_cast<LineWarp<N1> *>(smraw)[w];
     line_init_barriers(smem_u32(&sm.bar[0]));
     uint32_t ph = 0;
-    const int total = *reinterpret_cast<volatile int *>(counter + 1);
+    const int first = *reinterpret_cast<volatile int *>(block + 1);
+    const int end = *reinterpret_cast<volatile int *>(block + 2);
     for (;;) {
         int item = 0;
         if (lane == 0)
-            item = atomicAdd(counter, 1);
+            item = first + atomicAdd(block, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total)
+        if (item >= end)
             break;
         const int2 tm = __ldg(task_member + item);  // (member, its task index)
-        const StageArgs &A = args[tm.x];
-        const int task = tm.y;
-        switch (A.n1) {
-        case 2: line_task<2, 0>(A, task, c_ops1d[2], *reinterpret_cast<LineWarp<2> *>(&sm), ph); break;
-        case 3: line_task<3, 0>(A, task, c_ops1d[3], *reinterpret_cast<LineWarp<3> *>(&sm), ph); break;
-        case 4: line_task<4, 0>(A, task, c_ops1d[4], sm, ph); break;
-        default: break;
-        }
+        line_task<N1, 0>(args[tm.x], tm.y, c_ops1d[N1], sm, ph);
     }
 }
-static_assert(sizeof(LineWarp<2>) <= sizeof(LineWarp<4>) && sizeof(LineWarp<3>) <= sizeof(LineWarp<4>),
-              "the batched launch keeps every degree in the p = 3 layout");
+
 static_assert(BGK_LINE_WARPS * sizeof(LineWarp<5>) <= 48 * 1024 && BGK_LINE_WARPS * sizeof(LineWarp<4>) <= 48 * 1024,
               "the line kernels stay within the default dynamic shared memory");
 
-// Copy the line operators of degree n1 - 1 into the constant table of the batched launch.
+// Copy the line operators of degree n1 - 1 into the constant table of the batched launches.
 cudaError_t set_batch_ops(int n1, const Ops &op)
 {
     return cudaMemcpyToSymbol(c_ops1d, &op, sizeof(Ops), (size_t)n1 * sizeof(Ops));
 }
 
-// The work counter is reset in the same stream before every launch (a captured memset node).
-cudaError_t launch_stage1d_batch(const StageArgs *d_args, const int2 *d_task_member, int *d_counter, int ctas,
+// The launch of degree n1 - 1: its counter is reset in the same stream before every launch (a captured
+// memset node); the first task and the end next to it are written with the task table.
+cudaError_t launch_stage1d_batch(int n1, const StageArgs *d_args, const int2 *d_task_member, int *d_block, int ctas,
                                  cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(d_block, 0, sizeof(int), s);
     if (e != cudaSuccess)
         return e;
-    k_stage1d_batch<<<ctas, kWarp * BGK_LINE_WARPS, BGK_LINE_WARPS * sizeof(LineWarp<4>), s>>>(d_args, d_task_member,
-                                                                                                d_counter);
+    switch (n1) {
+    case 2: k_stage1d_batch<2><<<ctas, kWarp * BGK_LINE_WARPS, BGK_LINE_WARPS * sizeof(LineWarp<2>), s>>>(
+        d_args, d_task_member, d_block); break;
+    case 3: k_stage1d_batch<3><<<ctas, kWarp * BGK_LINE_WARPS, BGK_LINE_WARPS * sizeof(LineWarp<3>), s>>>(
+        d_args, d_task_member, d_block); break;
+    case 4: k_stage1d_batch<4><<<ctas, kWarp * BGK_LINE_WARPS, BGK_LINE_WARPS * sizeof(LineWarp<4>), s>>>(
+        d_args, d_task_member, d_block); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-// CTAs of the persistent launch: every SM filled to the kernel's occupancy.
-int stage1d_batch_ctas()
+// CTAs of the persistent launch of degree n1 - 1: every SM filled to the kernel's occupancy.
+int stage1d_batch_ctas(int n1)
 {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage1d_batch, kWarp * BGK_LINE_WARPS,
-                                                  BGK_LINE_WARPS * sizeof(LineWarp<4>));
+    if (n1 == 2)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage1d_batch<2>, kWarp * BGK_LINE_WARPS,
+                                                      BGK_LINE_WARPS * sizeof(LineWarp<2>));
+    else if (n1 == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage1d_batch<3>, kWarp * BGK_LINE_WARPS,
+                                                      BGK_LINE_WARPS * sizeof(LineWarp<3>));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_stage1d_batch<4>, kWarp * BGK_LINE_WARPS,
+                                                      BGK_LINE_WARPS * sizeof(LineWarp<4>));
     return nsm * (per > 0 ? per : 1);
 }
 
@@ -479,9 +474,9 @@ cudaError_t prepare_stage(int dim, int p)
         case 3: return prepare_stage3_p3();
         }
     } else if (dim == 1 && p >= 1 && p <= 5) {
-        return cudaSuccess;  // the line kernels use static shared memory only
+        return cudaSuccess;  // the line kernels stay within the default dynamic shared memory
     } else if (dim == 2 && p >= 1 && p <= 3) {
-        return cudaSuccess;  // so do the quadrilateral kernels
+        return cudaSuccess;  // the quadrilateral kernels use static shared memory only
     }
     return cudaErrorInvalidValue;
 }
