@@ -548,8 +548,14 @@ cudaError_t launch3_any(const StageArgs &A, int mode, int oct, cudaStream_t s)
     if (A.met)  // curvilinear hexahedra: the metric, the upwind side per lane
         return A.ftab ? (general ? launch3<N1, 0, 8, 1, 2>(A, s) : launch3<N1, 0, 8, 0, 2>(A, s))
                       : (general ? launch3c<N1, 1>(A, s) : launch3c<N1, 0>(A, s));
-    if constexpr (N1 <= 3)  // p <= 2: one warp per element
-        return general ? launch3w_oct<N1, 1>(A, oct, s) : launch3w_oct<N1, 0>(A, oct, s);
+    if constexpr (N1 <= 3) {  // p <= 2: one warp per element
+        // Dirichlet faces and the limiter only (no wall, force or variable tau, one spacing): GEN = 2
+        bool full = A.fpar != nullptr || !A.viso || A.vtau;
+        for (int f = 0; f < 6; f++)
+            full = full || A.mesh.bc[f] == 2;
+        return !general ? launch3w_oct<N1, 0>(A, oct, s)
+                        : (full ? launch3w_oct<N1, 1>(A, oct, s) : launch3w_oct<N1, 2>(A, oct, s));
+    }
     else
         return general ? launch3s_oct<N1, 1>(A, oct, s) : launch3s_oct<N1, 0>(A, oct, s);
 }

@@ -2,6 +2,8 @@
 // form): one warp per element, every operand staged in shared memory by bulk asynchronous copies.
 // Instantiated in k_stage3_p1.cu and k_stage3_p2.cu.
 #pragma once
+#include <type_traits>
+
 #include "stage_common.cuh"
 
 #ifndef BGK_STAGE3W_WARPS
@@ -29,6 +31,10 @@ namespace bgk {
 //          the z-upwind neighbour (read by the z-lines), then the tile's output, transposed, for the
 //          moment sums; each slot takes the next tile's copies as soon as it is consumed;
 //   tab[2] the tile's velocity table (grid indices, W, energy weight), with f_s on its barrier.
+// Forms: GEN = 0 every face periodic or an exchange face, no force, no limiter, constant tau, one
+// velocity spacing; GEN = 2 adds Dirichlet ghosts and the limiter; GEN = 1 everything (diffuse walls,
+// the force source, variable tau, per-axis spacings). Feature tests that are uniform over a launch sit
+// outside the unrolled node loops, so every such loop stays one basic block.
 // ------------------------------------------------------------------------------------------------
 template <int N1, int GEN>
 struct __align__(16) Stage3wWarp {  // a multiple of 16 bytes, so every warp's copy targets stay aligned
@@ -37,7 +43,7 @@ struct __align__(16) Stage3wWarp {  // a multiple of 16 bytes, so every warp's c
     float sl[3][NP][kWarp];
     float tab[2][5][kWarp];
     float par[(NP + 1) / 2][kParamStride][2];  // BGK exponents by node pair (the last pair repeats node NP-1)
-    float fpar[GEN ? NP : 1][GEN ? kParamStride : 1];
+    float fpar[GEN == 1 ? NP : 1][GEN == 1 ? kParamStride : 1];
     unsigned long long bar[5];  // fs and the table of tile parity 0 and 1, sl[0..2]
 };
 
@@ -74,7 +80,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
             const int c = q % kParamStride, s2 = (q / kParamStride) & 1, h = q / (2 * kParamStride);
             sm.par[h][c][s2] = __ldg(src + min(2 * h + s2, NP - 1) * kParamStride + c);
         }
-        if (GEN && A.fpar) {
+        if (GEN == 1 && A.fpar) {
             const float4 *f4 = reinterpret_cast<const float4 *>(A.fpar + (int64_t)e * NP * kParamStride);
             float4 *d4 = reinterpret_cast<float4 *>(&sm.fpar[0][0]);
             for (int q = lane; q < NP * kParamStride / 4; q += kWarp)
@@ -211,12 +217,16 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
             issue_elem(OCT < 8 ? csrc : role_src(en, oct), vl, ka);
         }
         // acc = an f^n + b (1 - dt/tau) f_s
+        // (the launch-uniform feature tests sit outside the unrolled node loops, which then stay one
+        // basic block each)
+        if (GEN == 1 && A.vtau) {
 #pragma unroll
-        for (int q = 0; q < NP; q++) {
-            float kbq = kb;
-            if (GEN && A.vtau)
-                kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[q / 2][6][q % 2]));
-            acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
+            for (int q = 0; q < NP; q++)
+                acc[q] = fmaf(A.an, acc[q], __fsub_rn(A.b, __fmul_rn(bdt, sm.par[q / 2][6][q % 2])) * f[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NP; q++)
+                acc[q] = fmaf(A.an, acc[q], kb * f[q]);
         }
         const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt;
         const float cz = -A.mesh.inv_h2[2] * x2 * bdt;
@@ -228,15 +238,29 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
             gx = enx != -1 ? 0.f : __ldg(A.ghost + fx * A.nslots + slot);
             gy = eny >= 0 ? 0.f : __ldg(A.ghost + fy * A.nslots + slot);
             gz = enz >= 0 ? 0.f : __ldg(A.ghost + fz * A.nslots + slot);
-            if (enx < 0 && A.mesh.bc[fx] == 2)
+            if (GEN == 1 && enx < 0 && A.mesh.bc[fx] == 2)
                 rwx = A.rhow + ((int64_t)fx * A.nfmax + face_elem(A.mesh, ec, 0)) * NQ;
-            if (eny < 0 && A.mesh.bc[fy] == 2)
+            if (GEN == 1 && eny < 0 && A.mesh.bc[fy] == 2)
                 rwy = A.rhow + ((int64_t)fy * A.nfmax + face_elem(A.mesh, ec, 1)) * NQ;
-            if (enz < 0 && A.mesh.bc[fz] == 2)
+            if (GEN == 1 && enz < 0 && A.mesh.bc[fz] == 2)
                 rwz = A.rhow + ((int64_t)fz * A.nfmax + face_elem(A.mesh, ec, 2)) * NQ;
         }
+        // the wall densities of one direction's face points (1 where the face is not a wall)
+        float rw[NQ];
+        auto wall_rows = [&](const float *p) {
+            if (GEN == 1 && p) {
+#pragma unroll
+                for (int k = 0; k < NQ; k++)
+                    rw[k] = __ldg(p + k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < NQ; k++)
+                    rw[k] = 1.f;
+            }
+        };
         // x-lines (iy, iz): nodes j + N1 iy + NQ iz
         wait(2 + kx);
+        wall_rows(rwx);
 #pragma unroll
         for (int ln = 0; ln < NQ; ln++) {  // ln = iy + N1 iz, the line's face point
             float fl[N1], sv[N1], v[N1];
@@ -245,7 +269,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                 fl[j] = f[j + N1 * ln];
                 v[j] = sm.sl[kx][j + N1 * ln][lane];
             }
-            const float bx = rwx ? gx * __ldg(rwx + ln) : gx;
+            const float bx = gx * rw[ln];
             if (l0)
                 line_sums_jump<N1, true>(sv, fl, enx != -1 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0], A.ops);
             else
@@ -257,6 +281,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
         }
         // y-lines (ix, iz): nodes ix + N1 j + NQ iz
         wait(2 + ky);
+        wall_rows(rwy);
 #pragma unroll
         for (int iz = 0; iz < N1; iz++)
 #pragma unroll
@@ -267,7 +292,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                     fl[j] = f[ix + N1 * j + NQ * iz];
                     v[j] = sm.sl[ky][ix + N1 * j + NQ * iz][lane];
                 }
-                const float by = rwy ? gy * __ldg(rwy + ix + N1 * iz) : gy;
+                const float by = gy * rw[ix + N1 * iz];
                 if (l1)
                     line_sums_jump<N1, true>(sv, fl, eny >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : by - fl[0], A.ops);
                 else
@@ -286,6 +311,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
         }
         // z-lines (ix, iy): nodes ix + N1 iy + NQ j
         wait(2 + ka);
+        wall_rows(rwz);
 #pragma unroll
         for (int q = 0; q < NQ; q++) {  // q = ix + N1 iy, the line's face point
             float fl[N1], sv[N1], v[N1];
@@ -294,7 +320,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                 fl[j] = f[q + NQ * j];
                 v[j] = sm.sl[ka][q + NQ * j][lane];
             }
-            const float bz = rwz ? gz * __ldg(rwz + q) : gz;
+            const float bz = gz * rw[q];
             if (l2)
                 line_sums_jump<N1, true>(sv, fl, enz >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bz - fl[0], A.ops);
             else
@@ -309,41 +335,55 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
         const float cg = A.kg * gm, cf = bdt * gm;
         const float xs = x0 * x0 + x1 * x1 + x2 * x2;
         const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
-        const bool iso = !GEN || A.viso;
+        const bool iso = GEN != 1 || A.viso;
         const unsigned long long M0 = pack2(m0, m0), M1 = pack2(m1, m1), M2 = pack2(m2, m2);
         const unsigned long long U0 = iso ? pack2(mms, mms) : pack2(mm0, mm0);
         const unsigned long long U1 = iso ? U0 : pack2(mm1, mm1);
         const unsigned long long U2 = iso ? 0ull : pack2(mm2, mm2);
         float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
+        auto bgk_src = [&](auto vtau_c, auto force_c) {
+            constexpr bool VT = decltype(vtau_c)::value, FP = decltype(force_c)::value;
 #pragma unroll
-        for (int h = 0; h < NH; h++) {
-            const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[h][0][0]);
-            const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];
-            const unsigned long long lin =
-                ffma2(pack2(p23.z, p23.w), M2,
-                      ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
-            const unsigned long long ex =
-                GEN ? ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
-                    : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
-            float g[2];
-            exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
+            for (int h = 0; h < NH; h++) {
+                const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[h][0][0]);
+                const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];
+                const unsigned long long lin =
+                    ffma2(pack2(p23.z, p23.w), M2,
+                          ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
+                const unsigned long long ex =
+                    GEN == 1
+                        ? ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
+                        : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
+                float g[2];
+                exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
 #pragma unroll
-            for (int s2 = 0; s2 < 2; s2++) {
-                const int q = 2 * h + s2;
-                if (q >= NP)
-                    break;
-                float gc = cg;
-                if (GEN && A.vtau) {
-                    const float itau = s2 == 0 ? p67.x : p67.y;
-                    gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
+                for (int s2 = 0; s2 < 2; s2++) {
+                    const int q = 2 * h + s2;
+                    if (q >= NP)
+                        break;
+                    float gc = cg;
+                    if constexpr (VT) {
+                        const float itau = s2 == 0 ? p67.x : p67.y;
+                        gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
+                    }
+                    if constexpr (FP) {
+                        const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[q][0]);
+                        const float qv = fmaf(sm.fpar[q][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
+                        gc = fmaf(cf, qv, cg);
+                    }
+                    acc[q] = fmaf(gc, g[s2], acc[q]);  // the stage output
                 }
-                if (GEN && A.fpar) {
-                    const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[q][0]);
-                    const float qv = fmaf(sm.fpar[q][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
-                    gc = fmaf(cf, qv, cg);
-                }
-                acc[q] = fmaf(gc, g[s2], acc[q]);  // the stage output
             }
+        };
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        if constexpr (GEN == 1) {
+            if (A.fpar)
+                A.vtau ? bgk_src(T_{}, T_{}) : bgk_src(F_{}, T_{});
+            else
+                A.vtau ? bgk_src(T_{}, F_{}) : bgk_src(F_{}, F_{});
+        } else {
+            bgk_src(F_{}, F_{});
         }
         if (GEN && A.limiter) {
             // Zhang-Shu (Sec. 2.1, Eqs. 10-11): the element mean (tensor Gauss-Legendre weights) and
@@ -457,12 +497,15 @@ cudaError_t prepare3w()
 {
     const int s0 = BGK_STAGE3W_WARPS * (int)sizeof(Stage3wWarp<N1, 0>);
     const int s1 = BGK_STAGE3W_WARPS * (int)sizeof(Stage3wWarp<N1, 1>);
+    const int s2 = BGK_STAGE3W_WARPS * (int)sizeof(Stage3wWarp<N1, 2>);
     cudaError_t e = cudaSuccess;
 #define BGK_P3W(O)                                                                                       \
     if (e == cudaSuccess)                                                                                \
         e = cudaFuncSetAttribute(k_stage3w<N1, O, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0); \
     if (e == cudaSuccess)                                                                                \
-        e = cudaFuncSetAttribute(k_stage3w<N1, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+        e = cudaFuncSetAttribute(k_stage3w<N1, O, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1); \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(k_stage3w<N1, O, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
     BGK_P3W(0) BGK_P3W(1) BGK_P3W(2) BGK_P3W(3) BGK_P3W(4) BGK_P3W(5) BGK_P3W(6) BGK_P3W(7) BGK_P3W(8)
 #undef BGK_P3W
     return e;
