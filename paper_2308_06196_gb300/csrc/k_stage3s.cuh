@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                 if (GEN && A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
                     const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
                     const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
-                    gc = fmaf(cf, qv, cg);
+                    gc = fmaf(cf, qv, gc);  // on top of the node's own Maxwellian weight
                 }
                 const float o = fmaf(gc, g[sl], a);
                 if (GEN && A.limiter) {  // stored after the limiter below

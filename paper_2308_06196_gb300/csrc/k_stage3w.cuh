@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                     if constexpr (FP) {
                         const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[q][0]);
                         const float qv = fmaf(sm.fpar[q][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
-                        gc = fmaf(cf, qv, cg);
+                        gc = fmaf(cf, qv, gc);  // on top of the node's own Maxwellian weight
                     }
                     acc[q] = fmaf(gc, g[s2], acc[q]);  // the stage output
                 }

@@ -153,6 +153,26 @@ def test_variable_tau_line_and_hexahedra():
 
 
 @pytest.mark.parametrize("p", [2, 3])
+def test_variable_tau_with_body_force(p):
+    # a per-point collision time and the body-force source together (the general hexahedral kernels):
+    # the Maxwellian's weight is the node's own b dt / tau plus the force polynomial, against the oracle
+    bc, bcs = tube()
+    force = (0.3, 0.1, 0.0)
+    s, _ = make(3, [4, 2, 2], p, 8, 7.0, 1.0, bc, bcs, mu_ref=2e-3, mu_omega=0.81, body_force=force)
+    pr = orc.Problem(3, [4, 2, 2], [0.0] * 3, [1.0] * 3, p, (8,) * 3, (-7.0,) * 3, (7.0,) * 3, 1.0,
+                     bc=np.asarray(bc).reshape(6), bc_state=np.asarray(bcs, dtype=float).reshape(30), force=force)
+    pr.set_viscosity(2e-3, 0.81)
+    prim = W.prim_sod(pr.points(), (1.0, 1.0), (0.125, 0.8))
+    s.set_state(prim)
+    pr.set_state(prim)
+    dt = min(pr.dt(0.1), s.dt(0.1))
+    s.step(dt, 6)
+    pr.step(dt, 6)
+    assert rel(s.moments(), pr.moments()) < 1e-5
+    assert rel(s.get_f(), pr.get_f()) < 1e-5
+
+
+@pytest.mark.parametrize("p", [2, 3])
 def test_general_kernel_matches_lean_and_oracle(p):
     # a positive smooth periodic state: the limiter never acts, so the general kernel (limiter on)
     # must give the lean kernel's result; both against the oracle
