@@ -250,12 +250,16 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
             if (zs)
                 bulk_g2s(sl0 + ka * kSlot + (lane - RZ) * N1 * kRow, zs + vl * tstride, N1 * kRow, bb);
         }
+        // (launch-uniform feature tests sit outside the unrolled node loops, which stay one basic block)
+        if (GEN && A.vtau) {
 #pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            float kbq = kb;
-            if (GEN && A.vtau)
-                kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
-            acc[q] = fmaf(A.an, acc[q], kbq * sm.fs[b][q + NQ * w][lane]);
+            for (int q = 0; q < NQ; q++)
+                acc[q] = fmaf(A.an, acc[q],
+                              __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2])) * sm.fs[b][q + NQ * w][lane]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                acc[q] = fmaf(A.an, acc[q], kb * sm.fs[b][q + NQ * w][lane]);
         }
         // The lines of direction d through this warp's nodes: x- and y-lines of layer w (their sums
         // go to acc), z-lines of slice w (their sums overwrite the rows they read, after B1). Line ln
@@ -391,44 +395,67 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
         const unsigned long long U2 = iso ? 0ull : pack2(mm2, mm2);
         float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
         float lsum = 0.f, lmin = 3.4e38f;
+        auto bgk_src = [&](auto vtau_c, auto force_c, auto lim_c) {
+            constexpr bool VT = decltype(vtau_c)::value, FP = decltype(force_c)::value;
+            constexpr bool LIM = decltype(lim_c)::value;
 #pragma unroll
-        for (int h = 0; h < (NQ + 1) / 2; h++) {
-            const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[w][h][0][0]);
-            const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];
-            const unsigned long long lin =
-                ffma2(pack2(p23.z, p23.w), M2,
-                      ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
-            const unsigned long long ex =
-                GEN ? ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
-                    : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
-            float g[2];
-            exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
+            for (int h = 0; h < (NQ + 1) / 2; h++) {
+                const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[w][h][0][0]);
+                const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];
+                const unsigned long long lin =
+                    ffma2(pack2(p23.z, p23.w), M2,
+                          ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
+                const unsigned long long ex =
+                    GEN ? ffma2(pack2(p45.x, p45.y), U0,
+                                ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
+                        : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
+                float g[2];
+                exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
 #pragma unroll
-            for (int sl = 0; sl < 2; sl++) {
-                const int q = 2 * h + sl;
-                if (q >= NQ)
-                    break;
-                const int i = q + NQ * w;
-                const float a = acc[q];
-                float gc = cg;
-                if (GEN && A.vtau) {
-                    const float itau = sl == 0 ? p67.x : p67.y;
-                    gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
+                for (int sl = 0; sl < 2; sl++) {
+                    const int q = 2 * h + sl;
+                    if (q >= NQ)
+                        break;
+                    const int i = q + NQ * w;
+                    const float a = acc[q];
+                    float gc = cg;
+                    if constexpr (VT) {
+                        const float itau = sl == 0 ? p67.x : p67.y;
+                        gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
+                    }
+                    if constexpr (FP) {
+                        const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
+                        const float qv =
+                            fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
+                        gc = fmaf(cf, qv, gc);  // on top of the node's own Maxwellian weight
+                    }
+                    const float o = fmaf(gc, g[sl], a);
+                    if constexpr (LIM) {
+                        lsum = fmaf(sm.met[i][1].w, o, lsum);
+                        lmin = fminf(lmin, o);
+                    } else {
+                        __stcs(dst + i * kWarp, o);
+                    }
+                    sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))] = o;
                 }
-                if (GEN && A.fpar) {
-                    const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
-                    const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
-                    gc = fmaf(cf, qv, gc);  // on top of the node's own Maxwellian weight
-                }
-                const float o = fmaf(gc, g[sl], a);
-                if (GEN && A.limiter) {
-                    lsum = fmaf(sm.met[i][1].w, o, lsum);
-                    lmin = fminf(lmin, o);
-                } else {
-                    __stcs(dst + i * kWarp, o);
-                }
-                sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))] = o;
             }
+        };
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        if constexpr (GEN) {
+            if (A.limiter) {
+                if (A.fpar)
+                    A.vtau ? bgk_src(T_{}, T_{}, T_{}) : bgk_src(F_{}, T_{}, T_{});
+                else
+                    A.vtau ? bgk_src(T_{}, F_{}, T_{}) : bgk_src(F_{}, F_{}, T_{});
+            } else {
+                if (A.fpar)
+                    A.vtau ? bgk_src(T_{}, T_{}, F_{}) : bgk_src(F_{}, T_{}, F_{});
+                else
+                    A.vtau ? bgk_src(T_{}, F_{}, F_{}) : bgk_src(F_{}, F_{}, F_{});
+            }
+        } else {
+            bgk_src(F_{}, F_{}, F_{});
         }
         if (GEN && A.limiter) {
             // Zhang-Shu (Sec. 2.1, Eqs. 10-11) over the physical element: weights W J over their sum
@@ -443,16 +470,16 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
             }
             mean *= sm.iwj;
             const float beta = mn < 0.f ? fminf(fabsf(mean / (mean - mn)), 1.f) : 1.f;
+            if (mn < 0.f) {
 #pragma unroll
-            for (int q = 0; q < NQ; q++) {
-                float &slot_o = sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))];
-                float o = slot_o;
-                if (mn < 0.f) {
-                    o = fmaf(beta, o - mean, mean);
-                    slot_o = o;
+                for (int q = 0; q < NQ; q++) {
+                    float &slot_o = sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))];
+                    slot_o = fmaf(beta, slot_o - mean, mean);
                 }
-                __stcs(dst + (q + NQ * w) * kWarp, o);
             }
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                __stcs(dst + (q + NQ * w) * kWarp, sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))]);
         }
         // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values
         __syncwarp();

@@ -2,6 +2,8 @@
 // operand staged in shared memory by bulk asynchronous copies; instantiated per degree in
 // k_stage3_p*.cu.
 #pragma once
+#include <type_traits>
+
 #include "stage_common.cuh"
 
 #ifndef BGK_STAGE3S_MINCTAS_P3
@@ -249,12 +251,15 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                 bulk_g2s(sl0 + ka * kSlot + (lane - RZ) * N1 * kRow, zs + vl * tstride, N1 * kRow, bb);
         }
         // acc = an f^n + b (1 - dt/tau) f_s, then x and y lines
+        // (launch-uniform feature tests sit outside the unrolled node loops, which stay one basic block)
+        if (GEN && A.vtau) {  // variable collision time: b (1 - dt/tau) of every node
 #pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            float kbq = kb;
-            if (GEN && A.vtau)  // variable collision time: b (1 - dt/tau) of this node
-                kbq = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2]));
-            acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
+            for (int q = 0; q < NQ; q++)
+                acc[q] = fmaf(A.an, acc[q], __fsub_rn(A.b, __fmul_rn(bdt, sm.par[w][q / 2][6][q % 2])) * f[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                acc[q] = fmaf(A.an, acc[q], kb * f[q]);
         }
         const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt;
         const float cz = -A.mesh.inv_h2[2] * x2 * bdt;
@@ -275,6 +280,19 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             if (enz < 0 && A.mesh.bc[fz] == 2)
                 rwz = A.rhow + ((int64_t)fz * A.nfmax + face_elem(A.mesh, ec, 2)) * NQ + N1 * w;
         }
+        // the wall densities of a direction's face points of this warp's lines (1 off a wall face)
+        float rw[N1];
+        auto wall_rows = [&](const float *p) {
+            if (GEN && p) {
+#pragma unroll
+                for (int k = 0; k < N1; k++)
+                    rw[k] = __ldg(p + k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < N1; k++)
+                    rw[k] = 1.f;
+            }
+        };
         // The three line directions. Where the upwind neighbour of the line ends is an element (not a
         // Dirichlet or wall ghost) and N1 is even, two adjacent lines run at a time on packed pairs.
         constexpr bool kPair = N1 % 2 == 0;
@@ -301,6 +319,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                 }
             }
         } else {
+            wall_rows(rwx);
 #pragma unroll
             for (int iy = 0; iy < N1; iy++) {
                 float fl[N1], sv[N1], v[N1];
@@ -309,7 +328,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                     fl[j] = f[j + N1 * iy];
                     v[j] = sm.sl[w][kx][j + N1 * iy][lane];
                 }
-                const float bx = rwx ? gx * __ldg(rwx + iy) : gx;
+                const float bx = gx * rw[iy];
                 if (l0)
                     line_sums_jump<N1, true>(sv, fl, enx != -1 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0],
                                              A.ops);
@@ -345,6 +364,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                 }
             }
         } else {
+            wall_rows(rwy);
 #pragma unroll
             for (int ix = 0; ix < N1; ix++) {
                 float fl[N1], sv[N1], v[N1];
@@ -353,7 +373,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                     fl[j] = f[ix + N1 * j];
                     v[j] = sm.sl[w][ky][ix + N1 * j][lane];
                 }
-                const float by = rwy ? gy * __ldg(rwy + ix) : gy;
+                const float by = gy * rw[ix];
                 if (l1)
                     line_sums_jump<N1, true>(sv, fl, eny >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : by - fl[0],
                                              A.ops);
@@ -400,6 +420,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                 }
             }
         } else {
+            wall_rows(rwz);
 #pragma unroll
             for (int ix = 0; ix < N1; ix++) {
                 const int q = ix + N1 * w;
@@ -409,7 +430,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                     fl[j] = sm.fs[b][q + NQ * j][lane];
                     v[j] = sm.sl[w][ka][ix + N1 * j][lane];
                 }
-                const float bz = rwz ? gz * __ldg(rwz + ix) : gz;
+                const float bz = gz * rw[ix];
                 if (l2)
                     line_sums_jump<N1, true>(sv, fl, enz >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bz - fl[0],
                                              A.ops);
@@ -452,44 +473,67 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         const unsigned long long U2 = iso ? 0ull : pack2(mm2, mm2);
         float *dst = A.dst + fidx(vl, e, 0, lane, E, NP);
         float lsum = 0.f, lmin = 3.4e38f;  // limiter: this layer's weighted sum and minimum
+        auto bgk_src = [&](auto vtau_c, auto force_c, auto lim_c) {
+            constexpr bool VT = decltype(vtau_c)::value, FP = decltype(force_c)::value;
+            constexpr bool LIM = decltype(lim_c)::value;
 #pragma unroll
-        for (int h = 0; h < (NQ + 1) / 2; h++) {
-            const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[w][h][0][0]);
-            const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];  // (c, c+1) of both nodes
-            const unsigned long long lin =
-                ffma2(pack2(p23.z, p23.w), M2,
-                      ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
-            const unsigned long long ex =
-                GEN ? ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
-                    : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
-            float g[2];
-            exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
+            for (int h = 0; h < (NQ + 1) / 2; h++) {
+                const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[w][h][0][0]);
+                const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];  // (c, c+1) of both nodes
+                const unsigned long long lin =
+                    ffma2(pack2(p23.z, p23.w), M2,
+                          ffma2(pack2(p23.x, p23.y), M1, ffma2(pack2(p01.z, p01.w), M0, pack2(p01.x, p01.y))));
+                const unsigned long long ex =
+                    GEN ? ffma2(pack2(p45.x, p45.y), U0,
+                                ffma2(pack2(p45.z, p45.w), U1, ffma2(pack2(p67.x, p67.y), U2, lin)))
+                        : ffma2(pack2(p45.x, p45.y), U0, ffma2(pack2(p45.z, p45.w), U0, lin));
+                float g[2];
+                exp2_fp32x2(ex, pack2(p67.z, p67.w), g[0], g[1]);
 #pragma unroll
-            for (int sl = 0; sl < 2; sl++) {
-                const int q = 2 * h + sl;
-                if (q >= NQ)
-                    break;
-                const int i = q + NQ * w;
-                const float a = acc[q];
-                float gc = cg;
-                if (GEN && A.vtau) {  // kg = b - kb exactly, kb as in the accumulator above
-                    const float itau = sl == 0 ? p67.x : p67.y;
-                    gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
+                for (int sl = 0; sl < 2; sl++) {
+                    const int q = 2 * h + sl;
+                    if (q >= NQ)
+                        break;
+                    const int i = q + NQ * w;
+                    const float a = acc[q];
+                    float gc = cg;
+                    if constexpr (VT) {  // kg = b - kb exactly, kb as in the accumulator above
+                        const float itau = sl == 0 ? p67.x : p67.y;
+                        gc = __fsub_rn(A.b, __fsub_rn(A.b, __fmul_rn(bdt, itau))) * gm;
+                    }
+                    if constexpr (FP) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
+                        const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
+                        const float qv =
+                            fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
+                        gc = fmaf(cf, qv, gc);  // on top of the node's own Maxwellian weight
+                    }
+                    const float o = fmaf(gc, g[sl], a);
+                    if constexpr (LIM) {  // stored after the limiter below
+                        lsum = fmaf(A.ops.wq[q % N1] * A.ops.wq[q / N1], o, lsum);
+                        lmin = fminf(lmin, o);
+                    } else {
+                        __stcs(dst + i * kWarp, o);
+                    }
+                    sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))] = o;  // for the moments below
                 }
-                if (GEN && A.fpar) {  // body-force source g (q0 + q . xi + q4 |xi|^2)
-                    const float4 fq = *reinterpret_cast<const float4 *>(&sm.fpar[i][0]);
-                    const float qv = fmaf(sm.fpar[i][4], xs, fmaf(fq.w, x2, fmaf(fq.z, x1, fmaf(fq.y, x0, fq.x))));
-                    gc = fmaf(cf, qv, gc);  // on top of the node's own Maxwellian weight
-                }
-                const float o = fmaf(gc, g[sl], a);
-                if (GEN && A.limiter) {  // stored after the limiter below
-                    lsum = fmaf(A.ops.wq[q % N1] * A.ops.wq[q / N1], o, lsum);
-                    lmin = fminf(lmin, o);
-                } else {
-                    __stcs(dst + i * kWarp, o);
-                }
-                sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))] = o;  // for the moments below
             }
+        };
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        if constexpr (GEN) {
+            if (A.limiter) {
+                if (A.fpar)
+                    A.vtau ? bgk_src(T_{}, T_{}, T_{}) : bgk_src(F_{}, T_{}, T_{});
+                else
+                    A.vtau ? bgk_src(T_{}, F_{}, T_{}) : bgk_src(F_{}, F_{}, T_{});
+            } else {
+                if (A.fpar)
+                    A.vtau ? bgk_src(T_{}, T_{}, F_{}) : bgk_src(F_{}, T_{}, F_{});
+                else
+                    A.vtau ? bgk_src(T_{}, F_{}, F_{}) : bgk_src(F_{}, F_{}, F_{});
+            }
+        } else {
+            bgk_src(F_{}, F_{}, F_{});
         }
         if (GEN && A.limiter) {
             // Zhang-Shu (Sec. 2.1, Eqs. 10-11): element mean and minimum of every velocity over the
@@ -504,16 +548,16 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
                 mn = fminf(mn, sm.lim[1][lw][lane]);
             }
             const float beta = mn < 0.f ? fminf(fabsf(mean / (mean - mn)), 1.f) : 1.f;
+            if (mn < 0.f) {
 #pragma unroll
-            for (int q = 0; q < NQ; q++) {
-                float &slot_o = sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))];
-                float o = slot_o;
-                if (mn < 0.f) {
-                    o = fmaf(beta, o - mean, mean);
-                    slot_o = o;
+                for (int q = 0; q < NQ; q++) {
+                    float &slot_o = sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))];
+                    slot_o = fmaf(beta, slot_o - mean, mean);
                 }
-                __stcs(dst + (q + NQ * w) * kWarp, o);
             }
+#pragma unroll
+            for (int q = 0; q < NQ; q++)
+                __stcs(dst + (q + NQ * w) * kWarp, sm.fs[b][q + NQ * w][lane ^ (4 * (q & 7))]);
         }
         // moments of this layer's nodes (Eq. 2 with Eq. 12) of the stored values (rows np + 8 h)
         __syncwarp();
