@@ -9,6 +9,7 @@
 // The stage never reads what another task of the same launch writes: it reads f_s (source), f^n,
 // the BGK exponent table and the ghost table, and writes only its own part of the destination and
 // of the partial-moment table. The destination may alias f^n (the last stage updates f^n in place).
+#include <type_traits>
 #include "stage_common.cuh"
 
 namespace bgk {
@@ -64,7 +65,7 @@ struct __align__(16) LineWarp {
 //      written as the task's FP32 partial; the Newton kernel sums the partials of all tasks exactly.
 // MODE 0: full stage. MODE 1: moments of src only (no advection, no store). ph: the phase parity
 // bits of the warp's two barriers, carried across the tasks a warp runs.
-template <int N1, int MODE>
+template <int N1, int MODE, bool VT>
 __device__ __forceinline__ void line_task(const StageArgs &A, const int task, const Ops &op, LineWarp<N1> &sm,
                                           uint32_t &ph)
 {
@@ -154,48 +155,41 @@ __device__ __forceinline__ void line_task(const StageArgs &A, const int task, co
             const float cd = cdt * x0;
             const float gm = sm.tab[b][3][lane] != 0.f ? 1.f : 0.f;  // the padding mask
             const float cg = A.kg * gm;
-            // 1. advection of every element of the run: acc = an f^n + kb f_s + cd (line sums)
+            // 1. advection of every element of the run: acc = an f^n + kb f_s + cd (line sums). Every
+            // element slot of the run is computed (those past a short run from stale rows, never stored),
+            // and the inflow side is one test per tile, so the unrolled loops stay one basic block each.
+            float gh = 0.f;  // the Dirichlet ghost value at the run's inflow end, where it is a boundary
+            if (left ? enL < 0 : enR < 0)
+                gh = __ldg(A.ghost + (left ? 0 : A.nslots) + slot);
+            auto advect = [&](auto left_c) {
+                constexpr bool LEFT = decltype(left_c)::value;
 #pragma unroll
-            for (int k = 0; k < K; k++) {
-                if (k >= ne)
-                    break;
-                float fl[N1], v[N1], sd[N1];
+                for (int k = 0; k < K; k++) {
+                    float fl[N1], v[N1], sd[N1];
 #pragma unroll
-                for (int j = 0; j < N1; j++)
-                    fl[j] = sm.fs[b][N1 + k * N1 + j][lane];
-                if (left) {
-                    float T;
-                    if (k > 0 || enL >= 0) {
-#pragma unroll
-                        for (int j = 0; j < N1; j++)
-                            v[j] = sm.fs[b][k * N1 + j][lane];
-                        T = trace_line<N1, true>(v, op);
-                    } else {
-                        T = __ldg(A.ghost + slot);
+                    for (int j = 0; j < N1; j++) {
+                        fl[j] = sm.fs[b][N1 + k * N1 + j][lane];
+                        v[j] = sm.fs[b][LEFT ? k * N1 + j : N1 + (k + 1) * N1 + j][lane];
                     }
-                    line_sums<N1, true>(sd, fl, T, op);
-                } else {
-                    float T;
-                    if (k < ne - 1 || enR >= 0) {
+                    const float tr = trace_line<N1, LEFT>(v, op);
+                    const bool inner = LEFT ? (k > 0 || enL >= 0) : (k < ne - 1 || enR >= 0);
+                    line_sums<N1, LEFT>(sd, fl, inner ? tr : gh, op);
 #pragma unroll
-                        for (int j = 0; j < N1; j++)
-                            v[j] = sm.fs[b][N1 + (k + 1) * N1 + j][lane];
-                        T = trace_line<N1, false>(v, op);
-                    } else {
-                        T = __ldg(A.ghost + A.nslots + slot);
+                    for (int j = 0; j < N1; j++) {
+                        const int r = k * N1 + j;
+                        const float fr = sm.fn[b][r][lane];
+                        const float fnv = has_fn ? fr : 0.f;
+                        float kbi = kb;
+                        if constexpr (VT)  // per-node weights, rounded so that kb + kg = b exactly
+                            kbi = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[r / 2][6][r % 2]));
+                        acc[r] = fmaf(cd, sd[j], fmaf(A.an, fnv, kbi * fl[j]));
                     }
-                    line_sums<N1, false>(sd, fl, T, op);
                 }
-#pragma unroll
-                for (int j = 0; j < N1; j++) {
-                    const int r = k * N1 + j;
-                    const float fnv = has_fn ? sm.fn[b][r][lane] : 0.f;
-                    float kbi = kb;
-                    if (A.vtau)  // per-node weights, rounded so that kb + kg = b exactly
-                        kbi = __fsub_rn(A.b, __fmul_rn(bdt, sm.par[r / 2][6][r % 2]));
-                    acc[r] = fmaf(cd, sd[j], fmaf(A.an, fnv, kbi * fl[j]));
-                }
-            }
+            };
+            if (left)
+                advect(std::true_type{});
+            else
+                advect(std::false_type{});
             // 2. BGK source towards the conservative Maxwellian, two nodes at a time
             const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
             const unsigned long long M0 = pack2(m0, m0), M1 = pack2(m1, m1), M2 = pack2(m2, m2);
@@ -203,9 +197,7 @@ __device__ __forceinline__ void line_task(const StageArgs &A, const int task, co
             const unsigned long long U1 = viso ? U0 : pack2(mm1, mm1);
             const unsigned long long U2 = viso ? 0ull : pack2(mm2, mm2);
 #pragma unroll
-            for (int h = 0; h < NH; h++) {
-                if (2 * h >= nr)
-                    break;
+            for (int h = 0; h < NH; h++) {  // pairs past a short run: clamped exponents, never stored
                 const float4 *pp = reinterpret_cast<const float4 *>(&sm.par[h][0][0]);
                 const float4 p01 = pp[0], p23 = pp[1], p45 = pp[2], p67 = pp[3];  // (c, c+1) of both nodes
                 const unsigned long long lin =
@@ -221,7 +213,7 @@ __device__ __forceinline__ void line_task(const StageArgs &A, const int task, co
                     if (r >= NW)
                         break;
                     float cgi = cg;
-                    if (A.vtau) {
+                    if constexpr (VT) {
                         const float kbi = __fsub_rn(A.b, __fmul_rn(bdt, s2 == 0 ? p67.x : p67.y));
                         cgi = __fsub_rn(A.b, kbi) * gm;
                     }
@@ -232,9 +224,7 @@ __device__ __forceinline__ void line_task(const StageArgs &A, const int task, co
                 // Zhang-Shu (Sec. 2.1, Eqs. 10-11): contract towards the element mean where a node
                 // value of this velocity is negative
 #pragma unroll
-                for (int k = 0; k < K; k++) {
-                    if (k >= ne)
-                        break;
+                for (int k = 0; k < K; k++) {  // (element slots past a short run: never stored)
                     float mean = 0.f, mn = acc[k * N1];
 #pragma unroll
                     for (int j = 0; j < N1; j++) {
@@ -366,7 +356,10 @@ __global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS) k_sta
     LineWarp<N1> &sm = reinterpret_cast<LineWarp<N1> *>(smraw)[w];
     line_init_barriers(smem_u32(&sm.bar[0]));
     uint32_t ph = 0;
-    line_task<N1, MODE>(A, task, A.ops, sm, ph);
+    if (MODE == 0 && A.vtau)
+        line_task<N1, MODE, true>(A, task, A.ops, sm, ph);
+    else
+        line_task<N1, MODE, false>(A, task, A.ops, sm, ph);
 }
 
 // Batched line-element stages: one persistent launch per degree over the tasks of that degree's
@@ -393,7 +386,10 @@ __global__ void __launch_bounds__(kWarp *BGK_LINE_WARPS, BGK_LINE_MINCTAS)
         if (item >= end)
             break;
         const int2 tm = __ldg(task_member + item);  // (member, its task index)
-        line_task<N1, 0>(args[tm.x], tm.y, c_ops1d[N1], sm, ph);
+        if (args[tm.x].vtau)
+            line_task<N1, 0, true>(args[tm.x], tm.y, c_ops1d[N1], sm, ph);
+        else
+            line_task<N1, 0, false>(args[tm.x], tm.y, c_ops1d[N1], sm, ph);
     }
 }
 
