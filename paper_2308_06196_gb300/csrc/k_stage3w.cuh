@@ -258,6 +258,9 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                     rw[k] = 1.f;
             }
         };
+        // whether a direction's inflow face has an element behind it (else its ghost value); the trace
+        // and the ghost jump are both formed and one is selected, so the line loops have no branch
+        const bool inx = GEN == 0 || enx != -1, iny = GEN == 0 || eny >= 0, inz = GEN == 0 || enz >= 0;
         // x-lines (iy, iz): nodes j + N1 iy + NQ iz
         wait(2 + kx);
         wall_rows(rwx);
@@ -270,11 +273,13 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                 v[j] = sm.sl[kx][j + N1 * ln][lane];
             }
             const float bx = gx * rw[ln];
-            if (l0)
-                line_sums_jump<N1, true>(sv, fl, enx != -1 ? trace_jump<N1, true>(v, fl[0], A.ops) : bx - fl[0], A.ops);
-            else
-                line_sums_jump<N1, false>(sv, fl, enx != -1 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bx - fl[N1 - 1],
-                                          A.ops);
+            if (l0) {
+                const float tj = trace_jump<N1, true>(v, fl[0], A.ops), gj = bx - fl[0];
+                line_sums_jump<N1, true>(sv, fl, inx ? tj : gj, A.ops);
+            } else {
+                const float tj = trace_jump<N1, false>(v, fl[N1 - 1], A.ops), gj = bx - fl[N1 - 1];
+                line_sums_jump<N1, false>(sv, fl, inx ? tj : gj, A.ops);
+            }
 #pragma unroll
             for (int j = 0; j < N1; j++)
                 acc[j + N1 * ln] = fmaf(cx, sv[j], acc[j + N1 * ln]);
@@ -293,11 +298,13 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                     v[j] = sm.sl[ky][ix + N1 * j + NQ * iz][lane];
                 }
                 const float by = gy * rw[ix + N1 * iz];
-                if (l1)
-                    line_sums_jump<N1, true>(sv, fl, eny >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : by - fl[0], A.ops);
-                else
-                    line_sums_jump<N1, false>(sv, fl, eny >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops)
-                                                               : by - fl[N1 - 1], A.ops);
+                if (l1) {
+                    const float tj = trace_jump<N1, true>(v, fl[0], A.ops), gj = by - fl[0];
+                    line_sums_jump<N1, true>(sv, fl, iny ? tj : gj, A.ops);
+                } else {
+                    const float tj = trace_jump<N1, false>(v, fl[N1 - 1], A.ops), gj = by - fl[N1 - 1];
+                    line_sums_jump<N1, false>(sv, fl, iny ? tj : gj, A.ops);
+                }
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     acc[ix + N1 * j + NQ * iz] = fmaf(cy, sv[j], acc[ix + N1 * j + NQ * iz]);
@@ -321,11 +328,13 @@ __global__ void __launch_bounds__(kWarp *BGK_STAGE3W_WARPS, (N1 == 3 ? BGK_STAGE
                 v[j] = sm.sl[ka][q + NQ * j][lane];
             }
             const float bz = gz * rw[q];
-            if (l2)
-                line_sums_jump<N1, true>(sv, fl, enz >= 0 ? trace_jump<N1, true>(v, fl[0], A.ops) : bz - fl[0], A.ops);
-            else
-                line_sums_jump<N1, false>(sv, fl, enz >= 0 ? trace_jump<N1, false>(v, fl[N1 - 1], A.ops) : bz - fl[N1 - 1],
-                                          A.ops);
+            if (l2) {
+                const float tj = trace_jump<N1, true>(v, fl[0], A.ops), gj = bz - fl[0];
+                line_sums_jump<N1, true>(sv, fl, inz ? tj : gj, A.ops);
+            } else {
+                const float tj = trace_jump<N1, false>(v, fl[N1 - 1], A.ops), gj = bz - fl[N1 - 1];
+                line_sums_jump<N1, false>(sv, fl, inz ? tj : gj, A.ops);
+            }
 #pragma unroll
             for (int j = 0; j < N1; j++)
                 acc[q + NQ * j] = fmaf(cz, sv[j], acc[q + NQ * j]);
