@@ -116,21 +116,21 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_sta
             // upwind neighbours (or the face's ghost) in x and y
             const int enx = upwind_neighbour(A.mesh, ec, 0, l0), eny = upwind_neighbour(A.mesh, ec, 1, l1);
             float vx[N1][N1], vy[N1][N1];
-            if (enx >= 0) {
-                const float *nb = A.src + fidx(vl, enx, 0, lane, E, NQ);
+            {  // (a boundary face: zeros, whose trace is discarded below)
+                const float *nb = A.src + fidx(vl, max(enx, 0), 0, lane, E, NQ);
 #pragma unroll
                 for (int iy = 0; iy < N1; iy++)
 #pragma unroll
                     for (int j = 0; j < N1; j++)
-                        vx[iy][j] = __ldg(nb + (j + N1 * iy) * kWarp);
+                        vx[iy][j] = enx >= 0 ? __ldg(nb + (j + N1 * iy) * kWarp) : 0.f;
             }
-            if (eny >= 0) {
-                const float *nb = A.src + fidx(vl, eny, 0, lane, E, NQ);
+            {
+                const float *nb = A.src + fidx(vl, max(eny, 0), 0, lane, E, NQ);
 #pragma unroll
                 for (int ix = 0; ix < N1; ix++)
 #pragma unroll
                     for (int j = 0; j < N1; j++)
-                        vy[ix][j] = __ldg(nb + (ix + N1 * j) * kWarp);
+                        vy[ix][j] = eny >= 0 ? __ldg(nb + (ix + N1 * j) * kWarp) : 0.f;
             }
             const float gx = enx >= 0 ? 0.f : __ldg(A.ghost + (l0 ? 0 : 1) * A.nslots + slot);
             const float gy = eny >= 0 ? 0.f : __ldg(A.ghost + (l1 ? 2 : 3) * A.nslots + slot);
@@ -148,10 +148,13 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_sta
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     fl[j] = f[j + N1 * iy];
-                if (l0)
-                    line_sums<N1, true>(sv, fl, enx >= 0 ? trace_line<N1, true>(vx[iy], A.ops) : gx, A.ops);
-                else
-                    line_sums<N1, false>(sv, fl, enx >= 0 ? trace_line<N1, false>(vx[iy], A.ops) : gx, A.ops);
+                if (l0) {
+                    const float t = trace_line<N1, true>(vx[iy], A.ops);
+                    line_sums<N1, true>(sv, fl, enx >= 0 ? t : gx, A.ops);
+                } else {
+                    const float t = trace_line<N1, false>(vx[iy], A.ops);
+                    line_sums<N1, false>(sv, fl, enx >= 0 ? t : gx, A.ops);
+                }
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
@@ -162,10 +165,13 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_sta
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     fl[j] = f[ix + N1 * j];
-                if (l1)
-                    line_sums<N1, true>(sv, fl, eny >= 0 ? trace_line<N1, true>(vy[ix], A.ops) : gy, A.ops);
-                else
-                    line_sums<N1, false>(sv, fl, eny >= 0 ? trace_line<N1, false>(vy[ix], A.ops) : gy, A.ops);
+                if (l1) {
+                    const float t = trace_line<N1, true>(vy[ix], A.ops);
+                    line_sums<N1, true>(sv, fl, eny >= 0 ? t : gy, A.ops);
+                } else {
+                    const float t = trace_line<N1, false>(vy[ix], A.ops);
+                    line_sums<N1, false>(sv, fl, eny >= 0 ? t : gy, A.ops);
+                }
 #pragma unroll
                 for (int j = 0; j < N1; j++)
                     acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         // Dirichlet or wall ghost) and N1 is even, two adjacent lines run at a time on packed pairs.
         constexpr bool kPair = N1 % 2 == 0;
         wait(2 + kx);
-        if (kPair && enx != -1) {
+        if (kPair && (GEN == 0 || enx != -1)) {
 #pragma unroll
             for (int iy = 0; iy < N1; iy += 2) {
                 unsigned long long fl[N1], sv[N1], v[N1];
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             }
         }
         wait(2 + ky);
-        if (kPair && eny >= 0) {
+        if (kPair && (GEN == 0 || eny >= 0)) {
 #pragma unroll
             for (int ix = 0; ix < N1; ix += 2) {
                 unsigned long long fl[N1], sv[N1], v[N1];
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         // z-lines of slice iy = w (all layers) from the shared tile, the upwind trace from the staged
         // neighbour rows; each line's derivative sums overwrite the rows it read
         wait(2 + ka);
-        if (kPair && enz >= 0) {
+        if (kPair && (GEN == 0 || enz >= 0)) {
 #pragma unroll
             for (int ix = 0; ix < N1; ix += 2) {
                 const int q = ix + N1 * w;
