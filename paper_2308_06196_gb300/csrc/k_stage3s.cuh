@@ -207,14 +207,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         if (OCT == 8 && vl + 1 < vl1)
             nbrs(vl + 1, enn);
         const bool more = vl + 1 < vl1;
-        // the other buffer's layer rows were last read and written before the previous tile's B2 (the
-        // z-lines) and by this warp's own moment pass, so the next tile's layer may land there now
-        __syncwarp();
-        if (lane == 0 && more) {
-            fence_proxy_async();
-            mbar_arrive_expect_tx(bar(b ^ 1), kSlot);
-            bulk_g2s(fs0 + (b ^ 1) * kFsBuf, csrc + (vl + 1) * tstride, kSlot, bar(b ^ 1));
-        }
         const int oct = OCT < 8 ? OCT : (int)__ldg(A.toct + vt);
         const bool l0 = (oct & 1) != 0, l1 = (oct & 2) != 0, l2 = (oct & 4) != 0;
         const int enx = en[0], eny = en[1], enz = en[2];
@@ -387,11 +379,19 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
             }
         }
         // slots kx and ky are consumed: the next tile's f^n and x-neighbour layer land there
+        // and the next tile's f_s layer into the other buffer, whose rows were last read and written
+        // before the previous tile's B2 (the z-lines) and by this warp's own moment pass: one code path
+        // for the three role lanes
         __syncwarp();
-        if (more && ((lane == RFN && has_fn) || lane == RX)) {
+        if (more && (lane == 0 || (lane == RFN && has_fn) || lane == RX)) {
+            const float *ns = lane == RX && OCT == 8 ? role_src(enn, (int)__ldg(A.toct + vt + 1)) : csrc;
+            const int k = lane == RX ? ky : kx;
+            const uint32_t bb = lane == 0 ? bar(b ^ 1) : bar(2 + k);
+            const uint32_t dst = lane == 0 ? fs0 + (b ^ 1) * kFsBuf : sl0 + k * kSlot;
             fence_proxy_async();
-            issue_layer(lane == RX && OCT == 8 ? role_src(enn, (int)__ldg(A.toct + vt + 1)) : csrc, vl + 1,
-                        lane == RX ? ky : kx);
+            mbar_arrive_expect_tx(bb, ns ? kSlot : 0);
+            if (ns)
+                bulk_g2s(dst, ns + (vl + 1) * cstride, kSlot, bb);
         }
         __syncthreads();  // B1: every layer of the element tile has landed (each warp waited for its own)
         // z-lines of slice iy = w (all layers) from the shared tile, the upwind trace from the staged
@@ -446,15 +446,17 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN ? BGK_STAGE3S_MINCT
         // slot ka is consumed: the next tile's y-neighbour layer lands there; warp 0 also brings the next
         // tile's velocity table into the other table buffer, which every warp is done with (B1)
         __syncwarp();
-        if (more && (lane == RY || (w == 0 && lane == RT))) {
+        if (more && (lane == RY || (w == 0 && lane == RT))) {  // one code path for both role lanes
+            const bool t = lane == RT;
+            const float *ys = t ? nullptr : (OCT < 8 ? csrc : role_src(enn, (int)__ldg(A.toct + vt + 1)));
+            const float *ns = t ? A.vtab + (int64_t)(vt + 1) * kTabRows * kWarp : (ys ? ys + (vl + 1) * cstride : nullptr);
+            const uint32_t bb = t ? tbar(b ^ 1) : bar(2 + ka);
+            const uint32_t dst = t ? smem_u32(&sm.tab[b ^ 1][0][0]) : sl0 + ka * kSlot;
+            const uint32_t bytes = t ? kTabRows * kRow : kSlot;
             fence_proxy_async();
-            if (lane == RY) {
-                issue_layer(OCT < 8 ? csrc : role_src(enn, (int)__ldg(A.toct + vt + 1)), vl + 1, ka);
-            } else {
-                mbar_arrive_expect_tx(tbar(b ^ 1), kTabRows * kRow);
-                bulk_g2s(smem_u32(&sm.tab[b ^ 1][0][0]), A.vtab + (int64_t)(vt + 1) * kTabRows * kWarp,
-                         kTabRows * kRow, tbar(b ^ 1));
-            }
+            mbar_arrive_expect_tx(bb, ns ? bytes : 0);
+            if (ns)
+                bulk_g2s(dst, ns, bytes, bb);
         }
         __syncthreads();  // B2: z-sums complete
 #pragma unroll
