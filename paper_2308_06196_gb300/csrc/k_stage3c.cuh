@@ -34,6 +34,9 @@ struct Stage3cSmem {
     float fpar[GEN ? NP : 1][GEN ? kParamStride : 4];
     float lim[GEN ? 2 : 1][GEN ? N1 : 1][GEN ? kWarp : 4];
     float4 met[NP][3];      // metric rows Ja^d; .w of row 0 = -b dt / J (the line sums' factor), of row 1 = W J
+    // where N1 is even, the rows of direction d again by the node pairs of two adjacent lines (see
+    // pair_row): (x_a, x_b, y_a, y_b), (z_a, z_b, s_a, s_b) with s = -b dt / J
+    float4 metp[N1 % 2 == 0 ? 3 : 1][N1 % 2 == 0 ? NP / 2 : 1][2];
     float4 fnm[3][2][NQ];   // shared face normals (direction, low/high side, face point)
     float iwj;              // 1 / sum_i W_i J_i
     unsigned long long bar[N1][5];
@@ -64,6 +67,15 @@ __device__ __forceinline__ void curv_line_c(float (&sv)[N1], const float (&fl)[N
             a = fmaf(op.DM[i][j], F[j], a);
         sv[i] = a;
     }
+}
+
+// Node pairs of the paired lines of direction d (N1 even): lines 2 lp and 2 lp + 1 of a warp, node j:
+// the pair's first node a (its partner a + N1 for d = 0, a + 1 otherwise) and its slot in metp[d].
+template <int N1>
+__host__ __device__ constexpr int pair_row(int d, int a)
+{
+    return d == 0 ? a % N1 + N1 * ((a / N1) % N1 / 2) + (N1 * N1 / 2) * (a / (N1 * N1))
+                  : (a % N1) / 2 + (N1 / 2) * (a / N1);
 }
 
 // GEN = 0: every face periodic, no body force, no limiter, constant tau and one velocity spacing on all
@@ -113,6 +125,21 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
             if (q % 3 == 0)
                 m.w = -bdt * m.w;  // rounded as the product the unstaged kernel forms at every use
             (&sm.met[0][0])[q] = m;
+        }
+        if constexpr (N1 % 2 == 0) {
+            for (int q = tid; q < 3 * NP; q += NT) {  // q = d NP + node a; the pair's first nodes only
+                const int d = q / NP, a = q % NP;
+                const bool first = d == 0 ? ((a / N1) % N1) % 2 == 0 : (a % N1) % 2 == 0;
+                if (!first)
+                    continue;
+                const int bn = a + (d == 0 ? N1 : 1);
+                const float4 ma = __ldg(A.met + ((int64_t)e * NP + a) * 3 + d);
+                const float4 mb = __ldg(A.met + ((int64_t)e * NP + bn) * 3 + d);
+                const float sa = -bdt * __ldg(A.met + ((int64_t)e * NP + a) * 3).w;
+                const float sb = -bdt * __ldg(A.met + ((int64_t)e * NP + bn) * 3).w;
+                sm.metp[d][pair_row<N1>(d, a)][0] = make_float4(ma.x, mb.x, ma.y, mb.y);
+                sm.metp[d][pair_row<N1>(d, a)][1] = make_float4(ma.z, mb.z, sa, sb);
+            }
         }
         for (int q = tid; q < 6 * NQ; q += NT)
             (&sm.fnm[0][0][0])[q] = __ldg(A.fnm + (int64_t)e * 6 * NQ + q);
@@ -331,24 +358,86 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                 if (A.mesh.bc[g] == 2)
                     rwS = A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + N1 * w;
             }
+            if constexpr (N1 % 2 == 0) {
+                // two adjacent lines at a time on packed FP32 pairs: the same operations, in the same
+                // order, as curv_line_c on each line (bit-identical results)
+                const unsigned long long X0 = pack2(x0, x0), X1 = pack2(x1, x1), X2 = pack2(x2, x2);
 #pragma unroll
-            for (int ln = 0; ln < N1; ln++) {
-                float fl[N1], u[N1], sv[N1], v[N1];
+                for (int ln = 0; ln < N1; ln += 2) {
+                    unsigned long long fl[N1], F[N1], v[N1], sp[N1];
 #pragma unroll
-                for (int j = 0; j < N1; j++) {
-                    fl[j] = sm.fs[b][node(ln, j)][lane];
-                    v[j] = sm.sl[w][ks][srow(ln, j)][lane];
-                    const float4 m = sm.met[node(ln, j)][d];
-                    u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
+                    for (int j = 0; j < N1; j++) {
+                        fl[j] = pack2(sm.fs[b][node(ln, j)][lane], sm.fs[b][node(ln + 1, j)][lane]);
+                        v[j] = pack2(sm.sl[w][ks][srow(ln, j)][lane], sm.sl[w][ks][srow(ln + 1, j)][lane]);
+                        const float4 *mp = &sm.metp[d][pair_row<N1>(d, node(ln, j))][0];
+                        const float4 p0 = mp[0], p1 = mp[1];
+                        const unsigned long long u =
+                            ffma2(pack2(p1.x, p1.y), X2, ffma2(pack2(p0.z, p0.w), X1, fmul2(pack2(p0.x, p0.y), X0)));
+                        F[j] = fmul2(u, fl[j]);
+                        sp[j] = pack2(p1.z, p1.w);
+                    }
+                    // the staged side's trace of both lines, and their own traces
+                    unsigned long long t = 0ull, oL = 0ull, oR = 0ull;
+#pragma unroll
+                    for (int j = 1; j < N1; j++)
+                        t = ffma2(dup2(cS[j]), fsub2(v[j], v[0]), t);
+                    t = fadd2(v[0], t);
+#pragma unroll
+                    for (int j = 0; j < N1; j++) {
+                        oL = ffma2(dup2(A.ops.lm[j]), fl[j], oL);
+                        oR = ffma2(dup2(A.ops.lp[j]), fl[j], oR);
+                    }
+                    float tS2[2], oL2[2], oR2[2], FI[2][2];
+                    unpack2(t, tS2[0], tS2[1]);
+                    unpack2(oL, oL2[0], oL2[1]);
+                    unpack2(oR, oR2[0], oR2[1]);
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const float tS = !GEN || es >= 0 ? tS2[h] : (rwS ? gS * __ldg(rwS + ln + h) : gS);
+                        const float tL = lo ? tS : tF[ln + h], tR = lo ? tF[ln + h] : tS;
+                        FI[0][h] = uL[ln + h] * (uL[ln + h] > 0.f ? tL : oL2[h]);
+                        FI[1][h] = uR[ln + h] * (uR[ln + h] < 0.f ? tR : oR2[h]);
+                    }
+                    const unsigned long long FIL = pack2(FI[0][0], FI[0][1]), FIR = pack2(FI[1][0], FI[1][1]);
+#pragma unroll
+                    for (int i = 0; i < N1; i++) {
+                        unsigned long long a = ffma2(dup2(A.ops.gl[i]), FIL, fmul2(dup2(A.ops.gr[i]), FIR));
+#pragma unroll
+                        for (int j = 0; j < N1; j++)
+                            a = ffma2(dup2(A.ops.DM[i][j]), F[j], a);
+                        float sa, sb;
+                        unpack2(a, sa, sb);
+                        if (d < 2) {
+                            float ca, cb;
+                            unpack2(sp[i], ca, cb);
+                            acc[node(ln, i) - NQ * w] = fmaf(ca, sa, acc[node(ln, i) - NQ * w]);
+                            acc[node(ln + 1, i) - NQ * w] = fmaf(cb, sb, acc[node(ln + 1, i) - NQ * w]);
+                        } else {
+                            sm.fs[b][node(ln, i)][lane] = sa;
+                            sm.fs[b][node(ln + 1, i)][lane] = sb;
+                        }
+                    }
                 }
-                const float tS = !GEN || es >= 0 ? trace(v, cS) : (rwS ? gS * __ldg(rwS + ln) : gS);
-                curv_line_c<N1>(sv, fl, u, uL[ln], uR[ln], lo ? tS : tF[ln], lo ? tF[ln] : tS, A.ops);
+            } else {
 #pragma unroll
-                for (int j = 0; j < N1; j++) {
-                    if (d < 2)
-                        acc[node(ln, j) - NQ * w] = fmaf(sm.met[node(ln, j)][0].w, sv[j], acc[node(ln, j) - NQ * w]);
-                    else
-                        sm.fs[b][node(ln, j)][lane] = sv[j];
+                for (int ln = 0; ln < N1; ln++) {
+                    float fl[N1], u[N1], sv[N1], v[N1];
+#pragma unroll
+                    for (int j = 0; j < N1; j++) {
+                        fl[j] = sm.fs[b][node(ln, j)][lane];
+                        v[j] = sm.sl[w][ks][srow(ln, j)][lane];
+                        const float4 m = sm.met[node(ln, j)][d];
+                        u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
+                    }
+                    const float tS = !GEN || es >= 0 ? trace(v, cS) : (rwS ? gS * __ldg(rwS + ln) : gS);
+                    curv_line_c<N1>(sv, fl, u, uL[ln], uR[ln], lo ? tS : tF[ln], lo ? tF[ln] : tS, A.ops);
+#pragma unroll
+                    for (int j = 0; j < N1; j++) {
+                        if (d < 2)
+                            acc[node(ln, j) - NQ * w] = fmaf(sm.met[node(ln, j)][0].w, sv[j], acc[node(ln, j) - NQ * w]);
+                        else
+                            sm.fs[b][node(ln, j)][lane] = sv[j];
+                    }
                 }
             }
         };
