@@ -194,9 +194,15 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE
         const int4 tb = cs.ftab[2 * d + side];
         if (tb.x < 0) {
             const float gv = __ldg(A.ghost + (int64_t)(-1 - tb.x) * A.nslots + slot);
+            if (tb.w >= 0) {  // a wall face (the test outside the loop: no load from an invalid address)
 #pragma unroll
-            for (int ln = 0; ln < N1; ln++)
-                t[ln] = tb.w >= 0 ? gv * __ldg(A.rhowu + (int64_t)tb.w * NQ + fp0 + ln) : gv;
+                for (int ln = 0; ln < N1; ln++)
+                    t[ln] = gv * __ldg(A.rhowu + (int64_t)tb.w * NQ + fp0 + ln);
+            } else {
+#pragma unroll
+                for (int ln = 0; ln < N1; ln++)
+                    t[ln] = gv;
+            }
             return;
         }
         const float *nb = A.src + fidx(vl, tb.x, 0, lane, E, NP);

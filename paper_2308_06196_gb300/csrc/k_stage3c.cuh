@@ -341,22 +341,37 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                     for (int ln = 0; ln < N1; ln++)
                         tF[ln] = trace(v[ln], cF);
                 } else {
+                    // (the wall test is outside the loops: no load is formed from a pointer that may be null)
                     const float gv = __ldg(A.ghost + (int64_t)g * A.nslots + slot);
-                    const float *rw = A.mesh.bc[g] == 2
-                                          ? A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + N1 * w
-                                          : nullptr;
+                    if (A.mesh.bc[g] == 2) {
+                        const float *rw = A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + N1 * w;
 #pragma unroll
-                    for (int ln = 0; ln < N1; ln++)
-                        tF[ln] = rw ? gv * __ldg(rw + ln) : gv;
+                        for (int ln = 0; ln < N1; ln++)
+                            tF[ln] = gv * __ldg(rw + ln);
+                    } else {
+#pragma unroll
+                        for (int ln = 0; ln < N1; ln++)
+                            tF[ln] = gv;
+                    }
                 }
             }
-            float gS = 0.f;  // the staged side's ghost value on a boundary face
-            const float *rwS = nullptr;
+            float gS[N1];  // the staged side's ghost value of every line on a boundary face
+#pragma unroll
+            for (int ln = 0; ln < N1; ln++)
+                gS[ln] = 0.f;
             if (GEN && es < 0) {
                 const int g = 2 * d + (lo ? 0 : 1);
-                gS = __ldg(A.ghost + (int64_t)g * A.nslots + slot);
-                if (A.mesh.bc[g] == 2)
-                    rwS = A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + N1 * w;
+                const float gv = __ldg(A.ghost + (int64_t)g * A.nslots + slot);
+                if (A.mesh.bc[g] == 2) {
+                    const float *rw = A.rhow + ((int64_t)g * A.nfmax + face_elem(A.mesh, ec, d)) * NQ + N1 * w;
+#pragma unroll
+                    for (int ln = 0; ln < N1; ln++)
+                        gS[ln] = gv * __ldg(rw + ln);
+                } else {
+#pragma unroll
+                    for (int ln = 0; ln < N1; ln++)
+                        gS[ln] = gv;
+                }
             }
             if constexpr (N1 % 2 == 0) {
                 // two adjacent lines at a time on packed FP32 pairs: the same operations, in the same
@@ -393,7 +408,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                     unpack2(oR, oR2[0], oR2[1]);
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
-                        const float tS = !GEN || es >= 0 ? tS2[h] : (rwS ? gS * __ldg(rwS + ln + h) : gS);
+                        const float tS = !GEN || es >= 0 ? tS2[h] : gS[ln + h];
                         const float tL = lo ? tS : tF[ln + h], tR = lo ? tF[ln + h] : tS;
                         FI[0][h] = uL[ln + h] * (uL[ln + h] > 0.f ? tL : oL2[h]);
                         FI[1][h] = uR[ln + h] * (uR[ln + h] < 0.f ? tR : oR2[h]);
@@ -429,7 +444,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
                         const float4 m = sm.met[node(ln, j)][d];
                         u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
                     }
-                    const float tS = !GEN || es >= 0 ? trace(v, cS) : (rwS ? gS * __ldg(rwS + ln) : gS);
+                    const float tS = !GEN || es >= 0 ? trace(v, cS) : gS[ln];
                     curv_line_c<N1>(sv, fl, u, uL[ln], uR[ln], lo ? tS : tF[ln], lo ? tF[ln] : tS, A.ops);
 #pragma unroll
                     for (int j = 0; j < N1; j++) {
