@@ -53,6 +53,9 @@ struct Stage3Smem {
 template <int N1>
 struct CurvSmem {
     float4 met[N1 * N1 * N1][3];
+    // where N1 is even, the rows of direction d again by the node pairs of two adjacent lines (pair_row):
+    // (x_a, x_b, y_a, y_b), (z_a, z_b, s_a, s_b) with s = -b dt / J
+    float4 metp[N1 % 2 == 0 ? 3 : 1][N1 % 2 == 0 ? N1 * N1 * N1 / 2 : 1][2];
     float4 fnm[3][2][N1 * N1];
     int4 ftab[6];                          // unstructured connectivity of the element (see StageArgs)
     unsigned char fbase[6][N1 * N1];
@@ -146,6 +149,22 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE
         if constexpr (CURV) {
             for (int q = tid; q < NP * 3; q += NT)
                 (&cs.met[0][0])[q] = __ldg(A.met + (int64_t)e * NP * 3 + q);
+            if constexpr (N1 % 2 == 0) {
+                const float bdt0 = A.b * A.dt;
+                for (int q = tid; q < 3 * NP; q += NT) {  // q = d NP + node a; the pairs' first nodes only
+                    const int d = q / NP, a = q % NP;
+                    const bool first = d == 0 ? ((a / N1) % N1) % 2 == 0 : (a % N1) % 2 == 0;
+                    if (!first)
+                        continue;
+                    const int bn = a + (d == 0 ? N1 : 1);
+                    const float4 ma = __ldg(A.met + ((int64_t)e * NP + a) * 3 + d);
+                    const float4 mb = __ldg(A.met + ((int64_t)e * NP + bn) * 3 + d);
+                    const float sa = -bdt0 * __ldg(A.met + ((int64_t)e * NP + a) * 3).w;
+                    const float sb = -bdt0 * __ldg(A.met + ((int64_t)e * NP + bn) * 3).w;
+                    cs.metp[d][pair_row<N1>(d, a)][0] = make_float4(ma.x, mb.x, ma.y, mb.y);
+                    cs.metp[d][pair_row<N1>(d, a)][1] = make_float4(ma.z, mb.z, sa, sb);
+                }
+            }
             for (int q = tid; q < 6 * NQ; q += NT)
                 (&cs.fnm[0][0][0])[q] = __ldg(A.fnm + (int64_t)e * 6 * NQ + q);
             if (tid == 0)
@@ -305,22 +324,72 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE
                     }
                     exteriors(vl, slot, d, 0, N1 * w, inL, tLs);
                     exteriors(vl, slot, d, 1, N1 * w, inR, tRs);
+                    if constexpr (N1 % 2 == 0) {
+                        // two adjacent lines on packed FP32 pairs, each half curv_line's operations in
+                        // its order (bit-identical results)
+                        const unsigned long long X0 = pack2(x0, x0), X1 = pack2(x1, x1), X2 = pack2(x2, x2);
 #pragma unroll
-                    for (int ln = 0; ln < N1; ln++) {
-                        float fl[N1], u[N1], sv[N1];
-                        int nd[N1], qi[N1];  // element node and in-layer node (compile-time) of the line
+                        for (int ln = 0; ln < N1; ln += 2) {
+                            unsigned long long fl[N1], F[N1], sp[N1];
+                            int qa[N1], qb[N1];
 #pragma unroll
-                        for (int j = 0; j < N1; j++) {
-                            qi[j] = d == 0 ? j + N1 * ln : ln + N1 * j;
-                            nd[j] = qi[j] + NQ * w;
-                            fl[j] = f[qi[j]];
-                            const float4 m = cs.met[nd[j]][d];
-                            u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
+                            for (int j = 0; j < N1; j++) {
+                                qa[j] = d == 0 ? j + N1 * ln : ln + N1 * j;
+                                qb[j] = qa[j] + (d == 0 ? N1 : 1);
+                                fl[j] = pack2(f[qa[j]], f[qb[j]]);
+                                const float4 *mp = &cs.metp[d][pair_row<N1>(d, qa[j] + NQ * w)][0];
+                                const float4 p0 = mp[0], p1 = mp[1];
+                                const unsigned long long u =
+                                    ffma2(pack2(p1.x, p1.y), X2, ffma2(pack2(p0.z, p0.w), X1, fmul2(pack2(p0.x, p0.y), X0)));
+                                F[j] = fmul2(u, fl[j]);
+                                sp[j] = pack2(p1.z, p1.w);
+                            }
+                            unsigned long long oL = 0ull, oR = 0ull;
+#pragma unroll
+                            for (int j = 0; j < N1; j++) {
+                                oL = ffma2(dup2(A.ops.lm[j]), fl[j], oL);
+                                oR = ffma2(dup2(A.ops.lp[j]), fl[j], oR);
+                            }
+                            float oL2[2], oR2[2], FI[2][2];
+                            unpack2(oL, oL2[0], oL2[1]);
+                            unpack2(oR, oR2[0], oR2[1]);
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                FI[0][h] = uLs[ln + h] * (uLs[ln + h] > 0.f ? tLs[ln + h] : oL2[h]);
+                                FI[1][h] = uRs[ln + h] * (uRs[ln + h] < 0.f ? tRs[ln + h] : oR2[h]);
+                            }
+                            const unsigned long long FIL = pack2(FI[0][0], FI[0][1]), FIR = pack2(FI[1][0], FI[1][1]);
+#pragma unroll
+                            for (int i = 0; i < N1; i++) {
+                                unsigned long long a = ffma2(dup2(A.ops.gl[i]), FIL, fmul2(dup2(A.ops.gr[i]), FIR));
+#pragma unroll
+                                for (int j = 0; j < N1; j++)
+                                    a = ffma2(dup2(A.ops.DM[i][j]), F[j], a);
+                                float sa, sb, ca, cb;
+                                unpack2(a, sa, sb);
+                                unpack2(sp[i], ca, cb);
+                                acc[qa[i]] = fmaf(ca, sa, acc[qa[i]]);
+                                acc[qb[i]] = fmaf(cb, sb, acc[qb[i]]);
+                            }
                         }
-                        curv_line<N1>(sv, fl, u, uLs[ln], uRs[ln], tLs[ln], tRs[ln], A.ops);
+                    } else {
 #pragma unroll
-                        for (int j = 0; j < N1; j++)
-                            acc[qi[j]] = fmaf(-bdt * cs.met[nd[j]][0].w, sv[j], acc[qi[j]]);
+                        for (int ln = 0; ln < N1; ln++) {
+                            float fl[N1], u[N1], sv[N1];
+                            int nd[N1], qi[N1];  // element node and in-layer node (compile-time) of the line
+#pragma unroll
+                            for (int j = 0; j < N1; j++) {
+                                qi[j] = d == 0 ? j + N1 * ln : ln + N1 * j;
+                                nd[j] = qi[j] + NQ * w;
+                                fl[j] = f[qi[j]];
+                                const float4 m = cs.met[nd[j]][d];
+                                u[j] = fmaf(m.z, x2, fmaf(m.y, x1, m.x * x0));
+                            }
+                            curv_line<N1>(sv, fl, u, uLs[ln], uRs[ln], tLs[ln], tRs[ln], A.ops);
+#pragma unroll
+                            for (int j = 0; j < N1; j++)
+                                acc[qi[j]] = fmaf(-bdt * cs.met[nd[j]][0].w, sv[j], acc[qi[j]]);
+                        }
                     }
                 }
                 __syncthreads();  // B1: the element tile is complete
@@ -342,6 +411,50 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE
                 }
                 exteriors(vl, slot, 2, 0, N1 * w, inL, tLs);
                 exteriors(vl, slot, 2, 1, N1 * w, inR, tRs);
+                if constexpr (N1 % 2 == 0) {  // paired z-lines (as the x- and y-lines above)
+                    const unsigned long long X0 = pack2(x0, x0), X1 = pack2(x1, x1), X2 = pack2(x2, x2);
+#pragma unroll
+                    for (int ln = 0; ln < N1; ln += 2) {
+                        unsigned long long fl[N1], F[N1];
+#pragma unroll
+                        for (int j = 0; j < N1; j++) {
+                            const int nd = ln + N1 * w + NQ * j;
+                            fl[j] = pack2(sm.tile[b][nd][lane], sm.tile[b][nd + 1][lane]);
+                            const float4 *mp = &cs.metp[2][pair_row<N1>(2, nd)][0];
+                            const float4 p0 = mp[0], p1 = mp[1];
+                            const unsigned long long u =
+                                ffma2(pack2(p1.x, p1.y), X2, ffma2(pack2(p0.z, p0.w), X1, fmul2(pack2(p0.x, p0.y), X0)));
+                            F[j] = fmul2(u, fl[j]);
+                        }
+                        unsigned long long oL = 0ull, oR = 0ull;
+#pragma unroll
+                        for (int j = 0; j < N1; j++) {
+                            oL = ffma2(dup2(A.ops.lm[j]), fl[j], oL);
+                            oR = ffma2(dup2(A.ops.lp[j]), fl[j], oR);
+                        }
+                        float oL2[2], oR2[2], FI[2][2];
+                        unpack2(oL, oL2[0], oL2[1]);
+                        unpack2(oR, oR2[0], oR2[1]);
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            FI[0][h] = uLs[ln + h] * (uLs[ln + h] > 0.f ? tLs[ln + h] : oL2[h]);
+                            FI[1][h] = uRs[ln + h] * (uRs[ln + h] < 0.f ? tRs[ln + h] : oR2[h]);
+                        }
+                        const unsigned long long FIL = pack2(FI[0][0], FI[0][1]), FIR = pack2(FI[1][0], FI[1][1]);
+#pragma unroll
+                        for (int i = 0; i < N1; i++) {
+                            unsigned long long a = ffma2(dup2(A.ops.gl[i]), FIL, fmul2(dup2(A.ops.gr[i]), FIR));
+#pragma unroll
+                            for (int j = 0; j < N1; j++)
+                                a = ffma2(dup2(A.ops.DM[i][j]), F[j], a);
+                            float sa, sb;
+                            unpack2(a, sa, sb);
+                            const int nd = ln + N1 * w + NQ * i;
+                            sm.zc[nd][lane] = sa;
+                            sm.zc[nd + 1][lane] = sb;
+                        }
+                    }
+                } else
 #pragma unroll
                 for (int ln = 0; ln < N1; ln++) {
                     float fl[N1], u[N1], sv[N1];
