@@ -142,39 +142,95 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_sta
                 acc[q] = fmaf(A.an, acc[q], kbq * f[q]);
             }
             const float cx = -A.mesh.inv_h2[0] * x0 * bdt, cy = -A.mesh.inv_h2[1] * x1 * bdt;
+            if constexpr (N1 % 2 == 0) {
+                // two adjacent lines of a direction at a time on packed FP32 pairs, the upwind value in
+                // jump form inside the trace (as the hexahedral kernels), selected against the ghost jump
+                constexpr int RL = 0, RR = N1 - 1;
 #pragma unroll
-            for (int iy = 0; iy < N1; iy++) {
-                float fl[N1], sv[N1];
+                for (int iy = 0; iy < N1; iy += 2) {
+                    unsigned long long fl[N1], v[N1], sv[N1];
 #pragma unroll
-                for (int j = 0; j < N1; j++)
-                    fl[j] = f[j + N1 * iy];
-                if (l0) {
-                    const float t = trace_line<N1, true>(vx[iy], A.ops);
-                    line_sums<N1, true>(sv, fl, enx >= 0 ? t : gx, A.ops);
-                } else {
-                    const float t = trace_line<N1, false>(vx[iy], A.ops);
-                    line_sums<N1, false>(sv, fl, enx >= 0 ? t : gx, A.ops);
+                    for (int j = 0; j < N1; j++) {
+                        fl[j] = pack2(f[j + N1 * iy], f[j + N1 * iy + N1]);
+                        v[j] = pack2(vx[iy][j], vx[iy + 1][j]);
+                    }
+                    if (l0) {
+                        const unsigned long long tj = trace_jump2<N1, true>(v, fl[RL], A.ops);
+                        const unsigned long long gj = fsub2(dup2(gx), fl[RL]);
+                        line_sums_jump2<N1, true>(sv, fl, enx >= 0 ? tj : gj, A.ops);
+                    } else {
+                        const unsigned long long tj = trace_jump2<N1, false>(v, fl[RR], A.ops);
+                        const unsigned long long gj = fsub2(dup2(gx), fl[RR]);
+                        line_sums_jump2<N1, false>(sv, fl, enx >= 0 ? tj : gj, A.ops);
+                    }
+#pragma unroll
+                    for (int j = 0; j < N1; j++) {
+                        float lo, hi;
+                        unpack2(sv[j], lo, hi);
+                        acc[j + N1 * iy] = fmaf(cx, lo, acc[j + N1 * iy]);
+                        acc[j + N1 * iy + N1] = fmaf(cx, hi, acc[j + N1 * iy + N1]);
+                    }
                 }
 #pragma unroll
-                for (int j = 0; j < N1; j++)
-                    acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
-            }
+                for (int ix = 0; ix < N1; ix += 2) {
+                    unsigned long long fl[N1], v[N1], sv[N1];
 #pragma unroll
-            for (int ix = 0; ix < N1; ix++) {
-                float fl[N1], sv[N1];
+                    for (int j = 0; j < N1; j++) {
+                        fl[j] = pack2(f[ix + N1 * j], f[ix + 1 + N1 * j]);
+                        v[j] = pack2(vy[ix][j], vy[ix + 1][j]);
+                    }
+                    if (l1) {
+                        const unsigned long long tj = trace_jump2<N1, true>(v, fl[RL], A.ops);
+                        const unsigned long long gj = fsub2(dup2(gy), fl[RL]);
+                        line_sums_jump2<N1, true>(sv, fl, eny >= 0 ? tj : gj, A.ops);
+                    } else {
+                        const unsigned long long tj = trace_jump2<N1, false>(v, fl[RR], A.ops);
+                        const unsigned long long gj = fsub2(dup2(gy), fl[RR]);
+                        line_sums_jump2<N1, false>(sv, fl, eny >= 0 ? tj : gj, A.ops);
+                    }
 #pragma unroll
-                for (int j = 0; j < N1; j++)
-                    fl[j] = f[ix + N1 * j];
-                if (l1) {
-                    const float t = trace_line<N1, true>(vy[ix], A.ops);
-                    line_sums<N1, true>(sv, fl, eny >= 0 ? t : gy, A.ops);
-                } else {
-                    const float t = trace_line<N1, false>(vy[ix], A.ops);
-                    line_sums<N1, false>(sv, fl, eny >= 0 ? t : gy, A.ops);
+                    for (int j = 0; j < N1; j++) {
+                        float lo, hi;
+                        unpack2(sv[j], lo, hi);
+                        acc[ix + N1 * j] = fmaf(cy, lo, acc[ix + N1 * j]);
+                        acc[ix + 1 + N1 * j] = fmaf(cy, hi, acc[ix + 1 + N1 * j]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int iy = 0; iy < N1; iy++) {
+                    float fl[N1], sv[N1];
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        fl[j] = f[j + N1 * iy];
+                    if (l0) {
+                        const float t = trace_line<N1, true>(vx[iy], A.ops);
+                        line_sums<N1, true>(sv, fl, enx >= 0 ? t : gx, A.ops);
+                    } else {
+                        const float t = trace_line<N1, false>(vx[iy], A.ops);
+                        line_sums<N1, false>(sv, fl, enx >= 0 ? t : gx, A.ops);
+                    }
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        acc[j + N1 * iy] = fmaf(cx, sv[j], acc[j + N1 * iy]);
                 }
 #pragma unroll
-                for (int j = 0; j < N1; j++)
-                    acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
+                for (int ix = 0; ix < N1; ix++) {
+                    float fl[N1], sv[N1];
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        fl[j] = f[ix + N1 * j];
+                    if (l1) {
+                        const float t = trace_line<N1, true>(vy[ix], A.ops);
+                        line_sums<N1, true>(sv, fl, eny >= 0 ? t : gy, A.ops);
+                    } else {
+                        const float t = trace_line<N1, false>(vy[ix], A.ops);
+                        line_sums<N1, false>(sv, fl, eny >= 0 ? t : gy, A.ops);
+                    }
+#pragma unroll
+                    for (int j = 0; j < N1; j++)
+                        acc[ix + N1 * j] = fmaf(cy, sv[j], acc[ix + N1 * j]);
+                }
             }
             // BGK source towards the conservative Maxwellian and the Shu-Osher combination, two nodes at
             // a time (exponent a + b.m + q |m|^2, or per-axis q on grids of several spacings)
