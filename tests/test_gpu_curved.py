@@ -180,13 +180,14 @@ def test_rejected_setups():
     assert err.value.code == BGK_EINVAL
 
 
-@pytest.mark.parametrize("bc", [None, "tube"])
-def test_unstructured_mesh_vs_oracle_and_structured(bc):
+@pytest.mark.parametrize("bc,p", [(None, 2), ("tube", 2), (None, 3), ("tube", 3), (None, 1)])
+def test_unstructured_mesh_vs_oracle_and_structured(bc, p):
     # the curved bump mesh relabelled as an unstructured mesh (random element order, every element's
     # local axes rotated): the GPU against the oracle on the same tables, and against the structured run
+    # (odd N1: one line at a time; even N1: two adjacent lines on packed pairs)
     from paper_2308_06196_gb300.bgk import Solver
 
-    ne, p, n, L = (3, 2, 2), 2, 6, 4.0
+    ne, n, L = (3, 2, 2), 6, 4.0
     bcs = None
     if bc == "tube":
         bc, bcs = tube()
@@ -315,8 +316,8 @@ def test_dirichlet_in_z_on_the_bump_mesh(precision, tol):
     assert rel(s.get_f(), pr.get_f()) < tol
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-10)])
-def test_unstructured_walls_vs_oracle_and_structured(precision, tol):
+@pytest.mark.parametrize("precision,tol,p", [(0, 1e-5, 2), (1, 1e-10, 2), (0, 1e-5, 3)])
+def test_unstructured_walls_vs_oracle_and_structured(precision, tol, p):
     # the wavy-walled channel (moving upper wall) relabelled and rotated: its walls are boundary faces of
     # the tables with the wall class; the GPU against the oracle on the same tables and against the
     # structured GPU run of the same mesh
@@ -326,7 +327,7 @@ def test_unstructured_walls_vs_oracle_and_structured(precision, tol):
     bcs = np.zeros((3, 2, 5))
     bcs[1, 0] = [0, 0.0, 0.0, 0.0, 1.0]
     bcs[1, 1] = [0, 0.2, 0.0, 0.0, 1.0]
-    ne, p, n, L, tau = (3, 3, 2), 2, 6, 4.0, 0.02
+    ne, n, L, tau = (3, 3, 2), 6, 4.0, 0.02
     s, pr, X = make(ne, p, n=n, L=L, tau=tau, bc=bc, bcs=bcs, kind="sine", eps=0.3, precision=precision)
     u = W.unstructured_box(ne, p, bc=bc, seed=9)
     m = u["node_map"]
