@@ -163,6 +163,11 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
 
     const bool has_fn = A.fn != nullptr;
     // the staged (octant-upwind) neighbour of every direction of tile vl, -1 on a Dirichlet or wall face
+    auto nbrs_oct = [&](int oct, int (&en)[3]) {
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            en[d] = upwind_neighbour(A.mesh, ec, d, ((oct >> d) & 1) != 0);
+    };
     auto nbrs = [&](int vl, int (&en)[3]) {
         const int oct = (int)__ldg(A.toct + A.vt0 + vl);
 #pragma unroll
@@ -198,6 +203,9 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
     int en[3];
     nbrs(vl0, en);
     const float *csrc = role_src(en);
+    // the neighbours and the role lanes' sources are recomputed only where the octant changes from one
+    // tile to the next (the velocities are ordered by octant, so within a chunk almost never)
+    int octc = (int)__ldg(A.toct + A.vt0 + vl0);
     const float *fsrc = A.src + fidx(0, e, NQ * w, 0, E, NP);  // lane 0's source (the same every tile)
     if (lane == 0) {
         mbar_arrive_expect_tx(bar(0), kSlot);
@@ -237,16 +245,18 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
         const int b = (vl - vl0) & 1;
         const int kx = ka == 2 ? 0 : ka + 1, ky = ka == 0 ? 2 : ka - 1;
         int enn[3] = {en[0], en[1], en[2]};
-        if (vl + 1 < vl1)
-            nbrs(vl + 1, enn);
         const bool more = vl + 1 < vl1;
+        const int octn = more ? (int)__ldg(A.toct + vt + 1) : octc;
+        const bool turn = octn != octc;  // the next tile lies in another octant
+        if (turn)
+            nbrs_oct(octn, enn);
         __syncwarp();
         if (lane == 0 && more) {
             fence_proxy_async();
             mbar_arrive_expect_tx(bar(b ^ 1), kSlot);
             bulk_g2s(fs0 + (b ^ 1) * kFsBuf, fsrc + (vl + 1) * tstride, kSlot, bar(b ^ 1));
         }
-        const int oct = (int)__ldg(A.toct + vt);
+        const int oct = octc;
         const bool l0 = (oct & 1) != 0, l1 = (oct & 2) != 0, l2 = (oct & 4) != 0;
         const int enx = en[0], eny = en[1], enz = en[2];
 
@@ -269,7 +279,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
         // slot ka is consumed: the z-neighbour's slice lands there
         __syncwarp();
         if (lane >= RZ && lane < RZ + N1) {
-            const float *zs = role_src(en);
+            const float *zs = csrc;
             const uint32_t bb = bar(2 + ka);
             fence_proxy_async();
             if (lane == RZ)
@@ -464,7 +474,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
         __syncwarp();
         if (more && ((lane == RFN && has_fn) || lane == RX)) {
             fence_proxy_async();
-            issue_layer(lane == RX ? role_src(enn) : csrc, vl + 1, lane == RX ? ky : kx);
+            issue_layer(lane == RX && turn ? role_src(enn) : csrc, vl + 1, lane == RX ? ky : kx);
         }
         __syncthreads();  // B1: every layer of the element tile has landed
         // z-lines of slice iy = w (all layers) from the shared tile
@@ -476,7 +486,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
         if (more && (lane == RY || (w == 0 && lane == RT))) {
             fence_proxy_async();
             if (lane == RY) {
-                issue_layer(role_src(enn), vl + 1, ka);
+                issue_layer(turn ? role_src(enn) : csrc, vl + 1, ka);
             } else {
                 mbar_arrive_expect_tx(tbar(b ^ 1), kTabRows * kRow);
                 bulk_g2s(smem_u32(&sm.tab[b ^ 1][0][0]), A.vtab + (int64_t)(vt + 1) * kTabRows * kWarp,
@@ -631,6 +641,10 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
 #pragma unroll
         for (int d = 0; d < 3; d++)
             en[d] = enn[d];
+        if (turn) {
+            csrc = role_src(en);
+            octc = octn;
+        }
         ka = ka == 2 ? 0 : ka + 1;
     }
     const int grp = A.group0 + gl;
