@@ -38,6 +38,9 @@ struct Stage3cSmem {
     // pair_row): (x_a, x_b, y_a, y_b), (z_a, z_b, s_a, s_b) with s = -b dt / J
     float4 metp[N1 % 2 == 0 ? 3 : 1][N1 % 2 == 0 ? NP / 2 : 1][2];
     float4 fnm[3][2][NQ];   // shared face normals (direction, low/high side, face point)
+    // where N1 is even, again by face-point pairs (fp, fp + 1) of the paired lines: (x_a, x_b, y_a, y_b),
+    // (z_a, z_b, 0, 0)
+    float4 fnmp[N1 % 2 == 0 ? 3 : 1][2][N1 % 2 == 0 ? NQ / 2 : 1][2];
     float iwj;              // 1 / sum_i W_i J_i
     unsigned long long bar[N1][5];
     unsigned long long tbar[2];
@@ -143,6 +146,15 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
         }
         for (int q = tid; q < 6 * NQ; q += NT)
             (&sm.fnm[0][0][0])[q] = __ldg(A.fnm + (int64_t)e * 6 * NQ + q);
+        if constexpr (N1 % 2 == 0) {
+            for (int q = tid; q < 3 * NQ; q += NT) {  // q = (d, side) NQ / 2 + pair
+                const int ds = q / (NQ / 2), pr = q % (NQ / 2);
+                const float4 na = __ldg(A.fnm + (int64_t)e * 6 * NQ + ds * NQ + 2 * pr);
+                const float4 nb = __ldg(A.fnm + (int64_t)e * 6 * NQ + ds * NQ + 2 * pr + 1);
+                sm.fnmp[ds / 2][ds % 2][pr][0] = make_float4(na.x, nb.x, na.y, nb.y);
+                sm.fnmp[ds / 2][ds % 2][pr][1] = make_float4(na.z, nb.z, 0.f, 0.f);
+            }
+        }
         if (tid == 0)
             sm.iwj = __ldg(A.iwj + e);
     }
@@ -325,14 +337,36 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
             };
             float uL[N1], uR[N1], tF[N1];
             bool far = false;
+            if constexpr (N1 % 2 == 0) {  // two face points at a time (the same operations per half)
+                const unsigned long long X0 = pack2(x0, x0), X1 = pack2(x1, x1), X2 = pack2(x2, x2);
 #pragma unroll
-            for (int ln = 0; ln < N1; ln++) {
-                const int fp = ln + N1 * w;
-                const float4 nL = sm.fnm[d][0][fp], nR = sm.fnm[d][1][fp];
-                uL[ln] = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
-                uR[ln] = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
-                tF[ln] = 0.f;
-                far = far || (lo ? uR[ln] < 0.f : uL[ln] > 0.f);
+                for (int ln = 0; ln < N1; ln += 2) {
+                    const int pr = (ln + N1 * w) / 2;
+                    float u2[2][2];
+#pragma unroll
+                    for (int sd = 0; sd < 2; sd++) {
+                        const float4 n0 = sm.fnmp[d][sd][pr][0], n1 = sm.fnmp[d][sd][pr][1];
+                        unpack2(ffma2(pack2(n1.x, n1.y), X2, ffma2(pack2(n0.z, n0.w), X1, fmul2(pack2(n0.x, n0.y), X0))),
+                                u2[sd][0], u2[sd][1]);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        uL[ln + h] = u2[0][h];
+                        uR[ln + h] = u2[1][h];
+                        tF[ln + h] = 0.f;
+                        far = far || (lo ? uR[ln + h] < 0.f : uL[ln + h] > 0.f);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int ln = 0; ln < N1; ln++) {
+                    const int fp = ln + N1 * w;
+                    const float4 nL = sm.fnm[d][0][fp], nR = sm.fnm[d][1][fp];
+                    uL[ln] = fmaf(nL.z, x2, fmaf(nL.y, x1, nL.x * x0));
+                    uR[ln] = fmaf(nR.z, x2, fmaf(nR.y, x1, nR.x * x0));
+                    tF[ln] = 0.f;
+                    far = far || (lo ? uR[ln] < 0.f : uL[ln] > 0.f);
+                }
             }
             if (__any_sync(0xffffffffu, far)) {
                 const int g = 2 * d + (lo ? 1 : 0);
