@@ -651,8 +651,8 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? BGK_STAGE3C_MINCTAS_P3 :
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     const float4 M4 = *reinterpret_cast<const float4 *>(&sm.tab[b][d][kk]);
-                    wv[1 + d][0] = pack2(W4.x * M4.x, W4.y * M4.y);
-                    wv[1 + d][1] = pack2(W4.z * M4.z, W4.w * M4.w);
+                    wv[1 + d][0] = fmul2(pack2(W4.x, W4.y), pack2(M4.x, M4.y));
+                    wv[1 + d][1] = fmul2(pack2(W4.z, W4.w), pack2(M4.z, M4.w));
                 }
             }
 #pragma unroll
