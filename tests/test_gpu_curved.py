@@ -104,9 +104,11 @@ def test_lean_and_general_curved_kernels_agree(p):
     assert rel(out[1][1], out[0][1]) < 1e-6
 
 
-def test_sine_mesh_tube_with_limiter_vs_oracle():
+@pytest.mark.parametrize("p", [2, 3])
+def test_sine_mesh_tube_with_limiter_vs_oracle(p):
+    # Dirichlet x ends on the sine mesh (odd N1: single lines; even N1: paired lines with their ghosts)
     bc, bcs = tube()
-    s, pr, X = make((4, 2, 2), 2, n=8, L=5.0, tau=2e-3, bc=bc, bcs=bcs, kind="sine", eps=0.3, limiter=True)
+    s, pr, X = make((4, 2, 2), p, n=8, L=5.0, tau=2e-3, bc=bc, bcs=bcs, kind="sine", eps=0.3, limiter=True)
     prim = W.prim_sod(X, (1.0, 1.0), (0.25, 0.8))
     s.set_state(prim)
     pr.set_state(prim)
@@ -233,7 +235,8 @@ def test_unstructured_table_rejected():
     assert err.value.code == BGK_EINVAL
 
 
-def test_curved_walls_vs_oracle_and_mass():
+@pytest.mark.parametrize("p", [2, 3])
+def test_curved_walls_vs_oracle_and_mass(p):
     # a channel with diffuse walls at y = 0 and 1 (the upper one moving in x), made wavy by the sine
     # mapping: per-face-point wall densities from the curved normals; the oracle on the same nodes, and
     # the J-weighted total mass conserved
@@ -241,7 +244,7 @@ def test_curved_walls_vs_oracle_and_mass():
     bcs = np.zeros((3, 2, 5))
     bcs[1, 0] = [0, 0.0, 0.0, 0.0, 1.0]
     bcs[1, 1] = [0, 0.2, 0.0, 0.0, 1.0]
-    ne, p = (3, 3, 2), 2
+    ne = (3, 3, 2)
     s, pr, X = make(ne, p, n=6, tau=0.02, bc=bc, bcs=bcs, kind="sine", eps=0.3)
     prim = W.smooth_prim(X, 3, seed=5, amp=0.2)
     s.set_state(prim)
@@ -298,14 +301,14 @@ def test_all_fp64_form_on_curved_meshes(case):
     assert rel(s.get_f(), pr.get_f()) < 1e-10
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-10)])
-def test_dirichlet_in_z_on_the_bump_mesh(precision, tol):
+@pytest.mark.parametrize("precision,tol,p", [(0, 1e-5, 2), (1, 1e-10, 2), (0, 1e-5, 3)])
+def test_dirichlet_in_z_on_the_bump_mesh(precision, tol, p):
     # the z face pair (the z-lines' ghosts) on a curved mesh
     bc = [[0, 0], [0, 0], [W.DIRICHLET, W.DIRICHLET]]
     bcs = np.zeros((3, 2, 5))
     bcs[2, 0] = [1.0, 0.0, 0.0, 0.2, 1.0]
     bcs[2, 1] = [0.5, 0.0, 0.1, 0.0, 0.9]
-    s, pr, X = make((2, 2, 3), 2, n=6, tau=0.02, bc=bc, bcs=bcs, precision=precision)
+    s, pr, X = make((2, 2, 3), p, n=6, tau=0.02, bc=bc, bcs=bcs, precision=precision)
     prim = W.smooth_prim(X, 3, seed=13, amp=0.2)
     s.set_state(prim)
     pr.set_state(prim)
