@@ -81,10 +81,36 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_sta
     prefetch_fn(vl0);
     __syncwarp();  // the parameter rows of every lane
 
+    // the tile's velocity rows (w psi, grid indices, mask) are loaded one tile ahead into registers
+    float wp_n[5], mi_n[3], gm_n = 0.f;
+    auto load_rows = [&](int vt) {
+        const int sl = vt * kWarp + lane;
+#pragma unroll
+        for (int c = 0; c < 5; c++)
+            wp_n[c] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+        if (MODE == 0) {
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+                mi_n[d] = __ldg(A.mi + d * A.nslots + sl);
+            gm_n = __ldg(A.gmask + sl);
+        }
+    };
+    if (vl0 < vl1)
+        load_rows(A.vt0 + vl0);
     for (int vl = vl0; vl < vl1; vl++) {
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
         const int b = (vl - vl0) & 1;
+        float wp_c[5], mi_c[3];
+#pragma unroll
+        for (int c = 0; c < 5; c++)
+            wp_c[c] = wp_n[c];
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            mi_c[d] = mi_n[d];
+        const float gm_c = gm_n;
+        if (vl + 1 < vl1)
+            load_rows(vt + 1);
         if (vl + 1 < vl1) {  // pending: tile vl, f^n vl, then tile vl + 1
             prefetch(vl + 1, b ^ 1);
             cp_wait<1>();
@@ -94,13 +120,13 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_sta
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < 5; c++)
-            sm.wpsi[c][lane] = __ldg(A.wpsi + ((int64_t)vt * 5 + c) * kWarp + lane);
+            sm.wpsi[c][lane] = wp_c[c];
         float f[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++)
             f[q] = sm.tile[b][q][lane];
         if (MODE == 0) {
-            const float m0 = __ldg(A.mi + slot), m1 = __ldg(A.mi + A.nslots + slot), m2 = __ldg(A.mi + 2 * A.nslots + slot);
+            const float m0 = mi_c[0], m1 = mi_c[1], m2 = mi_c[2];
             const float x0 = fmaf(A.vs[0], m0, A.vc[0]), x1 = fmaf(A.vs[1], m1, A.vc[1]);
             const bool l0 = OCT < 8 ? (OCT & 1) != 0 : x0 >= 0.f;
             const bool l1 = OCT < 8 ? (OCT & 2) != 0 : x1 >= 0.f;
@@ -234,7 +260,7 @@ __global__ void __launch_bounds__(kWarp *kWarpsPerCta, BGK_STAGE2_MINCTAS) k_sta
             }
             // BGK source towards the conservative Maxwellian and the Shu-Osher combination, two nodes at
             // a time (exponent a + b.m + q |m|^2, or per-axis q on grids of several spacings)
-            const float gm = __ldg(A.gmask + slot);
+            const float gm = gm_c;
             const float cg = A.kg * gm;
             const float mm0 = m0 * m0, mm1 = m1 * m1, mm2 = m2 * m2, mms = mm0 + mm1 + mm2;
             const unsigned long long M0 = pack2(m0, m0), M1 = pack2(m1, m1), M2 = pack2(m2, m2);
