@@ -263,11 +263,25 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE
     };
     prefetch(vl0, 0);
     prefetch_fn(vl0);
+    // the tile's grid indices and padding mask, loaded one tile ahead into registers
+    float mi_n[3], gm_n = 0.f;
+    auto load_rows = [&](int vt) {
+        const int sl = vt * kWarp + lane;
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            mi_n[d] = __ldg(A.mi + d * A.nslots + sl);
+        gm_n = __ldg(A.gmask + sl);
+    };
+    if (vl0 < vl1)
+        load_rows(A.vt0 + vl0);
 
     for (int vl = vl0; vl < vl1; vl++) {
         const int vt = A.vt0 + vl;
         const int slot = vt * kWarp + lane;
         const int b = (vl - vl0) & 1;
+        const float m0 = mi_n[0], m1 = mi_n[1], m2 = mi_n[2], gm_c = gm_n;
+        if (vl + 1 < vl1)
+            load_rows(vt + 1);
         // the other buffer was last read before the previous tile's B2, which every warp has passed;
         // pending groups: tile vl, f^n vl (issued last tile), then tile vl + 1
         if (vl + 1 < vl1) {
@@ -277,7 +291,6 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE
             cp_wait<0>();
         }
         __syncwarp();
-        const float m0 = __ldg(A.mi + slot), m1 = __ldg(A.mi + A.nslots + slot), m2 = __ldg(A.mi + 2 * A.nslots + slot);
         const float x0 = fmaf(A.vs[0], m0, A.vc[0]), x1 = fmaf(A.vs[1], m1, A.vc[1]), x2 = fmaf(A.vs[2], m2, A.vc[2]);
         float f[NQ];
 #pragma unroll
@@ -474,7 +487,7 @@ __global__ void __launch_bounds__(kWarp *N1, (N1 >= 4 ? (GEN || CURV ? BGK_STAGE
                 __syncthreads();  // B2: z-sums complete
             }
             // BGK source towards the conservative Maxwellian, Shu-Osher combination, store
-            const float gm = __ldg(A.gmask + slot);
+            const float gm = gm_c;
             const float cg = A.kg * gm, cf = bdt * gm;
             const float xs = x0 * x0 + x1 * x1 + x2 * x2;
             // squared indices (exact); the lean form has one spacing on every axis and needs their sum
